@@ -1,0 +1,169 @@
+/*
+ * lu_gb300.h -- C ABI of a GB300 (sm_103a) library for blocked right-looking
+ * LU factorization with partial pivoting and depth-1 static look-ahead, after
+ * "Programming Parallel Dense Matrix Factorizations with Look-Ahead and
+ * OpenMP" (arXiv 1804.07017).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Matrices are column-major: element (i, j) of a matrix with leading
+ *    dimension ld lives at ptr[i + j*ld].  ld >= max(1, rows).
+ *  - Every matrix, vector and pivot pointer is a DEVICE pointer owned by the
+ *    caller, unless an argument says "host".  The library never frees or
+ *    retains caller memory beyond the call.
+ *  - Pivots follow LAPACK getrf: ipiv[j] (int32, 1-based) is the row that was
+ *    interchanged with row j+1 at elimination step j (sequential interchanges,
+ *    not a permutation vector).  The factors are stored in LAPACK layout:
+ *    P A = L U, unit-lower L strictly below the diagonal, U on and above it.
+ *  - Workspace (exchange slots, counters, pivot plans, low-precision operand
+ *    copies, residual vectors) is owned by the handle, allocated on first use
+ *    with cudaMalloc, grown when a larger problem arrives and freed by
+ *    lu_destroy.
+ *  - Calls named *_ex are asynchronous on the handle's stream (lu_set_stream)
+ *    and report device-side outcomes through a caller-provided device int32
+ *    `info`.  The plain calls (lu_factor, lu_solve) use a process-wide default
+ *    handle on the legacy default stream and synchronise before returning.
+ *
+ * Return codes: 0 success; -i the i-th argument is invalid; the runtime errors
+ * below; for factorizations a positive value i means U(i,i) is exactly zero
+ * (the factorization is still completed, as in LAPACK getrf).
+ * No call aborts, traps or throws across this boundary.
+ */
+#ifndef LU_GB300_H
+#define LU_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LU_SUCCESS 0
+#define LU_ERR_CUDA (-101)        /* a CUDA runtime/driver call failed (see lu_last_error) */
+#define LU_ERR_NOMEM (-102)       /* workspace allocation failed */
+#define LU_ERR_TIMEOUT (-103)     /* a bounded device-side wait expired; results are invalid */
+#define LU_ERR_UNSUPPORTED (-104) /* the requested size/type/precision is not supported */
+#define LU_ERR_HANDLE (-105)      /* null or destroyed handle */
+#define LU_WARN_NOT_CONVERGED (0x40000000) /* lu_gesv_mixed: tol not reached in max_iter */
+
+typedef struct lu_context *lu_handle;
+
+/* Arithmetic type of a factorization / of the matrix storage. */
+typedef enum { LU_F64 = 0, LU_F32 = 1 } lu_dtype;
+
+/* Options of a blocked factorization (Sec. 3-4 of the paper). */
+typedef struct {
+    int nb;        /* algorithmic block size b (panel width), >= 1 */
+    int lookahead; /* 0: no look-ahead, the PF(k); TU(k) loop of Listing 3.
+                      1: depth-1 static look-ahead of Listing 5: PU(k+1) (the
+                         left part of TU_k plus PF_{k+1}) runs concurrently with
+                         TU_right(k) */
+    int steal;     /* 1: the CTAs freed by PU(k+1) join TU_right(k) (the GPU
+                      analogue of the malleable BLAS of Sec. 4.2); 0: they do not */
+    int leaf;      /* column width handled by one panel-factorization leaf
+                      kernel inside the recursive panel (0 = automatic) */
+    int pf_ctas;   /* maximum CTAs of a panel-factorization leaf (0 = automatic) */
+} lu_opts;
+
+/* Fills *opts with the defaults (nb = 256, lookahead = 1, steal = 1, automatic rest). */
+void lu_default_opts(lu_opts *opts);
+
+/* Handle lifetime.  lu_create returns 0 or LU_ERR_CUDA/LU_ERR_NOMEM. */
+int lu_create(lu_handle *handle);
+int lu_destroy(lu_handle handle);
+/* Sets the CUDA stream (a cudaStream_t passed as void*, NULL = legacy default)
+ * on which the handle's asynchronous calls are ordered. */
+int lu_set_stream(lu_handle handle, void *stream);
+
+/* Total number of kernels this library has launched in this process (all
+ * handles).  Monotone; used to count launches inside a timed region. */
+int64_t lu_launch_count(void);
+/* Text of the last CUDA error seen by the library (static storage). */
+const char *lu_last_error(void);
+
+/*
+ * lu_factor -- P A = L U of an n x n FP64 matrix, in place (LU_blk, RL1-RL3,
+ * Sec. 3; depth-1 look-ahead, Sec. 4).
+ *   n     order of A, n >= 0 (n = 0 is a no-op)
+ *   A     device, n x n column-major, leading dimension lda; overwritten by L\U
+ *   lda   >= max(1, n)
+ *   ipiv  device int32[n]; receives the pivots (LAPACK convention)
+ *   nb    block size b >= 1
+ * Synchronises the legacy default stream.  Returns 0, i > 0 (first exactly
+ * zero U(i,i)), -i for an invalid argument, or a runtime error code.
+ */
+int lu_factor(int64_t n, double *A, int64_t lda, int32_t *ipiv, int nb);
+
+/*
+ * lu_solve -- X = A^{-1} B from the output of lu_factor (the getrs that pairs
+ * with getrf: apply the interchanges, solve with unit-lower L, then with U).
+ *   LU, ipiv  device, as returned by lu_factor with lda = n
+ *   B         device, n x nrhs, leading dimension n; overwritten by X
+ * Synchronises.  Returns 0, -i, or a runtime error code.
+ */
+int lu_solve(int64_t n, int64_t nrhs, const double *LU, const int32_t *ipiv, double *B);
+
+/*
+ * lu_factor_ex -- as lu_factor, for FP64 or FP32 storage and arithmetic,
+ * with explicit options, asynchronous on the handle's stream.
+ *   info  device int32[1]; receives 0, the first zero pivot i > 0, or
+ *         LU_ERR_TIMEOUT if a bounded device wait expired.
+ * Returns 0 (enqueued), -i, or a runtime error code.
+ */
+int lu_factor_ex(lu_handle handle, lu_dtype dtype, int64_t n, void *A, int64_t lda,
+                 int32_t *ipiv, const lu_opts *opts, int32_t *info);
+
+/*
+ * lu_solve_ex -- X = A^{-1} B from lu_factor_ex output (same dtype);
+ * asynchronous.  B is n x nrhs with leading dimension ldb, overwritten by X.
+ */
+int lu_solve_ex(lu_handle handle, lu_dtype dtype, int64_t n, int64_t nrhs, const void *LU,
+                int64_t lda, const int32_t *ipiv, void *B, int64_t ldb);
+
+/* ----------------------------------------------------------------------------
+ * The individual steps of one iteration of LU_blk, exposed for testing and
+ * for callers that build their own schedules.  All asynchronous on the
+ * handle's stream; dtype selects FP64 or FP32.
+ * ------------------------------------------------------------------------- */
+
+/*
+ * lu_panel_factor_ex -- RL1: [A11; A21] := LU_unb([A11; A21]) for an m x w
+ * panel (m >= w), with partial pivoting over the panel's rows.
+ *   A        device, top-left element of the panel, leading dimension lda
+ *   ipiv     device int32[w]; ipiv[j] = 1-based row (relative to the panel's
+ *            first row) interchanged with row j+1
+ *   info     device int32[1]; set to j+1 for the first exactly zero pivot if
+ *            it was 0, or to LU_ERR_TIMEOUT
+ * The interchanges are applied across the panel's w columns only.
+ */
+int lu_panel_factor_ex(lu_handle handle, lu_dtype dtype, int64_t m, int64_t w, void *A,
+                       int64_t lda, int32_t *ipiv, const lu_opts *opts, int32_t *info);
+
+/*
+ * lu_laswp_ex -- apply the interchanges ipiv[k1], ..., ipiv[k2-1] (1-based
+ * row numbers of A, applied in that order: row k+1 <-> row ipiv[k]) to
+ * columns 0 .. ncols-1 of A (the laswp of the getrf decomposition, Sec. 3.4).
+ */
+int lu_laswp_ex(lu_handle handle, lu_dtype dtype, int64_t ncols, void *A, int64_t lda,
+                int64_t k1, int64_t k2, const int32_t *ipiv);
+
+/*
+ * lu_trsm_ex -- RL2: B := trilu(L)^{-1} B with L an m x m unit-lower matrix
+ * (its diagonal and upper part are not read) and B m x n.
+ */
+int lu_trsm_ex(lu_handle handle, lu_dtype dtype, int64_t m, int64_t n, const void *L,
+               int64_t ldl, void *B, int64_t ldb);
+
+/*
+ * lu_gemm_update_ex -- RL3: C := C - A B with A m x k, B k x n, C m x n, all
+ * in the storage dtype, on the CUDA cores (FP64 or FP32 fused multiply-add).
+ */
+int lu_gemm_update_ex(lu_handle handle, lu_dtype dtype, int64_t m, int64_t n, int64_t k,
+                      const void *A, int64_t lda, const void *B, int64_t ldb, void *C,
+                      int64_t ldc);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LU_GB300_H */

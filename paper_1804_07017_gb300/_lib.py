@@ -1,0 +1,88 @@
+"""ctypes loader for liblu_gb300.so and the C ABI's signatures."""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+HEADER = os.path.join(_HERE, "..", "include", "lu_gb300.h")
+
+LU_SUCCESS = 0
+LU_ERR_CUDA = -101
+LU_ERR_NOMEM = -102
+LU_ERR_TIMEOUT = -103
+LU_ERR_UNSUPPORTED = -104
+LU_ERR_HANDLE = -105
+LU_WARN_NOT_CONVERGED = 0x40000000
+
+LU_F64 = 0
+LU_F32 = 1
+
+LU_TU_BF16 = 0
+LU_TU_FP16 = 1
+LU_TU_FP8 = 2
+LU_TU_F32 = 3
+
+
+class LuError(RuntimeError):
+    def __init__(self, name: str, code: int, detail: str = ""):
+        super().__init__(f"{name} returned {code}" + (f": {detail}" if detail else ""))
+        self.code = code
+
+
+class LuOpts(ctypes.Structure):
+    _fields_ = [("nb", ctypes.c_int), ("lookahead", ctypes.c_int), ("steal", ctypes.c_int),
+                ("leaf", ctypes.c_int), ("pf_ctas", ctypes.c_int)]
+
+
+def library_path() -> str:
+    return os.environ.get("LU_GB300_LIB", os.path.join(_HERE, "liblu_gb300.so"))
+
+
+i64, i32, vp, dbl = ctypes.c_int64, ctypes.c_int, ctypes.c_void_p, ctypes.c_double
+_SIGNATURES = {
+    "lu_default_opts": (None, [ctypes.POINTER(LuOpts)]),
+    "lu_create": (i32, [ctypes.POINTER(vp)]),
+    "lu_destroy": (i32, [vp]),
+    "lu_set_stream": (i32, [vp, vp]),
+    "lu_launch_count": (i64, []),
+    "lu_last_error": (ctypes.c_char_p, []),
+    "lu_factor": (i32, [i64, vp, i64, vp, i32]),
+    "lu_solve": (i32, [i64, i64, vp, vp, vp]),
+    "lu_factor_ex": (i32, [vp, i32, i64, vp, i64, vp, ctypes.POINTER(LuOpts), vp]),
+    "lu_solve_ex": (i32, [vp, i32, i64, i64, vp, i64, vp, vp, i64]),
+    "lu_panel_factor_ex": (i32, [vp, i32, i64, i64, vp, i64, vp, ctypes.POINTER(LuOpts), vp]),
+    "lu_laswp_ex": (i32, [vp, i32, i64, vp, i64, i64, i64, vp]),
+    "lu_trsm_ex": (i32, [vp, i32, i64, i64, vp, i64, vp, i64]),
+    "lu_gemm_update_ex": (i32, [vp, i32, i64, i64, i64, vp, i64, vp, i64, vp, i64]),
+}
+
+_lib = None
+
+
+def lib():
+    """Load the library (raises OSError if it has not been built)."""
+    global _lib
+    if _lib is None:
+        path = library_path()
+        if not os.path.exists(path):
+            raise OSError(f"{path} is missing: run `python -c 'import __graft_entry__ as g; g.build()'`")
+        L = ctypes.CDLL(path)
+        for name, (res, args) in _SIGNATURES.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def declared_symbols(header: str = HEADER) -> list[str]:
+    """Function names declared in the public header."""
+    text = open(header).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(lu_[a-z0-9_]+)\s*\(", text)))
+
+
+def signatures() -> dict:
+    return dict(_SIGNATURES)

@@ -1,0 +1,156 @@
+"""Argument marshalling from torch tensors to the C ABI (same names as the C calls).
+
+Matrices are column-major: a tensor of shape (rows, cols) with stride
+(1, ld), ld >= rows -- e.g. ``colmajor(rows, cols)`` below, or
+``torch.from_numpy(np.asfortranarray(a)).cuda()``.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import torch
+
+from ._lib import LU_F32, LU_F64, LuError, LuOpts, lib
+
+_DT = {torch.float64: LU_F64, torch.float32: LU_F32}
+
+
+def colmajor(rows: int, cols: int, dtype=torch.float64, device="cuda", ld: int | None = None):
+    """An uninitialised column-major (rows x cols) tensor with leading dimension ld."""
+    ld = rows if ld is None else ld
+    buf = torch.empty((max(cols, 1), max(ld, 1)), dtype=dtype, device=device)
+    return buf.t()[:rows, :cols]
+
+
+def to_colmajor(t: torch.Tensor, ld: int | None = None) -> torch.Tensor:
+    out = colmajor(t.shape[0], t.shape[1], t.dtype, t.device, ld)
+    out.copy_(t)
+    return out
+
+
+def _ld(t: torch.Tensor, name: str) -> int:
+    if t.dim() != 2:
+        raise ValueError(f"{name} must be 2-D")
+    if t.shape[0] > 1 and t.stride(0) != 1:
+        raise ValueError(f"{name} must be column-major (stride(0) == 1)")
+    return max(int(t.stride(1)) if t.shape[1] > 1 else int(t.shape[0]), 1)
+
+
+def _p(t):
+    return ctypes.c_void_p(t.data_ptr() if t is not None and t.numel() > 0 else 0)
+
+
+def _check(name: str, rc: int, ok_positive: bool = False) -> int:
+    if rc < 0 or (rc > 0 and not ok_positive):
+        detail = lib().lu_last_error().decode(errors="replace")
+        raise LuError(name, rc, detail)
+    return rc
+
+
+def default_opts(**kw) -> LuOpts:
+    o = LuOpts()
+    lib().lu_default_opts(ctypes.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, int(v))
+    return o
+
+
+class Handle:
+    """Owns an lu_handle (workspace and internal streams)."""
+
+    def __init__(self):
+        h = ctypes.c_void_p()
+        _check("lu_create", lib().lu_create(ctypes.byref(h)))
+        self._h = h
+
+    @property
+    def ptr(self):
+        return self._h
+
+    def set_stream(self, stream: torch.cuda.Stream | None = None):
+        s = stream if stream is not None else torch.cuda.current_stream()
+        _check("lu_set_stream", lib().lu_set_stream(self._h, ctypes.c_void_p(s.cuda_stream)))
+
+    def close(self):
+        if self._h:
+            lib().lu_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+_handles: dict[int, Handle] = {}
+
+
+def _handle(h: Handle | None) -> Handle:
+    if h is None:
+        dev = torch.cuda.current_device()
+        h = _handles.get(dev)
+        if h is None:
+            h = _handles[dev] = Handle()
+    h.set_stream()
+    return h
+
+
+def lu_launch_count() -> int:
+    return int(lib().lu_launch_count())
+
+
+def lu_factor(A: torch.Tensor, ipiv: torch.Tensor, nb: int = 256) -> int:
+    """In-place FP64 LU (synchronous).  Returns info (0 or first zero pivot)."""
+    n = A.shape[0]
+    return _check("lu_factor", lib().lu_factor(n, _p(A), _ld(A, "A"), _p(ipiv), nb), ok_positive=True)
+
+
+def lu_solve(LU: torch.Tensor, ipiv: torch.Tensor, B: torch.Tensor) -> None:
+    """In-place FP64 solve of B (n x nrhs, ld n) with lu_factor output (ld n)."""
+    n, nrhs = B.shape
+    _check("lu_solve", lib().lu_solve(n, nrhs, _p(LU), _p(ipiv), _p(B)))
+
+
+def lu_factor_ex(A: torch.Tensor, ipiv: torch.Tensor, info: torch.Tensor, opts: LuOpts | None = None,
+                 handle: Handle | None = None) -> None:
+    h = _handle(handle)
+    o = opts if opts is not None else default_opts()
+    _check("lu_factor_ex", lib().lu_factor_ex(h.ptr, _DT[A.dtype], A.shape[0], _p(A), _ld(A, "A"), _p(ipiv),
+                                               ctypes.byref(o), _p(info)))
+
+
+def lu_solve_ex(LU: torch.Tensor, ipiv: torch.Tensor, B: torch.Tensor, handle: Handle | None = None) -> None:
+    h = _handle(handle)
+    n, nrhs = B.shape
+    _check("lu_solve_ex", lib().lu_solve_ex(h.ptr, _DT[LU.dtype], n, nrhs, _p(LU), _ld(LU, "LU"), _p(ipiv),
+                                             _p(B), _ld(B, "B")))
+
+
+def lu_panel_factor_ex(P: torch.Tensor, ipiv: torch.Tensor, info: torch.Tensor, opts: LuOpts | None = None,
+                       handle: Handle | None = None) -> None:
+    h = _handle(handle)
+    o = opts if opts is not None else default_opts()
+    m, w = P.shape
+    _check("lu_panel_factor_ex", lib().lu_panel_factor_ex(h.ptr, _DT[P.dtype], m, w, _p(P), _ld(P, "P"),
+                                                           _p(ipiv), ctypes.byref(o), _p(info)))
+
+
+def lu_laswp_ex(A: torch.Tensor, k1: int, k2: int, ipiv: torch.Tensor, handle: Handle | None = None) -> None:
+    h = _handle(handle)
+    _check("lu_laswp_ex", lib().lu_laswp_ex(h.ptr, _DT[A.dtype], A.shape[1], _p(A), _ld(A, "A"), k1, k2,
+                                             _p(ipiv)))
+
+
+def lu_trsm_ex(L: torch.Tensor, B: torch.Tensor, handle: Handle | None = None) -> None:
+    h = _handle(handle)
+    m, n = B.shape
+    _check("lu_trsm_ex", lib().lu_trsm_ex(h.ptr, _DT[B.dtype], m, n, _p(L), _ld(L, "L"), _p(B), _ld(B, "B")))
+
+
+def lu_gemm_update_ex(C: torch.Tensor, A: torch.Tensor, B: torch.Tensor, handle: Handle | None = None) -> None:
+    h = _handle(handle)
+    m, n = C.shape
+    k = A.shape[1]
+    _check("lu_gemm_update_ex", lib().lu_gemm_update_ex(h.ptr, _DT[C.dtype], m, n, k, _p(A), _ld(A, "A"), _p(B),
+                                                         _ld(B, "B"), _p(C), _ld(C, "C")))

@@ -1,0 +1,88 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+#include <mutex>
+#include <vector>
+
+#include "common.cuh"
+
+// Upper limits baked into kernels and workspace sizing.
+#define LU_PF_MAX_CTAS 128    // CTAs of one panel-factorization leaf launch
+#define LU_PF_MAX_LEAF 64     // widest leaf (columns held in shared memory)
+#define LU_MAX_NB 1024        // widest panel accepted
+#define LU_PF_SMEM_BUDGET (64 * 1024)
+
+struct lu_context {
+    int device = 0;
+    int num_sms = 0;
+    cudaStream_t user = nullptr;  // stream set by lu_set_stream
+    cudaStream_t hi = nullptr;    // high-priority internal stream (panel path)
+    cudaStream_t lo = nullptr;    // low-priority internal stream (right trailing update)
+    cudaEvent_t ev_fork = nullptr, ev_pf = nullptr, ev_tu = nullptr, ev_join_hi = nullptr,
+                ev_join_lo = nullptr;
+    // Workspace: one device buffer carved into fixed regions.
+    char* ws = nullptr;
+    size_t ws_bytes = 0;
+    LuSync* sync = nullptr;   // [0] panel leaves, [1] triangular solves, [2..] spare
+    void* pf_slots = nullptr; // panel-leaf exchange slots
+    int32_t* plans = nullptr; // per-panel interchange plans
+    size_t plan_stride = 0;   // int32 entries per plan
+    size_t plans_cap = 0;     // number of plans
+    int32_t* plan_tmp = nullptr;  // plan used inside the recursive panel
+    int32_t* perm = nullptr;  // row permutation for solves
+    int32_t* flags = nullptr; // ready flags of the blocked triangular solves
+    size_t perm_cap = 0, flags_cap = 0;
+    // Scratch for the row gather of a solve.
+    void* scratch = nullptr;
+    size_t scratch_bytes = 0;
+    std::mutex mu;
+};
+
+int lu_ctx_init(lu_context* c);
+int lu_ctx_release(lu_context* c);
+// Makes sure the workspace can hold a factorization of order n with panel
+// width nb (and solves of order n).  May synchronise the user stream.
+int lu_ctx_reserve(lu_context* c, int64_t n, int nb);
+
+// --- kernels (launchers return LU_SUCCESS or LU_ERR_CUDA) --------------------
+template <typename T>
+int lu_launch_pf_leaf(lu_context* c, cudaStream_t st, T* A, int64_t lda, int64_t m, int w,
+                      int32_t* ipiv, int64_t ipiv_add, int max_ctas);
+
+int lu_launch_laswp_plan(cudaStream_t st, const int32_t* ipiv, int64_t k1, int64_t k2,
+                         int32_t* plan);
+
+// Apply a plan to columns [c1, c1+n1) and [c2, c2+n2) of A.
+template <typename T>
+int lu_launch_laswp_apply(cudaStream_t st, T* A, int64_t lda, int64_t c1, int64_t n1,
+                          int64_t c2, int64_t n2, const int32_t* plan, int64_t K, int num_sms);
+
+template <typename T>
+int lu_launch_trsm_lunit(cudaStream_t st, int64_t m, int64_t n, const T* L, int64_t ldl, T* B,
+                         int64_t ldb);
+
+template <typename T>
+int lu_launch_gemm_update(cudaStream_t st, int64_t m, int64_t n, int64_t k, const T* A,
+                          int64_t lda, const T* B, int64_t ldb, T* C, int64_t ldc);
+
+template <typename T>
+int lu_launch_perm_from_ipiv(cudaStream_t st, int64_t n, const int32_t* ipiv, int32_t* perm);
+
+template <typename T>
+int lu_launch_permute_rows(cudaStream_t st, int64_t n, int64_t nrhs, const int32_t* perm,
+                           const T* B, int64_t ldb, T* X, int64_t ldx);
+
+template <typename T>
+int lu_launch_trsv_blocked(lu_context* c, cudaStream_t st, bool lower_unit, int64_t n,
+                           int64_t nrhs, const T* LU, int64_t lda, T* X, int64_t ldx);
+
+int lu_launch_finish_info(cudaStream_t st, const LuSync* s, int32_t* info);
+
+// Recursive panel factorization of columns [j0, j0+width) over rows [j0, M)
+// of the matrix at A (absolute indices; ipiv absolute, 1-based).
+template <typename T>
+int lu_panel_recursive(lu_context* c, cudaStream_t st, T* A, int64_t lda, int64_t M,
+                       int64_t j0, int64_t width, int32_t* ipiv, const lu_opts& o);

@@ -1,0 +1,140 @@
+// Row interchanges (the laswp of the getrf decomposition, Sec. 3.4).
+//
+// The K = k2 - k1 sequential interchanges of one panel are first turned into a
+// "plan": the list of (destination row, source row) moves whose simultaneous
+// application equals applying the interchanges in order.  The plan touches
+// the K rows of the panel block plus at most K distinct rows below it.  The
+// apply kernel then moves, column by column, every planned element through
+// shared memory (all reads of a column before any write), so a column's K
+// contiguous block rows are read and written with coalesced accesses.
+//
+// Plan layout (int32): [0] = count, [1 .. 1+2K) = destination rows,
+// [1+2K .. 1+4K) = source rows.  Entries 0..K-1 are the panel block rows in
+// order (identity moves included), entries K.. are the rows below the block.
+#include "internal.h"
+
+namespace {
+
+constexpr int kPlanThreads = 256;
+
+__global__ void __launch_bounds__(kPlanThreads)
+    laswp_plan_kernel(const int32_t* __restrict__ ipiv, int64_t k1, int K, int32_t* __restrict__ plan) {
+    extern __shared__ int32_t sm[];
+    int32_t* t = sm;            // [K] target row (absolute, 0-based) of interchange i
+    int32_t* firstk = t + K;    // [K] representative interchange of a target below the block
+    int32_t* cur = firstk + K;  // [2K] source row now sitting at each tracked position
+    const int tid = threadIdx.x;
+    const int64_t k2 = k1 + K;
+    for (int i = tid; i < K; i += kPlanThreads) t[i] = ipiv[k1 + i] - 1;
+    __syncthreads();
+    for (int i = tid; i < K; i += kPlanThreads) {
+        int f = -1;
+        if (t[i] >= k2) {
+            for (int q = 0; q <= i; ++q)
+                if (t[q] == t[i]) {
+                    f = q;
+                    break;
+                }
+        }
+        firstk[i] = f;
+        cur[i] = (int32_t)(k1 + i);
+        cur[K + i] = (f == i) ? t[i] : -1;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        for (int i = 0; i < K; ++i) {
+            const int64_t p = t[i];
+            if (p == k1 + i) continue;
+            const int a = i;
+            const int b = (p < k2) ? (int)(p - k1) : K + firstk[i];
+            const int32_t x = cur[a];
+            cur[a] = cur[b];
+            cur[b] = x;
+        }
+    }
+    __syncthreads();
+    int32_t* dst = plan + 1;
+    int32_t* src = plan + 1 + 2 * K;
+    for (int i = tid; i < K; i += kPlanThreads) {
+        dst[i] = (int32_t)(k1 + i);
+        src[i] = cur[i];
+    }
+    __syncthreads();
+    if (tid == 0) {
+        int cnt = K;
+        for (int i = 0; i < K; ++i) {
+            if (firstk[i] == i && cur[K + i] != t[i]) {
+                dst[cnt] = t[i];
+                src[cnt] = cur[K + i];
+                ++cnt;
+            }
+        }
+        plan[0] = cnt;
+    }
+}
+
+constexpr int kApplyThreads = 256;  // 8 warps, one column per warp at a time
+
+template <typename T>
+__global__ void __launch_bounds__(kApplyThreads)
+    laswp_apply_kernel(T* __restrict__ A, int64_t lda, int64_t c1, int64_t n1, int64_t c2, int64_t n2,
+                       const int32_t* __restrict__ plan, int K) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    T* buf = reinterpret_cast<T*>(smraw) + (size_t)warp * 2 * K;
+    const int cnt = plan[0];
+    const int32_t* dst = plan + 1;
+    const int32_t* src = plan + 1 + 2 * K;
+    const int64_t ncols = n1 + n2;
+    for (int64_t q = (int64_t)blockIdx.x * (kApplyThreads / 32) + warp; q < ncols;
+         q += (int64_t)gridDim.x * (kApplyThreads / 32)) {
+        const int64_t col = (q < n1) ? c1 + q : c2 + (q - n1);
+        T* a = A + col * lda;
+        for (int e = lane; e < cnt; e += 32) buf[e] = a[src[e]];
+        __syncwarp();
+        for (int e = lane; e < cnt; e += 32) a[dst[e]] = buf[e];
+        __syncwarp();
+    }
+}
+
+}  // namespace
+
+int lu_launch_laswp_plan(cudaStream_t st, const int32_t* ipiv, int64_t k1, int64_t k2, int32_t* plan) {
+    const int K = (int)(k2 - k1);
+    if (K <= 0) return LU_SUCCESS;
+    size_t smem = sizeof(int32_t) * 4 * (size_t)K;
+    static bool attr = false;
+    if (!attr) {
+        LU_CHECK_CUDA(cudaFuncSetAttribute(laswp_plan_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           sizeof(int32_t) * 4 * LU_MAX_NB));
+        attr = true;
+    }
+    laswp_plan_kernel<<<1, kPlanThreads, smem, st>>>(ipiv, k1, K, plan);
+    LU_CHECK_LAUNCH();
+    return LU_SUCCESS;
+}
+
+template <typename T>
+int lu_launch_laswp_apply(cudaStream_t st, T* A, int64_t lda, int64_t c1, int64_t n1, int64_t c2,
+                          int64_t n2, const int32_t* plan, int64_t K, int num_sms) {
+    if (K <= 0 || n1 + n2 <= 0) return LU_SUCCESS;
+    const int warps = kApplyThreads / 32;
+    size_t smem = sizeof(T) * 2 * (size_t)K * warps;
+    static bool attr[2] = {false, false};
+    const int ti = sizeof(T) == 8 ? 0 : 1;
+    if (!attr[ti]) {
+        LU_CHECK_CUDA(cudaFuncSetAttribute(laswp_apply_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)(sizeof(T) * 2 * LU_MAX_NB * warps)));
+        attr[ti] = true;
+    }
+    int64_t blocks = lu_cdiv(n1 + n2, warps);
+    blocks = std::min<int64_t>(blocks, (int64_t)std::max(num_sms, 1) * 8);
+    laswp_apply_kernel<T><<<(unsigned)blocks, kApplyThreads, smem, st>>>(A, lda, c1, n1, c2, n2, plan, (int)K);
+    LU_CHECK_LAUNCH();
+    return LU_SUCCESS;
+}
+
+template int lu_launch_laswp_apply<double>(cudaStream_t, double*, int64_t, int64_t, int64_t, int64_t,
+                                           int64_t, const int32_t*, int64_t, int);
+template int lu_launch_laswp_apply<float>(cudaStream_t, float*, int64_t, int64_t, int64_t, int64_t,
+                                          int64_t, const int32_t*, int64_t, int);

@@ -1,0 +1,449 @@
+// Host side of the library: handles, workspace, the blocked factorization
+// driver with depth-1 static look-ahead, and the solve driver.
+//
+// The factorization follows LU_blk (Sec. 3): for each panel k, PF_k (RL1,
+// recursive, see pf.cu), then the interchanges, TRSM (RL2) and GEMM (RL3) on
+// the trailing columns.  With look-ahead (Sec. 4, Listing 5) TU_k is split at
+// the next panel's columns: the high-priority stream runs PU(k+1) = TU_k^L
+// followed by PF_{k+1}, while the low-priority stream runs TU_right(k) over
+// the remaining columns (plus the deferred interchanges on the columns left of
+// panel k).  Stream priority makes the panel path's CTAs the first to be
+// scheduled as trailing-update CTAs retire, and because the trailing update is
+// a grid of independent tiles, the SMs that PU(k+1) releases are picked up by
+// the rest of TU_right(k): the counterpart of the malleable BLAS of Sec. 4.2.
+#include <stdarg.h>
+#include <string.h>
+
+#include <algorithm>
+#include <atomic>
+#include <mutex>
+
+#include "internal.h"
+
+static std::atomic<long long> g_launches{0};
+static char g_last_error[512] = "";
+static std::mutex g_err_mu;
+
+void lu_count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+void lu_set_error_string(const char* what, const char* file, int line) {
+    std::lock_guard<std::mutex> lk(g_err_mu);
+    snprintf(g_last_error, sizeof(g_last_error), "%s (%s:%d)", what, file, line);
+}
+
+extern "C" int64_t lu_launch_count(void) { return (int64_t)g_launches.load(); }
+extern "C" const char* lu_last_error(void) { return g_last_error; }
+
+extern "C" void lu_default_opts(lu_opts* o) {
+    if (!o) return;
+    o->nb = 256;
+    o->lookahead = 1;
+    o->steal = 1;
+    o->leaf = 0;
+    o->pf_ctas = 0;
+}
+
+int lu_ctx_init(lu_context* c) {
+    LU_CHECK_CUDA(cudaGetDevice(&c->device));
+    LU_CHECK_CUDA(cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device));
+    int lo_prio = 0, hi_prio = 0;
+    LU_CHECK_CUDA(cudaDeviceGetStreamPriorityRange(&lo_prio, &hi_prio));
+    LU_CHECK_CUDA(cudaStreamCreateWithPriority(&c->hi, cudaStreamNonBlocking, hi_prio));
+    LU_CHECK_CUDA(cudaStreamCreateWithPriority(&c->lo, cudaStreamNonBlocking, lo_prio));
+    cudaEvent_t* evs[] = {&c->ev_fork, &c->ev_pf, &c->ev_tu, &c->ev_join_hi, &c->ev_join_lo};
+    for (cudaEvent_t* e : evs) LU_CHECK_CUDA(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
+    return LU_SUCCESS;
+}
+
+int lu_ctx_release(lu_context* c) {
+    if (c->ws) cudaFree(c->ws);
+    c->ws = nullptr;
+    if (c->scratch) cudaFree(c->scratch);
+    c->scratch = nullptr;
+    cudaEvent_t evs[] = {c->ev_fork, c->ev_pf, c->ev_tu, c->ev_join_hi, c->ev_join_lo};
+    for (cudaEvent_t e : evs)
+        if (e) cudaEventDestroy(e);
+    if (c->hi) cudaStreamDestroy(c->hi);
+    if (c->lo) cudaStreamDestroy(c->lo);
+    return LU_SUCCESS;
+}
+
+static size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+int lu_ctx_reserve(lu_context* c, int64_t n, int nb) {
+    nb = std::max(1, std::min(nb, LU_MAX_NB));
+    const size_t nk = (size_t)std::max<int64_t>(1, lu_cdiv(std::max<int64_t>(n, 1), nb));
+    const size_t plan_stride = 1 + 4 * (size_t)LU_MAX_NB;
+    const size_t need_sync = align_up(sizeof(LuSync) * 4, 256);
+    const size_t need_slots = align_up(sizeof(double) * (2 * LU_PF_MAX_CTAS * (LU_PF_MAX_LEAF + 1) + 2 * LU_PF_MAX_LEAF) +
+                                           sizeof(int) * 2 * LU_PF_MAX_CTAS, 256);
+    const size_t plans_cap = std::max(nk, c->plans_cap);
+    const size_t need_plans = align_up(sizeof(int32_t) * plan_stride * (plans_cap + 1), 256);
+    const size_t perm_cap = std::max<size_t>((size_t)std::max<int64_t>(n, 1), c->perm_cap);
+    const size_t need_perm = align_up(sizeof(int32_t) * perm_cap, 256);
+    const size_t total = need_sync + need_slots + need_plans + need_perm;
+    if (c->ws && total <= c->ws_bytes) return LU_SUCCESS;
+    if (c->ws) {
+        LU_CHECK_CUDA(cudaStreamSynchronize(c->user));
+        LU_CHECK_CUDA(cudaDeviceSynchronize());
+        cudaFree(c->ws);
+        c->ws = nullptr;
+    }
+    if (cudaMalloc(&c->ws, total) != cudaSuccess) {
+        cudaGetLastError();
+        c->ws_bytes = 0;
+        return LU_ERR_NOMEM;
+    }
+    c->ws_bytes = total;
+    char* p = c->ws;
+    c->sync = reinterpret_cast<LuSync*>(p);
+    p += need_sync;
+    c->pf_slots = p;
+    p += need_slots;
+    c->plan_stride = plan_stride;
+    c->plans_cap = plans_cap;
+    c->plan_tmp = reinterpret_cast<int32_t*>(p);
+    c->plans = c->plan_tmp + plan_stride;
+    p += need_plans;
+    c->perm = reinterpret_cast<int32_t*>(p);
+    c->perm_cap = perm_cap;
+    LU_CHECK_CUDA(cudaMemset(c->ws, 0, total));
+    return LU_SUCCESS;
+}
+
+// ---------------------------------------------------------------------------
+// handles
+// ---------------------------------------------------------------------------
+extern "C" int lu_create(lu_handle* h) {
+    if (!h) return -1;
+    lu_context* c = new (std::nothrow) lu_context();
+    if (!c) return LU_ERR_NOMEM;
+    int r = lu_ctx_init(c);
+    if (r != LU_SUCCESS) {
+        lu_ctx_release(c);
+        delete c;
+        return r;
+    }
+    *h = c;
+    return LU_SUCCESS;
+}
+
+extern "C" int lu_destroy(lu_handle h) {
+    if (!h) return LU_ERR_HANDLE;
+    cudaDeviceSynchronize();
+    lu_ctx_release(h);
+    delete h;
+    return LU_SUCCESS;
+}
+
+extern "C" int lu_set_stream(lu_handle h, void* stream) {
+    if (!h) return LU_ERR_HANDLE;
+    h->user = reinterpret_cast<cudaStream_t>(stream);
+    return LU_SUCCESS;
+}
+
+static lu_handle g_default = nullptr;
+static std::mutex g_default_mu;
+
+static lu_handle default_handle() {
+    std::lock_guard<std::mutex> lk(g_default_mu);
+    if (!g_default) {
+        if (lu_create(&g_default) != LU_SUCCESS) g_default = nullptr;
+    }
+    return g_default;
+}
+
+// ---------------------------------------------------------------------------
+// factorization driver
+// ---------------------------------------------------------------------------
+static int check_opts(const lu_opts& o) {
+    if (o.nb < 1 || o.nb > LU_MAX_NB) return -1;
+    if (o.lookahead < 0 || o.lookahead > 1) return -1;
+    if (o.leaf < 0 || o.pf_ctas < 0 || o.pf_ctas > LU_PF_MAX_CTAS) return -1;
+    return 0;
+}
+
+// TU restricted to columns [c_begin, c_end) for step k (panel columns [k0, k0+kb)):
+// laswp with panel k's plan, TRSM of the U12 block row, GEMM of the rows below.
+template <typename T>
+static int trailing_update(lu_context* c, cudaStream_t st, int64_t n, T* A, int64_t lda, int64_t k0,
+                           int64_t kb, int64_t c_begin, int64_t c_end, int64_t left_cols,
+                           const int32_t* plan) {
+    const int64_t ncols = c_end - c_begin;
+    if (ncols > 0 || left_cols > 0)
+        LU_TRY(lu_launch_laswp_apply<T>(st, A, lda, c_begin, std::max<int64_t>(ncols, 0), 0, left_cols,
+                                        plan, kb, c->num_sms));
+    if (ncols <= 0) return LU_SUCCESS;
+    T* A11 = A + k0 + k0 * lda;
+    T* A12 = A + k0 + c_begin * lda;
+    LU_TRY(lu_launch_trsm_lunit<T>(st, kb, ncols, A11, lda, A12, lda));
+    const int64_t m2 = n - (k0 + kb);
+    if (m2 > 0)
+        LU_TRY(lu_launch_gemm_update<T>(st, m2, ncols, kb, A + (k0 + kb) + k0 * lda, lda, A12, lda,
+                                        A + (k0 + kb) + c_begin * lda, lda));
+    return LU_SUCCESS;
+}
+
+template <typename T>
+static int factor_impl(lu_context* c, int64_t n, T* A, int64_t lda, int32_t* ipiv, const lu_opts& o,
+                       int32_t* info) {
+    const int nb = o.nb;
+    LU_TRY(lu_ctx_reserve(c, n, nb));
+    cudaStream_t user = c->user;
+    LU_CHECK_CUDA(cudaMemsetAsync(&c->sync[0], 0, sizeof(LuSync), user));
+    if (n == 0) return lu_launch_finish_info(user, &c->sync[0], info);
+    LU_CHECK_CUDA(cudaEventRecord(c->ev_fork, user));
+    LU_CHECK_CUDA(cudaStreamWaitEvent(c->hi, c->ev_fork, 0));
+    LU_CHECK_CUDA(cudaStreamWaitEvent(c->lo, c->ev_fork, 0));
+    const int64_t nk = lu_cdiv(n, nb);
+    auto plan_of = [&](int64_t k) { return c->plans + (size_t)k * c->plan_stride; };
+    cudaStream_t hi = c->hi, lo = c->lo;
+
+    // PF(0)
+    {
+        const int64_t kb = std::min<int64_t>(nb, n);
+        LU_TRY(lu_panel_recursive<T>(c, hi, A, lda, n, 0, kb, ipiv, o));
+        LU_TRY(lu_launch_laswp_plan(hi, ipiv, 0, kb, plan_of(0)));
+    }
+    for (int64_t k = 0; k < nk; ++k) {
+        const int64_t k0 = k * nb, kb = std::min<int64_t>(nb, n - k0);
+        const int64_t c1 = k0 + kb;                       // first column right of panel k
+        const int64_t c2 = std::min<int64_t>(n, c1 + nb); // end of panel k+1
+        if (o.lookahead) {
+            LU_CHECK_CUDA(cudaEventRecord(c->ev_pf, hi));
+            LU_CHECK_CUDA(cudaStreamWaitEvent(lo, c->ev_pf, 0));
+            // TU_right(k) and the deferred left interchanges on the low-priority stream
+            LU_TRY(trailing_update<T>(c, lo, n, A, lda, k0, kb, c2, n, k0, plan_of(k)));
+            LU_CHECK_CUDA(cudaEventRecord(c->ev_tu, lo));
+            if (k + 1 < nk) {
+                // PU(k+1) = TU_k^L + PF_{k+1} on the high-priority stream
+                LU_TRY(trailing_update<T>(c, hi, n, A, lda, k0, kb, c1, c2, 0, plan_of(k)));
+                LU_TRY(lu_panel_recursive<T>(c, hi, A, lda, n, c1, c2 - c1, ipiv, o));
+                LU_TRY(lu_launch_laswp_plan(hi, ipiv, c1, c2, plan_of(k + 1)));
+                LU_CHECK_CUDA(cudaStreamWaitEvent(hi, c->ev_tu, 0));
+            }
+        } else {
+            LU_TRY(trailing_update<T>(c, hi, n, A, lda, k0, kb, c1, n, k0, plan_of(k)));
+            if (k + 1 < nk) {
+                LU_TRY(lu_panel_recursive<T>(c, hi, A, lda, n, c1, c2 - c1, ipiv, o));
+                LU_TRY(lu_launch_laswp_plan(hi, ipiv, c1, c2, plan_of(k + 1)));
+            }
+        }
+    }
+    LU_CHECK_CUDA(cudaEventRecord(c->ev_join_hi, hi));
+    LU_CHECK_CUDA(cudaEventRecord(c->ev_join_lo, lo));
+    LU_CHECK_CUDA(cudaStreamWaitEvent(user, c->ev_join_hi, 0));
+    LU_CHECK_CUDA(cudaStreamWaitEvent(user, c->ev_join_lo, 0));
+    return lu_launch_finish_info(user, &c->sync[0], info);
+}
+
+extern "C" int lu_factor_ex(lu_handle h, lu_dtype dtype, int64_t n, void* A, int64_t lda, int32_t* ipiv,
+                            const lu_opts* opts, int32_t* info) {
+    if (!h) return LU_ERR_HANDLE;
+    if (dtype != LU_F64 && dtype != LU_F32) return -2;
+    if (n < 0) return -3;
+    if (n > 0 && !A) return -4;
+    if (lda < std::max<int64_t>(1, n)) return -5;
+    if (n > 0 && !ipiv) return -6;
+    lu_opts o;
+    lu_default_opts(&o);
+    if (opts) o = *opts;
+    if (check_opts(o) != 0) return -7;
+    if (!info) return -8;
+    if (n > INT32_MAX / 2) return LU_ERR_UNSUPPORTED;
+    std::lock_guard<std::mutex> lk(h->mu);
+    if (dtype == LU_F64) return factor_impl<double>(h, n, (double*)A, lda, ipiv, o, info);
+    return factor_impl<float>(h, n, (float*)A, lda, ipiv, o, info);
+}
+
+extern "C" int lu_factor(int64_t n, double* A, int64_t lda, int32_t* ipiv, int nb) {
+    if (n < 0) return -1;
+    if (n > 0 && !A) return -2;
+    if (lda < std::max<int64_t>(1, n)) return -3;
+    if (n > 0 && !ipiv) return -4;
+    if (nb < 1 || nb > LU_MAX_NB) return -5;
+    lu_handle h = default_handle();
+    if (!h) return LU_ERR_CUDA;
+    lu_opts o;
+    lu_default_opts(&o);
+    o.nb = nb;
+    int32_t* dinfo = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(h->mu);
+        LU_TRY(lu_ctx_reserve(h, n, nb));
+        dinfo = reinterpret_cast<int32_t*>(&h->sync[3].info);
+    }
+    cudaStream_t saved = h->user;
+    h->user = nullptr;
+    int r = lu_factor_ex(h, LU_F64, n, A, lda, ipiv, &o, dinfo);
+    h->user = saved;
+    if (r != LU_SUCCESS) return r;
+    int32_t info = 0;
+    LU_CHECK_CUDA(cudaMemcpy(&info, dinfo, sizeof(int32_t), cudaMemcpyDeviceToHost));
+    return info;
+}
+
+// ---------------------------------------------------------------------------
+// solve driver
+// ---------------------------------------------------------------------------
+template <typename T>
+static int solve_impl(lu_context* c, int64_t n, int64_t nrhs, const T* LU, int64_t lda, const int32_t* ipiv,
+                      T* B, int64_t ldb, T* tmp) {
+    cudaStream_t st = c->user;
+    LU_TRY(lu_ctx_reserve(c, n, 1));
+    LU_TRY(lu_launch_perm_from_ipiv<T>(st, n, ipiv, c->perm));
+    LU_TRY(lu_launch_permute_rows<T>(st, n, nrhs, c->perm, B, ldb, tmp, n));
+    LU_CHECK_CUDA(cudaMemcpy2DAsync(B, ldb * sizeof(T), tmp, n * sizeof(T), n * sizeof(T), nrhs,
+                                    cudaMemcpyDeviceToDevice, st));
+    LU_TRY(lu_launch_trsv_blocked<T>(c, st, true, n, nrhs, LU, lda, B, ldb));
+    LU_TRY(lu_launch_trsv_blocked<T>(c, st, false, n, nrhs, LU, lda, B, ldb));
+    return LU_SUCCESS;
+}
+
+// Scratch for the row gather of a solve (n x nrhs), owned by the handle.
+static int solve_scratch(lu_context* c, size_t bytes, void** out) {
+    if (c->scratch_bytes < bytes) {
+        if (c->scratch) {
+            LU_CHECK_CUDA(cudaDeviceSynchronize());
+            cudaFree(c->scratch);
+            c->scratch = nullptr;
+            c->scratch_bytes = 0;
+        }
+        if (cudaMalloc(&c->scratch, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            return LU_ERR_NOMEM;
+        }
+        c->scratch_bytes = bytes;
+    }
+    *out = c->scratch;
+    return LU_SUCCESS;
+}
+
+extern "C" int lu_solve_ex(lu_handle h, lu_dtype dtype, int64_t n, int64_t nrhs, const void* LU, int64_t lda,
+                           const int32_t* ipiv, void* B, int64_t ldb) {
+    if (!h) return LU_ERR_HANDLE;
+    if (dtype != LU_F64 && dtype != LU_F32) return -2;
+    if (n < 0) return -3;
+    if (nrhs < 0) return -4;
+    if (n > 0 && !LU) return -5;
+    if (lda < std::max<int64_t>(1, n)) return -6;
+    if (n > 0 && !ipiv) return -7;
+    if (n > 0 && nrhs > 0 && !B) return -8;
+    if (ldb < std::max<int64_t>(1, n)) return -9;
+    if (n == 0 || nrhs == 0) return LU_SUCCESS;
+    std::lock_guard<std::mutex> lk(h->mu);
+    const size_t es = dtype == LU_F64 ? 8 : 4;
+    void* tmp = nullptr;
+    LU_TRY(solve_scratch(h, es * (size_t)n * (size_t)nrhs, &tmp));
+    if (dtype == LU_F64)
+        return solve_impl<double>(h, n, nrhs, (const double*)LU, lda, ipiv, (double*)B, ldb, (double*)tmp);
+    return solve_impl<float>(h, n, nrhs, (const float*)LU, lda, ipiv, (float*)B, ldb, (float*)tmp);
+}
+
+extern "C" int lu_solve(int64_t n, int64_t nrhs, const double* LU, const int32_t* ipiv, double* B) {
+    if (n < 0) return -1;
+    if (nrhs < 0) return -2;
+    if (n > 0 && !LU) return -3;
+    if (n > 0 && !ipiv) return -4;
+    if (n > 0 && nrhs > 0 && !B) return -5;
+    lu_handle h = default_handle();
+    if (!h) return LU_ERR_CUDA;
+    cudaStream_t saved = h->user;
+    h->user = nullptr;
+    int r = lu_solve_ex(h, LU_F64, n, nrhs, LU, std::max<int64_t>(1, n), ipiv, B, std::max<int64_t>(1, n));
+    h->user = saved;
+    if (r != LU_SUCCESS) return r;
+    LU_CHECK_CUDA(cudaStreamSynchronize(nullptr));
+    int err = 0;
+    if (h->sync) LU_CHECK_CUDA(cudaMemcpy(&err, &h->sync[1].error, sizeof(int), cudaMemcpyDeviceToHost));
+    if (err != 0) {
+        cudaMemset(&h->sync[1].error, 0, sizeof(int));
+        return err;
+    }
+    return LU_SUCCESS;
+}
+
+// ---------------------------------------------------------------------------
+// individual steps
+// ---------------------------------------------------------------------------
+extern "C" int lu_panel_factor_ex(lu_handle h, lu_dtype dtype, int64_t m, int64_t w, void* A, int64_t lda,
+                                  int32_t* ipiv, const lu_opts* opts, int32_t* info) {
+    if (!h) return LU_ERR_HANDLE;
+    if (dtype != LU_F64 && dtype != LU_F32) return -2;
+    if (m < 0) return -3;
+    if (w < 0 || w > m || w > LU_MAX_NB) return -4;
+    if (m > 0 && w > 0 && !A) return -5;
+    if (lda < std::max<int64_t>(1, m)) return -6;
+    if (w > 0 && !ipiv) return -7;
+    lu_opts o;
+    lu_default_opts(&o);
+    if (opts) o = *opts;
+    if (check_opts(o) != 0) return -8;
+    if (!info) return -9;
+    std::lock_guard<std::mutex> lk(h->mu);
+    LU_TRY(lu_ctx_reserve(h, m, (int)std::max<int64_t>(w, 1)));
+    LU_CHECK_CUDA(cudaMemsetAsync(&h->sync[0], 0, sizeof(LuSync), h->user));
+    if (w > 0) {
+        if (dtype == LU_F64)
+            LU_TRY(lu_panel_recursive<double>(h, h->user, (double*)A, lda, m, 0, w, ipiv, o));
+        else
+            LU_TRY(lu_panel_recursive<float>(h, h->user, (float*)A, lda, m, 0, w, ipiv, o));
+    }
+    return lu_launch_finish_info(h->user, &h->sync[0], info);
+}
+
+extern "C" int lu_laswp_ex(lu_handle h, lu_dtype dtype, int64_t ncols, void* A, int64_t lda, int64_t k1,
+                           int64_t k2, const int32_t* ipiv) {
+    if (!h) return LU_ERR_HANDLE;
+    if (dtype != LU_F64 && dtype != LU_F32) return -2;
+    if (ncols < 0) return -3;
+    if (ncols > 0 && !A) return -4;
+    if (lda < 1) return -5;
+    if (k1 < 0) return -6;
+    if (k2 < k1 || k2 - k1 > LU_MAX_NB) return -7;
+    if (k2 > k1 && !ipiv) return -8;
+    if (ncols == 0 || k2 == k1) return LU_SUCCESS;
+    std::lock_guard<std::mutex> lk(h->mu);
+    LU_TRY(lu_ctx_reserve(h, k2, (int)(k2 - k1)));
+    LU_TRY(lu_launch_laswp_plan(h->user, ipiv, k1, k2, h->plan_tmp));
+    if (dtype == LU_F64)
+        return lu_launch_laswp_apply<double>(h->user, (double*)A, lda, 0, ncols, 0, 0, h->plan_tmp, k2 - k1,
+                                             h->num_sms);
+    return lu_launch_laswp_apply<float>(h->user, (float*)A, lda, 0, ncols, 0, 0, h->plan_tmp, k2 - k1,
+                                        h->num_sms);
+}
+
+extern "C" int lu_trsm_ex(lu_handle h, lu_dtype dtype, int64_t m, int64_t n, const void* L, int64_t ldl, void* B,
+                          int64_t ldb) {
+    if (!h) return LU_ERR_HANDLE;
+    if (dtype != LU_F64 && dtype != LU_F32) return -2;
+    if (m < 0 || m > LU_MAX_NB) return -3;
+    if (n < 0) return -4;
+    if (m > 0 && !L) return -5;
+    if (ldl < std::max<int64_t>(1, m)) return -6;
+    if (m > 0 && n > 0 && !B) return -7;
+    if (ldb < std::max<int64_t>(1, m)) return -8;
+    if (dtype == LU_F64)
+        return lu_launch_trsm_lunit<double>(h->user, m, n, (const double*)L, ldl, (double*)B, ldb);
+    return lu_launch_trsm_lunit<float>(h->user, m, n, (const float*)L, ldl, (float*)B, ldb);
+}
+
+extern "C" int lu_gemm_update_ex(lu_handle h, lu_dtype dtype, int64_t m, int64_t n, int64_t k, const void* A,
+                                 int64_t lda, const void* B, int64_t ldb, void* C, int64_t ldc) {
+    if (!h) return LU_ERR_HANDLE;
+    if (dtype != LU_F64 && dtype != LU_F32) return -2;
+    if (m < 0) return -3;
+    if (n < 0) return -4;
+    if (k < 0 || k > INT32_MAX) return -5;
+    if (m > 0 && k > 0 && !A) return -6;
+    if (lda < std::max<int64_t>(1, m)) return -7;
+    if (k > 0 && n > 0 && !B) return -8;
+    if (ldb < std::max<int64_t>(1, k)) return -9;
+    if (m > 0 && n > 0 && !C) return -10;
+    if (ldc < std::max<int64_t>(1, m)) return -11;
+    if (dtype == LU_F64)
+        return lu_launch_gemm_update<double>(h->user, m, n, k, (const double*)A, lda, (const double*)B, ldb,
+                                             (double*)C, ldc);
+    return lu_launch_gemm_update<float>(h->user, m, n, k, (const float*)A, lda, (const float*)B, ldb, (float*)C,
+                                        ldc);
+}

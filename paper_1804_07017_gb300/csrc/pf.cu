@@ -1,0 +1,254 @@
+// Panel factorization PF (RL1 of LU_blk, Sec. 3): [A11; A21] := LU_unb([A11; A21]).
+//
+// A tall panel is factored recursively: the left half, then the interchanges
+// applied to the right half, its TRSM (RL2) and GEMM (RL3) update inside the
+// panel, the right half, and finally the right half's interchanges applied to
+// the left half.  The recursion bottoms out in a leaf of at most
+// LU_PF_MAX_LEAF columns factored column by column by one multi-CTA kernel:
+//
+//   * the leaf's rows are split across G CTAs, each holding its R x w block
+//     in shared memory for the whole leaf;
+//   * per column: every CTA finds its local pivot candidate (warp-shuffle
+//     argmax, ties to the smallest row), publishes value, row index and the
+//     candidate row; one grid barrier; every CTA then picks the global pivot
+//     (first maximum), swaps rows, scales the column by a true division and
+//     applies the rank-1 update to the remaining leaf columns, fusing the
+//     next column's candidate search into that update.
+//
+// One grid barrier per column is the latency floor of partial pivoting: the
+// pivot of column j depends on the fully updated column j.
+#include <climits>
+
+#include "internal.h"
+
+namespace {
+
+template <typename T>
+__device__ __forceinline__ void argmax_merge(T& v, int& i, T ov, int oi) {
+    if (ov > v || (ov == v && oi < i)) {
+        v = ov;
+        i = oi;
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void warp_argmax(T& v, int& i) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        T ov = __shfl_xor_sync(0xffffffffu, v, o);
+        int oi = __shfl_xor_sync(0xffffffffu, i, o);
+        argmax_merge(v, i, ov, oi);
+    }
+}
+
+template <typename T, int NT>
+__global__ void __launch_bounds__(NT) pf_leaf_kernel(T* __restrict__ A, int64_t lda, int m, int w,
+                                                     int R, int32_t* __restrict__ ipiv,
+                                                     int ipiv_add, LuSync* __restrict__ sync,
+                                                     T* __restrict__ slots,
+                                                     int* __restrict__ slot_idx) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* sA = reinterpret_cast<T*>(smem_raw);  // [w][R], column-major block of this CTA's rows
+    T* prow = sA + (size_t)w * R;             // pivot row (w values)
+    T* jrowv = prow + w;                      // previous contents of row jj (w values)
+    __shared__ T red_v[NT / 32];
+    __shared__ int red_i[NT / 32];
+    __shared__ T sh_bv;
+    __shared__ int sh_bi, sh_p, sh_gw, sh_flag;
+
+    const int G = gridDim.x, g = blockIdx.x, tid = threadIdx.x;
+    const int lane = tid & 31, warp = tid >> 5;
+    const int row0 = g * R;
+    const int nrows = max(0, min(R, m - row0));
+
+    T* cand_val = slots;                                   // [2][MAXC]
+    T* cand_row = slots + 2 * LU_PF_MAX_CTAS;              // [2][MAXC][MAXW]
+    T* jrow = cand_row + 2 * LU_PF_MAX_CTAS * LU_PF_MAX_LEAF;  // [2][MAXW]
+    int* cand_idx = slot_idx;                              // [2][MAXC]
+
+    for (int c = 0; c < w; ++c)
+        for (int r = tid; r < nrows; r += NT) sA[c * R + r] = A[(int64_t)(row0 + r) + (int64_t)c * lda];
+    __syncthreads();
+
+    T bv = T(-1);
+    int bi = INT_MAX;
+    for (int r = tid; r < nrows; r += NT) argmax_merge(bv, bi, (T)fabs(sA[r]), row0 + r);
+
+    for (int jj = 0; jj < w; ++jj) {
+        const int buf = jj & 1;
+        // ---- local candidate (block argmax) ----
+        warp_argmax(bv, bi);
+        if (lane == 0) {
+            red_v[warp] = bv;
+            red_i[warp] = bi;
+        }
+        __syncthreads();
+        if (warp == 0) {
+            T v = (lane < NT / 32) ? red_v[lane] : T(-1);
+            int i = (lane < NT / 32) ? red_i[lane] : INT_MAX;
+            warp_argmax(v, i);
+            if (lane == 0) {
+                sh_bv = v;
+                sh_bi = i;
+            }
+        }
+        __syncthreads();
+        // ---- publish candidate (value, row, row contents) and row jj ----
+        const int my_bi = sh_bi;
+        if (tid == 0) {
+            cand_val[buf * LU_PF_MAX_CTAS + g] = sh_bv;
+            cand_idx[buf * LU_PF_MAX_CTAS + g] = my_bi;
+        }
+        if (tid < w && my_bi != INT_MAX)
+            cand_row[(buf * LU_PF_MAX_CTAS + g) * LU_PF_MAX_LEAF + tid] = sA[tid * R + (my_bi - row0)];
+        if (jj >= row0 && jj < row0 + nrows && tid < w)
+            jrow[buf * LU_PF_MAX_LEAF + tid] = sA[tid * R + (jj - row0)];
+        __threadfence();
+        if (!lu_grid_barrier(sync, (unsigned)(jj + 1) * (unsigned)G, &sh_flag)) break;
+        // ---- global pivot: first maximum over all CTAs' candidates ----
+        if (warp == 0) {
+            T v = T(-1);
+            int i = INT_MAX, q_best = -1;
+            for (int q = lane; q < G; q += 32) {
+                T cv = __ldcg(&cand_val[buf * LU_PF_MAX_CTAS + q]);
+                int ci = __ldcg(&cand_idx[buf * LU_PF_MAX_CTAS + q]);
+                if (ci != INT_MAX && (cv > v || (cv == v && ci < i))) {
+                    v = cv;
+                    i = ci;
+                    q_best = q;
+                }
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                T ov = __shfl_xor_sync(0xffffffffu, v, o);
+                int oi = __shfl_xor_sync(0xffffffffu, i, o);
+                int oq = __shfl_xor_sync(0xffffffffu, q_best, o);
+                if (ov > v || (ov == v && oi < i)) {
+                    v = ov;
+                    i = oi;
+                    q_best = oq;
+                }
+            }
+            if (lane == 0) {
+                sh_p = (i == INT_MAX) ? jj : i;
+                sh_gw = (i == INT_MAX) ? -1 : q_best;
+            }
+        }
+        __syncthreads();
+        const int p = sh_p, gw = sh_gw;
+        if (tid < w) {
+            T jv = __ldcg(&jrow[buf * LU_PF_MAX_LEAF + tid]);
+            jrowv[tid] = jv;
+            prow[tid] = (gw >= 0) ? __ldcg(&cand_row[(buf * LU_PF_MAX_CTAS + gw) * LU_PF_MAX_LEAF + tid]) : jv;
+        }
+        if (g == 0 && tid == 0) ipiv[jj] = p + 1 + ipiv_add;
+        __syncthreads();
+        // ---- interchange rows jj and p (within this leaf's columns) ----
+        if (p != jj && tid < w) {
+            if (p >= row0 && p < row0 + nrows) sA[tid * R + (p - row0)] = jrowv[tid];
+            if (jj >= row0 && jj < row0 + nrows) sA[tid * R + (jj - row0)] = prow[tid];
+        }
+        const T piv = prow[jj];
+        if (piv == T(0) && g == 0 && tid == 0) atomicCAS(&sync->info, 0, jj + 1 + ipiv_add);
+        __syncthreads();
+        // ---- scale column jj, rank-1 update, next column's local candidate ----
+        bv = T(-1);
+        bi = INT_MAX;
+        const bool has_next = jj + 1 < w;
+        for (int r = tid; r < nrows; r += NT) {
+            const int gr = row0 + r;
+            if (gr <= jj) continue;
+            if (piv != T(0)) {
+                const T l = sA[jj * R + r] / piv;
+                sA[jj * R + r] = l;
+                for (int c = jj + 1; c < w; ++c) sA[c * R + r] = fma(-l, prow[c], sA[c * R + r]);
+            }
+            if (has_next) argmax_merge(bv, bi, (T)fabs(sA[(jj + 1) * R + r]), gr);
+        }
+    }
+    __syncthreads();
+    for (int c = 0; c < w; ++c)
+        for (int r = tid; r < nrows; r += NT) A[(int64_t)(row0 + r) + (int64_t)c * lda] = sA[c * R + r];
+    lu_grid_exit(sync);
+}
+
+constexpr int kPfThreads = 256;
+
+}  // namespace
+
+template <typename T>
+int lu_launch_pf_leaf(lu_context* c, cudaStream_t st, T* A, int64_t lda, int64_t m, int w,
+                      int32_t* ipiv, int64_t ipiv_add, int max_ctas) {
+    if (w < 1 || w > LU_PF_MAX_LEAF || m < w) return LU_ERR_UNSUPPORTED;
+    if (max_ctas <= 0 || max_ctas > LU_PF_MAX_CTAS) max_ctas = LU_PF_MAX_CTAS;
+    // Rows per CTA: a multiple of 32, enough CTAs to hold all rows within the budget.
+    int64_t R = lu_cdiv(m, max_ctas);
+    R = std::max<int64_t>(32, lu_cdiv(R, 32) * 32);
+    size_t smem = (size_t)(R * w + 2 * w) * sizeof(T);
+    if (smem > (size_t)LU_PF_SMEM_BUDGET) return LU_ERR_UNSUPPORTED;
+    int G = (int)lu_cdiv(m, R);
+    if (G > LU_PF_MAX_CTAS) return LU_ERR_UNSUPPORTED;
+    static bool attr_set[2] = {false, false};
+    const int ti = sizeof(T) == 8 ? 0 : 1;
+    if (!attr_set[ti]) {
+        LU_CHECK_CUDA(cudaFuncSetAttribute(pf_leaf_kernel<T, kPfThreads>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           LU_PF_SMEM_BUDGET));
+        attr_set[ti] = true;
+    }
+    T* slots = reinterpret_cast<T*>(c->pf_slots);
+    int* slot_idx = reinterpret_cast<int*>(reinterpret_cast<char*>(c->pf_slots) +
+                                           sizeof(double) * (2 * LU_PF_MAX_CTAS * (LU_PF_MAX_LEAF + 1) +
+                                                             2 * LU_PF_MAX_LEAF));
+    pf_leaf_kernel<T, kPfThreads><<<G, kPfThreads, smem, st>>>(A, lda, (int)m, w, (int)R, ipiv,
+                                                                (int)ipiv_add, &c->sync[0], slots,
+                                                                slot_idx);
+    LU_CHECK_LAUNCH();
+    return LU_SUCCESS;
+}
+
+template <typename T>
+int lu_panel_recursive(lu_context* c, cudaStream_t st, T* A, int64_t lda, int64_t M, int64_t j0,
+                       int64_t width, int32_t* ipiv, const lu_opts& o) {
+    if (width <= 0) return LU_SUCCESS;
+    int leaf = o.leaf > 0 ? std::min(o.leaf, LU_PF_MAX_LEAF) : 32;
+    // Narrow the leaf until one CTA's share of the rows fits in shared memory.
+    const int64_t rows = M - j0;
+    while (leaf > 1) {
+        int64_t R = std::max<int64_t>(32, lu_cdiv(lu_cdiv(rows, LU_PF_MAX_CTAS), 32) * 32);
+        if ((size_t)(R * leaf + 2 * leaf) * sizeof(T) <= (size_t)LU_PF_SMEM_BUDGET) break;
+        leaf >>= 1;
+    }
+    if (width <= leaf) {
+        return lu_launch_pf_leaf<T>(c, st, A + j0 + j0 * lda, lda, rows, (int)width, ipiv + j0, j0,
+                                    o.pf_ctas);
+    }
+    int64_t w1 = ((width / 2 + 7) / 8) * 8;
+    if (w1 >= width) w1 = width / 2;
+    if (w1 < 1) w1 = 1;
+    const int64_t w2 = width - w1;
+    LU_TRY(lu_panel_recursive<T>(c, st, A, lda, M, j0, w1, ipiv, o));
+    // interchanges of the left half applied to the right half's columns
+    LU_TRY(lu_launch_laswp_plan(st, ipiv, j0, j0 + w1, c->plan_tmp));
+    LU_TRY(lu_launch_laswp_apply<T>(st, A, lda, j0 + w1, w2, 0, 0, c->plan_tmp, w1, c->num_sms));
+    // RL2 and RL3 restricted to the panel
+    LU_TRY(lu_launch_trsm_lunit<T>(st, w1, w2, A + j0 + j0 * lda, lda, A + j0 + (j0 + w1) * lda, lda));
+    if (M - j0 - w1 > 0)
+        LU_TRY(lu_launch_gemm_update<T>(st, M - j0 - w1, w2, w1, A + (j0 + w1) + j0 * lda, lda,
+                                        A + j0 + (j0 + w1) * lda, lda,
+                                        A + (j0 + w1) + (j0 + w1) * lda, lda));
+    LU_TRY(lu_panel_recursive<T>(c, st, A, lda, M, j0 + w1, w2, ipiv, o));
+    // interchanges of the right half applied back to the left half's columns
+    LU_TRY(lu_launch_laswp_plan(st, ipiv, j0 + w1, j0 + width, c->plan_tmp));
+    LU_TRY(lu_launch_laswp_apply<T>(st, A, lda, j0, w1, 0, 0, c->plan_tmp, w2, c->num_sms));
+    return LU_SUCCESS;
+}
+
+template int lu_launch_pf_leaf<double>(lu_context*, cudaStream_t, double*, int64_t, int64_t, int,
+                                       int32_t*, int64_t, int);
+template int lu_launch_pf_leaf<float>(lu_context*, cudaStream_t, float*, int64_t, int64_t, int,
+                                      int32_t*, int64_t, int);
+template int lu_panel_recursive<double>(lu_context*, cudaStream_t, double*, int64_t, int64_t,
+                                        int64_t, int64_t, int32_t*, const lu_opts&);
+template int lu_panel_recursive<float>(lu_context*, cudaStream_t, float*, int64_t, int64_t,
+                                       int64_t, int64_t, int32_t*, const lu_opts&);

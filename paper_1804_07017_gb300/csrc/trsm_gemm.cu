@@ -1,0 +1,189 @@
+// RL2 and RL3 of LU_blk (Sec. 3) on the CUDA cores, in the storage precision.
+//
+//   trsm_lunit:   B := trilu(L)^{-1} B   (L m x m unit lower, m <= 1024)
+//   gemm_update:  C := C - A B           (FP64/FP32 fused multiply-add)
+//
+// Every output element is computed in a fixed order that does not depend on
+// where its tile starts, so splitting an update into column ranges (the
+// static look-ahead's TU^L / TU^R split, Sec. 4) gives bit-identical results.
+#include "internal.h"
+
+namespace {
+
+constexpr int kTrsmThreads = 256;
+
+// One CTA solves COLS right-hand-side columns held in shared memory, sweeping
+// 32-row diagonal blocks: a warp-shuffle substitution inside the block, then a
+// rank-32 update of the rows below it.
+template <typename T, int COLS>
+__global__ void __launch_bounds__(kTrsmThreads)
+    trsm_lunit_kernel(int m, int64_t n, const T* __restrict__ L, int64_t ldl, T* __restrict__ B,
+                      int64_t ldb) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int mp = (m + 31) & ~31;
+    T* sB = reinterpret_cast<T*>(smraw);  // [COLS][mp]
+    T* sL = sB + (size_t)COLS * mp;        // [32][33] diagonal block, sL[j*33 + i] = L(J+i, J+j)
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t col0 = (int64_t)blockIdx.x * COLS;
+    const int nc = (int)min((int64_t)COLS, n - col0);
+    for (int c = 0; c < COLS; ++c)
+        for (int r = tid; r < mp; r += kTrsmThreads)
+            sB[c * mp + r] = (c < nc && r < m) ? B[r + (col0 + c) * ldb] : T(0);
+    for (int J = 0; J < m; J += 32) {
+        const int jb = min(32, m - J);
+        __syncthreads();
+        for (int e = tid; e < 32 * 32; e += kTrsmThreads) {
+            const int i = e & 31, j = e >> 5;
+            sL[j * 33 + i] = (i < jb && j < jb) ? L[(int64_t)(J + i) + (int64_t)(J + j) * ldl] : T(0);
+        }
+        __syncthreads();
+        for (int c = warp; c < COLS; c += kTrsmThreads / 32) {
+            T v = sB[c * mp + J + lane];
+            for (int j = 0; j < jb; ++j) {
+                const T xj = __shfl_sync(0xffffffffu, v, j);
+                if (lane > j) v = fma(-sL[j * 33 + lane], xj, v);
+            }
+            if (lane < jb) sB[c * mp + J + lane] = v;
+        }
+        __syncthreads();
+        for (int r = J + jb + tid; r < m; r += kTrsmThreads) {
+            T acc[COLS];
+#pragma unroll
+            for (int c = 0; c < COLS; ++c) acc[c] = T(0);
+            for (int j = 0; j < jb; ++j) {
+                const T l = L[(int64_t)r + (int64_t)(J + j) * ldl];
+#pragma unroll
+                for (int c = 0; c < COLS; ++c) acc[c] = fma(l, sB[c * mp + J + j], acc[c]);
+            }
+#pragma unroll
+            for (int c = 0; c < COLS; ++c) sB[c * mp + r] -= acc[c];
+        }
+    }
+    __syncthreads();
+    for (int c = 0; c < nc; ++c)
+        for (int r = tid; r < m; r += kTrsmThreads) B[r + (col0 + c) * ldb] = sB[c * mp + r];
+}
+
+constexpr int kGemmThreads = 256;
+constexpr int BM = 64, BN = 64, BK = 16;
+
+// C := C - A B with a 64x64 tile per CTA and a 4x4 register tile per thread;
+// thread (tx, ty) owns rows tx + 16 i and columns ty + 16 j so that shared
+// memory reads and the epilogue's column-major accesses are both coalesced.
+template <typename T>
+__global__ void __launch_bounds__(kGemmThreads)
+    gemm_update_kernel(int64_t m, int64_t n, int k, const T* __restrict__ A, int64_t lda,
+                       const T* __restrict__ B, int64_t ldb, T* __restrict__ C, int64_t ldc) {
+    __shared__ T sA[2][BK][BM];
+    __shared__ T sB[2][BK][BN + 1];
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const int64_t i0 = (int64_t)blockIdx.x * BM, j0 = (int64_t)blockIdx.y * BN;
+    T acc[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = T(0);
+    T ra[4], rb[4];
+    auto load_regs = [&](int p0) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int e = tid + q * kGemmThreads;
+            const int i = e & (BM - 1), p = e >> 6;  // A tile: 64 rows x 16 cols
+            ra[q] = (i0 + i < m && p0 + p < k) ? A[(i0 + i) + (int64_t)(p0 + p) * lda] : T(0);
+            const int pb = e & (BK - 1), jb = e >> 4;  // B tile: 16 rows x 64 cols
+            rb[q] = (p0 + pb < k && j0 + jb < n) ? B[(int64_t)(p0 + pb) + (j0 + jb) * ldb] : T(0);
+        }
+    };
+    auto store_smem = [&](int s) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int e = tid + q * kGemmThreads;
+            sA[s][e >> 6][e & (BM - 1)] = ra[q];
+            sB[s][e & (BK - 1)][e >> 4] = rb[q];
+        }
+    };
+    load_regs(0);
+    store_smem(0);
+    __syncthreads();
+    int s = 0;
+    for (int p0 = 0; p0 < k; p0 += BK) {
+        const bool more = p0 + BK < k;
+        if (more) load_regs(p0 + BK);
+#pragma unroll
+        for (int p = 0; p < BK; ++p) {
+            T a[4], b[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                a[q] = sA[s][p][tx + 16 * q];
+                b[q] = sB[s][p][ty + 16 * q];
+            }
+#pragma unroll
+            for (int x = 0; x < 4; ++x)
+#pragma unroll
+                for (int y = 0; y < 4; ++y) acc[x][y] = fma(a[x], b[y], acc[x][y]);
+        }
+        if (more) {
+            store_smem(s ^ 1);
+            __syncthreads();
+            s ^= 1;
+        }
+    }
+#pragma unroll
+    for (int y = 0; y < 4; ++y) {
+        const int64_t j = j0 + ty + 16 * y;
+        if (j >= n) continue;
+#pragma unroll
+        for (int x = 0; x < 4; ++x) {
+            const int64_t i = i0 + tx + 16 * x;
+            if (i < m) C[i + j * ldc] -= acc[x][y];
+        }
+    }
+}
+
+}  // namespace
+
+template <typename T>
+int lu_launch_trsm_lunit(cudaStream_t st, int64_t m, int64_t n, const T* L, int64_t ldl, T* B,
+                         int64_t ldb) {
+    if (m <= 0 || n <= 0) return LU_SUCCESS;
+    if (m > LU_MAX_NB) return LU_ERR_UNSUPPORTED;
+    const int mp = (int)((m + 31) & ~31);
+    const size_t smem16 = sizeof(T) * ((size_t)16 * mp + 32 * 33);
+    const size_t smem8 = sizeof(T) * ((size_t)8 * mp + 32 * 33);
+    static bool attr[2] = {false, false};
+    const int ti = sizeof(T) == 8 ? 0 : 1;
+    if (!attr[ti]) {
+        LU_CHECK_CUDA(cudaFuncSetAttribute(trsm_lunit_kernel<T, 16>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+        LU_CHECK_CUDA(cudaFuncSetAttribute(trsm_lunit_kernel<T, 8>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+        attr[ti] = true;
+    }
+    if (smem16 <= 64 * 1024) {
+        trsm_lunit_kernel<T, 16><<<(unsigned)lu_cdiv(n, 16), kTrsmThreads, smem16, st>>>((int)m, n, L, ldl, B, ldb);
+    } else {
+        trsm_lunit_kernel<T, 8><<<(unsigned)lu_cdiv(n, 8), kTrsmThreads, smem8, st>>>((int)m, n, L, ldl, B, ldb);
+    }
+    LU_CHECK_LAUNCH();
+    return LU_SUCCESS;
+}
+
+template <typename T>
+int lu_launch_gemm_update(cudaStream_t st, int64_t m, int64_t n, int64_t k, const T* A, int64_t lda,
+                          const T* B, int64_t ldb, T* C, int64_t ldc) {
+    if (m <= 0 || n <= 0 || k <= 0) return LU_SUCCESS;
+    if (lu_cdiv(n, BN) > 65535) return LU_ERR_UNSUPPORTED;
+    dim3 grid((unsigned)lu_cdiv(m, BM), (unsigned)lu_cdiv(n, BN));
+    gemm_update_kernel<T><<<grid, kGemmThreads, 0, st>>>(m, n, (int)k, A, lda, B, ldb, C, ldc);
+    LU_CHECK_LAUNCH();
+    return LU_SUCCESS;
+}
+
+template int lu_launch_trsm_lunit<double>(cudaStream_t, int64_t, int64_t, const double*, int64_t,
+                                          double*, int64_t);
+template int lu_launch_trsm_lunit<float>(cudaStream_t, int64_t, int64_t, const float*, int64_t,
+                                         float*, int64_t);
+template int lu_launch_gemm_update<double>(cudaStream_t, int64_t, int64_t, int64_t, const double*,
+                                           int64_t, const double*, int64_t, double*, int64_t);
+template int lu_launch_gemm_update<float>(cudaStream_t, int64_t, int64_t, int64_t, const float*,
+                                          int64_t, const float*, int64_t, float*, int64_t);
