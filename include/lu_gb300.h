@@ -51,6 +51,16 @@ typedef struct lu_context *lu_handle;
 /* Arithmetic type of a factorization / of the matrix storage. */
 typedef enum { LU_F64 = 0, LU_F32 = 1 } lu_dtype;
 
+/* Operand precision of the tensor-core trailing update in the mixed-precision
+ * path (panels, triangular solves and the stored factors stay FP32; the
+ * products accumulate in FP32). */
+typedef enum {
+    LU_TU_BF16 = 0, /* bf16 operands, tcgen05.mma kind::f16 */
+    LU_TU_FP16 = 1, /* fp16 operands, tcgen05.mma kind::f16 */
+    LU_TU_FP8 = 2,  /* e4m3 operands with power-of-two block scales, kind::f8f6f4 */
+    LU_TU_F32 = 3   /* FP32 on the CUDA cores (no tensor cores; a reference point) */
+} lu_prec;
+
 /* Options of a blocked factorization (Sec. 3-4 of the paper). */
 typedef struct {
     int nb;        /* algorithmic block size b (panel width), >= 1 */
@@ -161,6 +171,16 @@ int lu_trsm_ex(lu_handle handle, lu_dtype dtype, int64_t m, int64_t n, const voi
 int lu_gemm_update_ex(lu_handle handle, lu_dtype dtype, int64_t m, int64_t n, int64_t k,
                       const void *A, int64_t lda, const void *B, int64_t ldb, void *C,
                       int64_t ldc);
+
+/*
+ * lu_gemm_update_tc_ex -- RL3, C := C - A B on the tensor cores: A (m x k) and
+ * B (k x n) are FP32 and are rounded to the operand type of `prec` (round to
+ * nearest even; LU_TU_BF16 or LU_TU_FP16), the products accumulate in FP32
+ * and C (FP32, m x n) is updated in place.  k must be a multiple of 64.
+ *   info  device int32[1]; 0, or LU_ERR_TIMEOUT if a bounded wait expired.
+ */
+int lu_gemm_update_tc_ex(lu_handle handle, lu_prec prec, int64_t m, int64_t n, int64_t k, const float *A,
+                         int64_t lda, const float *B, int64_t ldb, float *C, int64_t ldc, int32_t *info);
 
 #ifdef __cplusplus
 }

@@ -56,6 +56,7 @@ _SIGNATURES = {
     "lu_laswp_ex": (i32, [vp, i32, i64, vp, i64, i64, i64, vp]),
     "lu_trsm_ex": (i32, [vp, i32, i64, i64, vp, i64, vp, i64]),
     "lu_gemm_update_ex": (i32, [vp, i32, i64, i64, i64, vp, i64, vp, i64, vp, i64]),
+    "lu_gemm_update_tc_ex": (i32, [vp, i32, i64, i64, i64, vp, i64, vp, i64, vp, i64, vp]),
 }
 
 _lib = None

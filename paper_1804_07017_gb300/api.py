@@ -154,3 +154,13 @@ def lu_gemm_update_ex(C: torch.Tensor, A: torch.Tensor, B: torch.Tensor, handle:
     k = A.shape[1]
     _check("lu_gemm_update_ex", lib().lu_gemm_update_ex(h.ptr, _DT[C.dtype], m, n, k, _p(A), _ld(A, "A"), _p(B),
                                                          _ld(B, "B"), _p(C), _ld(C, "C")))
+
+
+def lu_gemm_update_tc_ex(C: torch.Tensor, A: torch.Tensor, B: torch.Tensor, prec: int, info: torch.Tensor,
+                         handle: Handle | None = None) -> None:
+    """C := C - round(A) round(B) on the tensor cores (FP32 C, A, B; k % 64 == 0)."""
+    h = _handle(handle)
+    m, n = C.shape
+    k = A.shape[1]
+    _check("lu_gemm_update_tc_ex", lib().lu_gemm_update_tc_ex(h.ptr, prec, m, n, k, _p(A), _ld(A, "A"), _p(B),
+                                                               _ld(B, "B"), _p(C), _ld(C, "C"), _p(info)))

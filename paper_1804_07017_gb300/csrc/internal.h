@@ -38,6 +38,10 @@ struct lu_context {
     // Scratch for the row gather of a solve.
     void* scratch = nullptr;
     size_t scratch_bytes = 0;
+    // Mixed-precision workspace (FP32 working copy, packed operands, IR vectors).
+    void* mx = nullptr;
+    size_t mx_bytes = 0;
+    double* host_eta = nullptr;  // pinned host word for the convergence test
     std::mutex mu;
 };
 

@@ -60,6 +60,10 @@ int lu_ctx_release(lu_context* c) {
     c->ws = nullptr;
     if (c->scratch) cudaFree(c->scratch);
     c->scratch = nullptr;
+    if (c->mx) cudaFree(c->mx);
+    c->mx = nullptr;
+    if (c->host_eta) cudaFreeHost(c->host_eta);
+    c->host_eta = nullptr;
     cudaEvent_t evs[] = {c->ev_fork, c->ev_pf, c->ev_tu, c->ev_join_hi, c->ev_join_lo};
     for (cudaEvent_t e : evs)
         if (e) cudaEventDestroy(e);

@@ -1,0 +1,74 @@
+"""GPU parity of the tensor-core trailing update (tcgen05 + TMA), through the C ABI.
+
+Reference: the oracle's RL3 update C - A B evaluated in FP64 on the operands
+rounded to the tensor-core operand type by the oracle's own ties-to-even
+rounding.  The kernel accumulates in FP32, so the stated tolerance is the
+FP32 accumulation bound (k + 2) u32 (|A||B| + |C|) elementwise.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lu():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import paper_1804_07017_gb300 as pkg
+    pkg.lib()
+    return pkg
+
+
+def dev32(a):
+    from paper_1804_07017_gb300.api import colmajor
+    t = colmajor(a.shape[0], a.shape[1], dtype=torch.float32)
+    t.copy_(torch.from_numpy(np.ascontiguousarray(a)).float())
+    return t
+
+
+@pytest.mark.parametrize("prec_name", ["bf16", "fp16"])
+@pytest.mark.parametrize("m,n,k", [(128, 256, 64), (256, 256, 64), (1000, 700, 256), (300, 5000, 64),
+                                   (4097, 129, 512), (1, 1, 64), (129, 257, 128)])
+def test_tc_update(lu, prec_name, m, n, k):
+    prec = lu.LU_TU_BF16 if prec_name == "bf16" else lu.LU_TU_FP16
+    rnd = oracle.round_bf16 if prec_name == "bf16" else oracle.round_fp16
+    g = synth.rng(31, m + n + k)
+    C0, A0, B0 = (g.standard_normal(size=s).astype(np.float32).astype(np.float64)
+                  for s in ((m, n), (m, k), (k, n)))
+    C = dev32(C0)
+    info = torch.full((1,), -7, dtype=torch.int32, device="cuda")
+    lu.lu_gemm_update_tc_ex(C, dev32(A0), dev32(B0), prec, info)
+    torch.cuda.synchronize()
+    assert int(info.item()) == 0
+    Ar, Br = rnd(A0), rnd(B0)
+    ref = oracle.gemm_update(C0, Ar, Br)
+    got = C.cpu().double().numpy()
+    scale = np.abs(Ar) @ np.abs(Br) + np.abs(C0)
+    u32 = np.finfo(np.float32).eps / 2
+    err = np.abs(got - ref)
+    assert np.all(err <= (k + 2) * u32 * scale), (err / scale).max()
+    # the rounding actually happened: against unrounded operands the result differs
+    # by about the operand rounding, far above the accumulation bound
+    if m * n > 1000:
+        ref_unrounded = oracle.gemm_update(C0, A0, B0)
+        assert np.abs(got - ref_unrounded).max() > 10 * ((k + 2) * u32 * scale).min()
+
+
+def test_tc_update_repeatable(lu):
+    m, n, k = 2000, 1500, 256
+    g = synth.rng(32, 0)
+    C0, A0, B0 = (g.standard_normal(size=s) for s in ((m, n), (m, k), (k, n)))
+    outs = []
+    for _ in range(3):
+        C = dev32(C0)
+        info = torch.zeros(1, dtype=torch.int32, device="cuda")
+        lu.lu_gemm_update_tc_ex(C, dev32(A0), dev32(B0), lu.LU_TU_BF16, info)
+        torch.cuda.synchronize()
+        outs.append(C.cpu().numpy())
+    # the dynamic tile schedule changes which CTA computes a tile, not the arithmetic
+    assert np.array_equal(outs[0], outs[1]) and np.array_equal(outs[0], outs[2])
