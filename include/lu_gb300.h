@@ -182,6 +182,45 @@ int lu_gemm_update_ex(lu_handle handle, lu_dtype dtype, int64_t m, int64_t n, in
 int lu_gemm_update_tc_ex(lu_handle handle, lu_prec prec, int64_t m, int64_t n, int64_t k, const float *A,
                          int64_t lda, const float *B, int64_t ldb, float *C, int64_t ldc, int32_t *info);
 
+/* ----------------------------------------------------------------------------
+ * Mixed precision (not in the paper, whose experiments are FP64 only): FP32
+ * panels, triangular solves and factors, a tensor-core trailing update, and
+ * FP64 iterative refinement of A x = b.
+ * ------------------------------------------------------------------------- */
+
+/*
+ * lu_factor_mixed_ex -- blocked FP32 LU of an n x n FP32 matrix with the same
+ * look-ahead schedule as lu_factor_ex, whose trailing update (RL3) runs on the
+ * tensor cores with operands rounded to `prec` (LU_TU_BF16 / LU_TU_FP16) and
+ * FP32 accumulation; LU_TU_F32 keeps it on the CUDA cores.  When nb is not a
+ * multiple of 64 the update falls back to FP32 on the CUDA cores.
+ * Asynchronous; info as in lu_factor_ex.
+ */
+int lu_factor_mixed_ex(lu_handle handle, lu_prec prec, int64_t n, float *A, int64_t lda, int32_t *ipiv,
+                       const lu_opts *opts, int32_t *info);
+
+/*
+ * lu_gesv_mixed -- solve A X = B for an n x n FP64 matrix A and n x nrhs FP64
+ * B: copy A to FP32, factor it with lu_factor_mixed_ex, solve in FP32, then
+ * refine in FP64: r = B - A X with the original A, stop when the normwise
+ * backward error eta = max_c ||r_c|| / (||A|| ||x_c|| + ||b_c||) (inf-norms)
+ * is <= tol, or after max_iter corrections.
+ *   A, B      device FP64, not modified
+ *   X         device FP64 n x nrhs (ldx), receives the solution (the iterate
+ *             with the smallest eta if tol was not reached)
+ *   tol       stopping threshold (1e-14 in the experiments), >= 0
+ *   max_iter  maximum number of corrections (30 in the experiments), >= 0
+ *   opts      factorization options (NULL = defaults)
+ *   iters     host; number of corrections applied to reach the returned X
+ *   bwd_err   host; eta of the returned X
+ * Synchronous (the host reads eta once per iteration).  Returns 0,
+ * LU_WARN_NOT_CONVERGED, i > 0 if U(i,i) of the FP32 factors is exactly zero,
+ * -i, or a runtime error code.
+ */
+int lu_gesv_mixed(lu_handle handle, lu_prec prec, int64_t n, int64_t nrhs, const double *A, int64_t lda,
+                  const double *B, int64_t ldb, double *X, int64_t ldx, double tol, int max_iter,
+                  const lu_opts *opts, int *iters, double *bwd_err);
+
 #ifdef __cplusplus
 }
 #endif

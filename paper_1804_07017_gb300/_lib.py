@@ -57,6 +57,9 @@ _SIGNATURES = {
     "lu_trsm_ex": (i32, [vp, i32, i64, i64, vp, i64, vp, i64]),
     "lu_gemm_update_ex": (i32, [vp, i32, i64, i64, i64, vp, i64, vp, i64, vp, i64]),
     "lu_gemm_update_tc_ex": (i32, [vp, i32, i64, i64, i64, vp, i64, vp, i64, vp, i64, vp]),
+    "lu_factor_mixed_ex": (i32, [vp, i32, i64, vp, i64, vp, ctypes.POINTER(LuOpts), vp]),
+    "lu_gesv_mixed": (i32, [vp, i32, i64, i64, vp, i64, vp, i64, vp, i64, dbl, i32, ctypes.POINTER(LuOpts),
+                            ctypes.POINTER(i32), ctypes.POINTER(dbl)]),
 }
 
 _lib = None

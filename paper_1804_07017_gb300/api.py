@@ -10,7 +10,7 @@ import ctypes
 
 import torch
 
-from ._lib import LU_F32, LU_F64, LuError, LuOpts, lib
+from ._lib import LU_F32, LU_F64, LU_WARN_NOT_CONVERGED, LuError, LuOpts, lib
 
 _DT = {torch.float64: LU_F64, torch.float32: LU_F32}
 
@@ -164,3 +164,28 @@ def lu_gemm_update_tc_ex(C: torch.Tensor, A: torch.Tensor, B: torch.Tensor, prec
     k = A.shape[1]
     _check("lu_gemm_update_tc_ex", lib().lu_gemm_update_tc_ex(h.ptr, prec, m, n, k, _p(A), _ld(A, "A"), _p(B),
                                                                _ld(B, "B"), _p(C), _ld(C, "C"), _p(info)))
+
+
+def lu_factor_mixed_ex(A: torch.Tensor, ipiv: torch.Tensor, info: torch.Tensor, prec: int, opts: LuOpts | None = None,
+                       handle: Handle | None = None) -> None:
+    """FP32 LU with the tensor-core trailing update (prec: LU_TU_BF16 / LU_TU_FP16 / LU_TU_F32)."""
+    h = _handle(handle)
+    o = opts if opts is not None else default_opts()
+    _check("lu_factor_mixed_ex", lib().lu_factor_mixed_ex(h.ptr, prec, A.shape[0], _p(A), _ld(A, "A"), _p(ipiv),
+                                                           ctypes.byref(o), _p(info)))
+
+
+def lu_gesv_mixed(A: torch.Tensor, B: torch.Tensor, X: torch.Tensor, prec: int, tol: float = 1e-14,
+                  max_iter: int = 30, opts: LuOpts | None = None, handle: Handle | None = None):
+    """Mixed-precision solve with FP64 refinement.  Returns (status, iters, eta);
+    status is 0 or LU_WARN_NOT_CONVERGED (other codes raise)."""
+    h = _handle(handle)
+    o = opts if opts is not None else default_opts()
+    n, nrhs = B.shape
+    iters = ctypes.c_int(0)
+    eta = ctypes.c_double(0.0)
+    rc = lib().lu_gesv_mixed(h.ptr, prec, n, nrhs, _p(A), _ld(A, "A"), _p(B), _ld(B, "B"), _p(X), _ld(X, "X"),
+                             float(tol), int(max_iter), ctypes.byref(o), ctypes.byref(iters), ctypes.byref(eta))
+    if rc != 0 and rc != LU_WARN_NOT_CONVERGED:
+        _check("lu_gesv_mixed", rc)
+    return rc, iters.value, eta.value

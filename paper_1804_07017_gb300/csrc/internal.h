@@ -22,11 +22,12 @@ struct lu_context {
     cudaStream_t hi = nullptr;    // high-priority internal stream (panel path)
     cudaStream_t lo = nullptr;    // low-priority internal stream (right trailing update)
     cudaEvent_t ev_fork = nullptr, ev_pf = nullptr, ev_tu = nullptr, ev_join_hi = nullptr,
-                ev_join_lo = nullptr;
+                ev_join_lo = nullptr, ev_steal = nullptr;
     // Workspace: one device buffer carved into fixed regions.
     char* ws = nullptr;
     size_t ws_bytes = 0;
-    LuSync* sync = nullptr;   // [0] panel leaves, [1] triangular solves, [2..] spare
+    LuSync* sync = nullptr;   // [0] panel leaves + factorization errors, [1] triangular solves,
+                              // [2] standalone tensor-core update, [3] lu_factor info, [4]/[5] tile counters
     void* pf_slots = nullptr; // panel-leaf exchange slots
     int32_t* plans = nullptr; // per-panel interchange plans
     size_t plan_stride = 0;   // int32 entries per plan
@@ -50,6 +51,7 @@ int lu_ctx_release(lu_context* c);
 // Makes sure the workspace can hold a factorization of order n with panel
 // width nb (and solves of order n).  May synchronise the user stream.
 int lu_ctx_reserve(lu_context* c, int64_t n, int nb);
+int lu_mx_reserve(lu_context* c, size_t bytes);
 
 // --- kernels (launchers return LU_SUCCESS or LU_ERR_CUDA) --------------------
 template <typename T>
@@ -90,3 +92,23 @@ int lu_launch_finish_info(cudaStream_t st, const LuSync* s, int32_t* info);
 template <typename T>
 int lu_panel_recursive(lu_context* c, cudaStream_t st, T* A, int64_t lda, int64_t M,
                        int64_t j0, int64_t width, int32_t* ipiv, const lu_opts& o);
+
+// Trailing-update engine for the mixed-precision factorization (mixed.cu):
+// packs each panel's L21 and, per update, U12, and runs the tensor-core GEMM.
+struct LuTuEngine {
+    virtual ~LuTuEngine() {}
+    virtual bool uses_tc(int64_t kb) const = 0;
+    // pack L21 of panel k (rows [k0+kb, n), columns [k0, k0+kb)) on stream st
+    virtual int pack_panel(cudaStream_t st, const float* A, int64_t lda, int64_t k, int64_t k0, int64_t kb) const = 0;
+    // C[k0+kb.., c_begin..c_end) -= L21 U12 for panel k; which = 0 (panel path) or 1 (right update)
+    virtual int update(cudaStream_t st, float* A, int64_t lda, int64_t k, int64_t k0, int64_t kb, int64_t c_begin,
+                       int64_t c_end, int which) const = 0;
+    // extra CTAs joining the right update of step k once the panel path is done
+    virtual int steal(cudaStream_t st, int64_t k) const = 0;
+};
+
+int lu_check_opts(const lu_opts& o);
+
+template <typename T>
+int lu_factor_blocked(lu_context* c, int64_t n, T* A, int64_t lda, int32_t* ipiv, const lu_opts& o, int32_t* info,
+                      const LuTuEngine* eng);

@@ -50,7 +50,7 @@ int lu_ctx_init(lu_context* c) {
     LU_CHECK_CUDA(cudaDeviceGetStreamPriorityRange(&lo_prio, &hi_prio));
     LU_CHECK_CUDA(cudaStreamCreateWithPriority(&c->hi, cudaStreamNonBlocking, hi_prio));
     LU_CHECK_CUDA(cudaStreamCreateWithPriority(&c->lo, cudaStreamNonBlocking, lo_prio));
-    cudaEvent_t* evs[] = {&c->ev_fork, &c->ev_pf, &c->ev_tu, &c->ev_join_hi, &c->ev_join_lo};
+    cudaEvent_t* evs[] = {&c->ev_fork, &c->ev_pf, &c->ev_tu, &c->ev_join_hi, &c->ev_join_lo, &c->ev_steal};
     for (cudaEvent_t* e : evs) LU_CHECK_CUDA(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
     return LU_SUCCESS;
 }
@@ -64,7 +64,7 @@ int lu_ctx_release(lu_context* c) {
     c->mx = nullptr;
     if (c->host_eta) cudaFreeHost(c->host_eta);
     c->host_eta = nullptr;
-    cudaEvent_t evs[] = {c->ev_fork, c->ev_pf, c->ev_tu, c->ev_join_hi, c->ev_join_lo};
+    cudaEvent_t evs[] = {c->ev_fork, c->ev_pf, c->ev_tu, c->ev_join_hi, c->ev_join_lo, c->ev_steal};
     for (cudaEvent_t e : evs)
         if (e) cudaEventDestroy(e);
     if (c->hi) cudaStreamDestroy(c->hi);
@@ -78,7 +78,7 @@ int lu_ctx_reserve(lu_context* c, int64_t n, int nb) {
     nb = std::max(1, std::min(nb, LU_MAX_NB));
     const size_t nk = (size_t)std::max<int64_t>(1, lu_cdiv(std::max<int64_t>(n, 1), nb));
     const size_t plan_stride = 1 + 4 * (size_t)LU_MAX_NB;
-    const size_t need_sync = align_up(sizeof(LuSync) * 4, 256);
+    const size_t need_sync = align_up(sizeof(LuSync) * 8, 256);
     const size_t need_slots = align_up(sizeof(double) * (2 * LU_PF_MAX_CTAS * (LU_PF_MAX_LEAF + 1) + 2 * LU_PF_MAX_LEAF) +
                                            sizeof(int) * 2 * LU_PF_MAX_CTAS, 256);
     const size_t plans_cap = std::max(nk, c->plans_cap);
@@ -160,7 +160,7 @@ static lu_handle default_handle() {
 // ---------------------------------------------------------------------------
 // factorization driver
 // ---------------------------------------------------------------------------
-static int check_opts(const lu_opts& o) {
+int lu_check_opts(const lu_opts& o) {
     if (o.nb < 1 || o.nb > LU_MAX_NB) return -1;
     if (o.lookahead < 0 || o.lookahead > 1) return -1;
     if (o.leaf < 0 || o.pf_ctas < 0 || o.pf_ctas > LU_PF_MAX_CTAS) return -1;
@@ -169,10 +169,11 @@ static int check_opts(const lu_opts& o) {
 
 // TU restricted to columns [c_begin, c_end) for step k (panel columns [k0, k0+kb)):
 // laswp with panel k's plan, TRSM of the U12 block row, GEMM of the rows below.
+// With a tensor-core engine the GEMM is the tcgen05 update on packed operands.
 template <typename T>
-static int trailing_update(lu_context* c, cudaStream_t st, int64_t n, T* A, int64_t lda, int64_t k0,
-                           int64_t kb, int64_t c_begin, int64_t c_end, int64_t left_cols,
-                           const int32_t* plan) {
+static int trailing_update(lu_context* c, cudaStream_t st, int64_t n, T* A, int64_t lda, int64_t k, int64_t k0,
+                           int64_t kb, int64_t c_begin, int64_t c_end, int64_t left_cols, const int32_t* plan,
+                           const LuTuEngine* eng, int which) {
     const int64_t ncols = c_end - c_begin;
     if (ncols > 0 || left_cols > 0)
         LU_TRY(lu_launch_laswp_apply<T>(st, A, lda, c_begin, std::max<int64_t>(ncols, 0), 0, left_cols,
@@ -182,15 +183,17 @@ static int trailing_update(lu_context* c, cudaStream_t st, int64_t n, T* A, int6
     T* A12 = A + k0 + c_begin * lda;
     LU_TRY(lu_launch_trsm_lunit<T>(st, kb, ncols, A11, lda, A12, lda));
     const int64_t m2 = n - (k0 + kb);
-    if (m2 > 0)
-        LU_TRY(lu_launch_gemm_update<T>(st, m2, ncols, kb, A + (k0 + kb) + k0 * lda, lda, A12, lda,
-                                        A + (k0 + kb) + c_begin * lda, lda));
-    return LU_SUCCESS;
+    if (m2 <= 0) return LU_SUCCESS;
+    if (eng && eng->uses_tc(kb)) {
+        return eng->update(st, (float*)A, lda, k, k0, kb, c_begin, c_end, which);
+    }
+    return lu_launch_gemm_update<T>(st, m2, ncols, kb, A + (k0 + kb) + k0 * lda, lda, A12, lda,
+                                    A + (k0 + kb) + c_begin * lda, lda);
 }
 
 template <typename T>
-static int factor_impl(lu_context* c, int64_t n, T* A, int64_t lda, int32_t* ipiv, const lu_opts& o,
-                       int32_t* info) {
+int lu_factor_blocked(lu_context* c, int64_t n, T* A, int64_t lda, int32_t* ipiv, const lu_opts& o, int32_t* info,
+                      const LuTuEngine* eng) {
     const int nb = o.nb;
     LU_TRY(lu_ctx_reserve(c, n, nb));
     cudaStream_t user = c->user;
@@ -202,13 +205,15 @@ static int factor_impl(lu_context* c, int64_t n, T* A, int64_t lda, int32_t* ipi
     const int64_t nk = lu_cdiv(n, nb);
     auto plan_of = [&](int64_t k) { return c->plans + (size_t)k * c->plan_stride; };
     cudaStream_t hi = c->hi, lo = c->lo;
-
-    // PF(0)
-    {
-        const int64_t kb = std::min<int64_t>(nb, n);
-        LU_TRY(lu_panel_recursive<T>(c, hi, A, lda, n, 0, kb, ipiv, o));
-        LU_TRY(lu_launch_laswp_plan(hi, ipiv, 0, kb, plan_of(0)));
-    }
+    // PF(k) followed by its interchange plan (and, for the tensor-core engine, the packed L21)
+    auto panel = [&](int64_t k) -> int {
+        const int64_t k0 = k * nb, kb = std::min<int64_t>(nb, n - k0);
+        LU_TRY(lu_panel_recursive<T>(c, hi, A, lda, n, k0, kb, ipiv, o));
+        LU_TRY(lu_launch_laswp_plan(hi, ipiv, k0, k0 + kb, plan_of(k)));
+        if (eng && eng->uses_tc(kb) && k0 + kb < n) LU_TRY(eng->pack_panel(hi, (const float*)A, lda, k, k0, kb));
+        return LU_SUCCESS;
+    };
+    LU_TRY(panel(0));
     for (int64_t k = 0; k < nk; ++k) {
         const int64_t k0 = k * nb, kb = std::min<int64_t>(nb, n - k0);
         const int64_t c1 = k0 + kb;                       // first column right of panel k
@@ -217,21 +222,18 @@ static int factor_impl(lu_context* c, int64_t n, T* A, int64_t lda, int32_t* ipi
             LU_CHECK_CUDA(cudaEventRecord(c->ev_pf, hi));
             LU_CHECK_CUDA(cudaStreamWaitEvent(lo, c->ev_pf, 0));
             // TU_right(k) and the deferred left interchanges on the low-priority stream
-            LU_TRY(trailing_update<T>(c, lo, n, A, lda, k0, kb, c2, n, k0, plan_of(k)));
+            LU_TRY(trailing_update<T>(c, lo, n, A, lda, k, k0, kb, c2, n, k0, plan_of(k), eng, 1));
             LU_CHECK_CUDA(cudaEventRecord(c->ev_tu, lo));
             if (k + 1 < nk) {
                 // PU(k+1) = TU_k^L + PF_{k+1} on the high-priority stream
-                LU_TRY(trailing_update<T>(c, hi, n, A, lda, k0, kb, c1, c2, 0, plan_of(k)));
-                LU_TRY(lu_panel_recursive<T>(c, hi, A, lda, n, c1, c2 - c1, ipiv, o));
-                LU_TRY(lu_launch_laswp_plan(hi, ipiv, c1, c2, plan_of(k + 1)));
+                LU_TRY(trailing_update<T>(c, hi, n, A, lda, k, k0, kb, c1, c2, 0, plan_of(k), eng, 0));
+                LU_TRY(panel(k + 1));
+                if (eng && o.steal) LU_TRY(eng->steal(hi, k));
                 LU_CHECK_CUDA(cudaStreamWaitEvent(hi, c->ev_tu, 0));
             }
         } else {
-            LU_TRY(trailing_update<T>(c, hi, n, A, lda, k0, kb, c1, n, k0, plan_of(k)));
-            if (k + 1 < nk) {
-                LU_TRY(lu_panel_recursive<T>(c, hi, A, lda, n, c1, c2 - c1, ipiv, o));
-                LU_TRY(lu_launch_laswp_plan(hi, ipiv, c1, c2, plan_of(k + 1)));
-            }
+            LU_TRY(trailing_update<T>(c, hi, n, A, lda, k, k0, kb, c1, n, k0, plan_of(k), eng, 0));
+            if (k + 1 < nk) LU_TRY(panel(k + 1));
         }
     }
     LU_CHECK_CUDA(cudaEventRecord(c->ev_join_hi, hi));
@@ -240,6 +242,11 @@ static int factor_impl(lu_context* c, int64_t n, T* A, int64_t lda, int32_t* ipi
     LU_CHECK_CUDA(cudaStreamWaitEvent(user, c->ev_join_lo, 0));
     return lu_launch_finish_info(user, &c->sync[0], info);
 }
+
+template int lu_factor_blocked<double>(lu_context*, int64_t, double*, int64_t, int32_t*, const lu_opts&, int32_t*,
+                                       const LuTuEngine*);
+template int lu_factor_blocked<float>(lu_context*, int64_t, float*, int64_t, int32_t*, const lu_opts&, int32_t*,
+                                      const LuTuEngine*);
 
 extern "C" int lu_factor_ex(lu_handle h, lu_dtype dtype, int64_t n, void* A, int64_t lda, int32_t* ipiv,
                             const lu_opts* opts, int32_t* info) {
@@ -252,12 +259,12 @@ extern "C" int lu_factor_ex(lu_handle h, lu_dtype dtype, int64_t n, void* A, int
     lu_opts o;
     lu_default_opts(&o);
     if (opts) o = *opts;
-    if (check_opts(o) != 0) return -7;
+    if (lu_check_opts(o) != 0) return -7;
     if (!info) return -8;
     if (n > INT32_MAX / 2) return LU_ERR_UNSUPPORTED;
     std::lock_guard<std::mutex> lk(h->mu);
-    if (dtype == LU_F64) return factor_impl<double>(h, n, (double*)A, lda, ipiv, o, info);
-    return factor_impl<float>(h, n, (float*)A, lda, ipiv, o, info);
+    if (dtype == LU_F64) return lu_factor_blocked<double>(h, n, (double*)A, lda, ipiv, o, info, nullptr);
+    return lu_factor_blocked<float>(h, n, (float*)A, lda, ipiv, o, info, nullptr);
 }
 
 extern "C" int lu_factor(int64_t n, double* A, int64_t lda, int32_t* ipiv, int nb) {
@@ -382,7 +389,7 @@ extern "C" int lu_panel_factor_ex(lu_handle h, lu_dtype dtype, int64_t m, int64_
     lu_opts o;
     lu_default_opts(&o);
     if (opts) o = *opts;
-    if (check_opts(o) != 0) return -8;
+    if (lu_check_opts(o) != 0) return -8;
     if (!info) return -9;
     std::lock_guard<std::mutex> lk(h->mu);
     LU_TRY(lu_ctx_reserve(h, m, (int)std::max<int64_t>(w, 1)));

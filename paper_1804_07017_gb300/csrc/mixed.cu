@@ -1,6 +1,9 @@
 // Mixed-precision path: FP32 panels and factors, trailing update on the tensor
 // cores with bf16/fp16 operands and FP32 accumulation.
+#include <math.h>
+
 #include "internal.h"
+#include "ir.h"
 #include "pack.h"
 #include "tc.h"
 
@@ -54,4 +57,256 @@ extern "C" int lu_gemm_update_tc_ex(lu_handle h, lu_prec prec, int64_t m, int64_
                                    256));
     }
     return lu_launch_finish_info(st, &h->sync[2], info);
+}
+
+// ---------------------------------------------------------------------------
+// Tensor-core trailing-update engine for the FP32 blocked factorization.
+// ---------------------------------------------------------------------------
+namespace {
+
+struct TcEngine final : LuTuEngine {
+    lu_context* c = nullptr;
+    int prec = LU_TU_BF16;
+    int64_t n = 0;
+    int nb = 0;
+    char* alo[2] = {nullptr, nullptr};  // packed L21 (K-major), n x nb each
+    char* blo[2] = {nullptr, nullptr};  // packed U12 (K-major), n x nb each
+    int* counter[2] = {nullptr, nullptr};
+    int* error = nullptr;
+    int grid_panel = 0, grid_right = 0, grid_steal = 0;
+    cudaEvent_t ev_ready = nullptr;
+    mutable int64_t last_k = -1;
+    mutable int64_t last_k0 = 0, last_kb = 0, last_cb = 0, last_ce = 0;
+
+    int fmt_pack() const { return prec == LU_TU_FP16 ? LU_PACK_FP16 : LU_PACK_BF16; }
+    int fmt_mma() const { return prec == LU_TU_FP16 ? LU_TC_FMT_F16 : LU_TC_FMT_BF16; }
+
+    bool uses_tc(int64_t kb) const override { return (prec == LU_TU_BF16 || prec == LU_TU_FP16) && kb % 64 == 0; }
+
+    int pack_panel(cudaStream_t st, const float* A, int64_t lda, int64_t k, int64_t k0, int64_t kb) const override {
+        return lu_launch_pack_rows(st, fmt_pack(), A + (k0 + kb) + k0 * lda, lda, n - (k0 + kb), (int)kb, alo[k & 1]);
+    }
+
+    int launch(cudaStream_t st, float* A, int64_t lda, int64_t k, int64_t k0, int64_t kb, int64_t cb, int64_t ce,
+               int which, int grid) const {
+        const int64_t m = n - (k0 + kb);
+        const char* bbuf = blo[k & 1] + (size_t)(cb - (k0 + kb)) * kb * 2;
+        return lu_launch_tc_update(st, LU_TC_KIND_F16, fmt_mma(), A, lda, k0 + kb, m, cb, ce - cb, kb, alo[k & 1], m,
+                                   bbuf, ce - cb, 1.0f, counter[which], error, grid, 256);
+    }
+
+    int update(cudaStream_t st, float* A, int64_t lda, int64_t k, int64_t k0, int64_t kb, int64_t cb, int64_t ce,
+               int which) const override {
+        char* bbuf = blo[k & 1] + (size_t)(cb - (k0 + kb)) * kb * 2;
+        LU_TRY(lu_launch_pack_cols(st, fmt_pack(), A + k0 + cb * lda, lda, ce - cb, (int)kb, bbuf));
+        LU_CHECK_CUDA(cudaMemsetAsync(counter[which], 0, sizeof(int), st));
+        if (which == 1) {
+            LU_CHECK_CUDA(cudaEventRecord(ev_ready, st));
+            last_k = k;
+            last_k0 = k0;
+            last_kb = kb;
+            last_cb = cb;
+            last_ce = ce;
+        }
+        return launch(st, A, lda, k, k0, kb, cb, ce, which, which == 0 ? grid_panel : grid_right);
+    }
+
+    float* A_ = nullptr;
+    int64_t lda_ = 0;
+
+    int steal(cudaStream_t st, int64_t k) const override {
+        if (last_k != k || grid_steal <= 0) return LU_SUCCESS;
+        LU_CHECK_CUDA(cudaStreamWaitEvent(st, ev_ready, 0));
+        return launch(st, A_, lda_, k, last_k0, last_kb, last_cb, last_ce, 1, grid_steal);
+    }
+};
+
+size_t tc_engine_bytes(int64_t n, int nb) { return 4 * al256((size_t)n * nb * 2); }
+
+int setup_engine(TcEngine& e, lu_context* c, int prec, int64_t n, int nb, char* base, float* A, int64_t lda,
+                 const lu_opts& o) {
+    e.c = c;
+    e.prec = prec;
+    e.n = n;
+    e.nb = nb;
+    const size_t one = al256((size_t)n * nb * 2);
+    e.alo[0] = base;
+    e.alo[1] = base + one;
+    e.blo[0] = base + 2 * one;
+    e.blo[1] = base + 3 * one;
+    e.counter[0] = (int*)&c->sync[4].ticket;
+    e.counter[1] = (int*)&c->sync[5].ticket;
+    e.error = &c->sync[0].error;
+    e.A_ = A;
+    e.lda_ = lda;
+    // With look-ahead the right update leaves some SMs to the panel path; with
+    // stealing, that many CTAs join the right update once the panel is done.
+    const int reserve = (o.lookahead && o.steal) ? std::max(8, c->num_sms / 8) : 0;
+    e.grid_right = std::max(1, c->num_sms - reserve);
+    e.grid_panel = c->num_sms;
+    e.grid_steal = reserve;
+    e.ev_ready = c->ev_steal;
+    return LU_SUCCESS;
+}
+
+}  // namespace
+
+// FP32 factorization with a tensor-core trailing update (the factor step of the
+// mixed-precision solver).  A32 is overwritten by the FP32 factors.
+static int factor_mixed(lu_context* c, int prec, int64_t n, float* A32, int64_t lda, int32_t* ipiv, const lu_opts& o,
+                        int32_t* info, char* engine_mem) {
+    if (prec == LU_TU_F32) return lu_factor_blocked<float>(c, n, A32, lda, ipiv, o, info, nullptr);
+    TcEngine e;
+    LU_TRY(setup_engine(e, c, prec, n, o.nb, engine_mem, A32, lda, o));
+    return lu_factor_blocked<float>(c, n, A32, lda, ipiv, o, info, &e);
+}
+
+extern "C" int lu_factor_mixed_ex(lu_handle h, lu_prec prec, int64_t n, float* A, int64_t lda, int32_t* ipiv,
+                                  const lu_opts* opts, int32_t* info) {
+    if (!h) return LU_ERR_HANDLE;
+    if (prec != LU_TU_BF16 && prec != LU_TU_FP16 && prec != LU_TU_F32) return -2;
+    if (n < 0) return -3;
+    if (n > 0 && !A) return -4;
+    if (lda < std::max<int64_t>(1, n)) return -5;
+    if (n > 0 && !ipiv) return -6;
+    lu_opts o;
+    lu_default_opts(&o);
+    if (opts) o = *opts;
+    if (lu_check_opts(o) != 0) return -7;
+    if (!info) return -8;
+    if (n > INT32_MAX / 2) return LU_ERR_UNSUPPORTED;
+    std::lock_guard<std::mutex> lk(h->mu);
+    LU_TRY(lu_ctx_reserve(h, n, o.nb));
+    LU_TRY(lu_mx_reserve(h, tc_engine_bytes(std::max<int64_t>(n, 1), o.nb)));
+    return factor_mixed(h, prec, n, A, lda, ipiv, o, info, (char*)h->mx);
+}
+
+// ---------------------------------------------------------------------------
+// Mixed-precision solver with FP64 iterative refinement.
+// ---------------------------------------------------------------------------
+extern "C" int lu_gesv_mixed(lu_handle h, lu_prec prec, int64_t n, int64_t nrhs, const double* A, int64_t lda,
+                             const double* B, int64_t ldb, double* X, int64_t ldx, double tol, int max_iter,
+                             const lu_opts* opts, int* iters, double* bwd_err) {
+    if (!h) return LU_ERR_HANDLE;
+    if (prec != LU_TU_BF16 && prec != LU_TU_FP16 && prec != LU_TU_F32) return -2;
+    if (n < 0) return -3;
+    if (nrhs < 0) return -4;
+    if (n > 0 && !A) return -5;
+    if (lda < std::max<int64_t>(1, n)) return -6;
+    if (n > 0 && nrhs > 0 && !B) return -7;
+    if (ldb < std::max<int64_t>(1, n)) return -8;
+    if (n > 0 && nrhs > 0 && !X) return -9;
+    if (ldx < std::max<int64_t>(1, n)) return -10;
+    if (!(tol >= 0.0)) return -11;
+    if (max_iter < 0) return -12;
+    lu_opts o;
+    lu_default_opts(&o);
+    if (opts) o = *opts;
+    if (lu_check_opts(o) != 0) return -13;
+    if (iters) *iters = 0;
+    if (bwd_err) *bwd_err = 0.0;
+    if (n == 0 || nrhs == 0) return LU_SUCCESS;
+    if (n > INT32_MAX / 2) return LU_ERR_UNSUPPORTED;
+    std::lock_guard<std::mutex> lk(h->mu);
+    cudaStream_t st = h->user;
+    LU_TRY(lu_ctx_reserve(h, n, o.nb));
+    if (!h->host_eta) LU_CHECK_CUDA(cudaMallocHost(&h->host_eta, 4 * sizeof(double)));
+    // workspace layout
+    const int64_t ld32 = (n + 31) / 32 * 32;
+    const int64_t nch = lu_ir_nchunks(n);
+    const int64_t rhs_chunk = std::min<int64_t>(nrhs, 16);
+    size_t off = 0;
+    auto take = [&](size_t bytes) { size_t o0 = off; off += al256(bytes); return o0; };
+    const size_t o_a32 = take(sizeof(float) * (size_t)ld32 * n);
+    const size_t o_eng = take(tc_engine_bytes(n, o.nb));
+    const size_t o_ipiv = take(sizeof(int32_t) * n);
+    const size_t o_perm = take(sizeof(int32_t) * n);
+    const size_t o_r = take(sizeof(double) * n * nrhs);
+    const size_t o_xb = take(sizeof(double) * n * nrhs);
+    const size_t o_r32 = take(sizeof(float) * n * nrhs);
+    const size_t o_d32 = take(sizeof(float) * n * nrhs);
+    const size_t o_part = take(sizeof(double) * nch * rhs_chunk * n);
+    const size_t o_sc = take(sizeof(double) * (8 + nrhs) + sizeof(int32_t) * 8);
+    LU_TRY(lu_mx_reserve(h, off));
+    char* base = (char*)h->mx;
+    float* A32 = (float*)(base + o_a32);
+    int32_t* ipiv = (int32_t*)(base + o_ipiv);
+    int32_t* perm = (int32_t*)(base + o_perm);
+    double* R = (double*)(base + o_r);
+    double* Xb = (double*)(base + o_xb);
+    float* r32 = (float*)(base + o_r32);
+    float* d32 = (float*)(base + o_d32);
+    double* part = (double*)(base + o_part);
+    double* sc = (double*)(base + o_sc);
+    double* anorm = sc;
+    double* eta = sc + 1;
+    double* eta_cols = sc + 8;
+    int32_t* dinfo = (int32_t*)(sc + 8 + nrhs);
+    unsigned int* done = (unsigned int*)(dinfo + 2);
+    LU_CHECK_CUDA(cudaMemsetAsync(sc, 0, sizeof(double) * (8 + nrhs) + sizeof(int32_t) * 8, st));
+
+    // 1. FP32 working copy, factorization with the tensor-core trailing update
+    LU_TRY(lu_launch_f64_to_f32(st, n, n, A, lda, A32, ld32));
+    LU_TRY(factor_mixed(h, prec, n, A32, ld32, ipiv, o, dinfo, base + o_eng));
+    LU_TRY(lu_launch_perm_from_ipiv<float>(st, n, ipiv, perm));
+    LU_TRY(lu_launch_norm_inf(st, n, A, lda, part, anorm));
+    // 2. x0 = U^-1 L^-1 P b in FP32
+    LU_TRY(lu_launch_f64_to_f32(st, n, nrhs, B, ldb, r32, n));
+    LU_TRY(lu_launch_permute_rows<float>(st, n, nrhs, perm, r32, n, d32, n));
+    LU_TRY(lu_launch_trsv_blocked<float>(h, st, true, n, nrhs, A32, ld32, d32, n));
+    LU_TRY(lu_launch_trsv_blocked<float>(h, st, false, n, nrhs, A32, ld32, d32, n));
+    LU_TRY(lu_launch_f32_to_f64(st, n, nrhs, d32, n, X, ldx));
+    // 3. refinement: r = b - A x (FP64), eta test on the host, d = (LU)^-1 P r (FP32), x += d (FP64)
+    double best = INFINITY;
+    int best_it = -1, it = 0;
+    int status = LU_SUCCESS;
+    for (;; ++it) {
+        for (int64_t c0 = 0; c0 < nrhs; c0 += 16) {
+            const int64_t nr = std::min<int64_t>(16, nrhs - c0);
+            LU_TRY(lu_launch_residual(st, n, nr, A, lda, X + c0 * ldx, ldx, B + c0 * ldb, ldb, R + c0 * n, n, part));
+        }
+        LU_TRY(lu_launch_eta(st, n, nrhs, R, n, X, ldx, B, ldb, anorm, eta_cols, eta, done));
+        LU_CHECK_CUDA(cudaMemcpyAsync(h->host_eta, eta, sizeof(double), cudaMemcpyDeviceToHost, st));
+        LU_CHECK_CUDA(cudaMemcpyAsync(h->host_eta + 1, dinfo, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+        LU_CHECK_CUDA(cudaStreamSynchronize(st));
+        const int32_t finfo = *reinterpret_cast<int32_t*>(h->host_eta + 1);
+        if (finfo != 0) {
+            status = finfo;  // exactly singular U (i > 0) or a device-side timeout (< 0)
+            break;
+        }
+        const double e = h->host_eta[0];
+        if (e < best) {
+            best = e;
+            best_it = it;
+            if (e > tol && it < max_iter)
+                LU_CHECK_CUDA(cudaMemcpy2DAsync(Xb, n * sizeof(double), X, ldx * sizeof(double), n * sizeof(double),
+                                                nrhs, cudaMemcpyDeviceToDevice, st));
+        }
+        if (e <= tol) break;
+        if (it >= max_iter || !(e == e)) {
+            status = LU_WARN_NOT_CONVERGED;
+            break;
+        }
+        LU_TRY(lu_launch_f64_to_f32(st, n, nrhs, R, n, r32, n));
+        LU_TRY(lu_launch_permute_rows<float>(st, n, nrhs, perm, r32, n, d32, n));
+        LU_TRY(lu_launch_trsv_blocked<float>(h, st, true, n, nrhs, A32, ld32, d32, n));
+        LU_TRY(lu_launch_trsv_blocked<float>(h, st, false, n, nrhs, A32, ld32, d32, n));
+        LU_TRY(lu_launch_add_f32_to_f64(st, n, nrhs, d32, n, X, ldx));
+    }
+    if (status == LU_WARN_NOT_CONVERGED && best_it >= 0 && best_it != it) {
+        LU_CHECK_CUDA(cudaMemcpy2DAsync(X, ldx * sizeof(double), Xb, n * sizeof(double), n * sizeof(double), nrhs,
+                                        cudaMemcpyDeviceToDevice, st));
+        LU_CHECK_CUDA(cudaStreamSynchronize(st));
+    }
+    if (iters) *iters = (status == LU_WARN_NOT_CONVERGED) ? best_it : it;
+    if (bwd_err) *bwd_err = best;
+    if (status == LU_SUCCESS) {
+        int err = 0;
+        LU_CHECK_CUDA(cudaMemcpy(&err, &h->sync[1].error, sizeof(int), cudaMemcpyDeviceToHost));
+        if (err != 0) {
+            cudaMemset(&h->sync[1].error, 0, sizeof(int));
+            return err;
+        }
+    }
+    return status;
 }

@@ -1,0 +1,136 @@
+"""GPU checks of the mixed-precision path: FP32 panels + tensor-core trailing
+update (bf16 / fp16; FP32 on the CUDA cores as a reference point) and FP64
+iterative refinement.
+
+Pass criteria: after refinement the normwise backward error eta of every
+solution, recomputed by the oracle in FP64 with compensated sums, is
+<= 1e-14.  The factorization error of the low-precision factors, the number
+of refinements and the forward error against the FP64 oracle's solution are
+reported numbers (printed), each with a loose sanity bound.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lu():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import paper_1804_07017_gb300 as pkg
+    pkg.lib()
+    return pkg
+
+
+def dev(a, dtype=torch.float64):
+    from paper_1804_07017_gb300.api import colmajor
+    a = np.asarray(a)
+    if a.ndim == 1:
+        a = a[:, None]
+    t = colmajor(a.shape[0], a.shape[1], dtype=dtype)
+    t.copy_(torch.from_numpy(np.ascontiguousarray(a)).to(dtype))
+    return t
+
+
+PRECS = {"bf16": 0, "fp16": 1, "f32": 3}
+UOP = {"bf16": 2.0 ** -9, "fp16": 2.0 ** -11, "f32": 2.0 ** -24}
+
+
+@pytest.mark.parametrize("prec", ["bf16", "fp16", "f32"])
+@pytest.mark.parametrize("n,nb", [(1024, 128), (2048, 256), (1000, 64)])
+def test_factor_mixed(lu, prec, n, nb):
+    A0 = synth.normal_matrix(n, seed=40, stream=n).astype(np.float32).astype(np.float64)
+    A = dev(A0, torch.float32)
+    ipiv = torch.zeros(n, dtype=torch.int32, device="cuda")
+    info = torch.full((1,), -7, dtype=torch.int32, device="cuda")
+    lu.lu_factor_mixed_ex(A, ipiv, info, PRECS[prec], lu.default_opts(nb=nb))
+    torch.cuda.synchronize()
+    assert int(info.item()) == 0
+    piv = ipiv.cpu().numpy()
+    ferr = oracle.factor_error(A0, A.cpu().double().numpy(), piv)
+    _, piv_o, _, gap = oracle.getrf(A0)
+    ndiff = int((piv != piv_o).sum())
+    print(f"\n[mixed factor] prec={prec} n={n} nb={nb}: ||PA-LU||/(n||A||) = {ferr:.3e}, "
+          f"pivots differing from the FP64 oracle: {ndiff}/{n}")
+    assert ferr <= 8 * UOP[prec]
+
+
+@pytest.mark.parametrize("prec", ["bf16", "fp16", "f32"])
+@pytest.mark.parametrize("n,nb,nrhs,kind", [(1024, 128, 1, "uniform"), (2048, 256, 1, "normal"),
+                                            (2048, 256, 16, "normal"), (1500, 128, 19, "normal"),
+                                            (2048, 256, 1, "rowscaled")])
+def test_gesv_mixed(lu, prec, n, nb, nrhs, kind):
+    if kind == "uniform":
+        A0 = synth.uniform_matrix(n, seed=0)
+    elif kind == "normal":
+        A0 = synth.normal_matrix(n, seed=41)
+    else:
+        A0 = synth.row_scaled(synth.normal_matrix(n, seed=42), seed=42)
+    if nrhs == 1:
+        B0 = synth.ones_rhs(A0)
+    else:
+        B0, _ = synth.random_rhs(A0, nrhs, seed=43)
+    X = dev(np.zeros_like(B0))
+    status, iters, eta_gpu = lu.lu_gesv_mixed(dev(A0), dev(B0), X, PRECS[prec], 1e-14, 30, lu.default_opts(nb=nb))
+    torch.cuda.synchronize()
+    x = X.cpu().numpy()
+    eta = oracle.backward_error(A0, x, B0)
+    LUo, pivo, _, _ = oracle.getrf(A0)
+    x_or = oracle.getrs(LUo, pivo, B0)
+    fwd = np.abs(x - x_or).max() / np.abs(x_or).max()
+    print(f"\n[gesv_mixed] prec={prec} n={n} nrhs={nrhs} {kind}: status={status} refinements={iters} "
+          f"eta(gpu)={eta_gpu:.2e} eta(oracle)={eta:.2e} ||x-x_oracle||/||x_oracle||={fwd:.2e}")
+    assert status == 0
+    assert eta <= 1e-14
+    assert iters <= 30
+
+
+def test_gesv_mixed_repeatable(lu):
+    n = 1024
+    A0 = synth.normal_matrix(n, seed=44)
+    B0 = synth.ones_rhs(A0)
+    xs = []
+    for _ in range(2):
+        X = dev(np.zeros_like(B0))
+        lu.lu_gesv_mixed(dev(A0), dev(B0), X, PRECS["bf16"], 1e-14, 30, lu.default_opts(nb=128))
+        torch.cuda.synchronize()
+        xs.append(X.cpu().numpy())
+    assert np.array_equal(xs[0], xs[1])
+
+
+def test_gesv_mixed_lookahead_variants_agree(lu):
+    """The three schedules (no look-ahead, look-ahead, look-ahead + stealing)
+    run the same arithmetic, so the FP32 factors are bit-identical."""
+    n, nb = 2048, 256
+    A0 = synth.normal_matrix(n, seed=45).astype(np.float32)
+    outs = []
+    for la, st in ((0, 0), (1, 0), (1, 1)):
+        A = dev(A0, torch.float32)
+        ipiv = torch.zeros(n, dtype=torch.int32, device="cuda")
+        info = torch.zeros(1, dtype=torch.int32, device="cuda")
+        lu.lu_factor_mixed_ex(A, ipiv, info, PRECS["bf16"], lu.default_opts(nb=nb, lookahead=la, steal=st))
+        torch.cuda.synchronize()
+        outs.append((A.cpu().numpy(), ipiv.cpu().numpy()))
+    for a, p in outs[1:]:
+        assert np.array_equal(a, outs[0][0]) and np.array_equal(p, outs[0][1])
+
+
+def test_gesv_mixed_16384_sampled(lu):
+    """The n = 16384, N(0,1), 1-RHS configuration at full size: the backward
+    error of the returned x over the whole system, recomputed on the host."""
+    n = 16384
+    A0 = synth.normal_matrix(n, seed=0)
+    B0 = synth.ones_rhs(A0)
+    X = dev(np.zeros_like(B0))
+    status, iters, eta_gpu = lu.lu_gesv_mixed(dev(A0), dev(B0), X, PRECS["bf16"], 1e-14, 30, lu.default_opts(nb=256))
+    torch.cuda.synchronize()
+    x = X.cpu().numpy()[:, 0]
+    r = B0[:, 0] - A0 @ x
+    eta = np.abs(r).max() / (np.abs(A0).sum(axis=1).max() * np.abs(x).max() + np.abs(B0).max())
+    print(f"\n[gesv_mixed 16384] status={status} refinements={iters} eta(gpu)={eta_gpu:.2e} eta(host)={eta:.2e}")
+    assert status == 0 and eta <= 1e-14

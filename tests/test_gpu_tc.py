@@ -52,11 +52,11 @@ def test_tc_update(lu, prec_name, m, n, k):
     u32 = np.finfo(np.float32).eps / 2
     err = np.abs(got - ref)
     assert np.all(err <= (k + 2) * u32 * scale), (err / scale).max()
-    # the rounding actually happened: against unrounded operands the result differs
-    # by about the operand rounding, far above the accumulation bound
+    # the rounding actually happened: against the unrounded operands some entries
+    # differ by more than the accumulation bound
     if m * n > 1000:
         ref_unrounded = oracle.gemm_update(C0, A0, B0)
-        assert np.abs(got - ref_unrounded).max() > 10 * ((k + 2) * u32 * scale).min()
+        assert np.any(np.abs(got - ref_unrounded) > (k + 2) * u32 * scale)
 
 
 def test_tc_update_repeatable(lu):
