@@ -1,0 +1,367 @@
+"""Benchmark: LU + solve GFLOP/s (2 n^3 / 3 per solve) on one GB300.
+
+Workload (default): the mixed-precision solver at n = 16384 -- A with iid
+N(0,1) entries (seed 0), one right-hand side b = A * ones, FP32 panel
+factorization, split-bf16 (bf16x3) tensor-core trailing update with FP32 accumulation,
+depth-1 look-ahead, FP64 iterative refinement to a normwise backward error
+<= 1e-14 (at most 30 corrections).  One step = one lu_gesv_mixed call (the
+factorization, the solve and every refinement iteration), with A and b
+resident in HBM (2 GiB, larger than L2).  The plain FP64 look-ahead LU + solve
+(+ FP64 refinement to the same 1e-14) is timed beside it on the same GPU.
+
+JSON line keys follow the harness contract: value / ms_per_step are the
+mixed solver's; "fp64_path" holds the FP64 comparison; "roofline" the
+dominant kernel measured with the library's per-launch CUDA events over the
+timed region; "cpu_baseline" the CPU oracle on a bounded sample.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_DEFAULT = 16384
+NB_DEFAULT = 256
+TOL = 1e-14
+MAX_ITER = 30
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), float(d["bf16_tflops"]), float(d.get("bf16_tflops_sustained", d["bf16_tflops"])), "measured"
+    except Exception:
+        return 6800.0, 1900.0, 1700.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks/throttle reasons sampled every 200 ms during the timed region."""
+
+    def __init__(self, index: int = 0):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        os.makedirs(os.path.dirname(self.path), exist_ok=True)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        try:
+            rows = [ln.split(",") for ln in open(self.path).read().strip().splitlines() if ln.strip()]
+        except Exception:
+            rows = []
+        sm = [float(r[1]) for r in rows if len(r) > 8 and r[1].strip().replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if len(r) > 8 and r[2].strip().replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            if len(r) > 8:
+                for nm, v in zip(names, r[5:9]):
+                    if "Active" in v and "Not" not in v:
+                        reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def make_inputs(n: int, nrhs: int, seed: int = 0):
+    import synth
+    A = synth.normal_matrix(n, seed=seed)
+    B = synth.ones_rhs(A, nrhs) if nrhs == 1 else synth.random_rhs(A, nrhs, seed=seed)[0]
+    return A, B
+
+
+def cpu_oracle_sample(n: int, seed: int, budget_s: float = 15.0):
+    """The CPU oracle (unblocked FP64 GEPP, OpenMP over columns of each rank-1
+    update) on the leading elimination steps of the same n x n matrix: time a
+    growing number of steps until ~budget_s of CPU work, report the flops those
+    steps perform (sum over steps j of 2 (n-j-1)^2 + (n-j-1)) per second."""
+    import numpy as np
+    import oracle
+    import synth
+    A = np.asfortranarray(synth.normal_matrix(n, seed=seed))
+    steps = 8
+    while True:
+        W = A.copy(order="F")
+        t0 = time.perf_counter()
+        oracle.getrf_steps_inplace(W, steps)
+        dt = time.perf_counter() - t0
+        if dt > budget_s / 3 or steps >= n:
+            break
+        steps = min(n, int(steps * max(2.0, (budget_s / 3) / max(dt, 1e-3))))
+    j = np.arange(steps, dtype=np.float64)
+    flops = float(np.sum(2.0 * (n - j - 1) ** 2 + (n - j - 1)))
+    return {"value": flops / dt / 1e9, "unit": "GFLOP/s", "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"first {steps} of {n} elimination steps of the unblocked FP64 oracle on the same "
+                      f"N(0,1) n={n} matrix ({dt:.1f} s, {flops:.3e} flops)", "seconds": dt}
+
+
+def run_reference(args):
+    """--impl reference: the CPU oracle as it stands, timed on the host cores on a
+    bounded sample of the same workload (rank 0 only)."""
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    n = args.n
+    budget = float(os.environ.get("LU_BENCH_REF_BUDGET_S", "6"))
+    vals = []
+    for _ in range(max(args.warmup, 0)):
+        cpu_oracle_sample(n, 0, budget_s=budget / 4)
+    sample = None
+    for _ in range(args.steps):
+        sample = cpu_oracle_sample(n, 0, budget_s=budget)
+        vals.append(sample["value"])
+    v = statistics.median(vals)
+    line = {"impl": "reference", "metric": "LU+solve GFLOP/s (2n^3/3), mixed+IR vs FP64 on same GB300 at bwd err <=1e-14",
+            "value": v, "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": workload_config(args),
+            "cpu_baseline": {"value": v, "unit": "GFLOP/s", "cores": sample["cores"], "kind": "oracle",
+                             "sample": sample["sample"]},
+            "e2e": {"value": v, "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def workload_config(args):
+    return {"workload": f"mixed-precision LU+solve+FP64 IR, n={args.n}, nb={args.nb}, N(0,1) seed 0, "
+                        f"{args.nrhs} rhs b=A*ones, FP32 panels, {args.prec} tensor-core TU, depth-1 look-ahead",
+            "n": args.n, "nb": args.nb, "nrhs": args.nrhs, "tu": args.prec, "lookahead": 1,
+            "tol": TOL, "max_iter": MAX_ITER, "l2": "inputs larger than L2 (A is 2 GiB FP64)"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--n", type=int, default=N_DEFAULT)
+    ap.add_argument("--nb", type=int, default=NB_DEFAULT)
+    ap.add_argument("--nrhs", type=int, default=1)
+    ap.add_argument("--prec", default="bf16x3", choices=["bf16x3", "bf16", "fp16", "f32"])
+    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison path")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle sample")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+
+    import paper_1804_07017_gb300 as lu
+    from paper_1804_07017_gb300 import _lib
+    from paper_1804_07017_gb300.api import colmajor
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    L = lu.lib()
+    n, nrhs = args.n, args.nrhs
+    prec = {"bf16": lu.LU_TU_BF16, "fp16": lu.LU_TU_FP16, "f32": lu.LU_TU_F32, "bf16x3": lu.LU_TU_BF16X3}[args.prec]
+    opts = lu.default_opts(nb=args.nb)
+    A0, B0 = make_inputs(n, nrhs)
+    A = colmajor(n, n)
+    A.copy_(torch.from_numpy(A0))
+    B = colmajor(n, nrhs)
+    B.copy_(torch.from_numpy(B0))
+    X = colmajor(n, nrhs)
+    flops = 2.0 * n ** 3 / 3.0
+
+    def step():
+        return lu.lu_gesv_mixed(A, B, X, prec, TOL, MAX_ITER, opts)
+
+    for _ in range(args.warmup):
+        step()
+    barrier()
+    L.lu_profile_reset()
+    L.lu_profile_enable(1)
+    launches0 = lu.lu_launch_count()
+    results = []
+    stream = torch.cuda.current_stream()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        barrier()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            results.append(step())
+        ev1.record(stream)
+        barrier()
+    L.lu_profile_enable(0)
+    launches = lu.lu_launch_count() - launches0
+    ms_total = ev0.elapsed_time(ev1)
+    if dist is not None:
+        t = torch.tensor([ms_total], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_total = float(t.item())
+    ms_step = ms_total / args.steps
+    value = world * flops / (ms_step * 1e-3) / 1e9
+    statuses = [r[0] for r in results]
+    iters = [r[1] for r in results]
+    etas = [r[2] for r in results]
+
+    # per-class kernel time over the timed region (library CUDA events on each launch's stream)
+    prof = {}
+    for i, name in enumerate(_lib.KERNEL_CLASSES):
+        cnt, ms, by, fl = (np.int64(0), np.float64(0), np.float64(0), np.float64(0))
+        import ctypes
+        c_cnt, c_ms, c_by, c_fl = ctypes.c_int64(), ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        L.lu_profile_read(i, ctypes.byref(c_cnt), ctypes.byref(c_ms), ctypes.byref(c_by), ctypes.byref(c_fl))
+        prof[name] = {"launches": c_cnt.value, "ms": c_ms.value, "bytes": c_by.value, "flops": c_fl.value}
+    clocks = clk.summary()
+
+    hbm, bf16_burst, bf16_sust, peak_src = load_peaks()
+    # dominant kernel: the class with the largest summed launch time
+    dom = max(prof, key=lambda k: prof[k]["ms"])
+    d = prof[dom]
+    avg_ms = d["ms"] / max(d["launches"], 1)
+    avg_bytes = d["bytes"] / max(d["launches"], 1)
+    avg_flops = d["flops"] / max(d["launches"], 1)
+    if dom == "tc_update":
+        # HBM-bound at nb = 256: 8 bytes of FP32 C per element vs 2 nb flops (nb/4 flop/byte << ridge)
+        ach = avg_bytes / (avg_ms * 1e-3) / 1e9
+        roof = {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                "peak_source": peak_src, "traffic": None, "bytes_per_launch": avg_bytes,
+                "avg_launch_ms": avg_ms, "launches": d["launches"],
+                "tensor_tflops": avg_flops / (avg_ms * 1e-3) / 1e12}
+    else:
+        ach = avg_bytes / (avg_ms * 1e-3) / 1e9
+        roof = {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                "peak_source": peak_src, "traffic": None, "bytes_per_launch": avg_bytes, "avg_launch_ms": avg_ms,
+                "launches": d["launches"]}
+    total_kernel_ms = sum(v["ms"] for v in prof.values())
+    shares = {k: round(v["ms"] / total_kernel_ms, 4) for k, v in prof.items() if v["launches"]}
+
+    # end to end through the C ABI with host buffers: H2D of A and b, solve, D2H of x
+    e2e = None
+    if rank == 0 or world > 1:
+        A_h = torch.from_numpy(np.asfortranarray(A0).T.copy()).pin_memory()  # row-major view of column-major data
+        B_h = torch.from_numpy(np.asfortranarray(B0).T.copy()).pin_memory()
+        X_h = torch.empty((nrhs, n), dtype=torch.float64).pin_memory()
+        At = A.t()  # (n, n) row-major view of the column-major device buffer
+        Bt = B.t()
+        Xt = X.t()
+        e_steps = max(1, min(args.steps, 3))
+        barrier()
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for _ in range(e_steps):
+            At.copy_(A_h, non_blocking=True)
+            Bt.copy_(B_h, non_blocking=True)
+            step()
+            X_h.copy_(Xt, non_blocking=True)
+        t1.record(stream)
+        torch.cuda.synchronize()
+        e_ms = t0.elapsed_time(t1) / e_steps
+        e2e = {"value": world * flops / (e_ms * 1e-3) / 1e9, "unit": "GFLOP/s",
+               "h2d_bytes_per_step": 8 * n * n + 8 * n * nrhs, "d2h_bytes_per_step": 8 * n * nrhs,
+               "ms_per_step": e_ms}
+
+    # plain FP64 look-ahead LU + solve (+ FP64 refinement to the same tolerance) on the same GPU
+    fp64 = None
+    if not args.no_fp64 and rank == 0:
+        fp64 = fp64_path(lu, A0, B0, n, nrhs, args.nb)
+
+    cpu = None
+    if not args.no_cpu and rank == 0:
+        cpu = cpu_oracle_sample(n, 0, budget_s=float(os.environ.get("LU_BENCH_CPU_BUDGET_S", "15")))
+        cpu.pop("seconds", None)
+
+    if rank == 0:
+        ok = all(s == 0 for s in statuses) and max(etas) <= TOL
+        line = {
+            "metric": "LU+solve GFLOP/s (2n^3/3), mixed+IR vs FP64 on same GB300 at bwd err <=1e-14",
+            "value": value, "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": {"bf16": "f32+bf16", "bf16x3": "f32+bf16x3", "fp16": "f32+fp16", "f32": "f32"}[args.prec] + "+f64-ir",
+            "data": "synthetic", "config": workload_config(args) | {"parallelism": f"replicas{world}"},
+            "converged": ok, "refinements": iters, "bwd_err": max(etas),
+            "gpu_launches": launches, "kernel_time_share": shares,
+            "roofline": roof, "clocks": clocks, "e2e": e2e, "fp64_path": fp64, "cpu_baseline": cpu,
+        }
+        if fp64 and fp64.get("value"):
+            line["speedup_vs_fp64_path"] = value / fp64["value"]
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def fp64_path(lu, A0, B0, n, nrhs, nb):
+    """FP64 look-ahead LU + solve; FP64 refinement (FP64 solves) until eta <= 1e-14."""
+    import numpy as np
+    import torch
+
+    from paper_1804_07017_gb300.api import colmajor
+    r = lu.lu_gesv_mixed  # noqa: F841  (same C ABI library)
+    A = colmajor(n, n)
+    Ad = colmajor(n, n)
+    Ad.copy_(torch.from_numpy(A0))
+    Bd = colmajor(n, nrhs)
+    Bd.copy_(torch.from_numpy(B0))
+    X = colmajor(n, nrhs)
+    status, iters, eta = None, None, None
+    try:
+        status, iters, eta = lu.lu_gesv_mixed(Ad, Bd, X, lu.LU_FULL_F64, TOL, MAX_ITER, lu.default_opts(nb=nb))
+        torch.cuda.synchronize()
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record()
+        status, iters, eta = lu.lu_gesv_mixed(Ad, Bd, X, lu.LU_FULL_F64, TOL, MAX_ITER, lu.default_opts(nb=nb))
+        t1.record()
+        torch.cuda.synchronize()
+        ms = t0.elapsed_time(t1)
+    except Exception as e:  # reported, not fatal for the headline
+        return {"error": str(e)}
+    del A
+    return {"value": 2.0 * n ** 3 / 3.0 / (ms * 1e-3) / 1e9, "unit": "GFLOP/s", "ms_per_step": ms, "steps": 1,
+            "warmup": 1, "refinements": iters, "bwd_err": eta, "status": status,
+            "what": "FP64 factorization (same look-ahead schedule, SIMT DFMA trailing update) + FP64 solve + FP64 refinement"}
+
+
+if __name__ == "__main__":
+    sys.exit(main())

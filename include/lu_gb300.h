@@ -58,7 +58,11 @@ typedef enum {
     LU_TU_BF16 = 0, /* bf16 operands, tcgen05.mma kind::f16 */
     LU_TU_FP16 = 1, /* fp16 operands, tcgen05.mma kind::f16 */
     LU_TU_FP8 = 2,  /* e4m3 operands with power-of-two block scales, kind::f8f6f4 */
-    LU_TU_F32 = 3   /* FP32 on the CUDA cores (no tensor cores; a reference point) */
+    LU_TU_F32 = 3,  /* FP32 on the CUDA cores (no tensor cores; a reference point) */
+    LU_TU_BF16X3 = 4, /* split bf16: each FP32 operand as hi + lo bf16, three products
+                         (hi*hi + hi*lo + lo*hi) accumulated in FP32, kind::f16 */
+    LU_FULL_F64 = 5 /* lu_gesv_mixed only: FP64 factors and FP64 correction solves
+                       (the plain FP64 path, refined the same way) */
 } lu_prec;
 
 /* Options of a blocked factorization (Sec. 3-4 of the paper). */
@@ -90,6 +94,28 @@ int lu_set_stream(lu_handle handle, void *stream);
 int64_t lu_launch_count(void);
 /* Text of the last CUDA error seen by the library (static storage). */
 const char *lu_last_error(void);
+
+/* Kernel classes of the built-in launch profiler. */
+enum {
+    LU_K_PANEL = 0,     /* panel-factorization leaf (RL1) */
+    LU_K_LASWP = 1,     /* interchange plans and row interchanges */
+    LU_K_TRSM = 2,      /* RL2 */
+    LU_K_GEMM = 3,      /* RL3 on the CUDA cores */
+    LU_K_TC_UPDATE = 4, /* RL3 on the tensor cores */
+    LU_K_PACK = 5,      /* operand rounding / packing for the tensor cores */
+    LU_K_SOLVE = 6,     /* triangular solves and row permutations of a solve */
+    LU_K_RESIDUAL = 7,  /* FP64 residuals, norms, conversions of the refinement */
+    LU_K_OTHER = 8,
+    LU_K_COUNT = 9
+};
+/* lu_profile_enable(1): from now on every kernel launch is bracketed by two CUDA
+ * events recorded on its own stream.  lu_profile_read synchronises the device
+ * and returns, for one class, the number of launches since the last reset, the
+ * sum of their event-to-event durations (ms) and of their algorithmic bytes
+ * and flops (host pointers, any may be NULL).  lu_profile_reset clears. */
+int lu_profile_enable(int on);
+int lu_profile_reset(void);
+int lu_profile_read(int kclass, int64_t *launches, double *ms, double *bytes, double *flops);
 
 /*
  * lu_factor -- P A = L U of an n x n FP64 matrix, in place (LU_blk, RL1-RL3,
@@ -175,7 +201,7 @@ int lu_gemm_update_ex(lu_handle handle, lu_dtype dtype, int64_t m, int64_t n, in
 /*
  * lu_gemm_update_tc_ex -- RL3, C := C - A B on the tensor cores: A (m x k) and
  * B (k x n) are FP32 and are rounded to the operand type of `prec` (round to
- * nearest even; LU_TU_BF16 or LU_TU_FP16), the products accumulate in FP32
+ * nearest even; LU_TU_BF16, LU_TU_FP16 or LU_TU_BF16X3), the products accumulate in FP32
  * and C (FP32, m x n) is updated in place.  k must be a multiple of 64.
  *   info  device int32[1]; 0, or LU_ERR_TIMEOUT if a bounded wait expired.
  */
@@ -193,7 +219,8 @@ int lu_gemm_update_tc_ex(lu_handle handle, lu_prec prec, int64_t m, int64_t n, i
  * look-ahead schedule as lu_factor_ex, whose trailing update (RL3) runs on the
  * tensor cores with operands rounded to `prec` (LU_TU_BF16 / LU_TU_FP16) and
  * FP32 accumulation; LU_TU_F32 keeps it on the CUDA cores.  When nb is not a
- * multiple of 64 the update falls back to FP32 on the CUDA cores.
+ * multiple of 64 the update falls back to FP32 on the CUDA cores.  LU_TU_BF16X3
+ * runs the same kernel on split operands with a three times longer K.
  * Asynchronous; info as in lu_factor_ex.
  */
 int lu_factor_mixed_ex(lu_handle handle, lu_prec prec, int64_t n, float *A, int64_t lda, int32_t *ipiv,
@@ -201,7 +228,8 @@ int lu_factor_mixed_ex(lu_handle handle, lu_prec prec, int64_t n, float *A, int6
 
 /*
  * lu_gesv_mixed -- solve A X = B for an n x n FP64 matrix A and n x nrhs FP64
- * B: copy A to FP32, factor it with lu_factor_mixed_ex, solve in FP32, then
+ * B: copy A to FP32, factor it with lu_factor_mixed_ex, solve in FP32 (with
+ * prec = LU_FULL_F64: copy, factor and solve in FP64 instead), then
  * refine in FP64: r = B - A X with the original A, stop when the normwise
  * backward error eta = max_c ||r_c|| / (||A|| ||x_c|| + ||b_c||) (inf-norms)
  * is <= tol, or after max_iter corrections.

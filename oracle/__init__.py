@@ -61,6 +61,7 @@ def _load():
         sig = {
             "oracle_num_threads": (i32, []),
             "oracle_getrf": (i32, [i64, i64, vp, i64, vp, vp, i32]),
+            "oracle_getrf_steps": (i32, [i64, i64, vp, i64, vp, vp, i32, i64]),
             "oracle_laswp": (None, [i64, vp, i64, i64, i64, vp]),
             "oracle_trsm_lower_unit": (None, [i64, i64, vp, i64, vp, i64]),
             "oracle_trsm_upper": (None, [i64, i64, vp, i64, vp, i64]),
@@ -111,6 +112,16 @@ def getrf(A, nthreads: int = 0):
     gap = np.zeros(max(k, 1), dtype=np.float64)
     info = lib.oracle_getrf(m, n, _ptr(LU), max(m, 1), _ptr(ipiv), _ptr(gap), int(nthreads))
     return LU, ipiv[:k].copy(), int(info), gap[:k].copy()
+
+
+def getrf_steps_inplace(A: np.ndarray, steps: int, nthreads: int = 0) -> int:
+    """Run the first `steps` elimination steps of getrf in place on a
+    Fortran-ordered float64 array (no copy; used to time a bounded sample)."""
+    lib = _load()
+    assert A.dtype == np.float64 and A.flags["F_CONTIGUOUS"]
+    m, n = A.shape
+    ipiv = np.zeros(max(min(m, n), 1), dtype=np.int32)
+    return int(lib.oracle_getrf_steps(m, n, _ptr(A), max(m, 1), _ptr(ipiv), None, int(nthreads), int(steps)))
 
 
 def laswp(A, k1: int, k2: int, ipiv):

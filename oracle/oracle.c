@@ -71,12 +71,16 @@ int oracle_num_threads(void)
  * element still sees the same operation sequence, so results do not depend on
  * the thread count.
  * Returns info: 0, or the 1-based index of the first exactly-zero pivot.
+ * oracle_getrf_steps stops after the first `steps` elimination steps (all of
+ * them when steps < 0): the leading part of the same computation, used to
+ * time a bounded sample of a large factorization.
  */
-int oracle_getrf(int64_t m, int64_t n, double *A, int64_t lda, int32_t *ipiv,
-                 double *gap, int nthreads)
+int oracle_getrf_steps(int64_t m, int64_t n, double *A, int64_t lda, int32_t *ipiv,
+                       double *gap, int nthreads, int64_t steps)
 {
     int info = 0;
     int64_t kmax = m < n ? m : n;
+    if (steps >= 0 && steps < kmax) kmax = steps;
 #ifdef _OPENMP
     if (nthreads < 1) nthreads = omp_get_max_threads();
 #else
@@ -129,6 +133,12 @@ int oracle_getrf(int64_t m, int64_t n, double *A, int64_t lda, int32_t *ipiv,
         }
     }
     return info;
+}
+
+int oracle_getrf(int64_t m, int64_t n, double *A, int64_t lda, int32_t *ipiv,
+                 double *gap, int nthreads)
+{
+    return oracle_getrf_steps(m, n, A, lda, ipiv, gap, nthreads, -1);
 }
 
 /*

@@ -19,10 +19,14 @@ LU_WARN_NOT_CONVERGED = 0x40000000
 LU_F64 = 0
 LU_F32 = 1
 
+KERNEL_CLASSES = ["panel", "laswp", "trsm", "gemm", "tc_update", "pack", "solve", "residual", "other"]
+
 LU_TU_BF16 = 0
 LU_TU_FP16 = 1
 LU_TU_FP8 = 2
 LU_TU_F32 = 3
+LU_TU_BF16X3 = 4
+LU_FULL_F64 = 5
 
 
 class LuError(RuntimeError):
@@ -57,6 +61,10 @@ _SIGNATURES = {
     "lu_trsm_ex": (i32, [vp, i32, i64, i64, vp, i64, vp, i64]),
     "lu_gemm_update_ex": (i32, [vp, i32, i64, i64, i64, vp, i64, vp, i64, vp, i64]),
     "lu_gemm_update_tc_ex": (i32, [vp, i32, i64, i64, i64, vp, i64, vp, i64, vp, i64, vp]),
+    "lu_profile_enable": (i32, [i32]),
+    "lu_profile_reset": (i32, []),
+    "lu_profile_read": (i32, [i32, ctypes.POINTER(i64), ctypes.POINTER(dbl), ctypes.POINTER(dbl),
+                              ctypes.POINTER(dbl)]),
     "lu_factor_mixed_ex": (i32, [vp, i32, i64, vp, i64, vp, ctypes.POINTER(LuOpts), vp]),
     "lu_gesv_mixed": (i32, [vp, i32, i64, i64, vp, i64, vp, i64, vp, i64, dbl, i32, ctypes.POINTER(LuOpts),
                             ctypes.POINTER(i32), ctypes.POINTER(dbl)]),

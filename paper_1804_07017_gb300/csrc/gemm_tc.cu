@@ -28,6 +28,7 @@
 #include <cudaTypedefs.h>
 
 #include "internal.h"
+#include "profile.h"
 #include "tc.h"
 
 namespace {
@@ -378,6 +379,8 @@ int launch_bn(cudaStream_t st, const CUtensorMap& ma, const CUtensorMap& mb, con
                                            L::kSmemBytes));
         attr = true;
     }
+    LuProfScope prof(st, LU_K_TC_UPDATE, 8.0 * p.m * p.ncols + (double)p.elem_bytes * p.k * (p.m + p.ncols),
+                     2.0 * p.m * p.ncols * p.k);
     tc_update_kernel<BN><<<grid, kThreads, L::kSmemBytes, st>>>(ma, mb, p);
     LU_CHECK_LAUNCH();
     return LU_SUCCESS;

@@ -112,3 +112,8 @@ int lu_check_opts(const lu_opts& o);
 template <typename T>
 int lu_factor_blocked(lu_context* c, int64_t n, T* A, int64_t lda, int32_t* ipiv, const lu_opts& o, int32_t* info,
                       const LuTuEngine* eng);
+
+// Operand precisions of the tensor-core trailing update.
+static inline bool lu_prec_is_tc(int prec) { return prec == LU_TU_BF16 || prec == LU_TU_FP16 || prec == LU_TU_BF16X3; }
+// pack.h format code of a tensor-core precision (LU_PACK_BF16 = 0, LU_PACK_FP16 = 1, LU_PACK_BF16X3 = 2)
+static inline int lu_prec_pack_fmt(int prec) { return prec == LU_TU_FP16 ? 1 : (prec == LU_TU_BF16X3 ? 2 : 0); }

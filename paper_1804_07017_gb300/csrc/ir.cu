@@ -7,6 +7,7 @@
 // Sums are formed in a fixed order (column chunks in increasing order, then
 // the chunk partials in increasing order), so results are deterministic.
 #include "internal.h"
+#include "profile.h"
 #include "ir.h"
 
 namespace {
@@ -139,30 +140,23 @@ __global__ void __launch_bounds__(1024) eta_kernel(int64_t n, int nrhs, const do
     }
 }
 
-__global__ void f64_to_f32_kernel(int64_t rows, int64_t cols, const double* __restrict__ in, int64_t ldi,
-                                  float* __restrict__ out, int64_t ldo) {
+template <typename Tin, typename Tout>
+__global__ void cast_kernel(int64_t rows, int64_t cols, const Tin* __restrict__ in, int64_t ldi, Tout* __restrict__ out,
+                            int64_t ldo) {
     const int64_t total = rows * cols;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
         const int64_t i = e % rows, j = e / rows;
-        out[i + j * ldo] = (float)in[i + j * ldi];
+        out[i + j * ldo] = (Tout)in[i + j * ldi];
     }
 }
 
-__global__ void add_f32_to_f64_kernel(int64_t rows, int64_t cols, const float* __restrict__ d, int64_t ldd,
-                                      double* __restrict__ x, int64_t ldx) {
-    const int64_t total = rows * cols;
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t i = e % rows, j = e / rows;
-        x[i + j * ldx] += (double)d[i + j * ldd];
-    }
-}
-
-__global__ void f32_to_f64_kernel(int64_t rows, int64_t cols, const float* __restrict__ d, int64_t ldd,
+template <typename Tin>
+__global__ void add_to_f64_kernel(int64_t rows, int64_t cols, const Tin* __restrict__ d, int64_t ldd,
                                   double* __restrict__ x, int64_t ldx) {
     const int64_t total = rows * cols;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
         const int64_t i = e % rows, j = e / rows;
-        x[i + j * ldx] = (double)d[i + j * ldd];
+        x[i + j * ldx] += (double)d[i + j * ldd];
     }
 }
 
@@ -179,8 +173,12 @@ int lu_launch_residual(cudaStream_t st, int64_t n, int64_t nrhs, const double* A
     for (int64_t c0 = 0; c0 < nrhs; c0 += kMaxRhs) {
         const int nr = (int)std::min<int64_t>(kMaxRhs, nrhs - c0);
         dim3 grid((unsigned)lu_cdiv(n, kRows), (unsigned)nch);
-        gemv_partial_kernel<false><<<grid, kRows, 0, st>>>(n, nr, A, lda, X + c0 * ldx, ldx, partial);
+        {
+            LuProfScope prof(st, LU_K_RESIDUAL, 8.0 * n * n + 8.0 * nch * nr * n, 2.0 * n * n * nr);
+            gemv_partial_kernel<false><<<grid, kRows, 0, st>>>(n, nr, A, lda, X + c0 * ldx, ldx, partial);
+        }
         LU_CHECK_LAUNCH();
+        LuProfScope prof(st, LU_K_RESIDUAL, 8.0 * nch * nr * n + 24.0 * n * nr, 0.0);
         residual_finish_kernel<<<grid_for(n * nr), 256, 0, st>>>(n, nr, nch, partial, B + c0 * ldb, ldb, R + c0 * ldr,
                                                                  ldr);
         LU_CHECK_LAUNCH();
@@ -192,8 +190,12 @@ int lu_launch_norm_inf(cudaStream_t st, int64_t n, const double* A, int64_t lda,
     if (n <= 0) return LU_SUCCESS;
     const int nch = (int)lu_ir_nchunks(n);
     dim3 grid((unsigned)lu_cdiv(n, kRows), (unsigned)nch);
-    gemv_partial_kernel<true><<<grid, kRows, 0, st>>>(n, 1, A, lda, nullptr, 0, partial);
+    {
+        LuProfScope prof(st, LU_K_RESIDUAL, 8.0 * n * n, 1.0 * n * n);
+        gemv_partial_kernel<true><<<grid, kRows, 0, st>>>(n, 1, A, lda, nullptr, 0, partial);
+    }
     LU_CHECK_LAUNCH();
+    LuProfScope prof(st, LU_K_RESIDUAL, 8.0 * nch * n, 0.0);
     norm_finish_kernel<<<1, 1024, 0, st>>>(n, nch, partial, out);
     LU_CHECK_LAUNCH();
     return LU_SUCCESS;
@@ -203,31 +205,33 @@ int lu_launch_eta(cudaStream_t st, int64_t n, int64_t nrhs, const double* R, int
                   const double* B, int64_t ldb, const double* anorm, double* eta_cols, double* out_eta,
                   unsigned int* done) {
     if (nrhs <= 0) return LU_SUCCESS;
+    LuProfScope prof(st, LU_K_RESIDUAL, 24.0 * n * nrhs, 0.0);
     eta_kernel<<<(unsigned)nrhs, 1024, 0, st>>>(n, (int)nrhs, R, ldr, X, ldx, B, ldb, anorm, eta_cols, out_eta, done);
     LU_CHECK_LAUNCH();
     return LU_SUCCESS;
 }
 
-int lu_launch_f64_to_f32(cudaStream_t st, int64_t rows, int64_t cols, const double* in, int64_t ldi, float* out,
-                         int64_t ldo) {
+template <typename Tin, typename Tout>
+int lu_launch_cast(cudaStream_t st, int64_t rows, int64_t cols, const Tin* in, int64_t ldi, Tout* out, int64_t ldo) {
     if (rows <= 0 || cols <= 0) return LU_SUCCESS;
-    f64_to_f32_kernel<<<grid_for(rows * cols), 256, 0, st>>>(rows, cols, in, ldi, out, ldo);
+    LuProfScope prof(st, LU_K_RESIDUAL, (double)(sizeof(Tin) + sizeof(Tout)) * rows * cols, 0.0);
+    cast_kernel<Tin, Tout><<<grid_for(rows * cols), 256, 0, st>>>(rows, cols, in, ldi, out, ldo);
     LU_CHECK_LAUNCH();
     return LU_SUCCESS;
 }
 
-int lu_launch_add_f32_to_f64(cudaStream_t st, int64_t rows, int64_t cols, const float* d, int64_t ldd, double* x,
-                             int64_t ldx) {
-    if (rows <= 0 || cols <= 0) return LU_SUCCESS;
-    add_f32_to_f64_kernel<<<grid_for(rows * cols), 256, 0, st>>>(rows, cols, d, ldd, x, ldx);
-    LU_CHECK_LAUNCH();
-    return LU_SUCCESS;
-}
-
-int lu_launch_f32_to_f64(cudaStream_t st, int64_t rows, int64_t cols, const float* d, int64_t ldd, double* x,
+template <typename Tin>
+int lu_launch_add_to_f64(cudaStream_t st, int64_t rows, int64_t cols, const Tin* d, int64_t ldd, double* x,
                          int64_t ldx) {
     if (rows <= 0 || cols <= 0) return LU_SUCCESS;
-    f32_to_f64_kernel<<<grid_for(rows * cols), 256, 0, st>>>(rows, cols, d, ldd, x, ldx);
+    LuProfScope prof(st, LU_K_RESIDUAL, (double)(sizeof(Tin) + 16) * rows * cols, 0.0);
+    add_to_f64_kernel<Tin><<<grid_for(rows * cols), 256, 0, st>>>(rows, cols, d, ldd, x, ldx);
     LU_CHECK_LAUNCH();
     return LU_SUCCESS;
 }
+
+template int lu_launch_cast<double, float>(cudaStream_t, int64_t, int64_t, const double*, int64_t, float*, int64_t);
+template int lu_launch_cast<float, double>(cudaStream_t, int64_t, int64_t, const float*, int64_t, double*, int64_t);
+template int lu_launch_cast<double, double>(cudaStream_t, int64_t, int64_t, const double*, int64_t, double*, int64_t);
+template int lu_launch_add_to_f64<float>(cudaStream_t, int64_t, int64_t, const float*, int64_t, double*, int64_t);
+template int lu_launch_add_to_f64<double>(cudaStream_t, int64_t, int64_t, const double*, int64_t, double*, int64_t);

@@ -13,9 +13,10 @@ int lu_launch_norm_inf(cudaStream_t st, int64_t n, const double* A, int64_t lda,
 int lu_launch_eta(cudaStream_t st, int64_t n, int64_t nrhs, const double* R, int64_t ldr, const double* X, int64_t ldx,
                   const double* B, int64_t ldb, const double* anorm, double* eta_cols, double* out_eta,
                   unsigned int* done);
-int lu_launch_f64_to_f32(cudaStream_t st, int64_t rows, int64_t cols, const double* in, int64_t ldi, float* out,
-                         int64_t ldo);
-int lu_launch_add_f32_to_f64(cudaStream_t st, int64_t rows, int64_t cols, const float* d, int64_t ldd, double* x,
-                             int64_t ldx);
-int lu_launch_f32_to_f64(cudaStream_t st, int64_t rows, int64_t cols, const float* d, int64_t ldd, double* x,
+// out = (Tout) in, elementwise over rows x cols
+template <typename Tin, typename Tout>
+int lu_launch_cast(cudaStream_t st, int64_t rows, int64_t cols, const Tin* in, int64_t ldi, Tout* out, int64_t ldo);
+// x += (double) d, elementwise over rows x cols
+template <typename Tin>
+int lu_launch_add_to_f64(cudaStream_t st, int64_t rows, int64_t cols, const Tin* d, int64_t ldd, double* x,
                          int64_t ldx);

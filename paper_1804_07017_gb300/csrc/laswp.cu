@@ -12,6 +12,7 @@
 // [1+2K .. 1+4K) = source rows.  Entries 0..K-1 are the panel block rows in
 // order (identity moves included), entries K.. are the rows below the block.
 #include "internal.h"
+#include "profile.h"
 
 namespace {
 
@@ -109,6 +110,7 @@ int lu_launch_laswp_plan(cudaStream_t st, const int32_t* ipiv, int64_t k1, int64
                                            sizeof(int32_t) * 4 * LU_MAX_NB));
         attr = true;
     }
+    LuProfScope prof(st, LU_K_LASWP, 20.0 * K, 0.0);
     laswp_plan_kernel<<<1, kPlanThreads, smem, st>>>(ipiv, k1, K, plan);
     LU_CHECK_LAUNCH();
     return LU_SUCCESS;
@@ -129,6 +131,7 @@ int lu_launch_laswp_apply(cudaStream_t st, T* A, int64_t lda, int64_t c1, int64_
     }
     int64_t blocks = lu_cdiv(n1 + n2, warps);
     blocks = std::min<int64_t>(blocks, (int64_t)std::max(num_sms, 1) * 8);
+    LuProfScope prof(st, LU_K_LASWP, 2.0 * 2.0 * K * (double)(n1 + n2) * sizeof(T), 0.0);
     laswp_apply_kernel<T><<<(unsigned)blocks, kApplyThreads, smem, st>>>(A, lda, c1, n1, c2, n2, plan, (int)K);
     LU_CHECK_LAUNCH();
     return LU_SUCCESS;

@@ -1,6 +1,8 @@
 // Mixed-precision path: FP32 panels and factors, trailing update on the tensor
 // cores with bf16/fp16 operands and FP32 accumulation.
 #include <math.h>
+#include <stdio.h>
+#include <stdlib.h>
 
 #include "internal.h"
 #include "ir.h"
@@ -29,7 +31,7 @@ static size_t al256(size_t x) { return (x + 255) / 256 * 256; }
 extern "C" int lu_gemm_update_tc_ex(lu_handle h, lu_prec prec, int64_t m, int64_t n, int64_t k, const float* A,
                                     int64_t lda, const float* B, int64_t ldb, float* C, int64_t ldc, int32_t* info) {
     if (!h) return LU_ERR_HANDLE;
-    if (prec != LU_TU_BF16 && prec != LU_TU_FP16) return -2;
+    if (!lu_prec_is_tc(prec)) return -2;
     if (m < 0) return -3;
     if (n < 0) return -4;
     if (k < 0 || k % 64 != 0) return -5;
@@ -45,16 +47,17 @@ extern "C" int lu_gemm_update_tc_ex(lu_handle h, lu_prec prec, int64_t m, int64_
     cudaStream_t st = h->user;
     LU_CHECK_CUDA(cudaMemsetAsync(&h->sync[2], 0, sizeof(LuSync), st));
     if (m > 0 && n > 0 && k > 0) {
-        const size_t abytes = al256((size_t)m * k * 2), bbytes = al256((size_t)n * k * 2);
+        const int fmt = lu_prec_pack_fmt(prec);
+        const int sg = lu_pack_segments(fmt);
+        const size_t abytes = al256((size_t)m * k * 2 * sg), bbytes = al256((size_t)n * k * 2 * sg);
         LU_TRY(lu_mx_reserve(h, abytes + bbytes));
         char* a = (char*)h->mx;
         char* b = a + abytes;
-        const int fmt = prec == LU_TU_BF16 ? LU_PACK_BF16 : LU_PACK_FP16;
         LU_TRY(lu_launch_pack_rows(st, fmt, A, lda, m, (int)k, a));
         LU_TRY(lu_launch_pack_cols(st, fmt, B, ldb, n, (int)k, b));
-        LU_TRY(lu_launch_tc_update(st, LU_TC_KIND_F16, prec == LU_TU_BF16 ? LU_TC_FMT_BF16 : LU_TC_FMT_F16, C, ldc, 0, m,
-                                   0, n, k, a, m, b, n, 1.0f, (int*)&h->sync[2].ticket, &h->sync[2].error, h->num_sms,
-                                   256));
+        LU_TRY(lu_launch_tc_update(st, LU_TC_KIND_F16, prec == LU_TU_FP16 ? LU_TC_FMT_F16 : LU_TC_FMT_BF16, C, ldc, 0,
+                                   m, 0, n, k * sg, a, m, b, n, 1.0f, (int*)&h->sync[2].ticket, &h->sync[2].error,
+                                   h->num_sms, 256));
     }
     return lu_launch_finish_info(st, &h->sync[2], info);
 }
@@ -78,10 +81,11 @@ struct TcEngine final : LuTuEngine {
     mutable int64_t last_k = -1;
     mutable int64_t last_k0 = 0, last_kb = 0, last_cb = 0, last_ce = 0;
 
-    int fmt_pack() const { return prec == LU_TU_FP16 ? LU_PACK_FP16 : LU_PACK_BF16; }
+    int fmt_pack() const { return lu_prec_pack_fmt(prec); }
     int fmt_mma() const { return prec == LU_TU_FP16 ? LU_TC_FMT_F16 : LU_TC_FMT_BF16; }
+    int segs() const { return lu_pack_segments(fmt_pack()); }
 
-    bool uses_tc(int64_t kb) const override { return (prec == LU_TU_BF16 || prec == LU_TU_FP16) && kb % 64 == 0; }
+    bool uses_tc(int64_t kb) const override { return lu_prec_is_tc(prec) && kb % 64 == 0; }
 
     int pack_panel(cudaStream_t st, const float* A, int64_t lda, int64_t k, int64_t k0, int64_t kb) const override {
         return lu_launch_pack_rows(st, fmt_pack(), A + (k0 + kb) + k0 * lda, lda, n - (k0 + kb), (int)kb, alo[k & 1]);
@@ -90,14 +94,14 @@ struct TcEngine final : LuTuEngine {
     int launch(cudaStream_t st, float* A, int64_t lda, int64_t k, int64_t k0, int64_t kb, int64_t cb, int64_t ce,
                int which, int grid) const {
         const int64_t m = n - (k0 + kb);
-        const char* bbuf = blo[k & 1] + (size_t)(cb - (k0 + kb)) * kb * 2;
-        return lu_launch_tc_update(st, LU_TC_KIND_F16, fmt_mma(), A, lda, k0 + kb, m, cb, ce - cb, kb, alo[k & 1], m,
-                                   bbuf, ce - cb, 1.0f, counter[which], error, grid, 256);
+        const char* bbuf = blo[k & 1] + (size_t)(cb - (k0 + kb)) * kb * 2 * segs();
+        return lu_launch_tc_update(st, LU_TC_KIND_F16, fmt_mma(), A, lda, k0 + kb, m, cb, ce - cb, kb * segs(),
+                                   alo[k & 1], m, bbuf, ce - cb, 1.0f, counter[which], error, grid, 256);
     }
 
     int update(cudaStream_t st, float* A, int64_t lda, int64_t k, int64_t k0, int64_t kb, int64_t cb, int64_t ce,
                int which) const override {
-        char* bbuf = blo[k & 1] + (size_t)(cb - (k0 + kb)) * kb * 2;
+        char* bbuf = blo[k & 1] + (size_t)(cb - (k0 + kb)) * kb * 2 * segs();
         LU_TRY(lu_launch_pack_cols(st, fmt_pack(), A + k0 + cb * lda, lda, ce - cb, (int)kb, bbuf));
         LU_CHECK_CUDA(cudaMemsetAsync(counter[which], 0, sizeof(int), st));
         if (which == 1) {
@@ -121,7 +125,10 @@ struct TcEngine final : LuTuEngine {
     }
 };
 
-size_t tc_engine_bytes(int64_t n, int nb) { return 4 * al256((size_t)n * nb * 2); }
+size_t tc_engine_bytes(int prec, int64_t n, int nb) {
+    if (!lu_prec_is_tc(prec)) return 256;
+    return 4 * al256((size_t)n * nb * 2 * lu_pack_segments(lu_prec_pack_fmt(prec)));
+}
 
 int setup_engine(TcEngine& e, lu_context* c, int prec, int64_t n, int nb, char* base, float* A, int64_t lda,
                  const lu_opts& o) {
@@ -129,7 +136,7 @@ int setup_engine(TcEngine& e, lu_context* c, int prec, int64_t n, int nb, char* 
     e.prec = prec;
     e.n = n;
     e.nb = nb;
-    const size_t one = al256((size_t)n * nb * 2);
+    const size_t one = al256((size_t)n * nb * 2 * lu_pack_segments(lu_prec_pack_fmt(prec)));
     e.alo[0] = base;
     e.alo[1] = base + one;
     e.blo[0] = base + 2 * one;
@@ -155,7 +162,7 @@ int setup_engine(TcEngine& e, lu_context* c, int prec, int64_t n, int nb, char* 
 // mixed-precision solver).  A32 is overwritten by the FP32 factors.
 static int factor_mixed(lu_context* c, int prec, int64_t n, float* A32, int64_t lda, int32_t* ipiv, const lu_opts& o,
                         int32_t* info, char* engine_mem) {
-    if (prec == LU_TU_F32) return lu_factor_blocked<float>(c, n, A32, lda, ipiv, o, info, nullptr);
+    if (!lu_prec_is_tc(prec)) return lu_factor_blocked<float>(c, n, A32, lda, ipiv, o, info, nullptr);
     TcEngine e;
     LU_TRY(setup_engine(e, c, prec, n, o.nb, engine_mem, A32, lda, o));
     return lu_factor_blocked<float>(c, n, A32, lda, ipiv, o, info, &e);
@@ -164,7 +171,7 @@ static int factor_mixed(lu_context* c, int prec, int64_t n, float* A32, int64_t 
 extern "C" int lu_factor_mixed_ex(lu_handle h, lu_prec prec, int64_t n, float* A, int64_t lda, int32_t* ipiv,
                                   const lu_opts* opts, int32_t* info) {
     if (!h) return LU_ERR_HANDLE;
-    if (prec != LU_TU_BF16 && prec != LU_TU_FP16 && prec != LU_TU_F32) return -2;
+    if (!lu_prec_is_tc(prec) && prec != LU_TU_F32) return -2;
     if (n < 0) return -3;
     if (n > 0 && !A) return -4;
     if (lda < std::max<int64_t>(1, n)) return -5;
@@ -177,18 +184,132 @@ extern "C" int lu_factor_mixed_ex(lu_handle h, lu_prec prec, int64_t n, float* A
     if (n > INT32_MAX / 2) return LU_ERR_UNSUPPORTED;
     std::lock_guard<std::mutex> lk(h->mu);
     LU_TRY(lu_ctx_reserve(h, n, o.nb));
-    LU_TRY(lu_mx_reserve(h, tc_engine_bytes(std::max<int64_t>(n, 1), o.nb)));
+    LU_TRY(lu_mx_reserve(h, tc_engine_bytes(prec, std::max<int64_t>(n, 1), o.nb)));
     return factor_mixed(h, prec, n, A, lda, ipiv, o, info, (char*)h->mx);
 }
 
 // ---------------------------------------------------------------------------
-// Mixed-precision solver with FP64 iterative refinement.
+// Solver with FP64 iterative refinement.  T is the working precision of the
+// factors and of the correction solves: float for the mixed-precision
+// variants, double for the plain FP64 reference path (LU_FULL_F64).
 // ---------------------------------------------------------------------------
+template <typename T>
+static int gesv_refined(lu_context* h, int prec, int64_t n, int64_t nrhs, const double* A, int64_t lda,
+                        const double* B, int64_t ldb, double* X, int64_t ldx, double tol, int max_iter,
+                        const lu_opts& o, int* iters, double* bwd_err) {
+    cudaStream_t st = h->user;
+    LU_TRY(lu_ctx_reserve(h, n, o.nb));
+    if (!h->host_eta) LU_CHECK_CUDA(cudaMallocHost(&h->host_eta, 4 * sizeof(double)));
+    const int64_t ldw = (n + 31) / 32 * 32;
+    const int64_t nch = lu_ir_nchunks(n);
+    const int64_t rhs_chunk = std::min<int64_t>(nrhs, 16);
+    size_t off = 0;
+    auto take = [&](size_t bytes) { size_t o0 = off; off += al256(bytes); return o0; };
+    const size_t o_aw = take(sizeof(T) * (size_t)ldw * n);
+    const size_t o_eng = take(sizeof(T) == 4 ? tc_engine_bytes(prec, n, o.nb) : 256);
+    const size_t o_ipiv = take(sizeof(int32_t) * n);
+    const size_t o_perm = take(sizeof(int32_t) * n);
+    const size_t o_r = take(sizeof(double) * n * nrhs);
+    const size_t o_xb = take(sizeof(double) * n * nrhs);
+    const size_t o_rw = take(sizeof(T) * n * nrhs);
+    const size_t o_dw = take(sizeof(T) * n * nrhs);
+    const size_t o_part = take(sizeof(double) * nch * rhs_chunk * n);
+    const size_t o_sc = take(sizeof(double) * (8 + nrhs) + sizeof(int32_t) * 8);
+    LU_TRY(lu_mx_reserve(h, off));
+    char* base = (char*)h->mx;
+    T* Aw = (T*)(base + o_aw);
+    int32_t* ipiv = (int32_t*)(base + o_ipiv);
+    int32_t* perm = (int32_t*)(base + o_perm);
+    double* R = (double*)(base + o_r);
+    double* Xb = (double*)(base + o_xb);
+    T* rw = (T*)(base + o_rw);
+    T* dw = (T*)(base + o_dw);
+    double* part = (double*)(base + o_part);
+    double* sc = (double*)(base + o_sc);
+    double* anorm = sc;
+    double* eta = sc + 1;
+    double* eta_cols = sc + 8;
+    int32_t* dinfo = (int32_t*)(sc + 8 + nrhs);
+    unsigned int* done = (unsigned int*)(dinfo + 2);
+    LU_CHECK_CUDA(cudaMemsetAsync(sc, 0, sizeof(double) * (8 + nrhs) + sizeof(int32_t) * 8, st));
+
+    // 1. working copy in T and its factorization
+    LU_TRY((lu_launch_cast<double, T>(st, n, n, A, lda, Aw, ldw)));
+    if (sizeof(T) == 4)
+        LU_TRY(factor_mixed(h, prec, n, (float*)Aw, ldw, ipiv, o, dinfo, base + o_eng));
+    else
+        LU_TRY(lu_factor_blocked<double>(h, n, (double*)Aw, ldw, ipiv, o, dinfo, nullptr));
+    LU_TRY(lu_launch_perm_from_ipiv<T>(st, n, ipiv, perm));
+    LU_TRY(lu_launch_norm_inf(st, n, A, lda, part, anorm));
+    // 2. x0 = U^-1 L^-1 P b in T
+    LU_TRY((lu_launch_cast<double, T>(st, n, nrhs, B, ldb, rw, n)));
+    LU_TRY(lu_launch_permute_rows<T>(st, n, nrhs, perm, rw, n, dw, n));
+    LU_TRY(lu_launch_trsv_blocked<T>(h, st, true, n, nrhs, Aw, ldw, dw, n));
+    LU_TRY(lu_launch_trsv_blocked<T>(h, st, false, n, nrhs, Aw, ldw, dw, n));
+    LU_TRY((lu_launch_cast<T, double>(st, n, nrhs, dw, n, X, ldx)));
+    // 3. refinement: r = b - A x (FP64), eta test on the host, d = (LU)^-1 P r (T), x += d (FP64)
+    double best = INFINITY;
+    int best_it = -1, it = 0;
+    int status = LU_SUCCESS;
+    const char* tr = getenv("LU_GB300_TRACE");
+    const bool trace = tr && tr[0] == '1';
+    for (;; ++it) {
+        for (int64_t c0 = 0; c0 < nrhs; c0 += 16) {
+            const int64_t nr = std::min<int64_t>(16, nrhs - c0);
+            LU_TRY(lu_launch_residual(st, n, nr, A, lda, X + c0 * ldx, ldx, B + c0 * ldb, ldb, R + c0 * n, n, part));
+        }
+        LU_TRY(lu_launch_eta(st, n, nrhs, R, n, X, ldx, B, ldb, anorm, eta_cols, eta, done));
+        LU_CHECK_CUDA(cudaMemcpyAsync(h->host_eta, eta, sizeof(double), cudaMemcpyDeviceToHost, st));
+        LU_CHECK_CUDA(cudaMemcpyAsync(h->host_eta + 1, dinfo, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+        LU_CHECK_CUDA(cudaStreamSynchronize(st));
+        const int32_t finfo = *reinterpret_cast<int32_t*>(h->host_eta + 1);
+        if (finfo != 0) {
+            status = finfo;  // exactly singular U (i > 0) or a device-side timeout (< 0)
+            break;
+        }
+        const double e = h->host_eta[0];
+        if (trace) fprintf(stderr, "[lu_gesv_mixed] iteration %d eta %.3e\n", it, e);
+        if (e < best) {
+            best = e;
+            best_it = it;
+            if (e > tol && it < max_iter)
+                LU_CHECK_CUDA(cudaMemcpy2DAsync(Xb, n * sizeof(double), X, ldx * sizeof(double), n * sizeof(double),
+                                                nrhs, cudaMemcpyDeviceToDevice, st));
+        }
+        if (e <= tol) break;
+        if (it >= max_iter || !(e == e)) {
+            status = LU_WARN_NOT_CONVERGED;
+            break;
+        }
+        LU_TRY((lu_launch_cast<double, T>(st, n, nrhs, R, n, rw, n)));
+        LU_TRY(lu_launch_permute_rows<T>(st, n, nrhs, perm, rw, n, dw, n));
+        LU_TRY(lu_launch_trsv_blocked<T>(h, st, true, n, nrhs, Aw, ldw, dw, n));
+        LU_TRY(lu_launch_trsv_blocked<T>(h, st, false, n, nrhs, Aw, ldw, dw, n));
+        LU_TRY(lu_launch_add_to_f64<T>(st, n, nrhs, dw, n, X, ldx));
+    }
+    if (status == LU_WARN_NOT_CONVERGED && best_it >= 0 && best_it != it) {
+        LU_CHECK_CUDA(cudaMemcpy2DAsync(X, ldx * sizeof(double), Xb, n * sizeof(double), n * sizeof(double), nrhs,
+                                        cudaMemcpyDeviceToDevice, st));
+        LU_CHECK_CUDA(cudaStreamSynchronize(st));
+    }
+    if (iters) *iters = (status == LU_WARN_NOT_CONVERGED) ? best_it : it;
+    if (bwd_err) *bwd_err = best;
+    if (status == LU_SUCCESS) {
+        int err = 0;
+        LU_CHECK_CUDA(cudaMemcpy(&err, &h->sync[1].error, sizeof(int), cudaMemcpyDeviceToHost));
+        if (err != 0) {
+            cudaMemset(&h->sync[1].error, 0, sizeof(int));
+            return err;
+        }
+    }
+    return status;
+}
+
 extern "C" int lu_gesv_mixed(lu_handle h, lu_prec prec, int64_t n, int64_t nrhs, const double* A, int64_t lda,
                              const double* B, int64_t ldb, double* X, int64_t ldx, double tol, int max_iter,
                              const lu_opts* opts, int* iters, double* bwd_err) {
     if (!h) return LU_ERR_HANDLE;
-    if (prec != LU_TU_BF16 && prec != LU_TU_FP16 && prec != LU_TU_F32) return -2;
+    if (!lu_prec_is_tc(prec) && prec != LU_TU_F32 && prec != LU_FULL_F64) return -2;
     if (n < 0) return -3;
     if (nrhs < 0) return -4;
     if (n > 0 && !A) return -5;
@@ -208,105 +329,7 @@ extern "C" int lu_gesv_mixed(lu_handle h, lu_prec prec, int64_t n, int64_t nrhs,
     if (n == 0 || nrhs == 0) return LU_SUCCESS;
     if (n > INT32_MAX / 2) return LU_ERR_UNSUPPORTED;
     std::lock_guard<std::mutex> lk(h->mu);
-    cudaStream_t st = h->user;
-    LU_TRY(lu_ctx_reserve(h, n, o.nb));
-    if (!h->host_eta) LU_CHECK_CUDA(cudaMallocHost(&h->host_eta, 4 * sizeof(double)));
-    // workspace layout
-    const int64_t ld32 = (n + 31) / 32 * 32;
-    const int64_t nch = lu_ir_nchunks(n);
-    const int64_t rhs_chunk = std::min<int64_t>(nrhs, 16);
-    size_t off = 0;
-    auto take = [&](size_t bytes) { size_t o0 = off; off += al256(bytes); return o0; };
-    const size_t o_a32 = take(sizeof(float) * (size_t)ld32 * n);
-    const size_t o_eng = take(tc_engine_bytes(n, o.nb));
-    const size_t o_ipiv = take(sizeof(int32_t) * n);
-    const size_t o_perm = take(sizeof(int32_t) * n);
-    const size_t o_r = take(sizeof(double) * n * nrhs);
-    const size_t o_xb = take(sizeof(double) * n * nrhs);
-    const size_t o_r32 = take(sizeof(float) * n * nrhs);
-    const size_t o_d32 = take(sizeof(float) * n * nrhs);
-    const size_t o_part = take(sizeof(double) * nch * rhs_chunk * n);
-    const size_t o_sc = take(sizeof(double) * (8 + nrhs) + sizeof(int32_t) * 8);
-    LU_TRY(lu_mx_reserve(h, off));
-    char* base = (char*)h->mx;
-    float* A32 = (float*)(base + o_a32);
-    int32_t* ipiv = (int32_t*)(base + o_ipiv);
-    int32_t* perm = (int32_t*)(base + o_perm);
-    double* R = (double*)(base + o_r);
-    double* Xb = (double*)(base + o_xb);
-    float* r32 = (float*)(base + o_r32);
-    float* d32 = (float*)(base + o_d32);
-    double* part = (double*)(base + o_part);
-    double* sc = (double*)(base + o_sc);
-    double* anorm = sc;
-    double* eta = sc + 1;
-    double* eta_cols = sc + 8;
-    int32_t* dinfo = (int32_t*)(sc + 8 + nrhs);
-    unsigned int* done = (unsigned int*)(dinfo + 2);
-    LU_CHECK_CUDA(cudaMemsetAsync(sc, 0, sizeof(double) * (8 + nrhs) + sizeof(int32_t) * 8, st));
-
-    // 1. FP32 working copy, factorization with the tensor-core trailing update
-    LU_TRY(lu_launch_f64_to_f32(st, n, n, A, lda, A32, ld32));
-    LU_TRY(factor_mixed(h, prec, n, A32, ld32, ipiv, o, dinfo, base + o_eng));
-    LU_TRY(lu_launch_perm_from_ipiv<float>(st, n, ipiv, perm));
-    LU_TRY(lu_launch_norm_inf(st, n, A, lda, part, anorm));
-    // 2. x0 = U^-1 L^-1 P b in FP32
-    LU_TRY(lu_launch_f64_to_f32(st, n, nrhs, B, ldb, r32, n));
-    LU_TRY(lu_launch_permute_rows<float>(st, n, nrhs, perm, r32, n, d32, n));
-    LU_TRY(lu_launch_trsv_blocked<float>(h, st, true, n, nrhs, A32, ld32, d32, n));
-    LU_TRY(lu_launch_trsv_blocked<float>(h, st, false, n, nrhs, A32, ld32, d32, n));
-    LU_TRY(lu_launch_f32_to_f64(st, n, nrhs, d32, n, X, ldx));
-    // 3. refinement: r = b - A x (FP64), eta test on the host, d = (LU)^-1 P r (FP32), x += d (FP64)
-    double best = INFINITY;
-    int best_it = -1, it = 0;
-    int status = LU_SUCCESS;
-    for (;; ++it) {
-        for (int64_t c0 = 0; c0 < nrhs; c0 += 16) {
-            const int64_t nr = std::min<int64_t>(16, nrhs - c0);
-            LU_TRY(lu_launch_residual(st, n, nr, A, lda, X + c0 * ldx, ldx, B + c0 * ldb, ldb, R + c0 * n, n, part));
-        }
-        LU_TRY(lu_launch_eta(st, n, nrhs, R, n, X, ldx, B, ldb, anorm, eta_cols, eta, done));
-        LU_CHECK_CUDA(cudaMemcpyAsync(h->host_eta, eta, sizeof(double), cudaMemcpyDeviceToHost, st));
-        LU_CHECK_CUDA(cudaMemcpyAsync(h->host_eta + 1, dinfo, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
-        LU_CHECK_CUDA(cudaStreamSynchronize(st));
-        const int32_t finfo = *reinterpret_cast<int32_t*>(h->host_eta + 1);
-        if (finfo != 0) {
-            status = finfo;  // exactly singular U (i > 0) or a device-side timeout (< 0)
-            break;
-        }
-        const double e = h->host_eta[0];
-        if (e < best) {
-            best = e;
-            best_it = it;
-            if (e > tol && it < max_iter)
-                LU_CHECK_CUDA(cudaMemcpy2DAsync(Xb, n * sizeof(double), X, ldx * sizeof(double), n * sizeof(double),
-                                                nrhs, cudaMemcpyDeviceToDevice, st));
-        }
-        if (e <= tol) break;
-        if (it >= max_iter || !(e == e)) {
-            status = LU_WARN_NOT_CONVERGED;
-            break;
-        }
-        LU_TRY(lu_launch_f64_to_f32(st, n, nrhs, R, n, r32, n));
-        LU_TRY(lu_launch_permute_rows<float>(st, n, nrhs, perm, r32, n, d32, n));
-        LU_TRY(lu_launch_trsv_blocked<float>(h, st, true, n, nrhs, A32, ld32, d32, n));
-        LU_TRY(lu_launch_trsv_blocked<float>(h, st, false, n, nrhs, A32, ld32, d32, n));
-        LU_TRY(lu_launch_add_f32_to_f64(st, n, nrhs, d32, n, X, ldx));
-    }
-    if (status == LU_WARN_NOT_CONVERGED && best_it >= 0 && best_it != it) {
-        LU_CHECK_CUDA(cudaMemcpy2DAsync(X, ldx * sizeof(double), Xb, n * sizeof(double), n * sizeof(double), nrhs,
-                                        cudaMemcpyDeviceToDevice, st));
-        LU_CHECK_CUDA(cudaStreamSynchronize(st));
-    }
-    if (iters) *iters = (status == LU_WARN_NOT_CONVERGED) ? best_it : it;
-    if (bwd_err) *bwd_err = best;
-    if (status == LU_SUCCESS) {
-        int err = 0;
-        LU_CHECK_CUDA(cudaMemcpy(&err, &h->sync[1].error, sizeof(int), cudaMemcpyDeviceToHost));
-        if (err != 0) {
-            cudaMemset(&h->sync[1].error, 0, sizeof(int));
-            return err;
-        }
-    }
-    return status;
+    if (prec == LU_FULL_F64)
+        return gesv_refined<double>(h, prec, n, nrhs, A, lda, B, ldb, X, ldx, tol, max_iter, o, iters, bwd_err);
+    return gesv_refined<float>(h, prec, n, nrhs, A, lda, B, ldb, X, ldx, tol, max_iter, o, iters, bwd_err);
 }

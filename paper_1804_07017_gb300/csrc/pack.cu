@@ -3,18 +3,41 @@
 // values that one output row (of L21) or one output column (of U12) contracts
 // over become contiguous -- the layout the TMA boxes and the tcgen05 shared
 // memory descriptors of gemm_tc.cu expect.
+//
+// Split-bf16 mode (LU_PACK_BF16X3): each FP32 value x is written as
+// hi = bf16(x) and lo = bf16(x - hi), and the K dimension is tripled so that
+// one plain bf16 GEMM computes hi_A hi_B + hi_A lo_B + lo_A hi_B:
+//     A row:    [ hi(0..k) | hi(0..k) | lo(0..k) ]
+//     B column: [ hi(0..k) | lo(0..k) | hi(0..k) ]
+// The dropped lo_A lo_B term is ~2^-16 relative, so the product carries about
+// 16 significant bits instead of 8, at three times the tensor work but the same
+// FP32 traffic of the updated matrix.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
 #include "internal.h"
+#include "profile.h"
 #include "pack.h"
 
 namespace {
 
 template <int FMT>
 __device__ __forceinline__ uint16_t to16(float x) {
-    if (FMT == LU_PACK_BF16) return __bfloat16_as_ushort(__float2bfloat16_rn(x));
-    return __half_as_ushort(__float2half_rn(x));
+    if (FMT == LU_PACK_FP16) return __half_as_ushort(__float2half_rn(x));
+    return __bfloat16_as_ushort(__float2bfloat16_rn(x));
+}
+
+__device__ __forceinline__ uint16_t bf16_lo(float x) {
+    const float hi = __bfloat162float(__float2bfloat16_rn(x));
+    return __bfloat16_as_ushort(__float2bfloat16_rn(x - hi));
+}
+
+// value of segment `seg` (0..2) of the split operand for A (rows) or B (columns)
+template <int FMT, bool IS_A>
+__device__ __forceinline__ uint16_t seg_val(float x, int seg) {
+    if (FMT != LU_PACK_BF16X3) return to16<FMT>(x);
+    const bool lo = IS_A ? (seg == 2) : (seg == 1);
+    return lo ? bf16_lo(x) : to16<LU_PACK_BF16>(x);
 }
 
 // Apack[r][kk] = round(A[r + kk*lda]) for r in [0, rows), kk in [0, k); out row stride = k.
@@ -22,17 +45,22 @@ __device__ __forceinline__ uint16_t to16(float x) {
 // column-major reads and the row-major writes are coalesced.
 template <int FMT>
 __global__ void __launch_bounds__(256) pack_rows_kernel(const float* __restrict__ A, int64_t lda, int64_t rows, int k,
-                                                        uint16_t* __restrict__ out) {
+                                                        uint16_t* __restrict__ out_base) {
     __shared__ uint16_t tile[32][64 + 2];
     const int64_t r0 = (int64_t)blockIdx.x * 32;
     const int k0 = blockIdx.y * 64;
+    const int seg = blockIdx.z;  // segment of the split operand (0 for single-term formats)
+    const int nseg = gridDim.z;
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
     for (int kk = ty; kk < 64; kk += 8) {
         const int64_t r = r0 + tx;
         const int kc = k0 + kk;
-        tile[tx][kk] = (r < rows && kc < k) ? to16<FMT>(A[r + (int64_t)kc * lda]) : (uint16_t)0;
+        tile[tx][kk] = (r < rows && kc < k) ? seg_val<FMT, true>(A[r + (int64_t)kc * lda], seg) : (uint16_t)0;
     }
     __syncthreads();
+    // row stride of the packed buffer is nseg * k; this segment starts at seg * k
+    uint16_t* out = out_base + (int64_t)seg * k;
+    const int64_t stride = (int64_t)nseg * k;
     // write: each warp writes rows; lane covers 2 consecutive k values (32-bit stores)
     for (int rr = ty; rr < 32; rr += 8) {
         const int64_t r = r0 + rr;
@@ -40,24 +68,27 @@ __global__ void __launch_bounds__(256) pack_rows_kernel(const float* __restrict_
         if (r < rows && kc < k) {
             if (kc + 1 < k && (k & 1) == 0) {
                 const uint32_t v = (uint32_t)tile[rr][2 * tx] | ((uint32_t)tile[rr][2 * tx + 1] << 16);
-                *reinterpret_cast<uint32_t*>(out + r * k + kc) = v;
+                *reinterpret_cast<uint32_t*>(out + r * stride + kc) = v;
             } else {
-                out[r * k + kc] = tile[rr][2 * tx];
-                if (kc + 1 < k) out[r * k + kc + 1] = tile[rr][2 * tx + 1];
+                out[r * stride + kc] = tile[rr][2 * tx];
+                if (kc + 1 < k) out[r * stride + kc + 1] = tile[rr][2 * tx + 1];
             }
         }
     }
 }
 
-// Bpack[c][kk] = round(B[kk + c*ldb]) for c in [0, cols): B's columns are already K-contiguous.
+// Bpack[c][seg*k + kk] = segment seg of B[kk + c*ldb], c in [0, cols): B's columns are
+// already K-contiguous.
 template <int FMT>
 __global__ void __launch_bounds__(256) pack_cols_kernel(const float* __restrict__ B, int64_t ldb, int64_t cols, int k,
-                                                        uint16_t* __restrict__ out) {
-    const int64_t total = cols * (int64_t)k;
+                                                        int nseg, uint16_t* __restrict__ out) {
+    const int64_t kt = (int64_t)k * nseg;
+    const int64_t total = cols * kt;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t c = e / k;
-        const int kk = (int)(e - c * k);
-        out[e] = to16<FMT>(B[kk + c * ldb]);
+        const int64_t c = e / kt;
+        const int q = (int)(e - c * kt);
+        const int seg = q / k, kk = q - seg * k;
+        out[e] = seg_val<FMT, false>(B[kk + c * ldb], seg);
     }
 }
 
@@ -66,23 +97,31 @@ __global__ void __launch_bounds__(256) pack_cols_kernel(const float* __restrict_
 int lu_launch_pack_rows(cudaStream_t st, int fmt, const float* A, int64_t lda, int64_t rows, int k, void* out) {
     if (rows <= 0 || k <= 0) return LU_SUCCESS;
     if (lu_cdiv(k, 64) > 65535) return LU_ERR_UNSUPPORTED;
-    dim3 grid((unsigned)lu_cdiv(rows, 32), (unsigned)lu_cdiv(k, 64));
+    const int nseg = lu_pack_segments(fmt);
+    dim3 grid((unsigned)lu_cdiv(rows, 32), (unsigned)lu_cdiv(k, 64), (unsigned)nseg);
+    LuProfScope prof(st, LU_K_PACK, (4.0 + 2.0 * nseg) * rows * k, 0.0);
     if (fmt == LU_PACK_BF16)
         pack_rows_kernel<LU_PACK_BF16><<<grid, 256, 0, st>>>(A, lda, rows, k, (uint16_t*)out);
-    else
+    else if (fmt == LU_PACK_FP16)
         pack_rows_kernel<LU_PACK_FP16><<<grid, 256, 0, st>>>(A, lda, rows, k, (uint16_t*)out);
+    else
+        pack_rows_kernel<LU_PACK_BF16X3><<<grid, 256, 0, st>>>(A, lda, rows, k, (uint16_t*)out);
     LU_CHECK_LAUNCH();
     return LU_SUCCESS;
 }
 
 int lu_launch_pack_cols(cudaStream_t st, int fmt, const float* B, int64_t ldb, int64_t cols, int k, void* out) {
     if (cols <= 0 || k <= 0) return LU_SUCCESS;
-    const int64_t total = cols * (int64_t)k;
+    const int nseg = lu_pack_segments(fmt);
+    const int64_t total = cols * (int64_t)k * nseg;
     const unsigned blocks = (unsigned)std::min<int64_t>(lu_cdiv(total, 256), 8192);
+    LuProfScope prof(st, LU_K_PACK, (4.0 / nseg + 2.0) * total, 0.0);
     if (fmt == LU_PACK_BF16)
-        pack_cols_kernel<LU_PACK_BF16><<<blocks, 256, 0, st>>>(B, ldb, cols, k, (uint16_t*)out);
+        pack_cols_kernel<LU_PACK_BF16><<<blocks, 256, 0, st>>>(B, ldb, cols, k, 1, (uint16_t*)out);
+    else if (fmt == LU_PACK_FP16)
+        pack_cols_kernel<LU_PACK_FP16><<<blocks, 256, 0, st>>>(B, ldb, cols, k, 1, (uint16_t*)out);
     else
-        pack_cols_kernel<LU_PACK_FP16><<<blocks, 256, 0, st>>>(B, ldb, cols, k, (uint16_t*)out);
+        pack_cols_kernel<LU_PACK_BF16X3><<<blocks, 256, 0, st>>>(B, ldb, cols, k, 3, (uint16_t*)out);
     LU_CHECK_LAUNCH();
     return LU_SUCCESS;
 }

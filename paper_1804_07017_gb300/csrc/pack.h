@@ -5,8 +5,11 @@
 
 #define LU_PACK_BF16 0
 #define LU_PACK_FP16 1
+#define LU_PACK_BF16X3 2  // split bf16: K tripled, [hi|hi|lo] for A rows, [hi|lo|hi] for B columns
 
-// out[r][kk] = round(A[r + kk*lda]), r < rows, kk < k (row stride k).
+static inline int lu_pack_segments(int fmt) { return fmt == LU_PACK_BF16X3 ? 3 : 1; }
+
+// out[r][s*k + kk] = segment s of round(A[r + kk*lda]), r < rows, kk < k (row stride segments*k).
 int lu_launch_pack_rows(cudaStream_t st, int fmt, const float* A, int64_t lda, int64_t rows, int k, void* out);
-// out[c][kk] = round(B[kk + c*ldb]), c < cols, kk < k (row stride k).
+// out[c][s*k + kk] = segment s of round(B[kk + c*ldb]), c < cols, kk < k (row stride segments*k).
 int lu_launch_pack_cols(cudaStream_t st, int fmt, const float* B, int64_t ldb, int64_t cols, int k, void* out);

@@ -20,6 +20,7 @@
 #include <climits>
 
 #include "internal.h"
+#include "profile.h"
 
 namespace {
 
@@ -200,6 +201,7 @@ int lu_launch_pf_leaf(lu_context* c, cudaStream_t st, T* A, int64_t lda, int64_t
     int* slot_idx = reinterpret_cast<int*>(reinterpret_cast<char*>(c->pf_slots) +
                                            sizeof(double) * (2 * LU_PF_MAX_CTAS * (LU_PF_MAX_LEAF + 1) +
                                                              2 * LU_PF_MAX_LEAF));
+    LuProfScope prof(st, LU_K_PANEL, 2.0 * m * w * sizeof(T), (double)m * w * w);
     pf_leaf_kernel<T, kPfThreads><<<G, kPfThreads, smem, st>>>(A, lda, (int)m, w, (int)R, ipiv,
                                                                 (int)ipiv_add, &c->sync[0], slots,
                                                                 slot_idx);

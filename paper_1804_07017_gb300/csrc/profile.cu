@@ -1,0 +1,109 @@
+// Built-in launch profiler: when enabled, every kernel launch of the library is
+// bracketed by a pair of CUDA events recorded on the launching stream, tagged
+// with its kernel class and its algorithmic bytes and flops.  lu_profile_read
+// synchronises, turns the event pairs into durations and aggregates them per
+// class.  Off by default; costs two event records per launch when on.
+#include <mutex>
+#include <vector>
+
+#include "internal.h"
+#include "profile.h"
+
+namespace {
+
+struct Rec {
+    int cls;
+    cudaEvent_t a, b;
+    double bytes, flops;
+};
+
+std::mutex g_mu;
+bool g_on = false;
+std::vector<Rec> g_recs;
+std::vector<cudaEvent_t> g_pool;
+struct Agg {
+    long long launches = 0;
+    double ms = 0, bytes = 0, flops = 0;
+};
+Agg g_agg[LU_K_COUNT];
+
+cudaEvent_t take_event() {
+    if (!g_pool.empty()) {
+        cudaEvent_t e = g_pool.back();
+        g_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return e;
+}
+
+void drain_locked() {
+    if (g_recs.empty()) return;
+    cudaDeviceSynchronize();
+    for (Rec& r : g_recs) {
+        float ms = 0.f;
+        if (r.a && r.b && cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
+            Agg& g = g_agg[r.cls];
+            g.launches += 1;
+            g.ms += ms;
+            g.bytes += r.bytes;
+            g.flops += r.flops;
+        } else {
+            cudaGetLastError();
+        }
+        if (r.a) g_pool.push_back(r.a);
+        if (r.b) g_pool.push_back(r.b);
+    }
+    g_recs.clear();
+}
+
+}  // namespace
+
+LuProfScope::LuProfScope(cudaStream_t st, int cls, double bytes, double flops) : st_(st) {
+    if (!g_on) return;
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (!g_on) return;
+    a_ = take_event();
+    b_ = take_event();
+    cls_ = cls;
+    bytes_ = bytes;
+    flops_ = flops;
+    if (a_) cudaEventRecord(a_, st_);
+    active_ = true;
+}
+
+LuProfScope::~LuProfScope() {
+    if (!active_) return;
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (b_) cudaEventRecord(b_, st_);
+    g_recs.push_back(Rec{cls_, a_, b_, bytes_, flops_});
+}
+
+extern "C" int lu_profile_enable(int on) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_on = on != 0;
+    return LU_SUCCESS;
+}
+
+extern "C" int lu_profile_reset(void) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    drain_locked();
+    for (auto& g : g_agg) g = Agg();
+    return LU_SUCCESS;
+}
+
+extern "C" int lu_profile_read(int kclass, int64_t* launches, double* ms, double* bytes, double* flops) {
+    if (kclass < 0 || kclass >= LU_K_COUNT) return -1;
+    std::lock_guard<std::mutex> lk(g_mu);
+    drain_locked();
+    const Agg& g = g_agg[kclass];
+    if (launches) *launches = g.launches;
+    if (ms) *ms = g.ms;
+    if (bytes) *bytes = g.bytes;
+    if (flops) *flops = g.flops;
+    return LU_SUCCESS;
+}

@@ -13,6 +13,7 @@
 //                    publishes.  Tickets make the wait graph acyclic whatever
 //                    the CTA scheduling order.
 #include "internal.h"
+#include "profile.h"
 
 namespace {
 
@@ -198,6 +199,7 @@ template <typename T>
 int lu_launch_perm_from_ipiv(cudaStream_t st, int64_t n, const int32_t* ipiv, int32_t* perm) {
     if (n <= 0) return LU_SUCCESS;
     const size_t smem = sizeof(int32_t) * (size_t)n;
+    LuProfScope prof(st, LU_K_SOLVE, 8.0 * n, 0.0);
     if (smem <= 200 * 1024) {
         static bool attr = false;
         if (!attr) {
@@ -219,6 +221,7 @@ int lu_launch_permute_rows(cudaStream_t st, int64_t n, int64_t nrhs, const int32
     if (n <= 0 || nrhs <= 0) return LU_SUCCESS;
     const int64_t total = n * nrhs;
     const unsigned blocks = (unsigned)std::min<int64_t>(lu_cdiv(total, 256), 4096);
+    LuProfScope prof(st, LU_K_SOLVE, 2.0 * n * nrhs * sizeof(T) + 4.0 * n, 0.0);
     permute_rows_kernel<T><<<blocks, 256, 0, st>>>(n, nrhs, perm, B, ldb, X, ldx);
     LU_CHECK_LAUNCH();
     return LU_SUCCESS;
@@ -234,6 +237,7 @@ int lu_launch_trsv_blocked(lu_context* c, cudaStream_t st, bool lower_unit, int6
         // reset the ticket and the done counter (the error word is kept: sticky)
         LU_CHECK_CUDA(cudaMemsetAsync(&c->sync[1].arrive, 0, sizeof(unsigned) * 2, st));
         LU_CHECK_CUDA(cudaMemsetAsync(&c->sync[1].ticket, 0, sizeof(unsigned), st));
+        LuProfScope prof(st, LU_K_SOLVE, sizeof(T) * (0.5 * n * n + 2.0 * n * nr), (double)n * n * nr);
         if (lower_unit)
             trsv_blocked_kernel<T, true><<<nblk, kTrsvThreads, 0, st>>>(n, nr, LU, lda, X + c0 * ldx, ldx, &c->sync[1]);
         else
@@ -244,6 +248,7 @@ int lu_launch_trsv_blocked(lu_context* c, cudaStream_t st, bool lower_unit, int6
 }
 
 int lu_launch_finish_info(cudaStream_t st, const LuSync* s, int32_t* info) {
+    LuProfScope prof(st, LU_K_OTHER, 16.0, 0.0);
     finish_info_kernel<<<1, 1, 0, st>>>(s, info);
     LU_CHECK_LAUNCH();
     return LU_SUCCESS;

@@ -7,6 +7,7 @@
 // where its tile starts, so splitting an update into column ranges (the
 // static look-ahead's TU^L / TU^R split, Sec. 4) gives bit-identical results.
 #include "internal.h"
+#include "profile.h"
 
 namespace {
 
@@ -159,6 +160,7 @@ int lu_launch_trsm_lunit(cudaStream_t st, int64_t m, int64_t n, const T* L, int6
                                            cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
         attr[ti] = true;
     }
+    LuProfScope prof(st, LU_K_TRSM, sizeof(T) * (2.0 * m * n + 0.5 * m * m), (double)m * m * n);
     if (smem16 <= 64 * 1024) {
         trsm_lunit_kernel<T, 16><<<(unsigned)lu_cdiv(n, 16), kTrsmThreads, smem16, st>>>((int)m, n, L, ldl, B, ldb);
     } else {
@@ -174,6 +176,7 @@ int lu_launch_gemm_update(cudaStream_t st, int64_t m, int64_t n, int64_t k, cons
     if (m <= 0 || n <= 0 || k <= 0) return LU_SUCCESS;
     if (lu_cdiv(n, BN) > 65535) return LU_ERR_UNSUPPORTED;
     dim3 grid((unsigned)lu_cdiv(m, BM), (unsigned)lu_cdiv(n, BN));
+    LuProfScope prof(st, LU_K_GEMM, sizeof(T) * (2.0 * m * n + (double)m * k + (double)k * n), 2.0 * m * n * k);
     gemm_update_kernel<T><<<grid, kGemmThreads, 0, st>>>(m, n, (int)k, A, lda, B, ldb, C, ldc);
     LU_CHECK_LAUNCH();
     return LU_SUCCESS;

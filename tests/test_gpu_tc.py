@@ -31,11 +31,19 @@ def dev32(a):
     return t
 
 
-@pytest.mark.parametrize("prec_name", ["bf16", "fp16"])
+def split_product(A, B):
+    """hi_A hi_B + hi_A lo_B + lo_A hi_B with hi = bf16(x), lo = bf16(x - hi): the
+    split-bf16 product, formed exactly in FP64 from the oracle's rounding."""
+    Ah, Bh = oracle.round_bf16(A), oracle.round_bf16(B)
+    Al, Bl = oracle.round_bf16(A - Ah), oracle.round_bf16(B - Bh)
+    return Ah @ Bh + Ah @ Bl + Al @ Bh, np.abs(Ah) @ np.abs(Bh) + np.abs(Ah) @ np.abs(Bl) + np.abs(Al) @ np.abs(Bh)
+
+
+@pytest.mark.parametrize("prec_name", ["bf16", "fp16", "bf16x3"])
 @pytest.mark.parametrize("m,n,k", [(128, 256, 64), (256, 256, 64), (1000, 700, 256), (300, 5000, 64),
                                    (4097, 129, 512), (1, 1, 64), (129, 257, 128)])
 def test_tc_update(lu, prec_name, m, n, k):
-    prec = lu.LU_TU_BF16 if prec_name == "bf16" else lu.LU_TU_FP16
+    prec = {"bf16": lu.LU_TU_BF16, "fp16": lu.LU_TU_FP16, "bf16x3": lu.LU_TU_BF16X3}[prec_name]
     rnd = oracle.round_bf16 if prec_name == "bf16" else oracle.round_fp16
     g = synth.rng(31, m + n + k)
     C0, A0, B0 = (g.standard_normal(size=s).astype(np.float32).astype(np.float64)
@@ -45,11 +53,21 @@ def test_tc_update(lu, prec_name, m, n, k):
     lu.lu_gemm_update_tc_ex(C, dev32(A0), dev32(B0), prec, info)
     torch.cuda.synchronize()
     assert int(info.item()) == 0
+    got = C.cpu().double().numpy()
+    u32 = np.finfo(np.float32).eps / 2
+    if prec_name == "bf16x3":
+        prod, aprod = split_product(A0, B0)
+        ref = C0 - prod
+        scale = aprod + np.abs(C0)
+        err = np.abs(got - ref)
+        assert np.all(err <= (3 * k + 2) * u32 * scale), (err / scale).max()
+        # and it is close to the exact FP64 product: only lo*lo (~2^-16 relative) is missing
+        exact = oracle.gemm_update(C0, A0, B0)
+        assert np.all(np.abs(got - exact) <= (2.0 ** -15 + (3 * k + 2) * u32) * (np.abs(A0) @ np.abs(B0) + np.abs(C0)))
+        return
     Ar, Br = rnd(A0), rnd(B0)
     ref = oracle.gemm_update(C0, Ar, Br)
-    got = C.cpu().double().numpy()
     scale = np.abs(Ar) @ np.abs(Br) + np.abs(C0)
-    u32 = np.finfo(np.float32).eps / 2
     err = np.abs(got - ref)
     assert np.all(err <= (k + 2) * u32 * scale), (err / scale).max()
     # the rounding actually happened: against the unrounded operands some entries
