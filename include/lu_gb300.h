@@ -61,8 +61,10 @@ typedef enum {
     LU_TU_F32 = 3,  /* FP32 on the CUDA cores (no tensor cores; a reference point) */
     LU_TU_BF16X3 = 4, /* split bf16: each FP32 operand as hi + lo bf16, three products
                          (hi*hi + hi*lo + lo*hi) accumulated in FP32, kind::f16 */
-    LU_FULL_F64 = 5 /* lu_gesv_mixed only: FP64 factors and FP64 correction solves
-                       (the plain FP64 path, refined the same way) */
+    LU_FULL_F64 = 5, /* lu_gesv_mixed only: FP64 factors and FP64 correction solves
+                        (the plain FP64 path, refined the same way) */
+    LU_TU_BF16X6 = 6 /* split bf16 in three parts, the six products of weight >= 2^-16
+                        (the full FP32 significand), kind::f16 */
 } lu_prec;
 
 /* Options of a blocked factorization (Sec. 3-4 of the paper). */
@@ -201,7 +203,7 @@ int lu_gemm_update_ex(lu_handle handle, lu_dtype dtype, int64_t m, int64_t n, in
 /*
  * lu_gemm_update_tc_ex -- RL3, C := C - A B on the tensor cores: A (m x k) and
  * B (k x n) are FP32 and are rounded to the operand type of `prec` (round to
- * nearest even; LU_TU_BF16, LU_TU_FP16 or LU_TU_BF16X3), the products accumulate in FP32
+ * nearest even; LU_TU_BF16, LU_TU_FP16, LU_TU_BF16X3 or LU_TU_BF16X6), the products accumulate in FP32
  * and C (FP32, m x n) is updated in place.  k must be a multiple of 64.
  *   info  device int32[1]; 0, or LU_ERR_TIMEOUT if a bounded wait expired.
  */
@@ -220,7 +222,7 @@ int lu_gemm_update_tc_ex(lu_handle handle, lu_prec prec, int64_t m, int64_t n, i
  * tensor cores with operands rounded to `prec` (LU_TU_BF16 / LU_TU_FP16) and
  * FP32 accumulation; LU_TU_F32 keeps it on the CUDA cores.  When nb is not a
  * multiple of 64 the update falls back to FP32 on the CUDA cores.  LU_TU_BF16X3
- * runs the same kernel on split operands with a three times longer K.
+ * and LU_TU_BF16X6 run the same kernel on split operands with a 3x / 6x longer K.
  * Asynchronous; info as in lu_factor_ex.
  */
 int lu_factor_mixed_ex(lu_handle handle, lu_prec prec, int64_t n, float *A, int64_t lda, int32_t *ipiv,

@@ -27,6 +27,7 @@ LU_TU_FP8 = 2
 LU_TU_F32 = 3
 LU_TU_BF16X3 = 4
 LU_FULL_F64 = 5
+LU_TU_BF16X6 = 6
 
 
 class LuError(RuntimeError):

@@ -13,7 +13,7 @@
 #define LU_PF_MAX_CTAS 128    // CTAs of one panel-factorization leaf launch
 #define LU_PF_MAX_LEAF 64     // widest leaf (columns held in shared memory)
 #define LU_MAX_NB 1024        // widest panel accepted
-#define LU_PF_SMEM_BUDGET (64 * 1024)
+#define LU_PF_SMEM_BUDGET (78 * 1024)
 
 struct lu_context {
     int device = 0;
@@ -54,6 +54,8 @@ int lu_ctx_reserve(lu_context* c, int64_t n, int nb);
 int lu_mx_reserve(lu_context* c, size_t bytes);
 
 // --- kernels (launchers return LU_SUCCESS or LU_ERR_CUDA) --------------------
+bool lu_pf_leaf_shape(int64_t m, int w, int esize, int max_ctas, int64_t* R_out, int64_t* G_out, size_t* smem_out);
+
 template <typename T>
 int lu_launch_pf_leaf(lu_context* c, cudaStream_t st, T* A, int64_t lda, int64_t m, int w,
                       int32_t* ipiv, int64_t ipiv_add, int max_ctas);
@@ -114,6 +116,10 @@ int lu_factor_blocked(lu_context* c, int64_t n, T* A, int64_t lda, int32_t* ipiv
                       const LuTuEngine* eng);
 
 // Operand precisions of the tensor-core trailing update.
-static inline bool lu_prec_is_tc(int prec) { return prec == LU_TU_BF16 || prec == LU_TU_FP16 || prec == LU_TU_BF16X3; }
-// pack.h format code of a tensor-core precision (LU_PACK_BF16 = 0, LU_PACK_FP16 = 1, LU_PACK_BF16X3 = 2)
-static inline int lu_prec_pack_fmt(int prec) { return prec == LU_TU_FP16 ? 1 : (prec == LU_TU_BF16X3 ? 2 : 0); }
+static inline bool lu_prec_is_tc(int prec) {
+    return prec == LU_TU_BF16 || prec == LU_TU_FP16 || prec == LU_TU_BF16X3 || prec == LU_TU_BF16X6;
+}
+// pack.h format code of a tensor-core precision (LU_PACK_BF16 0, FP16 1, BF16X3 2, BF16X6 3)
+static inline int lu_prec_pack_fmt(int prec) {
+    return prec == LU_TU_FP16 ? 1 : (prec == LU_TU_BF16X3 ? 2 : (prec == LU_TU_BF16X6 ? 3 : 0));
+}

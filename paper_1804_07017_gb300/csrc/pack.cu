@@ -11,7 +11,9 @@
 //     B column: [ hi(0..k) | lo(0..k) | hi(0..k) ]
 // The dropped lo_A lo_B term is ~2^-16 relative, so the product carries about
 // 16 significant bits instead of 8, at three times the tensor work but the same
-// FP32 traffic of the updated matrix.
+// FP32 traffic of the updated matrix.  LU_PACK_BF16X6 splits into three parts
+// and keeps the six products whose weight is at least 2^-16, which carries the
+// full 24-bit FP32 significand.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -27,17 +29,31 @@ __device__ __forceinline__ uint16_t to16(float x) {
     return __bfloat16_as_ushort(__float2bfloat16_rn(x));
 }
 
-__device__ __forceinline__ uint16_t bf16_lo(float x) {
-    const float hi = __bfloat162float(__float2bfloat16_rn(x));
-    return __bfloat16_as_ushort(__float2bfloat16_rn(x - hi));
+// part 0 = bf16(x), part 1 = bf16(x - part0), part 2 = bf16(x - part0 - part1); the
+// differences are exact in FP32 because each part removes the leading bits.
+__device__ __forceinline__ uint16_t bf16_part(float x, int part) {
+    const float p0 = __bfloat162float(__float2bfloat16_rn(x));
+    if (part == 0) return __bfloat16_as_ushort(__float2bfloat16_rn(x));
+    const float r1 = x - p0;
+    const float p1 = __bfloat162float(__float2bfloat16_rn(r1));
+    if (part == 1) return __bfloat16_as_ushort(__float2bfloat16_rn(r1));
+    return __bfloat16_as_ushort(__float2bfloat16_rn(r1 - p1));
 }
 
-// value of segment `seg` (0..2) of the split operand for A (rows) or B (columns)
+// Which part each K segment holds, for A rows and for B columns:
+//   x3: A [0,0,1]  B [0,1,0]              -> p0p0 + p0p1 + p1p0
+//   x6: A [0,0,1,0,1,2]  B [0,1,0,2,1,0]  -> p0p0 + p0p1 + p1p0 + p0p2 + p1p1 + p2p0
+__device__ __forceinline__ int seg_part(int fmt, bool is_a, int seg) {
+    if (fmt == LU_PACK_BF16X3) return is_a ? (seg == 2 ? 1 : 0) : (seg == 1 ? 1 : 0);
+    const int a[6] = {0, 0, 1, 0, 1, 2}, b[6] = {0, 1, 0, 2, 1, 0};
+    return is_a ? a[seg] : b[seg];
+}
+
+// value of segment `seg` of the split operand for A (rows) or B (columns)
 template <int FMT, bool IS_A>
 __device__ __forceinline__ uint16_t seg_val(float x, int seg) {
-    if (FMT != LU_PACK_BF16X3) return to16<FMT>(x);
-    const bool lo = IS_A ? (seg == 2) : (seg == 1);
-    return lo ? bf16_lo(x) : to16<LU_PACK_BF16>(x);
+    if (FMT != LU_PACK_BF16X3 && FMT != LU_PACK_BF16X6) return to16<FMT>(x);
+    return bf16_part(x, seg_part(FMT, IS_A, seg));
 }
 
 // Apack[r][kk] = round(A[r + kk*lda]) for r in [0, rows), kk in [0, k); out row stride = k.
@@ -104,8 +120,10 @@ int lu_launch_pack_rows(cudaStream_t st, int fmt, const float* A, int64_t lda, i
         pack_rows_kernel<LU_PACK_BF16><<<grid, 256, 0, st>>>(A, lda, rows, k, (uint16_t*)out);
     else if (fmt == LU_PACK_FP16)
         pack_rows_kernel<LU_PACK_FP16><<<grid, 256, 0, st>>>(A, lda, rows, k, (uint16_t*)out);
-    else
+    else if (fmt == LU_PACK_BF16X3)
         pack_rows_kernel<LU_PACK_BF16X3><<<grid, 256, 0, st>>>(A, lda, rows, k, (uint16_t*)out);
+    else
+        pack_rows_kernel<LU_PACK_BF16X6><<<grid, 256, 0, st>>>(A, lda, rows, k, (uint16_t*)out);
     LU_CHECK_LAUNCH();
     return LU_SUCCESS;
 }
@@ -120,8 +138,10 @@ int lu_launch_pack_cols(cudaStream_t st, int fmt, const float* B, int64_t ldb, i
         pack_cols_kernel<LU_PACK_BF16><<<blocks, 256, 0, st>>>(B, ldb, cols, k, 1, (uint16_t*)out);
     else if (fmt == LU_PACK_FP16)
         pack_cols_kernel<LU_PACK_FP16><<<blocks, 256, 0, st>>>(B, ldb, cols, k, 1, (uint16_t*)out);
-    else
+    else if (fmt == LU_PACK_BF16X3)
         pack_cols_kernel<LU_PACK_BF16X3><<<blocks, 256, 0, st>>>(B, ldb, cols, k, 3, (uint16_t*)out);
+    else
+        pack_cols_kernel<LU_PACK_BF16X6><<<blocks, 256, 0, st>>>(B, ldb, cols, k, 6, (uint16_t*)out);
     LU_CHECK_LAUNCH();
     return LU_SUCCESS;
 }

@@ -6,8 +6,9 @@
 #define LU_PACK_BF16 0
 #define LU_PACK_FP16 1
 #define LU_PACK_BF16X3 2  // split bf16: K tripled, [hi|hi|lo] for A rows, [hi|lo|hi] for B columns
+#define LU_PACK_BF16X6 3  // three-part split bf16, six products, K six times longer
 
-static inline int lu_pack_segments(int fmt) { return fmt == LU_PACK_BF16X3 ? 3 : 1; }
+static inline int lu_pack_segments(int fmt) { return fmt == LU_PACK_BF16X3 ? 3 : (fmt == LU_PACK_BF16X6 ? 6 : 1); }
 
 // out[r][s*k + kk] = segment s of round(A[r + kk*lda]), r < rows, kk < k (row stride segments*k).
 int lu_launch_pack_rows(cudaStream_t st, int fmt, const float* A, int64_t lda, int64_t rows, int k, void* out);

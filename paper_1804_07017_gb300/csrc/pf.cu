@@ -52,6 +52,9 @@ __global__ void __launch_bounds__(NT) pf_leaf_kernel(T* __restrict__ A, int64_t 
     T* sA = reinterpret_cast<T*>(smem_raw);  // [w][R], column-major block of this CTA's rows
     T* prow = sA + (size_t)w * R;             // pivot row (w values)
     T* jrowv = prow + w;                      // previous contents of row jj (w values)
+    T* s_rows = jrowv + w;                    // [G][w] every CTA's candidate row
+    T* s_cv = s_rows + (size_t)gridDim.x * w; // [G] candidate values
+    int* s_ci = reinterpret_cast<int*>(s_cv + gridDim.x);  // [G] candidate rows
     __shared__ T red_v[NT / 32];
     __shared__ int red_i[NT / 32];
     __shared__ T sh_bv;
@@ -104,15 +107,26 @@ __global__ void __launch_bounds__(NT) pf_leaf_kernel(T* __restrict__ A, int64_t 
             cand_row[(buf * LU_PF_MAX_CTAS + g) * LU_PF_MAX_LEAF + tid] = sA[tid * R + (my_bi - row0)];
         if (jj >= row0 && jj < row0 + nrows && tid < w)
             jrow[buf * LU_PF_MAX_LEAF + tid] = sA[tid * R + (jj - row0)];
-        __threadfence();
+        if (tid < w) __threadfence();
         if (!lu_grid_barrier(sync, (unsigned)(jj + 1) * (unsigned)G, &sh_flag)) break;
+        // ---- one round trip: every candidate's value, index and row, plus row jj ----
+        for (int q = tid; q < G; q += NT) {
+            s_cv[q] = __ldcg(&cand_val[buf * LU_PF_MAX_CTAS + q]);
+            s_ci[q] = __ldcg(&cand_idx[buf * LU_PF_MAX_CTAS + q]);
+        }
+        for (int e = tid; e < G * w; e += NT) {
+            const int q = e / w, c = e - q * w;
+            s_rows[e] = __ldcg(&cand_row[(buf * LU_PF_MAX_CTAS + q) * LU_PF_MAX_LEAF + c]);
+        }
+        if (tid < w) jrowv[tid] = __ldcg(&jrow[buf * LU_PF_MAX_LEAF + tid]);
+        __syncthreads();
         // ---- global pivot: first maximum over all CTAs' candidates ----
         if (warp == 0) {
             T v = T(-1);
             int i = INT_MAX, q_best = -1;
             for (int q = lane; q < G; q += 32) {
-                T cv = __ldcg(&cand_val[buf * LU_PF_MAX_CTAS + q]);
-                int ci = __ldcg(&cand_idx[buf * LU_PF_MAX_CTAS + q]);
+                const T cv = s_cv[q];
+                const int ci = s_ci[q];
                 if (ci != INT_MAX && (cv > v || (cv == v && ci < i))) {
                     v = cv;
                     i = ci;
@@ -137,11 +151,7 @@ __global__ void __launch_bounds__(NT) pf_leaf_kernel(T* __restrict__ A, int64_t 
         }
         __syncthreads();
         const int p = sh_p, gw = sh_gw;
-        if (tid < w) {
-            T jv = __ldcg(&jrow[buf * LU_PF_MAX_LEAF + tid]);
-            jrowv[tid] = jv;
-            prow[tid] = (gw >= 0) ? __ldcg(&cand_row[(buf * LU_PF_MAX_CTAS + gw) * LU_PF_MAX_LEAF + tid]) : jv;
-        }
+        if (tid < w) prow[tid] = (gw >= 0) ? s_rows[gw * w + tid] : jrowv[tid];
         if (g == 0 && tid == 0) ipiv[jj] = p + 1 + ipiv_add;
         __syncthreads();
         // ---- interchange rows jj and p (within this leaf's columns) ----
@@ -177,18 +187,37 @@ constexpr int kPfThreads = 256;
 
 }  // namespace
 
+// Leaf shape: as few CTAs as the shared-memory budget allows (fewer CTAs make the
+// per-column grid barrier cheaper), rows per CTA a multiple of 32.
+bool lu_pf_leaf_shape(int64_t m, int w, int esize, int max_ctas, int64_t* R_out, int64_t* G_out, size_t* smem_out) {
+    auto smem_of = [&](int64_t R, int64_t G) {
+        return (size_t)(R * w + 2 * w + G * w + G) * esize + (size_t)G * sizeof(int);
+    };
+    int64_t R = ((int64_t)LU_PF_SMEM_BUDGET / esize - 2 * w) / w;  // rows that fit with no exchange area
+    R = R / 32 * 32;
+    int64_t Rmin = std::max<int64_t>(32, lu_cdiv(lu_cdiv(m, max_ctas), 32) * 32);
+    if (R > lu_cdiv(m, 32) * 32) R = lu_cdiv(m, 32) * 32;
+    while (R >= Rmin) {
+        const int64_t G = lu_cdiv(m, R);
+        if (G <= max_ctas && smem_of(R, G) <= (size_t)LU_PF_SMEM_BUDGET) {
+            *R_out = R;
+            *G_out = G;
+            *smem_out = smem_of(R, G);
+            return true;
+        }
+        R -= 32;
+    }
+    return false;
+}
+
 template <typename T>
 int lu_launch_pf_leaf(lu_context* c, cudaStream_t st, T* A, int64_t lda, int64_t m, int w,
                       int32_t* ipiv, int64_t ipiv_add, int max_ctas) {
     if (w < 1 || w > LU_PF_MAX_LEAF || m < w) return LU_ERR_UNSUPPORTED;
     if (max_ctas <= 0 || max_ctas > LU_PF_MAX_CTAS) max_ctas = LU_PF_MAX_CTAS;
-    // Rows per CTA: a multiple of 32, enough CTAs to hold all rows within the budget.
-    int64_t R = lu_cdiv(m, max_ctas);
-    R = std::max<int64_t>(32, lu_cdiv(R, 32) * 32);
-    size_t smem = (size_t)(R * w + 2 * w) * sizeof(T);
-    if (smem > (size_t)LU_PF_SMEM_BUDGET) return LU_ERR_UNSUPPORTED;
-    int G = (int)lu_cdiv(m, R);
-    if (G > LU_PF_MAX_CTAS) return LU_ERR_UNSUPPORTED;
+    int64_t R = 0, G = 0;
+    size_t smem = 0;
+    if (!lu_pf_leaf_shape(m, w, (int)sizeof(T), max_ctas, &R, &G, &smem)) return LU_ERR_UNSUPPORTED;
     static bool attr_set[2] = {false, false};
     const int ti = sizeof(T) == 8 ? 0 : 1;
     if (!attr_set[ti]) {
@@ -202,7 +231,7 @@ int lu_launch_pf_leaf(lu_context* c, cudaStream_t st, T* A, int64_t lda, int64_t
                                            sizeof(double) * (2 * LU_PF_MAX_CTAS * (LU_PF_MAX_LEAF + 1) +
                                                              2 * LU_PF_MAX_LEAF));
     LuProfScope prof(st, LU_K_PANEL, 2.0 * m * w * sizeof(T), (double)m * w * w);
-    pf_leaf_kernel<T, kPfThreads><<<G, kPfThreads, smem, st>>>(A, lda, (int)m, w, (int)R, ipiv,
+    pf_leaf_kernel<T, kPfThreads><<<(unsigned)G, kPfThreads, smem, st>>>(A, lda, (int)m, w, (int)R, ipiv,
                                                                 (int)ipiv_add, &c->sync[0], slots,
                                                                 slot_idx);
     LU_CHECK_LAUNCH();
@@ -214,11 +243,13 @@ int lu_panel_recursive(lu_context* c, cudaStream_t st, T* A, int64_t lda, int64_
                        int64_t width, int32_t* ipiv, const lu_opts& o) {
     if (width <= 0) return LU_SUCCESS;
     int leaf = o.leaf > 0 ? std::min(o.leaf, LU_PF_MAX_LEAF) : 32;
-    // Narrow the leaf until one CTA's share of the rows fits in shared memory.
+    // Narrow the leaf until the rows fit in the leaf grid's shared memory.
     const int64_t rows = M - j0;
+    const int max_ctas = o.pf_ctas > 0 ? o.pf_ctas : LU_PF_MAX_CTAS;
     while (leaf > 1) {
-        int64_t R = std::max<int64_t>(32, lu_cdiv(lu_cdiv(rows, LU_PF_MAX_CTAS), 32) * 32);
-        if ((size_t)(R * leaf + 2 * leaf) * sizeof(T) <= (size_t)LU_PF_SMEM_BUDGET) break;
+        int64_t R, G;
+        size_t smem;
+        if (lu_pf_leaf_shape(rows, leaf, (int)sizeof(T), max_ctas, &R, &G, &smem)) break;
         leaf >>= 1;
     }
     if (width <= leaf) {

@@ -5,7 +5,7 @@
 //   permute_rows:    X := P B (gather)
 //   trsv_blocked:    X := L^{-1} X (unit lower) or X := U^{-1} X, for up to 16
 //                    right-hand sides per launch.  Rows are cut into 128-row
-//                    blocks; a CTA takes the next block in dependency order
+//                    (FP32) / 64-row (FP64) blocks; a CTA takes the next block in dependency order
 //                    from an atomic ticket, accumulates the contributions of
 //                    already-solved blocks as they are published (a monotone
 //                    "done" counter read with acquire loads and a bounded
@@ -65,26 +65,46 @@ __global__ void permute_rows_kernel(int64_t n, int64_t nrhs, const int32_t* __re
     }
 }
 
-constexpr int kBS = 128;       // rows per block
 constexpr int kNR = 16;        // right-hand sides per launch
 constexpr int kTrsvThreads = 256;
 
+template <typename T>
+struct TrsvCfg {
+    static constexpr int BS = sizeof(T) == 4 ? 128 : 64;  // rows per block
+    static constexpr int kSplit = kTrsvThreads / BS;      // threads sharing one row of a source block
+    static constexpr size_t smem = sizeof(T) * ((size_t)BS * (BS + 1) + 2 * (size_t)kNR * BS);
+};
+
+// One CTA per BS-row block, taken in dependency order from an atomic ticket.
+// The diagonal block is staged in shared memory before the CTA waits for its
+// predecessors, so the critical path per block is: observe the predecessor's
+// "done" count, add that block's contribution, run the register-resident
+// substitution of the diagonal block, publish.
 template <typename T, bool LOWER>
 __global__ void __launch_bounds__(kTrsvThreads)
     trsv_blocked_kernel(int64_t n, int nrhs, const T* __restrict__ LU, int64_t lda, T* __restrict__ X,
                         int64_t ldx, LuSync* __restrict__ sync) {
-    __shared__ T sX[kNR][kBS];
-    __shared__ T sPart[kNR][kBS];
+    using C = TrsvCfg<T>;
+    constexpr int BS = C::BS;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    T* sD = reinterpret_cast<T*>(smraw);   // [BS][BS+1], sD[i*(BS+1) + j] = LU(r0+i, r0+j)
+    T* sX = sD + BS * (BS + 1);            // [kNR][BS]
+    T* sPart = sX + kNR * BS;              // [kNR][BS]
     __shared__ int s_chain, s_ready, s_flag;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int nblk = (int)((n + kBS - 1) / kBS);
+    const int nblk = (int)((n + BS - 1) / BS);
     if (tid == 0) s_chain = (int)atomicAdd(&sync->ticket, 1u);
     __syncthreads();
     const int chain = s_chain;  // position in dependency order
     const int blk = LOWER ? chain : nblk - 1 - chain;
-    const int64_t r0 = (int64_t)blk * kBS;
-    const int rows = (int)min((int64_t)kBS, n - r0);
-    const int r = tid % kBS, h = tid / kBS;  // two halves split the columns of each source block
+    const int64_t r0 = (int64_t)blk * BS;
+    const int rows = (int)min((int64_t)BS, n - r0);
+    // stage the diagonal block (independent of every other block)
+    for (int e = tid; e < BS * BS; e += kTrsvThreads) {
+        const int i = e % BS, j = e / BS;
+        sD[i * (BS + 1) + j] = (i < rows && j < rows) ? LU[(r0 + i) + (r0 + j) * lda] : T(0);
+    }
+    const int r = tid % BS, h = tid / BS;
     T acc[kNR];
 #pragma unroll
     for (int c = 0; c < kNR; ++c) acc[c] = T(0);
@@ -117,14 +137,21 @@ __global__ void __launch_bounds__(kTrsvThreads)
         const int ready = min(s_ready, chain);
         for (int q = processed; q < ready; ++q) {
             const int I = LOWER ? q : nblk - 1 - q;
-            const int64_t c0 = (int64_t)I * kBS;
-            const int cols = (int)min((int64_t)kBS, n - c0);
+            const int64_t c0 = (int64_t)I * BS;
+            const int cols = (int)min((int64_t)BS, n - c0);
             if (r < rows) {
-                for (int j = h; j < cols; j += 2) {
-                    const T l = LU[(r0 + r) + (c0 + j) * lda];
+                const T* lrow = LU + (r0 + r) + c0 * lda;
+                const T* xs = X + c0;
+                if (nrhs == 1) {
+#pragma unroll 4
+                    for (int j = h; j < cols; j += C::kSplit) acc[0] = fma(lrow[j * lda], __ldcg(xs + j), acc[0]);
+                } else {
+                    for (int j = h; j < cols; j += C::kSplit) {
+                        const T l = lrow[j * lda];
 #pragma unroll
-                    for (int c = 0; c < kNR; ++c)
-                        if (c < nrhs) acc[c] = fma(l, __ldcg(&X[(c0 + j) + c * ldx]), acc[c]);
+                        for (int c = 0; c < kNR; ++c)
+                            if (c < nrhs) acc[c] = fma(l, __ldcg(xs + j + c * ldx), acc[c]);
+                    }
                 }
             }
         }
@@ -132,56 +159,63 @@ __global__ void __launch_bounds__(kTrsvThreads)
         __syncthreads();
     }
     if (!ok) return;
-    // combine the two halves: sX = rhs - contributions
-    if (h == 1) {
+    // combine the kSplit partial sums: sX = rhs - contributions
+    for (int hh = 1; hh < C::kSplit; ++hh) {
+        if (h == hh) {
 #pragma unroll
-        for (int c = 0; c < kNR; ++c) sPart[c][r] = acc[c];
+            for (int c = 0; c < kNR; ++c) sPart[c * BS + r] = (hh == 1 ? T(0) : sPart[c * BS + r]) + acc[c];
+        }
+        __syncthreads();
     }
-    __syncthreads();
     if (h == 0) {
 #pragma unroll
         for (int c = 0; c < kNR; ++c)
-            sX[c][r] = (r < rows && c < nrhs) ? X[(r0 + r) + c * ldx] - (acc[c] + sPart[c][r]) : T(0);
+            sX[c * BS + r] = (r < rows && c < nrhs)
+                                 ? X[(r0 + r) + c * ldx] - (acc[c] + (C::kSplit > 1 ? sPart[c * BS + r] : T(0)))
+                                 : T(0);
     }
     __syncthreads();
-    // diagonal block, in 32-row sub-blocks
-    const int nsub = (rows + 31) / 32;
-    for (int sidx = 0; sidx < nsub; ++sidx) {
-        const int sb = LOWER ? sidx : nsub - 1 - sidx;
-        const int j0 = sb * 32;
-        const int jb = min(32, rows - j0);
-        // warp-level substitution inside the 32x32 sub-block, one rhs per warp
-        for (int c = warp; c < nrhs; c += kTrsvThreads / 32) {
-            T v = (lane < jb) ? sX[c][j0 + lane] : T(0);
-            if (LOWER) {
-                for (int j = 0; j < jb; ++j) {
-                    const T xj = __shfl_sync(0xffffffffu, v, j);
-                    if (lane > j && lane < jb) v = fma(-LU[(r0 + j0 + lane) + (r0 + j0 + j) * lda], xj, v);
-                }
-            } else {
-                for (int j = jb - 1; j >= 0; --j) {
-                    if (lane == j) v = v / LU[(r0 + j0 + j) + (r0 + j0 + j) * lda];
-                    const T xj = __shfl_sync(0xffffffffu, v, j);
-                    if (lane < j) v = fma(-LU[(r0 + j0 + lane) + (r0 + j0 + j) * lda], xj, v);
+    // register-resident substitution of the diagonal block: lane holds rows lane + 32 q
+    constexpr int RQ = BS / 32;
+    for (int c = warp; c < nrhs; c += kTrsvThreads / 32) {
+        T v[RQ];
+#pragma unroll
+        for (int q = 0; q < RQ; ++q) v[q] = sX[c * BS + lane + 32 * q];
+        if (LOWER) {
+#pragma unroll
+            for (int q0 = 0; q0 < RQ; ++q0) {
+                for (int jj = 0; jj < 32; ++jj) {
+                    const int j = q0 * 32 + jj;
+                    const T xj = __shfl_sync(0xffffffffu, v[q0], jj);
+#pragma unroll
+                    for (int q = q0; q < RQ; ++q) {
+                        const int i = lane + 32 * q;
+                        if (i > j) v[q] = fma(-sD[i * (BS + 1) + j], xj, v[q]);
+                    }
                 }
             }
-            if (lane < jb) sX[c][j0 + lane] = v;
+        } else {
+#pragma unroll
+            for (int q0 = RQ - 1; q0 >= 0; --q0) {
+                for (int jj = 31; jj >= 0; --jj) {
+                    const int j = q0 * 32 + jj;
+                    if (lane == jj && j < rows) v[q0] = v[q0] / sD[j * (BS + 1) + j];
+                    const T xj = __shfl_sync(0xffffffffu, v[q0], jj);
+#pragma unroll
+                    for (int q = 0; q <= q0; ++q) {
+                        const int i = lane + 32 * q;
+                        if (i < j) v[q] = fma(-sD[i * (BS + 1) + j], xj, v[q]);
+                    }
+                }
+            }
         }
-        __syncthreads();
-        // update the other rows of this block that come later in the sweep
-        const int lo = LOWER ? j0 + jb : 0;
-        const int hi = LOWER ? rows : j0;
-        for (int e = tid; e < (hi - lo) * nrhs; e += kTrsvThreads) {
-            const int rr = lo + e % (hi - lo), c = e / (hi - lo);
-            T a = T(0);
-            for (int j = 0; j < jb; ++j) a = fma(LU[(r0 + rr) + (r0 + j0 + j) * lda], sX[c][j0 + j], a);
-            sX[c][rr] -= a;
-        }
-        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < RQ; ++q) sX[c * BS + lane + 32 * q] = v[q];
     }
+    __syncthreads();
     for (int e = tid; e < rows * nrhs; e += kTrsvThreads) {
         const int rr = e % rows, c = e / rows;
-        X[(r0 + rr) + c * ldx] = sX[c][rr];
+        X[(r0 + rr) + c * ldx] = sX[c * BS + rr];
     }
     __threadfence();
     __syncthreads();
@@ -231,7 +265,17 @@ template <typename T>
 int lu_launch_trsv_blocked(lu_context* c, cudaStream_t st, bool lower_unit, int64_t n, int64_t nrhs,
                            const T* LU, int64_t lda, T* X, int64_t ldx) {
     if (n <= 0 || nrhs <= 0) return LU_SUCCESS;
-    const int nblk = (int)lu_cdiv(n, kBS);
+    using C = TrsvCfg<T>;
+    const int nblk = (int)lu_cdiv(n, C::BS);
+    static bool attr[2] = {false, false};
+    const int ti = sizeof(T) == 8 ? 0 : 1;
+    if (!attr[ti]) {
+        LU_CHECK_CUDA(cudaFuncSetAttribute(trsv_blocked_kernel<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)C::smem));
+        LU_CHECK_CUDA(cudaFuncSetAttribute(trsv_blocked_kernel<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)C::smem));
+        attr[ti] = true;
+    }
     for (int64_t c0 = 0; c0 < nrhs; c0 += kNR) {
         const int nr = (int)std::min<int64_t>(kNR, nrhs - c0);
         // reset the ticket and the done counter (the error word is kept: sticky)
@@ -239,9 +283,11 @@ int lu_launch_trsv_blocked(lu_context* c, cudaStream_t st, bool lower_unit, int6
         LU_CHECK_CUDA(cudaMemsetAsync(&c->sync[1].ticket, 0, sizeof(unsigned), st));
         LuProfScope prof(st, LU_K_SOLVE, sizeof(T) * (0.5 * n * n + 2.0 * n * nr), (double)n * n * nr);
         if (lower_unit)
-            trsv_blocked_kernel<T, true><<<nblk, kTrsvThreads, 0, st>>>(n, nr, LU, lda, X + c0 * ldx, ldx, &c->sync[1]);
+            trsv_blocked_kernel<T, true><<<nblk, kTrsvThreads, C::smem, st>>>(n, nr, LU, lda, X + c0 * ldx, ldx,
+                                                                              &c->sync[1]);
         else
-            trsv_blocked_kernel<T, false><<<nblk, kTrsvThreads, 0, st>>>(n, nr, LU, lda, X + c0 * ldx, ldx, &c->sync[1]);
+            trsv_blocked_kernel<T, false><<<nblk, kTrsvThreads, C::smem, st>>>(n, nr, LU, lda, X + c0 * ldx, ldx,
+                                                                               &c->sync[1]);
         LU_CHECK_LAUNCH();
     }
     return LU_SUCCESS;

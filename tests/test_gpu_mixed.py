@@ -37,13 +37,13 @@ def dev(a, dtype=torch.float64):
     return t
 
 
-PRECS = {"bf16": 0, "fp16": 1, "f32": 3, "bf16x3": 4, "f64": 5}
-UOP = {"bf16": 2.0 ** -9, "fp16": 2.0 ** -11, "f32": 2.0 ** -24, "bf16x3": 2.0 ** -16}
+PRECS = {"bf16": 0, "fp16": 1, "f32": 3, "bf16x3": 4, "f64": 5, "bf16x6": 6}
+UOP = {"bf16": 2.0 ** -9, "fp16": 2.0 ** -11, "f32": 2.0 ** -24, "bf16x3": 2.0 ** -16, "bf16x6": 2.0 ** -22}
 # variants whose factors are accurate enough for classical refinement to reach 1e-14 on these inputs
-CONVERGING = ("f32", "bf16x3", "f64")
+CONVERGING = ("f32", "bf16x3", "bf16x6", "f64")
 
 
-@pytest.mark.parametrize("prec", ["bf16", "fp16", "f32", "bf16x3"])
+@pytest.mark.parametrize("prec", ["bf16", "fp16", "f32", "bf16x3", "bf16x6"])
 @pytest.mark.parametrize("n,nb", [(1024, 128), (2048, 256), (1000, 64)])
 def test_factor_mixed(lu, prec, n, nb):
     A0 = synth.normal_matrix(n, seed=40, stream=n).astype(np.float32).astype(np.float64)
@@ -62,7 +62,7 @@ def test_factor_mixed(lu, prec, n, nb):
     assert ferr <= 8 * UOP[prec]
 
 
-@pytest.mark.parametrize("prec", ["bf16", "fp16", "f32", "bf16x3", "f64"])
+@pytest.mark.parametrize("prec", ["bf16", "fp16", "f32", "bf16x3", "bf16x6", "f64"])
 @pytest.mark.parametrize("n,nb,nrhs,kind", [(1024, 128, 1, "uniform"), (2048, 256, 1, "normal"),
                                             (2048, 256, 16, "normal"), (1500, 128, 19, "normal"),
                                             (2048, 256, 1, "rowscaled")])
@@ -87,8 +87,9 @@ def test_gesv_mixed(lu, prec, n, nb, nrhs, kind):
     fwd = np.abs(x - x_or).max() / np.abs(x_or).max()
     print(f"\n[gesv_mixed] prec={prec} n={n} nrhs={nrhs} {kind}: status={status} refinements={iters} "
           f"eta(gpu)={eta_gpu:.2e} eta(oracle)={eta:.2e} ||x-x_oracle||/||x_oracle||={fwd:.2e}")
-    # the returned iterate's backward error is the one the solver reports
-    assert abs(eta - eta_gpu) <= 1e-3 * eta_gpu + 1e-17
+    # the returned iterate's backward error is the one the solver reports (the GPU
+    # forms the residual without compensation: rounding ~ sqrt(n) u)
+    assert abs(eta - eta_gpu) <= 1e-3 * eta_gpu + np.sqrt(n) * np.finfo(float).eps
     if prec in CONVERGING:
         assert status == 0
     if status == 0:
@@ -134,7 +135,7 @@ def test_gesv_mixed_16384_sampled(lu):
     A0 = synth.normal_matrix(n, seed=0)
     B0 = synth.ones_rhs(A0)
     X = dev(np.zeros_like(B0))
-    status, iters, eta_gpu = lu.lu_gesv_mixed(dev(A0), dev(B0), X, PRECS["bf16x3"], 1e-14, 30, lu.default_opts(nb=256))
+    status, iters, eta_gpu = lu.lu_gesv_mixed(dev(A0), dev(B0), X, PRECS["bf16x6"], 1e-14, 30, lu.default_opts(nb=256))
     torch.cuda.synchronize()
     x = X.cpu().numpy()[:, 0]
     r = B0[:, 0] - A0 @ x

@@ -31,6 +31,22 @@ def dev32(a):
     return t
 
 
+def split_parts(X):
+    p0 = oracle.round_bf16(X)
+    p1 = oracle.round_bf16(X - p0)
+    p2 = oracle.round_bf16(X - p0 - p1)
+    return p0, p1, p2
+
+
+def split6_product(A, B):
+    """The six-product three-part split-bf16 product, exact in FP64."""
+    a, b = split_parts(A), split_parts(B)
+    pairs = ((0, 0), (0, 1), (1, 0), (0, 2), (1, 1), (2, 0))
+    prod = sum(a[i] @ b[j] for i, j in pairs)
+    aprod = sum(np.abs(a[i]) @ np.abs(b[j]) for i, j in pairs)
+    return prod, aprod
+
+
 def split_product(A, B):
     """hi_A hi_B + hi_A lo_B + lo_A hi_B with hi = bf16(x), lo = bf16(x - hi): the
     split-bf16 product, formed exactly in FP64 from the oracle's rounding."""
@@ -39,11 +55,12 @@ def split_product(A, B):
     return Ah @ Bh + Ah @ Bl + Al @ Bh, np.abs(Ah) @ np.abs(Bh) + np.abs(Ah) @ np.abs(Bl) + np.abs(Al) @ np.abs(Bh)
 
 
-@pytest.mark.parametrize("prec_name", ["bf16", "fp16", "bf16x3"])
+@pytest.mark.parametrize("prec_name", ["bf16", "fp16", "bf16x3", "bf16x6"])
 @pytest.mark.parametrize("m,n,k", [(128, 256, 64), (256, 256, 64), (1000, 700, 256), (300, 5000, 64),
                                    (4097, 129, 512), (1, 1, 64), (129, 257, 128)])
 def test_tc_update(lu, prec_name, m, n, k):
-    prec = {"bf16": lu.LU_TU_BF16, "fp16": lu.LU_TU_FP16, "bf16x3": lu.LU_TU_BF16X3}[prec_name]
+    prec = {"bf16": lu.LU_TU_BF16, "fp16": lu.LU_TU_FP16, "bf16x3": lu.LU_TU_BF16X3,
+            "bf16x6": lu.LU_TU_BF16X6}[prec_name]
     rnd = oracle.round_bf16 if prec_name == "bf16" else oracle.round_fp16
     g = synth.rng(31, m + n + k)
     C0, A0, B0 = (g.standard_normal(size=s).astype(np.float32).astype(np.float64)
@@ -55,6 +72,15 @@ def test_tc_update(lu, prec_name, m, n, k):
     assert int(info.item()) == 0
     got = C.cpu().double().numpy()
     u32 = np.finfo(np.float32).eps / 2
+    if prec_name == "bf16x6":
+        prod, aprod = split6_product(A0, B0)
+        ref = C0 - prod
+        scale = aprod + np.abs(C0)
+        assert np.all(np.abs(got - ref) <= (6 * k + 2) * u32 * scale)
+        # only products of weight <= 2^-24 are dropped: FP32-accurate
+        exact = oracle.gemm_update(C0, A0, B0)
+        assert np.all(np.abs(got - exact) <= (2.0 ** -21 + (6 * k + 2) * u32) * (np.abs(A0) @ np.abs(B0) + np.abs(C0)))
+        return
     if prec_name == "bf16x3":
         prod, aprod = split_product(A0, B0)
         ref = C0 - prod
