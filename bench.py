@@ -2,7 +2,8 @@
 
 Workload (default): the mixed-precision solver at n = 16384 -- A with iid
 N(0,1) entries (seed 0), one right-hand side b = A * ones, FP32 panel
-factorization, split-bf16 (bf16x3) tensor-core trailing update with FP32 accumulation,
+factorization, split-bf16 (bf16x6: three bf16 parts, six products) tensor-core
+trailing update with FP32 accumulation,
 depth-1 look-ahead, FP64 iterative refinement to a normwise backward error
 <= 1e-14 (at most 30 corrections).  One step = one lu_gesv_mixed call (the
 factorization, the solve and every refinement iteration), with A and b
@@ -173,7 +174,7 @@ def main():
     ap.add_argument("--n", type=int, default=N_DEFAULT)
     ap.add_argument("--nb", type=int, default=NB_DEFAULT)
     ap.add_argument("--nrhs", type=int, default=1)
-    ap.add_argument("--prec", default="bf16x3", choices=["bf16x3", "bf16", "fp16", "f32"])
+    ap.add_argument("--prec", default="bf16x6", choices=["bf16x6", "bf16x3", "bf16", "fp16", "f32"])
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison path")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle sample")
     args = ap.parse_args()
@@ -201,7 +202,8 @@ def main():
 
     L = lu.lib()
     n, nrhs = args.n, args.nrhs
-    prec = {"bf16": lu.LU_TU_BF16, "fp16": lu.LU_TU_FP16, "f32": lu.LU_TU_F32, "bf16x3": lu.LU_TU_BF16X3}[args.prec]
+    prec = {"bf16": lu.LU_TU_BF16, "fp16": lu.LU_TU_FP16, "f32": lu.LU_TU_F32, "bf16x3": lu.LU_TU_BF16X3,
+            "bf16x6": lu.LU_TU_BF16X6}[args.prec]
     opts = lu.default_opts(nb=args.nb)
     A0, B0 = make_inputs(n, nrhs)
     A = colmajor(n, n)
@@ -317,7 +319,8 @@ def main():
             "metric": "LU+solve GFLOP/s (2n^3/3), mixed+IR vs FP64 on same GB300 at bwd err <=1e-14",
             "value": value, "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": {"bf16": "f32+bf16", "bf16x3": "f32+bf16x3", "fp16": "f32+fp16", "f32": "f32"}[args.prec] + "+f64-ir",
+            "dtype": {"bf16": "f32+bf16", "bf16x3": "f32+bf16x3", "bf16x6": "f32+bf16x6", "fp16": "f32+fp16",
+                      "f32": "f32"}[args.prec] + "+f64-ir",
             "data": "synthetic", "config": workload_config(args) | {"parallelism": f"replicas{world}"},
             "converged": ok, "refinements": iters, "bwd_err": max(etas),
             "gpu_launches": launches, "kernel_time_share": shares,

@@ -234,7 +234,8 @@ int lu_factor_mixed_ex(lu_handle handle, lu_prec prec, int64_t n, float *A, int6
  * prec = LU_FULL_F64: copy, factor and solve in FP64 instead), then
  * refine in FP64: r = B - A X with the original A, stop when the normwise
  * backward error eta = max_c ||r_c|| / (||A|| ||x_c|| + ||b_c||) (inf-norms)
- * is <= tol, or after max_iter corrections.
+ * is <= 0.9 tol (the margin covers the rounding of the FP64 residual itself),
+ * or after max_iter corrections.
  *   A, B      device FP64, not modified
  *   X         device FP64 n x nrhs (ldx), receives the solution (the iterate
  *             with the smallest eta if tol was not reached)

@@ -272,11 +272,13 @@ static int gesv_refined(lu_context* h, int prec, int64_t n, int64_t nrhs, const 
         if (e < best) {
             best = e;
             best_it = it;
-            if (e > tol && it < max_iter)
+            if (e > 0.9 * tol && it < max_iter)
                 LU_CHECK_CUDA(cudaMemcpy2DAsync(Xb, n * sizeof(double), X, ldx * sizeof(double), n * sizeof(double),
                                                 nrhs, cudaMemcpyDeviceToDevice, st));
         }
-        if (e <= tol) break;
+        // the residual is formed in plain FP64 (rounding ~ sqrt(n) u relative to |A||x|), so
+        // convergence is declared with a 10% margin to keep the exact eta below tol
+        if (e <= 0.9 * tol) break;
         if (it >= max_iter || !(e == e)) {
             status = LU_WARN_NOT_CONVERGED;
             break;
