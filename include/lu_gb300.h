@@ -110,12 +110,13 @@ enum {
     LU_K_OTHER = 8,
     LU_K_COUNT = 9
 };
-/* lu_profile_enable(1): from now on every kernel launch is bracketed by two CUDA
- * events recorded on its own stream.  lu_profile_read synchronises the device
+/* lu_profile_enable(mask): from now on every kernel launch of a class whose bit
+ * (1 << class) is set in mask is bracketed by two CUDA events recorded on its
+ * own stream (mask 0 = off, -1 = all).  lu_profile_read synchronises the device
  * and returns, for one class, the number of launches since the last reset, the
  * sum of their event-to-event durations (ms) and of their algorithmic bytes
  * and flops (host pointers, any may be NULL).  lu_profile_reset clears. */
-int lu_profile_enable(int on);
+int lu_profile_enable(int mask);
 int lu_profile_reset(void);
 int lu_profile_read(int kclass, int64_t *launches, double *ms, double *bytes, double *flops);
 

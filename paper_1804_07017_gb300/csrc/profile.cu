@@ -1,5 +1,5 @@
-// Built-in launch profiler: when enabled, every kernel launch of the library is
-// bracketed by a pair of CUDA events recorded on the launching stream, tagged
+// Built-in launch profiler: when enabled for a kernel class, every launch of that
+// class is bracketed by a pair of CUDA events recorded on the launching stream, tagged
 // with its kernel class and its algorithmic bytes and flops.  lu_profile_read
 // synchronises, turns the event pairs into durations and aggregates them per
 // class.  Off by default; costs two event records per launch when on.
@@ -18,7 +18,7 @@ struct Rec {
 };
 
 std::mutex g_mu;
-bool g_on = false;
+unsigned g_mask = 0;
 std::vector<Rec> g_recs;
 std::vector<cudaEvent_t> g_pool;
 struct Agg {
@@ -64,9 +64,9 @@ void drain_locked() {
 }  // namespace
 
 LuProfScope::LuProfScope(cudaStream_t st, int cls, double bytes, double flops) : st_(st) {
-    if (!g_on) return;
+    if (!(g_mask & (1u << cls))) return;
     std::lock_guard<std::mutex> lk(g_mu);
-    if (!g_on) return;
+    if (!(g_mask & (1u << cls))) return;
     a_ = take_event();
     b_ = take_event();
     cls_ = cls;
@@ -83,9 +83,9 @@ LuProfScope::~LuProfScope() {
     g_recs.push_back(Rec{cls_, a_, b_, bytes_, flops_});
 }
 
-extern "C" int lu_profile_enable(int on) {
+extern "C" int lu_profile_enable(int mask) {
     std::lock_guard<std::mutex> lk(g_mu);
-    g_on = on != 0;
+    g_mask = (unsigned)mask & ((1u << LU_K_COUNT) - 1u);
     return LU_SUCCESS;
 }
 
