@@ -161,8 +161,10 @@ struct TcLayout {
     static constexpr int kSmemBytes = kMiscOffset + 64 + 1024;  // + alignment slack
 };
 
+// 144 registers x 320 threads leaves room on the SM for a panel-factorization CTA
+// (256 threads x <= 64 registers) next to this one.
 template <int BN>
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __maxnreg__(144)
     tc_update_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, TcUpdateParams p) {
     using L = TcLayout<BN>;
     extern __shared__ uint8_t smem_raw[];

@@ -14,6 +14,7 @@
 #define LU_PF_MAX_LEAF 64     // widest leaf (columns held in shared memory)
 #define LU_MAX_NB 1024        // widest panel accepted
 #define LU_PF_SMEM_BUDGET (78 * 1024)
+#define LU_PF_MAX_CTAS_CLUSTER 16  // CTAs of a cluster panel leaf (non-portable cluster size)
 
 struct lu_context {
     int device = 0;
@@ -43,6 +44,9 @@ struct lu_context {
     void* mx = nullptr;
     size_t mx_bytes = 0;
     double* host_eta = nullptr;  // pinned host word for the convergence test
+    // Shared memory a panel leaf CTA may use: small enough, on the mixed path, to
+    // sit beside a tensor-core trailing-update CTA on the same SM.
+    size_t pf_smem_budget = 160 * 1024;
     std::mutex mu;
 };
 
@@ -88,6 +92,12 @@ int lu_launch_trsv_blocked(lu_context* c, cudaStream_t st, bool lower_unit, int6
                            int64_t nrhs, const T* LU, int64_t lda, T* X, int64_t ldx);
 
 int lu_launch_finish_info(cudaStream_t st, const LuSync* s, int32_t* info);
+
+template <typename T>
+bool lu_pf_cluster_shape(int64_t m, int w, size_t budget, int* C_out, int* R_out, size_t* smem_out);
+template <typename T>
+int lu_launch_pf_leaf_cluster(cudaStream_t st, T* A, int64_t lda, int64_t m, int w, int C, int R, size_t smem,
+                              int64_t left_cols, int64_t right_cols, int32_t* ipiv, int64_t ipiv_add, int* info);
 
 // Recursive panel factorization of columns [j0, j0+width) over rows [j0, M)
 // of the matrix at A (absolute indices; ipiv absolute, 1-based).

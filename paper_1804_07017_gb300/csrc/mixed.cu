@@ -148,7 +148,7 @@ int setup_engine(TcEngine& e, lu_context* c, int prec, int64_t n, int nb, char* 
     e.lda_ = lda;
     // With look-ahead the right update leaves some SMs to the panel path; with
     // stealing, that many CTAs join the right update once the panel is done.
-    const int reserve = (o.lookahead && o.steal) ? std::max(8, c->num_sms / 8) : 0;
+    const int reserve = (o.lookahead && o.steal) ? std::max(4, c->num_sms / 16) : 0;
     e.grid_right = std::max(1, c->num_sms - reserve);
     e.grid_panel = c->num_sms;
     e.grid_steal = reserve;
@@ -165,7 +165,12 @@ static int factor_mixed(lu_context* c, int prec, int64_t n, float* A32, int64_t 
     if (!lu_prec_is_tc(prec)) return lu_factor_blocked<float>(c, n, A32, lda, ipiv, o, info, nullptr);
     TcEngine e;
     LU_TRY(setup_engine(e, c, prec, n, o.nb, engine_mem, A32, lda, o));
-    return lu_factor_blocked<float>(c, n, A32, lda, ipiv, o, info, &e);
+    // panel leaves must fit beside a tensor-core update CTA on the same SM
+    const size_t saved = c->pf_smem_budget;
+    c->pf_smem_budget = LU_PF_SMEM_BUDGET;
+    const int r = lu_factor_blocked<float>(c, n, A32, lda, ipiv, o, info, &e);
+    c->pf_smem_budget = saved;
+    return r;
 }
 
 extern "C" int lu_factor_mixed_ex(lu_handle h, lu_prec prec, int64_t n, float* A, int64_t lda, int32_t* ipiv,

@@ -238,13 +238,74 @@ int lu_launch_pf_leaf(lu_context* c, cudaStream_t st, T* A, int64_t lda, int64_t
     return LU_SUCCESS;
 }
 
+namespace {
+
+// One level of the recursive panel: columns [j0, j0+width) over rows [j0, M);
+// [pc0, pc0+pw) is the whole panel, whose other columns a cluster leaf updates
+// with its own interchanges.
 template <typename T>
-int lu_panel_recursive(lu_context* c, cudaStream_t st, T* A, int64_t lda, int64_t M, int64_t j0,
-                       int64_t width, int32_t* ipiv, const lu_opts& o) {
+int panel_rec(lu_context* c, cudaStream_t st, T* A, int64_t lda, int64_t M, int64_t j0, int64_t width,
+              int32_t* ipiv, const lu_opts& o, int leaf, bool cluster, int64_t pc0, int64_t pw) {
     if (width <= 0) return LU_SUCCESS;
-    int leaf = o.leaf > 0 ? std::min(o.leaf, LU_PF_MAX_LEAF) : 32;
-    // Narrow the leaf until the rows fit in the leaf grid's shared memory.
     const int64_t rows = M - j0;
+    if (width <= leaf) {
+        if (cluster) {
+            int C = 0, R = 0;
+            size_t smem = 0;
+            if (lu_pf_cluster_shape<T>(rows, (int)width, c->pf_smem_budget, &C, &R, &smem))
+                return lu_launch_pf_leaf_cluster<T>(st, A + j0 + j0 * lda, lda, rows, (int)width, C, R, smem, j0 - pc0,
+                                                    pc0 + pw - (j0 + width), ipiv + j0, j0, &c->sync[0].info);
+            return LU_ERR_UNSUPPORTED;
+        }
+        return lu_launch_pf_leaf<T>(c, st, A + j0 + j0 * lda, lda, rows, (int)width, ipiv + j0, j0, o.pf_ctas);
+    }
+    int64_t w1 = ((width / 2 + 7) / 8) * 8;
+    if (w1 >= width) w1 = width / 2;
+    if (w1 < 1) w1 = 1;
+    const int64_t w2 = width - w1;
+    LU_TRY(panel_rec<T>(c, st, A, lda, M, j0, w1, ipiv, o, leaf, cluster, pc0, pw));
+    if (!cluster) {
+        // interchanges of the left half applied to the right half's columns
+        LU_TRY(lu_launch_laswp_plan(st, ipiv, j0, j0 + w1, c->plan_tmp));
+        LU_TRY(lu_launch_laswp_apply<T>(st, A, lda, j0 + w1, w2, 0, 0, c->plan_tmp, w1, c->num_sms));
+    }
+    // RL2 and RL3 restricted to the panel
+    LU_TRY(lu_launch_trsm_lunit<T>(st, w1, w2, A + j0 + j0 * lda, lda, A + j0 + (j0 + w1) * lda, lda));
+    if (M - j0 - w1 > 0)
+        LU_TRY(lu_launch_gemm_update<T>(st, M - j0 - w1, w2, w1, A + (j0 + w1) + j0 * lda, lda,
+                                        A + j0 + (j0 + w1) * lda, lda, A + (j0 + w1) + (j0 + w1) * lda, lda));
+    LU_TRY(panel_rec<T>(c, st, A, lda, M, j0 + w1, w2, ipiv, o, leaf, cluster, pc0, pw));
+    if (!cluster) {
+        // interchanges of the right half applied back to the left half's columns
+        LU_TRY(lu_launch_laswp_plan(st, ipiv, j0 + w1, j0 + width, c->plan_tmp));
+        LU_TRY(lu_launch_laswp_apply<T>(st, A, lda, j0, w1, 0, 0, c->plan_tmp, w2, c->num_sms));
+    }
+    return LU_SUCCESS;
+}
+
+}  // namespace
+
+template <typename T>
+int lu_panel_recursive(lu_context* c, cudaStream_t st, T* A, int64_t lda, int64_t M, int64_t j0, int64_t width,
+                       int32_t* ipiv, const lu_opts& o) {
+    if (width <= 0) return LU_SUCCESS;
+    const int64_t rows = M - j0;
+    // Cluster leaves (distributed shared memory, hardware barrier) when the tallest
+    // leaf fits one cluster; otherwise grid-barrier leaves.
+    int leaf = o.leaf > 0 ? std::min(o.leaf, LU_PF_MAX_LEAF) : 32;
+    while (leaf > 8) {
+        int C, R;
+        size_t smem;
+        if (lu_pf_cluster_shape<T>(rows, std::min<int>(leaf, (int)width), c->pf_smem_budget, &C, &R, &smem)) break;
+        leaf >>= 1;
+    }
+    {
+        int C, R;
+        size_t smem;
+        if (lu_pf_cluster_shape<T>(rows, std::min<int>(leaf, (int)width), c->pf_smem_budget, &C, &R, &smem))
+            return panel_rec<T>(c, st, A, lda, M, j0, width, ipiv, o, leaf, true, j0, width);
+    }
+    leaf = o.leaf > 0 ? std::min(o.leaf, LU_PF_MAX_LEAF) : 32;
     const int max_ctas = o.pf_ctas > 0 ? o.pf_ctas : LU_PF_MAX_CTAS;
     while (leaf > 1) {
         int64_t R, G;
@@ -252,29 +313,7 @@ int lu_panel_recursive(lu_context* c, cudaStream_t st, T* A, int64_t lda, int64_
         if (lu_pf_leaf_shape(rows, leaf, (int)sizeof(T), max_ctas, &R, &G, &smem)) break;
         leaf >>= 1;
     }
-    if (width <= leaf) {
-        return lu_launch_pf_leaf<T>(c, st, A + j0 + j0 * lda, lda, rows, (int)width, ipiv + j0, j0,
-                                    o.pf_ctas);
-    }
-    int64_t w1 = ((width / 2 + 7) / 8) * 8;
-    if (w1 >= width) w1 = width / 2;
-    if (w1 < 1) w1 = 1;
-    const int64_t w2 = width - w1;
-    LU_TRY(lu_panel_recursive<T>(c, st, A, lda, M, j0, w1, ipiv, o));
-    // interchanges of the left half applied to the right half's columns
-    LU_TRY(lu_launch_laswp_plan(st, ipiv, j0, j0 + w1, c->plan_tmp));
-    LU_TRY(lu_launch_laswp_apply<T>(st, A, lda, j0 + w1, w2, 0, 0, c->plan_tmp, w1, c->num_sms));
-    // RL2 and RL3 restricted to the panel
-    LU_TRY(lu_launch_trsm_lunit<T>(st, w1, w2, A + j0 + j0 * lda, lda, A + j0 + (j0 + w1) * lda, lda));
-    if (M - j0 - w1 > 0)
-        LU_TRY(lu_launch_gemm_update<T>(st, M - j0 - w1, w2, w1, A + (j0 + w1) + j0 * lda, lda,
-                                        A + j0 + (j0 + w1) * lda, lda,
-                                        A + (j0 + w1) + (j0 + w1) * lda, lda));
-    LU_TRY(lu_panel_recursive<T>(c, st, A, lda, M, j0 + w1, w2, ipiv, o));
-    // interchanges of the right half applied back to the left half's columns
-    LU_TRY(lu_launch_laswp_plan(st, ipiv, j0 + w1, j0 + width, c->plan_tmp));
-    LU_TRY(lu_launch_laswp_apply<T>(st, A, lda, j0, w1, 0, 0, c->plan_tmp, w2, c->num_sms));
-    return LU_SUCCESS;
+    return panel_rec<T>(c, st, A, lda, M, j0, width, ipiv, o, leaf, false, j0, width);
 }
 
 template int lu_launch_pf_leaf<double>(lu_context*, cudaStream_t, double*, int64_t, int64_t, int,
