@@ -57,7 +57,8 @@ typedef enum { LU_F64 = 0, LU_F32 = 1 } lu_dtype;
 typedef enum {
     LU_TU_BF16 = 0, /* bf16 operands, tcgen05.mma kind::f16 */
     LU_TU_FP16 = 1, /* fp16 operands, tcgen05.mma kind::f16 */
-    LU_TU_FP8 = 2,  /* e4m3 operands with power-of-two block scales, kind::f8f6f4 */
+    LU_TU_FP8 = 2,  /* e4m3 operands with power-of-two block scales (one per row of L21,
+                       one per column of U12), kind::f8f6f4; nb a multiple of 128 */
     LU_TU_F32 = 3,  /* FP32 on the CUDA cores (no tensor cores; a reference point) */
     LU_TU_BF16X3 = 4, /* split bf16: each FP32 operand as hi + lo bf16, three products
                          (hi*hi + hi*lo + lo*hi) accumulated in FP32, kind::f16 */
@@ -204,12 +205,23 @@ int lu_gemm_update_ex(lu_handle handle, lu_dtype dtype, int64_t m, int64_t n, in
 /*
  * lu_gemm_update_tc_ex -- RL3, C := C - A B on the tensor cores: A (m x k) and
  * B (k x n) are FP32 and are rounded to the operand type of `prec` (round to
- * nearest even; LU_TU_BF16, LU_TU_FP16, LU_TU_BF16X3 or LU_TU_BF16X6), the products accumulate in FP32
- * and C (FP32, m x n) is updated in place.  k must be a multiple of 64.
+ * nearest even; LU_TU_BF16, LU_TU_FP16, LU_TU_BF16X3 or LU_TU_BF16X6; with LU_TU_FP8 each row of A and
+ * each column of B is scaled by a power of two 2^e, e the smallest integer with max|block| / 2^e <= 448,
+ * before rounding to e4m3), the products accumulate in FP32, the scales are applied to the FP32
+ * accumulator, and C (FP32, m x n) is updated in place.  k must be a multiple of 64 (128 for FP8).
  *   info  device int32[1]; 0, or LU_ERR_TIMEOUT if a bounded wait expired.
  */
 int lu_gemm_update_tc_ex(lu_handle handle, lu_prec prec, int64_t m, int64_t n, int64_t k, const float *A,
                          int64_t lda, const float *B, int64_t ldb, float *C, int64_t ldc, int32_t *info);
+
+/*
+ * lu_selftest_wait_timeout -- diagnostic of the failure path shared by every
+ * kernel that synchronises CTAs through global memory: launches a grid barrier
+ * that can never complete, whose bounded wait gives up after limit_ns
+ * nanoseconds (1 .. 2e9) of device time; *status (device int32) receives
+ * LU_ERR_TIMEOUT when the path works.  Asynchronous; leaves the device usable.
+ */
+int lu_selftest_wait_timeout(lu_handle handle, int64_t limit_ns, int32_t *status);
 
 /* ----------------------------------------------------------------------------
  * Mixed precision (not in the paper, whose experiments are FP64 only): FP32

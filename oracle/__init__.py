@@ -18,6 +18,8 @@ Each routine states the passage of the paper it restates:
 * ``backward_error`` / ``factor_error`` -- the normwise backward errors used
   as pass criteria (definitions, compensated sums).
 * ``round_*`` -- ties-to-even rounding onto bf16 / fp16 / e4m3 / fp32.
+* ``quant_e4m3_rows`` / ``quant_e4m3_cols`` -- power-of-two block scaling onto
+  e4m3 (one scale per row of L21 / per column of U12) for the FP8 update.
 
 Parity status: every function here is pinned by tests/test_oracle_pins.py.
 """
@@ -74,6 +76,7 @@ def _load():
             "oracle_round_fp16": (None, [i64, vp, vp]),
             "oracle_round_e4m3": (None, [i64, vp, vp]),
             "oracle_round_fp32": (None, [i64, vp, vp]),
+            "oracle_quant_e4m3_blocks": (None, [i64, i64, vp, i64, i64, vp, vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -219,3 +222,26 @@ def round_e4m3(x):
 
 def round_fp32(x):
     return _round("oracle_round_fp32", x)
+
+
+def quant_e4m3_rows(X):
+    """Per-row power-of-two scaled e4m3 quantisation.  Returns (Q, s) with
+    X ~= diag(s) Q; Q holds e4m3 values, s powers of two."""
+    lib = _load()
+    Xf = _f64(X)
+    m, k = Xf.shape
+    Q = np.zeros_like(Xf)
+    sc = np.zeros(max(m, 1))
+    lib.oracle_quant_e4m3_blocks(m, k, _ptr(Xf), 1, max(m, 1), _ptr(Q), _ptr(sc))
+    return Q, sc[:m]
+
+
+def quant_e4m3_cols(X):
+    """Per-column power-of-two scaled e4m3 quantisation: X ~= Q diag(t)."""
+    lib = _load()
+    Xf = _f64(X)
+    k, n = Xf.shape
+    Q = np.zeros_like(Xf)
+    sc = np.zeros(max(n, 1))
+    lib.oracle_quant_e4m3_blocks(n, k, _ptr(Xf), max(k, 1), 1, _ptr(Q), _ptr(sc))
+    return Q, sc[:n]

@@ -388,3 +388,42 @@ void oracle_round_fp32(int64_t count, const double *in, double *out)
         out[i] = r;
     }
 }
+
+/*
+ * Power-of-two block scaling onto e4m3 for the FP8 trailing update.  Each
+ * block (one row of the L21 operand, or one column of the U12 operand) gets
+ * the scale 2^e with e the smallest integer such that amax / 2^e <= 448, the
+ * largest finite e4m3 value: with amax = f 2^x, f in [0.5, 1), and
+ * 448 = 0.875 2^9, e = x - 9 + (f > 0.875).  A block of zeros gets e = 0.
+ * The stored value is e4m3(v / 2^e) (ties to even, saturating), so
+ * q * 2^e is the dequantised operand.  The exponent is an exact integer
+ * decision taken from the block's maximum, identical in any precision that
+ * represents amax exactly.
+ *   X: nblk blocks of len values; block b starts at X + b*bstride, its
+ *      elements are estride apart.  Q: same layout.  scale[b] = 2^e.
+ */
+void oracle_quant_e4m3_blocks(int64_t nblk, int64_t len, const double *X, int64_t bstride,
+                              int64_t estride, double *Q, double *scale)
+{
+    for (int64_t b = 0; b < nblk; ++b) {
+        double amax = 0.0;
+        for (int64_t i = 0; i < len; ++i) {
+            double v = fabs(X[b * bstride + i * estride]);
+            if (v > amax) amax = v;
+        }
+        int e = 0;
+        if (amax > 0.0) {
+            int x;
+            double f = frexp(amax, &x);
+            e = x - 9 + (f > 0.875 ? 1 : 0);
+        }
+        double sc = ldexp(1.0, e);
+        scale[b] = sc;
+        for (int64_t i = 0; i < len; ++i) {
+            double v = X[b * bstride + i * estride] / sc;
+            double r = round_to_format(v, 3, -6);
+            if (fabs(r) > 448.0 && !isnan(r)) r = r > 0 ? 448.0 : -448.0;
+            Q[b * bstride + i * estride] = r;
+        }
+    }
+}

@@ -62,6 +62,7 @@ _SIGNATURES = {
     "lu_trsm_ex": (i32, [vp, i32, i64, i64, vp, i64, vp, i64]),
     "lu_gemm_update_ex": (i32, [vp, i32, i64, i64, i64, vp, i64, vp, i64, vp, i64]),
     "lu_gemm_update_tc_ex": (i32, [vp, i32, i64, i64, i64, vp, i64, vp, i64, vp, i64, vp]),
+    "lu_selftest_wait_timeout": (i32, [vp, i64, vp]),
     "lu_profile_enable": (i32, [i32]),
     "lu_profile_reset": (i32, []),
     "lu_profile_read": (i32, [i32, ctypes.POINTER(i64), ctypes.POINTER(dbl), ctypes.POINTER(dbl),

@@ -78,7 +78,8 @@ __device__ __forceinline__ unsigned int lu_atom_add_release(unsigned int* p, uns
 // Grid-wide barrier for a launch whose CTAs are all resident.  Thread 0 of each
 // CTA arrives and spins (bounded); returns false if the wait timed out or
 // another CTA reported an error, in which case the caller must leave.
-__device__ __forceinline__ bool lu_grid_barrier(LuSync* s, unsigned int target, int* sh_flag) {
+__device__ __forceinline__ bool lu_grid_barrier(LuSync* s, unsigned int target, int* sh_flag,
+                                                uint64_t limit_ns = LU_WAIT_NS) {
     __syncthreads();
     if (threadIdx.x == 0) {
         int ok = 1;
@@ -90,7 +91,7 @@ __device__ __forceinline__ bool lu_grid_barrier(LuSync* s, unsigned int target, 
                 if (lu_ld_acquire_s32(&s->error) != 0) { ok = 0; break; }
                 uint64_t t = lu_globaltimer();
                 if (t0 == 0) t0 = t;
-                else if (t - t0 > LU_WAIT_NS) {
+                else if (t - t0 > limit_ns) {
                     atomicExch(&s->error, LU_ERR_TIMEOUT);
                     ok = 0;
                     break;

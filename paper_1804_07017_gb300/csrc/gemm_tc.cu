@@ -28,6 +28,7 @@
 #include <cudaTypedefs.h>
 
 #include "internal.h"
+#include "ptx.cuh"
 #include "profile.h"
 #include "tc.h"
 
@@ -40,60 +41,6 @@ constexpr int kRing = 4;         // tile-index ring depth
 constexpr int kThreads = 320;    // 10 warps
 constexpr int kEpiWarps = 8;
 constexpr uint64_t kWaitNs = 2000000000ull;
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
-    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(smem_u32(bar)) : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
-    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(smem_u32(bar)),
-                 "r"(bytes)
-                 : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-// Bounded wait on one phase of an mbarrier.  Returns false (and raises the
-// CTA-wide abort flag) if it gives up.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
-    if (mbar_try_wait(bar, parity)) return true;
-    uint64_t t0 = lu_globaltimer();
-    uint32_t spins = 0;
-    while (!mbar_try_wait(bar, parity)) {
-        if ((++spins & 63u) == 0) {
-            if (*abort_flag) return false;
-            if (lu_globaltimer() - t0 > kWaitNs) {
-                *abort_flag = 1;
-                return false;
-            }
-        }
-    }
-    return true;
-}
-
-__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y) {
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
-            smem_u32(dst)),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
-        : "memory");
-}
 
 // Shared-memory matrix descriptor for a K-major operand tile written by TMA with
 // 128-byte swizzling: 8-row x 128-byte swizzle atoms stacked at 1024-byte
@@ -321,9 +268,19 @@ __global__ void __maxnreg__(144)
                 for (int j = 0; j < 32; ++j)
                     cv[j] = (row_ok && c_local + j < p.ncols) ? __ldcs(cp + (int64_t)j * p.ldc) : 0.f;
                 tmem_ld32(tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(ab * BN + ct), acc);
+                if (p.rscale) {
+                    // power-of-two block scales: exact rescaling of the FP32 accumulator
+                    const float rs = row_ok ? p.rscale[r_local] * p.scale : 0.f;
 #pragma unroll
-                for (int j = 0; j < 32; ++j)
-                    if (row_ok && c_local + j < p.ncols) __stcs(cp + (int64_t)j * p.ldc, cv[j] - acc[j] * p.scale);
+                    for (int j = 0; j < 32; ++j)
+                        if (row_ok && c_local + j < p.ncols)
+                            __stcs(cp + (int64_t)j * p.ldc, cv[j] - acc[j] * (rs * p.cscale[c_local + j]));
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 32; ++j)
+                        if (row_ok && c_local + j < p.ncols)
+                            __stcs(cp + (int64_t)j * p.ldc, cv[j] - acc[j] * p.scale);
+                }
             }
             tc_fence_before();
             __syncwarp();
@@ -397,7 +354,8 @@ int lu_tc_smem_bytes(int bn) { return bn == 256 ? TcLayout<256>::kSmemBytes : Tc
 // b_rows >= ncols).
 int lu_launch_tc_update(cudaStream_t st, int kind, int fmt, float* C, int64_t ldc, int64_t row0, int64_t m,
                         int64_t col0, int64_t ncols, int64_t k, const void* Abuf, int64_t a_rows, const void* Bbuf,
-                        int64_t b_rows, float scale, int* counter, int* error, int grid, int bn) {
+                        int64_t b_rows, float scale, int* counter, int* error, int grid, int bn,
+                        const float* rscale, const float* cscale) {
     if (m <= 0 || ncols <= 0) return LU_SUCCESS;
     const int elem = (kind == LU_TC_KIND_F16) ? 2 : 1;
     const int kchunk = 128 / elem;
@@ -424,6 +382,8 @@ int lu_launch_tc_update(cudaStream_t st, int kind, int fmt, float* C, int64_t ld
     p.error = error;
     p.kind = kind;
     p.scale = scale;
+    p.rscale = rscale;
+    p.cscale = cscale;
     // instruction descriptor: D = F32, A/B format, both K-major, N >> 3, M >> 4
     uint32_t idesc = (1u << 4) | ((uint32_t)fmt << 7) | ((uint32_t)fmt << 10) | ((uint32_t)(bn >> 3) << 17) |
                      ((uint32_t)(kTM >> 4) << 24);

@@ -97,7 +97,7 @@ template <typename T>
 bool lu_pf_cluster_shape(int64_t m, int w, size_t budget, int* C_out, int* R_out, size_t* smem_out);
 template <typename T>
 int lu_launch_pf_leaf_cluster(cudaStream_t st, T* A, int64_t lda, int64_t m, int w, int C, int R, size_t smem,
-                              int64_t left_cols, int64_t right_cols, int32_t* ipiv, int64_t ipiv_add, int* info);
+                              int64_t left_cols, int64_t right_cols, int32_t* ipiv, int64_t ipiv_add, LuSync* sync);
 
 // Recursive panel factorization of columns [j0, j0+width) over rows [j0, M)
 // of the matrix at A (absolute indices; ipiv absolute, 1-based).
@@ -127,7 +127,8 @@ int lu_factor_blocked(lu_context* c, int64_t n, T* A, int64_t lda, int32_t* ipiv
 
 // Operand precisions of the tensor-core trailing update.
 static inline bool lu_prec_is_tc(int prec) {
-    return prec == LU_TU_BF16 || prec == LU_TU_FP16 || prec == LU_TU_BF16X3 || prec == LU_TU_BF16X6;
+    return prec == LU_TU_BF16 || prec == LU_TU_FP16 || prec == LU_TU_BF16X3 || prec == LU_TU_BF16X6 ||
+           prec == LU_TU_FP8;
 }
 // pack.h format code of a tensor-core precision (LU_PACK_BF16 0, FP16 1, BF16X3 2, BF16X6 3)
 static inline int lu_prec_pack_fmt(int prec) {

@@ -34,7 +34,7 @@ extern "C" int lu_gemm_update_tc_ex(lu_handle h, lu_prec prec, int64_t m, int64_
     if (!lu_prec_is_tc(prec)) return -2;
     if (m < 0) return -3;
     if (n < 0) return -4;
-    if (k < 0 || k % 64 != 0) return -5;
+    if (k < 0 || k % (prec == LU_TU_FP8 ? 128 : 64) != 0) return -5;
     if (m > 0 && k > 0 && !A) return -6;
     if (lda < std::max<int64_t>(1, m)) return -7;
     if (k > 0 && n > 0 && !B) return -8;
@@ -46,7 +46,19 @@ extern "C" int lu_gemm_update_tc_ex(lu_handle h, lu_prec prec, int64_t m, int64_
     LU_TRY(lu_ctx_reserve(h, 1, 1));
     cudaStream_t st = h->user;
     LU_CHECK_CUDA(cudaMemsetAsync(&h->sync[2], 0, sizeof(LuSync), st));
-    if (m > 0 && n > 0 && k > 0) {
+    if (m > 0 && n > 0 && k > 0 && prec == LU_TU_FP8) {
+        const size_t abytes = al256((size_t)m * k), bbytes = al256((size_t)n * k);
+        const size_t rbytes = al256(sizeof(float) * m), cbytes = al256(sizeof(float) * n);
+        LU_TRY(lu_mx_reserve(h, abytes + bbytes + rbytes + cbytes));
+        char* a = (char*)h->mx;
+        char* b = a + abytes;
+        float* rs = (float*)(b + bbytes);
+        float* cs = (float*)((char*)rs + rbytes);
+        LU_TRY(lu_launch_pack_rows_e4m3(st, A, lda, m, (int)k, rs, a));
+        LU_TRY(lu_launch_pack_cols_e4m3(st, B, ldb, n, (int)k, cs, b));
+        LU_TRY(lu_launch_tc_update(st, LU_TC_KIND_F8, LU_TC_FMT_E4M3, C, ldc, 0, m, 0, n, k, a, m, b, n, 1.0f,
+                                   (int*)&h->sync[2].ticket, &h->sync[2].error, h->num_sms, 256, rs, cs));
+    } else if (m > 0 && n > 0 && k > 0) {
         const int fmt = lu_prec_pack_fmt(prec);
         const int sg = lu_pack_segments(fmt);
         const size_t abytes = al256((size_t)m * k * 2 * sg), bbytes = al256((size_t)n * k * 2 * sg);
@@ -81,28 +93,43 @@ struct TcEngine final : LuTuEngine {
     mutable int64_t last_k = -1;
     mutable int64_t last_k0 = 0, last_kb = 0, last_cb = 0, last_ce = 0;
 
+    bool fp8() const { return prec == LU_TU_FP8; }
     int fmt_pack() const { return lu_prec_pack_fmt(prec); }
-    int fmt_mma() const { return prec == LU_TU_FP16 ? LU_TC_FMT_F16 : LU_TC_FMT_BF16; }
-    int segs() const { return lu_pack_segments(fmt_pack()); }
+    int fmt_mma() const { return fp8() ? LU_TC_FMT_E4M3 : (prec == LU_TU_FP16 ? LU_TC_FMT_F16 : LU_TC_FMT_BF16); }
+    int segs() const { return fp8() ? 1 : lu_pack_segments(fmt_pack()); }
+    int esize() const { return fp8() ? 1 : 2; }
+    // FP8: the block scales follow the e4m3 bytes in each operand buffer
+    size_t scale_off() const { return al256((size_t)n * nb); }
+    float* rscale(int64_t k) const { return reinterpret_cast<float*>(alo[k & 1] + scale_off()); }
+    float* cscale(int64_t k, int64_t off) const { return reinterpret_cast<float*>(blo[k & 1] + scale_off()) + off; }
 
-    bool uses_tc(int64_t kb) const override { return lu_prec_is_tc(prec) && kb % 64 == 0; }
+    bool uses_tc(int64_t kb) const override { return lu_prec_is_tc(prec) && kb % (fp8() ? 128 : 64) == 0; }
 
     int pack_panel(cudaStream_t st, const float* A, int64_t lda, int64_t k, int64_t k0, int64_t kb) const override {
+        if (fp8())
+            return lu_launch_pack_rows_e4m3(st, A + (k0 + kb) + k0 * lda, lda, n - (k0 + kb), (int)kb, rscale(k),
+                                            alo[k & 1]);
         return lu_launch_pack_rows(st, fmt_pack(), A + (k0 + kb) + k0 * lda, lda, n - (k0 + kb), (int)kb, alo[k & 1]);
     }
 
     int launch(cudaStream_t st, float* A, int64_t lda, int64_t k, int64_t k0, int64_t kb, int64_t cb, int64_t ce,
                int which, int grid) const {
         const int64_t m = n - (k0 + kb);
-        const char* bbuf = blo[k & 1] + (size_t)(cb - (k0 + kb)) * kb * 2 * segs();
-        return lu_launch_tc_update(st, LU_TC_KIND_F16, fmt_mma(), A, lda, k0 + kb, m, cb, ce - cb, kb * segs(),
-                                   alo[k & 1], m, bbuf, ce - cb, 1.0f, counter[which], error, grid, 256);
+        const int64_t off = cb - (k0 + kb);
+        const char* bbuf = blo[k & 1] + (size_t)off * kb * esize() * segs();
+        return lu_launch_tc_update(st, fp8() ? LU_TC_KIND_F8 : LU_TC_KIND_F16, fmt_mma(), A, lda, k0 + kb, m, cb,
+                                   ce - cb, kb * segs(), alo[k & 1], m, bbuf, ce - cb, 1.0f, counter[which], error,
+                                   grid, 256, fp8() ? rscale(k) : nullptr, fp8() ? cscale(k, off) : nullptr);
     }
 
     int update(cudaStream_t st, float* A, int64_t lda, int64_t k, int64_t k0, int64_t kb, int64_t cb, int64_t ce,
                int which) const override {
-        char* bbuf = blo[k & 1] + (size_t)(cb - (k0 + kb)) * kb * 2 * segs();
-        LU_TRY(lu_launch_pack_cols(st, fmt_pack(), A + k0 + cb * lda, lda, ce - cb, (int)kb, bbuf));
+        const int64_t off = cb - (k0 + kb);
+        char* bbuf = blo[k & 1] + (size_t)off * kb * esize() * segs();
+        if (fp8())
+            LU_TRY(lu_launch_pack_cols_e4m3(st, A + k0 + cb * lda, lda, ce - cb, (int)kb, cscale(k, off), bbuf));
+        else
+            LU_TRY(lu_launch_pack_cols(st, fmt_pack(), A + k0 + cb * lda, lda, ce - cb, (int)kb, bbuf));
         LU_CHECK_CUDA(cudaMemsetAsync(counter[which], 0, sizeof(int), st));
         if (which == 1) {
             LU_CHECK_CUDA(cudaEventRecord(ev_ready, st));
@@ -127,6 +154,7 @@ struct TcEngine final : LuTuEngine {
 
 size_t tc_engine_bytes(int prec, int64_t n, int nb) {
     if (!lu_prec_is_tc(prec)) return 256;
+    if (prec == LU_TU_FP8) return 4 * al256(al256((size_t)n * nb) + sizeof(float) * (size_t)n);
     return 4 * al256((size_t)n * nb * 2 * lu_pack_segments(lu_prec_pack_fmt(prec)));
 }
 
@@ -136,7 +164,7 @@ int setup_engine(TcEngine& e, lu_context* c, int prec, int64_t n, int nb, char* 
     e.prec = prec;
     e.n = n;
     e.nb = nb;
-    const size_t one = al256((size_t)n * nb * 2 * lu_pack_segments(lu_prec_pack_fmt(prec)));
+    const size_t one = tc_engine_bytes(prec, n, nb) / 4;
     e.alo[0] = base;
     e.alo[1] = base + one;
     e.blo[0] = base + 2 * one;
@@ -317,6 +345,7 @@ extern "C" int lu_gesv_mixed(lu_handle h, lu_prec prec, int64_t n, int64_t nrhs,
                              const lu_opts* opts, int* iters, double* bwd_err) {
     if (!h) return LU_ERR_HANDLE;
     if (!lu_prec_is_tc(prec) && prec != LU_TU_F32 && prec != LU_FULL_F64) return -2;
+    if (prec == LU_TU_FP8 && opts && opts->nb % 128 != 0) return -13;
     if (n < 0) return -3;
     if (nrhs < 0) return -4;
     if (n > 0 && !A) return -5;

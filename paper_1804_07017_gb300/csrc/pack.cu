@@ -16,6 +16,7 @@
 // full 24-bit FP32 significand.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
+#include <cuda_fp8.h>
 
 #include "internal.h"
 #include "profile.h"
@@ -108,7 +109,98 @@ __global__ void __launch_bounds__(256) pack_cols_kernel(const float* __restrict_
     }
 }
 
+// ---------------------------------------------------------------------------
+// e4m3 operands with power-of-two block scales (one scale per row of L21, one
+// per column of U12).  The exponent is the smallest e with amax / 2^e <= 448:
+// with amax = f 2^x, f in [0.5, 1) and 448 = 0.875 2^9, e = x - 9 + (f > 0.875).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int e4m3_block_exponent(float amax) {
+    if (!(amax > 0.f)) return 0;
+    int x;
+    const float f = frexpf(amax, &x);
+    return x - 9 + (f > 0.875f ? 1 : 0);
+}
+
+__device__ __forceinline__ uint8_t to_e4m3(float v) {
+    return (uint8_t)__nv_cvt_float_to_fp8(v, __NV_SATFINITE, __NV_E4M3);
+}
+
+// rscale[r] = 2^e of row r (one thread per row; column-major reads are coalesced across threads)
+__global__ void __launch_bounds__(256) row_scale_kernel(const float* __restrict__ A, int64_t lda, int64_t rows, int k,
+                                                        float* __restrict__ rscale) {
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= rows) return;
+    float amax = 0.f;
+    for (int kk = 0; kk < k; ++kk) amax = fmaxf(amax, fabsf(A[r + (int64_t)kk * lda]));
+    rscale[r] = ldexpf(1.f, e4m3_block_exponent(amax));
+}
+
+// out[r][kk] = e4m3(A[r + kk*lda] / rscale[r]), 32-row x 64-column tiles through shared memory
+__global__ void __launch_bounds__(256) pack_rows_e4m3_kernel(const float* __restrict__ A, int64_t lda, int64_t rows,
+                                                             int k, const float* __restrict__ rscale,
+                                                             uint8_t* __restrict__ out) {
+    __shared__ uint8_t tile[32][64 + 4];
+    const int64_t r0 = (int64_t)blockIdx.x * 32;
+    const int k0 = blockIdx.y * 64;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    const int64_t r = r0 + tx;
+    const int sexp = (r < rows) ? -ilogbf(rscale[r]) : 0;
+    for (int kk = ty; kk < 64; kk += 8) {
+        const int kc = k0 + kk;
+        tile[tx][kk] = (r < rows && kc < k) ? to_e4m3(ldexpf(A[r + (int64_t)kc * lda], sexp)) : (uint8_t)0;
+    }
+    __syncthreads();
+    for (int rr = ty; rr < 32; rr += 8) {
+        const int64_t ro = r0 + rr;
+        const int kc = k0 + 2 * tx;
+        if (ro < rows && kc < k) {
+            out[ro * k + kc] = tile[rr][2 * tx];
+            if (kc + 1 < k) out[ro * k + kc + 1] = tile[rr][2 * tx + 1];
+        }
+    }
+}
+
+// one warp per column of B (K-contiguous): block maximum, scale, e4m3 bytes
+__global__ void __launch_bounds__(256) pack_cols_e4m3_kernel(const float* __restrict__ B, int64_t ldb, int64_t cols,
+                                                             int k, float* __restrict__ cscale,
+                                                             uint8_t* __restrict__ out) {
+    const int lane = threadIdx.x & 31;
+    const int64_t c = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (c >= cols) return;
+    const float* b = B + c * ldb;
+    float amax = 0.f;
+    for (int kk = lane; kk < k; kk += 32) amax = fmaxf(amax, fabsf(b[kk]));
+    for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+    const int e = e4m3_block_exponent(amax);
+    if (lane == 0) cscale[c] = ldexpf(1.f, e);
+    for (int kk = lane; kk < k; kk += 32) out[c * k + kk] = to_e4m3(ldexpf(b[kk], -e));
+}
+
 }  // namespace
+
+int lu_launch_pack_rows_e4m3(cudaStream_t st, const float* A, int64_t lda, int64_t rows, int k, float* rscale,
+                             void* out) {
+    if (rows <= 0 || k <= 0) return LU_SUCCESS;
+    {
+        LuProfScope prof(st, LU_K_PACK, 4.0 * rows * k, 0.0);
+        row_scale_kernel<<<(unsigned)lu_cdiv(rows, 256), 256, 0, st>>>(A, lda, rows, k, rscale);
+    }
+    LU_CHECK_LAUNCH();
+    dim3 grid((unsigned)lu_cdiv(rows, 32), (unsigned)lu_cdiv(k, 64));
+    LuProfScope prof(st, LU_K_PACK, 5.0 * rows * k, 0.0);
+    pack_rows_e4m3_kernel<<<grid, 256, 0, st>>>(A, lda, rows, k, rscale, (uint8_t*)out);
+    LU_CHECK_LAUNCH();
+    return LU_SUCCESS;
+}
+
+int lu_launch_pack_cols_e4m3(cudaStream_t st, const float* B, int64_t ldb, int64_t cols, int k, float* cscale,
+                             void* out) {
+    if (cols <= 0 || k <= 0) return LU_SUCCESS;
+    LuProfScope prof(st, LU_K_PACK, 5.0 * cols * k, 0.0);
+    pack_cols_e4m3_kernel<<<(unsigned)lu_cdiv(cols, 8), 256, 0, st>>>(B, ldb, cols, k, cscale, (uint8_t*)out);
+    LU_CHECK_LAUNCH();
+    return LU_SUCCESS;
+}
 
 int lu_launch_pack_rows(cudaStream_t st, int fmt, const float* A, int64_t lda, int64_t rows, int k, void* out) {
     if (rows <= 0 || k <= 0) return LU_SUCCESS;

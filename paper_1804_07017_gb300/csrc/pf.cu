@@ -254,7 +254,7 @@ int panel_rec(lu_context* c, cudaStream_t st, T* A, int64_t lda, int64_t M, int6
             size_t smem = 0;
             if (lu_pf_cluster_shape<T>(rows, (int)width, c->pf_smem_budget, &C, &R, &smem))
                 return lu_launch_pf_leaf_cluster<T>(st, A + j0 + j0 * lda, lda, rows, (int)width, C, R, smem, j0 - pc0,
-                                                    pc0 + pw - (j0 + width), ipiv + j0, j0, &c->sync[0].info);
+                                                    pc0 + pw - (j0 + width), ipiv + j0, j0, &c->sync[0]);
             return LU_ERR_UNSUPPORTED;
         }
         return lu_launch_pf_leaf<T>(c, st, A + j0 + j0 * lda, lda, rows, (int)width, ipiv + j0, j0, o.pf_ctas);

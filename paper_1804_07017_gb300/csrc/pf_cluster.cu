@@ -20,6 +20,8 @@
 #include <cooperative_groups.h>
 
 #include <climits>
+#include <cstdio>
+#include <cstdlib>
 
 #include "internal.h"
 #include "profile.h"
@@ -46,164 +48,179 @@ struct Slot {
     T jrow[2][LU_PF_MAX_LEAF];
 };
 
+// Warp-wide first-maximum reduction of (value, row, source) triples.
 template <typename T>
-__global__ void __launch_bounds__(kNT) pf_leaf_cluster_kernel(T* __restrict__ A, int64_t lda, int m, int w, int R,
-                                                              int left_cols, int right_cols,
-                                                              int32_t* __restrict__ ipiv, int ipiv_add,
-                                                              int* __restrict__ info) {
+__device__ __forceinline__ void warp_best(T& v, int& i, int& q) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const T ov = __shfl_xor_sync(0xffffffffu, v, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, i, o);
+        const int oq = __shfl_xor_sync(0xffffffffu, q, o);
+        if (ov > v || (ov == v && oi < i)) {
+            v = ov;
+            i = oi;
+            q = oq;
+        }
+    }
+}
+
+// W: compiled leaf width (so every per-row update is straight-line code); the
+// leaf factors its first w <= W columns.  RQ: rows per thread (thread t owns
+// rows t + kNT*q of its CTA's block).
+// The block is row-major in shared memory with a padded stride W+1.
+template <typename T, int W, int RQ>
+__global__ void __launch_bounds__(kNT) pf_leaf_cluster_kernel(T* __restrict__ A, int64_t lda, int m, int w,
+                                                              int left_cols, int right_cols, int32_t* __restrict__ ipiv,
+                                                              int ipiv_add, LuSync* __restrict__ sync) {
+    int* info = &sync->info;
+    constexpr int R = kNT * RQ;
+    constexpr int WP = W + 1;
     cg::cluster_group cluster = cg::this_cluster();
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T* sA = reinterpret_cast<T*>(smem_raw);                        // [w][R]
-    Slot<T>* slot = reinterpret_cast<Slot<T>*>(sA + (size_t)w * R);  // this CTA's exchange slot
-    T* cand_rows = reinterpret_cast<T*>(slot + 1);                  // [C][w] candidates read back
-    T* prow = cand_rows + (size_t)LU_PF_MAX_CTAS_CLUSTER * w;        // pivot row
-    T* jrowv = prow + w;                                            // row jj before the swap
+    T* sA = reinterpret_cast<T*>(smem_raw);                       // [R][WP]
+    Slot<T>* slot = reinterpret_cast<Slot<T>*>(sA + (size_t)R * WP);
     __shared__ T red_v[kNT / 32];
     __shared__ int red_i[kNT / 32];
-    __shared__ T s_cv[LU_PF_MAX_CTAS_CLUSTER];
-    __shared__ int s_ci[LU_PF_MAX_CTAS_CLUSTER];
-    __shared__ int sh_bi, sh_p, sh_gw;
-    __shared__ T sh_bv;
-    __shared__ int s_piv[LU_PF_MAX_LEAF];
-    // interchange plan for the other panel columns
-    __shared__ int s_dst[2 * LU_PF_MAX_LEAF], s_src[2 * LU_PF_MAX_LEAF], s_cnt;
+    __shared__ int s_piv[W];
+    __shared__ int s_dst[2 * W], s_src[2 * W], s_cnt;
+    __shared__ int s_ok;
 
     const int C = (int)cluster.num_blocks();
     const int g = (int)cluster.block_rank();
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int row0 = g * R;
     const int nrows = max(0, min(R, m - row0));
+    // the cluster's CTAs synchronise through the bounded grid barrier on sync
+    unsigned int phase = 0;
 
-    for (int c = 0; c < w; ++c)
-        for (int r = tid; r < nrows; r += kNT) sA[c * R + r] = A[(int64_t)(row0 + r) + (int64_t)c * lda];
+    for (int c = 0; c < W; ++c)
+#pragma unroll
+        for (int q = 0; q < RQ; ++q) {
+            const int r = tid + kNT * q;
+            if (r < nrows) sA[r * WP + c] = (c < w) ? A[(int64_t)(row0 + r) + (int64_t)c * lda] : T(0);
+        }
     __syncthreads();
 
+    // local candidate of column 0
     T bv = T(-1);
     int bi = INT_MAX;
-    for (int r = tid; r < nrows; r += kNT) cmerge(bv, bi, (T)fabs(sA[r]), row0 + r);
-
-    for (int jj = 0; jj < w; ++jj) {
-        const int buf = jj & 1;
-        // ---- local candidate ----
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            T ov = __shfl_xor_sync(0xffffffffu, bv, o);
-            int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-            cmerge(bv, bi, ov, oi);
-        }
+    for (int q = 0; q < RQ; ++q) {
+        const int r = tid + kNT * q;
+        if (r < nrows) cmerge(bv, bi, (T)fabs(sA[r * WP]), row0 + r);
+    }
+
+    // block reduction + publish of column jj's candidate into slot[jj & 1]
+    auto publish = [&](int jj) {
+        int dummy = 0;
+        warp_best(bv, bi, dummy);
         if (lane == 0) {
             red_v[warp] = bv;
             red_i[warp] = bi;
         }
         __syncthreads();
-        if (warp == 0) {
-            T v = (lane < kNT / 32) ? red_v[lane] : T(-1);
-            int i = (lane < kNT / 32) ? red_i[lane] : INT_MAX;
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                T ov = __shfl_xor_sync(0xffffffffu, v, o);
-                int oi = __shfl_xor_sync(0xffffffffu, i, o);
-                cmerge(v, i, ov, oi);
-            }
-            if (lane == 0) {
-                sh_bv = v;
-                sh_bi = i;
-            }
-        }
-        __syncthreads();
-        // ---- publish into this CTA's slot ----
-        const int my_bi = sh_bi;
+        T v = (lane < kNT / 32) ? red_v[lane] : T(-1);
+        int i = (lane < kNT / 32) ? red_i[lane] : INT_MAX;
+        warp_best(v, i, dummy);
+        const int buf = jj & 1;
         if (tid == 0) {
-            slot->val[buf] = sh_bv;
-            slot->idx[buf] = my_bi;
+            slot->val[buf] = v;
+            slot->idx[buf] = i;
         }
-        if (tid < w) {
-            if (my_bi != INT_MAX) slot->row[buf][tid] = sA[tid * R + (my_bi - row0)];
-            if (jj >= row0 && jj < row0 + nrows) slot->jrow[buf][tid] = sA[tid * R + (jj - row0)];
+        // the candidate row and row jj are copied by the warp that owns them
+        if (i != INT_MAX) {
+            const int lr = i - row0;
+            if (warp == (lr % kNT) >> 5)
+                for (int c = lane; c < W; c += 32) slot->row[buf][c] = sA[lr * WP + c];
         }
-        cluster.sync();
-        // ---- read every CTA's candidate and row jj ----
-        for (int q = tid; q < C; q += kNT) {
-            const Slot<T>* rs = cluster.map_shared_rank(slot, q);
-            s_cv[q] = rs->val[buf];
-            s_ci[q] = rs->idx[buf];
+        if (jj >= row0 && jj < row0 + nrows) {
+            const int lr = jj - row0;
+            if (warp == (lr % kNT) >> 5)
+                for (int c = lane; c < W; c += 32) slot->jrow[buf][c] = sA[lr * WP + c];
         }
-        for (int e = tid; e < C * w; e += kNT) {
-            const int q = e / w, c = e - q * w;
-            const Slot<T>* rs = cluster.map_shared_rank(slot, q);
-            cand_rows[e] = rs->row[buf][c];
+        return lu_grid_barrier(sync, (++phase) * (unsigned)C, &s_ok);
+    };
+
+    bool ok = publish(0);
+    for (int jj = 0; jj < w && ok; ++jj) {
+        const int buf = jj & 1;
+        // ---- every warp selects the pivot from the C published candidates ----
+        T cv = T(-1);
+        int ci = INT_MAX, cq = -1;
+        if (lane < C) {
+            const Slot<T>* rs = cluster.map_shared_rank(slot, lane);
+            cv = rs->val[buf];
+            ci = rs->idx[buf];
+            cq = (ci == INT_MAX) ? -1 : lane;
+            if (ci == INT_MAX) cv = T(-1);
         }
-        if (tid < w) {
-            const int owner = jj / R;
-            const Slot<T>* rs = cluster.map_shared_rank(slot, owner);
-            jrowv[tid] = rs->jrow[buf][tid];
+        warp_best(cv, ci, cq);
+        const int p = (ci == INT_MAX) ? jj : ci;
+        // lane c holds element c of the pivot row and of row jj (W <= 32 lanes)
+        T pr = T(0), jr = T(0);
+        if (lane < W) {
+            const Slot<T>* ro = cluster.map_shared_rank(slot, jj / R);
+            jr = ro->jrow[buf][lane];
+            pr = (cq >= 0) ? cluster.map_shared_rank(slot, cq)->row[buf][lane] : jr;
         }
-        __syncthreads();
-        if (warp == 0) {
-            T v = T(-1);
-            int i = INT_MAX, qb = -1;
-            for (int q = lane; q < C; q += 32) {
-                if (s_ci[q] != INT_MAX && (s_cv[q] > v || (s_cv[q] == v && s_ci[q] < i))) {
-                    v = s_cv[q];
-                    i = s_ci[q];
-                    qb = q;
-                }
-            }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                T ov = __shfl_xor_sync(0xffffffffu, v, o);
-                int oi = __shfl_xor_sync(0xffffffffu, i, o);
-                int oq = __shfl_xor_sync(0xffffffffu, qb, o);
-                if (ov > v || (ov == v && oi < i)) {
-                    v = ov;
-                    i = oi;
-                    qb = oq;
-                }
-            }
-            if (lane == 0) {
-                sh_p = (i == INT_MAX) ? jj : i;
-                sh_gw = (i == INT_MAX) ? -1 : qb;
-            }
-        }
-        __syncthreads();
-        const int p = sh_p, gw = sh_gw;
-        if (tid < w) prow[tid] = (gw >= 0) ? cand_rows[gw * w + tid] : jrowv[tid];
         if (tid == 0) {
             s_piv[jj] = p;
             if (g == 0) ipiv[jj] = p + 1 + ipiv_add;
         }
-        __syncthreads();
-        if (p != jj && tid < w) {
-            if (p >= row0 && p < row0 + nrows) sA[tid * R + (p - row0)] = jrowv[tid];
-            if (jj >= row0 && jj < row0 + nrows) sA[tid * R + (jj - row0)] = prow[tid];
+        // ---- interchange rows jj and p inside this CTA's block ----
+        if (p != jj) {
+            if (p >= row0 && p < row0 + nrows) {
+                const int lr = p - row0;
+                if (warp == (lr % kNT) >> 5 && lane < W) sA[lr * WP + lane] = jr;
+            }
+            if (jj >= row0 && jj < row0 + nrows) {
+                const int lr = jj - row0;
+                if (warp == (lr % kNT) >> 5 && lane < W) sA[lr * WP + lane] = pr;
+            }
         }
-        const T piv = prow[jj];
+        __syncwarp();
+        T prv[W];
+#pragma unroll
+        for (int c = 0; c < W; ++c) prv[c] = __shfl_sync(0xffffffffu, pr, c);
+        const T piv = __shfl_sync(0xffffffffu, pr, jj);
         if (piv == T(0) && g == 0 && tid == 0) atomicCAS(info, 0, jj + 1 + ipiv_add);
-        __syncthreads();
+        // ---- scale column jj, rank-1 update, next column's local candidate ----
         bv = T(-1);
         bi = INT_MAX;
-        const bool has_next = jj + 1 < w;
-        for (int r = tid; r < nrows; r += kNT) {
+#pragma unroll
+        for (int q = 0; q < RQ; ++q) {
+            const int r = tid + kNT * q;
             const int gr = row0 + r;
-            if (gr <= jj) continue;
-            if (piv != T(0)) {
-                const T l = sA[jj * R + r] / piv;
-                sA[jj * R + r] = l;
-                for (int c = jj + 1; c < w; ++c) sA[c * R + r] = fma(-l, prow[c], sA[c * R + r]);
+            if (r < nrows && gr > jj) {
+                T* rowp = sA + r * WP;
+                if (piv != T(0)) {
+                    const T l = rowp[jj] / piv;
+                    rowp[jj] = l;
+#pragma unroll
+                    for (int c = 0; c < W; ++c)
+                        if (c > jj) rowp[c] = fma(-l, prv[c], rowp[c]);
+                }
+                if (jj + 1 < w) cmerge(bv, bi, (T)fabs(rowp[jj + 1]), gr);
             }
-            if (has_next) cmerge(bv, bi, (T)fabs(sA[(jj + 1) * R + r]), gr);
         }
+        if (jj + 1 < w) ok = publish(jj + 1);
     }
-    // every CTA is done reading the other CTAs' slots before any CTA may exit
-    cluster.sync();
+    // no CTA leaves while another may still read its slot
+    if (ok) ok = lu_grid_barrier(sync, (++phase) * (unsigned)C, &s_ok);
+    lu_grid_exit(sync);
+    if (!ok) return;
     for (int c = 0; c < w; ++c)
-        for (int r = tid; r < nrows; r += kNT) A[(int64_t)(row0 + r) + (int64_t)c * lda] = sA[c * R + r];
+#pragma unroll
+        for (int q = 0; q < RQ; ++q) {
+            const int r = tid + kNT * q;
+            if (r < nrows) A[(int64_t)(row0 + r) + (int64_t)c * lda] = sA[r * WP + c];
+        }
     const int other = left_cols + right_cols;
     if (other <= 0) return;
     // ---- the leaf's interchanges on the other columns of the panel ----
-    // Plan: positions 0..w-1 (leaf rows) and the distinct targets below them.
+    // Plan: positions 0..W-1 (leaf rows) and the distinct targets below them.
     if (tid == 0) {
-        int tgt[LU_PF_MAX_LEAF], cur[2 * LU_PF_MAX_LEAF];
+        int tgt[W], cur[2 * W];
         int nt = 0;
         for (int i = 0; i < w; ++i) cur[i] = i;
         for (int k = 0; k < w; ++k) {
@@ -249,24 +266,39 @@ __global__ void __launch_bounds__(kNT) pf_leaf_cluster_kernel(T* __restrict__ A,
     for (int q = g * (kNT / 32) + warp; q < other; q += C * (kNT / 32)) {
         const int64_t col = (q < left_cols) ? (int64_t)q - left_cols : (int64_t)w + (q - left_cols);
         T* a = A + col * lda;
-        T v[(2 * LU_PF_MAX_LEAF) / 32];
+        T v[(2 * W + 31) / 32];
 #pragma unroll
-        for (int t = 0; t < (2 * LU_PF_MAX_LEAF) / 32; ++t)
+        for (int t = 0; t < (2 * W + 31) / 32; ++t)
             if (lane + 32 * t < cnt) v[t] = a[s_src[lane + 32 * t]];
         __syncwarp();
 #pragma unroll
-        for (int t = 0; t < (2 * LU_PF_MAX_LEAF) / 32; ++t)
+        for (int t = 0; t < (2 * W + 31) / 32; ++t)
             if (lane + 32 * t < cnt) a[s_dst[lane + 32 * t]] = v[t];
     }
 }
 
-size_t cluster_smem(int w, int R, int esize) {
-    const size_t slot = esize == 8 ? sizeof(Slot<double>) : sizeof(Slot<float>);
-    return (size_t)w * R * esize + slot + (size_t)LU_PF_MAX_CTAS_CLUSTER * w * esize + 2 * (size_t)w * esize + 16;
+template <typename T>
+size_t cluster_smem(int w, int rq) {
+    return (size_t)kNT * rq * (w + 1) * sizeof(T) + sizeof(Slot<T>) + 16;
 }
 
+
 template <typename T>
-int max_clusters_for(int C, size_t smem) {
+struct LeafTable {
+    typedef void (*Fn)(T*, int64_t, int, int, int, int, int32_t*, int, LuSync*);
+    static Fn get(int w, int rq) {
+#define LU_LEAF_CASE(WW, RR) \
+    if (w == WW && rq == RR) return pf_leaf_cluster_kernel<T, WW, RR>;
+        LU_LEAF_CASE(8, 1) LU_LEAF_CASE(8, 2) LU_LEAF_CASE(8, 4) LU_LEAF_CASE(8, 8)
+        LU_LEAF_CASE(16, 1) LU_LEAF_CASE(16, 2) LU_LEAF_CASE(16, 4) LU_LEAF_CASE(16, 8)
+        LU_LEAF_CASE(32, 1) LU_LEAF_CASE(32, 2) LU_LEAF_CASE(32, 4)
+#undef LU_LEAF_CASE
+        return nullptr;
+    }
+};
+
+template <typename T>
+int max_clusters_for(typename LeafTable<T>::Fn fn, int C, size_t smem) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(C, 1, 1);
     cfg.blockDim = dim3(kNT, 1, 1);
@@ -279,7 +311,7 @@ int max_clusters_for(int C, size_t smem) {
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     int num = 0;
-    if (cudaOccupancyMaxActiveClusters(&num, pf_leaf_cluster_kernel<T>, &cfg) != cudaSuccess) {
+    if (cudaOccupancyMaxActiveClusters(&num, fn, &cfg) != cudaSuccess) {
         cudaGetLastError();
         return 0;
     }
@@ -294,15 +326,20 @@ static int cluster_limit() {
     static int lim[2] = {-1, -1};
     const int ti = sizeof(T) == 8 ? 0 : 1;
     if (lim[ti] >= 0) return lim[ti];
+    const int ws[3] = {8, 16, 32}, rqs[4] = {1, 2, 4, 8};
+    for (int w : ws)
+        for (int rq : rqs) {
+            auto fn = LeafTable<T>::get(w, rq);
+            if (!fn) continue;
+            if (cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)
+                cudaGetLastError();
+            if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024) != cudaSuccess)
+                cudaGetLastError();
+        }
     int best = 0;
-    if (cudaFuncSetAttribute(pf_leaf_cluster_kernel<T>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
-        cudaSuccess)
-        cudaGetLastError();
-    if (cudaFuncSetAttribute(pf_leaf_cluster_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024) !=
-        cudaSuccess)
-        cudaGetLastError();
+    auto fn = LeafTable<T>::get(16, 1);
     for (int C = LU_PF_MAX_CTAS_CLUSTER; C >= 1; C >>= 1) {
-        if (max_clusters_for<T>(C, 64 * 1024) > 0) {
+        if (max_clusters_for<T>(fn, C, cluster_smem<T>(16, 1)) > 0) {
             best = C;
             break;
         }
@@ -311,28 +348,40 @@ static int cluster_limit() {
     return best;
 }
 
-// Shape of a cluster leaf: C CTAs of R rows (a multiple of 32) within the budget.
+// Shape of a cluster leaf: C CTAs of kNT*rq rows within the shared-memory budget,
+// w one of the compiled widths (8, 16, 32).
+static int compiled_width(int w) { return w <= 8 ? 8 : (w <= 16 ? 16 : (w <= 32 ? 32 : 0)); }
+
 template <typename T>
 bool lu_pf_cluster_shape(int64_t m, int w, size_t budget, int* C_out, int* R_out, size_t* smem_out) {
+    w = compiled_width(w);
+    if (w == 0) return false;
     const int cmax = cluster_limit<T>();
-    if (cmax <= 0 || w > LU_PF_MAX_LEAF) return false;
-    for (int C = 1; C <= cmax; C <<= 1) {
-        const int64_t R = std::max<int64_t>(32, lu_cdiv(lu_cdiv(m, C), 32) * 32);
-        const size_t smem = cluster_smem(w, (int)R, (int)sizeof(T));
-        // prefer few CTAs, but not so few that one CTA's update work dominates the barrier
-        if (smem <= budget && (R <= 1024 || C == cmax)) {
-            *C_out = C;
-            *R_out = (int)R;
-            *smem_out = smem;
-            return true;
-        }
+    if (cmax <= 0) return false;
+    const int rqs[4] = {1, 2, 4, 8};
+    for (int rq : rqs) {
+        if (!LeafTable<T>::get(w, rq)) continue;
+        const int64_t R = (int64_t)kNT * rq;
+        const int64_t C = lu_cdiv(m, R);
+        if (C > cmax) continue;
+        const size_t smem = cluster_smem<T>(w, rq);
+        if (smem > budget) return false;
+        int Cp = 1;
+        while (Cp < C) Cp <<= 1;  // power-of-two cluster sizes
+        if (Cp > cmax) continue;
+        *C_out = Cp;
+        *R_out = (int)R;
+        *smem_out = smem;
+        return true;
     }
     return false;
 }
 
 template <typename T>
 int lu_launch_pf_leaf_cluster(cudaStream_t st, T* A, int64_t lda, int64_t m, int w, int C, int R, size_t smem,
-                              int64_t left_cols, int64_t right_cols, int32_t* ipiv, int64_t ipiv_add, int* info) {
+                              int64_t left_cols, int64_t right_cols, int32_t* ipiv, int64_t ipiv_add, LuSync* sync) {
+    auto fn = LeafTable<T>::get(compiled_width(w), R / kNT);
+    if (!fn) return LU_ERR_UNSUPPORTED;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(C, 1, 1);
     cfg.blockDim = dim3(kNT, 1, 1);
@@ -347,8 +396,11 @@ int lu_launch_pf_leaf_cluster(cudaStream_t st, T* A, int64_t lda, int64_t m, int
     cfg.numAttrs = 1;
     LuProfScope prof(st, LU_K_PANEL, 2.0 * m * w * sizeof(T) + 4.0 * w * (left_cols + right_cols) * sizeof(T),
                      (double)m * w * w);
-    LU_CHECK_CUDA(cudaLaunchKernelEx(&cfg, pf_leaf_cluster_kernel<T>, A, lda, (int)m, w, R, (int)left_cols,
-                                     (int)right_cols, ipiv, (int)ipiv_add, info));
+    if (getenv("LU_GB300_TRACE_LAUNCH"))
+        fprintf(stderr, "[lu launch] cluster leaf esize %d m %lld w %d C %d R %d smem %zu left %lld right %lld\n",
+                (int)sizeof(T), (long long)m, w, C, R, smem, (long long)left_cols, (long long)right_cols);
+    LU_CHECK_CUDA(cudaLaunchKernelEx(&cfg, fn, A, lda, (int)m, w, (int)left_cols, (int)right_cols, ipiv,
+                                     (int)ipiv_add, sync));
     lu_count_launch();
     return LU_SUCCESS;
 }
@@ -356,6 +408,6 @@ int lu_launch_pf_leaf_cluster(cudaStream_t st, T* A, int64_t lda, int64_t m, int
 template bool lu_pf_cluster_shape<double>(int64_t, int, size_t, int*, int*, size_t*);
 template bool lu_pf_cluster_shape<float>(int64_t, int, size_t, int*, int*, size_t*);
 template int lu_launch_pf_leaf_cluster<double>(cudaStream_t, double*, int64_t, int64_t, int, int, int, size_t, int64_t,
-                                               int64_t, int32_t*, int64_t, int*);
+                                               int64_t, int32_t*, int64_t, LuSync*);
 template int lu_launch_pf_leaf_cluster<float>(cudaStream_t, float*, int64_t, int64_t, int, int, int, size_t, int64_t,
-                                              int64_t, int32_t*, int64_t, int*);
+                                              int64_t, int32_t*, int64_t, LuSync*);

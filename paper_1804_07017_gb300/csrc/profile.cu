@@ -3,6 +3,9 @@
 // with its kernel class and its algorithmic bytes and flops.  lu_profile_read
 // synchronises, turns the event pairs into durations and aggregates them per
 // class.  Off by default; costs two event records per launch when on.
+#include <stdio.h>
+#include <stdlib.h>
+
 #include <mutex>
 #include <vector>
 
@@ -63,7 +66,20 @@ void drain_locked() {
 
 }  // namespace
 
+static int trace_launches() {
+    static int t = -1;
+    if (t < 0) {
+        const char* e = getenv("LU_GB300_TRACE_LAUNCH");
+        t = (e && e[0] == '1') ? 1 : 0;
+    }
+    return t;
+}
+
 LuProfScope::LuProfScope(cudaStream_t st, int cls, double bytes, double flops) : st_(st) {
+    if (trace_launches()) {
+        fprintf(stderr, "[lu launch] class %d bytes %.0f flops %.0f\n", cls, bytes, flops);
+        fflush(stderr);
+    }
     if (!(g_mask & (1u << cls))) return;
     std::lock_guard<std::mutex> lk(g_mu);
     if (!(g_mask & (1u << cls))) return;

@@ -12,7 +12,10 @@
 //                    wait), solves its diagonal block in shared memory and
 //                    publishes.  Tickets make the wait graph acyclic whatever
 //                    the CTA scheduling order.
+#include <cudaTypedefs.h>
+
 #include "internal.h"
+#include "ptx.cuh"
 #include "profile.h"
 
 namespace {
@@ -72,19 +75,30 @@ template <typename T>
 struct TrsvCfg {
     static constexpr int BS = sizeof(T) == 4 ? 128 : 64;  // rows per block
     static constexpr int kSplit = kTrsvThreads / BS;      // threads sharing one row of a source block
+    static constexpr int kTile = BS * BS;                 // elements of one staged tile
+    // diagonal tile + two off-diagonal tiles (column-major, dense), rhs block, partial sums,
+    // mbarriers and 1 KB of alignment slack
+    static constexpr size_t smem = sizeof(T) * (3 * (size_t)kTile + 2 * (size_t)kNR * BS) + 64 + 1024;
+};
+
+template <typename T>
+struct TrsvPlainCfg {
+    static constexpr int BS = sizeof(T) == 4 ? 128 : 64;  // rows per block
+    static constexpr int kSplit = kTrsvThreads / BS;      // threads sharing one row of a source block
     static constexpr size_t smem = sizeof(T) * ((size_t)BS * (BS + 1) + 2 * (size_t)kNR * BS);
 };
 
-// One CTA per BS-row block, taken in dependency order from an atomic ticket.
-// The diagonal block is staged in shared memory before the CTA waits for its
+// Fallback for factors whose leading dimension TMA cannot address (not a
+// multiple of 16 bytes).  One CTA per BS-row block, taken in dependency order
+// from an atomic ticket.  The diagonal block is staged in shared memory before the CTA waits for its
 // predecessors, so the critical path per block is: observe the predecessor's
 // "done" count, add that block's contribution, run the register-resident
 // substitution of the diagonal block, publish.
 template <typename T, bool LOWER>
 __global__ void __launch_bounds__(kTrsvThreads)
-    trsv_blocked_kernel(int64_t n, int nrhs, const T* __restrict__ LU, int64_t lda, T* __restrict__ X,
+    trsv_plain_kernel(int64_t n, int nrhs, const T* __restrict__ LU, int64_t lda, T* __restrict__ X,
                         int64_t ldx, LuSync* __restrict__ sync) {
-    using C = TrsvCfg<T>;
+    using C = TrsvPlainCfg<T>;
     constexpr int BS = C::BS;
     extern __shared__ __align__(16) unsigned char smraw[];
     T* sD = reinterpret_cast<T*>(smraw);   // [BS][BS+1], sD[i*(BS+1) + j] = LU(r0+i, r0+j)
@@ -222,6 +236,201 @@ __global__ void __launch_bounds__(kTrsvThreads)
     if (tid == 0) lu_st_release(&sync->arrive, (unsigned)(chain + 1));
 }
 
+// One CTA per BS-row block, taken in dependency order from an atomic ticket.
+// The diagonal tile and the off-diagonal tiles L(blk, I) are brought into
+// shared memory by TMA (2-D tiled cp.async.bulk.tensor, double-buffered, one
+// tile ahead of use), so the critical path per block is: observe the
+// predecessor's "done" count, read its solution block (L2), add its
+// contribution from shared memory, run the register-resident substitution of
+// the diagonal block, publish.
+template <typename T, bool LOWER>
+__global__ void __launch_bounds__(kTrsvThreads)
+    trsv_tma_kernel(const __grid_constant__ CUtensorMap tmL, int64_t n, int nrhs, T* __restrict__ X, int64_t ldx,
+                    LuSync* __restrict__ sync) {
+    using C = TrsvCfg<T>;
+    constexpr int BS = C::BS;
+    extern __shared__ unsigned char smraw[];
+    unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~uintptr_t(1023));
+    T* sD = reinterpret_cast<T*>(base);           // [BS cols][BS rows] diagonal tile
+    T* sT = sD + C::kTile;                        // two off-diagonal tiles
+    T* sX = sT + 2 * C::kTile;                    // [kNR][BS]
+    T* sPart = sX + kNR * BS;                     // [kNR][BS]
+    uint64_t* bars = reinterpret_cast<uint64_t*>(sPart + kNR * BS);  // [0] diag, [1],[2] tiles
+    __shared__ int s_chain, s_ready, s_flag;
+    __shared__ volatile int s_abort;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int nblk = (int)((n + BS - 1) / BS);
+    const uint32_t tile_bytes = (uint32_t)(C::kTile * sizeof(T));
+    if (tid == 0) {
+        s_chain = (int)atomicAdd(&sync->ticket, 1u);
+        s_abort = 0;
+        for (int b = 0; b < 3; ++b) mbar_init(&bars[b], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    __syncthreads();
+    const int chain = s_chain;  // position in dependency order
+    const int blk = LOWER ? chain : nblk - 1 - chain;
+    const int64_t r0 = (int64_t)blk * BS;
+    const int rows = (int)min((int64_t)BS, n - r0);
+    auto src_block = [&](int q) { return LOWER ? q : nblk - 1 - q; };
+    if (tid == 0) {
+        mbar_arrive_expect_tx(&bars[0], tile_bytes);
+        tma_load_2d(sD, &tmL, &bars[0], (int)r0, (int)r0);
+        if (chain > 0) {
+            mbar_arrive_expect_tx(&bars[1], tile_bytes);
+            tma_load_2d(sT, &tmL, &bars[1], (int)r0, src_block(0) * BS);
+        }
+    }
+    const int r = tid % BS, h = tid / BS;
+    T acc[kNR];
+#pragma unroll
+    for (int c = 0; c < kNR; ++c) acc[c] = T(0);
+
+    int processed = 0;
+    int issued = chain > 0 ? 1 : 0;  // off-diagonal tiles requested so far (uniform across the CTA)
+    int consumed = 0;                // tiles whose arrival was observed
+    bool ok = true;
+    while (processed < chain) {
+        if (tid == 0) {
+            unsigned v;
+            uint64_t t0 = 0;
+            unsigned spins = 0;
+            int flag = 1;
+            while ((int)(v = lu_ld_acquire(&sync->arrive)) <= processed) {
+                if (((++spins) & 255u) == 0) {
+                    if (lu_ld_acquire_s32(&sync->error) != 0) { flag = 0; break; }
+                    uint64_t t = lu_globaltimer();
+                    if (t0 == 0) t0 = t;
+                    else if (t - t0 > LU_WAIT_NS) {
+                        atomicExch(&sync->error, LU_ERR_TIMEOUT);
+                        flag = 0;
+                        break;
+                    }
+                }
+            }
+            s_ready = (int)v;
+            s_flag = flag;
+        }
+        __syncthreads();
+        if (!s_flag) { ok = false; break; }
+        const int ready = min(s_ready, chain);
+        for (int q = processed; q < ready; ++q) {
+            // prefetch the next tile into the other buffer (its previous tile was consumed)
+            if (q + 1 < chain) issued = q + 2;
+            if (tid == 0 && q + 1 < chain) {
+                const int nb = (q + 1) & 1;
+                mbar_arrive_expect_tx(&bars[1 + nb], tile_bytes);
+                tma_load_2d(sT + nb * C::kTile, &tmL, &bars[1 + nb], (int)r0, src_block(q + 1) * BS);
+            }
+            const int I = src_block(q);
+            const int64_t c0 = (int64_t)I * BS;
+            const int cols = (int)min((int64_t)BS, n - c0);
+            for (int e = tid; e < kNR * BS; e += kTrsvThreads) {
+                const int c = e / BS, j = e % BS;
+                sX[e] = (c < nrhs && j < cols) ? __ldcg(&X[(c0 + j) + c * ldx]) : T(0);
+            }
+            if (!mbar_wait(&bars[1 + (q & 1)], (q >> 1) & 1, &s_abort)) { ok = false; }
+            __syncthreads();
+            if (!ok || s_abort) { ok = false; break; }
+            consumed = q + 1;
+            const T* tile = sT + (q & 1) * C::kTile;
+            if (nrhs == 1) {
+#pragma unroll 8
+                for (int j = h; j < BS; j += C::kSplit) acc[0] = fma(tile[j * BS + r], sX[j], acc[0]);
+            } else {
+                for (int j = h; j < BS; j += C::kSplit) {
+                    const T l = tile[j * BS + r];
+#pragma unroll
+                    for (int c = 0; c < kNR; ++c)
+                        if (c < nrhs) acc[c] = fma(l, sX[c * BS + j], acc[c]);
+                }
+            }
+            __syncthreads();
+        }
+        if (!ok) break;
+        processed = ready;
+    }
+    if (ok && !mbar_wait(&bars[0], 0, &s_abort)) ok = false;
+    __syncthreads();
+    if (!ok || s_abort) {
+        if (tid == 0) {
+            atomicExch(&sync->error, LU_ERR_TIMEOUT);
+            // drain (bounded) the tile copies this CTA issued, so none lands after it exits
+            for (int q = consumed; q < issued; ++q) {
+                const uint64_t t0 = lu_globaltimer();
+                while (!mbar_try_wait(&bars[1 + (q & 1)], (q >> 1) & 1))
+                    if (lu_globaltimer() - t0 > LU_MBAR_WAIT_NS) break;
+            }
+            const uint64_t t0 = lu_globaltimer();
+            while (!mbar_try_wait(&bars[0], 0))
+                if (lu_globaltimer() - t0 > LU_MBAR_WAIT_NS) break;
+        }
+        return;
+    }
+    // combine the kSplit partial sums: sX = rhs - contributions
+    for (int hh = 1; hh < C::kSplit; ++hh) {
+        if (h == hh) {
+#pragma unroll
+            for (int c = 0; c < kNR; ++c) sPart[c * BS + r] = (hh == 1 ? T(0) : sPart[c * BS + r]) + acc[c];
+        }
+        __syncthreads();
+    }
+    if (h == 0) {
+#pragma unroll
+        for (int c = 0; c < kNR; ++c)
+            sX[c * BS + r] = (r < rows && c < nrhs)
+                                 ? X[(r0 + r) + c * ldx] - (acc[c] + (C::kSplit > 1 ? sPart[c * BS + r] : T(0)))
+                                 : T(0);
+    }
+    __syncthreads();
+    // register-resident substitution of the diagonal block: lane holds rows lane + 32 q
+    constexpr int RQ = BS / 32;
+    for (int c = warp; c < nrhs; c += kTrsvThreads / 32) {
+        T v[RQ];
+#pragma unroll
+        for (int q = 0; q < RQ; ++q) v[q] = sX[c * BS + lane + 32 * q];
+        if (LOWER) {
+#pragma unroll
+            for (int q0 = 0; q0 < RQ; ++q0) {
+                for (int jj = 0; jj < 32; ++jj) {
+                    const int j = q0 * 32 + jj;
+                    const T xj = __shfl_sync(0xffffffffu, v[q0], jj);
+#pragma unroll
+                    for (int q = q0; q < RQ; ++q) {
+                        const int i = lane + 32 * q;
+                        if (i > j) v[q] = fma(-sD[j * BS + i], xj, v[q]);
+                    }
+                }
+            }
+        } else {
+#pragma unroll
+            for (int q0 = RQ - 1; q0 >= 0; --q0) {
+                for (int jj = 31; jj >= 0; --jj) {
+                    const int j = q0 * 32 + jj;
+                    if (lane == jj && j < rows) v[q0] = v[q0] / sD[j * BS + j];
+                    const T xj = __shfl_sync(0xffffffffu, v[q0], jj);
+#pragma unroll
+                    for (int q = 0; q <= q0; ++q) {
+                        const int i = lane + 32 * q;
+                        if (i < j) v[q] = fma(-sD[j * BS + i], xj, v[q]);
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < RQ; ++q) sX[c * BS + lane + 32 * q] = v[q];
+    }
+    __syncthreads();
+    for (int e = tid; e < rows * nrhs; e += kTrsvThreads) {
+        const int rr = e % rows, c = e / rows;
+        X[(r0 + rr) + c * ldx] = sX[c * BS + rr];
+    }
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) lu_st_release(&sync->arrive, (unsigned)(chain + 1));
+}
+
 __global__ void finish_info_kernel(const LuSync* __restrict__ s, int32_t* __restrict__ info) {
     const int e = s->error;
     info[0] = e != 0 ? e : s->info;
@@ -262,17 +471,79 @@ int lu_launch_permute_rows(cudaStream_t st, int64_t n, int64_t nrhs, const int32
 }
 
 template <typename T>
-int lu_launch_trsv_blocked(lu_context* c, cudaStream_t st, bool lower_unit, int64_t n, int64_t nrhs,
-                           const T* LU, int64_t lda, T* X, int64_t ldx) {
-    if (n <= 0 || nrhs <= 0) return LU_SUCCESS;
-    using C = TrsvCfg<T>;
+static int trsv_plain(lu_context* c, cudaStream_t st, bool lower_unit, int64_t n, int64_t nrhs, const T* LU,
+                      int64_t lda, T* X, int64_t ldx) {
+    using C = TrsvPlainCfg<T>;
     const int nblk = (int)lu_cdiv(n, C::BS);
     static bool attr[2] = {false, false};
     const int ti = sizeof(T) == 8 ? 0 : 1;
     if (!attr[ti]) {
-        LU_CHECK_CUDA(cudaFuncSetAttribute(trsv_blocked_kernel<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        LU_CHECK_CUDA(cudaFuncSetAttribute(trsv_plain_kernel<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            (int)C::smem));
-        LU_CHECK_CUDA(cudaFuncSetAttribute(trsv_blocked_kernel<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        LU_CHECK_CUDA(cudaFuncSetAttribute(trsv_plain_kernel<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)C::smem));
+        attr[ti] = true;
+    }
+    for (int64_t c0 = 0; c0 < nrhs; c0 += kNR) {
+        const int nr = (int)std::min<int64_t>(kNR, nrhs - c0);
+        LU_CHECK_CUDA(cudaMemsetAsync(&c->sync[1].arrive, 0, sizeof(unsigned) * 2, st));
+        LU_CHECK_CUDA(cudaMemsetAsync(&c->sync[1].ticket, 0, sizeof(unsigned), st));
+        LuProfScope prof(st, LU_K_SOLVE, sizeof(T) * (0.5 * n * n + 2.0 * n * nr), (double)n * n * nr);
+        if (lower_unit)
+            trsv_plain_kernel<T, true><<<nblk, kTrsvThreads, C::smem, st>>>(n, nr, LU, lda, X + c0 * ldx, ldx,
+                                                                            &c->sync[1]);
+        else
+            trsv_plain_kernel<T, false><<<nblk, kTrsvThreads, C::smem, st>>>(n, nr, LU, lda, X + c0 * ldx, ldx,
+                                                                             &c->sync[1]);
+        LU_CHECK_LAUNCH();
+    }
+    return LU_SUCCESS;
+}
+
+// 2-D tensor map over the n x n factor matrix (column-major: rows innermost),
+// one box = one BS x BS tile.
+template <typename T>
+static int make_factor_map(CUtensorMap* map, const T* LU, int64_t n, int64_t lda) {
+    static PFN_cuTensorMapEncodeTiled_v12000 enc = nullptr;
+    if (!enc) {
+        cudaDriverEntryPointQueryResult q;
+        void* fn = nullptr;
+        LU_CHECK_CUDA(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q));
+        if (q != cudaDriverEntryPointSuccess || !fn) return LU_ERR_CUDA;
+        enc = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    }
+    using C = TrsvCfg<T>;
+    cuuint64_t dims[2] = {(cuuint64_t)n, (cuuint64_t)n};
+    cuuint64_t strides[1] = {(cuuint64_t)(lda * sizeof(T))};
+    cuuint32_t box[2] = {(cuuint32_t)C::BS, (cuuint32_t)C::BS};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = enc(map, sizeof(T) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2,
+                     const_cast<T*>(LU), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                     CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        lu_set_error_string("cuTensorMapEncodeTiled failed (triangular solve)", __FILE__, __LINE__);
+        return LU_ERR_CUDA;
+    }
+    return LU_SUCCESS;
+}
+
+template <typename T>
+int lu_launch_trsv_blocked(lu_context* c, cudaStream_t st, bool lower_unit, int64_t n, int64_t nrhs, const T* LU,
+                           int64_t lda, T* X, int64_t ldx) {
+    if (n <= 0 || nrhs <= 0) return LU_SUCCESS;
+    using C = TrsvCfg<T>;
+    const int nblk = (int)lu_cdiv(n, C::BS);
+    // TMA needs a 16-byte aligned base and a leading dimension that is a multiple of 16 bytes
+    if ((reinterpret_cast<uintptr_t>(LU) & 15) != 0 || (lda * sizeof(T)) % 16 != 0)
+        return trsv_plain(c, st, lower_unit, n, nrhs, LU, lda, X, ldx);
+    CUtensorMap map;
+    LU_TRY(make_factor_map<T>(&map, LU, n, lda));
+    static bool attr[2] = {false, false};
+    const int ti = sizeof(T) == 8 ? 0 : 1;
+    if (!attr[ti]) {
+        LU_CHECK_CUDA(cudaFuncSetAttribute(trsv_tma_kernel<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)C::smem));
+        LU_CHECK_CUDA(cudaFuncSetAttribute(trsv_tma_kernel<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            (int)C::smem));
         attr[ti] = true;
     }
@@ -283,11 +554,9 @@ int lu_launch_trsv_blocked(lu_context* c, cudaStream_t st, bool lower_unit, int6
         LU_CHECK_CUDA(cudaMemsetAsync(&c->sync[1].ticket, 0, sizeof(unsigned), st));
         LuProfScope prof(st, LU_K_SOLVE, sizeof(T) * (0.5 * n * n + 2.0 * n * nr), (double)n * n * nr);
         if (lower_unit)
-            trsv_blocked_kernel<T, true><<<nblk, kTrsvThreads, C::smem, st>>>(n, nr, LU, lda, X + c0 * ldx, ldx,
-                                                                              &c->sync[1]);
+            trsv_tma_kernel<T, true><<<nblk, kTrsvThreads, C::smem, st>>>(map, n, nr, X + c0 * ldx, ldx, &c->sync[1]);
         else
-            trsv_blocked_kernel<T, false><<<nblk, kTrsvThreads, C::smem, st>>>(n, nr, LU, lda, X + c0 * ldx, ldx,
-                                                                               &c->sync[1]);
+            trsv_tma_kernel<T, false><<<nblk, kTrsvThreads, C::smem, st>>>(map, n, nr, X + c0 * ldx, ldx, &c->sync[1]);
         LU_CHECK_LAUNCH();
     }
     return LU_SUCCESS;

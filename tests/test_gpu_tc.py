@@ -55,12 +55,14 @@ def split_product(A, B):
     return Ah @ Bh + Ah @ Bl + Al @ Bh, np.abs(Ah) @ np.abs(Bh) + np.abs(Ah) @ np.abs(Bl) + np.abs(Al) @ np.abs(Bh)
 
 
-@pytest.mark.parametrize("prec_name", ["bf16", "fp16", "bf16x3", "bf16x6"])
+@pytest.mark.parametrize("prec_name", ["bf16", "fp16", "bf16x3", "bf16x6", "fp8"])
 @pytest.mark.parametrize("m,n,k", [(128, 256, 64), (256, 256, 64), (1000, 700, 256), (300, 5000, 64),
                                    (4097, 129, 512), (1, 1, 64), (129, 257, 128)])
 def test_tc_update(lu, prec_name, m, n, k):
     prec = {"bf16": lu.LU_TU_BF16, "fp16": lu.LU_TU_FP16, "bf16x3": lu.LU_TU_BF16X3,
-            "bf16x6": lu.LU_TU_BF16X6}[prec_name]
+            "bf16x6": lu.LU_TU_BF16X6, "fp8": lu.LU_TU_FP8}[prec_name]
+    if prec_name == "fp8" and k % 128:
+        pytest.skip("the e4m3 path takes k in multiples of 128")
     rnd = oracle.round_bf16 if prec_name == "bf16" else oracle.round_fp16
     g = synth.rng(31, m + n + k)
     C0, A0, B0 = (g.standard_normal(size=s).astype(np.float32).astype(np.float64)
@@ -72,6 +74,17 @@ def test_tc_update(lu, prec_name, m, n, k):
     assert int(info.item()) == 0
     got = C.cpu().double().numpy()
     u32 = np.finfo(np.float32).eps / 2
+    if prec_name == "fp8":
+        # power-of-two block scales (per row of A, per column of B), e4m3 values, FP32
+        # accumulation; the oracle's quantiser decides the same exponents exactly
+        Qa, sa = oracle.quant_e4m3_rows(A0)
+        Qb, tb = oracle.quant_e4m3_cols(B0)
+        Ad, Bd = Qa * sa[:, None], Qb * tb[None, :]
+        ref = C0 - Ad @ Bd
+        scale = np.abs(Ad) @ np.abs(Bd) + np.abs(C0)
+        err = np.abs(got - ref)
+        assert np.all(err <= (k + 2) * u32 * scale), (err / scale).max()
+        return
     if prec_name == "bf16x6":
         prod, aprod = split6_product(A0, B0)
         ref = C0 - prod

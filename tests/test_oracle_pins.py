@@ -327,3 +327,28 @@ def test_thread_count_does_not_change_results():
     r4 = oracle.getrf(A, nthreads=4)
     np.testing.assert_array_equal(r1[0], r4[0])
     np.testing.assert_array_equal(r1[1], r4[1])
+
+
+def test_e4m3_block_quantiser():
+    """Power-of-two block scaling: the scale is the smallest power of two that
+    brings the block maximum to <= 448 (so 224 < amax/s <= 448), the stored
+    values are e4m3-representable and equal torch's e4m3 conversion of X/s."""
+    g = synth.rng(15, 0)
+    X = g.standard_normal((40, 64)) * 10.0 ** g.uniform(-6, 6, size=(40, 1))
+    X[3] = 0.0
+    X[5, :] = 448.0 * 2.0 ** -7  # amax exactly a power-of-two multiple of 448: no extra halving
+    Q, s = oracle.quant_e4m3_rows(X)
+    amax = np.abs(X).max(axis=1)
+    nz = amax > 0
+    assert np.all(np.log2(s) == np.round(np.log2(s)))
+    assert np.all((amax[nz] / s[nz] <= 448.0) & (amax[nz] / s[nz] > 224.0))
+    assert s[3] == 1.0 and np.all(Q[3] == 0.0)
+    assert s[5] == 2.0 ** -7
+    np.testing.assert_array_equal(oracle.round_e4m3(Q), Q)
+    torch = pytest.importorskip("torch")
+    if hasattr(torch, "float8_e4m3fn"):
+        ref = torch.from_numpy((X / s[:, None]).astype(np.float32)).to(torch.float8_e4m3fn).double().numpy()
+        np.testing.assert_array_equal(Q, ref)
+    Qc, t = oracle.quant_e4m3_cols(X.T)
+    np.testing.assert_array_equal(Qc, Q.T)
+    np.testing.assert_array_equal(t, s)
