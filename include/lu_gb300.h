@@ -32,6 +32,7 @@
 #ifndef LU_GB300_H
 #define LU_GB300_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -213,6 +214,33 @@ int lu_gemm_update_ex(lu_handle handle, lu_dtype dtype, int64_t m, int64_t n, in
  */
 int lu_gemm_update_tc_ex(lu_handle handle, lu_prec prec, int64_t m, int64_t n, int64_t k, const float *A,
                          int64_t lda, const float *B, int64_t ldb, float *C, int64_t ldc, int32_t *info);
+
+/*
+ * lu_panel_factor_noalloc -- the panel factorization of lu_panel_factor_ex for
+ * callers that cannot allocate device memory: code running where cudaMalloc
+ * is unavailable or not allowed (a host callback, an allocator's own code
+ * path, a latency-critical loop that preallocated everything, a process whose
+ * device memory pool belongs to someone else).  The paper has no counterpart;
+ * it is an interface convenience.
+ *   dtype, m, w, A, lda, ipiv, opts, info   as in lu_panel_factor_ex
+ *   stream   cudaStream_t (as void*, NULL = legacy default) the work is queued on
+ * Allocates nothing: no cudaMalloc, cudaFree or allocating library call.  The
+ * scratch it needs (synchronisation counters, the panel leaf's exchange slots
+ * and one interchange plan) is a statically sized __device__ array inside the
+ * library, lu_noalloc_scratch_bytes() bytes (about 155 KB), held by every GPU
+ * that loads the library until the process exits.  The first call on a device
+ * looks up the array's device address (cudaGetSymbolAddress, with that device
+ * current): make it before any stream capture.  Every call on a device shares
+ * the array and finds the previous call's contents in it (the counters are
+ * cleared at the start of each call), so calls that overlap on the GPU race:
+ * serialise them.  Returns -i for an invalid argument, LU_ERR_UNSUPPORTED when
+ * w > 1024 (the plan the array holds covers at most 1024 interchanges) or the
+ * panel does not fit the leaf kernels, LU_ERR_CUDA, or 0 when enqueued.
+ */
+int lu_panel_factor_noalloc(lu_dtype dtype, int64_t m, int64_t w, void *A, int64_t lda, int32_t *ipiv,
+                            const lu_opts *opts, int32_t *info, void *stream);
+/* Size in bytes of the static scratch array used by lu_panel_factor_noalloc. */
+size_t lu_noalloc_scratch_bytes(void);
 
 /*
  * lu_selftest_wait_timeout -- diagnostic of the failure path shared by every

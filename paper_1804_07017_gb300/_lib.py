@@ -62,6 +62,8 @@ _SIGNATURES = {
     "lu_trsm_ex": (i32, [vp, i32, i64, i64, vp, i64, vp, i64]),
     "lu_gemm_update_ex": (i32, [vp, i32, i64, i64, i64, vp, i64, vp, i64, vp, i64]),
     "lu_gemm_update_tc_ex": (i32, [vp, i32, i64, i64, i64, vp, i64, vp, i64, vp, i64, vp]),
+    "lu_panel_factor_noalloc": (i32, [i32, i64, i64, vp, i64, vp, ctypes.POINTER(LuOpts), vp, vp]),
+    "lu_noalloc_scratch_bytes": (ctypes.c_size_t, []),
     "lu_selftest_wait_timeout": (i32, [vp, i64, vp]),
     "lu_profile_enable": (i32, [i32]),
     "lu_profile_reset": (i32, []),

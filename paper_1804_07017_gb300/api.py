@@ -189,3 +189,15 @@ def lu_gesv_mixed(A: torch.Tensor, B: torch.Tensor, X: torch.Tensor, prec: int, 
     if rc != 0 and rc != LU_WARN_NOT_CONVERGED:
         _check("lu_gesv_mixed", rc)
     return rc, iters.value, eta.value
+
+
+def lu_panel_factor_noalloc(P: torch.Tensor, ipiv: torch.Tensor, info: torch.Tensor, opts: LuOpts | None = None,
+                            stream: torch.cuda.Stream | None = None) -> None:
+    """Panel factorization that allocates no device memory (scratch in a static
+    device array inside the library; concurrent calls on one device race)."""
+    o = opts if opts is not None else default_opts()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    m, w = P.shape
+    _check("lu_panel_factor_noalloc", lib().lu_panel_factor_noalloc(_DT[P.dtype], m, w, _p(P), _ld(P, "P"),
+                                                                     _p(ipiv), ctypes.byref(o), _p(info),
+                                                                     ctypes.c_void_p(s.cuda_stream)))
