@@ -110,7 +110,8 @@ enum {
     LU_K_SOLVE = 6,     /* triangular solves and row permutations of a solve */
     LU_K_RESIDUAL = 7,  /* FP64 residuals, norms, conversions of the refinement */
     LU_K_OTHER = 8,
-    LU_K_COUNT = 9
+    LU_K_BATCHED = 9,   /* the persistent batched factorization + solve */
+    LU_K_COUNT = 10
 };
 /* lu_profile_enable(mask): from now on every kernel launch of a class whose bit
  * (1 << class) is set in mask is bracketed by two CUDA events recorded on its
@@ -292,6 +293,37 @@ int lu_factor_mixed_ex(lu_handle handle, lu_prec prec, int64_t n, float *A, int6
 int lu_gesv_mixed(lu_handle handle, lu_prec prec, int64_t n, int64_t nrhs, const double *A, int64_t lda,
                   const double *B, int64_t ldb, double *X, int64_t ldx, double tol, int max_iter,
                   const lu_opts *opts, int *iters, double *bwd_err);
+
+/* ----------------------------------------------------------------------------
+ * Batched (not in the paper): many independent small systems in one launch.
+ * ------------------------------------------------------------------------- */
+
+/*
+ * lu_gesv_batched -- for each i < batch, P_i A_i = L_i U_i in place (LU_blk,
+ * RL1-RL3, with 32-column panels) and, if B is not NULL, B_i := A_i^{-1} B_i.
+ * One persistent launch: matrices are taken largest first from an atomic
+ * counter by CTAs that each factor (and solve) one matrix at a time.
+ *   dtype    LU_F64 or LU_F32 (all matrices the same type)
+ *   n        device int32[batch], orders, 0 <= n_i <= 512
+ *   A        device array of batch device pointers, column-major A_i
+ *   lda      device int64[batch], lda_i >= max(1, n_i)
+ *   ipiv     device array of batch device pointers to int32[n_i]
+ *   nrhs     device int32[batch], 0 <= nrhs_i <= 8 (ignored when B is NULL)
+ *   B        NULL, or device array of batch device pointers to n_i x nrhs_i
+ *   ldb      device int64[batch] (ignored when B is NULL)
+ *   info     device int32[batch]: 0; i > 0 = first exactly zero pivot (the
+ *            system is then not solved); -4 bad lda_i; -9 bad ldb_i;
+ *            LU_ERR_UNSUPPORTED for n_i or nrhs_i out of range
+ * Asynchronous on the handle's stream; the launch can be captured in a CUDA
+ * graph (its order/counter workspace is allocated on the first call).
+ * Returns 0 (enqueued), -i for an invalid host argument, or a runtime error.
+ */
+int lu_gesv_batched(lu_handle handle, lu_dtype dtype, int batch, const int32_t *n, void *const *A,
+                    const int64_t *lda, int32_t *const *ipiv, const int32_t *nrhs, void *const *B,
+                    const int64_t *ldb, int32_t *info);
+/* lu_factor_batched -- lu_gesv_batched without right-hand sides. */
+int lu_factor_batched(lu_handle handle, lu_dtype dtype, int batch, const int32_t *n, void *const *A,
+                      const int64_t *lda, int32_t *const *ipiv, int32_t *info);
 
 #ifdef __cplusplus
 }

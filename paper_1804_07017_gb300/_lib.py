@@ -19,7 +19,7 @@ LU_WARN_NOT_CONVERGED = 0x40000000
 LU_F64 = 0
 LU_F32 = 1
 
-KERNEL_CLASSES = ["panel", "laswp", "trsm", "gemm", "tc_update", "pack", "solve", "residual", "other"]
+KERNEL_CLASSES = ["panel", "laswp", "trsm", "gemm", "tc_update", "pack", "solve", "residual", "other", "batched"]
 
 LU_TU_BF16 = 0
 LU_TU_FP16 = 1
@@ -69,6 +69,8 @@ _SIGNATURES = {
     "lu_profile_reset": (i32, []),
     "lu_profile_read": (i32, [i32, ctypes.POINTER(i64), ctypes.POINTER(dbl), ctypes.POINTER(dbl),
                               ctypes.POINTER(dbl)]),
+    "lu_gesv_batched": (i32, [vp, i32, i32, vp, vp, vp, vp, vp, vp, vp, vp]),
+    "lu_factor_batched": (i32, [vp, i32, i32, vp, vp, vp, vp, vp]),
     "lu_factor_mixed_ex": (i32, [vp, i32, i64, vp, i64, vp, ctypes.POINTER(LuOpts), vp]),
     "lu_gesv_mixed": (i32, [vp, i32, i64, i64, vp, i64, vp, i64, vp, i64, dbl, i32, ctypes.POINTER(LuOpts),
                             ctypes.POINTER(i32), ctypes.POINTER(dbl)]),

@@ -201,3 +201,31 @@ def lu_panel_factor_noalloc(P: torch.Tensor, ipiv: torch.Tensor, info: torch.Ten
     _check("lu_panel_factor_noalloc", lib().lu_panel_factor_noalloc(_DT[P.dtype], m, w, _p(P), _ld(P, "P"),
                                                                      _p(ipiv), ctypes.byref(o), _p(info),
                                                                      ctypes.c_void_p(s.cuda_stream)))
+
+
+class Batch:
+    """Device-side descriptor arrays for lu_gesv_batched built from lists of
+    column-major tensors (all of one dtype)."""
+
+    def __init__(self, mats, ipivs, rhs=None):
+        dev = mats[0].device
+        self.mats, self.ipivs, self.rhs = mats, ipivs, rhs
+        self.n = torch.tensor([m.shape[0] for m in mats], dtype=torch.int32, device=dev)
+        self.A = torch.tensor([m.data_ptr() for m in mats], dtype=torch.int64, device=dev)
+        self.lda = torch.tensor([_ld(m, "A") for m in mats], dtype=torch.int64, device=dev)
+        self.ipiv = torch.tensor([p.data_ptr() for p in ipivs], dtype=torch.int64, device=dev)
+        self.info = torch.zeros(len(mats), dtype=torch.int32, device=dev)
+        if rhs is not None:
+            self.nrhs = torch.tensor([b.shape[1] for b in rhs], dtype=torch.int32, device=dev)
+            self.B = torch.tensor([b.data_ptr() for b in rhs], dtype=torch.int64, device=dev)
+            self.ldb = torch.tensor([_ld(b, "B") for b in rhs], dtype=torch.int64, device=dev)
+        self.dtype = _DT[mats[0].dtype]
+
+
+def lu_gesv_batched(batch: Batch, handle: Handle | None = None) -> None:
+    h = _handle(handle)
+    has_b = batch.rhs is not None
+    _check("lu_gesv_batched", lib().lu_gesv_batched(
+        h.ptr, batch.dtype, len(batch.mats), _p(batch.n), _p(batch.A), _p(batch.lda), _p(batch.ipiv),
+        _p(batch.nrhs) if has_b else None, _p(batch.B) if has_b else None, _p(batch.ldb) if has_b else None,
+        _p(batch.info)))

@@ -1,0 +1,384 @@
+// Batched LU with partial pivoting and solve: many independent small matrices
+// (n <= 512) in one persistent launch (not part of the paper).
+//
+// A first single-CTA kernel orders the matrices by decreasing n (counting
+// sort), so that the persistent CTAs, which take matrices from an atomic
+// counter, start the largest ones first (longest-processing-time order).
+// Each CTA factors its matrix with the blocked right-looking algorithm of
+// LU_blk (Sec. 3) scaled down to one CTA:
+//   PF   the 32-column panel is loaded into shared memory and eliminated
+//        column by column (block argmax, first maximum, true division);
+//   the panel's interchanges are applied to the other columns, then RL2
+//   (unit-lower solve of the U12 row block, one column per thread) and RL3
+//   (A22 -= L21 U12 with 4x4 register tiles, L21 from shared memory);
+// and then, if right-hand sides are given, solves P A X = B for them.
+#include <climits>
+
+#include "internal.h"
+#include "profile.h"
+
+namespace {
+
+constexpr int kBT = 256;     // threads per CTA
+constexpr int kBNB = 32;     // panel width
+constexpr int kNMAX = 512;   // largest order handled
+constexpr int kMaxRhs = 8;   // right-hand sides handled together
+
+template <typename T>
+struct BatchSmem {
+    // panel [kBNB][kNMAX] column-major, then a U12 tile [kBNB][64] for the update
+    static constexpr size_t bytes = sizeof(T) * ((size_t)kBNB * kNMAX + (size_t)kBNB * 64) + 64;
+};
+
+// order[] = matrix indices by decreasing n; n > kNMAX or
+// n < 0 are placed last and flagged by the main kernel.
+__global__ void __launch_bounds__(1024) batch_order_kernel(int batch, const int32_t* __restrict__ nvec,
+                                                           int32_t* __restrict__ order, int* __restrict__ counter) {
+    __shared__ int cnt[kNMAX + 2];
+    __shared__ int start[kNMAX + 2];
+    for (int i = threadIdx.x; i < kNMAX + 2; i += blockDim.x) cnt[i] = 0;
+    __syncthreads();
+    auto key = [&](int i) {
+        const int n = nvec[i];
+        return (n < 0 || n > kNMAX) ? kNMAX + 1 : kNMAX - n;  // 0 = largest
+    };
+    for (int i = threadIdx.x; i < batch; i += blockDim.x) atomicAdd(&cnt[key(i)], 1);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int s = 0;
+        for (int b = 0; b < kNMAX + 2; ++b) {
+            start[b] = s;
+            s += cnt[b];
+        }
+        *counter = 0;
+    }
+    __syncthreads();
+    // scatter (the order among equal n is irrelevant to the results)
+    for (int i = threadIdx.x; i < batch; i += blockDim.x) order[atomicAdd(&start[key(i)], 1)] = i;
+}
+
+template <typename T>
+__device__ void block_argmax(T v, int i, T* red_v, int* red_i, T& out_v, int& out_i) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const T ov = __shfl_xor_sync(0xffffffffu, v, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, i, o);
+        if (ov > v || (ov == v && oi < i)) {
+            v = ov;
+            i = oi;
+        }
+    }
+    if (lane == 0) {
+        red_v[warp] = v;
+        red_i[warp] = i;
+    }
+    __syncthreads();
+    if (warp == 0) {
+        v = (lane < kBT / 32) ? red_v[lane] : T(-1);
+        i = (lane < kBT / 32) ? red_i[lane] : INT_MAX;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const T ov = __shfl_xor_sync(0xffffffffu, v, o);
+            const int oi = __shfl_xor_sync(0xffffffffu, i, o);
+            if (ov > v || (ov == v && oi < i)) {
+                v = ov;
+                i = oi;
+            }
+        }
+        if (lane == 0) {
+            red_v[0] = v;
+            red_i[0] = i;
+        }
+    }
+    __syncthreads();
+    out_v = red_v[0];
+    out_i = red_i[0];
+    __syncthreads();
+}
+
+// Factor one n x n matrix (column-major, lda) in place; ipiv 1-based; returns info.
+template <typename T>
+__device__ int factor_one(int n, T* __restrict__ A, int64_t lda, int32_t* __restrict__ ipiv, T* sP, T* sU,
+                          T* red_v, int* red_i) {
+    const int tid = threadIdx.x;
+    int finfo = 0;
+    for (int k0 = 0; k0 < n; k0 += kBNB) {
+        const int kb = min(kBNB, n - k0);
+        const int m = n - k0;
+        // ---- PF: panel rows [k0, n) x columns [k0, k0+kb) in shared memory ----
+        for (int c = 0; c < kb; ++c)
+            for (int r = tid; r < m; r += kBT) sP[c * kNMAX + r] = A[(int64_t)(k0 + r) + (int64_t)(k0 + c) * lda];
+        __syncthreads();
+        for (int j = 0; j < kb; ++j) {
+            T bv = T(-1);
+            int bi = INT_MAX;
+            for (int r = j + tid; r < m; r += kBT) {
+                const T v = fabs(sP[j * kNMAX + r]);
+                if (v > bv || (v == bv && r < bi)) {
+                    bv = v;
+                    bi = r;
+                }
+            }
+            T pv;
+            int p;
+            block_argmax(bv, bi, red_v, red_i, pv, p);
+            if (p == INT_MAX) p = j;
+            if (tid == 0) ipiv[k0 + j] = k0 + p + 1;
+            if (p != j && tid < kb) {
+                const T t = sP[tid * kNMAX + j];
+                sP[tid * kNMAX + j] = sP[tid * kNMAX + p];
+                sP[tid * kNMAX + p] = t;
+            }
+            __syncthreads();
+            const T piv = sP[j * kNMAX + j];
+            if (piv == T(0)) {
+                if (finfo == 0) finfo = k0 + j + 1;
+                continue;
+            }
+            for (int r = j + 1 + tid; r < m; r += kBT) {
+                const T l = sP[j * kNMAX + r] / piv;
+                sP[j * kNMAX + r] = l;
+                for (int c = j + 1; c < kb; ++c) sP[c * kNMAX + r] = fma(-l, sP[c * kNMAX + j], sP[c * kNMAX + r]);
+            }
+            __syncthreads();
+        }
+        for (int c = 0; c < kb; ++c)
+            for (int r = tid; r < m; r += kBT) A[(int64_t)(k0 + r) + (int64_t)(k0 + c) * lda] = sP[c * kNMAX + r];
+        // ---- the panel's interchanges on the other columns (one thread per column) ----
+        const int others = n - kb;
+        for (int q = tid; q < others; q += kBT) {
+            const int col = (q < k0) ? q : q + kb;
+            T* a = A + (int64_t)col * lda;
+            for (int j = 0; j < kb; ++j) {
+                const int p = ipiv[k0 + j] - 1;
+                if (p != k0 + j) {
+                    const T t = a[k0 + j];
+                    a[k0 + j] = a[p];
+                    a[p] = t;
+                }
+            }
+        }
+        __syncthreads();
+        const int nr = n - k0 - kb;  // trailing columns
+        if (nr <= 0) continue;
+        // ---- RL2: U12 := trilu(L11)^-1 A12, one column per thread ----
+        for (int c = tid; c < nr; c += kBT) {
+            T x[kBNB];
+            T* a = A + (int64_t)(k0 + kb + c) * lda + k0;
+#pragma unroll
+            for (int i = 0; i < kBNB; ++i) x[i] = (i < kb) ? a[i] : T(0);
+#pragma unroll
+            for (int j = 0; j < kBNB; ++j)
+#pragma unroll
+                for (int i = j + 1; i < kBNB; ++i)
+                    if (i < kb) x[i] = fma(-sP[j * kNMAX + i], x[j], x[i]);
+#pragma unroll
+            for (int i = 0; i < kBNB; ++i)
+                if (i < kb) a[i] = x[i];
+        }
+        __syncthreads();
+        // ---- RL3: A22 -= L21 U12 in 64x64 output tiles, 4x4 per thread ----
+        const int mr = m - kb;  // rows below the panel
+        const int tx = tid & 15, ty = tid >> 4;
+        for (int j0 = 0; j0 < nr; j0 += 64) {
+            // U12 columns j0 .. j0+63 into shared memory
+            for (int e = tid; e < kBNB * 64; e += kBT) {
+                const int kk = e & (kBNB - 1), jj = e / kBNB;
+                sU[kk * 64 + jj] = (kk < kb && j0 + jj < nr) ? A[(int64_t)(k0 + kk) + (int64_t)(k0 + kb + j0 + jj) * lda]
+                                                              : T(0);
+            }
+            __syncthreads();
+            for (int i0 = 0; i0 < mr; i0 += 64) {
+                T acc[4][4];
+#pragma unroll
+                for (int a = 0; a < 4; ++a)
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) acc[a][b] = T(0);
+                for (int kk = 0; kk < kb; ++kk) {
+                    T lv[4], uv[4];
+#pragma unroll
+                    for (int a = 0; a < 4; ++a) {
+                        const int r = i0 + tx + 16 * a;
+                        lv[a] = (r < mr) ? sP[kk * kNMAX + kb + r] : T(0);
+                        uv[a] = sU[kk * 64 + ty + 16 * a];
+                    }
+#pragma unroll
+                    for (int a = 0; a < 4; ++a)
+#pragma unroll
+                        for (int b = 0; b < 4; ++b) acc[a][b] = fma(lv[a], uv[b], acc[a][b]);
+                }
+#pragma unroll
+                for (int b = 0; b < 4; ++b) {
+                    const int jc = j0 + ty + 16 * b;
+                    if (jc >= nr) continue;
+                    T* col = A + (int64_t)(k0 + kb + jc) * lda + (k0 + kb);
+#pragma unroll
+                    for (int a = 0; a < 4; ++a) {
+                        const int r = i0 + tx + 16 * a;
+                        if (r < mr) col[r] -= acc[a][b];
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    return finfo;
+}
+
+// X := (P A)^-1 B with the factors in A; B n x nrhs (nrhs <= kMaxRhs), staged in shared memory.
+template <typename T>
+__device__ void solve_one(int n, const T* __restrict__ A, int64_t lda, const int32_t* __restrict__ ipiv, int nrhs,
+                          T* __restrict__ B, int64_t ldb, T* sB) {
+    const int tid = threadIdx.x;
+    for (int e = tid; e < n * nrhs; e += kBT) {
+        const int i = e % n, c = e / n;
+        sB[c * kNMAX + i] = B[i + (int64_t)c * ldb];
+    }
+    __syncthreads();
+    if (tid < nrhs) {
+        for (int k = 0; k < n; ++k) {
+            const int p = ipiv[k] - 1;
+            if (p != k) {
+                const T t = sB[tid * kNMAX + k];
+                sB[tid * kNMAX + k] = sB[tid * kNMAX + p];
+                sB[tid * kNMAX + p] = t;
+            }
+        }
+    }
+    __syncthreads();
+    for (int j = 0; j < n; ++j) {  // unit lower
+        for (int e = tid; e < (n - j - 1) * nrhs; e += kBT) {
+            const int i = j + 1 + e % (n - j - 1), c = e / (n - j - 1);
+            sB[c * kNMAX + i] = fma(-A[i + (int64_t)j * lda], sB[c * kNMAX + j], sB[c * kNMAX + i]);
+        }
+        __syncthreads();
+    }
+    for (int j = n - 1; j >= 0; --j) {  // upper
+        if (tid < nrhs) sB[tid * kNMAX + j] /= A[j + (int64_t)j * lda];
+        __syncthreads();
+        for (int e = tid; e < j * nrhs; e += kBT) {
+            const int i = e % j, c = e / j;
+            sB[c * kNMAX + i] = fma(-A[i + (int64_t)j * lda], sB[c * kNMAX + j], sB[c * kNMAX + i]);
+        }
+        __syncthreads();
+    }
+    for (int e = tid; e < n * nrhs; e += kBT) {
+        const int i = e % n, c = e / n;
+        B[i + (int64_t)c * ldb] = sB[c * kNMAX + i];
+    }
+    __syncthreads();
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kBT) batched_gesv_kernel(int batch, const int32_t* __restrict__ nvec,
+                                                           T* const* __restrict__ Aptr, const int64_t* __restrict__ ldav,
+                                                           int32_t* const* __restrict__ ipivp,
+                                                           const int32_t* __restrict__ nrhsv, T* const* __restrict__ Bptr,
+                                                           const int64_t* __restrict__ ldbv,
+                                                           int32_t* __restrict__ info,
+                                                           const int32_t* __restrict__ order, int* __restrict__ counter) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    T* sP = reinterpret_cast<T*>(smraw);
+    T* sU = sP + (size_t)kBNB * kNMAX;
+    __shared__ T red_v[kBT / 32];
+    __shared__ int red_i[kBT / 32];
+    __shared__ int s_idx;
+    for (;;) {
+        if (threadIdx.x == 0) s_idx = atomicAdd(counter, 1);
+        __syncthreads();
+        const int idx = s_idx;
+        __syncthreads();
+        if (idx >= batch) break;
+        const int mid = order[idx];
+        const int n = nvec[mid];
+        const int64_t lda = ldav[mid];
+        if (n < 0 || n > kNMAX) {
+            if (threadIdx.x == 0) info[mid] = LU_ERR_UNSUPPORTED;
+            continue;
+        }
+        if (lda < max(1, n)) {
+            if (threadIdx.x == 0) info[mid] = -4;
+            continue;
+        }
+        int finfo = 0;
+        if (n > 0) finfo = factor_one<T>(n, Aptr[mid], lda, ipivp[mid], sP, sU, red_v, red_i);
+        if (threadIdx.x == 0) info[mid] = finfo;
+        if (Bptr && n > 0 && finfo == 0) {
+            const int nrhs = nrhsv[mid];
+            const int64_t ldb = ldbv[mid];
+            if (nrhs < 0 || nrhs > kMaxRhs || ldb < max(1, n)) {
+                if (threadIdx.x == 0) info[mid] = nrhs < 0 || nrhs > kMaxRhs ? LU_ERR_UNSUPPORTED : -9;
+                continue;
+            }
+            if (nrhs > 0) solve_one<T>(n, Aptr[mid], lda, ipivp[mid], nrhs, Bptr[mid], ldb, sP);
+        }
+    }
+}
+
+}  // namespace
+
+template <typename T>
+static int gesv_batched_impl(lu_context* c, int batch, const int32_t* n, T* const* A, const int64_t* lda,
+                             int32_t* const* ipiv, const int32_t* nrhs, T* const* B, const int64_t* ldb, int32_t* info) {
+    cudaStream_t st = c->user;
+    const size_t need = sizeof(int32_t) * ((size_t)batch + 64);
+    if (c->batch_ws_bytes < need) {
+        if (c->batch_ws) {
+            LU_CHECK_CUDA(cudaStreamSynchronize(st));
+            cudaFree(c->batch_ws);
+            c->batch_ws = nullptr;
+            c->batch_ws_bytes = 0;
+        }
+        if (cudaMalloc(&c->batch_ws, need) != cudaSuccess) {
+            cudaGetLastError();
+            return LU_ERR_NOMEM;
+        }
+        c->batch_ws_bytes = need;
+    }
+    int* counter = reinterpret_cast<int*>(c->batch_ws);
+    int32_t* order = reinterpret_cast<int32_t*>(c->batch_ws) + 64;
+    {
+        LuProfScope prof(st, LU_K_OTHER, 12.0 * batch, 0.0);
+        batch_order_kernel<<<1, 1024, 0, st>>>(batch, n, order, counter);
+    }
+    LU_CHECK_LAUNCH();
+    static bool attr[2] = {false, false};
+    const int ti = sizeof(T) == 8 ? 0 : 1;
+    if (!attr[ti]) {
+        LU_CHECK_CUDA(cudaFuncSetAttribute(batched_gesv_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)BatchSmem<T>::bytes));
+        attr[ti] = true;
+    }
+    int per_sm = 0;
+    LU_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batched_gesv_kernel<T>, kBT,
+                                                                BatchSmem<T>::bytes));
+    const int grid = std::max(1, std::min(batch, c->num_sms * std::max(per_sm, 1)));
+    LuProfScope prof(st, LU_K_BATCHED, 0.0, 0.0);
+    batched_gesv_kernel<T><<<grid, kBT, BatchSmem<T>::bytes, st>>>(batch, n, A, lda, ipiv, nrhs, B, ldb, info, order,
+                                                                   counter);
+    LU_CHECK_LAUNCH();
+    return LU_SUCCESS;
+}
+
+extern "C" int lu_gesv_batched(lu_handle h, lu_dtype dtype, int batch, const int32_t* n, void* const* A,
+                               const int64_t* lda, int32_t* const* ipiv, const int32_t* nrhs, void* const* B,
+                               const int64_t* ldb, int32_t* info) {
+    if (!h) return LU_ERR_HANDLE;
+    if (dtype != LU_F64 && dtype != LU_F32) return -2;
+    if (batch < 0) return -3;
+    if (batch > 0 && (!n || !A || !lda || !ipiv)) return -4;
+    if (B && (!nrhs || !ldb)) return -8;
+    if (batch > 0 && !info) return -11;
+    if (batch == 0) return LU_SUCCESS;
+    std::lock_guard<std::mutex> lk(h->mu);
+    LU_TRY(lu_ctx_reserve(h, 1, 1));
+    if (dtype == LU_F64)
+        return gesv_batched_impl<double>(h, batch, n, (double* const*)A, lda, ipiv, nrhs, (double* const*)B, ldb, info);
+    return gesv_batched_impl<float>(h, batch, n, (float* const*)A, lda, ipiv, nrhs, (float* const*)B, ldb, info);
+}
+
+extern "C" int lu_factor_batched(lu_handle h, lu_dtype dtype, int batch, const int32_t* n, void* const* A,
+                                 const int64_t* lda, int32_t* const* ipiv, int32_t* info) {
+    return lu_gesv_batched(h, dtype, batch, n, A, lda, ipiv, nullptr, nullptr, nullptr, info);
+}

@@ -44,6 +44,9 @@ struct lu_context {
     void* mx = nullptr;
     size_t mx_bytes = 0;
     double* host_eta = nullptr;  // pinned host word for the convergence test
+    // Batched path: matrix order (largest first) and the work counter.
+    void* batch_ws = nullptr;
+    size_t batch_ws_bytes = 0;
     // Shared memory a panel leaf CTA may use: small enough, on the mixed path, to
     // sit beside a tensor-core trailing-update CTA on the same SM.
     size_t pf_smem_budget = 160 * 1024;

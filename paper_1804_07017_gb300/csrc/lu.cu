@@ -64,6 +64,8 @@ int lu_ctx_release(lu_context* c) {
     c->mx = nullptr;
     if (c->host_eta) cudaFreeHost(c->host_eta);
     c->host_eta = nullptr;
+    if (c->batch_ws) cudaFree(c->batch_ws);
+    c->batch_ws = nullptr;
     cudaEvent_t evs[] = {c->ev_fork, c->ev_pf, c->ev_tu, c->ev_join_hi, c->ev_join_lo, c->ev_steal};
     for (cudaEvent_t e : evs)
         if (e) cudaEventDestroy(e);
