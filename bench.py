@@ -405,9 +405,10 @@ def run_batched(args):
             restore()
             torch.cuda.synchronize()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            graph.replay()
-            e1.record(stream)
+            with torch.cuda.stream(stream):
+                e0.record(stream)
+                graph.replay()
+                e1.record(stream)
             torch.cuda.synchronize()
             if it >= args.warmup:
                 times.append(e0.elapsed_time(e1))

@@ -68,7 +68,10 @@ __device__ __forceinline__ void warp_best(T& v, int& i, int& q) {
 // leaf factors its first w <= W columns.  RQ: rows per thread (thread t owns
 // rows t + kNT*q of its CTA's block).
 // The block is row-major in shared memory with a padded stride W+1.
-template <typename T, int W, int RQ>
+// HW = true: the cluster's hardware barrier (barrier.cluster arrive / wait, split
+// so that a CTA arrives as soon as it has published and waits only when it
+// needs the other candidates); HW = false: the bounded grid barrier on sync.
+template <typename T, int W, int RQ, bool HW>
 __global__ void __launch_bounds__(kNT) pf_leaf_cluster_kernel(T* __restrict__ A, int64_t lda, int m, int w,
                                                               int left_cols, int right_cols, int32_t* __restrict__ ipiv,
                                                               int ipiv_add, LuSync* __restrict__ sync) {
@@ -138,12 +141,17 @@ __global__ void __launch_bounds__(kNT) pf_leaf_cluster_kernel(T* __restrict__ A,
             if (warp == (lr % kNT) >> 5)
                 for (int c = lane; c < W; c += 32) slot->jrow[buf][c] = sA[lr * WP + c];
         }
+        if (HW) {
+            cluster.barrier_arrive();
+            return true;
+        }
         return lu_grid_barrier(sync, (++phase) * (unsigned)C, &s_ok);
     };
 
     bool ok = publish(0);
     for (int jj = 0; jj < w && ok; ++jj) {
         const int buf = jj & 1;
+        if (HW) cluster.barrier_wait();
         // ---- every warp selects the pivot from the C published candidates ----
         T cv = T(-1);
         int ci = INT_MAX, cq = -1;
@@ -206,9 +214,13 @@ __global__ void __launch_bounds__(kNT) pf_leaf_cluster_kernel(T* __restrict__ A,
         if (jj + 1 < w) ok = publish(jj + 1);
     }
     // no CTA leaves while another may still read its slot
-    if (ok) ok = lu_grid_barrier(sync, (++phase) * (unsigned)C, &s_ok);
-    lu_grid_exit(sync);
-    if (!ok) return;
+    if (HW) {
+        cluster.sync();
+    } else {
+        if (ok) ok = lu_grid_barrier(sync, (++phase) * (unsigned)C, &s_ok);
+        lu_grid_exit(sync);
+        if (!ok) return;
+    }
     for (int c = 0; c < w; ++c)
 #pragma unroll
         for (int q = 0; q < RQ; ++q) {
@@ -286,9 +298,9 @@ size_t cluster_smem(int w, int rq) {
 template <typename T>
 struct LeafTable {
     typedef void (*Fn)(T*, int64_t, int, int, int, int, int32_t*, int, LuSync*);
-    static Fn get(int w, int rq) {
+    static Fn get(int w, int rq, bool hw) {
 #define LU_LEAF_CASE(WW, RR) \
-    if (w == WW && rq == RR) return pf_leaf_cluster_kernel<T, WW, RR>;
+    if (w == WW && rq == RR) return hw ? pf_leaf_cluster_kernel<T, WW, RR, true> : pf_leaf_cluster_kernel<T, WW, RR, false>;
         LU_LEAF_CASE(8, 1) LU_LEAF_CASE(8, 2) LU_LEAF_CASE(8, 4) LU_LEAF_CASE(8, 8)
         LU_LEAF_CASE(16, 1) LU_LEAF_CASE(16, 2) LU_LEAF_CASE(16, 4) LU_LEAF_CASE(16, 8)
         LU_LEAF_CASE(32, 1) LU_LEAF_CASE(32, 2) LU_LEAF_CASE(32, 4)
@@ -327,17 +339,18 @@ static int cluster_limit() {
     const int ti = sizeof(T) == 8 ? 0 : 1;
     if (lim[ti] >= 0) return lim[ti];
     const int ws[3] = {8, 16, 32}, rqs[4] = {1, 2, 4, 8};
-    for (int w : ws)
-        for (int rq : rqs) {
-            auto fn = LeafTable<T>::get(w, rq);
-            if (!fn) continue;
-            if (cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)
-                cudaGetLastError();
-            if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024) != cudaSuccess)
-                cudaGetLastError();
-        }
+    for (int hw = 0; hw < 2; ++hw)
+        for (int w : ws)
+            for (int rq : rqs) {
+                auto fn = LeafTable<T>::get(w, rq, hw != 0);
+                if (!fn) continue;
+                if (cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)
+                    cudaGetLastError();
+                if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024) != cudaSuccess)
+                    cudaGetLastError();
+            }
     int best = 0;
-    auto fn = LeafTable<T>::get(16, 1);
+    auto fn = LeafTable<T>::get(16, 1, false);
     for (int C = LU_PF_MAX_CTAS_CLUSTER; C >= 1; C >>= 1) {
         if (max_clusters_for<T>(fn, C, cluster_smem<T>(16, 1)) > 0) {
             best = C;
@@ -360,7 +373,7 @@ bool lu_pf_cluster_shape(int64_t m, int w, size_t budget, int* C_out, int* R_out
     if (cmax <= 0) return false;
     const int rqs[4] = {1, 2, 4, 8};
     for (int rq : rqs) {
-        if (!LeafTable<T>::get(w, rq)) continue;
+        if (!LeafTable<T>::get(w, rq, false)) continue;
         const int64_t R = (int64_t)kNT * rq;
         const int64_t C = lu_cdiv(m, R);
         if (C > cmax) continue;
@@ -380,7 +393,13 @@ bool lu_pf_cluster_shape(int64_t m, int w, size_t budget, int* C_out, int* R_out
 template <typename T>
 int lu_launch_pf_leaf_cluster(cudaStream_t st, T* A, int64_t lda, int64_t m, int w, int C, int R, size_t smem,
                               int64_t left_cols, int64_t right_cols, int32_t* ipiv, int64_t ipiv_add, LuSync* sync) {
-    auto fn = LeafTable<T>::get(compiled_width(w), R / kNT);
+    // LU_GB300_PF_BARRIER=global selects the bounded global-memory barrier
+    static int hw = -1;
+    if (hw < 0) {
+        const char* e = getenv("LU_GB300_PF_BARRIER");
+        hw = (e && e[0] == 'g') ? 0 : 1;
+    }
+    auto fn = LeafTable<T>::get(compiled_width(w), R / kNT, hw != 0);
     if (!fn) return LU_ERR_UNSUPPORTED;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(C, 1, 1);
