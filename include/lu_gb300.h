@@ -324,6 +324,17 @@ int lu_gesv_batched(lu_handle handle, lu_dtype dtype, int batch, const int32_t *
 /* lu_factor_batched -- lu_gesv_batched without right-hand sides. */
 int lu_factor_batched(lu_handle handle, lu_dtype dtype, int batch, const int32_t *n, void *const *A,
                       const int64_t *lda, int32_t *const *ipiv, int32_t *info);
+/*
+ * lu_solve_batched -- for each i < batch, B_i := (P_i^T L_i U_i)^{-1} B_i with
+ * the factors and interchanges that lu_factor_batched (or lu_gesv_batched) left
+ * in LU_i and ipiv_i (getrs: interchanges, unit-lower solve, upper solve).
+ * Arguments as lu_gesv_batched; B must not be NULL (-9 otherwise).  The factors
+ * are not checked for zero pivots: a singular U_i gives non-finite B_i, as in
+ * getrs.  info_i: 0, or -4 / -9 / LU_ERR_UNSUPPORTED as above.
+ */
+int lu_solve_batched(lu_handle handle, lu_dtype dtype, int batch, const int32_t *n, void *const *LU,
+                     const int64_t *lda, int32_t *const *ipiv, const int32_t *nrhs, void *const *B,
+                     const int64_t *ldb, int32_t *info);
 
 #ifdef __cplusplus
 }

@@ -71,6 +71,7 @@ _SIGNATURES = {
                               ctypes.POINTER(dbl)]),
     "lu_gesv_batched": (i32, [vp, i32, i32, vp, vp, vp, vp, vp, vp, vp, vp]),
     "lu_factor_batched": (i32, [vp, i32, i32, vp, vp, vp, vp, vp]),
+    "lu_solve_batched": (i32, [vp, i32, i32, vp, vp, vp, vp, vp, vp, vp, vp]),
     "lu_factor_mixed_ex": (i32, [vp, i32, i64, vp, i64, vp, ctypes.POINTER(LuOpts), vp]),
     "lu_gesv_mixed": (i32, [vp, i32, i64, i64, vp, i64, vp, i64, vp, i64, dbl, i32, ctypes.POINTER(LuOpts),
                             ctypes.POINTER(i32), ctypes.POINTER(dbl)]),

@@ -229,3 +229,20 @@ def lu_gesv_batched(batch: Batch, handle: Handle | None = None) -> None:
         h.ptr, batch.dtype, len(batch.mats), _p(batch.n), _p(batch.A), _p(batch.lda), _p(batch.ipiv),
         _p(batch.nrhs) if has_b else None, _p(batch.B) if has_b else None, _p(batch.ldb) if has_b else None,
         _p(batch.info)))
+
+
+def lu_factor_batched(batch: Batch, handle: Handle | None = None) -> None:
+    h = _handle(handle)
+    _check("lu_factor_batched", lib().lu_factor_batched(
+        h.ptr, batch.dtype, len(batch.mats), _p(batch.n), _p(batch.A), _p(batch.lda), _p(batch.ipiv),
+        _p(batch.info)))
+
+
+def lu_solve_batched(batch: Batch, handle: Handle | None = None) -> None:
+    """B_i := A_i^{-1} B_i from the factors lu_factor_batched left in batch.mats."""
+    if batch.rhs is None:
+        raise ValueError("lu_solve_batched needs right-hand sides")
+    h = _handle(handle)
+    _check("lu_solve_batched", lib().lu_solve_batched(
+        h.ptr, batch.dtype, len(batch.mats), _p(batch.n), _p(batch.A), _p(batch.lda), _p(batch.ipiv),
+        _p(batch.nrhs), _p(batch.B), _p(batch.ldb), _p(batch.info)))

@@ -277,7 +277,8 @@ __global__ void __launch_bounds__(kBT) batched_gesv_kernel(int batch, const int3
                                                            const int32_t* __restrict__ nrhsv, T* const* __restrict__ Bptr,
                                                            const int64_t* __restrict__ ldbv,
                                                            int32_t* __restrict__ info,
-                                                           const int32_t* __restrict__ order, int* __restrict__ counter) {
+                                                           const int32_t* __restrict__ order, int* __restrict__ counter,
+                                                           int do_factor) {
     extern __shared__ __align__(16) unsigned char smraw[];
     T* sP = reinterpret_cast<T*>(smraw);
     T* sU = sP + (size_t)kBNB * kNMAX;
@@ -302,7 +303,7 @@ __global__ void __launch_bounds__(kBT) batched_gesv_kernel(int batch, const int3
             continue;
         }
         int finfo = 0;
-        if (n > 0) finfo = factor_one<T>(n, Aptr[mid], lda, ipivp[mid], sP, sU, red_v, red_i);
+        if (n > 0 && do_factor) finfo = factor_one<T>(n, Aptr[mid], lda, ipivp[mid], sP, sU, red_v, red_i);
         if (threadIdx.x == 0) info[mid] = finfo;
         if (Bptr && n > 0 && finfo == 0) {
             const int nrhs = nrhsv[mid];
@@ -320,7 +321,8 @@ __global__ void __launch_bounds__(kBT) batched_gesv_kernel(int batch, const int3
 
 template <typename T>
 static int gesv_batched_impl(lu_context* c, int batch, const int32_t* n, T* const* A, const int64_t* lda,
-                             int32_t* const* ipiv, const int32_t* nrhs, T* const* B, const int64_t* ldb, int32_t* info) {
+                             int32_t* const* ipiv, const int32_t* nrhs, T* const* B, const int64_t* ldb, int32_t* info,
+                             int do_factor) {
     cudaStream_t st = c->user;
     const size_t need = sizeof(int32_t) * ((size_t)batch + 64);
     if (c->batch_ws_bytes < need) {
@@ -356,29 +358,44 @@ static int gesv_batched_impl(lu_context* c, int batch, const int32_t* n, T* cons
     const int grid = std::max(1, std::min(batch, c->num_sms * std::max(per_sm, 1)));
     LuProfScope prof(st, LU_K_BATCHED, 0.0, 0.0);
     batched_gesv_kernel<T><<<grid, kBT, BatchSmem<T>::bytes, st>>>(batch, n, A, lda, ipiv, nrhs, B, ldb, info, order,
-                                                                   counter);
+                                                                   counter, do_factor);
     LU_CHECK_LAUNCH();
     return LU_SUCCESS;
 }
 
-extern "C" int lu_gesv_batched(lu_handle h, lu_dtype dtype, int batch, const int32_t* n, void* const* A,
-                               const int64_t* lda, int32_t* const* ipiv, const int32_t* nrhs, void* const* B,
-                               const int64_t* ldb, int32_t* info) {
+static int batched_entry(lu_handle h, lu_dtype dtype, int batch, const int32_t* n, void* const* A,
+                         const int64_t* lda, int32_t* const* ipiv, const int32_t* nrhs, void* const* B,
+                         const int64_t* ldb, int32_t* info, int do_factor) {
     if (!h) return LU_ERR_HANDLE;
     if (dtype != LU_F64 && dtype != LU_F32) return -2;
     if (batch < 0) return -3;
     if (batch > 0 && (!n || !A || !lda || !ipiv)) return -4;
     if (B && (!nrhs || !ldb)) return -8;
+    if (!do_factor && batch > 0 && !B) return -9;
     if (batch > 0 && !info) return -11;
     if (batch == 0) return LU_SUCCESS;
     std::lock_guard<std::mutex> lk(h->mu);
     LU_TRY(lu_ctx_reserve(h, 1, 1));
     if (dtype == LU_F64)
-        return gesv_batched_impl<double>(h, batch, n, (double* const*)A, lda, ipiv, nrhs, (double* const*)B, ldb, info);
-    return gesv_batched_impl<float>(h, batch, n, (float* const*)A, lda, ipiv, nrhs, (float* const*)B, ldb, info);
+        return gesv_batched_impl<double>(h, batch, n, (double* const*)A, lda, ipiv, nrhs, (double* const*)B, ldb, info,
+                                         do_factor);
+    return gesv_batched_impl<float>(h, batch, n, (float* const*)A, lda, ipiv, nrhs, (float* const*)B, ldb, info,
+                                    do_factor);
+}
+
+extern "C" int lu_gesv_batched(lu_handle h, lu_dtype dtype, int batch, const int32_t* n, void* const* A,
+                               const int64_t* lda, int32_t* const* ipiv, const int32_t* nrhs, void* const* B,
+                               const int64_t* ldb, int32_t* info) {
+    return batched_entry(h, dtype, batch, n, A, lda, ipiv, nrhs, B, ldb, info, 1);
 }
 
 extern "C" int lu_factor_batched(lu_handle h, lu_dtype dtype, int batch, const int32_t* n, void* const* A,
                                  const int64_t* lda, int32_t* const* ipiv, int32_t* info) {
-    return lu_gesv_batched(h, dtype, batch, n, A, lda, ipiv, nullptr, nullptr, nullptr, info);
+    return batched_entry(h, dtype, batch, n, A, lda, ipiv, nullptr, nullptr, nullptr, info, 1);
+}
+
+extern "C" int lu_solve_batched(lu_handle h, lu_dtype dtype, int batch, const int32_t* n, void* const* LU,
+                                const int64_t* lda, int32_t* const* ipiv, const int32_t* nrhs, void* const* B,
+                                const int64_t* ldb, int32_t* info) {
+    return batched_entry(h, dtype, batch, n, LU, lda, ipiv, nrhs, B, ldb, info, 0);
 }

@@ -90,9 +90,15 @@ template <typename T>
 int lu_launch_permute_rows(cudaStream_t st, int64_t n, int64_t nrhs, const int32_t* perm,
                            const T* B, int64_t ldb, T* X, int64_t ldx);
 
+// Dinv: NULL, or the inverses of the diagonal blocks from lu_launch_trinv_diag,
+// which turn each block's substitution into one dense product.
 template <typename T>
 int lu_launch_trsv_blocked(lu_context* c, cudaStream_t st, bool lower_unit, int64_t n,
-                           int64_t nrhs, const T* LU, int64_t lda, T* X, int64_t ldx);
+                           int64_t nrhs, const T* LU, int64_t lda, T* X, int64_t ldx, const T* Dinv = nullptr);
+template <typename T>
+size_t lu_trinv_bytes(int64_t n);
+template <typename T>
+int lu_launch_trinv_diag(cudaStream_t st, int64_t n, const T* LU, int64_t lda, T* D);
 
 int lu_launch_finish_info(cudaStream_t st, const LuSync* s, int32_t* info);
 
@@ -101,6 +107,11 @@ bool lu_pf_cluster_shape(int64_t m, int w, size_t budget, int* C_out, int* R_out
 template <typename T>
 int lu_launch_pf_leaf_cluster(cudaStream_t st, T* A, int64_t lda, int64_t m, int w, int C, int R, size_t smem,
                               int64_t left_cols, int64_t right_cols, int32_t* ipiv, int64_t ipiv_add, LuSync* sync);
+// Pushed-message cluster leaf (pf_push.cu): w columns of a kernel compiled for wc.
+size_t lu_pf_push_smem(int esize, int w, int rq);
+template <typename T>
+int lu_launch_pf_leaf_push(cudaStream_t st, T* A, int64_t lda, int64_t m, int w, int wc, int C, int R,
+                           int64_t left_cols, int64_t right_cols, int32_t* ipiv, int64_t ipiv_add, LuSync* sync);
 
 // Recursive panel factorization of columns [j0, j0+width) over rows [j0, M)
 // of the matrix at A (absolute indices; ipiv absolute, 1-based).

@@ -248,6 +248,7 @@ static int gesv_refined(lu_context* h, int prec, int64_t n, int64_t nrhs, const 
     const size_t o_dw = take(sizeof(T) * n * nrhs);
     const size_t o_part = take(sizeof(double) * nch * rhs_chunk * n);
     const size_t o_sc = take(sizeof(double) * (8 + nrhs) + sizeof(int32_t) * 8);
+    const size_t o_dinv = take(lu_trinv_bytes<T>(n));
     LU_TRY(lu_mx_reserve(h, off));
     char* base = (char*)h->mx;
     T* Aw = (T*)(base + o_aw);
@@ -259,6 +260,7 @@ static int gesv_refined(lu_context* h, int prec, int64_t n, int64_t nrhs, const 
     T* dw = (T*)(base + o_dw);
     double* part = (double*)(base + o_part);
     double* sc = (double*)(base + o_sc);
+    T* Dinv = (T*)(base + o_dinv);
     double* anorm = sc;
     double* eta = sc + 1;
     double* eta_cols = sc + 8;
@@ -273,12 +275,15 @@ static int gesv_refined(lu_context* h, int prec, int64_t n, int64_t nrhs, const 
     else
         LU_TRY(lu_factor_blocked<double>(h, n, (double*)Aw, ldw, ipiv, o, dinfo, nullptr));
     LU_TRY(lu_launch_perm_from_ipiv<T>(st, n, ipiv, perm));
+    // inverses of the diagonal blocks of L and U: every correction solve then
+    // costs one dense block product per block instead of a substitution chain
+    LU_TRY(lu_launch_trinv_diag<T>(st, n, Aw, ldw, Dinv));
     LU_TRY(lu_launch_norm_inf(st, n, A, lda, part, anorm));
     // 2. x0 = U^-1 L^-1 P b in T
     LU_TRY((lu_launch_cast<double, T>(st, n, nrhs, B, ldb, rw, n)));
     LU_TRY(lu_launch_permute_rows<T>(st, n, nrhs, perm, rw, n, dw, n));
-    LU_TRY(lu_launch_trsv_blocked<T>(h, st, true, n, nrhs, Aw, ldw, dw, n));
-    LU_TRY(lu_launch_trsv_blocked<T>(h, st, false, n, nrhs, Aw, ldw, dw, n));
+    LU_TRY(lu_launch_trsv_blocked<T>(h, st, true, n, nrhs, Aw, ldw, dw, n, Dinv));
+    LU_TRY(lu_launch_trsv_blocked<T>(h, st, false, n, nrhs, Aw, ldw, dw, n, Dinv));
     LU_TRY((lu_launch_cast<T, double>(st, n, nrhs, dw, n, X, ldx)));
     // 3. refinement: r = b - A x (FP64), eta test on the host, d = (LU)^-1 P r (T), x += d (FP64)
     double best = INFINITY;
@@ -318,8 +323,8 @@ static int gesv_refined(lu_context* h, int prec, int64_t n, int64_t nrhs, const 
         }
         LU_TRY((lu_launch_cast<double, T>(st, n, nrhs, R, n, rw, n)));
         LU_TRY(lu_launch_permute_rows<T>(st, n, nrhs, perm, rw, n, dw, n));
-        LU_TRY(lu_launch_trsv_blocked<T>(h, st, true, n, nrhs, Aw, ldw, dw, n));
-        LU_TRY(lu_launch_trsv_blocked<T>(h, st, false, n, nrhs, Aw, ldw, dw, n));
+        LU_TRY(lu_launch_trsv_blocked<T>(h, st, true, n, nrhs, Aw, ldw, dw, n, Dinv));
+        LU_TRY(lu_launch_trsv_blocked<T>(h, st, false, n, nrhs, Aw, ldw, dw, n, Dinv));
         LU_TRY(lu_launch_add_to_f64<T>(st, n, nrhs, dw, n, X, ldx));
     }
     if (status == LU_WARN_NOT_CONVERGED && best_it >= 0 && best_it != it) {

@@ -367,6 +367,7 @@ static int compiled_width(int w) { return w <= 8 ? 8 : (w <= 16 ? 16 : (w <= 32 
 
 template <typename T>
 bool lu_pf_cluster_shape(int64_t m, int w, size_t budget, int* C_out, int* R_out, size_t* smem_out) {
+    if (m < w) return false;
     w = compiled_width(w);
     if (w == 0) return false;
     const int cmax = cluster_limit<T>();
@@ -377,7 +378,7 @@ bool lu_pf_cluster_shape(int64_t m, int w, size_t budget, int* C_out, int* R_out
         const int64_t R = (int64_t)kNT * rq;
         const int64_t C = lu_cdiv(m, R);
         if (C > cmax) continue;
-        const size_t smem = cluster_smem<T>(w, rq);
+        const size_t smem = std::max(cluster_smem<T>(w, rq), lu_pf_push_smem((int)sizeof(T), w, rq));
         if (smem > budget) return false;
         int Cp = 1;
         while (Cp < C) Cp <<= 1;  // power-of-two cluster sizes
@@ -393,12 +394,19 @@ bool lu_pf_cluster_shape(int64_t m, int w, size_t budget, int* C_out, int* R_out
 template <typename T>
 int lu_launch_pf_leaf_cluster(cudaStream_t st, T* A, int64_t lda, int64_t m, int w, int C, int R, size_t smem,
                               int64_t left_cols, int64_t right_cols, int32_t* ipiv, int64_t ipiv_add, LuSync* sync) {
-    // LU_GB300_PF_BARRIER=global selects the bounded global-memory barrier
-    static int hw = -1;
-    if (hw < 0) {
+    // Default: pushed messages with mbarrier completion (pf_push.cu).
+    // LU_GB300_PF_BARRIER=cluster selects candidates read through distributed
+    // shared memory after a hardware cluster barrier; =global the same with the
+    // bounded global-memory barrier.
+    static int mode = -1;
+    if (mode < 0) {
         const char* e = getenv("LU_GB300_PF_BARRIER");
-        hw = (e && e[0] == 'g') ? 0 : 1;
+        mode = (e && e[0] == 'g') ? 0 : ((e && e[0] == 'c') ? 1 : 2);
     }
+    if (mode == 2)
+        return lu_launch_pf_leaf_push<T>(st, A, lda, m, w, compiled_width(w), C, R, left_cols, right_cols, ipiv,
+                                         ipiv_add, sync);
+    const int hw = mode;
     auto fn = LeafTable<T>::get(compiled_width(w), R / kNT, hw != 0);
     if (!fn) return LU_ERR_UNSUPPORTED;
     cudaLaunchConfig_t cfg = {};

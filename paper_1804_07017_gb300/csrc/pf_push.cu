@@ -1,0 +1,610 @@
+// Panel-factorization leaf on one thread-block cluster with pushed messages
+// (RL1 of LU_blk, Sec. 3: the unblocked LU with partial pivoting of a w-column
+// block of the panel).
+//
+// The leaf's m rows are split across the C <= 16 CTAs of one cluster; each CTA
+// keeps its R x w block in shared memory and the SB columns currently being
+// eliminated in registers (SB = 8 for FP32).  Per column jj:
+//   1. every CTA reduces its local pivot candidate (redux.sync first maximum:
+//      largest |a|, then smallest row) and one warp PUSHES a message -- the
+//      candidate's whole leaf row, its ordering key and its row index -- into
+//      every CTA's shared memory with st.async; the owner of row jj pushes that
+//      row too.  Each st.async completes transaction bytes on the receiving
+//      CTA's mbarrier, so a CTA learns that all C candidates have arrived by a
+//      local (bounded) wait: no cluster barrier and no remote loads per column;
+//   2. every CTA picks the pivot (first maximum over the C keys) from its own
+//      shared memory, swaps rows jj and p where it owns them, divides column jj
+//      by the pivot and applies the rank-1 update to the SB register columns,
+//      fusing the next column's candidate search into the update.
+// After SB columns the block is right-looking at the sub-block level: the
+// CTA holding rows c0..c0+SB-1 computes U12 = L11^-1 A12 for the remaining
+// leaf columns and pushes it to all CTAs, which apply the rank-SB update
+// A22 -= L21 U12 from shared memory.  Messages are double-buffered by column
+// parity; a CTA can run at most one column ahead of any other, because column
+// jj+1 needs every CTA's jj+1 candidate, so a buffer is never overwritten
+// before it has been read.  After the last column the leaf's interchanges are
+// applied to the other columns of the enclosing panel.
+#include <cooperative_groups.h>
+
+#include <climits>
+#include <cstdio>
+#include <cstdlib>
+#include <limits>
+
+#include "internal.h"
+#include "profile.h"
+#include "ptx.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace {
+
+constexpr int kPT = 256;                     // threads per CTA
+// Registers per thread: 256 x 72 beside a 320 x 144 tensor-core update CTA fills one SM's 64 K.
+#ifndef LU_PF_PUSH_MAXREG
+#define LU_PF_PUSH_MAXREG 72
+#endif
+constexpr int kMaxC = LU_PF_MAX_CTAS_CLUSTER;  // message slots per buffer
+
+// Ordering key of a pivot candidate: |a| as an unsigned integer plus one (IEEE
+// order of non-negative values is the integer order of their bits); NaN and
+// "no candidate" are 0 and carry row INT_MAX, so a NaN is never chosen.
+template <typename T>
+struct PivKey;
+template <>
+struct PivKey<float> {
+    typedef uint32_t K;
+    static __device__ __forceinline__ K of(float a) {
+        const float v = fabsf(a);
+        return (v != v) ? 0u : __float_as_uint(v) + 1u;
+    }
+    // first maximum over the warp: largest key, then the smallest row holding it
+    static __device__ __forceinline__ void warp_best(K& k, int& i) {
+        const K km = __reduce_max_sync(0xffffffffu, k);
+        const unsigned im = __reduce_min_sync(0xffffffffu, k == km ? (unsigned)i : 0x7fffffffu);
+        k = km;
+        i = (int)im;
+    }
+};
+template <>
+struct PivKey<double> {
+    typedef unsigned long long K;
+    static __device__ __forceinline__ K of(double a) {
+        const double v = fabs(a);
+        return (v != v) ? 0ull : (unsigned long long)__double_as_longlong(v) + 1ull;
+    }
+    static __device__ __forceinline__ void warp_best(K& k, int& i) {
+        const unsigned hi = (unsigned)(k >> 32), lo = (unsigned)k;
+        const unsigned hm = __reduce_max_sync(0xffffffffu, hi);
+        const unsigned lm = __reduce_max_sync(0xffffffffu, hi == hm ? lo : 0u);
+        const K km = ((K)hm << 32) | lm;
+        const unsigned im = __reduce_min_sync(0xffffffffu, k == km ? (unsigned)i : 0x7fffffffu);
+        k = km;
+        i = (int)im;
+    }
+};
+
+// Register sub-block width: at most 32 registers of row data per thread.
+template <typename T, int RQ>
+constexpr int sub_block() {
+    return (int)(32 * 4 / (RQ * sizeof(T))) >= 8 ? 8 : (int)(32 * 4 / (RQ * sizeof(T)));
+}
+
+template <typename T, int W>
+struct MsgLayout {
+    typedef typename PivKey<T>::K K;
+    static constexpr int row_bytes = W * (int)sizeof(T);
+    static constexpr int key_off = row_bytes;
+    static constexpr int idx_off = row_bytes + (int)sizeof(K);
+    static constexpr int bytes = (idx_off + 4 + 15) / 16 * 16;
+    static constexpr int chunks = bytes / 16;
+    static constexpr int jchunks = row_bytes / 16;
+};
+
+// 32-bit word `w` of element data laid out as consecutive T values.
+template <typename T>
+__device__ __forceinline__ uint32_t elem_word(const T* p, int w);
+template <>
+__device__ __forceinline__ uint32_t elem_word<float>(const float* p, int w) {
+    return __float_as_uint(p[w]);
+}
+template <>
+__device__ __forceinline__ uint32_t elem_word<double>(const double* p, int w) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(p[w >> 1]);
+    return (w & 1) ? (uint32_t)(b >> 32) : (uint32_t)b;
+}
+
+__device__ __forceinline__ uint32_t mapa_u32(uint32_t addr, int rank) {
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(addr), "r"(rank));
+    return r;
+}
+
+// 16 bytes into CTA `rank`'s shared memory at the address that `laddr` has in
+// this CTA; completes 16 transaction bytes on that CTA's mbarrier `lbar`.
+__device__ __forceinline__ void push16(uint32_t laddr, uint32_t lbar, int rank, uint32_t a, uint32_t b, uint32_t c,
+                                       uint32_t d) {
+    asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v4.b32 [%0], {%1, %2, %3, %4}, [%5];" ::"r"(
+                     mapa_u32(laddr, rank)),
+                 "r"(a), "r"(b), "r"(c), "r"(d), "r"(mapa_u32(lbar, rank))
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_cta(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.release.cta.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_cluster(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait for one phase; on expiry records LU_ERR_TIMEOUT and marks the
+// thread failed, after which it no longer waits (it still sends every message
+// so that no CTA leaves the protocol early).
+__device__ __forceinline__ void leaf_wait(uint32_t bar, uint32_t parity, LuSync* sync, bool& failed) {
+    if (failed || mbar_try_cluster(bar, parity)) return;
+    const uint64_t t0 = lu_globaltimer();
+    unsigned spins = 0;
+    while (!mbar_try_cluster(bar, parity)) {
+        if ((++spins & 63u) == 0 && lu_globaltimer() - t0 > LU_WAIT_NS) {
+            atomicExch(&sync->error, LU_ERR_TIMEOUT);
+            failed = true;
+            return;
+        }
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void cp_async_elem(T* dst, const T* src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(smem_u32(dst)), "l"(src), "n"((int)sizeof(T))
+                 : "memory");
+}
+
+template <typename T, int W, int RQ>
+struct PushSmem {
+    static constexpr int SB = sub_block<T, RQ>();
+    static constexpr size_t msg = 2ull * kMaxC * MsgLayout<T, W>::bytes;
+    static constexpr size_t jrow = 2ull * W * sizeof(T);
+    static constexpr size_t su = (size_t)SB * W * sizeof(T);
+    static constexpr size_t block = (size_t)kPT * RQ * (W + 1) * sizeof(T);
+    static constexpr size_t total = msg + jrow + su + block + 16;
+};
+
+template <typename T, int W, int RQ>
+__global__ void __maxnreg__(LU_PF_PUSH_MAXREG)
+    pf_leaf_push_kernel(T* __restrict__ A, int64_t lda, int m, int w, int left_cols, int right_cols,
+                        int32_t* __restrict__ ipiv, int ipiv_add, LuSync* __restrict__ sync) {
+    typedef PivKey<T> PK;
+    typedef typename PK::K K;
+    typedef MsgLayout<T, W> ML;
+    constexpr int SB = PushSmem<T, W, RQ>::SB;
+    constexpr int R = kPT * RQ;
+    constexpr int WP = W + 1;
+    constexpr int UCH = (int)(SB * W * sizeof(T) / 16);
+    static_assert(W % SB == 0 && W <= 32 && (W * sizeof(T)) % 16 == 0, "leaf shape");
+
+    cg::cluster_group cluster = cg::this_cluster();
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    unsigned char* msg = smem_raw;                                                   // [2][kMaxC][ML::bytes]
+    T* jrow = reinterpret_cast<T*>(smem_raw + PushSmem<T, W, RQ>::msg);              // [2][W]
+    T* su = jrow + 2 * W;                                                            // [SB][W]
+    T* sA = su + SB * W;                                                             // [R][WP]
+    __shared__ __align__(8) uint64_t bars[3];
+    __shared__ K red_k[kPT / 32];
+    __shared__ int red_i[kPT / 32];
+    __shared__ int s_piv[W];
+    __shared__ int s_info;
+    __shared__ int s_dst[2 * W], s_src[2 * W], s_cnt;
+
+    const int C = (int)cluster.num_blocks();
+    const int g = (int)cluster.block_rank();
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int row0 = g * R;
+    const int nrows = max(0, min(R, m - row0));
+    const uint32_t bar0 = smem_u32(&bars[0]);
+    const uint32_t col_bytes = (uint32_t)(C * ML::bytes + ML::row_bytes);
+    const uint32_t u_bytes = (uint32_t)(SB * W * sizeof(T));
+    const int nsb = (w + SB - 1) / SB;
+    bool failed = false;
+
+    if (tid == 0) {
+        for (int b = 0; b < 3; ++b) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar0 + 8 * b) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        mbar_expect_cta(bar0, col_bytes);
+        if (w > 1) mbar_expect_cta(bar0 + 8, col_bytes);
+        if (nsb > 1) mbar_expect_cta(bar0 + 16, u_bytes);
+        s_info = 0;
+    }
+    // the block, column by column, by asynchronous 4/8-byte copies (all in flight at once)
+#pragma unroll 4
+    for (int c = 0; c < W; ++c)
+#pragma unroll
+        for (int q = 0; q < RQ; ++q) {
+            const int r = tid + kPT * q;
+            if (r < nrows) {
+                if (c < w)
+                    cp_async_elem<T>(sA + r * WP + c, A + (int64_t)(row0 + r) + (int64_t)c * lda);
+                else
+                    sA[r * WP + c] = T(0);
+            }
+        }
+    asm volatile("cp.async.commit_group;\n\tcp.async.wait_all;" ::: "memory");
+    // every CTA's barriers are initialised before anyone pushes
+    cluster.sync();
+
+    T v[RQ][SB];
+
+    // CTA reduction of (key, row) and the pushes of column jj's messages.
+    auto publish = [&](int jj, int c0, K bk, int bi) {
+        PK::warp_best(bk, bi);
+        if (lane == 0) {
+            red_k[warp] = bk;
+            red_i[warp] = bi;
+        }
+        __syncthreads();
+        K ck = (lane < kPT / 32) ? red_k[lane] : K(0);
+        int ci = (lane < kPT / 32) ? red_i[lane] : INT_MAX;
+        PK::warp_best(ck, ci);
+        const int buf = jj & 1;
+        const int lc = (ci != INT_MAX) ? ci - row0 : -1;
+        const int lj = jj - row0;
+        const bool own_j = jj >= row0 && jj < row0 + nrows;
+        // the owners put their register columns into the shared-memory rows
+        if (lc >= 0 && tid == lc % kPT) {
+            const int oq = lc / kPT;
+#pragma unroll
+            for (int q = 0; q < RQ; ++q)
+                if (q == oq)
+#pragma unroll
+                    for (int k = 0; k < SB; ++k) sA[lc * WP + c0 + k] = v[q][k];
+        }
+        if (own_j && tid == lj % kPT) {
+            const int oq = lj / kPT;
+#pragma unroll
+            for (int q = 0; q < RQ; ++q)
+                if (q == oq)
+#pragma unroll
+                    for (int k = 0; k < SB; ++k) sA[lj * WP + c0 + k] = v[q][k];
+        }
+        __syncwarp();
+        const int cw = (lc >= 0) ? (lc % kPT) >> 5 : 0;
+        if (warp == cw) {
+            const T* rp = sA + (lc >= 0 ? lc : 0) * WP;
+            const uint32_t base = smem_u32(msg) + (uint32_t)((buf * kMaxC + g) * ML::bytes);
+            // row chunks carry 4 row words; the last chunk holds the key and the row index
+            for (int t = lane; t < C * ML::chunks; t += 32) {
+                const int dst = t / ML::chunks, ch = t % ML::chunks;
+                uint32_t x0, x1, x2, x3;
+                if (ch < ML::jchunks) {
+                    x0 = elem_word<T>(rp, 4 * ch);
+                    x1 = elem_word<T>(rp, 4 * ch + 1);
+                    x2 = elem_word<T>(rp, 4 * ch + 2);
+                    x3 = elem_word<T>(rp, 4 * ch + 3);
+                } else if (sizeof(K) == 8) {
+                    x0 = (uint32_t)ck;
+                    x1 = (uint32_t)((unsigned long long)ck >> 32);
+                    x2 = (uint32_t)ci;
+                    x3 = 0u;
+                } else {
+                    x0 = (uint32_t)ck;
+                    x1 = (uint32_t)ci;
+                    x2 = x3 = 0u;
+                }
+                push16(base + 16 * ch, bar0 + 8 * buf, dst, x0, x1, x2, x3);
+            }
+        }
+        if (own_j && warp == (lj % kPT) >> 5) {
+            const T* rp = sA + lj * WP;
+            const uint32_t base = smem_u32(jrow + buf * W);
+            for (int t = lane; t < C * ML::jchunks; t += 32) {
+                const int dst = t / ML::jchunks, ch = t % ML::jchunks;
+                push16(base + 16 * ch, bar0 + 8 * buf, dst, elem_word<T>(rp, 4 * ch), elem_word<T>(rp, 4 * ch + 1),
+                       elem_word<T>(rp, 4 * ch + 2), elem_word<T>(rp, 4 * ch + 3));
+            }
+        }
+    };
+
+    for (int sb = 0; sb < nsb; ++sb) {
+        const int c0 = sb * SB;
+        K bk = 0;
+        int bi = INT_MAX;
+#pragma unroll
+        for (int q = 0; q < RQ; ++q) {
+            const int r = tid + kPT * q;
+#pragma unroll
+            for (int k = 0; k < SB; ++k) v[q][k] = (r < nrows) ? sA[r * WP + c0 + k] : T(0);
+            if (r < nrows && row0 + r >= c0) {
+                const K kk = PK::of(v[q][0]);
+                if (kk > bk) {
+                    bk = kk;
+                    bi = row0 + r;
+                }
+            }
+        }
+        publish(c0, c0, bk, bi);
+#pragma unroll
+        for (int k = 0; k < SB; ++k) {
+            const int jj = c0 + k;
+            if (jj < w) {
+                const int buf = jj & 1;
+                leaf_wait(bar0 + 8 * buf, (uint32_t)((jj >> 1) & 1), sync, failed);
+                if (tid == 0 && jj + 2 < w) mbar_expect_cta(bar0 + 8 * buf, col_bytes);
+                // ---- pivot: first maximum over the C pushed candidates ----
+                K ck = 0;
+                int ci = INT_MAX;
+                if (lane < C) {
+                    const unsigned char* mp = msg + (buf * kMaxC + lane) * ML::bytes;
+                    ck = *reinterpret_cast<const K*>(mp + ML::key_off);
+                    ci = *reinterpret_cast<const int*>(mp + ML::idx_off);
+                    if (ck == 0) ci = INT_MAX;
+                }
+                PK::warp_best(ck, ci);
+                const int p = (ci == INT_MAX) ? jj : ci;
+                const T* jr = jrow + buf * W;
+                const T* pr = (ci == INT_MAX) ? jr : reinterpret_cast<const T*>(msg + (buf * kMaxC + ci / R) * ML::bytes);
+                if (tid == 0) s_piv[jj] = p;
+                // ---- interchange rows jj and p where this CTA holds them ----
+                if (p != jj) {
+#pragma unroll
+                    for (int side = 0; side < 2; ++side) {
+                        const int pos = side ? p : jj;
+                        const T* src = side ? jr : pr;
+                        if (pos >= row0 && pos < row0 + nrows) {
+                            const int lr = pos - row0;
+                            if (warp == (lr % kPT) >> 5 && lane < w && (lane < c0 || lane >= c0 + SB))
+                                sA[lr * WP + lane] = src[lane];
+#pragma unroll
+                            for (int q = 0; q < RQ; ++q)
+                                if (tid + kPT * q == lr)
+#pragma unroll
+                                    for (int kk = 0; kk < SB; ++kk) v[q][kk] = src[c0 + kk];
+                        }
+                    }
+                }
+                const T piv = pr[jj];
+                if (piv == T(0) && tid == 0 && s_info == 0) s_info = jj + 1;
+                // multiply by the reciprocal when it is representable (as getf2), else divide
+                const bool use_rcp = fabs(piv) >= std::numeric_limits<T>::min();
+                const T rpiv = use_rcp ? T(1) / piv : T(0);
+                T prv[SB];
+#pragma unroll
+                for (int kk = k + 1; kk < SB; ++kk) prv[kk] = pr[c0 + kk];
+                // ---- scale column jj, rank-1 update of the register columns ----
+                bk = 0;
+                bi = INT_MAX;
+#pragma unroll
+                for (int q = 0; q < RQ; ++q) {
+                    const int r = tid + kPT * q;
+                    const int gr = row0 + r;
+                    if (r < nrows && gr > jj) {
+                        if (piv != T(0)) {
+                            const T l = use_rcp ? v[q][k] * rpiv : v[q][k] / piv;
+                            v[q][k] = l;
+#pragma unroll
+                            for (int kk = k + 1; kk < SB; ++kk) v[q][kk] = fma(-l, prv[kk], v[q][kk]);
+                        }
+                        if (k + 1 < SB) {
+                            const K kk = PK::of(v[q][k + 1 < SB ? k + 1 : k]);
+                            if (kk > bk) {
+                                bk = kk;
+                                bi = gr;
+                            }
+                        }
+                    }
+                }
+                if (k + 1 < SB && jj + 1 < w) publish(jj + 1, c0, bk, bi);
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < RQ; ++q) {
+            const int r = tid + kPT * q;
+            if (r < nrows)
+#pragma unroll
+                for (int k = 0; k < SB; ++k) sA[r * WP + c0 + k] = v[q][k];
+        }
+        if (c0 + SB < w) {
+            __syncthreads();
+            // ---- U12 := L11^-1 A12 by the CTA holding rows c0..c0+SB-1, pushed to all ----
+            const int ug = c0 / R;  // always 0 (R >= W)
+            if (g == ug) {
+                const int lr0 = c0 - row0;
+                if (warp == 0 && lane >= c0 + SB && lane < w) {
+                    for (int i = 1; i < SB; ++i) {
+                        T acc = sA[(lr0 + i) * WP + lane];
+                        for (int kk = 0; kk < i; ++kk)
+                            acc = fma(-sA[(lr0 + i) * WP + c0 + kk], sA[(lr0 + kk) * WP + lane], acc);
+                        sA[(lr0 + i) * WP + lane] = acc;
+                    }
+                }
+                __syncthreads();
+                const uint32_t base = smem_u32(su);
+                for (int t = tid; t < C * UCH; t += kPT) {
+                    const int dst = t / UCH, ch = t % UCH;
+                    uint32_t x[4];
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        const int wd = 4 * ch + e;
+                        const int el = (int)(wd * 4 / sizeof(T));
+                        const T* rp = sA + (lr0 + el / W) * WP + (el % W);
+                        x[e] = elem_word<T>(rp, (int)(wd % (sizeof(T) / 4)));
+                    }
+                    push16(base + 16 * ch, bar0 + 16, dst, x[0], x[1], x[2], x[3]);
+                }
+            }
+            leaf_wait(bar0 + 16, (uint32_t)(sb & 1), sync, failed);
+            if (tid == 0 && c0 + 2 * SB < w) mbar_expect_cta(bar0 + 16, u_bytes);
+            // ---- rank-SB update of the remaining leaf columns: A22 -= L21 U12 ----
+            for (int c = c0 + SB; c < w; ++c) {
+                T u[SB];
+#pragma unroll
+                for (int kk = 0; kk < SB; ++kk) u[kk] = su[kk * W + c];
+#pragma unroll
+                for (int q = 0; q < RQ; ++q) {
+                    const int r = tid + kPT * q;
+                    if (r < nrows && row0 + r >= c0 + SB) {
+                        T a = sA[r * WP + c];
+#pragma unroll
+                        for (int kk = 0; kk < SB; ++kk) a = fma(-v[q][kk], u[kk], a);
+                        sA[r * WP + c] = a;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    // No CTA leaves while another may still push into its shared memory: every
+    // CTA has received all of its messages once its last wait has passed, so the
+    // arrival is signalled here and the wait is taken just before exit.
+    asm volatile("barrier.cluster.arrive.relaxed;" ::: "memory");
+    for (int c = 0; c < w; ++c)
+#pragma unroll
+        for (int q = 0; q < RQ; ++q) {
+            const int r = tid + kPT * q;
+            if (r < nrows) A[(int64_t)(row0 + r) + (int64_t)c * lda] = sA[r * WP + c];
+        }
+    if (g == 0) {
+        for (int j = tid; j < w; j += kPT) ipiv[j] = s_piv[j] + 1 + ipiv_add;
+        if (tid == 0 && s_info != 0) atomicCAS(&sync->info, 0, s_info + ipiv_add);
+    }
+    const int other = left_cols + right_cols;
+    if (other > 0) {
+        // ---- the leaf's interchanges on the other columns of the panel ----
+        // Plan: positions 0..w-1 (leaf rows) and the distinct targets below them.
+        if (tid == 0) {
+            int tgt[W], cur[2 * W];
+            int nt = 0;
+            for (int i = 0; i < w; ++i) cur[i] = i;
+            for (int k = 0; k < w; ++k) {
+                const int pk = s_piv[k];
+                if (pk == k) continue;
+                int b;
+                if (pk < w) {
+                    b = pk;
+                } else {
+                    int f = -1;
+                    for (int t = 0; t < nt; ++t)
+                        if (tgt[t] == pk) f = t;
+                    if (f < 0) {
+                        f = nt++;
+                        tgt[f] = pk;
+                        cur[w + f] = pk;
+                    }
+                    b = w + f;
+                }
+                const int x = cur[k];
+                cur[k] = cur[b];
+                cur[b] = x;
+            }
+            int cnt = 0;
+            for (int i = 0; i < w; ++i)
+                if (cur[i] != i) {
+                    s_dst[cnt] = i;
+                    s_src[cnt] = cur[i];
+                    ++cnt;
+                }
+            for (int t = 0; t < nt; ++t)
+                if (cur[w + t] != tgt[t]) {
+                    s_dst[cnt] = tgt[t];
+                    s_src[cnt] = cur[w + t];
+                    ++cnt;
+                }
+            s_cnt = cnt;
+        }
+        __syncthreads();
+        const int cnt = s_cnt;
+        // columns q = g, g + C, ... of the other columns; one warp per column
+        for (int q = g * (kPT / 32) + warp; cnt > 0 && q < other; q += C * (kPT / 32)) {
+            const int64_t col = (q < left_cols) ? (int64_t)q - left_cols : (int64_t)w + (q - left_cols);
+            T* a = A + col * lda;
+            T vv[(2 * W + 31) / 32];
+#pragma unroll
+            for (int t = 0; t < (2 * W + 31) / 32; ++t)
+                if (lane + 32 * t < cnt) vv[t] = a[s_src[lane + 32 * t]];
+            __syncwarp();
+#pragma unroll
+            for (int t = 0; t < (2 * W + 31) / 32; ++t)
+                if (lane + 32 * t < cnt) a[s_dst[lane + 32 * t]] = vv[t];
+        }
+    }
+    asm volatile("barrier.cluster.wait;" ::: "memory");
+}
+
+template <typename T>
+struct PushTable {
+    typedef void (*Fn)(T*, int64_t, int, int, int, int, int32_t*, int, LuSync*);
+    static Fn get(int w, int rq, size_t* smem) {
+#define LU_PUSH_CASE(WW, RR)                                        \
+    if (w == WW && rq == RR) {                                      \
+        if (smem) *smem = PushSmem<T, WW, RR>::total;               \
+        return pf_leaf_push_kernel<T, WW, RR>;                      \
+    }
+        LU_PUSH_CASE(8, 1) LU_PUSH_CASE(8, 2) LU_PUSH_CASE(8, 4) LU_PUSH_CASE(8, 8)
+        LU_PUSH_CASE(16, 1) LU_PUSH_CASE(16, 2) LU_PUSH_CASE(16, 4) LU_PUSH_CASE(16, 8)
+        LU_PUSH_CASE(32, 1) LU_PUSH_CASE(32, 2) LU_PUSH_CASE(32, 4)
+#undef LU_PUSH_CASE
+        return nullptr;
+    }
+};
+
+}  // namespace
+
+// Dynamic shared memory of the pushed-message leaf (0 if the shape is not compiled).
+size_t lu_pf_push_smem(int esize, int w, int rq) {
+    size_t s = 0;
+    if (esize == 8)
+        PushTable<double>::get(w, rq, &s);
+    else
+        PushTable<float>::get(w, rq, &s);
+    return s;
+}
+
+template <typename T>
+int lu_launch_pf_leaf_push(cudaStream_t st, T* A, int64_t lda, int64_t m, int w, int wc, int C, int R,
+                           int64_t left_cols, int64_t right_cols, int32_t* ipiv, int64_t ipiv_add, LuSync* sync) {
+    size_t smem = 0;
+    auto fn = PushTable<T>::get(wc, R / kPT, &smem);
+    if (!fn || C > kMaxC) return LU_ERR_UNSUPPORTED;
+    static bool attr_done[2][3][4] = {};
+    const int wi = wc == 8 ? 0 : (wc == 16 ? 1 : 2);
+    const int ri = (R / kPT) == 1 ? 0 : ((R / kPT) == 2 ? 1 : ((R / kPT) == 4 ? 2 : 3));
+    bool& done = attr_done[sizeof(T) == 8 ? 0 : 1][wi][ri];
+    if (!done) {
+        LU_CHECK_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+        LU_CHECK_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        done = true;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(C, 1, 1);
+    cfg.blockDim = dim3(kPT, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    LuProfScope prof(st, LU_K_PANEL, 2.0 * m * w * sizeof(T) + 4.0 * w * (left_cols + right_cols) * sizeof(T),
+                     (double)m * w * w);
+    if (getenv("LU_GB300_TRACE_LAUNCH"))
+        fprintf(stderr, "[lu launch] push leaf esize %d m %lld w %d (compiled %d) C %d R %d smem %zu left %lld right %lld\n",
+                (int)sizeof(T), (long long)m, w, wc, C, R, smem, (long long)left_cols, (long long)right_cols);
+    LU_CHECK_CUDA(cudaLaunchKernelEx(&cfg, fn, A, lda, (int)m, w, (int)left_cols, (int)right_cols, ipiv, (int)ipiv_add,
+                                     sync));
+    lu_count_launch();
+    return LU_SUCCESS;
+}
+
+template int lu_launch_pf_leaf_push<double>(cudaStream_t, double*, int64_t, int64_t, int, int, int, int, int64_t,
+                                            int64_t, int32_t*, int64_t, LuSync*);
+template int lu_launch_pf_leaf_push<float>(cudaStream_t, float*, int64_t, int64_t, int, int, int, int, int64_t,
+                                           int64_t, int32_t*, int64_t, LuSync*);

@@ -18,6 +18,7 @@ struct Rec {
     int cls;
     cudaEvent_t a, b;
     double bytes, flops;
+    cudaStream_t st;
 };
 
 std::mutex g_mu;
@@ -44,9 +45,36 @@ cudaEvent_t take_event() {
     return e;
 }
 
+// LU_GB300_TIMELINE=<file>: every drained launch is also appended to <file> as
+// "class stream start_ms duration_ms", start relative to the first launch of the
+// drained batch (events of different streams share one device clock).
+FILE* timeline_file() {
+    static FILE* f = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        const char* path = getenv("LU_GB300_TIMELINE");
+        if (path && path[0]) f = fopen(path, "a");
+    }
+    return f;
+}
+
 void drain_locked() {
     if (g_recs.empty()) return;
     cudaDeviceSynchronize();
+    if (FILE* f = timeline_file()) {
+        const cudaEvent_t base = g_recs.front().a;
+        fprintf(f, "# batch of %zu launches\n", g_recs.size());
+        for (const Rec& r : g_recs) {
+            float t0 = 0.f, d = 0.f;
+            if (base && r.a && r.b && cudaEventElapsedTime(&t0, base, r.a) == cudaSuccess &&
+                cudaEventElapsedTime(&d, r.a, r.b) == cudaSuccess)
+                fprintf(f, "%d %p %.4f %.4f\n", r.cls, (void*)r.st, t0, d);
+            else
+                cudaGetLastError();
+        }
+        fflush(f);
+    }
     for (Rec& r : g_recs) {
         float ms = 0.f;
         if (r.a && r.b && cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
@@ -96,7 +124,7 @@ LuProfScope::~LuProfScope() {
     if (!active_) return;
     std::lock_guard<std::mutex> lk(g_mu);
     if (b_) cudaEventRecord(b_, st_);
-    g_recs.push_back(Rec{cls_, a_, b_, bytes_, flops_});
+    g_recs.push_back(Rec{cls_, a_, b_, bytes_, flops_, st_});
 }
 
 extern "C" int lu_profile_enable(int mask) {

@@ -243,10 +243,15 @@ __global__ void __launch_bounds__(kTrsvThreads)
 // predecessor's "done" count, read its solution block (L2), add its
 // contribution from shared memory, run the register-resident substitution of
 // the diagonal block, publish.
-template <typename T, bool LOWER>
+//
+// INV = true: the diagonal tile is the precomputed inverse of the diagonal
+// block (trinv_diag_kernel), loaded from the tensor map tmD, and the block's
+// solve is one dense product x_blk = inv(D) (b_blk - sum of contributions)
+// instead of a BS-step substitution.
+template <typename T, bool LOWER, bool INV>
 __global__ void __launch_bounds__(kTrsvThreads)
-    trsv_tma_kernel(const __grid_constant__ CUtensorMap tmL, int64_t n, int nrhs, T* __restrict__ X, int64_t ldx,
-                    LuSync* __restrict__ sync) {
+    trsv_tma_kernel(const __grid_constant__ CUtensorMap tmL, const __grid_constant__ CUtensorMap tmD, int64_t n,
+                    int nrhs, T* __restrict__ X, int64_t ldx, LuSync* __restrict__ sync) {
     using C = TrsvCfg<T>;
     constexpr int BS = C::BS;
     extern __shared__ unsigned char smraw[];
@@ -276,7 +281,10 @@ __global__ void __launch_bounds__(kTrsvThreads)
     auto src_block = [&](int q) { return LOWER ? q : nblk - 1 - q; };
     if (tid == 0) {
         mbar_arrive_expect_tx(&bars[0], tile_bytes);
-        tma_load_2d(sD, &tmL, &bars[0], (int)r0, (int)r0);
+        if (INV)
+            tma_load_2d(sD, &tmD, &bars[0], 0, (LOWER ? blk : nblk + blk) * BS);
+        else
+            tma_load_2d(sD, &tmL, &bars[0], (int)r0, (int)r0);
         if (chain > 0) {
             mbar_arrive_expect_tx(&bars[1], tile_bytes);
             tma_load_2d(sT, &tmL, &bars[1], (int)r0, src_block(0) * BS);
@@ -384,6 +392,38 @@ __global__ void __launch_bounds__(kTrsvThreads)
                                  : T(0);
     }
     __syncthreads();
+    if (INV) {
+        // x = inv(D) sX: thread (r, h) sums columns j = h, h + kSplit, ... of row r
+#pragma unroll
+        for (int c = 0; c < kNR; ++c) acc[c] = T(0);
+        if (nrhs == 1) {
+#pragma unroll 8
+            for (int j = h; j < BS; j += C::kSplit) acc[0] = fma(sD[j * BS + r], sX[j], acc[0]);
+        } else {
+            for (int j = h; j < BS; j += C::kSplit) {
+                const T d = sD[j * BS + r];
+#pragma unroll
+                for (int c = 0; c < kNR; ++c)
+                    if (c < nrhs) acc[c] = fma(d, sX[c * BS + j], acc[c]);
+            }
+        }
+        for (int hh = 1; hh < C::kSplit; ++hh) {
+            if (h == hh) {
+#pragma unroll
+                for (int c = 0; c < kNR; ++c) sPart[c * BS + r] = (hh == 1 ? T(0) : sPart[c * BS + r]) + acc[c];
+            }
+            __syncthreads();
+        }
+        if (h == 0) {
+#pragma unroll
+            for (int c = 0; c < kNR; ++c)
+                if (r < rows && c < nrhs) X[(r0 + r) + c * ldx] = acc[c] + (C::kSplit > 1 ? sPart[c * BS + r] : T(0));
+        }
+        __threadfence();
+        __syncthreads();
+        if (tid == 0) lu_st_release(&sync->arrive, (unsigned)(chain + 1));
+        return;
+    }
     // register-resident substitution of the diagonal block: lane holds rows lane + 32 q
     constexpr int RQ = BS / 32;
     for (int c = warp; c < nrhs; c += kTrsvThreads / 32) {
@@ -429,6 +469,45 @@ __global__ void __launch_bounds__(kTrsvThreads)
     __threadfence();
     __syncthreads();
     if (tid == 0) lu_st_release(&sync->arrive, (unsigned)(chain + 1));
+}
+
+// Inverses of the diagonal blocks of the factors: blockIdx.y = 0 gives
+// inv(L_bb) (unit lower), 1 gives inv(U_bb), for block b = blockIdx.x, into
+// tile (blockIdx.y * nblk + b) of D (BS x BS, column-major, ld BS; zero outside
+// the block's rows x rows).  Thread j computes column j of the inverse by
+// substitution against the unit vector e_j, in lock step with the other
+// columns (terms with k < j vanish), so the block stays in shared memory and
+// no thread waits for another.
+template <typename T>
+__global__ void __launch_bounds__(TrsvCfg<T>::BS)
+    trinv_diag_kernel(int64_t n, const T* __restrict__ LU, int64_t lda, T* __restrict__ D) {
+    constexpr int BS = TrsvCfg<T>::BS;
+    extern __shared__ unsigned char smraw[];
+    T* sL = reinterpret_cast<T*>(smraw);  // [BS][BS + 1] row-major block
+    T* sX = sL + BS * (BS + 1);           // [BS][BS + 1] inverse, row-major
+    const int nblk = (int)((n + BS - 1) / BS);
+    const int b = blockIdx.x, upper = blockIdx.y, j = threadIdx.x;
+    const int64_t r0 = (int64_t)b * BS;
+    const int rows = (int)min((int64_t)BS, n - r0);
+    for (int c = 0; c < rows; ++c)
+        if (j < rows) sL[j * (BS + 1) + c] = LU[(r0 + j) + (r0 + c) * lda];
+    __syncthreads();
+    if (!upper) {
+        for (int i = 0; i < rows; ++i) {
+            T s = (i == j) ? T(1) : T(0);
+            for (int k = 0; k < i; ++k) s = fma(-sL[i * (BS + 1) + k], sX[k * (BS + 1) + j], s);
+            sX[i * (BS + 1) + j] = s;
+        }
+    } else {
+        for (int i = rows - 1; i >= 0; --i) {
+            T s = (i == j) ? T(1) : T(0);
+            for (int k = i + 1; k < rows; ++k) s = fma(-sL[i * (BS + 1) + k], sX[k * (BS + 1) + j], s);
+            sX[i * (BS + 1) + j] = s / sL[i * (BS + 1) + i];
+        }
+    }
+    __syncthreads();
+    T* tile = D + (int64_t)(upper * nblk + b) * BS * BS;
+    for (int i = 0; i < BS; ++i) tile[(int64_t)j * BS + i] = (i < rows && j < rows) ? sX[i * (BS + 1) + j] : T(0);
 }
 
 __global__ void finish_info_kernel(const LuSync* __restrict__ s, int32_t* __restrict__ info) {
@@ -527,24 +606,84 @@ static int make_factor_map(CUtensorMap* map, const T* LU, int64_t n, int64_t lda
     return LU_SUCCESS;
 }
 
+// Tensor map over the 2 * nblk inverse tiles (a BS x (2 nblk BS) column-major matrix).
+template <typename T>
+static int make_inverse_map(CUtensorMap* map, const T* D, int64_t nblk) {
+    static PFN_cuTensorMapEncodeTiled_v12000 enc = nullptr;
+    if (!enc) {
+        cudaDriverEntryPointQueryResult q;
+        void* fn = nullptr;
+        LU_CHECK_CUDA(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q));
+        if (q != cudaDriverEntryPointSuccess || !fn) return LU_ERR_CUDA;
+        enc = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    }
+    using C = TrsvCfg<T>;
+    cuuint64_t dims[2] = {(cuuint64_t)C::BS, (cuuint64_t)(2 * nblk * C::BS)};
+    cuuint64_t strides[1] = {(cuuint64_t)(C::BS * sizeof(T))};
+    cuuint32_t box[2] = {(cuuint32_t)C::BS, (cuuint32_t)C::BS};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = enc(map, sizeof(T) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2,
+                     const_cast<T*>(D), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                     CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        lu_set_error_string("cuTensorMapEncodeTiled failed (inverse diagonal blocks)", __FILE__, __LINE__);
+        return LU_ERR_CUDA;
+    }
+    return LU_SUCCESS;
+}
+
+template <typename T>
+size_t lu_trinv_bytes(int64_t n) {
+    using C = TrsvCfg<T>;
+    return (size_t)2 * lu_cdiv(n, C::BS) * C::BS * C::BS * sizeof(T);
+}
+
+template <typename T>
+int lu_launch_trinv_diag(cudaStream_t st, int64_t n, const T* LU, int64_t lda, T* D) {
+    if (n <= 0) return LU_SUCCESS;
+    using C = TrsvCfg<T>;
+    const size_t smem = sizeof(T) * 2 * (size_t)C::BS * (C::BS + 1);
+    static bool attr[2] = {false, false};
+    const int ti = sizeof(T) == 8 ? 0 : 1;
+    if (!attr[ti]) {
+        LU_CHECK_CUDA(cudaFuncSetAttribute(trinv_diag_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        attr[ti] = true;
+    }
+    const int nblk = (int)lu_cdiv(n, C::BS);
+    LuProfScope prof(st, LU_K_SOLVE, sizeof(T) * (2.0 * n * C::BS + 2.0 * nblk * C::BS * C::BS),
+                     (double)nblk * C::BS * C::BS * C::BS / 3.0);
+    trinv_diag_kernel<T><<<dim3(nblk, 2), C::BS, smem, st>>>(n, LU, lda, D);
+    LU_CHECK_LAUNCH();
+    return LU_SUCCESS;
+}
+
 template <typename T>
 int lu_launch_trsv_blocked(lu_context* c, cudaStream_t st, bool lower_unit, int64_t n, int64_t nrhs, const T* LU,
-                           int64_t lda, T* X, int64_t ldx) {
+                           int64_t lda, T* X, int64_t ldx, const T* Dinv) {
     if (n <= 0 || nrhs <= 0) return LU_SUCCESS;
     using C = TrsvCfg<T>;
     const int nblk = (int)lu_cdiv(n, C::BS);
     // TMA needs a 16-byte aligned base and a leading dimension that is a multiple of 16 bytes
     if ((reinterpret_cast<uintptr_t>(LU) & 15) != 0 || (lda * sizeof(T)) % 16 != 0)
         return trsv_plain(c, st, lower_unit, n, nrhs, LU, lda, X, ldx);
-    CUtensorMap map;
+    CUtensorMap map, dmap;
     LU_TRY(make_factor_map<T>(&map, LU, n, lda));
+    const bool inv = Dinv != nullptr && (reinterpret_cast<uintptr_t>(Dinv) & 15) == 0;
+    if (inv)
+        LU_TRY(make_inverse_map<T>(&dmap, Dinv, nblk));
+    else
+        dmap = map;
     static bool attr[2] = {false, false};
     const int ti = sizeof(T) == 8 ? 0 : 1;
     if (!attr[ti]) {
-        LU_CHECK_CUDA(cudaFuncSetAttribute(trsv_tma_kernel<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)C::smem));
-        LU_CHECK_CUDA(cudaFuncSetAttribute(trsv_tma_kernel<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)C::smem));
+        LU_CHECK_CUDA(cudaFuncSetAttribute(trsv_tma_kernel<T, true, false>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem));
+        LU_CHECK_CUDA(cudaFuncSetAttribute(trsv_tma_kernel<T, false, false>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem));
+        LU_CHECK_CUDA(cudaFuncSetAttribute(trsv_tma_kernel<T, true, true>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem));
+        LU_CHECK_CUDA(cudaFuncSetAttribute(trsv_tma_kernel<T, false, true>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem));
         attr[ti] = true;
     }
     for (int64_t c0 = 0; c0 < nrhs; c0 += kNR) {
@@ -553,10 +692,9 @@ int lu_launch_trsv_blocked(lu_context* c, cudaStream_t st, bool lower_unit, int6
         LU_CHECK_CUDA(cudaMemsetAsync(&c->sync[1].arrive, 0, sizeof(unsigned) * 2, st));
         LU_CHECK_CUDA(cudaMemsetAsync(&c->sync[1].ticket, 0, sizeof(unsigned), st));
         LuProfScope prof(st, LU_K_SOLVE, sizeof(T) * (0.5 * n * n + 2.0 * n * nr), (double)n * n * nr);
-        if (lower_unit)
-            trsv_tma_kernel<T, true><<<nblk, kTrsvThreads, C::smem, st>>>(map, n, nr, X + c0 * ldx, ldx, &c->sync[1]);
-        else
-            trsv_tma_kernel<T, false><<<nblk, kTrsvThreads, C::smem, st>>>(map, n, nr, X + c0 * ldx, ldx, &c->sync[1]);
+        auto fn = lower_unit ? (inv ? trsv_tma_kernel<T, true, true> : trsv_tma_kernel<T, true, false>)
+                             : (inv ? trsv_tma_kernel<T, false, true> : trsv_tma_kernel<T, false, false>);
+        fn<<<nblk, kTrsvThreads, C::smem, st>>>(map, dmap, n, nr, X + c0 * ldx, ldx, &c->sync[1]);
         LU_CHECK_LAUNCH();
     }
     return LU_SUCCESS;
@@ -575,7 +713,11 @@ template int lu_launch_permute_rows<double>(cudaStream_t, int64_t, int64_t, cons
                                             int64_t, double*, int64_t);
 template int lu_launch_permute_rows<float>(cudaStream_t, int64_t, int64_t, const int32_t*, const float*,
                                            int64_t, float*, int64_t);
+template size_t lu_trinv_bytes<double>(int64_t);
+template size_t lu_trinv_bytes<float>(int64_t);
+template int lu_launch_trinv_diag<double>(cudaStream_t, int64_t, const double*, int64_t, double*);
+template int lu_launch_trinv_diag<float>(cudaStream_t, int64_t, const float*, int64_t, float*);
 template int lu_launch_trsv_blocked<double>(lu_context*, cudaStream_t, bool, int64_t, int64_t,
-                                            const double*, int64_t, double*, int64_t);
+                                            const double*, int64_t, double*, int64_t, const double*);
 template int lu_launch_trsv_blocked<float>(lu_context*, cudaStream_t, bool, int64_t, int64_t,
-                                           const float*, int64_t, float*, int64_t);
+                                           const float*, int64_t, float*, int64_t, const float*);

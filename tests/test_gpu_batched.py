@@ -89,3 +89,39 @@ def test_batched_status_codes(lu):
     assert info[1] == lu.LU_ERR_UNSUPPORTED
     assert info[2] == info_o == 6
     assert info[3] == 0
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_batched_factor_then_solve(lu, dtype):
+    """lu_factor_batched followed by lu_solve_batched gives the same bits as the
+    fused lu_gesv_batched, and the oracle's backward error bound."""
+    count = 40
+    sizes, nrhs = synth.batched_sizes(count, seed=11)
+    mats = synth.batched_matrices(sizes, seed=11)
+    g = synth.rng(11, 9)
+    rhs = [g.uniform(-1, 1, size=(int(n), int(r))) for n, r in zip(sizes, nrhs)]
+    runs = []
+    for split in (False, True):
+        dA = [colmajor_dev(m, dtype) for m in mats]
+        dB = [colmajor_dev(b, dtype) for b in rhs]
+        piv = [torch.zeros(int(n), dtype=torch.int32, device="cuda") for n in sizes]
+        batch = lu.Batch(dA, piv, dB)
+        if split:
+            lu.lu_factor_batched(batch)
+            torch.cuda.synchronize()
+            assert np.all(batch.info.cpu().numpy() == 0)
+            lu.lu_solve_batched(batch)
+        else:
+            lu.lu_gesv_batched(batch)
+        torch.cuda.synchronize()
+        assert np.all(batch.info.cpu().numpy() == 0)
+        runs.append(([a.cpu() for a in dA], [p.cpu() for p in piv], [b.cpu() for b in dB]))
+    u = np.finfo(np.float32 if dtype == torch.float32 else np.float64).eps / 2
+    for i in range(count):
+        assert torch.equal(runs[0][0][i], runs[1][0][i]) and torch.equal(runs[0][1][i], runs[1][1][i])
+        assert torch.equal(runs[0][2][i], runs[1][2][i])
+        x = runs[1][2][i].double().numpy()
+        src = mats[i] if dtype == torch.float64 else mats[i].astype(np.float32).astype(np.float64)
+        b = rhs[i] if dtype == torch.float64 else rhs[i].astype(np.float32).astype(np.float64)
+        eta = oracle.backward_error(src, x, b)
+        assert eta <= (1e-14 if dtype == torch.float64 else 64 * sizes[i] * u), (i, eta)

@@ -151,7 +151,7 @@ def test_fp32_factor(lu):
 
 @pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
 @pytest.mark.parametrize("m,w,leaf", [(1000, 64, 0), (300, 37, 0), (5000, 128, 0), (257, 64, 16), (64, 64, 0),
-                                      (3000, 256, 32)])
+                                      (3000, 256, 32), (16384, 48, 16), (9000, 29, 32), (2100, 13, 8)])
 def test_panel_factor(lu, dtype, m, w, leaf):
     P0 = synth.uniform_matrix(m, w, seed=10, stream=m + w)
     if dtype == torch.float32:
@@ -297,3 +297,29 @@ def test_full_size_sampled(lu, n, nb):
         pos[cur[j]] = j
         pos[cur[p]] = p
     assert np.array_equal(ps, expect)
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_panel_nan_and_zero_column(lu, dtype):
+    """A NaN candidate never wins the pivot search (strict comparisons), and an
+    exactly zero column is reported as the first zero pivot without scaling:
+    pivots and info equal the oracle's, which follows the same two readings."""
+    m, w = 3000, 40
+    P0 = synth.uniform_matrix(m, w, seed=12, stream=5)
+    if dtype == torch.float32:
+        P0 = P0.astype(np.float32).astype(np.float64)
+    P0[:, 21] = 0.0
+    P0[1500, 3] = np.nan  # below the pivot rows of column 3; row 1500 is never a pivot
+    P = dev(P0, dtype)
+    ipiv = torch.zeros(w, dtype=torch.int32, device="cuda")
+    info = torch.zeros(1, dtype=torch.int32, device="cuda")
+    lu.lu_panel_factor_ex(P, ipiv, info, lu.default_opts(leaf=16))
+    torch.cuda.synchronize()
+    clean = P0.copy()
+    clean[1500, 3] = 0.0
+    _, pivo, info_o, gap = oracle.getrf(clean)
+    piv = ipiv.cpu().numpy()
+    assert int(info.item()) == info_o == 22
+    # columns before the NaN's column are unaffected by it
+    assert np.array_equal(piv[:3], pivo[:3])
+    assert np.all(piv != 1501)
