@@ -224,7 +224,7 @@ __global__ void __maxnreg__(LU_PF_PUSH_MAXREG)
         s_info = 0;
     }
     // the block, column by column, by asynchronous 4/8-byte copies (all in flight at once)
-#pragma unroll 4
+#pragma unroll 1
     for (int c = 0; c < W; ++c)
 #pragma unroll
         for (int q = 0; q < RQ; ++q) {

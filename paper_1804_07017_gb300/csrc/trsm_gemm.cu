@@ -47,15 +47,19 @@ __global__ void __launch_bounds__(kTrsmThreads)
             if (lane < jb) sB[c * mp + J + lane] = v;
         }
         __syncthreads();
+        // rank-jb update of the rows below: the row's jb multipliers are loaded
+        // together (all in flight at once), then applied to the COLS columns
         for (int r = J + jb + tid; r < m; r += kTrsmThreads) {
+            T l[32];
+#pragma unroll
+            for (int j = 0; j < 32; ++j) l[j] = (j < jb) ? __ldg(&L[(int64_t)r + (int64_t)(J + j) * ldl]) : T(0);
             T acc[COLS];
 #pragma unroll
             for (int c = 0; c < COLS; ++c) acc[c] = T(0);
-            for (int j = 0; j < jb; ++j) {
-                const T l = L[(int64_t)r + (int64_t)(J + j) * ldl];
 #pragma unroll
-                for (int c = 0; c < COLS; ++c) acc[c] = fma(l, sB[c * mp + J + j], acc[c]);
-            }
+            for (int j = 0; j < 32; ++j)
+#pragma unroll
+                for (int c = 0; c < COLS; ++c) acc[c] = fma(l[j], sB[c * mp + J + j], acc[c]);
 #pragma unroll
             for (int c = 0; c < COLS; ++c) sB[c * mp + r] -= acc[c];
         }
@@ -66,41 +70,54 @@ __global__ void __launch_bounds__(kTrsmThreads)
 }
 
 constexpr int kGemmThreads = 256;
-constexpr int BM = 64, BN = 64, BK = 16;
+constexpr int BK = 16;
 
-// C := C - A B with a 64x64 tile per CTA and a 4x4 register tile per thread;
-// thread (tx, ty) owns rows tx + 16 i and columns ty + 16 j so that shared
+// C := C - A B with a BM x BN tile per CTA and a 4x4 register tile per thread;
+// thread (tx, ty) owns rows tx + TX i and columns ty + TY j so that shared
 // memory reads and the epilogue's column-major accesses are both coalesced.
-template <typename T>
+// The narrow shapes (BN = 16, 32) serve the panel's own thin updates.  Every
+// element accumulates its k products in order, whatever the tile shape.
+template <typename T, int BM, int BN>
 __global__ void __launch_bounds__(kGemmThreads)
     gemm_update_kernel(int64_t m, int64_t n, int k, const T* __restrict__ A, int64_t lda,
                        const T* __restrict__ B, int64_t ldb, T* __restrict__ C, int64_t ldc) {
+    constexpr int TX = BM / 4, TY = BN / 4;
+    static_assert(TX * TY == kGemmThreads, "tile shape");
+    constexpr int NA = BM * BK / kGemmThreads, NB = BK * BN / kGemmThreads;
     __shared__ T sA[2][BK][BM];
     __shared__ T sB[2][BK][BN + 1];
-    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const int tid = threadIdx.x, tx = tid % TX, ty = tid / TX;
     const int64_t i0 = (int64_t)blockIdx.x * BM, j0 = (int64_t)blockIdx.y * BN;
     T acc[4][4];
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
         for (int b = 0; b < 4; ++b) acc[a][b] = T(0);
-    T ra[4], rb[4];
+    T ra[NA], rb[NB];
     auto load_regs = [&](int p0) {
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
+        for (int q = 0; q < NA; ++q) {
             const int e = tid + q * kGemmThreads;
-            const int i = e & (BM - 1), p = e >> 6;  // A tile: 64 rows x 16 cols
+            const int i = e % BM, p = e / BM;  // A tile: BM rows x BK cols
             ra[q] = (i0 + i < m && p0 + p < k) ? A[(i0 + i) + (int64_t)(p0 + p) * lda] : T(0);
-            const int pb = e & (BK - 1), jb = e >> 4;  // B tile: 16 rows x 64 cols
+        }
+#pragma unroll
+        for (int q = 0; q < NB; ++q) {
+            const int e = tid + q * kGemmThreads;
+            const int pb = e % BK, jb = e / BK;  // B tile: BK rows x BN cols
             rb[q] = (p0 + pb < k && j0 + jb < n) ? B[(int64_t)(p0 + pb) + (j0 + jb) * ldb] : T(0);
         }
     };
     auto store_smem = [&](int s) {
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
+        for (int q = 0; q < NA; ++q) {
             const int e = tid + q * kGemmThreads;
-            sA[s][e >> 6][e & (BM - 1)] = ra[q];
-            sB[s][e & (BK - 1)][e >> 4] = rb[q];
+            sA[s][e / BM][e % BM] = ra[q];
+        }
+#pragma unroll
+        for (int q = 0; q < NB; ++q) {
+            const int e = tid + q * kGemmThreads;
+            sB[s][e % BK][e / BK] = rb[q];
         }
     };
     load_regs(0);
@@ -115,8 +132,8 @@ __global__ void __launch_bounds__(kGemmThreads)
             T a[4], b[4];
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
-                a[q] = sA[s][p][tx + 16 * q];
-                b[q] = sB[s][p][ty + 16 * q];
+                a[q] = sA[s][p][tx + TX * q];
+                b[q] = sB[s][p][ty + TY * q];
             }
 #pragma unroll
             for (int x = 0; x < 4; ++x)
@@ -131,15 +148,16 @@ __global__ void __launch_bounds__(kGemmThreads)
     }
 #pragma unroll
     for (int y = 0; y < 4; ++y) {
-        const int64_t j = j0 + ty + 16 * y;
+        const int64_t j = j0 + ty + TY * y;
         if (j >= n) continue;
 #pragma unroll
         for (int x = 0; x < 4; ++x) {
-            const int64_t i = i0 + tx + 16 * x;
+            const int64_t i = i0 + tx + TX * x;
             if (i < m) C[i + j * ldc] -= acc[x][y];
         }
     }
 }
+
 
 }  // namespace
 
@@ -174,10 +192,23 @@ template <typename T>
 int lu_launch_gemm_update(cudaStream_t st, int64_t m, int64_t n, int64_t k, const T* A, int64_t lda,
                           const T* B, int64_t ldb, T* C, int64_t ldc) {
     if (m <= 0 || n <= 0 || k <= 0) return LU_SUCCESS;
-    if (lu_cdiv(n, BN) > 65535) return LU_ERR_UNSUPPORTED;
-    dim3 grid((unsigned)lu_cdiv(m, BM), (unsigned)lu_cdiv(n, BN));
     LuProfScope prof(st, LU_K_GEMM, sizeof(T) * (2.0 * m * n + (double)m * k + (double)k * n), 2.0 * m * n * k);
-    gemm_update_kernel<T><<<grid, kGemmThreads, 0, st>>>(m, n, (int)k, A, lda, B, ldb, C, ldc);
+    if constexpr (sizeof(T) == 4) {
+        if (n <= 16) {
+            gemm_update_kernel<T, 256, 16><<<dim3((unsigned)lu_cdiv(m, 256), (unsigned)lu_cdiv(n, 16)), kGemmThreads,
+                                              0, st>>>(m, n, (int)k, A, lda, B, ldb, C, ldc);
+            LU_CHECK_LAUNCH();
+            return LU_SUCCESS;
+        }
+    }
+    if (n <= 32) {
+        gemm_update_kernel<T, 128, 32><<<dim3((unsigned)lu_cdiv(m, 128), (unsigned)lu_cdiv(n, 32)), kGemmThreads, 0,
+                                          st>>>(m, n, (int)k, A, lda, B, ldb, C, ldc);
+    } else {
+        if (lu_cdiv(n, 64) > 65535) return LU_ERR_UNSUPPORTED;
+        gemm_update_kernel<T, 64, 64><<<dim3((unsigned)lu_cdiv(m, 64), (unsigned)lu_cdiv(n, 64)), kGemmThreads, 0,
+                                        st>>>(m, n, (int)k, A, lda, B, ldb, C, ldc);
+    }
     LU_CHECK_LAUNCH();
     return LU_SUCCESS;
 }
@@ -190,3 +221,4 @@ template int lu_launch_gemm_update<double>(cudaStream_t, int64_t, int64_t, int64
                                            int64_t, const double*, int64_t, double*, int64_t);
 template int lu_launch_gemm_update<float>(cudaStream_t, int64_t, int64_t, int64_t, const float*,
                                           int64_t, const float*, int64_t, float*, int64_t);
+
