@@ -120,6 +120,11 @@ enum {
  * sum of their event-to-event durations (ms) and of their algorithmic bytes
  * and flops (host pointers, any may be NULL).  lu_profile_reset clears. */
 int lu_profile_enable(int mask);
+/* lu_profile_stride(every): with every = s > 1 only one launch in s of each
+ * profiled class (the 1st, the (s+1)th, ...) carries events, so that a profile
+ * taken inside a timed region perturbs it less; launches and durations read
+ * back are those of the sampled launches.  every <= 1 samples all (default). */
+int lu_profile_stride(int every);
 int lu_profile_reset(void);
 int lu_profile_read(int kclass, int64_t *launches, double *ms, double *bytes, double *flops);
 

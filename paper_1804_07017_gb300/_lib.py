@@ -66,6 +66,7 @@ _SIGNATURES = {
     "lu_noalloc_scratch_bytes": (ctypes.c_size_t, []),
     "lu_selftest_wait_timeout": (i32, [vp, i64, vp]),
     "lu_profile_enable": (i32, [i32]),
+    "lu_profile_stride": (i32, [i32]),
     "lu_profile_reset": (i32, []),
     "lu_profile_read": (i32, [i32, ctypes.POINTER(i64), ctypes.POINTER(dbl), ctypes.POINTER(dbl),
                               ctypes.POINTER(dbl)]),

@@ -75,6 +75,12 @@ template <typename T>
 int lu_launch_laswp_apply(cudaStream_t st, T* A, int64_t lda, int64_t c1, int64_t n1,
                           int64_t c2, int64_t n2, const int32_t* plan, int64_t K, int num_sms);
 
+// RL2 + RL3 of a narrow panel node in one launch (w1, w2 <= 32), bit-identical to
+// lu_launch_trsm_lunit followed by lu_launch_gemm_update.  arrivals: one zeroed
+// counter (left zeroed).
+template <typename T>
+int lu_launch_trsm_gemm_narrow(cudaStream_t st, int64_t m2, int64_t w2, int64_t w1, const T* L11, T* A12,
+                               const T* A21, T* A22, int64_t lda, unsigned* arrivals);
 template <typename T>
 int lu_launch_trsm_lunit(cudaStream_t st, int64_t m, int64_t n, const T* L, int64_t ldl, T* B,
                          int64_t ldb);

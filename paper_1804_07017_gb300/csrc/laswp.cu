@@ -18,60 +18,73 @@ namespace {
 
 constexpr int kPlanThreads = 256;
 
+// The source row of a tracked position x is found by running the K
+// transpositions (k1 + q <-> t[q]) backwards from x: after the interchanges in
+// order, position x holds the row that sigma_0(sigma_1(...sigma_{K-1}(x)))
+// held before.  Every position's chain is independent, so one thread follows
+// one position; the rows below the block that receive a different row (first
+// occurrence of each target) are then compacted in order by one warp.
 __global__ void __launch_bounds__(kPlanThreads)
     laswp_plan_kernel(const int32_t* __restrict__ ipiv, int64_t k1, int K, int32_t* __restrict__ plan) {
     extern __shared__ int32_t sm[];
     int32_t* t = sm;            // [K] target row (absolute, 0-based) of interchange i
-    int32_t* firstk = t + K;    // [K] representative interchange of a target below the block
-    int32_t* cur = firstk + K;  // [2K] source row now sitting at each tracked position
+    int32_t* g = t + K;         // [K] 1 if interchange i's target is a first occurrence below the block that moves
+    int32_t* gsrc = g + K;      // [K] the row that target position ends up holding
+    int32_t* rank = gsrc + K;   // [K] exclusive prefix of g
+    __shared__ int s_total;
     const int tid = threadIdx.x;
-    const int64_t k2 = k1 + K;
+    const int kb = (int)k1, ke = (int)(k1 + K);
     for (int i = tid; i < K; i += kPlanThreads) t[i] = ipiv[k1 + i] - 1;
     __syncthreads();
-    for (int i = tid; i < K; i += kPlanThreads) {
-        int f = -1;
-        if (t[i] >= k2) {
-            for (int q = 0; q <= i; ++q)
-                if (t[q] == t[i]) {
-                    f = q;
-                    break;
-                }
+    auto chain = [&](int x) {
+#pragma unroll 8
+        for (int q = K - 1; q >= 0; --q) {
+            const int p = t[q], b = kb + q;
+            x = (x == b) ? p : ((x == p) ? b : x);
         }
-        firstk[i] = f;
-        cur[i] = (int32_t)(k1 + i);
-        cur[K + i] = (f == i) ? t[i] : -1;
-    }
-    __syncthreads();
-    if (tid == 0) {
-        for (int i = 0; i < K; ++i) {
-            const int64_t p = t[i];
-            if (p == k1 + i) continue;
-            const int a = i;
-            const int b = (p < k2) ? (int)(p - k1) : K + firstk[i];
-            const int32_t x = cur[a];
-            cur[a] = cur[b];
-            cur[b] = x;
-        }
-    }
-    __syncthreads();
+        return x;
+    };
     int32_t* dst = plan + 1;
     int32_t* src = plan + 1 + 2 * K;
     for (int i = tid; i < K; i += kPlanThreads) {
-        dst[i] = (int32_t)(k1 + i);
-        src[i] = cur[i];
-    }
-    __syncthreads();
-    if (tid == 0) {
-        int cnt = K;
-        for (int i = 0; i < K; ++i) {
-            if (firstk[i] == i && cur[K + i] != t[i]) {
-                dst[cnt] = t[i];
-                src[cnt] = cur[K + i];
-                ++cnt;
+        dst[i] = kb + i;
+        src[i] = chain(kb + i);
+        int flag = 0, s = 0;
+        const int ti = t[i];
+        if (ti >= ke) {
+            bool first = true;
+            for (int q = 0; q < i; ++q)
+                if (t[q] == ti) {
+                    first = false;
+                    break;
+                }
+            if (first) {
+                s = chain(ti);
+                flag = s != ti;
             }
         }
-        plan[0] = cnt;
+        g[i] = flag;
+        gsrc[i] = s;
     }
+    __syncthreads();
+    if (tid < 32) {
+        int run = 0;
+        for (int base = 0; base < K; base += 32) {
+            const int i = base + tid;
+            const int f = (i < K) ? g[i] : 0;
+            const unsigned bal = __ballot_sync(0xffffffffu, f);
+            if (i < K) rank[i] = run + __popc(bal & ((1u << tid) - 1u));
+            run += __popc(bal);
+        }
+        if (tid == 0) s_total = run;
+    }
+    __syncthreads();
+    for (int i = tid; i < K; i += kPlanThreads)
+        if (g[i]) {
+            dst[K + rank[i]] = t[i];
+            src[K + rank[i]] = gsrc[i];
+        }
+    if (tid == 0) plan[0] = K + s_total;
 }
 
 constexpr int kApplyThreads = 256;  // 8 warps, one column per warp at a time

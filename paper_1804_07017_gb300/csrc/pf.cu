@@ -269,11 +269,18 @@ int panel_rec(lu_context* c, cudaStream_t st, T* A, int64_t lda, int64_t M, int6
         LU_TRY(lu_launch_laswp_plan(st, ipiv, j0, j0 + w1, c->plan_tmp));
         LU_TRY(lu_launch_laswp_apply<T>(st, A, lda, j0 + w1, w2, 0, 0, c->plan_tmp, w1, c->num_sms));
     }
-    // RL2 and RL3 restricted to the panel
-    LU_TRY(lu_launch_trsm_lunit<T>(st, w1, w2, A + j0 + j0 * lda, lda, A + j0 + (j0 + w1) * lda, lda));
-    if (M - j0 - w1 > 0)
-        LU_TRY(lu_launch_gemm_update<T>(st, M - j0 - w1, w2, w1, A + (j0 + w1) + j0 * lda, lda,
-                                        A + j0 + (j0 + w1) * lda, lda, A + (j0 + w1) + (j0 + w1) * lda, lda));
+    // RL2 and RL3 restricted to the panel; narrow nodes in one launch (the arrival
+    // counter is the ticket word of the panel's sync block, unused by the leaves)
+    if (w1 <= 32 && w2 <= 32) {
+        LU_TRY(lu_launch_trsm_gemm_narrow<T>(st, M - j0 - w1, w2, w1, A + j0 + j0 * lda, A + j0 + (j0 + w1) * lda,
+                                             A + (j0 + w1) + j0 * lda, A + (j0 + w1) + (j0 + w1) * lda, lda,
+                                             &c->sync[0].ticket));
+    } else {
+        LU_TRY(lu_launch_trsm_lunit<T>(st, w1, w2, A + j0 + j0 * lda, lda, A + j0 + (j0 + w1) * lda, lda));
+        if (M - j0 - w1 > 0)
+            LU_TRY(lu_launch_gemm_update<T>(st, M - j0 - w1, w2, w1, A + (j0 + w1) + j0 * lda, lda,
+                                            A + j0 + (j0 + w1) * lda, lda, A + (j0 + w1) + (j0 + w1) * lda, lda));
+    }
     LU_TRY(panel_rec<T>(c, st, A, lda, M, j0 + w1, w2, ipiv, o, leaf, cluster, pc0, pw));
     if (!cluster) {
         // interchanges of the right half applied back to the left half's columns

@@ -361,11 +361,14 @@ __global__ void __maxnreg__(LU_PF_PUSH_MAXREG)
                             const int lr = pos - row0;
                             if (warp == (lr % kPT) >> 5 && lane < w && (lane < c0 || lane >= c0 + SB))
                                 sA[lr * WP + lane] = src[lane];
+                            if (tid == lr % kPT) {
+                                const int oq = lr / kPT;
 #pragma unroll
-                            for (int q = 0; q < RQ; ++q)
-                                if (tid + kPT * q == lr)
+                                for (int q = 0; q < RQ; ++q)
+                                    if (q == oq)
 #pragma unroll
-                                    for (int kk = 0; kk < SB; ++kk) v[q][kk] = src[c0 + kk];
+                                        for (int kk = 0; kk < SB; ++kk) v[q][kk] = src[c0 + kk];
+                            }
                         }
                     }
                 }

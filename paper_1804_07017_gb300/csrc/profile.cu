@@ -23,6 +23,8 @@ struct Rec {
 
 std::mutex g_mu;
 unsigned g_mask = 0;
+int g_stride = 1;
+long long g_seen[LU_K_COUNT] = {};
 std::vector<Rec> g_recs;
 std::vector<cudaEvent_t> g_pool;
 struct Agg {
@@ -111,6 +113,7 @@ LuProfScope::LuProfScope(cudaStream_t st, int cls, double bytes, double flops) :
     if (!(g_mask & (1u << cls))) return;
     std::lock_guard<std::mutex> lk(g_mu);
     if (!(g_mask & (1u << cls))) return;
+    if (g_stride > 1 && (g_seen[cls]++ % g_stride) != 0) return;
     a_ = take_event();
     b_ = take_event();
     cls_ = cls;
@@ -133,10 +136,18 @@ extern "C" int lu_profile_enable(int mask) {
     return LU_SUCCESS;
 }
 
+extern "C" int lu_profile_stride(int every) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_stride = every > 1 ? every : 1;
+    for (auto& s : g_seen) s = 0;
+    return LU_SUCCESS;
+}
+
 extern "C" int lu_profile_reset(void) {
     std::lock_guard<std::mutex> lk(g_mu);
     drain_locked();
     for (auto& g : g_agg) g = Agg();
+    for (auto& s : g_seen) s = 0;
     return LU_SUCCESS;
 }
 

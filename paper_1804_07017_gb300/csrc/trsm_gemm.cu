@@ -159,6 +159,119 @@ __global__ void __launch_bounds__(kGemmThreads)
 }
 
 
+
+// RL2 + RL3 of a narrow node of the recursive panel (w1 <= 32, w2 <= 32) in one
+// launch:  U12 := trilu(L11)^{-1} A12,  A22 := A22 - A21 U12.
+// Every CTA solves the w1 x w2 block U12 itself, in shared memory, with the
+// same operations in the same order as trsm_lunit_kernel (a warp per column,
+// lane = row, x_i := fma(-L(i, j), x_j, x_i) for j = 0, 1, ...), then applies
+// its BM-row tile of the update with gemm_update_kernel's accumulation order,
+// so the results are bit-identical to the two separate launches.  U12 is
+// written back over A12 by the last CTA to have read A12 (an arrival counter
+// that this CTA resets), so no CTA can read an already solved block.
+template <typename T, int BM, int BN>
+__global__ void __launch_bounds__(kGemmThreads)
+    trsm_gemm_narrow_kernel(int64_t m2, int w2, int w1, const T* __restrict__ L11, T* __restrict__ A12,
+                            const T* __restrict__ A21, T* __restrict__ A22, int64_t lda, unsigned* __restrict__ arrivals) {
+    constexpr int TX = BM / 4, TY = BN / 4;
+    static_assert(TX * TY == kGemmThreads, "tile shape");
+    constexpr int NA = BM * BK / kGemmThreads;
+    __shared__ T sL[32 * 33];              // sL[j * 33 + i] = L(i, j)
+    __shared__ T sU[32][BN + 1];           // U12, row p = k index
+    extern __shared__ __align__(16) unsigned char smraw[];
+    T* sA = reinterpret_cast<T*>(smraw);   // [2][BK][BM] A21 k-chunks
+    __shared__ int s_last;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t i0 = (int64_t)blockIdx.x * BM;
+    for (int e = tid; e < 32 * 32; e += kGemmThreads) {
+        const int i = e & 31, j = e >> 5;
+        sL[j * 33 + i] = (i < w1 && j < w1) ? L11[i + (int64_t)j * lda] : T(0);
+    }
+    for (int e = tid; e < 32 * BN; e += kGemmThreads) {
+        const int i = e & 31, j = e >> 5;
+        sU[i][j] = (i < w1 && j < w2) ? A12[i + (int64_t)j * lda] : T(0);
+    }
+    __syncthreads();
+    if (tid == 0) {
+        const unsigned old = atomicAdd(arrivals, 1u);
+        s_last = old == gridDim.x - 1;
+        if (s_last) *arrivals = 0u;
+    }
+    for (int c = warp; c < BN; c += kGemmThreads / 32) {
+        T v = sU[lane][c];
+        for (int j = 0; j < w1; ++j) {
+            const T xj = __shfl_sync(0xffffffffu, v, j);
+            if (lane > j) v = fma(-sL[j * 33 + lane], xj, v);
+        }
+        if (lane < w1) sU[lane][c] = v;
+    }
+    __syncthreads();
+    if (s_last)
+        for (int e = tid; e < w1 * w2; e += kGemmThreads) {
+            const int i = e % w1, j = e / w1;
+            A12[i + (int64_t)j * lda] = sU[i][j];
+        }
+    if (i0 >= m2) return;
+    const int tx = tid % TX, ty = tid / TX;
+    T acc[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = T(0);
+    T ra[NA];
+    auto load_regs = [&](int p0) {
+#pragma unroll
+        for (int q = 0; q < NA; ++q) {
+            const int e = tid + q * kGemmThreads;
+            const int i = e % BM, p = e / BM;
+            ra[q] = (i0 + i < m2 && p0 + p < w1) ? A21[(i0 + i) + (int64_t)(p0 + p) * lda] : T(0);
+        }
+    };
+    auto store_smem = [&](int s) {
+#pragma unroll
+        for (int q = 0; q < NA; ++q) {
+            const int e = tid + q * kGemmThreads;
+            sA[(s * BK + e / BM) * BM + e % BM] = ra[q];
+        }
+    };
+    load_regs(0);
+    store_smem(0);
+    __syncthreads();
+    int s = 0;
+    for (int p0 = 0; p0 < w1; p0 += BK) {
+        const bool more = p0 + BK < w1;
+        if (more) load_regs(p0 + BK);
+#pragma unroll
+        for (int p = 0; p < BK; ++p) {
+            T a[4], b[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                a[q] = sA[(s * BK + p) * BM + tx + TX * q];
+                b[q] = sU[p0 + p][ty + TY * q];
+            }
+#pragma unroll
+            for (int x = 0; x < 4; ++x)
+#pragma unroll
+                for (int y = 0; y < 4; ++y) acc[x][y] = fma(a[x], b[y], acc[x][y]);
+        }
+        if (more) {
+            store_smem(s ^ 1);
+            __syncthreads();
+            s ^= 1;
+        }
+    }
+#pragma unroll
+    for (int y = 0; y < 4; ++y) {
+        const int j = ty + TY * y;
+        if (j >= w2) continue;
+#pragma unroll
+        for (int x = 0; x < 4; ++x) {
+            const int64_t i = i0 + tx + TX * x;
+            if (i < m2) A22[i + (int64_t)j * lda] -= acc[x][y];
+        }
+    }
+}
+
 }  // namespace
 
 template <typename T>
@@ -222,3 +335,36 @@ template int lu_launch_gemm_update<double>(cudaStream_t, int64_t, int64_t, int64
 template int lu_launch_gemm_update<float>(cudaStream_t, int64_t, int64_t, int64_t, const float*,
                                           int64_t, const float*, int64_t, float*, int64_t);
 
+
+template <typename T, int BM, int BN>
+static int launch_narrow(cudaStream_t st, int64_t m2, int64_t w2, int64_t w1, const T* L11, T* A12, const T* A21,
+                         T* A22, int64_t lda, unsigned* arrivals) {
+    const size_t smem = sizeof(T) * 2 * BK * BM;
+    static bool attr = false;
+    if (!attr) {
+        LU_CHECK_CUDA(cudaFuncSetAttribute(trsm_gemm_narrow_kernel<T, BM, BN>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        attr = true;
+    }
+    const unsigned gx = (unsigned)std::max<int64_t>(1, lu_cdiv(m2, BM));
+    trsm_gemm_narrow_kernel<T, BM, BN><<<gx, kGemmThreads, smem, st>>>(m2, (int)w2, (int)w1, L11, A12, A21, A22, lda,
+                                                                      arrivals);
+    LU_CHECK_LAUNCH();
+    return LU_SUCCESS;
+}
+
+template <typename T>
+int lu_launch_trsm_gemm_narrow(cudaStream_t st, int64_t m2, int64_t w2, int64_t w1, const T* L11, T* A12,
+                               const T* A21, T* A22, int64_t lda, unsigned* arrivals) {
+    if (w2 <= 0 || w1 <= 0) return LU_SUCCESS;
+    if (w1 > 32 || w2 > 32) return LU_ERR_UNSUPPORTED;
+    LuProfScope prof(st, LU_K_TRSM, sizeof(T) * (2.0 * m2 * w2 + (double)m2 * w1 + 2.0 * w1 * w2),
+                     (double)w1 * w1 * w2 + 2.0 * m2 * w2 * w1);
+    if (w2 <= 16) return launch_narrow<T, 256, 16>(st, m2, w2, w1, L11, A12, A21, A22, lda, arrivals);
+    return launch_narrow<T, 128, 32>(st, m2, w2, w1, L11, A12, A21, A22, lda, arrivals);
+}
+
+template int lu_launch_trsm_gemm_narrow<double>(cudaStream_t, int64_t, int64_t, int64_t, const double*, double*,
+                                                const double*, double*, int64_t, unsigned*);
+template int lu_launch_trsm_gemm_narrow<float>(cudaStream_t, int64_t, int64_t, int64_t, const float*, float*,
+                                               const float*, float*, int64_t, unsigned*);
