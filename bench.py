@@ -178,11 +178,13 @@ def main():
     ap.add_argument("--prec", default="bf16x6", choices=["bf16x6", "bf16x3", "bf16", "fp16", "f32"])
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison path")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle sample")
-    ap.add_argument("--workload", default="mixed", choices=["mixed", "batched"],
+    ap.add_argument("--workload", default="mixed", choices=["mixed", "batched", "configs"],
                     help="mixed: the n=16384 solver (default); batched: 4096 uneven systems")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "configs":
+        return run_configs(args)
     if args.workload == "batched":
         return run_batched(args)
 
@@ -350,6 +352,91 @@ def main():
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
+    return 0
+
+
+def run_configs(args):
+    """The comparisons of the hot-path configurations, one JSON object:
+    c1  FP64, n = 8192, nb = 256, N(0,1): look-ahead off / depth 1 / depth 1 with
+        stealing (factorization + solve, GFLOP/s of 2n^3/3);
+    c2  n = 16384, nb = 256: the mixed solver with each trailing-update precision
+        (N(0,1), one rhs), then bf16x6 on the row-scaled matrix and with 16 rhs;
+    c3  n = 32768, nb = 256, A = diag(10^u) G: bf16x6 and e4m3 updates.
+    Each configuration runs once untimed, then once timed with CUDA events."""
+    import numpy as np
+    import torch
+
+    import paper_1804_07017_gb300 as lu
+    import synth
+    from paper_1804_07017_gb300.api import colmajor
+
+    torch.cuda.set_device(0)
+    out = {"metric": "LU+solve GFLOP/s (2n^3/3) per configuration", "unit": "GFLOP/s", "data": "synthetic"}
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        r = fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1), r
+
+    # c1: FP64 look-ahead comparison
+    n = 8192
+    A0 = synth.normal_matrix(n, seed=0)
+    b0 = synth.ones_rhs(A0)
+    A = colmajor(n, n)
+    B = colmajor(n, 1)
+    ipiv = torch.zeros(n, dtype=torch.int32, device="cuda")
+    info = torch.zeros(1, dtype=torch.int32, device="cuda")
+    Ah = torch.from_numpy(A0).cuda()
+    bh = torch.from_numpy(b0).cuda()
+    c1 = {}
+    for name, la, steal in (("lookahead_off", 0, 0), ("lookahead_1", 1, 0), ("lookahead_1_steal", 1, 1)):
+        o = lu.default_opts(nb=256, lookahead=la, steal=steal)
+
+        def run():
+            A.copy_(Ah)
+            B.copy_(bh)
+            lu.lu_factor_ex(A, ipiv, info, o)
+            lu.lu_solve_ex(A, ipiv, B)
+
+        ms, _ = timed(run)
+        c1[name] = {"ms": ms, "gflops": 2 * n ** 3 / 3 / ms / 1e6, "info": int(info.item())}
+    out["c1_fp64_n8192"] = c1
+    del A, B, Ah, bh
+
+    def mixed(n, A0, B0, precs, tag):
+        A = colmajor(n, n)
+        A.copy_(torch.from_numpy(A0))
+        B = colmajor(n, B0.shape[1])
+        B.copy_(torch.from_numpy(B0))
+        X = colmajor(n, B0.shape[1])
+        res = {}
+        for name in precs:
+            code = {"bf16": 0, "fp16": 1, "fp8": 2, "f32": 3, "bf16x3": 4, "f64": 5, "bf16x6": 6}[name]
+            ms, (st, it, eta) = timed(lambda: lu.lu_gesv_mixed(A, B, X, code, TOL, MAX_ITER,
+                                                                 lu.default_opts(nb=256)))
+            res[f"{tag}{name}"] = {"ms": ms, "gflops": 2 * n ** 3 / 3 / ms / 1e6, "status": int(st),
+                                   "refinements": int(it), "bwd_err": float(eta),
+                                   "converged": int(st) == 0}
+        return res
+
+    n = 16384
+    A0 = synth.normal_matrix(n, seed=0)
+    c2 = mixed(n, A0, synth.ones_rhs(A0), ["bf16x6", "bf16x3", "bf16", "fp16", "f32", "f64"], "")
+    B16, _ = synth.random_rhs(A0, 16, seed=1)
+    c2.update(mixed(n, A0, B16, ["bf16x6"], "rhs16_"))
+    R0 = synth.row_scaled(A0, seed=3)
+    c2.update(mixed(n, R0, synth.ones_rhs(R0), ["bf16x6"], "rowscaled_"))
+    out["c2_mixed_n16384"] = c2
+    del A0, R0, B16
+    n = 32768
+    D0 = synth.diag_scaled_normal(n, seed=0)
+    out["c3_n32768_diag_scaled"] = mixed(n, D0, synth.ones_rhs(D0), ["bf16x6", "fp8"], "")
+    print(json.dumps(out))
     return 0
 
 
