@@ -98,9 +98,13 @@ int lu_launch_permute_rows(cudaStream_t st, int64_t n, int64_t nrhs, const int32
 
 // Dinv: NULL, or the inverses of the diagonal blocks from lu_launch_trinv_diag,
 // which turn each block's substitution into one dense product.
+// xtag (FP32, one rhs, with Dinv): n zero-initialised 64-bit words through which the
+// blocks pass their solved values tagged with a per-launch id (one global round trip
+// per dependency instead of a counter plus a load).
 template <typename T>
 int lu_launch_trsv_blocked(lu_context* c, cudaStream_t st, bool lower_unit, int64_t n,
-                           int64_t nrhs, const T* LU, int64_t lda, T* X, int64_t ldx, const T* Dinv = nullptr);
+                           int64_t nrhs, const T* LU, int64_t lda, T* X, int64_t ldx, const T* Dinv = nullptr,
+                           unsigned long long* xtag = nullptr);
 template <typename T>
 size_t lu_trinv_bytes(int64_t n);
 template <typename T>

@@ -37,7 +37,7 @@ __global__ void __launch_bounds__(kPlanThreads)
     for (int i = tid; i < K; i += kPlanThreads) t[i] = ipiv[k1 + i] - 1;
     __syncthreads();
     auto chain = [&](int x) {
-#pragma unroll 8
+#pragma unroll 1
         for (int q = K - 1; q >= 0; --q) {
             const int p = t[q], b = kb + q;
             x = (x == b) ? p : ((x == p) ? b : x);

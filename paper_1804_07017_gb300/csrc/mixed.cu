@@ -250,6 +250,7 @@ static int gesv_refined(lu_context* h, int prec, int64_t n, int64_t nrhs, const 
     const size_t o_part = take(sizeof(double) * nch * rhs_chunk * n);
     const size_t o_sc = take(sizeof(double) * (8 + nrhs) + sizeof(int32_t) * 8);
     const size_t o_dinv = take(lu_trinv_bytes<T>(n));
+    const size_t o_xtag = take(sizeof(unsigned long long) * n);
     LU_TRY(lu_mx_reserve(h, off));
     char* base = (char*)h->mx;
     T* Aw = (T*)(base + o_aw);
@@ -262,12 +263,14 @@ static int gesv_refined(lu_context* h, int prec, int64_t n, int64_t nrhs, const 
     double* part = (double*)(base + o_part);
     double* sc = (double*)(base + o_sc);
     T* Dinv = (T*)(base + o_dinv);
+    unsigned long long* xtag = (unsigned long long*)(base + o_xtag);
     double* anorm = sc;
     double* eta = sc + 1;
     double* eta_cols = sc + 8;
     int32_t* dinfo = (int32_t*)(sc + 8 + nrhs);
     unsigned int* done = (unsigned int*)(dinfo + 2);
     LU_CHECK_CUDA(cudaMemsetAsync(sc, 0, sizeof(double) * (8 + nrhs) + sizeof(int32_t) * 8, st));
+    LU_CHECK_CUDA(cudaMemsetAsync(xtag, 0, sizeof(unsigned long long) * n, st));
 
     // 1. working copy in T and its factorization
     LU_TRY((lu_launch_cast<double, T>(st, n, n, A, lda, Aw, ldw)));
@@ -283,8 +286,8 @@ static int gesv_refined(lu_context* h, int prec, int64_t n, int64_t nrhs, const 
     // 2. x0 = U^-1 L^-1 P b in T
     LU_TRY((lu_launch_cast<double, T>(st, n, nrhs, B, ldb, rw, n)));
     LU_TRY(lu_launch_permute_rows<T>(st, n, nrhs, perm, rw, n, dw, n));
-    LU_TRY(lu_launch_trsv_blocked<T>(h, st, true, n, nrhs, Aw, ldw, dw, n, Dinv));
-    LU_TRY(lu_launch_trsv_blocked<T>(h, st, false, n, nrhs, Aw, ldw, dw, n, Dinv));
+    LU_TRY(lu_launch_trsv_blocked<T>(h, st, true, n, nrhs, Aw, ldw, dw, n, Dinv, xtag));
+    LU_TRY(lu_launch_trsv_blocked<T>(h, st, false, n, nrhs, Aw, ldw, dw, n, Dinv, xtag));
     LU_TRY((lu_launch_cast<T, double>(st, n, nrhs, dw, n, X, ldx)));
     // 3. refinement: r = b - A x (FP64), eta test on the host, d = (LU)^-1 P r (T), x += d (FP64)
     double best = INFINITY;
@@ -324,8 +327,8 @@ static int gesv_refined(lu_context* h, int prec, int64_t n, int64_t nrhs, const 
         }
         LU_TRY((lu_launch_cast<double, T>(st, n, nrhs, R, n, rw, n)));
         LU_TRY(lu_launch_permute_rows<T>(st, n, nrhs, perm, rw, n, dw, n));
-        LU_TRY(lu_launch_trsv_blocked<T>(h, st, true, n, nrhs, Aw, ldw, dw, n, Dinv));
-        LU_TRY(lu_launch_trsv_blocked<T>(h, st, false, n, nrhs, Aw, ldw, dw, n, Dinv));
+        LU_TRY(lu_launch_trsv_blocked<T>(h, st, true, n, nrhs, Aw, ldw, dw, n, Dinv, xtag));
+        LU_TRY(lu_launch_trsv_blocked<T>(h, st, false, n, nrhs, Aw, ldw, dw, n, Dinv, xtag));
         LU_TRY(lu_launch_add_to_f64<T>(st, n, nrhs, dw, n, X, ldx));
     }
     if (status == LU_WARN_NOT_CONVERGED && best_it >= 0 && best_it != it) {

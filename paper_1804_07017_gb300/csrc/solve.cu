@@ -14,6 +14,8 @@
 //                    the CTA scheduling order.
 #include <cudaTypedefs.h>
 
+#include <atomic>
+
 #include "internal.h"
 #include "ptx.cuh"
 #include "profile.h"
@@ -471,6 +473,143 @@ __global__ void __launch_bounds__(kTrsvThreads)
     if (tid == 0) lu_st_release(&sync->arrive, (unsigned)(chain + 1));
 }
 
+
+// FP32, one right-hand side, inverse diagonal blocks: the solved values travel
+// as 64-bit words {tag << 32 | value bits} in a side buffer xt, written by the
+// block's CTA once and polled element by element by its successors, so one
+// global round trip carries both the "ready" signal and the data (no counter,
+// no fence).  tag is unique per launch, so words of earlier launches never
+// match.  Each CTA prefetches its own right-hand side before it waits.  Per
+// predecessor: poll its BS words (a bounded spin per thread), add its tile's
+// contribution (tiles staged by TMA one ahead), then x = inv(D) (b - sum).
+__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long* p) {
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+template <bool LOWER>
+__global__ void __launch_bounds__(kTrsvThreads)
+    trsv_tag_kernel(const __grid_constant__ CUtensorMap tmL, const __grid_constant__ CUtensorMap tmD, int64_t n,
+                    float* __restrict__ X, unsigned long long* __restrict__ xt, unsigned tag,
+                    LuSync* __restrict__ sync) {
+    using C = TrsvCfg<float>;
+    constexpr int BS = C::BS;
+    extern __shared__ unsigned char smraw[];
+    unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~uintptr_t(1023));
+    float* sD = reinterpret_cast<float*>(base);   // [BS cols][BS rows] inverse of the diagonal block
+    float* sT = sD + C::kTile;                    // two off-diagonal tiles
+    float* sX = sT + 2 * C::kTile;                // [BS]
+    float* sPart = sX + kNR * BS;                 // [BS]
+    uint64_t* bars = reinterpret_cast<uint64_t*>(sPart + kNR * BS);
+    __shared__ int s_chain;
+    __shared__ volatile int s_abort;
+    const int tid = threadIdx.x;
+    const int nblk = (int)((n + BS - 1) / BS);
+    const uint32_t tile_bytes = (uint32_t)(C::kTile * sizeof(float));
+    if (tid == 0) {
+        s_chain = (int)atomicAdd(&sync->ticket, 1u);
+        s_abort = 0;
+        for (int b = 0; b < 3; ++b) mbar_init(&bars[b], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    __syncthreads();
+    const int chain = s_chain;
+    const int blk = LOWER ? chain : nblk - 1 - chain;
+    const int64_t r0 = (int64_t)blk * BS;
+    const int rows = (int)min((int64_t)BS, n - r0);
+    auto src_block = [&](int q) { return LOWER ? q : nblk - 1 - q; };
+    if (tid == 0) {
+        mbar_arrive_expect_tx(&bars[0], tile_bytes);
+        tma_load_2d(sD, &tmD, &bars[0], 0, (LOWER ? blk : nblk + blk) * BS);
+        if (chain > 0) {
+            mbar_arrive_expect_tx(&bars[1], tile_bytes);
+            tma_load_2d(sT, &tmL, &bars[1], (int)r0, src_block(0) * BS);
+        }
+    }
+    const int r = tid % BS, h = tid / BS;
+    const float b = (h == 0 && r < rows) ? X[r0 + r] : 0.f;
+    float acc = 0.f;
+    int issued = chain > 0 ? 1 : 0, consumed = 0;
+    bool ok = true;
+    for (int q = 0; q < chain && ok; ++q) {
+        if (tid == 0 && q + 1 < chain) {
+            const int nb = (q + 1) & 1;
+            mbar_arrive_expect_tx(&bars[1 + nb], tile_bytes);
+            tma_load_2d(sT + nb * C::kTile, &tmL, &bars[1 + nb], (int)r0, src_block(q + 1) * BS);
+            issued = q + 2;
+        }
+        const int64_t c0 = (int64_t)src_block(q) * BS;
+        const int cols = (int)min((int64_t)BS, n - c0);
+        if (h == 0) {
+            float v = 0.f;
+            if (r < cols) {
+                const unsigned long long* w = xt + c0 + r;
+                unsigned long long x = ld_relaxed_u64(w);
+                if ((unsigned)(x >> 32) != tag) {
+                    const uint64_t t0 = lu_globaltimer();
+                    unsigned spins = 0;
+                    while ((unsigned)((x = ld_relaxed_u64(w)) >> 32) != tag) {
+                        if ((++spins & 255u) == 0) {
+                            if (s_abort) break;
+                            if (lu_globaltimer() - t0 > LU_WAIT_NS) {
+                                s_abort = 1;
+                                break;
+                            }
+                        }
+                    }
+                }
+                v = __uint_as_float((unsigned)x);
+            }
+            sX[r] = v;
+        }
+        if (!mbar_wait(&bars[1 + (q & 1)], (q >> 1) & 1, &s_abort)) ok = false;
+        __syncthreads();
+        if (!ok || s_abort) {
+            ok = false;
+            break;
+        }
+        consumed = q + 1;
+        const float* tile = sT + (q & 1) * C::kTile;
+#pragma unroll 8
+        for (int j = h; j < BS; j += C::kSplit) acc = fmaf(tile[j * BS + r], sX[j], acc);
+        __syncthreads();
+    }
+    if (ok && !mbar_wait(&bars[0], 0, &s_abort)) ok = false;
+    __syncthreads();
+    if (!ok || s_abort) {
+        if (tid == 0) {
+            atomicExch(&sync->error, LU_ERR_TIMEOUT);
+            for (int q = consumed; q < issued; ++q) {
+                const uint64_t t0 = lu_globaltimer();
+                while (!mbar_try_wait(&bars[1 + (q & 1)], (q >> 1) & 1))
+                    if (lu_globaltimer() - t0 > LU_MBAR_WAIT_NS) break;
+            }
+            const uint64_t t0 = lu_globaltimer();
+            while (!mbar_try_wait(&bars[0], 0))
+                if (lu_globaltimer() - t0 > LU_MBAR_WAIT_NS) break;
+        }
+        return;
+    }
+    // rhs - contributions, then x = inv(D) (rhs - contributions)
+    if (h == 1) sPart[r] = acc;
+    __syncthreads();
+    if (h == 0) sX[r] = (r < rows) ? b - (acc + sPart[r]) : 0.f;
+    __syncthreads();
+    float y = 0.f;
+#pragma unroll 8
+    for (int j = h; j < BS; j += C::kSplit) y = fmaf(sD[j * BS + r], sX[j], y);
+    if (h == 1) sPart[r] = y;
+    __syncthreads();
+    if (h == 0 && r < rows) {
+        const float x = y + sPart[r];
+        X[r0 + r] = x;
+        const unsigned long long word = ((unsigned long long)tag << 32) | __float_as_uint(x);
+        asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(xt + r0 + r), "l"(word) : "memory");
+    }
+}
+
 // Inverses of the diagonal blocks of the factors: blockIdx.y = 0 gives
 // inv(L_bb) (unit lower), 1 gives inv(U_bb), for block b = blockIdx.x, into
 // tile (blockIdx.y * nblk + b) of D (BS x BS, column-major, ld BS; zero outside
@@ -659,7 +798,7 @@ int lu_launch_trinv_diag(cudaStream_t st, int64_t n, const T* LU, int64_t lda, T
 
 template <typename T>
 int lu_launch_trsv_blocked(lu_context* c, cudaStream_t st, bool lower_unit, int64_t n, int64_t nrhs, const T* LU,
-                           int64_t lda, T* X, int64_t ldx, const T* Dinv) {
+                           int64_t lda, T* X, int64_t ldx, const T* Dinv, unsigned long long* xtag) {
     if (n <= 0 || nrhs <= 0) return LU_SUCCESS;
     using C = TrsvCfg<T>;
     const int nblk = (int)lu_cdiv(n, C::BS);
@@ -685,6 +824,50 @@ int lu_launch_trsv_blocked(lu_context* c, cudaStream_t st, bool lower_unit, int6
         LU_CHECK_CUDA(cudaFuncSetAttribute(trsv_tma_kernel<T, false, true>,
                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem));
         attr[ti] = true;
+    }
+    if constexpr (sizeof(T) == 4) {
+        if (inv && xtag && nrhs == 1) {
+            static bool tattr = false;
+            if (!tattr) {
+                LU_CHECK_CUDA(cudaFuncSetAttribute(trsv_tag_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   (int)C::smem));
+                LU_CHECK_CUDA(cudaFuncSetAttribute(trsv_tag_kernel<false>,
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem));
+                tattr = true;
+            }
+            // tags are unique per launch within the process (0 is never used: the buffer starts zeroed)
+            static std::atomic<unsigned> next_tag{1};
+            unsigned tag = next_tag.fetch_add(1);
+            if (tag == 0) tag = next_tag.fetch_add(1);
+            LU_CHECK_CUDA(cudaMemsetAsync(&c->sync[1].ticket, 0, sizeof(unsigned), st));
+            LuProfScope prof(st, LU_K_SOLVE, sizeof(T) * (0.5 * n * n + 2.0 * n), (double)n * n);
+            auto fn = lower_unit ? trsv_tag_kernel<true> : trsv_tag_kernel<false>;
+            fn<<<nblk, kTrsvThreads, C::smem, st>>>(map, dmap, n, (float*)X, xtag, tag, &c->sync[1]);
+            LU_CHECK_LAUNCH();
+            return LU_SUCCESS;
+        }
+    }
+    if constexpr (sizeof(T) == 4) {
+        if (inv && xtag && nrhs == 1) {
+            static bool tattr = false;
+            if (!tattr) {
+                LU_CHECK_CUDA(cudaFuncSetAttribute(trsv_tag_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   (int)C::smem));
+                LU_CHECK_CUDA(cudaFuncSetAttribute(trsv_tag_kernel<false>,
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem));
+                tattr = true;
+            }
+            // tags are unique per launch within the process (0 is never used: the buffer starts zeroed)
+            static std::atomic<unsigned> next_tag{1};
+            unsigned tag = next_tag.fetch_add(1);
+            if (tag == 0) tag = next_tag.fetch_add(1);
+            LU_CHECK_CUDA(cudaMemsetAsync(&c->sync[1].ticket, 0, sizeof(unsigned), st));
+            LuProfScope prof(st, LU_K_SOLVE, sizeof(T) * (0.5 * n * n + 2.0 * n), (double)n * n);
+            auto fn = lower_unit ? trsv_tag_kernel<true> : trsv_tag_kernel<false>;
+            fn<<<nblk, kTrsvThreads, C::smem, st>>>(map, dmap, n, (float*)X, xtag, tag, &c->sync[1]);
+            LU_CHECK_LAUNCH();
+            return LU_SUCCESS;
+        }
     }
     for (int64_t c0 = 0; c0 < nrhs; c0 += kNR) {
         const int nr = (int)std::min<int64_t>(kNR, nrhs - c0);
@@ -718,6 +901,8 @@ template size_t lu_trinv_bytes<float>(int64_t);
 template int lu_launch_trinv_diag<double>(cudaStream_t, int64_t, const double*, int64_t, double*);
 template int lu_launch_trinv_diag<float>(cudaStream_t, int64_t, const float*, int64_t, float*);
 template int lu_launch_trsv_blocked<double>(lu_context*, cudaStream_t, bool, int64_t, int64_t,
-                                            const double*, int64_t, double*, int64_t, const double*);
+                                            const double*, int64_t, double*, int64_t, const double*,
+                                            unsigned long long*);
 template int lu_launch_trsv_blocked<float>(lu_context*, cudaStream_t, bool, int64_t, int64_t,
-                                           const float*, int64_t, float*, int64_t, const float*);
+                                           const float*, int64_t, float*, int64_t, const float*,
+                                           unsigned long long*);
