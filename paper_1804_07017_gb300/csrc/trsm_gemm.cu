@@ -69,6 +69,64 @@ __global__ void __launch_bounds__(kTrsmThreads)
         for (int r = tid; r < m; r += kTrsmThreads) B[r + (col0 + c) * ldb] = sB[c * mp + r];
 }
 
+
+// The same solve as trsm_lunit_kernel (identical operations in identical
+// order, so identical results) with the strictly lower triangle of L staged in
+// shared memory once, packed by rows (row i at i(i-1)/2), so the 32-row sweep
+// makes no global accesses: the panel-width TRSM of the look-ahead step
+// (m = nb <= 256) otherwise pays two dependent global round trips per block.
+template <typename T, int COLS>
+__global__ void __launch_bounds__(kTrsmThreads)
+    trsm_lunit_staged_kernel(int m, int64_t n, const T* __restrict__ L, int64_t ldl, T* __restrict__ B,
+                             int64_t ldb) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int mp = (m + 31) & ~31;
+    T* sB = reinterpret_cast<T*>(smraw);       // [COLS][mp]
+    T* sLp = sB + (size_t)COLS * mp;           // packed strictly lower triangle
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t col0 = (int64_t)blockIdx.x * COLS;
+    const int nc = (int)min((int64_t)COLS, n - col0);
+    for (int e = tid; e < m * m; e += kTrsmThreads) {
+        const int i = e % m, j = e / m;
+        if (i > j) sLp[i * (i - 1) / 2 + j] = L[(int64_t)i + (int64_t)j * ldl];
+    }
+    for (int c = 0; c < COLS; ++c)
+        for (int r = tid; r < mp; r += kTrsmThreads)
+            sB[c * mp + r] = (c < nc && r < m) ? B[r + (col0 + c) * ldb] : T(0);
+    __syncthreads();
+    for (int J = 0; J < m; J += 32) {
+        const int jb = min(32, m - J);
+        for (int c = warp; c < COLS; c += kTrsmThreads / 32) {
+            T v = sB[c * mp + J + lane];
+            const int i = J + lane;
+            for (int j = 0; j < jb; ++j) {
+                const T xj = __shfl_sync(0xffffffffu, v, j);
+                if (lane > j && lane < jb) v = fma(-sLp[i * (i - 1) / 2 + J + j], xj, v);
+            }
+            if (lane < jb) sB[c * mp + J + lane] = v;
+        }
+        __syncthreads();
+        for (int r = J + jb + tid; r < m; r += kTrsmThreads) {
+            const T* lr = sLp + r * (r - 1) / 2 + J;
+            T l[32];
+#pragma unroll
+            for (int j = 0; j < 32; ++j) l[j] = (j < jb) ? lr[j] : T(0);
+            T acc[COLS];
+#pragma unroll
+            for (int c = 0; c < COLS; ++c) acc[c] = T(0);
+#pragma unroll
+            for (int j = 0; j < 32; ++j)
+#pragma unroll
+                for (int c = 0; c < COLS; ++c) acc[c] = fma(l[j], sB[c * mp + J + j], acc[c]);
+#pragma unroll
+            for (int c = 0; c < COLS; ++c) sB[c * mp + r] -= acc[c];
+        }
+        __syncthreads();
+    }
+    for (int c = 0; c < nc; ++c)
+        for (int r = tid; r < m; r += kTrsmThreads) B[r + (col0 + c) * ldb] = sB[c * mp + r];
+}
+
 constexpr int kGemmThreads = 256;
 constexpr int BK = 16;
 
@@ -292,7 +350,20 @@ int lu_launch_trsm_lunit(cudaStream_t st, int64_t m, int64_t n, const T* L, int6
         attr[ti] = true;
     }
     LuProfScope prof(st, LU_K_TRSM, sizeof(T) * (2.0 * m * n + 0.5 * m * m), (double)m * m * n);
-    if (smem16 <= 64 * 1024) {
+    // stage L in shared memory when the packed triangle and a 16-column block fit and
+    // few CTAs share it (the look-ahead and in-panel solves); a wide solve keeps the
+    // per-block loads, which many CTAs share through L2
+    const size_t staged = sizeof(T) * ((size_t)16 * mp + (size_t)m * (m - 1) / 2);
+    if (m > 32 && n <= 512 && staged <= 160 * 1024) {
+        static bool sattr[2] = {false, false};
+        if (!sattr[ti]) {
+            LU_CHECK_CUDA(cudaFuncSetAttribute(trsm_lunit_staged_kernel<T, 16>,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024));
+            sattr[ti] = true;
+        }
+        trsm_lunit_staged_kernel<T, 16><<<(unsigned)lu_cdiv(n, 16), kTrsmThreads, staged, st>>>((int)m, n, L, ldl, B,
+                                                                                              ldb);
+    } else if (smem16 <= 64 * 1024) {
         trsm_lunit_kernel<T, 16><<<(unsigned)lu_cdiv(n, 16), kTrsmThreads, smem16, st>>>((int)m, n, L, ldl, B, ldb);
     } else {
         trsm_lunit_kernel<T, 8><<<(unsigned)lu_cdiv(n, 8), kTrsmThreads, smem8, st>>>((int)m, n, L, ldl, B, ldb);
