@@ -114,14 +114,21 @@ int lu_launch_finish_info(cudaStream_t st, const LuSync* s, int32_t* info);
 
 template <typename T>
 bool lu_pf_cluster_shape(int64_t m, int w, size_t budget, int* C_out, int* R_out, size_t* smem_out);
+// sib > 0: the leaf also applies L11^-1 to the top rows of the first sib columns to its
+// right (its sibling's U12); kprev > 0: the leaf first applies the preceding sibling's
+// rank-kprev update to its own columns.  Both need the pushed-message leaf
+// (lu_pf_leaf_pairs_supported).
 template <typename T>
 int lu_launch_pf_leaf_cluster(cudaStream_t st, T* A, int64_t lda, int64_t m, int w, int C, int R, size_t smem,
-                              int64_t left_cols, int64_t right_cols, int32_t* ipiv, int64_t ipiv_add, LuSync* sync);
+                              int64_t left_cols, int64_t right_cols, int32_t* ipiv, int64_t ipiv_add, LuSync* sync,
+                              int sib = 0, int kprev = 0);
+bool lu_pf_leaf_pairs_supported();
 // Pushed-message cluster leaf (pf_push.cu): w columns of a kernel compiled for wc.
 size_t lu_pf_push_smem(int esize, int w, int rq);
 template <typename T>
 int lu_launch_pf_leaf_push(cudaStream_t st, T* A, int64_t lda, int64_t m, int w, int wc, int C, int R,
-                           int64_t left_cols, int64_t right_cols, int32_t* ipiv, int64_t ipiv_add, LuSync* sync);
+                           int64_t left_cols, int64_t right_cols, int32_t* ipiv, int64_t ipiv_add, LuSync* sync,
+                           int sib, int kprev);
 
 // Recursive panel factorization of columns [j0, j0+width) over rows [j0, M)
 // of the matrix at A (absolute indices; ipiv absolute, 1-based).

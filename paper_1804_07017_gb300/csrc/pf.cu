@@ -263,6 +263,20 @@ int panel_rec(lu_context* c, cudaStream_t st, T* A, int64_t lda, int64_t M, int6
     if (w1 >= width) w1 = width / 2;
     if (w1 < 1) w1 = 1;
     const int64_t w2 = width - w1;
+    // Two 16-column leaves: the first also forms its sibling's U12 and the second
+    // applies the matching rank-w1 update in its prologue (no launch in between).
+    if (cluster && w1 <= 16 && w2 <= 16 && w1 <= leaf && w2 <= leaf && lu_pf_leaf_pairs_supported()) {
+        int Ca = 0, Ra = 0, Cb = 0, Rb = 0;
+        size_t sa = 0, sb = 0;
+        if (lu_pf_cluster_shape<T>(rows, (int)w1, c->pf_smem_budget, &Ca, &Ra, &sa) &&
+            lu_pf_cluster_shape<T>(rows - w1, (int)w2, c->pf_smem_budget, &Cb, &Rb, &sb)) {
+            LU_TRY(lu_launch_pf_leaf_cluster<T>(st, A + j0 + j0 * lda, lda, rows, (int)w1, Ca, Ra, sa, j0 - pc0,
+                                                pc0 + pw - (j0 + w1), ipiv + j0, j0, &c->sync[0], (int)w2, 0));
+            const int64_t jb = j0 + w1;
+            return lu_launch_pf_leaf_cluster<T>(st, A + jb + jb * lda, lda, rows - w1, (int)w2, Cb, Rb, sb, jb - pc0,
+                                                pc0 + pw - (jb + w2), ipiv + jb, jb, &c->sync[0], 0, (int)w1);
+        }
+    }
     LU_TRY(panel_rec<T>(c, st, A, lda, M, j0, w1, ipiv, o, leaf, cluster, pc0, pw));
     if (!cluster) {
         // interchanges of the left half applied to the right half's columns

@@ -391,21 +391,30 @@ bool lu_pf_cluster_shape(int64_t m, int w, size_t budget, int* C_out, int* R_out
     return false;
 }
 
-template <typename T>
-int lu_launch_pf_leaf_cluster(cudaStream_t st, T* A, int64_t lda, int64_t m, int w, int C, int R, size_t smem,
-                              int64_t left_cols, int64_t right_cols, int32_t* ipiv, int64_t ipiv_add, LuSync* sync) {
-    // Default: pushed messages with mbarrier completion (pf_push.cu).
-    // LU_GB300_PF_BARRIER=cluster selects candidates read through distributed
-    // shared memory after a hardware cluster barrier; =global the same with the
-    // bounded global-memory barrier.
+// Default: pushed messages with mbarrier completion (pf_push.cu).
+// LU_GB300_PF_BARRIER=cluster selects candidates read through distributed
+// shared memory after a hardware cluster barrier; =global the same with the
+// bounded global-memory barrier.
+static int leaf_mode() {
     static int mode = -1;
     if (mode < 0) {
         const char* e = getenv("LU_GB300_PF_BARRIER");
         mode = (e && e[0] == 'g') ? 0 : ((e && e[0] == 'c') ? 1 : 2);
     }
+    return mode;
+}
+
+bool lu_pf_leaf_pairs_supported() { return leaf_mode() == 2; }
+
+template <typename T>
+int lu_launch_pf_leaf_cluster(cudaStream_t st, T* A, int64_t lda, int64_t m, int w, int C, int R, size_t smem,
+                              int64_t left_cols, int64_t right_cols, int32_t* ipiv, int64_t ipiv_add, LuSync* sync,
+                              int sib, int kprev) {
+    const int mode = leaf_mode();
     if (mode == 2)
         return lu_launch_pf_leaf_push<T>(st, A, lda, m, w, compiled_width(w), C, R, left_cols, right_cols, ipiv,
-                                         ipiv_add, sync);
+                                         ipiv_add, sync, sib, kprev);
+    if (sib != 0 || kprev != 0) return LU_ERR_UNSUPPORTED;
     const int hw = mode;
     auto fn = LeafTable<T>::get(compiled_width(w), R / kNT, hw != 0);
     if (!fn) return LU_ERR_UNSUPPORTED;
@@ -435,6 +444,6 @@ int lu_launch_pf_leaf_cluster(cudaStream_t st, T* A, int64_t lda, int64_t m, int
 template bool lu_pf_cluster_shape<double>(int64_t, int, size_t, int*, int*, size_t*);
 template bool lu_pf_cluster_shape<float>(int64_t, int, size_t, int*, int*, size_t*);
 template int lu_launch_pf_leaf_cluster<double>(cudaStream_t, double*, int64_t, int64_t, int, int, int, size_t, int64_t,
-                                               int64_t, int32_t*, int64_t, LuSync*);
+                                               int64_t, int32_t*, int64_t, LuSync*, int, int);
 template int lu_launch_pf_leaf_cluster<float>(cudaStream_t, float*, int64_t, int64_t, int, int, int, size_t, int64_t,
-                                              int64_t, int32_t*, int64_t, LuSync*);
+                                              int64_t, int32_t*, int64_t, LuSync*, int, int);

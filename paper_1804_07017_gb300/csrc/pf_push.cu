@@ -45,6 +45,7 @@ constexpr int kPT = 256;                     // threads per CTA
 #define LU_PF_PUSH_MAXREG 72
 #endif
 constexpr int kMaxC = LU_PF_MAX_CTAS_CLUSTER;  // message slots per buffer
+constexpr int kMaxPrev = 16;                   // widest preceding sibling folded into a leaf's prologue
 
 // Ordering key of a pivot candidate: |a| as an unsigned integer plus one (IEEE
 // order of non-negative values is the integer order of their bits); NaN and
@@ -178,10 +179,40 @@ struct PushSmem {
     static constexpr size_t total = msg + jrow + su + block + 16;
 };
 
+
+// Prologue of a leaf that follows a sibling leaf: the sibling's rank-kprev
+// update of this leaf's rows, A(r, c) -= sum_k L(r, k) U12(k, c), with the
+// multipliers L(r, k) in the kprev columns left of the leaf and U12 staged in
+// sU (kprev x (W+1)); the same k-ordered FMA accumulation followed by one
+// subtraction as the separate update kernel.  Kept out of line so that its
+// registers do not add to the column loop's.
+template <typename T, int W, int RQ>
+__device__ __noinline__ void leaf_prologue(const T* __restrict__ A, int64_t lda, int row0, int nrows, int w,
+                                           int kprev, T* __restrict__ sA, const T* __restrict__ sU) {
+    constexpr int WP = W + 1;
+#pragma unroll 1
+    for (int q = 0; q < RQ; ++q) {
+        const int r = threadIdx.x + kPT * q;
+        if (r >= nrows) continue;
+        T l[kMaxPrev];
+#pragma unroll
+        for (int k = 0; k < kMaxPrev; ++k)
+            l[k] = (k < kprev) ? A[(int64_t)(row0 + r) + (int64_t)(k - kprev) * lda] : T(0);
+#pragma unroll 1
+        for (int c = 0; c < w; ++c) {
+            T acc = T(0);
+#pragma unroll
+            for (int k = 0; k < kMaxPrev; ++k)
+                if (k < kprev) acc = fma(l[k], sU[k * (W + 1) + c], acc);
+            sA[r * WP + c] -= acc;
+        }
+    }
+}
+
 template <typename T, int W, int RQ>
 __global__ void __maxnreg__(LU_PF_PUSH_MAXREG)
     pf_leaf_push_kernel(T* __restrict__ A, int64_t lda, int m, int w, int left_cols, int right_cols,
-                        int32_t* __restrict__ ipiv, int ipiv_add, LuSync* __restrict__ sync) {
+                        int32_t* __restrict__ ipiv, int ipiv_add, LuSync* __restrict__ sync, int sib, int kprev) {
     typedef PivKey<T> PK;
     typedef typename PK::K K;
     typedef MsgLayout<T, W> ML;
@@ -203,6 +234,7 @@ __global__ void __maxnreg__(LU_PF_PUSH_MAXREG)
     __shared__ int s_piv[W];
     __shared__ int s_info;
     __shared__ int s_dst[2 * W], s_src[2 * W], s_cnt;
+    __shared__ T sU0[kMaxPrev][W + 1];  // U12 of the preceding sibling leaf (prologue)
 
     const int C = (int)cluster.num_blocks();
     const int g = (int)cluster.block_rank();
@@ -237,8 +269,17 @@ __global__ void __maxnreg__(LU_PF_PUSH_MAXREG)
             }
         }
     asm volatile("cp.async.commit_group;\n\tcp.async.wait_all;" ::: "memory");
+    // U12 of the preceding sibling leaf: rows -kprev..-1 of this leaf's columns
+    for (int e = tid; e < kprev * w; e += kPT) {
+        const int k = e % kprev, c = e / kprev;
+        sU0[k][c] = A[(int64_t)(k - kprev) + (int64_t)c * lda];
+    }
     // every CTA's barriers are initialised before anyone pushes
     cluster.sync();
+    if (kprev > 0) {
+        leaf_prologue<T, W, RQ>(A, lda, row0, nrows, w, kprev, sA, &sU0[0][0]);
+        __syncthreads();
+    }
 
     T v[RQ][SB];
 
@@ -523,8 +564,34 @@ __global__ void __maxnreg__(LU_PF_PUSH_MAXREG)
         }
         __syncthreads();
         const int cnt = s_cnt;
+        // The sibling's columns (the first sib right columns): CTA 0 applies the
+        // interchanges and then solves their top w rows with this leaf's unit-lower
+        // L11 (lane = row, x_i := fma(-L(i, j), x_j, x_i) for j = 0, 1, ...), which
+        // makes them the sibling's U12; the sibling folds the matching update into
+        // its prologue.
+        if (g == 0) {
+            for (int t = warp; t < sib; t += kPT / 32) {
+                T* a = A + (int64_t)(w + t) * lda;
+                T vv[(2 * W + 31) / 32];
+#pragma unroll
+                for (int u = 0; u < (2 * W + 31) / 32; ++u)
+                    if (lane + 32 * u < cnt) vv[u] = a[s_src[lane + 32 * u]];
+                __syncwarp();
+#pragma unroll
+                for (int u = 0; u < (2 * W + 31) / 32; ++u)
+                    if (lane + 32 * u < cnt) a[s_dst[lane + 32 * u]] = vv[u];
+                __syncwarp();
+                T x = (lane < w) ? a[lane] : T(0);
+                for (int j = 0; j < w; ++j) {
+                    const T xj = __shfl_sync(0xffffffffu, x, j);
+                    if (lane > j && lane < w) x = fma(-sA[lane * WP + j], xj, x);
+                }
+                if (lane < w) a[lane] = x;
+            }
+        }
         // columns q = g, g + C, ... of the other columns; one warp per column
         for (int q = g * (kPT / 32) + warp; cnt > 0 && q < other; q += C * (kPT / 32)) {
+            if (q >= left_cols && q < left_cols + sib) continue;
             const int64_t col = (q < left_cols) ? (int64_t)q - left_cols : (int64_t)w + (q - left_cols);
             T* a = A + col * lda;
             T vv[(2 * W + 31) / 32];
@@ -542,7 +609,7 @@ __global__ void __maxnreg__(LU_PF_PUSH_MAXREG)
 
 template <typename T>
 struct PushTable {
-    typedef void (*Fn)(T*, int64_t, int, int, int, int, int32_t*, int, LuSync*);
+    typedef void (*Fn)(T*, int64_t, int, int, int, int, int32_t*, int, LuSync*, int, int);
     static Fn get(int w, int rq, size_t* smem) {
 #define LU_PUSH_CASE(WW, RR)                                        \
     if (w == WW && rq == RR) {                                      \
@@ -571,10 +638,12 @@ size_t lu_pf_push_smem(int esize, int w, int rq) {
 
 template <typename T>
 int lu_launch_pf_leaf_push(cudaStream_t st, T* A, int64_t lda, int64_t m, int w, int wc, int C, int R,
-                           int64_t left_cols, int64_t right_cols, int32_t* ipiv, int64_t ipiv_add, LuSync* sync) {
+                           int64_t left_cols, int64_t right_cols, int32_t* ipiv, int64_t ipiv_add, LuSync* sync,
+                           int sib, int kprev) {
     size_t smem = 0;
     auto fn = PushTable<T>::get(wc, R / kPT, &smem);
-    if (!fn || C > kMaxC) return LU_ERR_UNSUPPORTED;
+    if (!fn || C > kMaxC || sib < 0 || sib > wc || sib > right_cols || kprev < 0 || kprev > kMaxPrev)
+        return LU_ERR_UNSUPPORTED;
     static bool attr_done[2][3][4] = {};
     const int wi = wc == 8 ? 0 : (wc == 16 ? 1 : 2);
     const int ri = (R / kPT) == 1 ? 0 : ((R / kPT) == 2 ? 1 : ((R / kPT) == 4 ? 2 : 3));
@@ -602,12 +671,12 @@ int lu_launch_pf_leaf_push(cudaStream_t st, T* A, int64_t lda, int64_t m, int w,
         fprintf(stderr, "[lu launch] push leaf esize %d m %lld w %d (compiled %d) C %d R %d smem %zu left %lld right %lld\n",
                 (int)sizeof(T), (long long)m, w, wc, C, R, smem, (long long)left_cols, (long long)right_cols);
     LU_CHECK_CUDA(cudaLaunchKernelEx(&cfg, fn, A, lda, (int)m, w, (int)left_cols, (int)right_cols, ipiv, (int)ipiv_add,
-                                     sync));
+                                     sync, sib, kprev));
     lu_count_launch();
     return LU_SUCCESS;
 }
 
 template int lu_launch_pf_leaf_push<double>(cudaStream_t, double*, int64_t, int64_t, int, int, int, int, int64_t,
-                                            int64_t, int32_t*, int64_t, LuSync*);
+                                            int64_t, int32_t*, int64_t, LuSync*, int, int);
 template int lu_launch_pf_leaf_push<float>(cudaStream_t, float*, int64_t, int64_t, int, int, int, int, int64_t,
-                                           int64_t, int32_t*, int64_t, LuSync*);
+                                           int64_t, int32_t*, int64_t, LuSync*, int, int);
