@@ -125,3 +125,42 @@ def test_batched_factor_then_solve(lu, dtype):
         b = rhs[i] if dtype == torch.float64 else rhs[i].astype(np.float32).astype(np.float64)
         eta = oracle.backward_error(src, x, b)
         assert eta <= (1e-14 if dtype == torch.float64 else 64 * sizes[i] * u), (i, eta)
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_batched_full_size_sampled(lu, dtype):
+    """The benchmarked batch at full size (4096 systems, n log-uniform in
+    [16, 512], nrhs 1..8, one launch): every info is 0 and a sample of 48
+    systems meets the parity criteria against the oracle."""
+    count = 4096
+    sizes, nrhs = synth.batched_sizes(count, seed=0)
+    mats = synth.batched_matrices(sizes, seed=0)
+    g = synth.rng(0, 9)
+    rhs = [g.uniform(-1, 1, size=(int(n), int(r))) for n, r in zip(sizes, nrhs)]
+    if dtype == torch.float32:
+        mats = [m.astype(np.float32).astype(np.float64) for m in mats]
+        rhs = [b.astype(np.float32).astype(np.float64) for b in rhs]
+    dA = [colmajor_dev(m, dtype) for m in mats]
+    dB = [colmajor_dev(b, dtype) for b in rhs]
+    piv = [torch.zeros(int(n), dtype=torch.int32, device="cuda") for n in sizes]
+    batch = lu.Batch(dA, piv, dB)
+    lu.lu_gesv_batched(batch)
+    torch.cuda.synchronize()
+    assert np.all(batch.info.cpu().numpy() == 0)
+    u = np.finfo(np.float32 if dtype == torch.float32 else np.float64).eps / 2
+    tau = 1e-8 if dtype == torch.float64 else 1e-3
+    pick = synth.rng(5, 5).choice(count, size=48, replace=False)
+    pick[:2] = [int(np.argmax(sizes)), int(np.argmin(sizes))]
+    for i in pick:
+        n = int(sizes[i])
+        LU = dA[i].cpu().double().numpy()
+        p = piv[i].cpu().numpy()
+        _, po, _, gap = oracle.getrf(mats[i])
+        sep = gap > tau
+        assert np.array_equal(p[sep], po[sep]), i
+        fe = oracle.factor_error(mats[i], LU, p)
+        eta = oracle.backward_error(mats[i], dB[i].cpu().double().numpy(), rhs[i])
+        if dtype == torch.float64:
+            assert fe <= 1e-14 and eta <= 1e-14, (i, n, fe, eta)
+        else:
+            assert fe <= 4 * u * 2 and eta <= 64 * n * u, (i, n, fe, eta)

@@ -169,3 +169,48 @@ def test_gesv_mixed_16384_sampled(lu):
     eta = np.abs(r).max() / (np.abs(A0).sum(axis=1).max() * np.abs(x).max() + np.abs(B0).max())
     print(f"\n[gesv_mixed 16384] status={status} refinements={iters} eta(gpu)={eta_gpu:.2e} eta(host)={eta:.2e}")
     assert status == 0 and eta <= 1e-14
+
+
+def test_gesv_full_size_n16384(lu):
+    """The benchmarked configuration at full size (n = 16384, nb = 256, N(0,1),
+    b = A * ones, split-bf16 x6 update, depth-1 look-ahead, FP64 refinement):
+    converged status, the oracle's normwise backward error (compensated sums) of
+    the returned x <= 1e-14, the forward error against x = ones within the
+    condition-number scale, and, on sampled rows of the FP32 factors,
+    ||(P A32 - L U)(i, :)||_1 / (n ||A||_inf) at the split-bf16 level."""
+    n = 16384
+    A0 = synth.normal_matrix(n, seed=0)
+    B0 = synth.ones_rhs(A0)
+    X = dev(np.zeros_like(B0))
+    status, iters, eta_gpu = lu.lu_gesv_mixed(dev(A0), dev(B0), X, PRECS["bf16x6"], 1e-14, 30,
+                                              lu.default_opts(nb=256))
+    torch.cuda.synchronize()
+    x = X.cpu().numpy()
+    eta = oracle.backward_error(A0, x, B0)
+    print(f"\n[gesv n=16384 bf16x6] status={status} refinements={iters} eta(gpu)={eta_gpu:.2e} eta(oracle)={eta:.2e} "
+          f"max|x-1|={np.abs(x - 1).max():.2e}")
+    assert status == 0 and iters <= 30
+    assert eta <= 1e-14
+    # the FP32 factorization of the same matrix, checked row by row on a sample
+    A32 = A0.astype(np.float32)
+    A = dev(A32.astype(np.float64), torch.float32)
+    ipiv = torch.zeros(n, dtype=torch.int32, device="cuda")
+    info = torch.zeros(1, dtype=torch.int32, device="cuda")
+    lu.lu_factor_mixed_ex(A, ipiv, info, PRECS["bf16x6"], lu.default_opts(nb=256))
+    torch.cuda.synchronize()
+    assert int(info.item()) == 0
+    LU = A.cpu().double().numpy()
+    piv = ipiv.cpu().numpy()
+    order = np.arange(n)
+    for k in range(n):
+        p = piv[k] - 1
+        order[k], order[p] = order[p], order[k]
+    Ad = A32.astype(np.float64)
+    anorm = np.abs(Ad).sum(axis=1).max()
+    U = np.triu(LU)
+    g = synth.rng(98, 0)
+    for i in np.concatenate([[0, 1, n // 2, n - 1], g.integers(0, n, size=12)]):
+        l = LU[i, : i + 1].copy()
+        l[i] = 1.0
+        r = Ad[order[i], :] - l @ U[: i + 1, :]
+        assert np.abs(r).sum() / (n * anorm) <= 8 * UOP["bf16x6"], i
