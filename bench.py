@@ -93,6 +93,24 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def max_over_ranks(x: float, dist_mod) -> float:
+    """The maximum of x over all ranks (x itself without a process group).  The
+    tensor lives where the backend wants it: CUDA for NCCL, host for gloo."""
+    if dist_mod is None:
+        return float(x)
+    import torch
+    dev = "cuda" if dist_mod.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist_mod.all_reduce(t, op=dist_mod.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(flops_per_rank: float, world: int, ms_per_step: float) -> float:
+    """Whole-job GFLOP/s: every rank solves its own system (replicas, weak
+    scaling), the step time is the slowest rank's."""
+    return world * flops_per_rank / (ms_per_step * 1e-3) / 1e9
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -167,6 +185,10 @@ def workload_config(args):
 
 
 def main():
+    return main_with_args(None)
+
+
+def main_with_args(argv):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
@@ -180,7 +202,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle sample")
     ap.add_argument("--workload", default="mixed", choices=["mixed", "batched", "configs"],
                     help="mixed: the n=16384 solver (default); batched: 4096 uneven systems")
-    args = ap.parse_args()
+    args = ap.parse_args(argv)
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "configs":
@@ -265,13 +287,9 @@ def main():
     L.lu_profile_enable(0)
     L.lu_profile_stride(1)
     launches = lu.lu_launch_count() - launches0
-    ms_total = ev0.elapsed_time(ev1)
-    if dist is not None:
-        t = torch.tensor([ms_total], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_total = float(t.item())
+    ms_total = max_over_ranks(ev0.elapsed_time(ev1), dist)
     ms_step = ms_total / args.steps
-    value = world * flops / (ms_step * 1e-3) / 1e9
+    value = job_throughput(flops, world, ms_step)
     statuses = [r[0] for r in results]
     iters = [r[1] for r in results]
     etas = [r[2] for r in results]
@@ -319,8 +337,8 @@ def main():
             X_h.copy_(Xt, non_blocking=True)
         t1.record(stream)
         torch.cuda.synchronize()
-        e_ms = t0.elapsed_time(t1) / e_steps
-        e2e = {"value": world * flops / (e_ms * 1e-3) / 1e9, "unit": "GFLOP/s",
+        e_ms = max_over_ranks(t0.elapsed_time(t1) / e_steps, dist)
+        e2e = {"value": job_throughput(flops, world, e_ms), "unit": "GFLOP/s",
                "h2d_bytes_per_step": 8 * n * n + 8 * n * nrhs, "d2h_bytes_per_step": 8 * n * nrhs,
                "ms_per_step": e_ms}
 
