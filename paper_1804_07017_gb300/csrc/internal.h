@@ -73,7 +73,7 @@ int lu_launch_laswp_plan(cudaStream_t st, const int32_t* ipiv, int64_t k1, int64
 // Apply a plan to columns [c1, c1+n1) and [c2, c2+n2) of A.
 template <typename T>
 int lu_launch_laswp_apply(cudaStream_t st, T* A, int64_t lda, int64_t c1, int64_t n1,
-                          int64_t c2, int64_t n2, const int32_t* plan, int64_t K, int num_sms);
+                          int64_t c2, int64_t n2, const int32_t* plan, int64_t K, int num_sms, int max_blocks = 0);
 
 // RL2 + RL3 of a narrow panel node in one launch (w1, w2 <= 32), bit-identical to
 // lu_launch_trsm_lunit followed by lu_launch_gemm_update.  arrivals: one zeroed
@@ -83,7 +83,7 @@ int lu_launch_trsm_gemm_narrow(cudaStream_t st, int64_t m2, int64_t w2, int64_t 
                                const T* A21, T* A22, int64_t lda, unsigned* arrivals);
 template <typename T>
 int lu_launch_trsm_lunit(cudaStream_t st, int64_t m, int64_t n, const T* L, int64_t ldl, T* B,
-                         int64_t ldb);
+                         int64_t ldb, int max_ctas = 0);
 
 template <typename T>
 int lu_launch_gemm_update(cudaStream_t st, int64_t m, int64_t n, int64_t k, const T* A,

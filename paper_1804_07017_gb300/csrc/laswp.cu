@@ -131,7 +131,7 @@ int lu_launch_laswp_plan(cudaStream_t st, const int32_t* ipiv, int64_t k1, int64
 
 template <typename T>
 int lu_launch_laswp_apply(cudaStream_t st, T* A, int64_t lda, int64_t c1, int64_t n1, int64_t c2,
-                          int64_t n2, const int32_t* plan, int64_t K, int num_sms) {
+                          int64_t n2, const int32_t* plan, int64_t K, int num_sms, int max_blocks) {
     if (K <= 0 || n1 + n2 <= 0) return LU_SUCCESS;
     const int warps = kApplyThreads / 32;
     size_t smem = sizeof(T) * 2 * (size_t)K * warps;
@@ -143,7 +143,7 @@ int lu_launch_laswp_apply(cudaStream_t st, T* A, int64_t lda, int64_t c1, int64_
         attr[ti] = true;
     }
     int64_t blocks = lu_cdiv(n1 + n2, warps);
-    blocks = std::min<int64_t>(blocks, (int64_t)std::max(num_sms, 1) * 8);
+    blocks = std::min<int64_t>(blocks, max_blocks > 0 ? (int64_t)max_blocks : (int64_t)std::max(num_sms, 1) * 8);
     LuProfScope prof(st, LU_K_LASWP, 2.0 * 2.0 * K * (double)(n1 + n2) * sizeof(T), 0.0);
     laswp_apply_kernel<T><<<(unsigned)blocks, kApplyThreads, smem, st>>>(A, lda, c1, n1, c2, n2, plan, (int)K);
     LU_CHECK_LAUNCH();
@@ -151,6 +151,6 @@ int lu_launch_laswp_apply(cudaStream_t st, T* A, int64_t lda, int64_t c1, int64_
 }
 
 template int lu_launch_laswp_apply<double>(cudaStream_t, double*, int64_t, int64_t, int64_t, int64_t,
-                                           int64_t, const int32_t*, int64_t, int);
+                                           int64_t, const int32_t*, int64_t, int, int);
 template int lu_launch_laswp_apply<float>(cudaStream_t, float*, int64_t, int64_t, int64_t, int64_t,
-                                          int64_t, const int32_t*, int64_t, int);
+                                          int64_t, const int32_t*, int64_t, int, int);

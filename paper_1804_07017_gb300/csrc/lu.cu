@@ -177,13 +177,16 @@ static int trailing_update(lu_context* c, cudaStream_t st, int64_t n, T* A, int6
                            int64_t kb, int64_t c_begin, int64_t c_end, int64_t left_cols, const int32_t* plan,
                            const LuTuEngine* eng, int which) {
     const int64_t ncols = c_end - c_begin;
+    // the right update's interchanges and RL2 run on at most the right update's share
+    // of the SMs (as its tensor-core part), leaving the rest to the panel path
+    const int cap = which == 1 ? std::max(1, c->num_sms - std::max(4, c->num_sms / 6)) : 0;
     if (ncols > 0 || left_cols > 0)
         LU_TRY(lu_launch_laswp_apply<T>(st, A, lda, c_begin, std::max<int64_t>(ncols, 0), 0, left_cols,
-                                        plan, kb, c->num_sms));
+                                        plan, kb, c->num_sms, cap));
     if (ncols <= 0) return LU_SUCCESS;
     T* A11 = A + k0 + k0 * lda;
     T* A12 = A + k0 + c_begin * lda;
-    LU_TRY(lu_launch_trsm_lunit<T>(st, kb, ncols, A11, lda, A12, lda));
+    LU_TRY(lu_launch_trsm_lunit<T>(st, kb, ncols, A11, lda, A12, lda, cap));
     const int64_t m2 = n - (k0 + kb);
     if (m2 <= 0) return LU_SUCCESS;
     if (eng && eng->uses_tc(kb)) {
@@ -221,14 +224,17 @@ int lu_factor_blocked(lu_context* c, int64_t n, T* A, int64_t lda, int32_t* ipiv
         const int64_t c1 = k0 + kb;                       // first column right of panel k
         const int64_t c2 = std::min<int64_t>(n, c1 + nb); // end of panel k+1
         if (o.lookahead) {
+            // PU(k+1) = TU_k^L + PF_{k+1} on the high-priority stream.  TU_k^L (the
+            // next panel's interchanges, RL2 and RL3: a few narrow launches) runs
+            // before TU_right(k) is released, so that it does not wait behind the
+            // right update's thousands of CTAs; PF_{k+1} then overlaps TU_right(k).
+            if (k + 1 < nk) LU_TRY(trailing_update<T>(c, hi, n, A, lda, k, k0, kb, c1, c2, 0, plan_of(k), eng, 0));
             LU_CHECK_CUDA(cudaEventRecord(c->ev_pf, hi));
             LU_CHECK_CUDA(cudaStreamWaitEvent(lo, c->ev_pf, 0));
             // TU_right(k) and the deferred left interchanges on the low-priority stream
             LU_TRY(trailing_update<T>(c, lo, n, A, lda, k, k0, kb, c2, n, k0, plan_of(k), eng, 1));
             LU_CHECK_CUDA(cudaEventRecord(c->ev_tu, lo));
             if (k + 1 < nk) {
-                // PU(k+1) = TU_k^L + PF_{k+1} on the high-priority stream
-                LU_TRY(trailing_update<T>(c, hi, n, A, lda, k, k0, kb, c1, c2, 0, plan_of(k), eng, 0));
                 LU_TRY(panel(k + 1));
                 if (eng && o.steal) LU_TRY(eng->steal(hi, k));
                 LU_CHECK_CUDA(cudaStreamWaitEvent(hi, c->ev_tu, 0));

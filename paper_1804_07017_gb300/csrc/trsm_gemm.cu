@@ -25,8 +25,11 @@ __global__ void __launch_bounds__(kTrsmThreads)
     T* sB = reinterpret_cast<T*>(smraw);  // [COLS][mp]
     T* sL = sB + (size_t)COLS * mp;        // [32][33] diagonal block, sL[j*33 + i] = L(J+i, J+j)
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int64_t col0 = (int64_t)blockIdx.x * COLS;
+    const int64_t nblocks = (n + COLS - 1) / COLS;
+    for (int64_t cb = blockIdx.x; cb < nblocks; cb += gridDim.x) {
+    const int64_t col0 = cb * COLS;
     const int nc = (int)min((int64_t)COLS, n - col0);
+    __syncthreads();
     for (int c = 0; c < COLS; ++c)
         for (int r = tid; r < mp; r += kTrsmThreads)
             sB[c * mp + r] = (c < nc && r < m) ? B[r + (col0 + c) * ldb] : T(0);
@@ -67,6 +70,7 @@ __global__ void __launch_bounds__(kTrsmThreads)
     __syncthreads();
     for (int c = 0; c < nc; ++c)
         for (int r = tid; r < m; r += kTrsmThreads) B[r + (col0 + c) * ldb] = sB[c * mp + r];
+    }
 }
 
 
@@ -334,7 +338,7 @@ __global__ void __launch_bounds__(kGemmThreads)
 
 template <typename T>
 int lu_launch_trsm_lunit(cudaStream_t st, int64_t m, int64_t n, const T* L, int64_t ldl, T* B,
-                         int64_t ldb) {
+                         int64_t ldb, int max_ctas) {
     if (m <= 0 || n <= 0) return LU_SUCCESS;
     if (m > LU_MAX_NB) return LU_ERR_UNSUPPORTED;
     const int mp = (int)((m + 31) & ~31);
@@ -349,6 +353,11 @@ int lu_launch_trsm_lunit(cudaStream_t st, int64_t m, int64_t n, const T* L, int6
                                            cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
         attr[ti] = true;
     }
+    // max_ctas > 0 caps the grid (the CTAs then loop over column blocks), so a wide
+    // solve on the low-priority stream leaves SMs to the panel path
+    auto grid_of = [&](int64_t blocks) {
+        return (unsigned)(max_ctas > 0 ? std::min<int64_t>(blocks, max_ctas) : blocks);
+    };
     LuProfScope prof(st, LU_K_TRSM, sizeof(T) * (2.0 * m * n + 0.5 * m * m), (double)m * m * n);
     // stage L in shared memory when the packed triangle and a 16-column block fit and
     // few CTAs share it (the look-ahead and in-panel solves); a wide solve keeps the
@@ -364,9 +373,9 @@ int lu_launch_trsm_lunit(cudaStream_t st, int64_t m, int64_t n, const T* L, int6
         trsm_lunit_staged_kernel<T, 16><<<(unsigned)lu_cdiv(n, 16), kTrsmThreads, staged, st>>>((int)m, n, L, ldl, B,
                                                                                               ldb);
     } else if (smem16 <= 64 * 1024) {
-        trsm_lunit_kernel<T, 16><<<(unsigned)lu_cdiv(n, 16), kTrsmThreads, smem16, st>>>((int)m, n, L, ldl, B, ldb);
+        trsm_lunit_kernel<T, 16><<<grid_of(lu_cdiv(n, 16)), kTrsmThreads, smem16, st>>>((int)m, n, L, ldl, B, ldb);
     } else {
-        trsm_lunit_kernel<T, 8><<<(unsigned)lu_cdiv(n, 8), kTrsmThreads, smem8, st>>>((int)m, n, L, ldl, B, ldb);
+        trsm_lunit_kernel<T, 8><<<grid_of(lu_cdiv(n, 8)), kTrsmThreads, smem8, st>>>((int)m, n, L, ldl, B, ldb);
     }
     LU_CHECK_LAUNCH();
     return LU_SUCCESS;
@@ -398,9 +407,9 @@ int lu_launch_gemm_update(cudaStream_t st, int64_t m, int64_t n, int64_t k, cons
 }
 
 template int lu_launch_trsm_lunit<double>(cudaStream_t, int64_t, int64_t, const double*, int64_t,
-                                          double*, int64_t);
+                                          double*, int64_t, int);
 template int lu_launch_trsm_lunit<float>(cudaStream_t, int64_t, int64_t, const float*, int64_t,
-                                         float*, int64_t);
+                                         float*, int64_t, int);
 template int lu_launch_gemm_update<double>(cudaStream_t, int64_t, int64_t, int64_t, const double*,
                                            int64_t, const double*, int64_t, double*, int64_t);
 template int lu_launch_gemm_update<float>(cudaStream_t, int64_t, int64_t, int64_t, const float*,
