@@ -312,6 +312,12 @@ def main_with_args(argv):
         roof["note"] = ("panel-factorization leaf (thread-block cluster, pushed candidate messages): bound by the "
                         "per-column exchange latency, not by HBM; bytes = read+write of the leaf block plus its "
                         "interchanges on the other panel columns")
+    if dom == "panel":
+        # latency view: the leaves' time per eliminated column (every column passes one leaf)
+        roof["latency"] = {"us_per_column": d["ms"] * PROF_STRIDE / args.steps / n * 1e3,
+                           "columns_per_step": n,
+                           "note": "pipelined, beside the tensor-core update; 2.8 us alone at m = 16384 "
+                                   "(profiles/pf_leaf_push_kernel_m16384_w16.md)"}
     roof["sampled"] = f"1 launch in {PROF_STRIDE} of the class carries events in the timed region"
     roof["launches_sampled"] = d["launches"]
     roof["launches"] = d["launches"] * PROF_STRIDE
