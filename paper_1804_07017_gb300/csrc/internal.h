@@ -50,9 +50,21 @@ struct lu_context {
     // Shared memory a panel leaf CTA may use: small enough, on the mixed path, to
     // sit beside a tensor-core trailing-update CTA on the same SM.
     size_t pf_smem_budget = 160 * 1024;
+    // Replay of the mixed factorization as a CUDA graph: the arguments it was
+    // captured for (fkey), the instantiated graph, its kernel count, and the key
+    // of the previous eager run (a key is captured on its second use).
+    cudaGraphExec_t fgraph_exec = nullptr;
+    cudaStream_t gs = nullptr;                    // capture/replay stream (non-blocking)
+    cudaEvent_t ev_g0 = nullptr, ev_g1 = nullptr; // user -> gs and gs -> user
+    long long fgraph_launches = 0;
+    uint64_t fkey[10] = {};
+    uint64_t fkey_seen[10] = {};
     std::mutex mu;
 };
 
+void lu_count_launches(long long k);
+long long lu_launches_so_far();
+int lu_profile_active();
 int lu_ctx_init(lu_context* c);
 int lu_ctx_release(lu_context* c);
 // Makes sure the workspace can hold a factorization of order n with panel

@@ -25,6 +25,8 @@ static char g_last_error[512] = "";
 static std::mutex g_err_mu;
 
 void lu_count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void lu_count_launches(long long k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+long long lu_launches_so_far() { return g_launches.load(); }
 
 void lu_set_error_string(const char* what, const char* file, int line) {
     std::lock_guard<std::mutex> lk(g_err_mu);
@@ -66,6 +68,13 @@ int lu_ctx_release(lu_context* c) {
     c->host_eta = nullptr;
     if (c->batch_ws) cudaFree(c->batch_ws);
     c->batch_ws = nullptr;
+    if (c->fgraph_exec) cudaGraphExecDestroy(c->fgraph_exec);
+    c->fgraph_exec = nullptr;
+    if (c->ev_g0) cudaEventDestroy(c->ev_g0);
+    if (c->ev_g1) cudaEventDestroy(c->ev_g1);
+    if (c->gs) cudaStreamDestroy(c->gs);
+    c->ev_g0 = c->ev_g1 = nullptr;
+    c->gs = nullptr;
     cudaEvent_t evs[] = {c->ev_fork, c->ev_pf, c->ev_tu, c->ev_join_hi, c->ev_join_lo, c->ev_steal};
     for (cudaEvent_t e : evs)
         if (e) cudaEventDestroy(e);

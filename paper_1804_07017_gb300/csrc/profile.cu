@@ -136,6 +136,10 @@ extern "C" int lu_profile_enable(int mask) {
     return LU_SUCCESS;
 }
 
+// Nonzero while any kernel class is profiled (graph replay is then bypassed, so
+// that every launch carries its events).
+int lu_profile_active() { return g_mask != 0 || timeline_file() != nullptr; }
+
 extern "C" int lu_profile_stride(int every) {
     std::lock_guard<std::mutex> lk(g_mu);
     g_stride = every > 1 ? every : 1;

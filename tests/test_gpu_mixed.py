@@ -214,3 +214,27 @@ def test_gesv_full_size_n16384(lu):
         l[i] = 1.0
         r = Ad[order[i], :] - l @ U[: i + 1, :]
         assert np.abs(r).sum() / (n * anorm) <= 8 * UOP["bf16x6"], i
+
+
+def test_factor_graph_replay_identical(lu):
+    """Repeated factorizations with the same arguments run eagerly, then are
+    captured and replayed as one CUDA graph: all runs give bit-identical factors
+    and pivots, and the launch counter advances by the same count each time."""
+    n, nb = 3000, 256
+    A0 = torch.from_numpy(synth.normal_matrix(n, seed=48)).float()
+    from paper_1804_07017_gb300.api import colmajor
+    A = colmajor(n, n, dtype=torch.float32)
+    ipiv = torch.zeros(n, dtype=torch.int32, device="cuda")
+    info = torch.zeros(1, dtype=torch.int32, device="cuda")
+    outs, counts = [], []
+    for _ in range(4):
+        A.copy_(A0)
+        c0 = lu.lu_launch_count()
+        lu.lu_factor_mixed_ex(A, ipiv, info, PRECS["bf16x6"], lu.default_opts(nb=nb))
+        torch.cuda.synchronize()
+        counts.append(lu.lu_launch_count() - c0)
+        assert int(info.item()) == 0
+        outs.append((A.cpu().clone(), ipiv.cpu().clone()))
+    for LU, p in outs[1:]:
+        assert torch.equal(LU, outs[0][0]) and torch.equal(p, outs[0][1])
+    assert counts[0] > 0 and len(set(counts)) == 1, counts
