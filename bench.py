@@ -30,7 +30,7 @@ sys.path.insert(0, ROOT)
 
 N_DEFAULT = 16384
 NB_DEFAULT = 256
-PROF_STRIDE = 8  # dominant-class launches timed with events inside the timed region: one in 8
+PROF_STRIDE = 7  # one dominant-class launch in 7 carries events (7: no common period with the panel recursion)
 TOL = 1e-14
 MAX_ITER = 30
 
