@@ -270,7 +270,11 @@ int lu_selftest_wait_timeout(lu_handle handle, int64_t limit_ns, int32_t *status
  * FP32 accumulation; LU_TU_F32 keeps it on the CUDA cores.  When nb is not a
  * multiple of 64 the update falls back to FP32 on the CUDA cores.  LU_TU_BF16X3
  * and LU_TU_BF16X6 run the same kernel on split operands with a 3x / 6x longer K.
- * Asynchronous; info as in lu_factor_ex.
+ * Asynchronous; info as in lu_factor_ex.  The launch sequence depends only on
+ * the arguments (pointers, sizes, options, handle stream): the second call with
+ * the same arguments captures it as a CUDA graph and later ones replay it (the
+ * data in those buffers may change freely between calls; while the launch
+ * profiler is enabled every call runs the launches directly).
  */
 int lu_factor_mixed_ex(lu_handle handle, lu_prec prec, int64_t n, float *A, int64_t lda, int32_t *ipiv,
                        const lu_opts *opts, int32_t *info);
