@@ -8,7 +8,8 @@
 // LU_blk (Sec. 3) scaled down to one CTA:
 //   PF   the 32-column panel is loaded into shared memory and eliminated
 //        column by column (block argmax, first maximum, true division);
-//   the panel's interchanges are applied to the other columns, then RL2
+//   the panel's interchanges, composed into one gather plan, are applied to
+//   the other columns a warp per column, then RL2
 //   (unit-lower solve of the U12 row block, one column per thread) and RL3
 //   (A22 -= L21 U12 with 4x4 register tiles, L21 from shared memory);
 // and then, if right-hand sides are given, solves P A X = B for them.
@@ -101,6 +102,8 @@ __device__ void block_argmax(T v, int i, T* red_v, int* red_i, T& out_v, int& ou
 template <typename T>
 __device__ int factor_one(int n, T* __restrict__ A, int64_t lda, int32_t* __restrict__ ipiv, T* sP, T* sU,
                           T* red_v, int* red_i) {
+    // interchange plan of the current panel (relative rows)
+    __shared__ int s_pdst[2 * kBNB], s_psrc[2 * kBNB], s_pcur[2 * kBNB], s_ptgt[kBNB], s_pb[kBNB], s_pcnt;
     const int tid = threadIdx.x;
     int finfo = 0;
     for (int k0 = 0; k0 < n; k0 += kBNB) {
@@ -145,17 +148,80 @@ __device__ int factor_one(int n, T* __restrict__ A, int64_t lda, int32_t* __rest
         }
         for (int c = 0; c < kb; ++c)
             for (int r = tid; r < m; r += kBT) A[(int64_t)(k0 + r) + (int64_t)(k0 + c) * lda] = sP[c * kNMAX + r];
-        // ---- the panel's interchanges on the other columns (one thread per column) ----
-        const int others = n - kb;
-        for (int q = tid; q < others; q += kBT) {
-            const int col = (q < k0) ? q : q + kb;
-            T* a = A + (int64_t)col * lda;
-            for (int j = 0; j < kb; ++j) {
-                const int p = ipiv[k0 + j] - 1;
-                if (p != k0 + j) {
-                    const T t = a[k0 + j];
-                    a[k0 + j] = a[p];
-                    a[p] = t;
+        // ---- the panel's interchanges on the other columns ----
+        // The kb sequential interchanges are composed once into a gather plan
+        // dst <- src over the panel rows and the distinct rows below them that they
+        // reach; a warp then moves a column's entries all at once (every value read
+        // before any is written), so a column costs one memory round trip instead of
+        // kb dependent ones.
+        if (tid < 32) {
+            const int lane = tid;
+            const unsigned full = 0xffffffffu;
+            const int pj = (lane < kb) ? ipiv[k0 + lane] - 1 - k0 : -1;
+            const bool below = pj >= kb;
+            const unsigned same = __match_any_sync(full, below ? pj : -1 - lane);
+            const int lead = __ffs(same) - 1;
+            const bool first = below && lead == lane;
+            const unsigned firsts = __ballot_sync(full, first);
+            const int f = __popc(firsts & ((1u << lead) - 1u));
+            if (lane < kb) s_pb[lane] = below ? kb + f : pj;
+            s_pcur[lane] = lane;
+            if (first) {
+                s_ptgt[f] = pj;
+                s_pcur[kb + f] = pj;
+            }
+            __syncwarp();
+            if (lane == 0)
+                for (int j = 0; j < kb; ++j) {
+                    const int bj = s_pb[j];
+                    if (bj != j) {
+                        const int x = s_pcur[j];
+                        s_pcur[j] = s_pcur[bj];
+                        s_pcur[bj] = x;
+                    }
+                }
+            __syncwarp();
+            const int nt = __popc(firsts);
+            const bool e0 = lane < kb && s_pcur[lane] != lane;
+            const bool e1 = lane < nt && s_pcur[kb + lane] != s_ptgt[lane];
+            const unsigned m0 = __ballot_sync(full, e0), m1 = __ballot_sync(full, e1);
+            const unsigned lt = (1u << lane) - 1u;
+            if (e0) {
+                const int i = __popc(m0 & lt);
+                s_pdst[i] = lane;
+                s_psrc[i] = s_pcur[lane];
+            }
+            if (e1) {
+                const int i = __popc(m0) + __popc(m1 & lt);
+                s_pdst[i] = s_ptgt[lane];
+                s_psrc[i] = s_pcur[kb + lane];
+            }
+            if (lane == 0) s_pcnt = __popc(m0) + __popc(m1);
+        }
+        __syncthreads();
+        {
+            const int cnt = s_pcnt, lane = tid & 31;
+            const bool h0 = lane < cnt, h1 = lane + 32 < cnt;
+            const int s0 = h0 ? s_psrc[lane] : 0, d0 = h0 ? s_pdst[lane] : 0;
+            const int s1 = h1 ? s_psrc[lane + 32] : 0, d1 = h1 ? s_pdst[lane + 32] : 0;
+            constexpr int kU = 4;  // columns per warp per round
+            const int others = n - kb;
+            for (int q0 = (tid >> 5) * kU; q0 < others && cnt > 0; q0 += (kBT / 32) * kU) {
+                T v0[kU], v1[kU];
+#pragma unroll
+                for (int u = 0; u < kU; ++u) {
+                    const int q = q0 + u;
+                    const T* a = A + (int64_t)((q < k0) ? q : q + kb) * lda + k0;
+                    v0[u] = (h0 && q < others) ? a[s0] : T(0);
+                    v1[u] = (h1 && q < others) ? a[s1] : T(0);
+                }
+                __syncwarp();
+#pragma unroll
+                for (int u = 0; u < kU; ++u) {
+                    const int q = q0 + u;
+                    T* a = A + (int64_t)((q < k0) ? q : q + kb) * lda + k0;
+                    if (h0 && q < others) a[d0] = v0[u];
+                    if (h1 && q < others) a[d1] = v1[u];
                 }
             }
         }
