@@ -7,12 +7,15 @@
 // Each CTA factors its matrix with the blocked right-looking algorithm of
 // LU_blk (Sec. 3) scaled down to one CTA:
 //   PF   the 32-column panel is loaded into shared memory and eliminated
-//        column by column (block argmax, first maximum, true division);
+//        column by column (block argmax, first maximum, true division; two
+//        barriers per column, the update of a column also finding the next
+//        column's pivot candidates);
 //   the panel's interchanges, composed into one gather plan, are applied to
 //   the other columns a warp per column, then RL2
 //   (unit-lower solve of the U12 row block, one column per thread) and RL3
 //   (A22 -= L21 U12 with 4x4 register tiles, L21 from shared memory);
-// and then, if right-hand sides are given, solves P A X = B for them.
+// and then, if right-hand sides are given, solves P A X = B for them by
+// blocks of factor columns staged in shared memory.
 #include <climits>
 
 #include "internal.h"
@@ -58,8 +61,12 @@ __global__ void __launch_bounds__(1024) batch_order_kernel(int batch, const int3
     for (int i = threadIdx.x; i < batch; i += blockDim.x) order[atomicAdd(&start[key(i)], 1)] = i;
 }
 
+// Row of the largest |value| over the CTA (first index among equal maxima;
+// NaN never wins), with one barrier: every thread reduces the per-warp winners
+// itself.  red_v/red_i hold kBT/32 slots; callers alternate two such buffers so
+// that the next call's writes cannot overtake this call's reads.
 template <typename T>
-__device__ void block_argmax(T v, int i, T* red_v, int* red_i, T& out_v, int& out_i) {
+__device__ int block_argmax(T v, int i, T* red_v, int* red_i) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -75,27 +82,18 @@ __device__ void block_argmax(T v, int i, T* red_v, int* red_i, T& out_v, int& ou
         red_i[warp] = i;
     }
     __syncthreads();
-    if (warp == 0) {
-        v = (lane < kBT / 32) ? red_v[lane] : T(-1);
-        i = (lane < kBT / 32) ? red_i[lane] : INT_MAX;
+    v = red_v[0];
+    i = red_i[0];
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            const T ov = __shfl_xor_sync(0xffffffffu, v, o);
-            const int oi = __shfl_xor_sync(0xffffffffu, i, o);
-            if (ov > v || (ov == v && oi < i)) {
-                v = ov;
-                i = oi;
-            }
-        }
-        if (lane == 0) {
-            red_v[0] = v;
-            red_i[0] = i;
+    for (int w = 1; w < kBT / 32; ++w) {
+        const T ov = red_v[w];
+        const int oi = red_i[w];
+        if (ov > v || (ov == v && oi < i)) {
+            v = ov;
+            i = oi;
         }
     }
-    __syncthreads();
-    out_v = red_v[0];
-    out_i = red_i[0];
-    __syncthreads();
+    return i;
 }
 
 // Factor one n x n matrix (column-major, lda) in place; ipiv 1-based; returns info.
@@ -113,19 +111,20 @@ __device__ int factor_one(int n, T* __restrict__ A, int64_t lda, int32_t* __rest
         for (int c = 0; c < kb; ++c)
             for (int r = tid; r < m; r += kBT) sP[c * kNMAX + r] = A[(int64_t)(k0 + r) + (int64_t)(k0 + c) * lda];
         __syncthreads();
-        for (int j = 0; j < kb; ++j) {
-            T bv = T(-1);
-            int bi = INT_MAX;
-            for (int r = j + tid; r < m; r += kBT) {
-                const T v = fabs(sP[j * kNMAX + r]);
-                if (v > bv || (v == bv && r < bi)) {
-                    bv = v;
-                    bi = r;
-                }
+        // Two barriers per column: one in the argmax, one after the row interchange.
+        // The update of column j also finds this thread's candidate for column j+1.
+        T bv = T(-1);
+        int bi = INT_MAX;
+        for (int r = tid; r < m; r += kBT) {
+            const T v = fabs(sP[r]);
+            if (v > bv || (v == bv && r < bi)) {
+                bv = v;
+                bi = r;
             }
-            T pv;
-            int p;
-            block_argmax(bv, bi, red_v, red_i, pv, p);
+        }
+        for (int j = 0; j < kb; ++j) {
+            const int buf = (j & 1) * (kBT / 32);
+            int p = block_argmax(bv, bi, red_v + buf, red_i + buf);
             if (p == INT_MAX) p = j;
             if (tid == 0) ipiv[k0 + j] = k0 + p + 1;
             if (p != j && tid < kb) {
@@ -135,17 +134,36 @@ __device__ int factor_one(int n, T* __restrict__ A, int64_t lda, int32_t* __rest
             }
             __syncthreads();
             const T piv = sP[j * kNMAX + j];
+            bv = T(-1);
+            bi = INT_MAX;
             if (piv == T(0)) {
                 if (finfo == 0) finfo = k0 + j + 1;
+                if (j + 1 < kb)
+                    for (int r = j + 1 + tid; r < m; r += kBT) {
+                        const T v = fabs(sP[(j + 1) * kNMAX + r]);
+                        if (v > bv || (v == bv && r < bi)) {
+                            bv = v;
+                            bi = r;
+                        }
+                    }
                 continue;
             }
             for (int r = j + 1 + tid; r < m; r += kBT) {
                 const T l = sP[j * kNMAX + r] / piv;
                 sP[j * kNMAX + r] = l;
-                for (int c = j + 1; c < kb; ++c) sP[c * kNMAX + r] = fma(-l, sP[c * kNMAX + j], sP[c * kNMAX + r]);
+                if (j + 1 < kb) {
+                    const T v1 = fma(-l, sP[(j + 1) * kNMAX + j], sP[(j + 1) * kNMAX + r]);
+                    sP[(j + 1) * kNMAX + r] = v1;
+                    const T a1 = fabs(v1);
+                    if (a1 > bv || (a1 == bv && r < bi)) {
+                        bv = a1;
+                        bi = r;
+                    }
+                }
+                for (int c = j + 2; c < kb; ++c) sP[c * kNMAX + r] = fma(-l, sP[c * kNMAX + j], sP[c * kNMAX + r]);
             }
-            __syncthreads();
         }
+        __syncthreads();
         for (int c = 0; c < kb; ++c)
             for (int r = tid; r < m; r += kBT) A[(int64_t)(k0 + r) + (int64_t)(k0 + c) * lda] = sP[c * kNMAX + r];
         // ---- the panel's interchanges on the other columns ----
@@ -292,11 +310,19 @@ __device__ int factor_one(int n, T* __restrict__ A, int64_t lda, int32_t* __rest
     return finfo;
 }
 
-// X := (P A)^-1 B with the factors in A; B n x nrhs (nrhs <= kMaxRhs), staged in shared memory.
+// X := (P A)^-1 B with the factors in A; B n x nrhs (nrhs <= kMaxRhs), staged in
+// shared memory with blocks of kSB factor columns beside it.  Per block, a warp
+// per right-hand side solves the diagonal block (lane = row, shuffles carry the
+// solved entries) and then every thread updates the remaining rows; each entry
+// receives its fma updates in the same order as the column-by-column
+// substitution, so the result does not depend on the block width.
 template <typename T>
 __device__ void solve_one(int n, const T* __restrict__ A, int64_t lda, const int32_t* __restrict__ ipiv, int nrhs,
                           T* __restrict__ B, int64_t ldb, T* sB) {
-    const int tid = threadIdx.x;
+    constexpr int kSB = kBNB - kMaxRhs;  // factor columns staged per block
+    T* sL = sB + kMaxRhs * kNMAX;
+    const unsigned full = 0xffffffffu;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     for (int e = tid; e < n * nrhs; e += kBT) {
         const int i = e % n, c = e / n;
         sB[c * kNMAX + i] = B[i + (int64_t)c * ldb];
@@ -313,19 +339,55 @@ __device__ void solve_one(int n, const T* __restrict__ A, int64_t lda, const int
         }
     }
     __syncthreads();
-    for (int j = 0; j < n; ++j) {  // unit lower
-        for (int e = tid; e < (n - j - 1) * nrhs; e += kBT) {
-            const int i = j + 1 + e % (n - j - 1), c = e / (n - j - 1);
-            sB[c * kNMAX + i] = fma(-A[i + (int64_t)j * lda], sB[c * kNMAX + j], sB[c * kNMAX + i]);
+    // unit lower, blocks forward; sL holds L[j0:n, j0:j0+jb] (rows relative to j0)
+    for (int j0 = 0; j0 < n; j0 += kSB) {
+        const int jb = min(kSB, n - j0), mr = n - j0;
+        for (int c = 0; c < jb; ++c)
+            for (int i = tid; i < mr; i += kBT) sL[c * kNMAX + i] = A[(int64_t)(j0 + i) + (int64_t)(j0 + c) * lda];
+        __syncthreads();
+        if (warp < nrhs) {
+            T* x = sB + warp * kNMAX + j0;
+            T xi = lane < jb ? x[lane] : T(0);
+            for (int j = 0; j < jb; ++j) {
+                const T xj = __shfl_sync(full, xi, j);
+                if (lane > j && lane < jb) xi = fma(-sL[j * kNMAX + lane], xj, xi);
+            }
+            if (lane < jb) x[lane] = xi;
+        }
+        __syncthreads();
+        const int rows = mr - jb;
+        for (int e = tid; e < rows * nrhs; e += kBT) {
+            const int i = jb + e % rows, c = e / rows;
+            T* x = sB + c * kNMAX + j0;
+            T xi = x[i];
+            for (int j = 0; j < jb; ++j) xi = fma(-sL[j * kNMAX + i], x[j], xi);
+            x[i] = xi;
         }
         __syncthreads();
     }
-    for (int j = n - 1; j >= 0; --j) {  // upper
-        if (tid < nrhs) sB[tid * kNMAX + j] /= A[j + (int64_t)j * lda];
+    // upper, blocks backward; sL holds U[0:j1, j0:j1]
+    for (int j1 = n; j1 > 0; j1 -= kSB) {
+        const int j0 = max(0, j1 - kSB), jb = j1 - j0;
+        for (int c = 0; c < jb; ++c)
+            for (int i = tid; i < j1; i += kBT) sL[c * kNMAX + i] = A[(int64_t)i + (int64_t)(j0 + c) * lda];
         __syncthreads();
-        for (int e = tid; e < j * nrhs; e += kBT) {
-            const int i = e % j, c = e / j;
-            sB[c * kNMAX + i] = fma(-A[i + (int64_t)j * lda], sB[c * kNMAX + j], sB[c * kNMAX + i]);
+        if (warp < nrhs) {
+            T* x = sB + warp * kNMAX + j0;
+            T xi = lane < jb ? x[lane] : T(0);
+            for (int j = jb - 1; j >= 0; --j) {
+                if (lane == j) xi = xi / sL[j * kNMAX + j0 + j];
+                const T xj = __shfl_sync(full, xi, j);
+                if (lane < j) xi = fma(-sL[j * kNMAX + j0 + lane], xj, xi);
+            }
+            if (lane < jb) x[lane] = xi;
+        }
+        __syncthreads();
+        for (int e = tid; e < j0 * nrhs; e += kBT) {
+            const int i = e % j0, c = e / j0;
+            T* x = sB + c * kNMAX;
+            T xi = x[i];
+            for (int j = jb - 1; j >= 0; --j) xi = fma(-sL[j * kNMAX + i], x[j0 + j], xi);
+            x[i] = xi;
         }
         __syncthreads();
     }
@@ -348,8 +410,8 @@ __global__ void __launch_bounds__(kBT) batched_gesv_kernel(int batch, const int3
     extern __shared__ __align__(16) unsigned char smraw[];
     T* sP = reinterpret_cast<T*>(smraw);
     T* sU = sP + (size_t)kBNB * kNMAX;
-    __shared__ T red_v[kBT / 32];
-    __shared__ int red_i[kBT / 32];
+    __shared__ T red_v[2 * (kBT / 32)];
+    __shared__ int red_i[2 * (kBT / 32)];
     __shared__ int s_idx;
     for (;;) {
         if (threadIdx.x == 0) s_idx = atomicAdd(counter, 1);
