@@ -274,11 +274,20 @@ __device__ int factor_one(int n, T* __restrict__ A, int64_t lda, int32_t* __rest
             }
             __syncthreads();
             for (int i0 = 0; i0 < mr; i0 += 64) {
-                T acc[4][4];
+                // the output tile is read before the product so that its load
+                // latency overlaps the kk loop
+                T acc[4][4], cv[4][4];
 #pragma unroll
-                for (int a = 0; a < 4; ++a)
+                for (int b = 0; b < 4; ++b) {
+                    const int jc = j0 + ty + 16 * b;
+                    const T* col = A + (int64_t)(k0 + kb + min(jc, nr - 1)) * lda + (k0 + kb);
 #pragma unroll
-                    for (int b = 0; b < 4; ++b) acc[a][b] = T(0);
+                    for (int a = 0; a < 4; ++a) {
+                        const int r = i0 + tx + 16 * a;
+                        cv[a][b] = (jc < nr && r < mr) ? col[r] : T(0);
+                        acc[a][b] = T(0);
+                    }
+                }
                 for (int kk = 0; kk < kb; ++kk) {
                     T lv[4], uv[4];
 #pragma unroll
@@ -300,7 +309,7 @@ __device__ int factor_one(int n, T* __restrict__ A, int64_t lda, int32_t* __rest
 #pragma unroll
                     for (int a = 0; a < 4; ++a) {
                         const int r = i0 + tx + 16 * a;
-                        if (r < mr) col[r] -= acc[a][b];
+                        if (r < mr) col[r] = cv[a][b] - acc[a][b];
                     }
                 }
             }

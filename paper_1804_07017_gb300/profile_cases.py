@@ -9,6 +9,10 @@
     python -m paper_1804_07017_gb300.profile_cases trsv --n 16384
         one FP32 LU of order n (mixed path), then its unit-lower and upper
         triangular solves through lu_solve_ex
+    python -m paper_1804_07017_gb300.profile_cases batched --count 4096 --prec 32
+        one persistent batched factor + solve of count systems, n_i log-uniform
+        in [16, 512], nrhs_i in 1..8, iid U[-1,1) (--prec 32 or 64 selects FP32
+        or FP64) through lu_gesv_batched
 
 Each case runs --reps times (default 2) and prints the event-timed duration of
 the last repetition.  Inputs are seeded and synthetic.
@@ -95,19 +99,42 @@ def case_trsv(a):
     print(f"trsv n={n}: solve {ms * 1e3:.1f} us, info={int(info.item())}")
 
 
+def case_batched(a):
+    sizes, nrhs = synth.batched_sizes(a.count, seed=0)
+    mats = synth.batched_matrices(sizes, seed=0)
+    g = synth.rng(0, 9)
+    dt = torch.float64 if a.prec == 64 else torch.float32
+    A0 = [torch.from_numpy(m).to(dt) for m in mats]
+    B0 = [torch.from_numpy(g.uniform(-1, 1, size=(int(n), int(r)))).to(dt) for n, r in zip(sizes, nrhs)]
+    dA = [lu.colmajor(x.shape[0], x.shape[1], dtype=dt) for x in A0]
+    dB = [lu.colmajor(x.shape[0], x.shape[1], dtype=dt) for x in B0]
+    piv = [torch.zeros(int(n), dtype=torch.int32, device="cuda") for n in sizes]
+    batch = lu.Batch(dA, piv, dB)
+    for d, x in zip(dA + dB, A0 + B0):
+        d.copy_(x)
+    ms = 0.0
+    for _ in range(a.reps):
+        for d, x in zip(dA + dB, A0 + B0):
+            d.copy_(x)
+        ms = _timed(lambda: lu.lu_gesv_batched(batch), 1)
+    ok = bool((batch.info == 0).all().item())
+    print(f"batched count={a.count} prec={a.prec}: {ms * 1e3:.1f} us, all info zero: {ok}")
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
-    ap.add_argument("case", choices=["leaf", "tc", "trsv"])
+    ap.add_argument("case", choices=["leaf", "tc", "trsv", "batched"])
     ap.add_argument("--m", type=int, default=16384)
     ap.add_argument("--n", type=int, default=8192)
     ap.add_argument("--w", type=int, default=16)
     ap.add_argument("--k", type=int, default=256)
     ap.add_argument("--prec", type=int, default=6)
+    ap.add_argument("--count", type=int, default=4096)
     ap.add_argument("--reps", type=int, default=2)
     a = ap.parse_args(argv)
     if not torch.cuda.is_available():
         raise SystemExit("a CUDA device is required")
-    {"leaf": case_leaf, "tc": case_tc, "trsv": case_trsv}[a.case](a)
+    {"leaf": case_leaf, "tc": case_tc, "trsv": case_trsv, "batched": case_batched}[a.case](a)
 
 
 if __name__ == "__main__":
