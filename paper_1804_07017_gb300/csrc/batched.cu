@@ -30,9 +30,35 @@ constexpr int kMaxRhs = 8;   // right-hand sides handled together
 
 template <typename T>
 struct BatchSmem {
-    // panel [kBNB][kNMAX] column-major, then a U12 tile [kBNB][64] for the update
-    static constexpr size_t bytes = sizeof(T) * ((size_t)kBNB * kNMAX + (size_t)kBNB * 64) + 64;
+    // panel [kBNB][kNMAX] column-major, then a U12 tile [kBNB][65] (64 columns) for the update
+    static constexpr size_t bytes = sizeof(T) * ((size_t)kBNB * kNMAX + (size_t)kBNB * 65) + 64;
 };
+
+constexpr int kUS = 65;      // row stride of the U12 tile (65: conflict-free transposed stores)
+
+// s[c * kNMAX + r] = g[r + c * ld] for r < rows (<= kNMAX), c < cols: eight columns
+// and both row halves are loaded before any is stored, so a thread keeps up to 16
+// global loads in flight instead of waiting on each.
+template <typename T>
+__device__ __forceinline__ void stage_cols(T* __restrict__ s, const T* __restrict__ g, int64_t ld, int rows, int cols) {
+    static_assert(kNMAX <= 2 * kBT, "two row slots per thread cover a column");
+    constexpr int kB = 8;
+    const int r0 = threadIdx.x, r1 = threadIdx.x + kBT;
+    for (int c0 = 0; c0 < cols; c0 += kB) {
+        T v0[kB], v1[kB];
+#pragma unroll
+        for (int u = 0; u < kB; ++u) {
+            const T* gc = g + (int64_t)min(c0 + u, cols - 1) * ld;
+            v0[u] = (c0 + u < cols && r0 < rows) ? gc[r0] : T(0);
+            v1[u] = (c0 + u < cols && r1 < rows) ? gc[r1] : T(0);
+        }
+#pragma unroll
+        for (int u = 0; u < kB; ++u) {
+            if (c0 + u < cols && r0 < rows) s[(c0 + u) * kNMAX + r0] = v0[u];
+            if (c0 + u < cols && r1 < rows) s[(c0 + u) * kNMAX + r1] = v1[u];
+        }
+    }
+}
 
 // order[] = matrix indices by decreasing n; n > kNMAX or
 // n < 0 are placed last and flagged by the main kernel.
@@ -108,8 +134,7 @@ __device__ int factor_one(int n, T* __restrict__ A, int64_t lda, int32_t* __rest
         const int kb = min(kBNB, n - k0);
         const int m = n - k0;
         // ---- PF: panel rows [k0, n) x columns [k0, k0+kb) in shared memory ----
-        for (int c = 0; c < kb; ++c)
-            for (int r = tid; r < m; r += kBT) sP[c * kNMAX + r] = A[(int64_t)(k0 + r) + (int64_t)(k0 + c) * lda];
+        stage_cols(sP, A + (int64_t)k0 + (int64_t)k0 * lda, lda, m, kb);
         __syncthreads();
         // Two barriers per column: one in the argmax, one after the row interchange.
         // The update of column j also finds this thread's candidate for column j+1.
@@ -267,10 +292,19 @@ __device__ int factor_one(int n, T* __restrict__ A, int64_t lda, int32_t* __rest
         const int tx = tid & 15, ty = tid >> 4;
         for (int j0 = 0; j0 < nr; j0 += 64) {
             // U12 columns j0 .. j0+63 into shared memory
-            for (int e = tid; e < kBNB * 64; e += kBT) {
-                const int kk = e & (kBNB - 1), jj = e / kBNB;
-                sU[kk * 64 + jj] = (kk < kb && j0 + jj < nr) ? A[(int64_t)(k0 + kk) + (int64_t)(k0 + kb + j0 + jj) * lda]
-                                                              : T(0);
+            {
+                constexpr int kPer = kBNB * 64 / kBT;
+                T v[kPer];
+#pragma unroll
+                for (int t = 0; t < kPer; ++t) {
+                    const int e = tid + t * kBT, kk = e & (kBNB - 1), jj = e / kBNB;
+                    v[t] = (kk < kb && j0 + jj < nr) ? A[(int64_t)(k0 + kk) + (int64_t)(k0 + kb + j0 + jj) * lda] : T(0);
+                }
+#pragma unroll
+                for (int t = 0; t < kPer; ++t) {
+                    const int e = tid + t * kBT, kk = e & (kBNB - 1), jj = e / kBNB;
+                    sU[kk * kUS + jj] = v[t];
+                }
             }
             __syncthreads();
             for (int i0 = 0; i0 < mr; i0 += 64) {
@@ -294,7 +328,7 @@ __device__ int factor_one(int n, T* __restrict__ A, int64_t lda, int32_t* __rest
                     for (int a = 0; a < 4; ++a) {
                         const int r = i0 + tx + 16 * a;
                         lv[a] = (r < mr) ? sP[kk * kNMAX + kb + r] : T(0);
-                        uv[a] = sU[kk * 64 + ty + 16 * a];
+                        uv[a] = sU[kk * kUS + ty + 16 * a];
                     }
 #pragma unroll
                     for (int a = 0; a < 4; ++a)
@@ -332,14 +366,13 @@ __device__ void solve_one(int n, const T* __restrict__ A, int64_t lda, const int
     T* sL = sB + kMaxRhs * kNMAX;
     const unsigned full = 0xffffffffu;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    for (int e = tid; e < n * nrhs; e += kBT) {
-        const int i = e % n, c = e / n;
-        sB[c * kNMAX + i] = B[i + (int64_t)c * ldb];
-    }
+    int* s_ipiv = reinterpret_cast<int*>(sL);  // free until the first factor block is staged
+    for (int k = tid; k < n; k += kBT) s_ipiv[k] = ipiv[k];
+    stage_cols(sB, B, ldb, n, nrhs);
     __syncthreads();
     if (tid < nrhs) {
         for (int k = 0; k < n; ++k) {
-            const int p = ipiv[k] - 1;
+            const int p = s_ipiv[k] - 1;
             if (p != k) {
                 const T t = sB[tid * kNMAX + k];
                 sB[tid * kNMAX + k] = sB[tid * kNMAX + p];
@@ -351,8 +384,7 @@ __device__ void solve_one(int n, const T* __restrict__ A, int64_t lda, const int
     // unit lower, blocks forward; sL holds L[j0:n, j0:j0+jb] (rows relative to j0)
     for (int j0 = 0; j0 < n; j0 += kSB) {
         const int jb = min(kSB, n - j0), mr = n - j0;
-        for (int c = 0; c < jb; ++c)
-            for (int i = tid; i < mr; i += kBT) sL[c * kNMAX + i] = A[(int64_t)(j0 + i) + (int64_t)(j0 + c) * lda];
+        stage_cols(sL, A + (int64_t)j0 + (int64_t)j0 * lda, lda, mr, jb);
         __syncthreads();
         if (warp < nrhs) {
             T* x = sB + warp * kNMAX + j0;
@@ -377,8 +409,7 @@ __device__ void solve_one(int n, const T* __restrict__ A, int64_t lda, const int
     // upper, blocks backward; sL holds U[0:j1, j0:j1]
     for (int j1 = n; j1 > 0; j1 -= kSB) {
         const int j0 = max(0, j1 - kSB), jb = j1 - j0;
-        for (int c = 0; c < jb; ++c)
-            for (int i = tid; i < j1; i += kBT) sL[c * kNMAX + i] = A[(int64_t)i + (int64_t)(j0 + c) * lda];
+        stage_cols(sL, A + (int64_t)j0 * lda, lda, j1, jb);
         __syncthreads();
         if (warp < nrhs) {
             T* x = sB + warp * kNMAX + j0;
