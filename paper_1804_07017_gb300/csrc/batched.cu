@@ -27,14 +27,29 @@ constexpr int kBT = 256;     // threads per CTA
 constexpr int kBNB = 32;     // panel width
 constexpr int kNMAX = 512;   // largest order handled
 constexpr int kMaxRhs = 8;   // right-hand sides handled together
+constexpr int kUS = 68;      // row stride of the U12 tile (16-byte rows for vector loads)
 
 template <typename T>
 struct BatchSmem {
-    // panel [kBNB][kNMAX] column-major, then a U12 tile [kBNB][65] (64 columns) for the update
-    static constexpr size_t bytes = sizeof(T) * ((size_t)kBNB * kNMAX + (size_t)kBNB * 65) + 64;
+    // panel [kBNB][kNMAX] column-major, then a U12 tile [kBNB][kUS] (64 columns) for the update
+    static constexpr size_t bytes = sizeof(T) * ((size_t)kBNB * kNMAX + (size_t)kBNB * kUS) + 64;
 };
 
-constexpr int kUS = 65;      // row stride of the U12 tile (65: conflict-free transposed stores)
+// Four consecutive values from 16-byte-aligned shared memory.
+__device__ __forceinline__ void load4(const float* p, float (&v)[4]) {
+    const float4 q = *reinterpret_cast<const float4*>(p);
+    v[0] = q.x;
+    v[1] = q.y;
+    v[2] = q.z;
+    v[3] = q.w;
+}
+__device__ __forceinline__ void load4(const double* p, double (&v)[4]) {
+    const double2 q0 = reinterpret_cast<const double2*>(p)[0], q1 = reinterpret_cast<const double2*>(p)[1];
+    v[0] = q0.x;
+    v[1] = q0.y;
+    v[2] = q1.x;
+    v[3] = q1.y;
+}
 
 // s[c * kNMAX + r] = g[r + c * ld] for r < rows (<= kNMAX), c < cols: eight columns
 // and both row halves are loaded before any is stored, so a thread keeps up to 16
@@ -288,6 +303,10 @@ __device__ int factor_one(int n, T* __restrict__ A, int64_t lda, int32_t* __rest
         }
         __syncthreads();
         // ---- RL3: A22 -= L21 U12 in 64x64 output tiles, 4x4 per thread ----
+        // Here kb == kBNB (a trailing block exists only after a full panel).  A thread
+        // owns rows i0 + tx + 16a and the four adjacent columns j0 + 4ty + b, so its
+        // U12 values are one vector load; L21 rows past mr hold stale shared data
+        // (inside the allocation) whose products are never stored.
         const int mr = m - kb;  // rows below the panel
         const int tx = tid & 15, ty = tid >> 4;
         for (int j0 = 0; j0 < nr; j0 += 64) {
@@ -298,7 +317,7 @@ __device__ int factor_one(int n, T* __restrict__ A, int64_t lda, int32_t* __rest
 #pragma unroll
                 for (int t = 0; t < kPer; ++t) {
                     const int e = tid + t * kBT, kk = e & (kBNB - 1), jj = e / kBNB;
-                    v[t] = (kk < kb && j0 + jj < nr) ? A[(int64_t)(k0 + kk) + (int64_t)(k0 + kb + j0 + jj) * lda] : T(0);
+                    v[t] = (j0 + jj < nr) ? A[(int64_t)(k0 + kk) + (int64_t)(k0 + kb + j0 + jj) * lda] : T(0);
                 }
 #pragma unroll
                 for (int t = 0; t < kPer; ++t) {
@@ -313,7 +332,7 @@ __device__ int factor_one(int n, T* __restrict__ A, int64_t lda, int32_t* __rest
                 T acc[4][4], cv[4][4];
 #pragma unroll
                 for (int b = 0; b < 4; ++b) {
-                    const int jc = j0 + ty + 16 * b;
+                    const int jc = j0 + 4 * ty + b;
                     const T* col = A + (int64_t)(k0 + kb + min(jc, nr - 1)) * lda + (k0 + kb);
 #pragma unroll
                     for (int a = 0; a < 4; ++a) {
@@ -322,14 +341,14 @@ __device__ int factor_one(int n, T* __restrict__ A, int64_t lda, int32_t* __rest
                         acc[a][b] = T(0);
                     }
                 }
-                for (int kk = 0; kk < kb; ++kk) {
+                const T* lp = sP + kb + i0 + tx;
+                const T* up = sU + 4 * ty;
+#pragma unroll 8
+                for (int kk = 0; kk < kBNB; ++kk) {
                     T lv[4], uv[4];
 #pragma unroll
-                    for (int a = 0; a < 4; ++a) {
-                        const int r = i0 + tx + 16 * a;
-                        lv[a] = (r < mr) ? sP[kk * kNMAX + kb + r] : T(0);
-                        uv[a] = sU[kk * kUS + ty + 16 * a];
-                    }
+                    for (int a = 0; a < 4; ++a) lv[a] = lp[kk * kNMAX + 16 * a];
+                    load4(up + kk * kUS, uv);
 #pragma unroll
                     for (int a = 0; a < 4; ++a)
 #pragma unroll
@@ -337,7 +356,7 @@ __device__ int factor_one(int n, T* __restrict__ A, int64_t lda, int32_t* __rest
                 }
 #pragma unroll
                 for (int b = 0; b < 4; ++b) {
-                    const int jc = j0 + ty + 16 * b;
+                    const int jc = j0 + 4 * ty + b;
                     if (jc >= nr) continue;
                     T* col = A + (int64_t)(k0 + kb + jc) * lda + (k0 + kb);
 #pragma unroll
