@@ -78,12 +78,12 @@ def random_rhs(A: np.ndarray, nrhs: int, seed: int = 0, stream: int = 1):
     return np.asfortranarray(A[:n, :n] @ X), X
 
 
-def separated_matrix(n: int, seed: int = 0, stream: int = 2, factor: float = 4.0):
+def separated_matrix(n: int, seed: int = 0, stream: int = 2, factor: float = 4.0, perm=None):
     """A = Pi D with D strictly column diagonally dominant by ``factor``.
 
     D has off-diagonal entries iid U[-1, 1) and d_jj = +-factor * (sum of
-    |d_ij| over i != j).  Row i of A is row perm[i] of D, i.e. A[i] = D[perm[i]].
-    Returns (A, perm).  Elimination with partial pivoting on such a matrix
+    |d_ij| over i != j).  Row i of A is row perm[i] of D, i.e. A[i] = D[perm[i]];
+    perm is drawn at random unless given.  Returns (A, perm).  Elimination with partial pivoting on such a matrix
     picks, at step j, the row holding D's diagonal entry of column j, so the
     pivot sequence is a closed-form function of perm and every pivot choice has
     a wide margin.
@@ -94,7 +94,8 @@ def separated_matrix(n: int, seed: int = 0, stream: int = 2, factor: float = 4.0
     colsum = np.abs(D).sum(axis=0)
     sign = np.where(g.uniform(size=n) < 0.5, -1.0, 1.0)
     D[np.arange(n), np.arange(n)] = sign * factor * np.maximum(colsum, 1.0)
-    perm = g.permutation(n)
+    drawn = g.permutation(n)
+    perm = drawn if perm is None else np.asarray(perm, dtype=np.int64)
     A = np.asfortranarray(D[perm, :])
     return A, perm
 

@@ -164,3 +164,39 @@ def test_batched_full_size_sampled(lu, dtype):
             assert fe <= 1e-14 and eta <= 1e-14, (i, n, fe, eta)
         else:
             assert fe <= 4 * u * 2 and eta <= 64 * n * u, (i, n, fe, eta)
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_batched_designed_pivot_sequences(lu, dtype):
+    """The batched kernel composes each panel's interchanges into one gather
+    plan; designed sequences (pivot_patterns: none, reversal, one row below
+    reached by every step, swaps inside the panel, random and mixed chains) must
+    come back exactly, with the factor and solve bounds of the parity test."""
+    import pivot_patterns as pp
+    cases = [(name, n) for name in pp.PATTERNS for n in (16, 31, 33, 64, 100, 257, 512)]
+    built = [pp.patterned_matrix(name, n, seed=5 + n) for name, n in cases]
+    mats = [a for a, _ in built]
+    pivs = [p for _, p in built]
+    g = synth.rng(13, 9)
+    rhs = [g.uniform(-1, 1, size=(a.shape[0], 1 + (i % 8))) for i, a in enumerate(mats)]
+    if dtype == torch.float32:
+        mats = [m.astype(np.float32).astype(np.float64) for m in mats]
+        rhs = [b.astype(np.float32).astype(np.float64) for b in rhs]
+    dA = [colmajor_dev(m, dtype, ld=int(m.shape[0]) + (i % 2)) for i, m in enumerate(mats)]
+    dB = [colmajor_dev(b, dtype) for b in rhs]
+    piv = [torch.zeros(a.shape[0], dtype=torch.int32, device="cuda") for a in mats]
+    batch = lu.Batch(dA, piv, dB)
+    lu.lu_gesv_batched(batch)
+    torch.cuda.synchronize()
+    assert np.all(batch.info.cpu().numpy() == 0)
+    u = np.finfo(np.float32 if dtype == torch.float32 else np.float64).eps / 2
+    for i, (name, n) in enumerate(cases):
+        p = piv[i].cpu().numpy()
+        assert np.array_equal(p, pivs[i]), (name, n, np.nonzero(p != pivs[i])[0][:10])
+        LU = dA[i].cpu().double().numpy()[:n, :n]
+        fe = oracle.factor_error(mats[i], LU, p)
+        eta = oracle.backward_error(mats[i], dB[i].cpu().double().numpy(), rhs[i])
+        if dtype == torch.float64:
+            assert fe <= 1e-14 and eta <= 1e-14, (name, n, fe, eta)
+        else:
+            assert fe <= 4 * u * 2 and eta <= 64 * n * u, (name, n, fe, eta)

@@ -323,3 +323,24 @@ def test_panel_nan_and_zero_column(lu, dtype):
     # columns before the NaN's column are unaffected by it
     assert np.array_equal(piv[:3], pivo[:3])
     assert np.all(piv != 1501)
+
+
+@pytest.mark.parametrize("name", ["last_row", "in_panel", "mixed", "reverse"])
+@pytest.mark.parametrize("dtype,n,nb", [(torch.float64, 700, 64), (torch.float64, 1500, 256),
+                                        (torch.float32, 700, 64)])
+def test_designed_pivot_sequences(lu, name, dtype, n, nb):
+    """Designed interchange sequences (pivot_patterns: repeated targets below a
+    panel, swaps inside it, long mixed chains) through the look-ahead
+    factorization: the leaves' argmax, the interchange plans on both sides of
+    each panel and the updates between must reproduce them exactly.  Patterns
+    are laid out per nb-wide panel and per 32-wide leaf."""
+    import pivot_patterns as pp
+    for panel in (nb, 32):
+        A0, piv = pp.patterned_matrix(name, n, seed=9, panel=panel)
+        if dtype == torch.float32:
+            A0 = A0.astype(np.float32).astype(np.float64)
+        _, LU, p, info = factor_gpu(lu, A0, nb, dtype=dtype)
+        assert info == 0
+        assert np.array_equal(p, piv), (panel, np.nonzero(p != piv)[0][:10])
+        bound = 1e-14 if dtype == torch.float64 else 4 * np.finfo(np.float32).eps
+        assert oracle.factor_error(A0, LU[:n, :n], p) <= bound

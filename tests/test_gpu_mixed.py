@@ -238,3 +238,24 @@ def test_factor_graph_replay_identical(lu):
     for LU, p in outs[1:]:
         assert torch.equal(LU, outs[0][0]) and torch.equal(p, outs[0][1])
     assert counts[0] > 0 and len(set(counts)) == 1, counts
+
+
+@pytest.mark.parametrize("prec", ["bf16x6", "bf16"])
+@pytest.mark.parametrize("name", ["last_row", "in_panel", "mixed"])
+def test_mixed_designed_pivot_sequences(lu, prec, name):
+    """The mixed factorization (FP32 panels, tensor-core update) takes exactly the
+    designed interchanges of a pivot_patterns matrix, whose pivots win by a
+    factor of four, far beyond the update's rounding."""
+    import pivot_patterns as pp
+    n, nb = 1000, 128
+    A0, piv = pp.patterned_matrix(name, n, seed=10, panel=nb)
+    A0 = A0.astype(np.float32).astype(np.float64)
+    A = dev(A0, torch.float32)
+    ipiv = torch.zeros(n, dtype=torch.int32, device="cuda")
+    info = torch.full((1,), -7, dtype=torch.int32, device="cuda")
+    lu.lu_factor_mixed_ex(A, ipiv, info, PRECS[prec], lu.default_opts(nb=nb))
+    torch.cuda.synchronize()
+    assert int(info.item()) == 0
+    p = ipiv.cpu().numpy()
+    assert np.array_equal(p, piv), np.nonzero(p != piv)[0][:10]
+    assert oracle.factor_error(A0, A.cpu().double().numpy(), p) <= 8 * UOP[prec]
