@@ -200,8 +200,9 @@ def main_with_args(argv):
     ap.add_argument("--prec", default="bf16x6", choices=["bf16x6", "bf16x3", "bf16", "fp16", "f32"])
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison path")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle sample")
-    ap.add_argument("--workload", default="mixed", choices=["mixed", "batched", "configs"],
-                    help="mixed: the n=16384 solver (default); batched: 4096 uneven systems")
+    ap.add_argument("--workload", default="mixed", choices=["mixed", "batched", "configs", "tune"],
+                    help="mixed: the n=16384 solver (default); batched: 4096 uneven systems; "
+                         "configs: the configuration comparisons; tune: the block-size sweeps")
     args = ap.parse_args(argv)
     if args.impl == "reference":
         return run_reference(args)
@@ -209,6 +210,8 @@ def main_with_args(argv):
         return run_configs(args)
     if args.workload == "batched":
         return run_batched(args)
+    if args.workload == "tune":
+        return run_tune(args)
 
     import numpy as np
     import torch
@@ -391,6 +394,29 @@ def main_with_args(argv):
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
+    return 0
+
+
+def run_tune(args):
+    """Block-size sweeps through the library's autotuner (lu_tune_nb): the mixed
+    factorization with the split-bf16 x6 update at n = 16384 and the FP64
+    factorization at n = 8192, each candidate timed three times on a seeded
+    U[-1,1) matrix (least time counts).  One JSON object with the times per nb
+    and the chosen nb."""
+    import torch
+
+    import paper_1804_07017_gb300 as lu
+
+    torch.cuda.set_device(0)
+    out = {"metric": "factorization ms per block size nb (least of 3 runs)", "unit": "ms", "data": "synthetic"}
+    sweeps = [("mixed_bf16x6_n16384", lu.LU_TU_BF16X6, 16384, [128, 192, 256, 320, 384, 512, 768, 1024]),
+              ("fp64_n8192", lu.LU_TUNE_F64, 8192, [128, 192, 256, 384, 512])]
+    for name, kind, n, cand in sweeps:
+        best, ms = lu.lu_tune_nb(kind, n, cand, reps=3)
+        out[name] = {"n": n, "best_nb": best,
+                     "ms": {str(c): (round(t, 3) if t >= 0 else None) for c, t in zip(cand, ms)},
+                     "gflops_at_best": round(2.0 * n ** 3 / 3.0 / (min(t for t in ms if t >= 0) * 1e-3) / 1e9, 1)}
+    print(json.dumps(out))
     return 0
 
 

@@ -45,6 +45,7 @@ extern "C" {
 #define LU_ERR_TIMEOUT (-103)     /* a bounded device-side wait expired; results are invalid */
 #define LU_ERR_UNSUPPORTED (-104) /* the requested size/type/precision is not supported */
 #define LU_ERR_HANDLE (-105)      /* null or destroyed handle */
+#define LU_ERR_IO (-106)          /* a tuning-table file could not be read, parsed or written */
 #define LU_WARN_NOT_CONVERGED (0x40000000) /* lu_gesv_mixed: tol not reached in max_iter */
 
 typedef struct lu_context *lu_handle;
@@ -71,7 +72,9 @@ typedef enum {
 
 /* Options of a blocked factorization (Sec. 3-4 of the paper). */
 typedef struct {
-    int nb;        /* algorithmic block size b (panel width), >= 1 */
+    int nb;        /* algorithmic block size b (panel width), 1..1024; 0 = the value
+                      lu_tune_nb measured for this factorization kind and n on
+                      this device, or 256 when none was measured */
     int lookahead; /* 0: no look-ahead, the PF(k); TU(k) loop of Listing 3.
                       1: depth-1 static look-ahead of Listing 5: PU(k+1) (the
                          left part of TU_k plus PF_{k+1}) runs concurrently with
@@ -135,7 +138,7 @@ int lu_profile_read(int kclass, int64_t *launches, double *ms, double *bytes, do
  *   A     device, n x n column-major, leading dimension lda; overwritten by L\U
  *   lda   >= max(1, n)
  *   ipiv  device int32[n]; receives the pivots (LAPACK convention)
- *   nb    block size b >= 1
+ *   nb    block size b, 1..1024, or 0 for the tuned value (see lu_tune_nb)
  * Synchronises the legacy default stream.  Returns 0, i > 0 (first exactly
  * zero U(i,i)), -i for an invalid argument, or a runtime error code.
  */
@@ -344,6 +347,65 @@ int lu_factor_batched(lu_handle handle, lu_dtype dtype, int batch, const int32_t
 int lu_solve_batched(lu_handle handle, lu_dtype dtype, int batch, const int32_t *n, void *const *LU,
                      const int64_t *lda, int32_t *const *ipiv, const int32_t *nrhs, void *const *B,
                      const int64_t *ldb, int32_t *info);
+
+/*
+ * Block-size autotuning.  Sec. 3 leaves the algorithmic block size b to the
+ * implementation (the paper's experiments fix b = 192 for their processor).  On
+ * the GPU, b trades the number of panel factorizations on the critical path of
+ * the look-ahead schedule (Sec. 4) against the width of the trailing updates,
+ * so the library measures it.  A process-wide table maps (device name,
+ * factorization kind, ceil(log2 n)) to the nb of least measured time;
+ * factorizations given nb = 0 take the table's value, else 256.  If the
+ * environment variable LU_GB300_TUNE_FILE names a file, the first nb = 0 lookup
+ * loads it (lu_tune_load).
+ *
+ * Factorization kinds: an lu_prec value other than LU_FULL_F64 (the mixed
+ * factorization of lu_factor_mixed_ex / lu_gesv_mixed with that update), or
+ * one of the two below.
+ */
+#define LU_TUNE_F64 100 /* FP64 factorization: lu_factor, lu_factor_ex(LU_F64), lu_gesv_mixed(LU_FULL_F64) */
+#define LU_TUNE_F32 101 /* FP32 factorization on the CUDA cores: lu_factor_ex(LU_F32) */
+
+/*
+ * lu_tune_nb -- time the factorization of `kind` on a seeded synthetic n x n
+ * matrix with iid U[-1,1) entries, for each candidate nb, and record the fastest.
+ *   h           handle; its stream orders the runs, and the call synchronises it
+ *   kind        factorization kind (above)
+ *   n           order, 1 <= n <= 2^30
+ *   candidates  host int[count], count >= 1: the nb values to try.  A value the
+ *               factorization rejects (outside 1..1024, not a multiple of 128 for
+ *               LU_TU_FP8, or too large for the memory) is skipped.
+ *   reps        >= 1 runs per candidate; the least time counts (the first run
+ *               of a mixed factorization is eager, the second captures its graph)
+ *   opts        look-ahead, stealing, leaf and pf_ctas used for every run
+ *               (NULL = defaults; its nb is ignored)
+ *   best_nb     host int (out): the candidate of least time, also stored in the table
+ *   ms          host float[count] or NULL (out): each candidate's least time in
+ *               milliseconds, -1 for a skipped one
+ * The scratch matrix (n*n elements of the kind's type) is allocated with
+ * cudaMalloc and freed before returning.  Returns 0, -i for an invalid argument,
+ * LU_ERR_NOMEM (scratch matrix), LU_ERR_UNSUPPORTED (no candidate ran) or a
+ * runtime error of the factorization.
+ */
+int lu_tune_nb(lu_handle h, int kind, int64_t n, const int *candidates, int count, int reps, const lu_opts *opts,
+               int *best_nb, float *ms);
+
+/* The table's nb for (device, kind, ceil(log2 n)), or 0 when there is none.
+ * device: host string, or NULL for the current CUDA device's name. */
+int lu_tune_get(const char *device, int kind, int64_t n);
+/* Stores nb (and its time in ms, informative) for (device, kind, ceil(log2 n)),
+ * replacing an entry with the same key.  Returns 0, -1 (device NULL without a
+ * CUDA device, empty, or holding a tab or newline), -2 (kind), -3 (n < 1), -4 (nb). */
+int lu_tune_set(const char *device, int kind, int64_t n, int nb, float ms);
+/* Empties the table.  Returns 0. */
+int lu_tune_clear(void);
+/* Writes the table to the host file `path` as text lines
+ * "device<TAB>kind<TAB>ceil(log2 n)<TAB>nb<TAB>ms".  Returns 0, -1 (NULL path) or LU_ERR_IO. */
+int lu_tune_save(const char *path);
+/* Merges the lines of such a file into the table (an entry replaces one with the
+ * same key).  Every line is validated first; on any malformed line nothing is
+ * merged.  Returns 0, -1 (NULL path) or LU_ERR_IO (unreadable or malformed). */
+int lu_tune_load(const char *path);
 
 #ifdef __cplusplus
 }

@@ -14,6 +14,7 @@ LU_ERR_NOMEM = -102
 LU_ERR_TIMEOUT = -103
 LU_ERR_UNSUPPORTED = -104
 LU_ERR_HANDLE = -105
+LU_ERR_IO = -106
 LU_WARN_NOT_CONVERGED = 0x40000000
 
 LU_F64 = 0
@@ -28,6 +29,9 @@ LU_TU_F32 = 3
 LU_TU_BF16X3 = 4
 LU_FULL_F64 = 5
 LU_TU_BF16X6 = 6
+
+LU_TUNE_F64 = 100
+LU_TUNE_F32 = 101
 
 
 class LuError(RuntimeError):
@@ -76,6 +80,13 @@ _SIGNATURES = {
     "lu_factor_mixed_ex": (i32, [vp, i32, i64, vp, i64, vp, ctypes.POINTER(LuOpts), vp]),
     "lu_gesv_mixed": (i32, [vp, i32, i64, i64, vp, i64, vp, i64, vp, i64, dbl, i32, ctypes.POINTER(LuOpts),
                             ctypes.POINTER(i32), ctypes.POINTER(dbl)]),
+    "lu_tune_nb": (i32, [vp, i32, i64, ctypes.POINTER(i32), i32, i32, ctypes.POINTER(LuOpts), ctypes.POINTER(i32),
+                         ctypes.POINTER(ctypes.c_float)]),
+    "lu_tune_get": (i32, [ctypes.c_char_p, i32, i64]),
+    "lu_tune_set": (i32, [ctypes.c_char_p, i32, i64, i32, ctypes.c_float]),
+    "lu_tune_clear": (i32, []),
+    "lu_tune_save": (i32, [ctypes.c_char_p]),
+    "lu_tune_load": (i32, [ctypes.c_char_p]),
 }
 
 _lib = None

@@ -246,3 +246,43 @@ def lu_solve_batched(batch: Batch, handle: Handle | None = None) -> None:
     _check("lu_solve_batched", lib().lu_solve_batched(
         h.ptr, batch.dtype, len(batch.mats), _p(batch.n), _p(batch.A), _p(batch.lda), _p(batch.ipiv),
         _p(batch.nrhs), _p(batch.B), _p(batch.ldb), _p(batch.info)))
+
+
+def lu_tune_nb(kind: int, n: int, candidates, reps: int = 3, opts: LuOpts | None = None,
+               handle: Handle | None = None):
+    """Times the factorization of `kind` (an lu_prec, LU_TUNE_F64 or LU_TUNE_F32) on
+    a synthetic n x n matrix for each candidate nb; returns (best_nb, ms list, -1 for
+    a skipped candidate) and stores best_nb in the library's table."""
+    h = _handle(handle)
+    cand = (ctypes.c_int * len(candidates))(*[int(c) for c in candidates])
+    ms = (ctypes.c_float * len(candidates))()
+    best = ctypes.c_int(0)
+    o = opts if opts is not None else default_opts()
+    _check("lu_tune_nb", lib().lu_tune_nb(h.ptr, int(kind), int(n), cand, len(candidates), int(reps),
+                                          ctypes.byref(o), ctypes.byref(best), ms))
+    return best.value, [float(t) for t in ms]
+
+
+def _dev(device):
+    return None if device is None else device.encode()
+
+
+def lu_tune_get(kind: int, n: int, device: str | None = None) -> int:
+    """The tuned nb for (device, kind, ceil(log2 n)), 0 if none (device None = current GPU)."""
+    return int(lib().lu_tune_get(_dev(device), int(kind), int(n)))
+
+
+def lu_tune_set(kind: int, n: int, nb: int, ms: float = 0.0, device: str | None = None) -> None:
+    _check("lu_tune_set", lib().lu_tune_set(_dev(device), int(kind), int(n), int(nb), float(ms)))
+
+
+def lu_tune_clear() -> None:
+    _check("lu_tune_clear", lib().lu_tune_clear())
+
+
+def lu_tune_save(path: str) -> None:
+    _check("lu_tune_save", lib().lu_tune_save(path.encode()))
+
+
+def lu_tune_load(path: str) -> None:
+    _check("lu_tune_load", lib().lu_tune_load(path.encode()))

@@ -13,6 +13,10 @@
 #define LU_PF_MAX_CTAS 128    // CTAs of one panel-factorization leaf launch
 #define LU_PF_MAX_LEAF 64     // widest leaf (columns held in shared memory)
 #define LU_MAX_NB 1024        // widest panel accepted
+
+// nb for a factorization called with nb = 0: the tuned value for (kind, n) on
+// the current device, else 256 (tune.cu).
+int lu_auto_nb(int kind, int64_t n);
 #define LU_PF_SMEM_BUDGET (78 * 1024)
 #define LU_PF_MAX_CTAS_CLUSTER 16  // CTAs of a cluster panel leaf (non-portable cluster size)
 

@@ -172,7 +172,7 @@ static lu_handle default_handle() {
 // factorization driver
 // ---------------------------------------------------------------------------
 int lu_check_opts(const lu_opts& o) {
-    if (o.nb < 1 || o.nb > LU_MAX_NB) return -1;
+    if (o.nb < 0 || o.nb > LU_MAX_NB) return -1;  // 0: resolved by the factorization entry points
     if (o.lookahead < 0 || o.lookahead > 1) return -1;
     if (o.leaf < 0 || o.pf_ctas < 0 || o.pf_ctas > LU_PF_MAX_CTAS) return -1;
     return 0;
@@ -209,6 +209,7 @@ template <typename T>
 int lu_factor_blocked(lu_context* c, int64_t n, T* A, int64_t lda, int32_t* ipiv, const lu_opts& o, int32_t* info,
                       const LuTuEngine* eng) {
     const int nb = o.nb;
+    if (nb < 1) return LU_ERR_UNSUPPORTED;  // nb = 0 is resolved before this point
     LU_TRY(lu_ctx_reserve(c, n, nb));
     cudaStream_t user = c->user;
     LU_CHECK_CUDA(cudaMemsetAsync(&c->sync[0], 0, sizeof(LuSync), user));
@@ -279,6 +280,7 @@ extern "C" int lu_factor_ex(lu_handle h, lu_dtype dtype, int64_t n, void* A, int
     if (lu_check_opts(o) != 0) return -7;
     if (!info) return -8;
     if (n > INT32_MAX / 2) return LU_ERR_UNSUPPORTED;
+    if (o.nb == 0) o.nb = lu_auto_nb(dtype == LU_F64 ? LU_TUNE_F64 : LU_TUNE_F32, n);
     std::lock_guard<std::mutex> lk(h->mu);
     if (dtype == LU_F64) return lu_factor_blocked<double>(h, n, (double*)A, lda, ipiv, o, info, nullptr);
     return lu_factor_blocked<float>(h, n, (float*)A, lda, ipiv, o, info, nullptr);
@@ -289,7 +291,7 @@ extern "C" int lu_factor(int64_t n, double* A, int64_t lda, int32_t* ipiv, int n
     if (n > 0 && !A) return -2;
     if (lda < std::max<int64_t>(1, n)) return -3;
     if (n > 0 && !ipiv) return -4;
-    if (nb < 1 || nb > LU_MAX_NB) return -5;
+    if (nb < 0 || nb > LU_MAX_NB) return -5;
     lu_handle h = default_handle();
     if (!h) return LU_ERR_CUDA;
     lu_opts o;

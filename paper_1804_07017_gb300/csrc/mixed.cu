@@ -292,6 +292,7 @@ extern "C" int lu_factor_mixed_ex(lu_handle h, lu_prec prec, int64_t n, float* A
     if (lu_check_opts(o) != 0) return -7;
     if (!info) return -8;
     if (n > INT32_MAX / 2) return LU_ERR_UNSUPPORTED;
+    if (o.nb == 0) o.nb = lu_auto_nb(prec, n);
     std::lock_guard<std::mutex> lk(h->mu);
     LU_TRY(lu_ctx_reserve(h, n, o.nb));
     LU_TRY(lu_mx_reserve(h, tc_engine_bytes(prec, std::max<int64_t>(n, 1), o.nb)));
@@ -449,6 +450,7 @@ extern "C" int lu_gesv_mixed(lu_handle h, lu_prec prec, int64_t n, int64_t nrhs,
     if (bwd_err) *bwd_err = 0.0;
     if (n == 0 || nrhs == 0) return LU_SUCCESS;
     if (n > INT32_MAX / 2) return LU_ERR_UNSUPPORTED;
+    if (o.nb == 0) o.nb = lu_auto_nb(prec == LU_FULL_F64 ? LU_TUNE_F64 : (int)prec, n);
     std::lock_guard<std::mutex> lk(h->mu);
     if (prec == LU_FULL_F64)
         return gesv_refined<double>(h, prec, n, nrhs, A, lda, B, ldb, X, ldx, tol, max_iter, o, iters, bwd_err);

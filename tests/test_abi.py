@@ -36,7 +36,8 @@ def test_argument_validation_without_gpu(built):
     assert L.lu_factor(-1, None, 1, None, 64) == -1
     assert L.lu_factor(4, None, 4, None, 64) == -2
     assert L.lu_factor(4, ctypes.c_void_p(16), 3, ctypes.c_void_p(16), 64) == -3
-    assert L.lu_factor(4, ctypes.c_void_p(16), 4, ctypes.c_void_p(16), 0) == -5
+    assert L.lu_factor(4, ctypes.c_void_p(16), 4, ctypes.c_void_p(16), -1) == -5
+    assert L.lu_factor(4, ctypes.c_void_p(16), 4, ctypes.c_void_p(16), 1025) == -5
     assert L.lu_solve(-2, 1, None, None, None) == -1
     assert L.lu_factor_ex(None, 0, 4, None, 4, None, None, None) == _lib.LU_ERR_HANDLE
     o = pkg.LuOpts()
@@ -51,3 +52,53 @@ def test_header_compiles_as_c(tmp_path):
     inc = os.path.join(os.path.dirname(_lib.HEADER))
     subprocess.run(["gcc", "-std=c99", "-Wall", "-Werror", "-c", str(src), "-I", inc, "-o", str(tmp_path / "t.o")],
                    check=True)
+
+
+def test_tune_table_round_trip(built, tmp_path):
+    """The nb table behind nb = 0 (lu_tune_*): set/get by (device, kind,
+    ceil(log2 n)), replacement, save/load round trip, rejection of malformed
+    files without partial merges, and argument checks, all on the host."""
+    L = pkg.lib()
+    dev = b"Test GPU"
+    assert L.lu_tune_clear() == 0
+    assert L.lu_tune_get(dev, pkg.LU_TU_BF16X6, 16384) == 0
+    assert L.lu_tune_set(dev, pkg.LU_TU_BF16X6, 16384, 512, 80.5) == 0
+    # one bucket per power of two: (8192, 16384] shares the entry, 16385 does not
+    assert L.lu_tune_get(dev, pkg.LU_TU_BF16X6, 8193) == 512
+    assert L.lu_tune_get(dev, pkg.LU_TU_BF16X6, 16385) == 0
+    assert L.lu_tune_get(dev, pkg.LU_TU_BF16, 16384) == 0
+    assert L.lu_tune_get(b"Other GPU", pkg.LU_TU_BF16X6, 16384) == 0
+    assert L.lu_tune_set(dev, pkg.LU_TU_BF16X6, 12000, 384, 70.0) == 0  # same key: replaced
+    assert L.lu_tune_get(dev, pkg.LU_TU_BF16X6, 16384) == 384
+    assert L.lu_tune_set(dev, pkg.LU_TUNE_F64, 8192, 256, 300.0) == 0
+    assert L.lu_tune_set(dev, pkg.LU_TU_FP8, 32768, 128, 200.0) == 0
+    # argument checks
+    assert L.lu_tune_set(b"", pkg.LU_TUNE_F64, 8192, 256, 0.0) == -1
+    assert L.lu_tune_set(b"a\tb", pkg.LU_TUNE_F64, 8192, 256, 0.0) == -1
+    assert L.lu_tune_set(dev, pkg.LU_FULL_F64, 8192, 256, 0.0) == -2
+    assert L.lu_tune_set(dev, 7, 8192, 256, 0.0) == -2
+    assert L.lu_tune_set(dev, pkg.LU_TUNE_F64, 0, 256, 0.0) == -3
+    assert L.lu_tune_set(dev, pkg.LU_TUNE_F64, 8192, 0, 0.0) == -4
+    assert L.lu_tune_set(dev, pkg.LU_TUNE_F64, 8192, 1025, 0.0) == -4
+    assert L.lu_tune_set(dev, pkg.LU_TU_FP8, 8192, 192, 0.0) == -4
+    assert L.lu_tune_save(None) == -1 and L.lu_tune_load(None) == -1
+    path = tmp_path / "tune.txt"
+    assert L.lu_tune_save(str(path).encode()) == 0
+    lines = path.read_text().splitlines()
+    assert sorted(lines) == sorted(["Test GPU\t6\t14\t384\t70", "Test GPU\t100\t13\t256\t300",
+                                    "Test GPU\t2\t15\t128\t200"])
+    assert L.lu_tune_clear() == 0 and L.lu_tune_get(dev, pkg.LU_TU_BF16X6, 16384) == 0
+    assert L.lu_tune_load(str(path).encode()) == 0
+    assert L.lu_tune_get(dev, pkg.LU_TU_BF16X6, 16384) == 384
+    assert L.lu_tune_get(dev, pkg.LU_TUNE_F64, 5000) == 256
+    assert L.lu_tune_get(dev, pkg.LU_TU_FP8, 20000) == 128
+    # malformed files are rejected whole
+    for bad in ["Test GPU\t6\t14\n", "Test GPU\t6\t14\t384\t70\textra\n", "\t6\t14\t384\t70\n",
+                "Test GPU\t9\t14\t384\t70\n", "Test GPU\t2\t14\t192\t70\n", "Test GPU\t6\t99\t384\t70\n"]:
+        f = tmp_path / "bad.txt"
+        f.write_text("New GPU\t6\t14\t512\t1\n" + bad)
+        assert L.lu_tune_load(str(f).encode()) == pkg.LU_ERR_IO, bad
+        assert L.lu_tune_get(b"New GPU", pkg.LU_TU_BF16X6, 16384) == 0
+    assert L.lu_tune_load(str(tmp_path / "missing.txt").encode()) == pkg.LU_ERR_IO
+    assert L.lu_tune_nb(None, pkg.LU_TUNE_F64, 64, None, 0, 1, None, None, None) == _lib.LU_ERR_HANDLE
+    assert L.lu_tune_clear() == 0
