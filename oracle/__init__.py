@@ -17,6 +17,9 @@ Each routine states the passage of the paper it restates:
 * ``getrs``  -- the triangular solves paired with getrf (not in the paper).
 * ``backward_error`` / ``factor_error`` -- the normwise backward errors used
   as pass criteria (definitions, compensated sums).
+* ``potrf`` -- Cholesky A = L L^T (unblocked, right-looking), the factorization
+  the paper names as fitting the same blocked / look-ahead skeleton (Sec. 1, 7).
+* ``chol_error`` -- ||A0 - L L^T|| / (n ||A0||) (compensated sums).
 * ``round_*`` -- ties-to-even rounding onto bf16 / fp16 / e4m3 / fp32.
 * ``quant_e4m3_rows`` / ``quant_e4m3_cols`` -- power-of-two block scaling onto
   e4m3 (one scale per row of L21 / per column of U12) for the FP8 update.
@@ -77,6 +80,8 @@ def _load():
             "oracle_round_e4m3": (None, [i64, vp, vp]),
             "oracle_round_fp32": (None, [i64, vp, vp]),
             "oracle_quant_e4m3_blocks": (None, [i64, i64, vp, i64, i64, vp, vp]),
+            "oracle_potrf": (i32, [i64, vp, i64]),
+            "oracle_chol_error": (dbl, [i64, vp, i64, vp, i64]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -245,3 +250,22 @@ def quant_e4m3_cols(X):
     sc = np.zeros(max(n, 1))
     lib.oracle_quant_e4m3_blocks(n, k, _ptr(Xf), max(k, 1), 1, _ptr(Q), _ptr(sc))
     return Q, sc[:n]
+
+
+def potrf(A):
+    """Cholesky factor of a symmetric positive definite matrix.  Returns (L, info):
+    L is the lower triangle (strict upper part zero) and info is 0, or j when
+    the leading j x j minor is not positive definite (L is then not meaningful)."""
+    lib = _load()
+    W = _f64(A)
+    n = W.shape[0]
+    info = lib.oracle_potrf(n, _ptr(W), max(n, 1))
+    return np.tril(W), int(info)
+
+
+def chol_error(A0, L) -> float:
+    """||A0 - L L^T||_inf / (n ||A0||_inf) with the lower triangle of L."""
+    lib = _load()
+    A0f, Lf = _f64(A0), _f64(L)
+    n = A0f.shape[0]
+    return float(lib.oracle_chol_error(n, _ptr(A0f), max(n, 1), _ptr(Lf), max(Lf.shape[0], 1)))

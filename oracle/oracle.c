@@ -33,6 +33,12 @@
  *                     solve, eta = ||b - A x|| / (||A|| ||x|| + ||b||) (inf-norms),
  *                     with compensated (Neumaier) sums so the residual is
  *                     accurate to ~1 ulp of its terms.
+ *   oracle_potrf   -- Cholesky A = L L^T of a symmetric positive definite
+ *                     matrix by the unblocked right-looking algorithm, the
+ *                     factorization the paper names as fitting the same
+ *                     blocked/look-ahead skeleton (Sec. 1, Sec. 7); lower
+ *                     triangle only.
+ *   oracle_chol_error -- ||A0 - L L^T|| / (n ||A0||) (inf-norms, compensated).
  *   oracle_round_bf16 / oracle_round_fp16 / oracle_quant_e4m3 -- IEEE-style
  *                     round-to-nearest-even onto the narrow formats used for
  *                     the mixed-precision trailing update operands.
@@ -426,4 +432,52 @@ void oracle_quant_e4m3_blocks(int64_t nblk, int64_t len, const double *X, int64_
             Q[b * bstride + i * estride] = r;
         }
     }
+}
+
+/* ---------------------------------------------------------------------------
+ * Cholesky factorization A = L L^T (lower), unblocked and right-looking: at
+ * step j the diagonal entry of the updated matrix must be positive; its square
+ * root is l_jj, the column below is divided by l_jj, and the trailing lower
+ * triangle loses the outer product of that column with itself.  Only the lower
+ * triangle (i >= j) is read or written.  Returns 0, or j+1 when the updated
+ * diagonal entry at step j is not positive (or NaN): the leading (j+1) x (j+1)
+ * minor is not positive definite; the matrix is then left as it was at that step.
+ * ------------------------------------------------------------------------- */
+int oracle_potrf(int64_t n, double *A, int64_t lda)
+{
+    for (int64_t j = 0; j < n; ++j) {
+        const double d = A[IDX(j, j, lda)];
+        if (!(d > 0.0)) return (int)(j + 1);
+        const double ljj = sqrt(d);
+        A[IDX(j, j, lda)] = ljj;
+        for (int64_t i = j + 1; i < n; ++i) A[IDX(i, j, lda)] = A[IDX(i, j, lda)] / ljj;
+        for (int64_t c = j + 1; c < n; ++c) {
+            const double lcj = A[IDX(c, j, lda)];
+            for (int64_t i = c; i < n; ++i) A[IDX(i, c, lda)] = A[IDX(i, c, lda)] - A[IDX(i, j, lda)] * lcj;
+        }
+    }
+    return 0;
+}
+
+/* ||A0 - L L^T||_inf / (n ||A0||_inf) for an n x n symmetric A0 (both
+ * triangles read) and the lower triangle of L; products summed compensated. */
+double oracle_chol_error(int64_t n, const double *A0, int64_t lda0, const double *L, int64_t ldl)
+{
+    if (n == 0) return 0.0;
+    double worst = 0.0;
+    for (int64_t i = 0; i < n; ++i) {
+        double s_row = 0.0, c_row = 0.0;
+        for (int64_t c = 0; c < n; ++c) {
+            /* (L L^T)(i,c) = sum_{p <= min(i,c)} L(i,p) L(c,p) */
+            double s = 0.0, comp = 0.0;
+            const int64_t pmax = i < c ? i : c;
+            for (int64_t p = 0; p <= pmax; ++p) neumaier_add(&s, &comp, L[IDX(i, p, ldl)] * L[IDX(c, p, ldl)]);
+            neumaier_add(&s, &comp, -A0[IDX(i, c, lda0)]);
+            neumaier_add(&s_row, &c_row, fabs(s + comp));
+        }
+        const double r = s_row + c_row;
+        if (r > worst || isnan(r)) worst = r;
+    }
+    const double anorm = oracle_norm_inf(n, n, A0, lda0);
+    return anorm > 0.0 ? worst / ((double)n * anorm) : (worst > 0.0 ? INFINITY : 0.0);
 }

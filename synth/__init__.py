@@ -100,6 +100,16 @@ def separated_matrix(n: int, seed: int = 0, stream: int = 2, factor: float = 4.0
     return A, perm
 
 
+def spd_matrix(n: int, seed: int = 0, stream: int = 7):
+    """Symmetric positive definite A = G G^T / n + I with G iid U[-1, 1)
+    (eigenvalues in [1, about 1 + 4/3]); both triangles stored, exactly symmetric."""
+    g = rng(seed, stream)
+    G = g.uniform(-1.0, 1.0, size=(n, n))
+    A = (G @ G.T) / max(n, 1)
+    A = 0.5 * (A + A.T) + np.eye(n)
+    return np.asfortranarray(A)
+
+
 def batched_sizes(count: int, seed: int = 0, stream: int = 5, lo: int = 16, hi: int = 512):
     """Sizes n_i = round(exp(U[ln lo, ln hi])) (log-uniform), and nrhs_i ~ U{1..8}."""
     g = rng(seed, stream)

@@ -366,3 +366,48 @@ def test_designed_pivot_sequences(name, n):
     assert info == 0
     assert np.array_equal(ipiv, piv)
     assert oracle.factor_error(A, LU, ipiv) <= 1e-15
+
+
+def test_potrf_integer_factor_exact():
+    """A = L0 L0^T with a small integer L0 (positive integer diagonal): every
+    step of the elimination is exact in FP64, so the Cholesky oracle must return
+    L0 bit for bit."""
+    g = synth.rng(12, 0)
+    for n in (1, 2, 5, 9):
+        L0 = np.tril(g.integers(-3, 4, size=(n, n)).astype(float), -1) + np.diag(g.integers(1, 4, size=n).astype(float))
+        A = L0 @ L0.T
+        L, info = oracle.potrf(A)
+        assert info == 0 and np.array_equal(L, L0)
+        assert oracle.chol_error(A, L) == 0.0
+
+
+@pytest.mark.parametrize("n", [3, 40, 130])
+def test_potrf_against_numpy(n):
+    A = synth.spd_matrix(n, seed=n)
+    assert np.array_equal(A, A.T)
+    L, info = oracle.potrf(A)
+    R = np.linalg.cholesky(A)  # LAPACK potrf, a third-party routine
+    assert info == 0
+    assert np.all(np.diag(L) > 0) and np.array_equal(L, np.tril(L))
+    assert np.abs(L - R).max() <= 1e-13 * np.abs(R).max()
+    assert oracle.chol_error(A, L) <= 4 * np.finfo(float).eps
+
+
+def test_potrf_not_positive_definite():
+    assert oracle.potrf(np.diag([1.0, 2.0, -1.0, 4.0]))[1] == 3
+    assert oracle.potrf(np.ones((2, 2)))[1] == 2  # the leading 2 x 2 minor is singular
+    assert oracle.potrf(np.zeros((1, 1)))[1] == 1
+    A = synth.spd_matrix(10, seed=1)
+    A[6, 6] = -100.0  # the leading 6 x 6 minor is untouched and positive definite
+    assert oracle.potrf(A)[1] == 7
+    B = A.copy()
+    B[6, 6] = np.nan
+    assert oracle.potrf(B)[1] == 7
+
+
+def test_chol_error_planted():
+    n, delta = 4, 0.125
+    L = np.eye(n)
+    L[1, 1] = 1 + delta
+    # (L L^T)(1,1) = (1 + delta)^2: one residual entry of 2 delta + delta^2 in row 1
+    assert oracle.chol_error(np.eye(n), L) == (2 * delta + delta ** 2) / n
