@@ -201,9 +201,10 @@ def main_with_args(argv):
     ap.add_argument("--prec", default="bf16x6", choices=["bf16x6", "bf16x3", "bf16", "fp16", "f32"])
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison path")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle sample")
-    ap.add_argument("--workload", default="mixed", choices=["mixed", "batched", "configs", "tune"],
+    ap.add_argument("--workload", default="mixed", choices=["mixed", "batched", "configs", "tune", "chol"],
                     help="mixed: the n=16384 solver (default); batched: 4096 uneven systems; "
-                         "configs: the configuration comparisons; tune: the block-size sweeps")
+                         "configs: the configuration comparisons; tune: the block-size sweeps; "
+                         "chol: the Cholesky factorization")
     args = ap.parse_args(argv)
     if args.impl == "reference":
         return run_reference(args)
@@ -213,6 +214,8 @@ def main_with_args(argv):
         return run_batched(args)
     if args.workload == "tune":
         return run_tune(args)
+    if args.workload == "chol":
+        return run_chol(args)
 
     import numpy as np
     import torch
@@ -395,6 +398,50 @@ def main_with_args(argv):
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
+    return 0
+
+
+def run_chol(args):
+    """Cholesky factorization (lu_potrf_ex, nb = 256, depth-1 look-ahead) of
+    A = G G^T / n + I, G iid U[-1,1) from a seeded torch generator (formed on the
+    device, outside the timed region): FP64 at n = 8192 and FP32 at n = 16384.
+    GFLOP/s of n^3/3 (the Cholesky count); two untimed runs, then the median of
+    three event-timed runs, A restored from a device copy before each."""
+    import statistics as st_
+    import torch
+
+    import paper_1804_07017_gb300 as lu
+    from paper_1804_07017_gb300.api import colmajor
+
+    torch.cuda.set_device(0)
+    out = {"metric": "Cholesky GFLOP/s (n^3/3)", "unit": "GFLOP/s", "data": "synthetic"}
+    for name, dt, n in (("f64_n8192", torch.float64, 8192), ("f32_n16384", torch.float32, 16384)):
+        g = torch.Generator(device="cuda")
+        g.manual_seed(0)
+        G = torch.rand((n, n), generator=g, device="cuda", dtype=dt) * 2 - 1
+        S = (G @ G.t()) / n
+        S = 0.5 * (S + S.t()) + torch.eye(n, device="cuda", dtype=dt)
+        del G
+        A = colmajor(n, n, dtype=dt)
+        info = torch.zeros(1, dtype=torch.int32, device="cuda")
+        o = lu.default_opts(nb=256)
+        times = []
+        for it in range(5):
+            A.copy_(S)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            lu.lu_potrf_ex(A, info, o)
+            e1.record()
+            torch.cuda.synchronize()
+            if it >= 2:
+                times.append(e0.elapsed_time(e1))
+        ms = st_.median(times)
+        out[name] = {"n": n, "ms": round(ms, 3), "gflops": round(n ** 3 / 3.0 / (ms * 1e-3) / 1e9, 1),
+                     "info": int(info.item())}
+        del S, A
+        torch.cuda.empty_cache()
+    print(json.dumps(out))
     return 0
 
 

@@ -349,6 +349,28 @@ int lu_solve_batched(lu_handle handle, lu_dtype dtype, int batch, const int32_t 
                      const int64_t *ldb, int32_t *info);
 
 /*
+ * lu_potrf_ex -- Cholesky factorization A = L L^T of a symmetric positive
+ * definite n x n matrix on the same blocked right-looking skeleton with depth-1
+ * look-ahead (Sec. 3-4; the paper names Cholesky among the factorizations that
+ * fit it).  Elimination without interchanges gives A = L~ U with U = D L~^T for
+ * such A; the call returns L = L~ D^{1/2}.
+ *   h      handle (its stream orders the work; asynchronous)
+ *   dtype  LU_F64 or LU_F32 (CUDA-core arithmetic)
+ *   n      order, n >= 0
+ *   A      device, n x n column-major with leading dimension lda, BOTH triangles
+ *          holding the symmetric matrix.  On exit the lower triangle (diagonal
+ *          included) holds L; the strict upper triangle is overwritten (it holds
+ *          D L~^T).
+ *   lda    >= max(1, n)
+ *   opts   nb (0 = tuned, see lu_tune_nb), lookahead; NULL = defaults
+ *   info   device int32 (out): 0, or j > 0 when the pivot of step j - 1 was not
+ *          positive (the leading j x j minor is not positive definite; L is then
+ *          not meaningful), or LU_ERR_TIMEOUT
+ * Returns 0, -i for an invalid argument, or a runtime error code.
+ */
+int lu_potrf_ex(lu_handle h, lu_dtype dtype, int64_t n, void *A, int64_t lda, const lu_opts *opts, int32_t *info);
+
+/*
  * Block-size autotuning.  Sec. 3 leaves the algorithmic block size b to the
  * implementation (the paper's experiments fix b = 192 for their processor).  On
  * the GPU, b trades the number of panel factorizations on the critical path of

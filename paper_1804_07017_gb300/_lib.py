@@ -80,6 +80,7 @@ _SIGNATURES = {
     "lu_factor_mixed_ex": (i32, [vp, i32, i64, vp, i64, vp, ctypes.POINTER(LuOpts), vp]),
     "lu_gesv_mixed": (i32, [vp, i32, i64, i64, vp, i64, vp, i64, vp, i64, dbl, i32, ctypes.POINTER(LuOpts),
                             ctypes.POINTER(i32), ctypes.POINTER(dbl)]),
+    "lu_potrf_ex": (i32, [vp, i32, i64, vp, i64, ctypes.POINTER(LuOpts), vp]),
     "lu_tune_nb": (i32, [vp, i32, i64, ctypes.POINTER(i32), i32, i32, ctypes.POINTER(LuOpts), ctypes.POINTER(i32),
                          ctypes.POINTER(ctypes.c_float)]),
     "lu_tune_get": (i32, [ctypes.c_char_p, i32, i64]),

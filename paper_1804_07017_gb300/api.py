@@ -248,6 +248,15 @@ def lu_solve_batched(batch: Batch, handle: Handle | None = None) -> None:
         _p(batch.nrhs), _p(batch.B), _p(batch.ldb), _p(batch.info)))
 
 
+def lu_potrf_ex(A: torch.Tensor, info: torch.Tensor, opts: LuOpts | None = None,
+                handle: Handle | None = None) -> None:
+    """In-place Cholesky A = L L^T (A symmetric positive definite, both triangles
+    stored, FP64 or FP32); L in the lower triangle, the strict upper overwritten."""
+    h = _handle(handle)
+    o = opts if opts is not None else default_opts()
+    _check("lu_potrf_ex", lib().lu_potrf_ex(h.ptr, _DT[A.dtype], A.shape[0], _p(A), _ld(A, "A"), ctypes.byref(o), _p(info)))
+
+
 def lu_tune_nb(kind: int, n: int, candidates, reps: int = 3, opts: LuOpts | None = None,
                handle: Handle | None = None):
     """Times the factorization of `kind` (an lu_prec, LU_TUNE_F64 or LU_TUNE_F32) on

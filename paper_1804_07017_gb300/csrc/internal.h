@@ -168,9 +168,17 @@ struct LuTuEngine {
 
 int lu_check_opts(const lu_opts& o);
 
+// pivot = false: elimination without interchanges (the Cholesky path, chol.cu):
+// panels by lu_panel_nopiv, no interchange plans or row exchanges, ipiv unused.
 template <typename T>
 int lu_factor_blocked(lu_context* c, int64_t n, T* A, int64_t lda, int32_t* ipiv, const lu_opts& o, int32_t* info,
-                      const LuTuEngine* eng);
+                      const LuTuEngine* eng, bool pivot = true);
+
+// Panel of columns [j0, j0+width) over rows [j0, M) eliminated without
+// interchanges (absolute indices); the first step whose pivot is not positive is
+// recorded (1-based) in sync->info.
+template <typename T>
+int lu_panel_nopiv(cudaStream_t st, T* A, int64_t lda, int64_t M, int64_t j0, int64_t width, LuSync* sync);
 
 // Operand precisions of the tensor-core trailing update.
 static inline bool lu_prec_is_tc(int prec) {

@@ -184,12 +184,12 @@ int lu_check_opts(const lu_opts& o) {
 template <typename T>
 static int trailing_update(lu_context* c, cudaStream_t st, int64_t n, T* A, int64_t lda, int64_t k, int64_t k0,
                            int64_t kb, int64_t c_begin, int64_t c_end, int64_t left_cols, const int32_t* plan,
-                           const LuTuEngine* eng, int which) {
+                           const LuTuEngine* eng, int which, bool pivot) {
     const int64_t ncols = c_end - c_begin;
     // the right update's interchanges and RL2 run on at most the right update's share
     // of the SMs (as its tensor-core part), leaving the rest to the panel path
     const int cap = which == 1 ? std::max(1, c->num_sms - std::max(4, c->num_sms / 6)) : 0;
-    if (ncols > 0 || left_cols > 0)
+    if (pivot && (ncols > 0 || left_cols > 0))
         LU_TRY(lu_launch_laswp_apply<T>(st, A, lda, c_begin, std::max<int64_t>(ncols, 0), 0, left_cols,
                                         plan, kb, c->num_sms, cap));
     if (ncols <= 0) return LU_SUCCESS;
@@ -207,7 +207,7 @@ static int trailing_update(lu_context* c, cudaStream_t st, int64_t n, T* A, int6
 
 template <typename T>
 int lu_factor_blocked(lu_context* c, int64_t n, T* A, int64_t lda, int32_t* ipiv, const lu_opts& o, int32_t* info,
-                      const LuTuEngine* eng) {
+                      const LuTuEngine* eng, bool pivot) {
     const int nb = o.nb;
     if (nb < 1) return LU_ERR_UNSUPPORTED;  // nb = 0 is resolved before this point
     LU_TRY(lu_ctx_reserve(c, n, nb));
@@ -223,6 +223,7 @@ int lu_factor_blocked(lu_context* c, int64_t n, T* A, int64_t lda, int32_t* ipiv
     // PF(k) followed by its interchange plan (and, for the tensor-core engine, the packed L21)
     auto panel = [&](int64_t k) -> int {
         const int64_t k0 = k * nb, kb = std::min<int64_t>(nb, n - k0);
+        if (!pivot) return lu_panel_nopiv<T>(hi, A, lda, n, k0, kb, &c->sync[0]);
         LU_TRY(lu_panel_recursive<T>(c, hi, A, lda, n, k0, kb, ipiv, o));
         LU_TRY(lu_launch_laswp_plan(hi, ipiv, k0, k0 + kb, plan_of(k)));
         if (eng && eng->uses_tc(kb) && k0 + kb < n) LU_TRY(eng->pack_panel(hi, (const float*)A, lda, k, k0, kb));
@@ -238,11 +239,12 @@ int lu_factor_blocked(lu_context* c, int64_t n, T* A, int64_t lda, int32_t* ipiv
             // next panel's interchanges, RL2 and RL3: a few narrow launches) runs
             // before TU_right(k) is released, so that it does not wait behind the
             // right update's thousands of CTAs; PF_{k+1} then overlaps TU_right(k).
-            if (k + 1 < nk) LU_TRY(trailing_update<T>(c, hi, n, A, lda, k, k0, kb, c1, c2, 0, plan_of(k), eng, 0));
+            if (k + 1 < nk)
+                LU_TRY(trailing_update<T>(c, hi, n, A, lda, k, k0, kb, c1, c2, 0, plan_of(k), eng, 0, pivot));
             LU_CHECK_CUDA(cudaEventRecord(c->ev_pf, hi));
             LU_CHECK_CUDA(cudaStreamWaitEvent(lo, c->ev_pf, 0));
             // TU_right(k) and the deferred left interchanges on the low-priority stream
-            LU_TRY(trailing_update<T>(c, lo, n, A, lda, k, k0, kb, c2, n, k0, plan_of(k), eng, 1));
+            LU_TRY(trailing_update<T>(c, lo, n, A, lda, k, k0, kb, c2, n, k0, plan_of(k), eng, 1, pivot));
             LU_CHECK_CUDA(cudaEventRecord(c->ev_tu, lo));
             if (k + 1 < nk) {
                 LU_TRY(panel(k + 1));
@@ -250,7 +252,7 @@ int lu_factor_blocked(lu_context* c, int64_t n, T* A, int64_t lda, int32_t* ipiv
                 LU_CHECK_CUDA(cudaStreamWaitEvent(hi, c->ev_tu, 0));
             }
         } else {
-            LU_TRY(trailing_update<T>(c, hi, n, A, lda, k, k0, kb, c1, n, k0, plan_of(k), eng, 0));
+            LU_TRY(trailing_update<T>(c, hi, n, A, lda, k, k0, kb, c1, n, k0, plan_of(k), eng, 0, pivot));
             if (k + 1 < nk) LU_TRY(panel(k + 1));
         }
     }
@@ -262,9 +264,9 @@ int lu_factor_blocked(lu_context* c, int64_t n, T* A, int64_t lda, int32_t* ipiv
 }
 
 template int lu_factor_blocked<double>(lu_context*, int64_t, double*, int64_t, int32_t*, const lu_opts&, int32_t*,
-                                       const LuTuEngine*);
+                                       const LuTuEngine*, bool);
 template int lu_factor_blocked<float>(lu_context*, int64_t, float*, int64_t, int32_t*, const lu_opts&, int32_t*,
-                                      const LuTuEngine*);
+                                      const LuTuEngine*, bool);
 
 extern "C" int lu_factor_ex(lu_handle h, lu_dtype dtype, int64_t n, void* A, int64_t lda, int32_t* ipiv,
                             const lu_opts* opts, int32_t* info) {
