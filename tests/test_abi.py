@@ -40,6 +40,7 @@ def test_argument_validation_without_gpu(built):
     assert L.lu_factor(4, ctypes.c_void_p(16), 4, ctypes.c_void_p(16), 1025) == -5
     assert L.lu_solve(-2, 1, None, None, None) == -1
     assert L.lu_factor_ex(None, 0, 4, None, 4, None, None, None) == _lib.LU_ERR_HANDLE
+    assert L.lu_potrf_ex(None, 0, 4, None, 4, None, None) == _lib.LU_ERR_HANDLE
     o = pkg.LuOpts()
     L.lu_default_opts(ctypes.byref(o))
     assert (o.nb, o.lookahead, o.steal) == (256, 1, 1)
