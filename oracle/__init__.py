@@ -20,6 +20,9 @@ Each routine states the passage of the paper it restates:
 * ``potrf`` -- Cholesky A = L L^T (unblocked, right-looking), the factorization
   the paper names as fitting the same blocked / look-ahead skeleton (Sec. 1, 7).
 * ``chol_error`` -- ||A0 - L L^T|| / (n ||A0||) (compensated sums).
+* ``geqr2`` -- Householder QR, the unblocked form of the geqrf the paper's QR
+  experiments reorganise with look-ahead (Sec. 6); ``qr_q`` forms Q from the
+  reflectors and ``qr_error`` gives ||A0 - Q R|| / (n ||A0||) and ||Q^T Q - I||.
 * ``round_*`` -- ties-to-even rounding onto bf16 / fp16 / e4m3 / fp32.
 * ``quant_e4m3_rows`` / ``quant_e4m3_cols`` -- power-of-two block scaling onto
   e4m3 (one scale per row of L21 / per column of U12) for the FP8 update.
@@ -82,6 +85,7 @@ def _load():
             "oracle_quant_e4m3_blocks": (None, [i64, i64, vp, i64, i64, vp, vp]),
             "oracle_potrf": (i32, [i64, vp, i64]),
             "oracle_chol_error": (dbl, [i64, vp, i64, vp, i64]),
+            "oracle_geqr2": (None, [i64, i64, vp, i64, vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -269,3 +273,40 @@ def chol_error(A0, L) -> float:
     A0f, Lf = _f64(A0), _f64(L)
     n = A0f.shape[0]
     return float(lib.oracle_chol_error(n, _ptr(A0f), max(n, 1), _ptr(Lf), max(Lf.shape[0], 1)))
+
+
+def geqr2(A):
+    """Householder QR of an m x n matrix.  Returns (QR, tau): R in the upper
+    triangle, the reflectors' vectors (unit first entry implied) below it, and
+    tau[j] the reflectors' scalars (LAPACK geqrf layout)."""
+    lib = _load()
+    W = _f64(A)
+    m, n = W.shape
+    tau = np.zeros(max(min(m, n), 1), dtype=np.float64)
+    lib.oracle_geqr2(m, n, _ptr(W), max(m, 1), _ptr(tau))
+    return W, tau[:min(m, n)].copy()
+
+
+def qr_q(QR, tau):
+    """Q (m x m) = H_0 H_1 ... H_{k-1} from geqr2's reflectors, H_j = I - tau_j v_j v_j^T."""
+    QR = np.asarray(QR, dtype=np.float64)
+    m = QR.shape[0]
+    Q = np.eye(m)
+    for j in range(len(tau) - 1, -1, -1):
+        v = np.zeros(m)
+        v[j] = 1.0
+        v[j + 1:] = QR[j + 1:, j]
+        Q -= tau[j] * np.outer(v, v @ Q)
+    return Q
+
+
+def qr_error(A0, QR, tau):
+    """(||A0 - Q R||_inf / (n ||A0||_inf), ||Q^T Q - I||_inf) for square or tall A0."""
+    A0 = np.asarray(A0, dtype=np.float64)
+    n = A0.shape[1]
+    Q = qr_q(QR, tau)
+    R = np.triu(np.asarray(QR, dtype=np.float64))
+    res = np.abs(A0 - Q @ R).sum(axis=1).max()
+    anorm = np.abs(A0).sum(axis=1).max()
+    orth = np.abs(Q.T @ Q - np.eye(Q.shape[0])).sum(axis=1).max()
+    return (res / (max(n, 1) * anorm) if anorm > 0 else res), orth

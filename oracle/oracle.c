@@ -39,6 +39,11 @@
  *                     blocked/look-ahead skeleton (Sec. 1, Sec. 7); lower
  *                     triangle only.
  *   oracle_chol_error -- ||A0 - L L^T|| / (n ||A0||) (inf-norms, compensated).
+ *   oracle_geqr2   -- QR factorization A = Q R by Householder reflectors, the
+ *                     unblocked form of the geqrf the paper's QR experiments
+ *                     reorganise with look-ahead (Sec. 6): reflector j maps the
+ *                     updated column j onto beta e_j, beta = -sign(a_jj) ||x||,
+ *                     and is applied to the columns to its right.
  *   oracle_round_bf16 / oracle_round_fp16 / oracle_quant_e4m3 -- IEEE-style
  *                     round-to-nearest-even onto the narrow formats used for
  *                     the mixed-precision trailing update operands.
@@ -480,4 +485,41 @@ double oracle_chol_error(int64_t n, const double *A0, int64_t lda0, const double
     }
     const double anorm = oracle_norm_inf(n, n, A0, lda0);
     return anorm > 0.0 ? worst / ((double)n * anorm) : (worst > 0.0 ? INFINITY : 0.0);
+}
+
+/* ---------------------------------------------------------------------------
+ * Householder QR of an m x n matrix, unblocked.  Step j (j < min(m, n)) takes
+ * x = A(j:m, j), alpha = x_0 and sigma = ||x(1:)||_2.  If sigma == 0 the
+ * reflector is the identity (tau_j = 0).  Otherwise beta = -sign(alpha)
+ * sqrt(alpha^2 + sigma^2), tau_j = (beta - alpha) / beta and
+ * v = [1; x(1:) / (alpha - beta)], so that (I - tau_j v v^T) x = beta e_0;
+ * A(j, j) := beta, A(j+1:m, j) := v(1:), and every column c > j becomes
+ * A(j:m, c) - tau_j v (v^T A(j:m, c)).  R is the upper triangle of the result.
+ * (No rescaling of norms near the underflow threshold.)
+ * ------------------------------------------------------------------------- */
+void oracle_geqr2(int64_t m, int64_t n, double *A, int64_t lda, double *tau)
+{
+    const int64_t k = m < n ? m : n;
+    for (int64_t j = 0; j < k; ++j) {
+        double ss = 0.0;
+        for (int64_t i = j + 1; i < m; ++i) ss += A[IDX(i, j, lda)] * A[IDX(i, j, lda)];
+        const double alpha = A[IDX(j, j, lda)];
+        if (ss == 0.0) {
+            tau[j] = 0.0;
+            continue;
+        }
+        const double norm = sqrt(alpha * alpha + ss);
+        const double beta = alpha >= 0.0 ? -norm : norm;
+        tau[j] = (beta - alpha) / beta;
+        const double scale = 1.0 / (alpha - beta);
+        for (int64_t i = j + 1; i < m; ++i) A[IDX(i, j, lda)] = A[IDX(i, j, lda)] * scale;
+        A[IDX(j, j, lda)] = beta;
+        for (int64_t c = j + 1; c < n; ++c) {
+            double w = A[IDX(j, c, lda)];
+            for (int64_t i = j + 1; i < m; ++i) w += A[IDX(i, j, lda)] * A[IDX(i, c, lda)];
+            const double tw = tau[j] * w;
+            A[IDX(j, c, lda)] = A[IDX(j, c, lda)] - tw;
+            for (int64_t i = j + 1; i < m; ++i) A[IDX(i, c, lda)] = A[IDX(i, c, lda)] - A[IDX(i, j, lda)] * tw;
+        }
+    }
 }

@@ -411,3 +411,47 @@ def test_chol_error_planted():
     L[1, 1] = 1 + delta
     # (L L^T)(1,1) = (1 + delta)^2: one residual entry of 2 delta + delta^2 in row 1
     assert oracle.chol_error(np.eye(n), L) == (2 * delta + delta ** 2) / n
+
+
+def test_geqr2_upper_triangular_is_untouched():
+    """A column that is already zero below the diagonal needs no reflector:
+    tau_j = 0 and R = A exactly."""
+    g = synth.rng(14, 0)
+    U = np.triu(g.uniform(-1, 1, size=(7, 7)))
+    QR, tau = oracle.geqr2(U)
+    assert np.array_equal(tau, np.zeros(7)) and np.array_equal(QR, U)
+
+
+def test_geqr2_hand_worked_2x2():
+    """A = [[3, 1], [4, 2]], worked by hand from the reflector definition:
+    alpha = 3, sigma = 4, beta = -5, tau = 8/5, v = [1, 1/2];
+    w = 1 + 2/2 = 2, R = [[-5, 1 - 16/5], [0, 2 - 8/5]] = [[-5, -2.2], [0, 0.4]]."""
+    QR, tau = oracle.geqr2(np.array([[3.0, 1.0], [4.0, 2.0]]))
+    assert tau[0] == 1.6 and tau[1] == 0.0
+    assert QR[0, 0] == -5.0 and QR[1, 0] == 0.5
+    assert abs(QR[0, 1] + 2.2) <= 4e-16 and abs(QR[1, 1] - 0.4) <= 4e-16
+
+
+@pytest.mark.parametrize("m,n", [(5, 5), (60, 60), (90, 40)])
+def test_geqr2_against_lapack_raw(m, n):
+    """numpy's 'raw' QR is LAPACK dgeqrf's output (reflectors below the diagonal,
+    R above, tau): the same convention, so every entry agrees to rounding."""
+    A = synth.uniform_matrix(max(m, n), seed=m + n)[:m, :n]
+    QR, tau = oracle.geqr2(A)
+    h, tau_l = np.linalg.qr(A, mode="raw")
+    scale = np.abs(A).max()
+    assert np.abs(QR - h.T).max() <= 1e-12 * scale
+    assert np.abs(tau - tau_l).max() <= 1e-12
+    res, orth = oracle.qr_error(A, QR, tau)
+    assert res <= 4 * np.finfo(float).eps and orth <= 8 * m * np.finfo(float).eps
+
+
+def test_qr_error_planted():
+    """For A0 = I the reflectors are identities (Q = I, R = I); a planted error
+    delta in R(0, 1) is reported as delta / n, and Q stays exactly orthogonal."""
+    n, delta = 5, 0.25
+    QR, tau = oracle.geqr2(np.eye(n))
+    assert np.array_equal(QR, np.eye(n)) and np.array_equal(tau, np.zeros(n))
+    QR[0, 1] += delta
+    res, orth = oracle.qr_error(np.eye(n), QR, tau)
+    assert res == delta / n and orth == 0.0
