@@ -70,7 +70,8 @@ int oracle_num_threads(void)
 /*
  * Unblocked right-looking LU with partial pivoting of an m x n matrix
  * (RL1, LU_unb).  For j = 0 .. min(m,n)-1:
- *   p  = smallest i >= j maximising |A(i,j)|   (first maximum wins)
+ *   p  = smallest i >= j maximising |A(i,j)|   (first maximum wins; NaN
+ *        candidates are never chosen, and p = j when all of them are NaN)
  *   ipiv[j] = p + 1
  *   if A(p,j) == 0: record info = j+1 (first only), skip scaling and update
  *   swap whole rows j and p (all n columns)
@@ -98,12 +99,16 @@ int oracle_getrf_steps(int64_t m, int64_t n, double *A, int64_t lda, int32_t *ip
     (void)nthreads;
 #endif
     for (int64_t j = 0; j < kmax; ++j) {
-        int64_t p = j;
-        double best = fabs(A[IDX(j, j, lda)]);
-        for (int64_t i = j + 1; i < m; ++i) {
+        /* NaN is unordered, so it maximises nothing: it is skipped, and a
+         * column whose every candidate is NaN keeps its diagonal position. */
+        int64_t p = -1;
+        double best = 0.0;
+        for (int64_t i = j; i < m; ++i) {
             double v = fabs(A[IDX(i, j, lda)]);
-            if (v > best) { best = v; p = i; }
+            if (isnan(v)) continue;
+            if (p < 0 || v > best) { best = v; p = i; }
         }
+        if (p < 0) p = j;
         if (gap) {
             double second = -1.0;
             for (int64_t i = j; i < m; ++i) {

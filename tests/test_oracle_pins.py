@@ -393,6 +393,32 @@ def test_potrf_against_numpy(n):
     assert oracle.chol_error(A, L) <= 4 * np.finfo(float).eps
 
 
+def test_nan_candidate_never_pivots():
+    """Reading of RL1's pivot search for NaN (the paper is silent): NaN is
+    unordered, so it maximises nothing and is never chosen; a column whose
+    every candidate is NaN keeps its diagonal position.  Worked by hand:
+    column 0 holds NaN, 3, 1 -> row 2 wins although the NaN comes first;
+    after the swap row 2 becomes [NaN, NaN, NaN] through l = NaN / 3;
+    column 1 holds NaN, -2/3 -> row 3; column 2 holds only NaN -> row 3
+    stays.  No exactly-zero pivot occurs (NaN == 0 is false)."""
+    A = np.array([[np.nan, 1.0, 0.0], [3.0, 2.0, 0.0], [1.0, 0.0, 4.0]])
+    LU, ipiv, info, _ = oracle.getrf(A)
+    assert list(ipiv) == [2, 3, 3] and info == 0
+    np.testing.assert_array_equal(LU[0], [3.0, 2.0, 0.0])
+    assert LU[1, 0] == 1.0 / 3.0 and LU[1, 2] == 4.0
+    assert abs(LU[1, 1] - (-2.0 / 3.0)) <= np.spacing(2.0 / 3.0)
+    assert np.all(np.isnan(LU[2]))
+    # every candidate NaN: the diagonal position is kept
+    LU, ipiv, info, _ = oracle.getrf(np.array([[np.nan, 1.0], [np.nan, 2.0]]))
+    assert list(ipiv) == [1, 2] and info == 0
+    # a NaN in the first candidate position loses as a zero there would
+    B = synth.uniform_matrix(9, seed=4)
+    B[0, 0] = 0.0
+    first = oracle.getrf(B)[1][0]
+    B[0, 0] = np.nan
+    assert first != 1 and oracle.getrf(B)[1][0] == first
+
+
 def test_potrf_not_positive_definite():
     assert oracle.potrf(np.diag([1.0, 2.0, -1.0, 4.0]))[1] == 3
     assert oracle.potrf(np.ones((2, 2)))[1] == 2  # the leading 2 x 2 minor is singular
