@@ -532,13 +532,7 @@ static int gesv_batched_impl(lu_context* c, int batch, const int32_t* n, T* cons
         batch_order_kernel<<<1, 1024, 0, st>>>(batch, n, order, counter);
     }
     LU_CHECK_LAUNCH();
-    static bool attr[2] = {false, false};
-    const int ti = sizeof(T) == 8 ? 0 : 1;
-    if (!attr[ti]) {
-        LU_CHECK_CUDA(cudaFuncSetAttribute(batched_gesv_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)BatchSmem<T>::bytes));
-        attr[ti] = true;
-    }
+    LU_TRY(lu_func_smem(batched_gesv_kernel<T>, (int)BatchSmem<T>::bytes));
     int per_sm = 0;
     LU_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batched_gesv_kernel<T>, kBT,
                                                                 BatchSmem<T>::bytes));

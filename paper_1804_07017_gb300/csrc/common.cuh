@@ -34,6 +34,16 @@
 void lu_set_error_string(const char* what, const char* file, int line);
 void lu_count_launch();
 
+// Kernel attributes belong to a device's context, so they are set once per
+// (current device, kernel): the dynamic shared-memory limit `smem_bytes` and,
+// with `nonportable_cluster`, permission for clusters above 8 CTAs.  Thread
+// safe; a failed set is not remembered, so the next call tries again.
+int lu_func_attrs(const void* fn, int smem_bytes, bool nonportable_cluster);
+template <typename F>
+inline int lu_func_smem(F* fn, int smem_bytes, bool nonportable_cluster = false) {
+    return lu_func_attrs(reinterpret_cast<const void*>(fn), smem_bytes, nonportable_cluster);
+}
+
 // Bounded-wait budget for every device-side spin (nanoseconds of %globaltimer).
 #define LU_WAIT_NS (4000000000ull)
 

@@ -332,12 +332,7 @@ int make_operand_map(CUtensorMap* map, const void* base, int elem_bytes, int64_t
 template <int BN>
 int launch_bn(cudaStream_t st, const CUtensorMap& ma, const CUtensorMap& mb, const TcUpdateParams& p, int grid) {
     using L = TcLayout<BN>;
-    static bool attr = false;
-    if (!attr) {
-        LU_CHECK_CUDA(cudaFuncSetAttribute(tc_update_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           L::kSmemBytes));
-        attr = true;
-    }
+    LU_TRY(lu_func_smem(tc_update_kernel<BN>, L::kSmemBytes));
     LuProfScope prof(st, LU_K_TC_UPDATE, 8.0 * p.m * p.ncols + (double)p.elem_bytes * p.k * (p.m + p.ncols),
                      2.0 * p.m * p.ncols * p.k);
     tc_update_kernel<BN><<<grid, kThreads, L::kSmemBytes, st>>>(ma, mb, p);

@@ -117,12 +117,7 @@ int lu_launch_laswp_plan(cudaStream_t st, const int32_t* ipiv, int64_t k1, int64
     const int K = (int)(k2 - k1);
     if (K <= 0) return LU_SUCCESS;
     size_t smem = sizeof(int32_t) * 4 * (size_t)K;
-    static bool attr = false;
-    if (!attr) {
-        LU_CHECK_CUDA(cudaFuncSetAttribute(laswp_plan_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           sizeof(int32_t) * 4 * LU_MAX_NB));
-        attr = true;
-    }
+    LU_TRY(lu_func_smem(laswp_plan_kernel, sizeof(int32_t) * 4 * LU_MAX_NB));
     LuProfScope prof(st, LU_K_LASWP, 20.0 * K, 0.0);
     laswp_plan_kernel<<<1, kPlanThreads, smem, st>>>(ipiv, k1, K, plan);
     LU_CHECK_LAUNCH();
@@ -135,13 +130,7 @@ int lu_launch_laswp_apply(cudaStream_t st, T* A, int64_t lda, int64_t c1, int64_
     if (K <= 0 || n1 + n2 <= 0) return LU_SUCCESS;
     const int warps = kApplyThreads / 32;
     size_t smem = sizeof(T) * 2 * (size_t)K * warps;
-    static bool attr[2] = {false, false};
-    const int ti = sizeof(T) == 8 ? 0 : 1;
-    if (!attr[ti]) {
-        LU_CHECK_CUDA(cudaFuncSetAttribute(laswp_apply_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)(sizeof(T) * 2 * LU_MAX_NB * warps)));
-        attr[ti] = true;
-    }
+    LU_TRY(lu_func_smem(laswp_apply_kernel<T>, (int)(sizeof(T) * 2 * LU_MAX_NB * warps)));
     int64_t blocks = lu_cdiv(n1 + n2, warps);
     blocks = std::min<int64_t>(blocks, max_blocks > 0 ? (int64_t)max_blocks : (int64_t)std::max(num_sms, 1) * 8);
     LuProfScope prof(st, LU_K_LASWP, 2.0 * 2.0 * K * (double)(n1 + n2) * sizeof(T), 0.0);

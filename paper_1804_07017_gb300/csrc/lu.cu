@@ -16,7 +16,9 @@
 
 #include <algorithm>
 #include <atomic>
+#include <map>
 #include <mutex>
+#include <utility>
 
 #include "internal.h"
 
@@ -31,6 +33,22 @@ long long lu_launches_so_far() { return g_launches.load(); }
 void lu_set_error_string(const char* what, const char* file, int line) {
     std::lock_guard<std::mutex> lk(g_err_mu);
     snprintf(g_last_error, sizeof(g_last_error), "%s (%s:%d)", what, file, line);
+}
+
+int lu_func_attrs(const void* fn, int smem_bytes, bool nonportable_cluster) {
+    static std::mutex mu;
+    static std::map<std::pair<int, const void*>, int> done;  // (device, kernel) -> shared-memory limit set
+    int dev = 0;
+    LU_CHECK_CUDA(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lk(mu);
+    const auto key = std::make_pair(dev, fn);
+    auto it = done.find(key);
+    if (it != done.end() && it->second >= smem_bytes) return LU_SUCCESS;
+    if (nonportable_cluster)
+        LU_CHECK_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+    LU_CHECK_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes));
+    done[key] = smem_bytes;
+    return LU_SUCCESS;
 }
 
 extern "C" int64_t lu_launch_count(void) { return (int64_t)g_launches.load(); }

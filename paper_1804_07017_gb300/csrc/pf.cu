@@ -218,14 +218,7 @@ int lu_launch_pf_leaf(lu_context* c, cudaStream_t st, T* A, int64_t lda, int64_t
     int64_t R = 0, G = 0;
     size_t smem = 0;
     if (!lu_pf_leaf_shape(m, w, (int)sizeof(T), max_ctas, &R, &G, &smem)) return LU_ERR_UNSUPPORTED;
-    static bool attr_set[2] = {false, false};
-    const int ti = sizeof(T) == 8 ? 0 : 1;
-    if (!attr_set[ti]) {
-        LU_CHECK_CUDA(cudaFuncSetAttribute(pf_leaf_kernel<T, kPfThreads>,
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           LU_PF_SMEM_BUDGET));
-        attr_set[ti] = true;
-    }
+    LU_TRY(lu_func_smem(pf_leaf_kernel<T, kPfThreads>, LU_PF_SMEM_BUDGET));
     T* slots = reinterpret_cast<T*>(c->pf_slots);
     int* slot_idx = reinterpret_cast<int*>(reinterpret_cast<char*>(c->pf_slots) +
                                            sizeof(double) * (2 * LU_PF_MAX_CTAS * (LU_PF_MAX_LEAF + 1) +

@@ -23,6 +23,9 @@
 #include <cstdio>
 #include <cstdlib>
 
+#include <map>
+#include <mutex>
+
 #include "internal.h"
 #include "profile.h"
 
@@ -332,22 +335,27 @@ int max_clusters_for(typename LeafTable<T>::Fn fn, int C, size_t smem) {
 
 }  // namespace
 
-// Largest cluster size usable for the leaf (0 if clusters are unavailable); cached per type.
+// Largest cluster size usable for the leaf (0 if clusters are unavailable); cached per
+// (device, type), since kernel attributes and cluster occupancy belong to a device.
 template <typename T>
 static int cluster_limit() {
-    static int lim[2] = {-1, -1};
-    const int ti = sizeof(T) == 8 ? 0 : 1;
-    if (lim[ti] >= 0) return lim[ti];
+    static std::mutex mu;
+    static std::map<int, int> lim;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = lim.find(dev);
+    if (it != lim.end()) return it->second;
     const int ws[3] = {8, 16, 32}, rqs[4] = {1, 2, 4, 8};
     for (int hw = 0; hw < 2; ++hw)
         for (int w : ws)
             for (int rq : rqs) {
                 auto fn = LeafTable<T>::get(w, rq, hw != 0);
                 if (!fn) continue;
-                if (cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)
-                    cudaGetLastError();
-                if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024) != cudaSuccess)
-                    cudaGetLastError();
+                if (lu_func_smem(fn, 220 * 1024, true) != LU_SUCCESS) cudaGetLastError();
             }
     int best = 0;
     auto fn = LeafTable<T>::get(16, 1, false);
@@ -357,7 +365,7 @@ static int cluster_limit() {
             break;
         }
     }
-    lim[ti] = best;
+    lim[dev] = best;
     return best;
 }
 

@@ -644,15 +644,7 @@ int lu_launch_pf_leaf_push(cudaStream_t st, T* A, int64_t lda, int64_t m, int w,
     auto fn = PushTable<T>::get(wc, R / kPT, &smem);
     if (!fn || C > kMaxC || sib < 0 || sib > wc || sib > right_cols || kprev < 0 || kprev > kMaxPrev)
         return LU_ERR_UNSUPPORTED;
-    static bool attr_done[2][3][4] = {};
-    const int wi = wc == 8 ? 0 : (wc == 16 ? 1 : 2);
-    const int ri = (R / kPT) == 1 ? 0 : ((R / kPT) == 2 ? 1 : ((R / kPT) == 4 ? 2 : 3));
-    bool& done = attr_done[sizeof(T) == 8 ? 0 : 1][wi][ri];
-    if (!done) {
-        LU_CHECK_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
-        LU_CHECK_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        done = true;
-    }
+    LU_TRY(lu_func_smem(fn, (int)smem, true));
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(C, 1, 1);
     cfg.blockDim = dim3(kPT, 1, 1);

@@ -662,12 +662,7 @@ int lu_launch_perm_from_ipiv(cudaStream_t st, int64_t n, const int32_t* ipiv, in
     const size_t smem = sizeof(int32_t) * (size_t)n;
     LuProfScope prof(st, LU_K_SOLVE, 8.0 * n, 0.0);
     if (smem <= 200 * 1024) {
-        static bool attr = false;
-        if (!attr) {
-            LU_CHECK_CUDA(cudaFuncSetAttribute(perm_from_ipiv_smem_kernel,
-                                               cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-            attr = true;
-        }
+        LU_TRY(lu_func_smem(perm_from_ipiv_smem_kernel, 200 * 1024));
         perm_from_ipiv_smem_kernel<<<1, 256, smem, st>>>((int)n, ipiv, perm);
     } else {
         perm_from_ipiv_global_kernel<<<1, 256, 0, st>>>(n, ipiv, perm);
@@ -693,15 +688,8 @@ static int trsv_plain(lu_context* c, cudaStream_t st, bool lower_unit, int64_t n
                       int64_t lda, T* X, int64_t ldx) {
     using C = TrsvPlainCfg<T>;
     const int nblk = (int)lu_cdiv(n, C::BS);
-    static bool attr[2] = {false, false};
-    const int ti = sizeof(T) == 8 ? 0 : 1;
-    if (!attr[ti]) {
-        LU_CHECK_CUDA(cudaFuncSetAttribute(trsv_plain_kernel<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)C::smem));
-        LU_CHECK_CUDA(cudaFuncSetAttribute(trsv_plain_kernel<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)C::smem));
-        attr[ti] = true;
-    }
+    LU_TRY(lu_func_smem(trsv_plain_kernel<T, true>, (int)C::smem));
+    LU_TRY(lu_func_smem(trsv_plain_kernel<T, false>, (int)C::smem));
     for (int64_t c0 = 0; c0 < nrhs; c0 += kNR) {
         const int nr = (int)std::min<int64_t>(kNR, nrhs - c0);
         LU_CHECK_CUDA(cudaMemsetAsync(&c->sync[1].arrive, 0, sizeof(unsigned) * 2, st));
@@ -782,12 +770,7 @@ int lu_launch_trinv_diag(cudaStream_t st, int64_t n, const T* LU, int64_t lda, T
     if (n <= 0) return LU_SUCCESS;
     using C = TrsvCfg<T>;
     const size_t smem = sizeof(T) * 2 * (size_t)C::BS * (C::BS + 1);
-    static bool attr[2] = {false, false};
-    const int ti = sizeof(T) == 8 ? 0 : 1;
-    if (!attr[ti]) {
-        LU_CHECK_CUDA(cudaFuncSetAttribute(trinv_diag_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        attr[ti] = true;
-    }
+    LU_TRY(lu_func_smem(trinv_diag_kernel<T>, (int)smem));
     const int nblk = (int)lu_cdiv(n, C::BS);
     LuProfScope prof(st, LU_K_SOLVE, sizeof(T) * (2.0 * n * C::BS + 2.0 * nblk * C::BS * C::BS),
                      (double)nblk * C::BS * C::BS * C::BS / 3.0);
@@ -812,29 +795,14 @@ int lu_launch_trsv_blocked(lu_context* c, cudaStream_t st, bool lower_unit, int6
         LU_TRY(make_inverse_map<T>(&dmap, Dinv, nblk));
     else
         dmap = map;
-    static bool attr[2] = {false, false};
-    const int ti = sizeof(T) == 8 ? 0 : 1;
-    if (!attr[ti]) {
-        LU_CHECK_CUDA(cudaFuncSetAttribute(trsv_tma_kernel<T, true, false>,
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem));
-        LU_CHECK_CUDA(cudaFuncSetAttribute(trsv_tma_kernel<T, false, false>,
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem));
-        LU_CHECK_CUDA(cudaFuncSetAttribute(trsv_tma_kernel<T, true, true>,
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem));
-        LU_CHECK_CUDA(cudaFuncSetAttribute(trsv_tma_kernel<T, false, true>,
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem));
-        attr[ti] = true;
-    }
+    LU_TRY(lu_func_smem(trsv_tma_kernel<T, true, false>, (int)C::smem));
+    LU_TRY(lu_func_smem(trsv_tma_kernel<T, false, false>, (int)C::smem));
+    LU_TRY(lu_func_smem(trsv_tma_kernel<T, true, true>, (int)C::smem));
+    LU_TRY(lu_func_smem(trsv_tma_kernel<T, false, true>, (int)C::smem));
     if constexpr (sizeof(T) == 4) {
         if (inv && xtag && nrhs == 1) {
-            static bool tattr = false;
-            if (!tattr) {
-                LU_CHECK_CUDA(cudaFuncSetAttribute(trsv_tag_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                   (int)C::smem));
-                LU_CHECK_CUDA(cudaFuncSetAttribute(trsv_tag_kernel<false>,
-                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem));
-                tattr = true;
-            }
+            LU_TRY(lu_func_smem(trsv_tag_kernel<true>, (int)C::smem));
+            LU_TRY(lu_func_smem(trsv_tag_kernel<false>, (int)C::smem));
             // tags are unique per launch within the process (0 is never used: the buffer starts zeroed)
             static std::atomic<unsigned> next_tag{1};
             unsigned tag = next_tag.fetch_add(1);
@@ -849,14 +817,8 @@ int lu_launch_trsv_blocked(lu_context* c, cudaStream_t st, bool lower_unit, int6
     }
     if constexpr (sizeof(T) == 4) {
         if (inv && xtag && nrhs == 1) {
-            static bool tattr = false;
-            if (!tattr) {
-                LU_CHECK_CUDA(cudaFuncSetAttribute(trsv_tag_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                   (int)C::smem));
-                LU_CHECK_CUDA(cudaFuncSetAttribute(trsv_tag_kernel<false>,
-                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem));
-                tattr = true;
-            }
+            LU_TRY(lu_func_smem(trsv_tag_kernel<true>, (int)C::smem));
+            LU_TRY(lu_func_smem(trsv_tag_kernel<false>, (int)C::smem));
             // tags are unique per launch within the process (0 is never used: the buffer starts zeroed)
             static std::atomic<unsigned> next_tag{1};
             unsigned tag = next_tag.fetch_add(1);

@@ -344,15 +344,8 @@ int lu_launch_trsm_lunit(cudaStream_t st, int64_t m, int64_t n, const T* L, int6
     const int mp = (int)((m + 31) & ~31);
     const size_t smem16 = sizeof(T) * ((size_t)16 * mp + 32 * 33);
     const size_t smem8 = sizeof(T) * ((size_t)8 * mp + 32 * 33);
-    static bool attr[2] = {false, false};
-    const int ti = sizeof(T) == 8 ? 0 : 1;
-    if (!attr[ti]) {
-        LU_CHECK_CUDA(cudaFuncSetAttribute(trsm_lunit_kernel<T, 16>,
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-        LU_CHECK_CUDA(cudaFuncSetAttribute(trsm_lunit_kernel<T, 8>,
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-        attr[ti] = true;
-    }
+    LU_TRY(lu_func_smem(trsm_lunit_kernel<T, 16>, 200 * 1024));
+    LU_TRY(lu_func_smem(trsm_lunit_kernel<T, 8>, 200 * 1024));
     // max_ctas > 0 caps the grid (the CTAs then loop over column blocks), so a wide
     // solve on the low-priority stream leaves SMs to the panel path
     auto grid_of = [&](int64_t blocks) {
@@ -364,12 +357,7 @@ int lu_launch_trsm_lunit(cudaStream_t st, int64_t m, int64_t n, const T* L, int6
     // per-block loads, which many CTAs share through L2
     const size_t staged = sizeof(T) * ((size_t)16 * mp + (size_t)m * (m - 1) / 2);
     if (m > 32 && n <= 512 && staged <= 160 * 1024) {
-        static bool sattr[2] = {false, false};
-        if (!sattr[ti]) {
-            LU_CHECK_CUDA(cudaFuncSetAttribute(trsm_lunit_staged_kernel<T, 16>,
-                                               cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024));
-            sattr[ti] = true;
-        }
+        LU_TRY(lu_func_smem(trsm_lunit_staged_kernel<T, 16>, 160 * 1024));
         trsm_lunit_staged_kernel<T, 16><<<(unsigned)lu_cdiv(n, 16), kTrsmThreads, staged, st>>>((int)m, n, L, ldl, B,
                                                                                               ldb);
     } else if (smem16 <= 64 * 1024) {
@@ -420,12 +408,7 @@ template <typename T, int BM, int BN>
 static int launch_narrow(cudaStream_t st, int64_t m2, int64_t w2, int64_t w1, const T* L11, T* A12, const T* A21,
                          T* A22, int64_t lda, unsigned* arrivals) {
     const size_t smem = sizeof(T) * 2 * BK * BM;
-    static bool attr = false;
-    if (!attr) {
-        LU_CHECK_CUDA(cudaFuncSetAttribute(trsm_gemm_narrow_kernel<T, BM, BN>,
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        attr = true;
-    }
+    LU_TRY(lu_func_smem(trsm_gemm_narrow_kernel<T, BM, BN>, (int)smem));
     const unsigned gx = (unsigned)std::max<int64_t>(1, lu_cdiv(m2, BM));
     trsm_gemm_narrow_kernel<T, BM, BN><<<gx, kGemmThreads, smem, st>>>(m2, (int)w2, (int)w1, L11, A12, A21, A22, lda,
                                                                       arrivals);

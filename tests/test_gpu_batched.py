@@ -200,3 +200,46 @@ def test_batched_designed_pivot_sequences(lu, dtype):
             assert fe <= 1e-14 and eta <= 1e-14, (name, n, fe, eta)
         else:
             assert fe <= 4 * u * 2 and eta <= 64 * n * u, (name, n, fe, eta)
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_batched_nan_first_candidate(lu, dtype):
+    """A NaN in the first candidate position of column 0 (A(0,0) = NaN) is
+    never chosen in the batched kernel either: the NaN row loses every search
+    it is the first candidate of and ends as the last row of the factors,
+    whole-row NaN, exactly as in the oracle; the other systems of the batch
+    are unaffected and meet the usual bounds."""
+    sizes = np.array([1, 2, 17, 33, 64, 100, 300, 512, 40, 96])
+    mats = [synth.uniform_matrix(int(n), seed=41, stream=int(n)) for n in sizes]
+    if dtype == torch.float32:
+        mats = [m.astype(np.float32).astype(np.float64) for m in mats]
+    poisoned = list(range(0, len(sizes) - 2))
+    for i in poisoned:
+        mats[i][0, 0] = np.nan
+    dA = [colmajor_dev(m, dtype) for m in mats]
+    piv = [torch.zeros(int(n), dtype=torch.int32, device="cuda") for n in sizes]
+    batch = lu.Batch(dA, piv)
+    lu.lu_factor_batched(batch)
+    torch.cuda.synchronize()
+    assert np.all(batch.info.cpu().numpy() == 0)
+    tau = 1e-8 if dtype == torch.float64 else 1e-3
+    tol = 1e-10 if dtype == torch.float64 else 1e-3
+    for i, n in enumerate(int(v) for v in sizes):
+        LU = dA[i].cpu().double().numpy()[:n, :n]
+        p = piv[i].cpu().numpy()
+        LU_o, po, info_o, gap = oracle.getrf(mats[i])
+        assert info_o == 0
+        nan = np.isnan(LU_o)
+        assert np.array_equal(np.isnan(LU), nan), (i, n)
+        if i in poisoned:
+            assert p[-1] == po[-1] == n and np.all(nan[n - 1]) and not nan[: n - 1].any()
+            if n > 1:
+                assert po[0] != 1 and p[0] == po[0]
+        else:
+            assert not nan.any()
+        sep = gap > tau
+        assert np.array_equal(p[sep], po[sep]), (i, n)
+        diff = np.nonzero(p != po)[0]
+        d = int(diff[0]) if diff.size else n
+        a, b = np.where(nan, 0.0, LU)[:d], np.where(nan, 0.0, LU_o)[:d]
+        assert np.abs(a - b).max(initial=0.0) <= tol * max(np.abs(b).max(initial=0.0), 1e-300), (i, n)

@@ -63,6 +63,24 @@ def check_pivots(piv, piv_o, gap, tau):
     assert bad.size == 0, f"pivots differ at separated steps {bad[:10]} (gaps {gap[bad[:10]]})"
 
 
+def compare_factors(LU, LU_o, piv, piv_o, gap, tau, tol):
+    """Pivots may differ only at steps whose candidates are not separated
+    (gap <= tau); the rows before the first differing step are final in both
+    factorizations (later interchanges only touch rows at or below their own
+    step), so they are always compared, entry by entry, relative to max|LU_o|.
+    NaN entries must sit in the same places.  Returns the relative error."""
+    check_pivots(piv, piv_o, gap, tau)
+    diff = np.nonzero(piv != piv_o)[0]
+    d = int(diff[0]) if diff.size else LU_o.shape[0]
+    a, b = LU[:d], LU_o[:d]
+    nan = np.isnan(b)
+    assert np.array_equal(np.isnan(a), nan)
+    scale = max(np.abs(b[~nan]).max(initial=0.0), 1e-300)
+    rel = float(np.abs(a[~nan] - b[~nan]).max(initial=0.0) / scale)
+    assert rel <= tol, (rel, d)
+    return rel
+
+
 @pytest.mark.parametrize("n,nb,ld_pad", [(1024, 64, 0), (1024, 64, 7), (333, 64, 0), (130, 32, 3), (1, 64, 0),
                                          (2, 64, 0), (700, 256, 0), (2048, 256, 0)])
 def test_factor_and_solve_fp64(lu, n, nb, ld_pad):
@@ -73,9 +91,7 @@ def test_factor_and_solve_fp64(lu, n, nb, ld_pad):
     check_pivots(piv, piv_o, gap, TAU64)
     LU = LU[:n, :n]
     assert oracle.factor_error(A0, LU, piv) <= 1e-14
-    if np.array_equal(piv, piv_o):
-        rel = np.abs(LU - LU_o).max() / max(np.abs(LU_o).max(), 1e-300)
-        assert rel <= 1e-10, rel
+    compare_factors(LU, LU_o, piv, piv_o, gap, TAU64, 1e-10)
     # |l_ij| <= 1 holds for the GPU factors too (the division is exact-rounded)
     assert np.all(np.abs(np.tril(LU, -1)) <= 1.0)
     b0 = synth.ones_rhs(A0)
@@ -87,6 +103,34 @@ def test_factor_and_solve_fp64(lu, n, nb, ld_pad):
     torch.cuda.synchronize()
     x = host(Bt)
     assert oracle.backward_error(A0, x, b0) <= 1e-14
+
+
+def test_c0_configuration(lu):
+    """The n = 1024 configuration exactly: A iid U[-1,1) from seed 0 (stream 0),
+    column-major with lda = n, nb = 64, depth-1 look-ahead, one right-hand side
+    b = A * ones(n).  Pivots equal the oracle's at every step (its smallest
+    relative gap between the two largest candidates is ~2e-4, far above any
+    rounding difference), the factors agree entry by entry to 1e-10 of
+    max|LU|, the factorization's backward error is <= 1e-14 and the solve's
+    eta <= 1e-14 (Sec. 3, LU_blk with RL1 = LU_unb)."""
+    n, nb = 1024, 64
+    A0 = synth.uniform_matrix(n, seed=0, stream=0)
+    A, LU, piv, info = factor_gpu(lu, A0, nb, lookahead=1)
+    LU_o, piv_o, info_o, gap = oracle.getrf(A0)
+    assert info == info_o == 0
+    assert gap.min() > TAU64
+    assert np.array_equal(piv, piv_o)
+    rel = np.abs(LU - LU_o).max() / np.abs(LU_o).max()
+    assert rel <= 1e-10, rel
+    assert oracle.factor_error(A0, LU, piv) <= 1e-14
+    b0 = synth.ones_rhs(A0)
+    Bt = dev(b0)
+    lu.lu_solve(A, torch.from_numpy(piv).cuda(), Bt)
+    torch.cuda.synchronize()
+    x = host(Bt)
+    assert oracle.backward_error(A0, x, b0) <= 1e-14
+    print(f"\n[c0] max|LU - LU_oracle|/max|LU_oracle| = {rel:.2e}, "
+          f"eta = {oracle.backward_error(A0, x, b0):.2e}, ||x - 1||_inf = {np.abs(x - 1).max():.2e}")
 
 
 def test_plain_lu_factor_entry(lu):
@@ -164,10 +208,8 @@ def test_panel_factor(lu, dtype, m, w, leaf):
     assert int(info.item()) == 0
     LUo, pivo, _, gap = oracle.getrf(P0)
     piv = ipiv.cpu().numpy()
-    check_pivots(piv, pivo, gap, TAU64 if dtype == torch.float64 else TAU32)
-    if np.array_equal(piv, pivo):
-        tol = 1e-12 if dtype == torch.float64 else 2e-4
-        assert np.abs(host(P) - LUo).max() <= tol * max(1.0, np.abs(LUo).max())
+    compare_factors(host(P), LUo, piv, pivo, gap, TAU64 if dtype == torch.float64 else TAU32,
+                    1e-12 if dtype == torch.float64 else 2e-4)
 
 
 @pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
@@ -299,30 +341,66 @@ def test_full_size_sampled(lu, n, nb):
     assert np.array_equal(ps, expect)
 
 
+def check_nan_factors(LU, LU_o, piv, piv_o, gap, tau, tol):
+    """Factors of an input holding NaN: NaN in the same places (one whole row,
+    the row that held the NaN), and the prefix comparison of compare_factors
+    on the finite entries (same pivots at separated steps)."""
+    nan = np.isnan(LU_o)
+    assert nan.any() and np.array_equal(np.isnan(LU), nan)
+    assert np.array_equal(np.nonzero(nan.all(axis=1))[0], np.nonzero(nan.any(axis=1))[0])
+    compare_factors(np.where(nan, 0.0, LU), np.where(nan, 0.0, LU_o), piv, piv_o, gap, tau, tol)
+
+
 @pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
 def test_panel_nan_and_zero_column(lu, dtype):
-    """A NaN candidate never wins the pivot search (strict comparisons), and an
-    exactly zero column is reported as the first zero pivot without scaling:
-    pivots and info equal the oracle's, which follows the same two readings."""
+    """A NaN candidate is never chosen, even in the first candidate position
+    (NaN is unordered, so it maximises nothing), and an exactly zero column is
+    reported as the first zero pivot without scaling.  P(0,0) = NaN: column 0
+    pivots on the largest finite entry, and the NaN row then carries NaN
+    through l = NaN / pivot into every later column, where it is skipped
+    again; column 21 is zero, so info = 22.  Pivots, info, the NaN pattern and
+    the finite entries equal the oracle's."""
     m, w = 3000, 40
     P0 = synth.uniform_matrix(m, w, seed=12, stream=5)
     if dtype == torch.float32:
         P0 = P0.astype(np.float32).astype(np.float64)
     P0[:, 21] = 0.0
-    P0[1500, 3] = np.nan  # below the pivot rows of column 3; row 1500 is never a pivot
+    P0[0, 0] = np.nan
     P = dev(P0, dtype)
     ipiv = torch.zeros(w, dtype=torch.int32, device="cuda")
     info = torch.zeros(1, dtype=torch.int32, device="cuda")
-    lu.lu_panel_factor_ex(P, ipiv, info, lu.default_opts(leaf=16))
-    torch.cuda.synchronize()
-    clean = P0.copy()
-    clean[1500, 3] = 0.0
-    _, pivo, info_o, gap = oracle.getrf(clean)
-    piv = ipiv.cpu().numpy()
-    assert int(info.item()) == info_o == 22
-    # columns before the NaN's column are unaffected by it
-    assert np.array_equal(piv[:3], pivo[:3])
-    assert np.all(piv != 1501)
+    for leaf in (16, 0):
+        P.copy_(dev(P0, dtype))
+        lu.lu_panel_factor_ex(P, ipiv, info, lu.default_opts(leaf=leaf))
+        torch.cuda.synchronize()
+        LU_o, pivo, info_o, gap = oracle.getrf(P0)
+        piv = ipiv.cpu().numpy()
+        assert pivo[0] != 1 and pivo[0] - 1 >= w  # the NaN row leaves the panel's rows
+        assert int(info.item()) == info_o == 22
+        check_nan_factors(host(P), LU_o, piv, pivo, gap, TAU64 if dtype == torch.float64 else TAU32,
+                          1e-12 if dtype == torch.float64 else 2e-4)
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_blocked_nan_first_candidate(lu, dtype):
+    """The blocked look-ahead factorization with A(0,0) = NaN.  The NaN row is
+    the first candidate of column 0 and loses; whenever later interchanges
+    bring it to the diagonal position of a step it is the first candidate
+    again and loses again, across panels, until the last step, where it is the
+    only candidate and stays.  Pivots, the NaN pattern and the finite entries
+    equal the oracle's."""
+    n, nb = 700, 64
+    A0 = synth.uniform_matrix(n, seed=31)
+    if dtype == torch.float32:
+        A0 = A0.astype(np.float32).astype(np.float64)
+    A0[0, 0] = np.nan
+    _, LU, piv, info = factor_gpu(lu, A0, nb, dtype=dtype, lookahead=1)
+    LU_o, piv_o, info_o, gap = oracle.getrf(A0)
+    assert info == info_o == 0
+    assert piv_o[0] != 1 and piv_o[-1] == n and piv[-1] == n
+    assert np.all(np.isnan(LU_o[n - 1])) and not np.isnan(LU_o[: n - 1]).any()
+    check_nan_factors(LU[:n, :n], LU_o, piv, piv_o, gap, TAU64 if dtype == torch.float64 else TAU32,
+                      1e-10 if dtype == torch.float64 else 1e-3)
 
 
 @pytest.mark.parametrize("name", ["last_row", "in_panel", "mixed", "reverse"])

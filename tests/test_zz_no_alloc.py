@@ -4,8 +4,14 @@ allowed).  Its scratch is a static device array inside the library instead of
 a handle's workspace.  The test calls it through the C ABI twice in a row (the
 array keeps the previous call's contents, so the second call checks that
 everything that must start at zero is cleared) and compares each result with
-the allocating entry point lu_panel_factor_ex on the same panel, with the
-tolerance the panel parity tests use.  This file is collected last.
+the allocating entry point lu_panel_factor_ex on the same panel: the two run
+the same kernels with the same options, so pivots and factors must be
+bit-identical.  Each result is also checked against the CPU oracle directly
+(pivots at separated steps, factors entry by entry).  The cases cover both
+leaf kinds: panels that fit one thread-block cluster, and panels too tall for
+one (40000 FP64 rows), which take the grid-barrier leaf and the in-panel
+interchange plan, the two largest regions of the static array.  This file is
+collected last.
 """
 import ctypes
 
@@ -13,6 +19,7 @@ import numpy as np
 import pytest
 import torch
 
+import oracle
 import synth
 
 pytestmark = pytest.mark.gpu
@@ -34,9 +41,11 @@ def dev(a, dtype):
     return t
 
 
-@pytest.mark.parametrize("dtype,m,w,tol", [(torch.float64, 3000, 128, 1e-12), (torch.float32, 5000, 256, 2e-4),
-                                           (torch.float64, 700, 37, 1e-12)])
-def test_noalloc_matches_allocating_entry_point(lu, dtype, m, w, tol):
+@pytest.mark.parametrize("dtype,m,w,tau,tol", [(torch.float64, 3000, 128, 1e-8, 1e-12),
+                                               (torch.float32, 5000, 256, 1e-3, 2e-4),
+                                               (torch.float64, 700, 37, 1e-8, 1e-12),
+                                               (torch.float64, 40000, 64, 1e-8, 1e-12)])
+def test_noalloc_matches_allocating_entry_point(lu, dtype, m, w, tau, tol):
     for call in range(2):
         P0 = synth.uniform_matrix(m, w, seed=61, stream=100 * call + w)
         if dtype == torch.float32:
@@ -51,10 +60,20 @@ def test_noalloc_matches_allocating_entry_point(lu, dtype, m, w, tol):
         lu.lu_panel_factor_noalloc(got, piv, info)
         torch.cuda.synchronize()
         assert int(info.item()) == 0 and int(info_ref.item()) == 0
-        assert np.array_equal(piv.cpu().numpy(), piv_ref.cpu().numpy())
+        p = piv.cpu().numpy()
+        assert np.array_equal(p, piv_ref.cpu().numpy())
         a = got.cpu().double().numpy()
-        b = ref.cpu().double().numpy()
-        assert np.abs(a - b).max() <= tol * max(1.0, np.abs(b).max())
+        assert np.array_equal(a, ref.cpu().double().numpy())
+        # and directly against the oracle (RL1 of Sec. 3, LU_unb)
+        LU_o, p_o, info_o, gap = oracle.getrf(P0)
+        assert info_o == 0
+        sep = gap > tau
+        assert np.array_equal(p[sep], p_o[sep])
+        diff = np.nonzero(p != p_o)[0]
+        d = int(diff[0]) if diff.size else w
+        assert np.abs(a[:d] - LU_o[:d]).max(initial=0.0) <= tol * np.abs(LU_o).max()
+        if d == w:
+            assert np.abs(a - LU_o).max() <= tol * np.abs(LU_o).max()
 
 
 def test_noalloc_zero_pivot_and_limits(lu):
