@@ -18,6 +18,7 @@ timed region; "cpu_baseline" the CPU oracle on a bounded sample.
 from __future__ import annotations
 
 import argparse
+import ctypes
 import json
 import os
 import statistics
@@ -25,6 +26,8 @@ import subprocess
 import sys
 import tempfile
 import time
+
+import numpy as np
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
@@ -201,11 +204,25 @@ def main_with_args(argv):
     ap.add_argument("--prec", default="bf16x6", choices=["bf16x6", "bf16x3", "bf16", "fp16", "f32"])
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison path")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle sample")
-    ap.add_argument("--workload", default="mixed", choices=["mixed", "batched", "configs", "tune", "chol"],
+    ap.add_argument("--workload", default="mixed",
+                    choices=["mixed", "batched", "configs", "tune", "chol", "profile"],
                     help="mixed: the n=16384 solver (default); batched: 4096 uneven systems; "
                          "configs: the configuration comparisons; tune: the block-size sweeps; "
-                         "chol: the Cholesky factorization")
+                         "chol: the Cholesky factorization; profile: one kernel case (--case) for "
+                         "profilers and event timing")
+    ap.add_argument("--case", default="leaf", choices=sorted(PROFILE_CASES),
+                    help="profile case: " + "; ".join(f"{k}: {v[1]}" for k, v in sorted(PROFILE_CASES.items())))
+    ap.add_argument("--shape", default="", help="profile case sizes, comma-separated (see --case)")
+    ap.add_argument("--dtype", default="f32", choices=["f32", "f64"], help="profile case storage type")
+    ap.add_argument("--reps", type=int, default=3, help="profile case repetitions (the median is reported)")
+    ap.add_argument("--summarize-launches", metavar="CSV", default=None,
+                    help="print per-kernel launches, total time and share from an ncu CSV launch list "
+                         "(--metrics gpu__time_duration.sum --csv) and exit; needs no GPU")
     args = ap.parse_args(argv)
+    if args.summarize_launches:
+        return summarize_launches(args.summarize_launches)
+    if args.workload == "profile":
+        return run_profile(args)
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "configs":
@@ -336,8 +353,8 @@ def main_with_args(argv):
         # latency view: the leaves' time per eliminated column (every column passes one leaf)
         roof["latency"] = {"us_per_column": d["ms"] * PROF_STRIDE / args.steps / n * 1e3,
                            "columns_per_step": n,
-                           "note": "pipelined, beside the tensor-core update; 2.8 us alone at m = 16384 "
-                                   "(profiles/pf_leaf_push_kernel_m16384_w16.md)"}
+                           "note": "pipelined, beside the tensor-core update; a leaf timed alone "
+                                   "(--workload profile --case leaf) takes 2.8 us per column at m = 16384"}
     roof["sampled"] = (f"1 launch in {PROF_STRIDE} of the class carries events, over {args.steps} timed steps "
                        f"of the same workload run after the value's timed region ({roof_ms_step:.1f} ms per step "
                        f"there: launches that carry events are not replayed as a graph)")
@@ -398,6 +415,241 @@ def main_with_args(argv):
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# Single-kernel cases (--workload profile): one launch of one step of the path
+# on seeded synthetic inputs, for ncu captures and event timing.  Each prints
+# one JSON line: the case, its sizes, the median event-timed duration over
+# --reps runs, and the algorithmic bytes and flops of one launch with the
+# achieved rates.
+
+def _shape(args, defaults):
+    vals = [int(v) for v in args.shape.split(",") if v.strip()] if args.shape else []
+    return vals + list(defaults[len(vals):])
+
+
+def _median_ms(fn, reps, before=None):
+    import torch
+    out = []
+    stream = torch.cuda.current_stream()
+    for _ in range(max(1, reps)):
+        if before is not None:
+            before()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        out.append(e0.elapsed_time(e1))
+    return statistics.median(out)
+
+
+def _prof_line(case, sizes, ms, nbytes, flops, **extra):
+    line = {"workload": "profile", "case": case, "sizes": sizes, "ms": ms,
+            "bytes": nbytes, "flops": flops,
+            "GB/s": nbytes / (ms * 1e-3) / 1e9 if ms > 0 else None,
+            "GFLOP/s": flops / (ms * 1e-3) / 1e9 if ms > 0 else None}
+    line.update(extra)
+    print(json.dumps(line), flush=True)
+
+
+def prof_leaf(args, lu, torch, dt):
+    """panel factorization of an m x w N(0,1) panel (w <= 32: one cluster-leaf launch)"""
+    import synth
+    m, w = _shape(args, (16384, 16))
+    P0 = torch.from_numpy(synth.normal_matrix(m, w, seed=3)).to(dt)
+    P = lu.colmajor(m, w, dtype=dt)
+    ipiv = torch.zeros(w, dtype=torch.int32, device="cuda")
+    info = torch.zeros(1, dtype=torch.int32, device="cuda")
+    ms = _median_ms(lambda: lu.lu_panel_factor_ex(P, ipiv, info, lu.default_opts(leaf=w)), args.reps,
+                    before=lambda: P.copy_(P0))
+    es = P.element_size()
+    _prof_line("leaf", {"m": m, "w": w}, ms, 2.0 * m * w * es, float(m) * w * w,
+               us_per_column=ms * 1e3 / w, info=int(info.item()))
+
+
+def prof_tc(args, lu, torch, dt):
+    """tensor-core trailing update C := C - A B, FP32 C (m x n), k = nb; --shape m,n,k,prec"""
+    import synth
+    m, n, k, prec = _shape(args, (8192, 8192, 256, 6))
+    g = synth.rng(5, 0)
+    C0 = torch.from_numpy(g.standard_normal((m, n))).float()
+    A = lu.colmajor(m, k, dtype=torch.float32)
+    B = lu.colmajor(k, n, dtype=torch.float32)
+    A.copy_(torch.from_numpy(g.standard_normal((m, k))).float())
+    B.copy_(torch.from_numpy(g.standard_normal((k, n))).float())
+    C = lu.colmajor(m, n, dtype=torch.float32)
+    info = torch.zeros(1, dtype=torch.int32, device="cuda")
+    ms = _median_ms(lambda: lu.lu_gemm_update_tc_ex(C, A, B, prec, info), args.reps, before=lambda: C.copy_(C0))
+    parts = {6: 6, 3: 3}.get(prec, 1)
+    _prof_line("tc", {"m": m, "n": n, "k": k, "prec": prec}, ms, 8.0 * m * n + 4.0 * k * (m + n),
+               2.0 * m * n * k, products=parts, info=int(info.item()))
+
+
+def prof_trsm(args, lu, torch, dt):
+    """RL2 A12 := L11^-1 A12 with unit-lower L11 (m x m) and A12 (m x n)"""
+    import synth
+    m, n = _shape(args, (256, 16128))
+    g = synth.rng(12, m)
+    L0 = np.tril(g.uniform(-1, 1, size=(m, m)), -1) + np.eye(m)
+    Lt = lu.colmajor(m, m, dtype=dt)
+    Lt.copy_(torch.from_numpy(L0).to(dt))
+    B0 = torch.from_numpy(g.uniform(-1, 1, size=(m, n))).to(dt)
+    B = lu.colmajor(m, n, dtype=dt)
+    ms = _median_ms(lambda: lu.lu_trsm_ex(Lt, B), args.reps, before=lambda: B.copy_(B0))
+    es = B.element_size()
+    _prof_line("trsm", {"m": m, "n": n}, ms, es * (2.0 * m * n + 0.5 * m * m), float(m) * m * n)
+
+
+def prof_laswp(args, lu, torch, dt):
+    """the interchanges of one nb-step applied to the other columns: rows
+    [k1, k1 + K) of an n x ncols matrix, targets drawn from [j, n)"""
+    import synth
+    n, ncols, K = _shape(args, (16384, 16128, 256))
+    g = synth.rng(11, 0)
+    ipiv = np.arange(1, n + 1, dtype=np.int32)
+    for j in range(K):
+        ipiv[j] = int(g.integers(j, n)) + 1
+    A = lu.colmajor(n, ncols, dtype=dt)
+    A.copy_(torch.from_numpy(g.uniform(-1, 1, size=(n, ncols))).to(dt))
+    piv = torch.from_numpy(ipiv).cuda()
+    moved = len({int(p) - 1 for p in ipiv[:K]} | set(range(K)))
+    ms = _median_ms(lambda: lu.lu_laswp_ex(A, 0, K, piv), args.reps)
+    es = A.element_size()
+    _prof_line("laswp", {"n": n, "ncols": ncols, "K": K}, ms, 2.0 * moved * ncols * es, 0.0,
+               rows_moved=moved, bytes_rule="each moved row read once and written once per column")
+
+
+def prof_gemm(args, lu, torch, dt):
+    """RL3 on the CUDA cores, C := C - A B (m x n, inner k)"""
+    import synth
+    m, n, k = _shape(args, (8192, 8192, 256))
+    g = synth.rng(13, 0)
+    C0 = torch.from_numpy(g.uniform(-1, 1, size=(m, n))).to(dt)
+    A = lu.colmajor(m, k, dtype=dt)
+    B = lu.colmajor(k, n, dtype=dt)
+    A.copy_(torch.from_numpy(g.uniform(-1, 1, size=(m, k))).to(dt))
+    B.copy_(torch.from_numpy(g.uniform(-1, 1, size=(k, n))).to(dt))
+    C = lu.colmajor(m, n, dtype=dt)
+    ms = _median_ms(lambda: lu.lu_gemm_update_ex(C, A, B), args.reps, before=lambda: C.copy_(C0))
+    es = C.element_size()
+    _prof_line("gemm", {"m": m, "n": n, "k": k}, ms, es * (2.0 * m * n + (m + n) * k), 2.0 * m * n * k)
+
+
+def prof_trsv(args, lu, torch, dt):
+    """solve with the factors of an FP32 mixed factorization of order n (N(0,1))"""
+    import synth
+    (n,) = _shape(args, (16384,))
+    A = lu.colmajor(n, n, dtype=torch.float32)
+    A.copy_(torch.from_numpy(synth.normal_matrix(n, seed=0)).float())
+    ipiv = torch.zeros(n, dtype=torch.int32, device="cuda")
+    info = torch.zeros(1, dtype=torch.int32, device="cuda")
+    lu.lu_factor_mixed_ex(A, ipiv, info, 6, lu.default_opts(nb=256))
+    torch.cuda.synchronize()
+    B0 = torch.ones((n, 1), dtype=torch.float32)
+    B = lu.colmajor(n, 1, dtype=torch.float32)
+    ms = _median_ms(lambda: lu.lu_solve_ex(A, ipiv, B), args.reps, before=lambda: B.copy_(B0))
+    _prof_line("trsv", {"n": n}, ms, 4.0 * n * n, 2.0 * n * n, info=int(info.item()))
+
+
+def prof_batched(args, lu, torch, dt):
+    """persistent batched factor + solve of count systems (n_i log-uniform in [16, 512], nrhs_i in 1..8)"""
+    import synth
+    (count,) = _shape(args, (4096,))
+    sizes, nrhs = synth.batched_sizes(count, seed=0)
+    mats = synth.batched_matrices(sizes, seed=0)
+    g = synth.rng(0, 9)
+    A0 = [torch.from_numpy(m).to(dt) for m in mats]
+    B0 = [torch.from_numpy(g.uniform(-1, 1, size=(int(n), int(r)))).to(dt) for n, r in zip(sizes, nrhs)]
+    dA = [lu.colmajor(x.shape[0], x.shape[1], dtype=dt) for x in A0]
+    dB = [lu.colmajor(x.shape[0], x.shape[1], dtype=dt) for x in B0]
+    piv = [torch.zeros(int(n), dtype=torch.int32, device="cuda") for n in sizes]
+    batch = lu.Batch(dA, piv, dB)
+
+    def restore():
+        for d, x in zip(dA + dB, A0 + B0):
+            d.copy_(x)
+
+    ms = _median_ms(lambda: lu.lu_gesv_batched(batch), args.reps, before=restore)
+    fl = float(sum(2.0 * int(n) ** 3 / 3 + 2.0 * int(n) ** 2 * int(r) for n, r in zip(sizes, nrhs)))
+    es = dA[0].element_size()
+    nb_ = float(sum(es * (2.0 * int(n) ** 2 + 2.0 * int(n) * int(r)) for n, r in zip(sizes, nrhs)))
+    _prof_line("batched", {"count": count}, ms, nb_, fl, all_info_zero=bool((batch.info == 0).all().item()))
+
+
+def prof_peak(args, lu, torch, dt):
+    """CUDA-core FMA throughput (lu_peak_fma): blocks = SMs x 8 of 256 threads, 8 chains each"""
+    L = lu.lib()
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    res = {}
+    for name, code, tdt, iters in (("f64", 0, torch.float64, 20000), ("f32", 1, torch.float32, 400000)):
+        blocks, threads = sms * 8, 256
+        sink = torch.empty(blocks * threads, dtype=tdt, device="cuda")
+        stream = torch.cuda.current_stream()
+
+        def run():
+            rc = L.lu_peak_fma(code, blocks, threads, iters, ctypes.c_void_p(sink.data_ptr()),
+                               ctypes.c_void_p(stream.cuda_stream))
+            if rc != 0:
+                raise RuntimeError(f"lu_peak_fma returned {rc}")
+
+        run()
+        with ClockSampler(torch.cuda.current_device()) as clk:
+            ms = _median_ms(run, max(args.reps, 5))
+        flops = 2.0 * L.lu_peak_fma_chains() * iters * blocks * threads
+        res[name] = {"GFLOP/s": flops / (ms * 1e-3) / 1e9, "ms": ms, "clocks": clk.summary()}
+    line = {"workload": "profile", "case": "peak", "fma_peak": res,
+            "how": "lu_peak_fma: SMs x 8 CTAs of 256 threads, 8 independent FMA chains per thread, "
+                   "median of CUDA-event-timed launches; no clock setting changed"}
+    print(json.dumps(line), flush=True)
+
+
+PROFILE_CASES = {
+    "leaf": (prof_leaf, "panel leaf, --shape m,w (16384,16)"),
+    "tc": (prof_tc, "tensor-core update, --shape m,n,k,prec (8192,8192,256,6)"),
+    "trsm": (prof_trsm, "RL2 solve, --shape m,n (256,16128)"),
+    "laswp": (prof_laswp, "row interchanges, --shape n,ncols,K (16384,16128,256)"),
+    "gemm": (prof_gemm, "RL3 on CUDA cores, --shape m,n,k (8192,8192,256)"),
+    "trsv": (prof_trsv, "triangular solves of an FP32 factorization, --shape n (16384)"),
+    "batched": (prof_batched, "batched factor + solve, --shape count (4096)"),
+    "peak": (prof_peak, "CUDA-core FMA throughput, FP64 and FP32"),
+}
+
+
+def summarize_launches(path):
+    """Per-kernel launches, device time and share of an ncu launch list."""
+    import collections
+    import csv
+    import re
+    with open(path) as f:
+        rows = [ln for ln in f if not ln.startswith("==")]
+    unit_ms = {"ns": 1e-6, "nsecond": 1e-6, "us": 1e-3, "usecond": 1e-3, "ms": 1.0, "msecond": 1.0}
+    agg = collections.defaultdict(lambda: [0, 0.0])
+    for r in csv.DictReader(rows):
+        if r.get("Metric Name") != "gpu__time_duration.sum":
+            continue
+        name = re.sub(r"^void\s+", "", re.sub(r"\(.*$", "", r["Kernel Name"]).replace("<unnamed>::", "")).strip()
+        agg[name][0] += 1
+        agg[name][1] += float(r["Metric Value"].replace(",", "")) * unit_ms.get(r["Metric Unit"], 1e-6)
+    total = sum(v[1] for v in agg.values())
+    print("| kernel | launches | total ms | share |\n|---|---:|---:|---:|")
+    for name, (cnt, ms) in sorted(agg.items(), key=lambda kv: -kv[1][1]):
+        print(f"| {name} | {cnt} | {ms:.3f} | {100 * ms / total if total else 0:.1f}% |")
+    print(f"| total | {sum(v[0] for v in agg.values())} | {total:.3f} | |")
+    return 0
+
+
+def run_profile(args):
+    import torch
+
+    import paper_1804_07017_gb300 as lu
+    if not torch.cuda.is_available():
+        raise SystemExit("a CUDA device is required")
+    dt = torch.float64 if args.dtype == "f64" else torch.float32
+    PROFILE_CASES[args.case][0](args, lu, torch, dt)
     return 0
 
 

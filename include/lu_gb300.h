@@ -252,6 +252,21 @@ int lu_panel_factor_noalloc(lu_dtype dtype, int64_t m, int64_t w, void *A, int64
 size_t lu_noalloc_scratch_bytes(void);
 
 /*
+ * lu_peak_fma -- measurement utility, not a step of the method (the paper
+ * measures on a multicore CPU and names no GPU peak): launches `blocks` CTAs of
+ * `threads` threads (32..256, a multiple of 32), each thread running
+ * lu_peak_fma_chains() independent fused multiply-add chains for `iters`
+ * iterations in FP64 (dtype LU_F64) or FP32 (LU_F32), and writes one value per
+ * thread to `sink` (device buffer of blocks * threads elements of that type,
+ * caller-owned).  The work is 2 * chains * iters * blocks * threads flops; the
+ * caller times the launch with CUDA events on `stream` and so obtains the
+ * CUDA cores' FMA throughput, the denominator of the kernels that run there.
+ * Asynchronous.  Returns -i for an invalid argument, LU_ERR_CUDA, or 0.
+ */
+int lu_peak_fma(lu_dtype dtype, int blocks, int threads, int64_t iters, void *sink, void *stream);
+int lu_peak_fma_chains(void);
+
+/*
  * lu_selftest_wait_timeout -- diagnostic of the failure path shared by every
  * kernel that synchronises CTAs through global memory: launches a grid barrier
  * that can never complete, whose bounded wait gives up after limit_ns

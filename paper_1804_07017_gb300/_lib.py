@@ -69,6 +69,8 @@ _SIGNATURES = {
     "lu_panel_factor_noalloc": (i32, [i32, i64, i64, vp, i64, vp, ctypes.POINTER(LuOpts), vp, vp]),
     "lu_noalloc_scratch_bytes": (ctypes.c_size_t, []),
     "lu_selftest_wait_timeout": (i32, [vp, i64, vp]),
+    "lu_peak_fma": (i32, [i32, i32, i32, i64, vp, vp]),
+    "lu_peak_fma_chains": (i32, []),
     "lu_profile_enable": (i32, [i32]),
     "lu_profile_stride": (i32, [i32]),
     "lu_profile_reset": (i32, []),
