@@ -78,15 +78,33 @@ typedef struct {
     int lookahead; /* 0: no look-ahead, the PF(k); TU(k) loop of Listing 3.
                       1: depth-1 static look-ahead of Listing 5: PU(k+1) (the
                          left part of TU_k plus PF_{k+1}) runs concurrently with
-                         TU_right(k) */
+                         TU_right(k).
+                      2: depth 2 (Sec. 4 notes that deeper look-ahead follows
+                         the same pattern): the high-priority stream also applies
+                         TU_k to panel k+2, so PF_{k+1} waits only for TU_k on its
+                         own columns and never for TU_right(k-1); the right update
+                         starts after panel k+2 */
     int steal;     /* 1: the CTAs freed by PU(k+1) join TU_right(k) (the GPU
                       analogue of the malleable BLAS of Sec. 4.2); 0: they do not */
     int leaf;      /* column width handled by one panel-factorization leaf
                       kernel inside the recursive panel (0 = automatic) */
     int pf_ctas;   /* maximum CTAs of a panel-factorization leaf (0 = automatic) */
+    int tu_reserve; /* with look-ahead: SMs the right trailing update leaves to the
+                      panel path (and that rejoin it as stealing CTAs once the
+                      panel is done); 0 = automatic (the tuned value, else a
+                      sixth of the SMs) */
+    int nsched;    /* > 0: per-step block sizes (the GPU form of the paper's
+                      early termination, Sec. 4.2: b adjusted from step to step);
+                      step k eliminates sched[k] columns, the last entry repeats,
+                      the final step takes what remains; 0 = the fixed nb */
+    const int32_t *sched; /* host array of nsched block sizes, each 1..1024 (the
+                      tensor-core update needs multiples of 64, FP8 of 128; other
+                      widths run that step's update on the CUDA cores); read
+                      during the call only */
 } lu_opts;
 
-/* Fills *opts with the defaults (nb = 256, lookahead = 1, steal = 1, automatic rest). */
+/* Fills *opts with the defaults (nb = 256, lookahead = 1, steal = 1, automatic
+ * rest, no schedule). */
 void lu_default_opts(lu_opts *opts);
 
 /* Handle lifetime.  lu_create returns 0 or LU_ERR_CUDA/LU_ERR_NOMEM. */
@@ -431,18 +449,79 @@ int lu_tune_nb(lu_handle h, int kind, int64_t n, const int *candidates, int coun
  * device: host string, or NULL for the current CUDA device's name. */
 int lu_tune_get(const char *device, int kind, int64_t n);
 /* Stores nb (and its time in ms, informative) for (device, kind, ceil(log2 n)),
- * replacing an entry with the same key.  Returns 0, -1 (device NULL without a
+ * replacing an entry with the same key (and any plan it held).  Returns 0, -1 (device NULL without a
  * CUDA device, empty, or holding a tab or newline), -2 (kind), -3 (n < 1), -4 (nb). */
 int lu_tune_set(const char *device, int kind, int64_t n, int nb, float ms);
 /* Empties the table.  Returns 0. */
 int lu_tune_clear(void);
 /* Writes the table to the host file `path` as text lines
- * "device<TAB>kind<TAB>ceil(log2 n)<TAB>nb<TAB>ms".  Returns 0, -1 (NULL path) or LU_ERR_IO. */
+ * "device<TAB>kind<TAB>ceil(log2 n)<TAB>nb<TAB>ms", followed for a tuned plan by
+ * "<TAB>reserve<TAB>depth<TAB>schedule" (comma-separated block sizes, "-" for
+ * none).  Returns 0, -1 (NULL path) or LU_ERR_IO. */
 int lu_tune_save(const char *path);
 /* Merges the lines of such a file into the table (an entry replaces one with the
  * same key).  Every line is validated first; on any malformed line nothing is
  * merged.  Returns 0, -1 (NULL path) or LU_ERR_IO (unreadable or malformed). */
 int lu_tune_load(const char *path);
+
+/*
+ * lu_tune_plan -- tune the whole schedule of the factorization of `kind` at
+ * order n on a seeded synthetic matrix (iid U[-1,1)), in four measured stages:
+ *   1. the block size b among 128, 192, 256, 320, 384, 512 (multiples of 64,
+ *      of 128 for LU_TU_FP8, on the tensor-core kinds);
+ *   2. with look-ahead, the SMs the right update leaves to the panel path
+ *      (lu_opts.tu_reserve) among 1/12, 1/6, 1/4 and 1/3 of the SMs;
+ *   3. with look-ahead, the depth 1 or 2;
+ *   4. a per-step schedule, the GPU form of the paper's early termination
+ *      (Sec. 4.2: b adjusted on the fly when PU(k+1) and TU_right(k) are out of
+ *      balance): the steps of the factorization at b/2, b and 2b are traced
+ *      (lu_step_trace), and walking the columns, each step takes the width whose
+ *      traced step at that position added the least critical-path time per
+ *      eliminated column; the schedule is kept only if it beats the fixed plan.
+ *   h         handle; its stream orders the runs, and the call synchronises it
+ *   reps      >= 1 runs per candidate, the least time counts (use 3: a repeated
+ *             mixed factorization is captured on its second run, replayed after)
+ *   opts      look-ahead on/off, stealing, leaf and pf_ctas for every run (NULL =
+ *             defaults); its nb, tu_reserve and schedule are ignored
+ *   best      host (out): the chosen options; best->sched points into `sched`
+ *   sched     host int32[cap] (out) for the schedule; a schedule longer than cap
+ *             is not chosen
+ *   best_ms   host float or NULL (out): the chosen plan's least time (ms)
+ *   fixed_ms  host float or NULL (out): the best plan without a schedule (ms)
+ * The plan is also stored in the table for (device, kind, ceil(log2 n)), where
+ * calls with nb = 0 find it.  The scratch matrix is allocated and freed inside.
+ * Returns 0, -i for an invalid argument, LU_ERR_NOMEM, LU_ERR_UNSUPPORTED (no
+ * candidate ran) or a runtime error of the factorization.
+ */
+int lu_tune_plan(lu_handle h, int kind, int64_t n, int reps, const lu_opts *opts, lu_opts *best, int32_t *sched,
+                 int cap, float *best_ms, float *fixed_ms);
+/* Stores a plan for (device, kind, ceil(log2 n)): nb, reserve (0 = automatic),
+ * depth (0 = the caller's), a schedule of nsched block sizes (host array, may
+ * be NULL when nsched is 0) and its time.  Returns 0 or -i for the i-th
+ * argument (-7: a width outside 1..1024, or not a multiple of 128 for FP8). */
+int lu_tune_plan_set(const char *device, int kind, int64_t n, int nb, int reserve, int depth, const int32_t *sched,
+                     int nsched, float ms);
+/* Reads the plan for (device, kind, ceil(log2 n)) into the non-NULL outputs
+ * (at most cap schedule entries; *nsched receives the full length).  Returns 1
+ * when an entry exists, else 0. */
+int lu_tune_plan_get(const char *device, int kind, int64_t n, int *nb, int *reserve, int *depth, int32_t *sched,
+                     int cap, int *nsched);
+
+/*
+ * lu_step_trace -- diagnostic of the look-ahead schedule (Sec. 4): with enable
+ * != 0, later factorizations on this handle record CUDA events around every
+ * step: on the panel stream from the start of PU(k+1) (TU_k on the next panel
+ * and PF_{k+1}) to its end, and on the update stream around TU_right(k).  A
+ * traced mixed factorization is not replayed as a graph.  Returns 0.
+ * lu_step_trace_read synchronises with the last traced factorization and fills,
+ * for its first min(cap, steps) steps, the panel's first column k0, its width
+ * kb, span_ms (the time from the step's start to the later of PU(k+1)'s and
+ * TU_right(k)'s ends: what the step adds to the critical path), pu_ms and
+ * tu_ms (any output may be NULL).  Returns the number of steps, or < 0.
+ */
+int lu_step_trace(lu_handle h, int enable);
+int64_t lu_step_trace_read(lu_handle h, int cap, int64_t *k0, int32_t *kb, float *span_ms, float *pu_ms,
+                           float *tu_ms);
 
 #ifdef __cplusplus
 }

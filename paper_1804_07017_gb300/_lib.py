@@ -42,7 +42,23 @@ class LuError(RuntimeError):
 
 class LuOpts(ctypes.Structure):
     _fields_ = [("nb", ctypes.c_int), ("lookahead", ctypes.c_int), ("steal", ctypes.c_int),
-                ("leaf", ctypes.c_int), ("pf_ctas", ctypes.c_int)]
+                ("leaf", ctypes.c_int), ("pf_ctas", ctypes.c_int), ("tu_reserve", ctypes.c_int),
+                ("nsched", ctypes.c_int), ("sched", ctypes.POINTER(ctypes.c_int32))]
+
+    def set_schedule(self, widths):
+        """Per-step block sizes (kept alive with the options); None or [] clears."""
+        if not widths:
+            self._sched_buf = None
+            self.nsched = 0
+            self.sched = None
+            return self
+        self._sched_buf = (ctypes.c_int32 * len(widths))(*[int(w) for w in widths])
+        self.nsched = len(widths)
+        self.sched = ctypes.cast(self._sched_buf, ctypes.POINTER(ctypes.c_int32))
+        return self
+
+    def schedule(self):
+        return [int(self.sched[i]) for i in range(self.nsched)] if self.nsched > 0 else []
 
 
 def library_path() -> str:
@@ -90,6 +106,17 @@ _SIGNATURES = {
     "lu_tune_clear": (i32, []),
     "lu_tune_save": (i32, [ctypes.c_char_p]),
     "lu_tune_load": (i32, [ctypes.c_char_p]),
+    "lu_tune_plan": (i32, [vp, i32, i64, i32, ctypes.POINTER(LuOpts), ctypes.POINTER(LuOpts),
+                           ctypes.POINTER(ctypes.c_int32), i32, ctypes.POINTER(ctypes.c_float),
+                           ctypes.POINTER(ctypes.c_float)]),
+    "lu_tune_plan_set": (i32, [ctypes.c_char_p, i32, i64, i32, i32, i32, ctypes.POINTER(ctypes.c_int32), i32,
+                               ctypes.c_float]),
+    "lu_tune_plan_get": (i32, [ctypes.c_char_p, i32, i64, ctypes.POINTER(i32), ctypes.POINTER(i32),
+                               ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_int32), i32, ctypes.POINTER(i32)]),
+    "lu_step_trace": (i32, [vp, i32]),
+    "lu_step_trace_read": (i64, [vp, i32, ctypes.POINTER(i64), ctypes.POINTER(ctypes.c_int32),
+                                 ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float),
+                                 ctypes.POINTER(ctypes.c_float)]),
 }
 
 _lib = None

@@ -51,7 +51,10 @@ def default_opts(**kw) -> LuOpts:
     o = LuOpts()
     lib().lu_default_opts(ctypes.byref(o))
     for k, v in kw.items():
-        setattr(o, k, int(v))
+        if k == "sched":
+            o.set_schedule(v)
+        else:
+            setattr(o, k, int(v))
     return o
 
 
@@ -295,3 +298,56 @@ def lu_tune_save(path: str) -> None:
 
 def lu_tune_load(path: str) -> None:
     _check("lu_tune_load", lib().lu_tune_load(path.encode()))
+
+
+def lu_tune_plan(kind: int, n: int, reps: int = 3, opts: LuOpts | None = None, handle: Handle | None = None,
+                 cap: int = 4096):
+    """Tunes the whole plan of the factorization of `kind` at order n (block size,
+    the right update's SM reserve, look-ahead depth, a per-step schedule) and
+    stores it in the table.  Returns (best opts, schedule list (empty: fixed nb),
+    best ms, best ms without a schedule)."""
+    h = _handle(handle)
+    o = opts if opts is not None else default_opts()
+    best = LuOpts()
+    buf = (ctypes.c_int32 * cap)()
+    bms, fms = ctypes.c_float(0), ctypes.c_float(0)
+    _check("lu_tune_plan", lib().lu_tune_plan(h.ptr, int(kind), int(n), int(reps), ctypes.byref(o),
+                                              ctypes.byref(best), buf, cap, ctypes.byref(bms), ctypes.byref(fms)))
+    sched = [int(buf[i]) for i in range(best.nsched)]
+    best.set_schedule(sched)
+    return best, sched, float(bms.value), float(fms.value)
+
+
+def lu_tune_plan_get(kind: int, n: int, device: str | None = None):
+    """(nb, reserve, depth, schedule) stored for (device, kind, ceil(log2 n)), or None."""
+    nb, res, dep, cnt = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    L = lib()
+    if not L.lu_tune_plan_get(_dev(device), int(kind), int(n), ctypes.byref(nb), ctypes.byref(res),
+                              ctypes.byref(dep), None, 0, ctypes.byref(cnt)):
+        return None
+    buf = (ctypes.c_int32 * max(cnt.value, 1))()
+    L.lu_tune_plan_get(_dev(device), int(kind), int(n), None, None, None, buf, cnt.value, None)
+    return nb.value, res.value, dep.value, [int(buf[i]) for i in range(cnt.value)]
+
+
+def lu_step_trace(enable: bool, handle: Handle | None = None) -> Handle:
+    """Turns the per-step trace of later factorizations on this handle on or off."""
+    h = _handle(handle)
+    _check("lu_step_trace", lib().lu_step_trace(h.ptr, 1 if enable else 0))
+    return h
+
+
+def lu_step_trace_read(handle: Handle | None = None):
+    """Per-step records of the last traced factorization: a list of dicts with
+    k0, kb, span_ms, pu_ms and tu_ms."""
+    h = _handle(handle)
+    L = lib()
+    cnt = int(L.lu_step_trace_read(h.ptr, 0, None, None, None, None, None))
+    if cnt < 0:
+        raise LuError("lu_step_trace_read", cnt)
+    k0 = (ctypes.c_int64 * max(cnt, 1))()
+    kb = (ctypes.c_int32 * max(cnt, 1))()
+    sp, pu, tu = ((ctypes.c_float * max(cnt, 1))() for _ in range(3))
+    L.lu_step_trace_read(h.ptr, cnt, k0, kb, sp, pu, tu)
+    return [{"k0": int(k0[i]), "kb": int(kb[i]), "span_ms": float(sp[i]), "pu_ms": float(pu[i]),
+             "tu_ms": float(tu[i])} for i in range(cnt)]

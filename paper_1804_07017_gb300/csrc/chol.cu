@@ -155,7 +155,7 @@ extern "C" int lu_potrf_ex(lu_handle h, lu_dtype dtype, int64_t n, void* A, int6
     if (lu_check_opts(o) != 0) return -6;
     if (!info) return -7;
     if (n > INT32_MAX / 2) return LU_ERR_UNSUPPORTED;
-    if (o.nb == 0) o.nb = lu_auto_nb(dtype == LU_F64 ? LU_TUNE_F64 : LU_TUNE_F32, n);
+    if (o.nb == 0 && o.nsched == 0) lu_auto_opts(dtype == LU_F64 ? LU_TUNE_F64 : LU_TUNE_F32, n, &o);
     std::lock_guard<std::mutex> lk(h->mu);
     if (dtype == LU_F64) return potrf_impl<double>(h, n, (double*)A, lda, o, info);
     return potrf_impl<float>(h, n, (float*)A, lda, o, info);

@@ -17,6 +17,12 @@
 // nb for a factorization called with nb = 0: the tuned value for (kind, n) on
 // the current device, else 256 (tune.cu).
 int lu_auto_nb(int kind, int64_t n);
+// Options of a factorization called with nb = 0 (and no schedule): the plan the
+// tuner stored for (kind, n) on the current device -- nb or a per-step schedule,
+// the right update's SM reserve (when o->tu_reserve is 0) and the look-ahead
+// depth (when look-ahead is on) -- else nb = 256.  A schedule points into
+// thread-local storage that stays valid until this thread's next call.
+void lu_auto_opts(int kind, int64_t n, lu_opts* o);
 #define LU_PF_SMEM_BUDGET (78 * 1024)
 #define LU_PF_MAX_CTAS_CLUSTER 16  // CTAs of a cluster panel leaf (non-portable cluster size)
 
@@ -27,7 +33,7 @@ struct lu_context {
     cudaStream_t hi = nullptr;    // high-priority internal stream (panel path)
     cudaStream_t lo = nullptr;    // low-priority internal stream (right trailing update)
     cudaEvent_t ev_fork = nullptr, ev_pf = nullptr, ev_tu = nullptr, ev_join_hi = nullptr,
-                ev_join_lo = nullptr, ev_steal = nullptr;
+                ev_join_lo = nullptr, ev_steal = nullptr, ev_tu2 = nullptr;
     // Workspace: one device buffer carved into fixed regions.
     char* ws = nullptr;
     size_t ws_bytes = 0;
@@ -54,6 +60,18 @@ struct lu_context {
     // Shared memory a panel leaf CTA may use: small enough, on the mixed path, to
     // sit beside a tensor-core trailing-update CTA on the same SM.
     size_t pf_smem_budget = 160 * 1024;
+    // SMs the right trailing update leaves to the panel path (set per factorization).
+    int tu_reserve = 0;
+    // Per-step trace of the look-ahead schedule (lu_step_trace): timing events
+    // around PU(k+1) on the panel stream and TU_right(k) on the update stream.
+    struct StepTrace {
+        cudaEvent_t pu0 = nullptr, pu1 = nullptr, tu0 = nullptr, tu1 = nullptr;
+        int64_t k0 = 0, kb = 0;
+        bool has_pu = false, has_tu = false;
+    };
+    bool trace_on = false;
+    std::vector<StepTrace> trace;
+    int64_t trace_steps = 0;
     // Replay of the mixed factorization as a CUDA graph: the arguments it was
     // captured for (fkey), the instantiated graph, its kernel count, and the key
     // of the previous eager run (a key is captured on its second use).
@@ -61,8 +79,8 @@ struct lu_context {
     cudaStream_t gs = nullptr;                    // capture/replay stream (non-blocking)
     cudaEvent_t ev_g0 = nullptr, ev_g1 = nullptr; // user -> gs and gs -> user
     long long fgraph_launches = 0;
-    uint64_t fkey[10] = {};
-    uint64_t fkey_seen[10] = {};
+    uint64_t fkey[12] = {};
+    uint64_t fkey_seen[12] = {};
     std::mutex mu;
 };
 
@@ -167,6 +185,11 @@ struct LuTuEngine {
 };
 
 int lu_check_opts(const lu_opts& o);
+// Column boundaries of the panels: panel k is [s[k], s[k+1]), from the schedule
+// (opts.sched) or the fixed nb; wmin/wmax receive the narrowest and widest width.
+void lu_panel_bounds(int64_t n, const lu_opts& o, std::vector<int64_t>* s, int* wmin, int* wmax);
+// SMs the right update leaves to the panel path (0 without look-ahead).
+int lu_resolve_reserve(const lu_context* c, const lu_opts& o);
 
 // pivot = false: elimination without interchanges (the Cholesky path, chol.cu):
 // panels by lu_panel_nopiv, no interchange plans or row exchanges, ipiv unused.

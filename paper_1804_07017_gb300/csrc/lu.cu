@@ -51,6 +51,40 @@ int lu_func_attrs(const void* fn, int smem_bytes, bool nonportable_cluster) {
     return LU_SUCCESS;
 }
 
+extern "C" int lu_step_trace(lu_handle h, int enable) {
+    if (!h) return LU_ERR_HANDLE;
+    std::lock_guard<std::mutex> lk(h->mu);
+    h->trace_on = enable != 0;
+    return LU_SUCCESS;
+}
+
+extern "C" int64_t lu_step_trace_read(lu_handle h, int cap, int64_t* k0, int32_t* kb, float* span_ms, float* pu_ms,
+                                      float* tu_ms) {
+    if (!h) return LU_ERR_HANDLE;
+    if (cap < 0) return -2;
+    std::lock_guard<std::mutex> lk(h->mu);
+    const int64_t cnt = std::min<int64_t>(h->trace_steps, (int64_t)h->trace.size());
+    for (int64_t i = 0; i < cnt && i < cap; ++i) {
+        const auto& t = h->trace[(size_t)i];
+        float pu = 0.f, tu = 0.f, tue = 0.f;
+        if (t.has_pu) {
+            LU_CHECK_CUDA(cudaEventSynchronize(t.pu1));
+            LU_CHECK_CUDA(cudaEventElapsedTime(&pu, t.pu0, t.pu1));
+        }
+        if (t.has_tu) {
+            LU_CHECK_CUDA(cudaEventSynchronize(t.tu1));
+            LU_CHECK_CUDA(cudaEventElapsedTime(&tu, t.tu0, t.tu1));
+            LU_CHECK_CUDA(cudaEventElapsedTime(&tue, t.pu0, t.tu1));
+        }
+        if (k0) k0[i] = t.k0;
+        if (kb) kb[i] = (int32_t)t.kb;
+        if (span_ms) span_ms[i] = std::max(pu, tue);
+        if (pu_ms) pu_ms[i] = pu;
+        if (tu_ms) tu_ms[i] = tu;
+    }
+    return cnt;
+}
+
 extern "C" int64_t lu_launch_count(void) { return (int64_t)g_launches.load(); }
 extern "C" const char* lu_last_error(void) { return g_last_error; }
 
@@ -61,6 +95,9 @@ extern "C" void lu_default_opts(lu_opts* o) {
     o->steal = 1;
     o->leaf = 0;
     o->pf_ctas = 0;
+    o->tu_reserve = 0;
+    o->nsched = 0;
+    o->sched = nullptr;
 }
 
 int lu_ctx_init(lu_context* c) {
@@ -70,7 +107,8 @@ int lu_ctx_init(lu_context* c) {
     LU_CHECK_CUDA(cudaDeviceGetStreamPriorityRange(&lo_prio, &hi_prio));
     LU_CHECK_CUDA(cudaStreamCreateWithPriority(&c->hi, cudaStreamNonBlocking, hi_prio));
     LU_CHECK_CUDA(cudaStreamCreateWithPriority(&c->lo, cudaStreamNonBlocking, lo_prio));
-    cudaEvent_t* evs[] = {&c->ev_fork, &c->ev_pf, &c->ev_tu, &c->ev_join_hi, &c->ev_join_lo, &c->ev_steal};
+    cudaEvent_t* evs[] = {&c->ev_fork, &c->ev_pf, &c->ev_tu, &c->ev_join_hi, &c->ev_join_lo, &c->ev_steal,
+                          &c->ev_tu2};
     for (cudaEvent_t* e : evs) LU_CHECK_CUDA(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
     return LU_SUCCESS;
 }
@@ -93,9 +131,15 @@ int lu_ctx_release(lu_context* c) {
     if (c->gs) cudaStreamDestroy(c->gs);
     c->ev_g0 = c->ev_g1 = nullptr;
     c->gs = nullptr;
-    cudaEvent_t evs[] = {c->ev_fork, c->ev_pf, c->ev_tu, c->ev_join_hi, c->ev_join_lo, c->ev_steal};
+    cudaEvent_t evs[] = {c->ev_fork, c->ev_pf, c->ev_tu, c->ev_join_hi, c->ev_join_lo, c->ev_steal, c->ev_tu2};
     for (cudaEvent_t e : evs)
         if (e) cudaEventDestroy(e);
+    for (auto& t : c->trace) {
+        cudaEvent_t te[] = {t.pu0, t.pu1, t.tu0, t.tu1};
+        for (cudaEvent_t e : te)
+            if (e) cudaEventDestroy(e);
+    }
+    c->trace.clear();
     if (c->hi) cudaStreamDestroy(c->hi);
     if (c->lo) cudaStreamDestroy(c->lo);
     return LU_SUCCESS;
@@ -191,9 +235,36 @@ static lu_handle default_handle() {
 // ---------------------------------------------------------------------------
 int lu_check_opts(const lu_opts& o) {
     if (o.nb < 0 || o.nb > LU_MAX_NB) return -1;  // 0: resolved by the factorization entry points
-    if (o.lookahead < 0 || o.lookahead > 1) return -1;
+    if (o.lookahead < 0 || o.lookahead > 2) return -1;
     if (o.leaf < 0 || o.pf_ctas < 0 || o.pf_ctas > LU_PF_MAX_CTAS) return -1;
+    if (o.tu_reserve < 0 || o.nsched < 0 || o.nsched > (1 << 20)) return -1;
+    if (o.nsched > 0) {
+        if (!o.sched) return -1;
+        for (int i = 0; i < o.nsched; ++i)
+            if (o.sched[i] < 1 || o.sched[i] > LU_MAX_NB) return -1;
+    }
     return 0;
+}
+
+void lu_panel_bounds(int64_t n, const lu_opts& o, std::vector<int64_t>* s, int* wmin, int* wmax) {
+    s->clear();
+    s->push_back(0);
+    int lo = LU_MAX_NB, hi = 1;
+    for (int64_t c = 0, k = 0; c < n; ++k) {
+        const int b = o.nsched > 0 ? o.sched[std::min<int64_t>(k, o.nsched - 1)] : o.nb;
+        lo = std::min(lo, b);
+        hi = std::max(hi, b);
+        c = std::min<int64_t>(n, c + b);
+        s->push_back(c);
+    }
+    if (wmin) *wmin = std::min(lo, hi);
+    if (wmax) *wmax = hi;
+}
+
+int lu_resolve_reserve(const lu_context* c, const lu_opts& o) {
+    if (!o.lookahead) return 0;
+    if (o.tu_reserve > 0) return std::min(o.tu_reserve, std::max(0, c->num_sms - 1));
+    return std::max(4, c->num_sms / 6);
 }
 
 // TU restricted to columns [c_begin, c_end) for step k (panel columns [k0, k0+kb)):
@@ -206,7 +277,7 @@ static int trailing_update(lu_context* c, cudaStream_t st, int64_t n, T* A, int6
     const int64_t ncols = c_end - c_begin;
     // the right update's interchanges and RL2 run on at most the right update's share
     // of the SMs (as its tensor-core part), leaving the rest to the panel path
-    const int cap = which == 1 ? std::max(1, c->num_sms - std::max(4, c->num_sms / 6)) : 0;
+    const int cap = which == 1 ? std::max(1, c->num_sms - c->tu_reserve) : 0;
     if (pivot && (ncols > 0 || left_cols > 0))
         LU_TRY(lu_launch_laswp_apply<T>(st, A, lda, c_begin, std::max<int64_t>(ncols, 0), 0, left_cols,
                                         plan, kb, c->num_sms, cap));
@@ -223,57 +294,105 @@ static int trailing_update(lu_context* c, cudaStream_t st, int64_t n, T* A, int6
                                     A + (k0 + kb) + c_begin * lda, lda);
 }
 
+// Timing events of one traced step (created on first use, kept by the handle).
+static int trace_slot(lu_context* c, int64_t k, lu_context::StepTrace** out) {
+    if ((int64_t)c->trace.size() <= k) c->trace.resize((size_t)k + 1);
+    lu_context::StepTrace& t = c->trace[(size_t)k];
+    cudaEvent_t* evs[] = {&t.pu0, &t.pu1, &t.tu0, &t.tu1};
+    for (cudaEvent_t* e : evs)
+        if (!*e) LU_CHECK_CUDA(cudaEventCreate(e));
+    *out = &t;
+    return LU_SUCCESS;
+}
+
 template <typename T>
 int lu_factor_blocked(lu_context* c, int64_t n, T* A, int64_t lda, int32_t* ipiv, const lu_opts& o, int32_t* info,
                       const LuTuEngine* eng, bool pivot) {
-    const int nb = o.nb;
-    if (nb < 1) return LU_ERR_UNSUPPORTED;  // nb = 0 is resolved before this point
-    LU_TRY(lu_ctx_reserve(c, n, nb));
+    if (o.nb < 1 && o.nsched < 1) return LU_ERR_UNSUPPORTED;  // nb = 0 is resolved before this point
+    std::vector<int64_t> s;
+    int wmin = 1, wmax = 1;
+    lu_panel_bounds(n, o, &s, &wmin, &wmax);
+    LU_TRY(lu_ctx_reserve(c, n, wmin));
     cudaStream_t user = c->user;
     LU_CHECK_CUDA(cudaMemsetAsync(&c->sync[0], 0, sizeof(LuSync), user));
+    c->trace_steps = 0;
     if (n == 0) return lu_launch_finish_info(user, &c->sync[0], info);
+    c->tu_reserve = lu_resolve_reserve(c, o);
     LU_CHECK_CUDA(cudaEventRecord(c->ev_fork, user));
     LU_CHECK_CUDA(cudaStreamWaitEvent(c->hi, c->ev_fork, 0));
     LU_CHECK_CUDA(cudaStreamWaitEvent(c->lo, c->ev_fork, 0));
-    const int64_t nk = lu_cdiv(n, nb);
+    const int64_t nk = (int64_t)s.size() - 1;
+    auto start = [&](int64_t j) { return s[(size_t)std::min(j, nk)]; };  // first column of panel j (n past the end)
     auto plan_of = [&](int64_t k) { return c->plans + (size_t)k * c->plan_stride; };
     cudaStream_t hi = c->hi, lo = c->lo;
+    const bool trace = c->trace_on;
     // PF(k) followed by its interchange plan (and, for the tensor-core engine, the packed L21)
     auto panel = [&](int64_t k) -> int {
-        const int64_t k0 = k * nb, kb = std::min<int64_t>(nb, n - k0);
+        const int64_t k0 = s[k], kb = s[k + 1] - s[k];
         if (!pivot) return lu_panel_nopiv<T>(hi, A, lda, n, k0, kb, &c->sync[0]);
         LU_TRY(lu_panel_recursive<T>(c, hi, A, lda, n, k0, kb, ipiv, o));
         LU_TRY(lu_launch_laswp_plan(hi, ipiv, k0, k0 + kb, plan_of(k)));
         if (eng && eng->uses_tc(kb) && k0 + kb < n) LU_TRY(eng->pack_panel(hi, (const float*)A, lda, k, k0, kb));
         return LU_SUCCESS;
     };
+    // TU_k restricted to columns [cb, ce), plus panel k's interchanges on `left` leading columns
+    auto tu = [&](cudaStream_t st, int64_t k, int64_t cb, int64_t ce, int64_t left, int which) -> int {
+        return trailing_update<T>(c, st, n, A, lda, k, s[k], s[k + 1] - s[k], cb, ce, left, plan_of(k), eng, which,
+                                  pivot);
+    };
     LU_TRY(panel(0));
+    const int depth = o.lookahead;
+    cudaEvent_t ev_tu[2] = {c->ev_tu, c->ev_tu2};  // TU_right of even / odd steps
     for (int64_t k = 0; k < nk; ++k) {
-        const int64_t k0 = k * nb, kb = std::min<int64_t>(nb, n - k0);
-        const int64_t c1 = k0 + kb;                       // first column right of panel k
-        const int64_t c2 = std::min<int64_t>(n, c1 + nb); // end of panel k+1
-        if (o.lookahead) {
-            // PU(k+1) = TU_k^L + PF_{k+1} on the high-priority stream.  TU_k^L (the
-            // next panel's interchanges, RL2 and RL3: a few narrow launches) runs
-            // before TU_right(k) is released, so that it does not wait behind the
-            // right update's thousands of CTAs; PF_{k+1} then overlaps TU_right(k).
-            if (k + 1 < nk)
-                LU_TRY(trailing_update<T>(c, hi, n, A, lda, k, k0, kb, c1, c2, 0, plan_of(k), eng, 0, pivot));
-            LU_CHECK_CUDA(cudaEventRecord(c->ev_pf, hi));
-            LU_CHECK_CUDA(cudaStreamWaitEvent(lo, c->ev_pf, 0));
-            // TU_right(k) and the deferred left interchanges on the low-priority stream
-            LU_TRY(trailing_update<T>(c, lo, n, A, lda, k, k0, kb, c2, n, k0, plan_of(k), eng, 1, pivot));
-            LU_CHECK_CUDA(cudaEventRecord(c->ev_tu, lo));
-            if (k + 1 < nk) {
-                LU_TRY(panel(k + 1));
-                if (eng && o.steal) LU_TRY(eng->steal(hi, k));
-                LU_CHECK_CUDA(cudaStreamWaitEvent(hi, c->ev_tu, 0));
-            }
-        } else {
-            LU_TRY(trailing_update<T>(c, hi, n, A, lda, k, k0, kb, c1, n, k0, plan_of(k), eng, 0, pivot));
+        const int64_t k0 = s[k];
+        lu_context::StepTrace* tr = nullptr;
+        if (trace) {
+            LU_TRY(trace_slot(c, k, &tr));
+            tr->k0 = k0;
+            tr->kb = s[k + 1] - k0;
+            tr->has_pu = k + 1 < nk;
+            tr->has_tu = true;
+            LU_CHECK_CUDA(cudaEventRecord(tr->pu0, hi));
+        }
+        if (depth == 0) {
+            // Listing 3: TU_k over every column right of panel k, then PF_{k+1}
+            if (tr) LU_CHECK_CUDA(cudaEventRecord(tr->tu0, hi));
+            LU_TRY(tu(hi, k, start(k + 1), n, k0, 0));
+            if (tr) LU_CHECK_CUDA(cudaEventRecord(tr->tu1, hi));
             if (k + 1 < nk) LU_TRY(panel(k + 1));
+            if (tr) LU_CHECK_CUDA(cudaEventRecord(tr->pu1, hi));
+            continue;
+        }
+        // Depth d: the high-priority stream owns the next d panels.  PU(k+1) =
+        // TU_k on panel k+1, then PF_{k+1}.  TU_k^L (a few narrow launches) is
+        // issued before TU_right(k) is released, so that it does not wait behind
+        // the right update's thousands of CTAs; PF_{k+1} then overlaps TU_right(k).
+        if (k + 1 < nk) LU_TRY(tu(hi, k, start(k + 1), start(k + 2), 0, 0));
+        LU_CHECK_CUDA(cudaEventRecord(c->ev_pf, hi));
+        LU_CHECK_CUDA(cudaStreamWaitEvent(lo, c->ev_pf, 0));
+        // TU_right(k): the columns past the panels the high-priority stream owns,
+        // and panel k's deferred interchanges on the columns left of it
+        if (tr) LU_CHECK_CUDA(cudaEventRecord(tr->tu0, lo));
+        LU_TRY(tu(lo, k, start(k + 1 + depth), n, k0, 1));
+        if (tr) LU_CHECK_CUDA(cudaEventRecord(tr->tu1, lo));
+        LU_CHECK_CUDA(cudaEventRecord(ev_tu[k & 1], lo));
+        if (k + 1 < nk) {
+            LU_TRY(panel(k + 1));
+            if (tr) LU_CHECK_CUDA(cudaEventRecord(tr->pu1, hi));
+            if (eng && o.steal) LU_TRY(eng->steal(hi, k));
+        }
+        if (depth == 1) {
+            // the next step's TU_k+1 on panel k+2 reads columns TU_right(k) writes
+            if (k + 1 < nk) LU_CHECK_CUDA(cudaStreamWaitEvent(hi, ev_tu[k & 1], 0));
+        } else if (k + 2 < nk) {
+            // depth 2: panel k+2 was part of TU_right(k-1); once that is done the
+            // high-priority stream applies TU_k to it, so PF_{k+2} in the next step
+            // waits for nothing on the update stream
+            if (k > 0) LU_CHECK_CUDA(cudaStreamWaitEvent(hi, ev_tu[(k - 1) & 1], 0));
+            LU_TRY(tu(hi, k, start(k + 2), start(k + 3), 0, 0));
         }
     }
+    if (trace) c->trace_steps = nk;
     LU_CHECK_CUDA(cudaEventRecord(c->ev_join_hi, hi));
     LU_CHECK_CUDA(cudaEventRecord(c->ev_join_lo, lo));
     LU_CHECK_CUDA(cudaStreamWaitEvent(user, c->ev_join_hi, 0));
@@ -300,7 +419,7 @@ extern "C" int lu_factor_ex(lu_handle h, lu_dtype dtype, int64_t n, void* A, int
     if (lu_check_opts(o) != 0) return -7;
     if (!info) return -8;
     if (n > INT32_MAX / 2) return LU_ERR_UNSUPPORTED;
-    if (o.nb == 0) o.nb = lu_auto_nb(dtype == LU_F64 ? LU_TUNE_F64 : LU_TUNE_F32, n);
+    if (o.nb == 0 && o.nsched == 0) lu_auto_opts(dtype == LU_F64 ? LU_TUNE_F64 : LU_TUNE_F32, n, &o);
     std::lock_guard<std::mutex> lk(h->mu);
     if (dtype == LU_F64) return lu_factor_blocked<double>(h, n, (double*)A, lda, ipiv, o, info, nullptr);
     return lu_factor_blocked<float>(h, n, (float*)A, lda, ipiv, o, info, nullptr);

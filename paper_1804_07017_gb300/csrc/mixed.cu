@@ -86,8 +86,13 @@ struct TcEngine final : LuTuEngine {
     int prec = LU_TU_BF16;
     int64_t n = 0;
     int nb = 0;
-    char* alo[2] = {nullptr, nullptr};  // packed L21 (K-major), n x nb each
-    char* blo[2] = {nullptr, nullptr};  // packed U12 (K-major), n x nb each
+    // packed L21 and U12 (K-major, n x nb each), one pair per panel in flight:
+    // two with depth-1 look-ahead, three with depth 2 (panel k's operands are
+    // read until TU_right(k) ends, which may be after PF_{k+2} starts)
+    static constexpr int kMaxBuf = 3;
+    int nbuf = 2;
+    char* alo[kMaxBuf] = {nullptr, nullptr, nullptr};
+    char* blo[kMaxBuf] = {nullptr, nullptr, nullptr};
     int* counter[2] = {nullptr, nullptr};
     int* error = nullptr;
     int grid_panel = 0, grid_right = 0, grid_steal = 0;
@@ -102,32 +107,32 @@ struct TcEngine final : LuTuEngine {
     int esize() const { return fp8() ? 1 : 2; }
     // FP8: the block scales follow the e4m3 bytes in each operand buffer
     size_t scale_off() const { return al256((size_t)n * nb); }
-    float* rscale(int64_t k) const { return reinterpret_cast<float*>(alo[k & 1] + scale_off()); }
-    float* cscale(int64_t k, int64_t off) const { return reinterpret_cast<float*>(blo[k & 1] + scale_off()) + off; }
+    float* rscale(int64_t k) const { return reinterpret_cast<float*>(alo[k % nbuf] + scale_off()); }
+    float* cscale(int64_t k, int64_t off) const { return reinterpret_cast<float*>(blo[k % nbuf] + scale_off()) + off; }
 
     bool uses_tc(int64_t kb) const override { return lu_prec_is_tc(prec) && kb % (fp8() ? 128 : 64) == 0; }
 
     int pack_panel(cudaStream_t st, const float* A, int64_t lda, int64_t k, int64_t k0, int64_t kb) const override {
         if (fp8())
             return lu_launch_pack_rows_e4m3(st, A + (k0 + kb) + k0 * lda, lda, n - (k0 + kb), (int)kb, rscale(k),
-                                            alo[k & 1]);
-        return lu_launch_pack_rows(st, fmt_pack(), A + (k0 + kb) + k0 * lda, lda, n - (k0 + kb), (int)kb, alo[k & 1]);
+                                            alo[k % nbuf]);
+        return lu_launch_pack_rows(st, fmt_pack(), A + (k0 + kb) + k0 * lda, lda, n - (k0 + kb), (int)kb, alo[k % nbuf]);
     }
 
     int launch(cudaStream_t st, float* A, int64_t lda, int64_t k, int64_t k0, int64_t kb, int64_t cb, int64_t ce,
                int which, int grid) const {
         const int64_t m = n - (k0 + kb);
         const int64_t off = cb - (k0 + kb);
-        const char* bbuf = blo[k & 1] + (size_t)off * kb * esize() * segs();
+        const char* bbuf = blo[k % nbuf] + (size_t)off * kb * esize() * segs();
         return lu_launch_tc_update(st, fp8() ? LU_TC_KIND_F8 : LU_TC_KIND_F16, fmt_mma(), A, lda, k0 + kb, m, cb,
-                                   ce - cb, kb * segs(), alo[k & 1], m, bbuf, ce - cb, 1.0f, counter[which], error,
+                                   ce - cb, kb * segs(), alo[k % nbuf], m, bbuf, ce - cb, 1.0f, counter[which], error,
                                    grid, 256, fp8() ? rscale(k) : nullptr, fp8() ? cscale(k, off) : nullptr);
     }
 
     int update(cudaStream_t st, float* A, int64_t lda, int64_t k, int64_t k0, int64_t kb, int64_t cb, int64_t ce,
                int which) const override {
         const int64_t off = cb - (k0 + kb);
-        char* bbuf = blo[k & 1] + (size_t)off * kb * esize() * segs();
+        char* bbuf = blo[k % nbuf] + (size_t)off * kb * esize() * segs();
         if (fp8())
             LU_TRY(lu_launch_pack_cols_e4m3(st, A + k0 + cb * lda, lda, ce - cb, (int)kb, cscale(k, off), bbuf));
         else
@@ -154,32 +159,58 @@ struct TcEngine final : LuTuEngine {
     }
 };
 
-size_t tc_engine_bytes(int prec, int64_t n, int nb) {
-    if (!lu_prec_is_tc(prec)) return 256;
-    if (prec == LU_TU_FP8) return 4 * al256(al256((size_t)n * nb) + sizeof(float) * (size_t)n);
-    return 4 * al256((size_t)n * nb * 2 * lu_pack_segments(lu_prec_pack_fmt(prec)));
+// Operand buffers of the engine for an order-n factorization with options o:
+// 2 * nbuf buffers sized for the widest panel of o's schedule.
+int engine_nbuf(const lu_opts& o) { return o.lookahead >= 2 ? 3 : 2; }
+
+int engine_width(int64_t n, const lu_opts& o) {
+    std::vector<int64_t> s;
+    int wmin = 1, wmax = 1;
+    lu_panel_bounds(std::max<int64_t>(n, 1), o, &s, &wmin, &wmax);
+    return wmax;
 }
 
-int setup_engine(TcEngine& e, lu_context* c, int prec, int64_t n, int nb, char* base, float* A, int64_t lda,
+// Narrowest panel of o's schedule: the handle workspace (interchange plans) is
+// sized for it before the engine takes pointers into that workspace.
+int narrowest(int64_t n, const lu_opts& o) {
+    std::vector<int64_t> s;
+    int wmin = 1, wmax = 1;
+    lu_panel_bounds(std::max<int64_t>(n, 1), o, &s, &wmin, &wmax);
+    return wmin;
+}
+
+size_t tc_engine_one(int prec, int64_t n, int nb) {
+    if (prec == LU_TU_FP8) return al256(al256((size_t)n * nb) + sizeof(float) * (size_t)n);
+    return al256((size_t)n * nb * 2 * lu_pack_segments(lu_prec_pack_fmt(prec)));
+}
+
+size_t tc_engine_bytes(int prec, int64_t n, const lu_opts& o) {
+    if (!lu_prec_is_tc(prec)) return 256;
+    return 2 * (size_t)engine_nbuf(o) * tc_engine_one(prec, n, engine_width(n, o));
+}
+
+int setup_engine(TcEngine& e, lu_context* c, int prec, int64_t n, char* base, float* A, int64_t lda,
                  const lu_opts& o) {
     e.c = c;
     e.prec = prec;
     e.n = n;
-    e.nb = nb;
-    const size_t one = tc_engine_bytes(prec, n, nb) / 4;
-    e.alo[0] = base;
-    e.alo[1] = base + one;
-    e.blo[0] = base + 2 * one;
-    e.blo[1] = base + 3 * one;
+    e.nb = engine_width(n, o);
+    e.nbuf = engine_nbuf(o);
+    const size_t one = tc_engine_one(prec, n, e.nb);
+    for (int i = 0; i < e.nbuf; ++i) {
+        e.alo[i] = base + (size_t)i * one;
+        e.blo[i] = base + (size_t)(e.nbuf + i) * one;
+    }
     e.counter[0] = (int*)&c->sync[4].ticket;
     e.counter[1] = (int*)&c->sync[5].ticket;
     e.error = &c->sync[0].error;
     e.A_ = A;
     e.lda_ = lda;
-    // With look-ahead the right update leaves some SMs to the panel path (a
-    // sixth: measured best at n = 16384 among 9, 24, 48, 76 and 100 of 152); with
-    // stealing, that many CTAs join the right update once the panel is done.
-    const int reserve = (o.lookahead && o.steal) ? std::max(4, c->num_sms / 6) : 0;
+    // With look-ahead the right update leaves some SMs to the panel path
+    // (opts.tu_reserve, by default a sixth: measured best at n = 16384 among 9,
+    // 24, 48, 76 and 100 of 152); with stealing, that many CTAs join the right
+    // update once the panel is done.
+    const int reserve = o.steal ? lu_resolve_reserve(c, o) : 0;
     e.grid_right = std::max(1, c->num_sms - reserve);
     e.grid_panel = c->num_sms;
     e.grid_steal = reserve;
@@ -195,19 +226,22 @@ static int factor_mixed(lu_context* c, int prec, int64_t n, float* A32, int64_t 
                         int32_t* info, char* engine_mem) {
     if (!lu_prec_is_tc(prec)) return lu_factor_blocked<float>(c, n, A32, lda, ipiv, o, info, nullptr);
     TcEngine e;
-    LU_TRY(setup_engine(e, c, prec, n, o.nb, engine_mem, A32, lda, o));
+    LU_TRY(setup_engine(e, c, prec, n, engine_mem, A32, lda, o));
     // panel leaves must fit beside a tensor-core update CTA on the same SM
     const size_t saved = c->pf_smem_budget;
     c->pf_smem_budget = LU_PF_SMEM_BUDGET;
     // The launch sequence depends only on these arguments, so a repeated call
     // replays it as one CUDA graph (no per-kernel launch gaps on the panel path):
     // a key is run eagerly on first use, captured on its second, replayed after.
-    const uint64_t key[10] = {(uint64_t)(uintptr_t)A32, (uint64_t)lda, (uint64_t)n, (uint64_t)(uintptr_t)ipiv,
+    uint64_t sched_hash = 1469598103934665603ull;  // FNV-1a over the schedule
+    for (int i = 0; i < o.nsched; ++i) sched_hash = (sched_hash ^ (uint64_t)(uint32_t)o.sched[i]) * 1099511628211ull;
+    const uint64_t key[12] = {(uint64_t)(uintptr_t)A32, (uint64_t)lda, (uint64_t)n, (uint64_t)(uintptr_t)ipiv,
                               (uint64_t)(uintptr_t)info, (uint64_t)prec,
                               ((uint64_t)o.nb << 32) | ((uint64_t)o.lookahead << 16) | (uint64_t)o.steal,
                               ((uint64_t)o.leaf << 32) | (uint64_t)o.pf_ctas, (uint64_t)(uintptr_t)engine_mem,
-                              (uint64_t)(uintptr_t)c->user};
-    bool use_graph = !lu_profile_active() && n > 0;
+                              (uint64_t)(uintptr_t)c->user,
+                              ((uint64_t)(uint32_t)o.tu_reserve << 32) | (uint64_t)(uint32_t)o.nsched, sched_hash};
+    bool use_graph = !lu_profile_active() && !c->trace_on && n > 0;
     if (use_graph && !c->gs) {
         // the caller's stream may be the legacy default stream, which cannot be
         // captured: the graph is captured on, and replayed from, a stream of its own
@@ -292,10 +326,10 @@ extern "C" int lu_factor_mixed_ex(lu_handle h, lu_prec prec, int64_t n, float* A
     if (lu_check_opts(o) != 0) return -7;
     if (!info) return -8;
     if (n > INT32_MAX / 2) return LU_ERR_UNSUPPORTED;
-    if (o.nb == 0) o.nb = lu_auto_nb(prec, n);
+    if (o.nb == 0 && o.nsched == 0) lu_auto_opts(prec, n, &o);
     std::lock_guard<std::mutex> lk(h->mu);
-    LU_TRY(lu_ctx_reserve(h, n, o.nb));
-    LU_TRY(lu_mx_reserve(h, tc_engine_bytes(prec, std::max<int64_t>(n, 1), o.nb)));
+    LU_TRY(lu_ctx_reserve(h, n, narrowest(n, o)));
+    LU_TRY(lu_mx_reserve(h, tc_engine_bytes(prec, std::max<int64_t>(n, 1), o)));
     return factor_mixed(h, prec, n, A, lda, ipiv, o, info, (char*)h->mx);
 }
 
@@ -309,7 +343,7 @@ static int gesv_refined(lu_context* h, int prec, int64_t n, int64_t nrhs, const 
                         const double* B, int64_t ldb, double* X, int64_t ldx, double tol, int max_iter,
                         const lu_opts& o, int* iters, double* bwd_err) {
     cudaStream_t st = h->user;
-    LU_TRY(lu_ctx_reserve(h, n, o.nb));
+    LU_TRY(lu_ctx_reserve(h, n, narrowest(n, o)));
     if (!h->host_eta) LU_CHECK_CUDA(cudaMallocHost(&h->host_eta, 4 * sizeof(double)));
     const int64_t ldw = (n + 31) / 32 * 32;
     const int64_t nch = lu_ir_nchunks(n);
@@ -317,7 +351,7 @@ static int gesv_refined(lu_context* h, int prec, int64_t n, int64_t nrhs, const 
     size_t off = 0;
     auto take = [&](size_t bytes) { size_t o0 = off; off += al256(bytes); return o0; };
     const size_t o_aw = take(sizeof(T) * (size_t)ldw * n);
-    const size_t o_eng = take(sizeof(T) == 4 ? tc_engine_bytes(prec, n, o.nb) : 256);
+    const size_t o_eng = take(sizeof(T) == 4 ? tc_engine_bytes(prec, n, o) : 256);
     const size_t o_ipiv = take(sizeof(int32_t) * n);
     const size_t o_perm = take(sizeof(int32_t) * n);
     const size_t o_r = take(sizeof(double) * n * nrhs);
@@ -450,7 +484,7 @@ extern "C" int lu_gesv_mixed(lu_handle h, lu_prec prec, int64_t n, int64_t nrhs,
     if (bwd_err) *bwd_err = 0.0;
     if (n == 0 || nrhs == 0) return LU_SUCCESS;
     if (n > INT32_MAX / 2) return LU_ERR_UNSUPPORTED;
-    if (o.nb == 0) o.nb = lu_auto_nb(prec == LU_FULL_F64 ? LU_TUNE_F64 : (int)prec, n);
+    if (o.nb == 0 && o.nsched == 0) lu_auto_opts(prec == LU_FULL_F64 ? LU_TUNE_F64 : (int)prec, n, &o);
     std::lock_guard<std::mutex> lk(h->mu);
     if (prec == LU_FULL_F64)
         return gesv_refined<double>(h, prec, n, nrhs, A, lda, B, ldb, X, ldx, tol, max_iter, o, iters, bwd_err);

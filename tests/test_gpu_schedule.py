@@ -1,0 +1,163 @@
+"""GPU checks of the schedule options of the blocked factorization: per-step
+block sizes (the GPU form of the paper's early termination, Sec. 4.2: b
+changed from step to step), depth-2 look-ahead, the SMs the right update
+leaves to the panel path, the per-step trace and the plan tuner.
+
+Pass criteria (as the other parity tests): against the CPU oracle, pivots
+bit-exact at separated steps, factorization backward error <= 1e-14 (FP64) or
+4 u32 (FP32), designed interchange sequences returned exactly, solve eta <=
+1e-14 after refinement; and, since depth, reserve and stealing only change
+which stream or CTA does an update and never an element's operations, the
+factors of one schedule are bit-identical across depths 0, 1, 2 and across
+reserves.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+TAU = {torch.float64: 1e-8, torch.float32: 1e-3}
+BOUND = {torch.float64: 1e-14, torch.float32: 4 * np.finfo(np.float32).eps}
+
+
+@pytest.fixture(scope="module")
+def lu():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import paper_1804_07017_gb300 as pkg
+    pkg.lib()
+    pkg.lu_tune_clear()
+    yield pkg
+    pkg.lu_tune_clear()
+
+
+def dev(a, dtype):
+    from paper_1804_07017_gb300.api import colmajor
+    a = np.asarray(a)
+    if a.ndim == 1:
+        a = a[:, None]
+    t = colmajor(a.shape[0], a.shape[1], dtype=dtype)
+    t.copy_(torch.from_numpy(np.ascontiguousarray(a)).to(dtype))
+    return t
+
+
+def factor(lu, A0, dtype, mixed=None, **opts):
+    n = A0.shape[0]
+    A = dev(A0, dtype)
+    ipiv = torch.zeros(n, dtype=torch.int32, device="cuda")
+    info = torch.full((1,), -7, dtype=torch.int32, device="cuda")
+    o = lu.default_opts(**opts)
+    if mixed is None:
+        lu.lu_factor_ex(A, ipiv, info, o)
+    else:
+        lu.lu_factor_mixed_ex(A, ipiv, info, mixed, o)
+    torch.cuda.synchronize()
+    return A.cpu().double().numpy()[:n, :n], ipiv.cpu().numpy(), int(info.item())
+
+
+SCHEDULES = [[64, 128, 96, 37, 256], [256, 192, 128, 64], [32], [300, 20, 512]]
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+@pytest.mark.parametrize("sched", SCHEDULES)
+def test_schedule_parity_and_depths_identical(lu, dtype, sched):
+    n = 1100
+    A0 = synth.uniform_matrix(n, seed=71, stream=len(sched))
+    if dtype == torch.float32:
+        A0 = A0.astype(np.float32).astype(np.float64)
+    LU_o, piv_o, _, gap = oracle.getrf(A0)
+    runs = []
+    for depth, reserve in ((0, 0), (1, 0), (2, 0), (1, 40), (2, 8)):
+        LU, piv, info = factor(lu, A0, dtype, nb=0, sched=sched, lookahead=depth, tu_reserve=reserve)
+        assert info == 0
+        runs.append((LU, piv))
+    LU, piv = runs[0]
+    sep = gap > TAU[dtype]
+    assert np.array_equal(piv[sep], piv_o[sep])
+    assert oracle.factor_error(A0, LU, piv) <= BOUND[dtype]
+    for LUd, pivd in runs[1:]:
+        assert np.array_equal(pivd, piv) and np.array_equal(LUd, LU)
+
+
+@pytest.mark.parametrize("name", ["last_row", "in_panel", "mixed", "reverse"])
+def test_schedule_designed_pivot_sequences(lu, name):
+    """Designed interchange sequences through panels of changing width (the
+    interchange plans, the leaves and the updates between them must return the
+    sequence exactly), FP64 with depth 2 and the tensor-core path (bf16x6)."""
+    import pivot_patterns as pp
+    n = 900
+    A0, piv_expect = pp.patterned_matrix(name, n, seed=19, panel=64)
+    LU, piv, info = factor(lu, A0, torch.float64, nb=0, sched=[128, 64, 192, 37], lookahead=2)
+    assert info == 0 and np.array_equal(piv, piv_expect)
+    assert oracle.factor_error(A0, LU, piv) <= 1e-14
+    A32 = A0.astype(np.float32).astype(np.float64)
+    LU, piv, info = factor(lu, A32, torch.float32, mixed=lu.LU_TU_BF16X6, nb=0, sched=[128, 64, 192, 256],
+                           lookahead=2)
+    assert info == 0 and np.array_equal(piv, piv_expect)
+
+
+def test_mixed_schedule_depth2_solve(lu):
+    """lu_gesv_mixed with a per-step schedule and depth-2 look-ahead: the
+    refined solution's eta <= 1e-14 (recomputed by the oracle), and the mixed
+    factors are bit-identical across depths 1 and 2 and across reserves."""
+    n = 2048
+    A0 = synth.normal_matrix(n, seed=72)
+    b0 = synth.ones_rhs(A0)
+    sched = [384, 256, 256, 192, 128, 64]
+    A, B, X = dev(A0, torch.float64), dev(b0, torch.float64), dev(np.zeros_like(b0), torch.float64)
+    for depth in (1, 2):
+        st, it, eta = lu.lu_gesv_mixed(A, B, X, lu.LU_TU_BF16X6, opts=lu.default_opts(nb=0, sched=sched,
+                                                                                          lookahead=depth))
+        torch.cuda.synchronize()
+        x = X.cpu().numpy()
+        assert st == 0 and oracle.backward_error(A0, x, b0) <= 1e-14, (depth, it, eta)
+    A32 = A0.astype(np.float32).astype(np.float64)
+    outs = [factor(lu, A32, torch.float32, mixed=lu.LU_TU_BF16X6, nb=0, sched=sched, lookahead=d, tu_reserve=r)
+            for d, r in ((1, 0), (2, 0), (2, 50), (1, 12))]
+    for LU, piv, info in outs:
+        assert info == 0
+        assert np.array_equal(piv, outs[0][1]) and np.array_equal(LU, outs[0][0])
+
+
+def test_step_trace(lu):
+    """The per-step trace covers every column once, in order, with positive
+    panel-path and update times."""
+    n, nb = 2048, 256
+    A0 = synth.normal_matrix(n, seed=73).astype(np.float32).astype(np.float64)
+    h = lu.lu_step_trace(True)
+    try:
+        factor(lu, A0, torch.float32, mixed=lu.LU_TU_BF16X6, nb=nb)
+        steps = lu.lu_step_trace_read(h)
+    finally:
+        lu.lu_step_trace(False)
+    assert len(steps) == n // nb
+    assert [s["k0"] for s in steps] == list(range(0, n, nb)) and all(s["kb"] == nb for s in steps)
+    assert all(s["span_ms"] > 0 and s["tu_ms"] >= 0 for s in steps)
+    assert all(s["pu_ms"] > 0 for s in steps[:-1])
+    print("\n[trace n=2048 nb=256] step span / PU(k+1) / TU_right(k) ms: " +
+          ", ".join(f"{s['span_ms']:.2f}/{s['pu_ms']:.2f}/{s['tu_ms']:.2f}" for s in steps))
+
+
+def test_tune_plan_and_nb_zero(lu):
+    """lu_tune_plan returns a plan no slower than the best fixed plan it
+    measured, stores it, and a factorization with nb = 0 applies it: its factors
+    are bit-identical to those of the returned options and pass the parity
+    criteria."""
+    n = 2048
+    best, sched, ms, fixed = lu.lu_tune_plan(lu.LU_TU_BF16X6, n, reps=3)
+    assert 0 < ms <= fixed
+    plan = lu.lu_tune_plan_get(lu.LU_TU_BF16X6, n)
+    assert plan is not None and plan[0] == best.nb and plan[3] == sched
+    assert best.lookahead in (1, 2) and best.tu_reserve >= 4
+    print(f"\n[tune plan n={n} bf16x6] nb={best.nb} reserve={best.tu_reserve} depth={best.lookahead} "
+          f"schedule={sched} best {ms:.2f} ms, fixed {fixed:.2f} ms")
+    A0 = synth.normal_matrix(n, seed=74).astype(np.float32).astype(np.float64)
+    LU0, p0, i0 = factor(lu, A0, torch.float32, mixed=lu.LU_TU_BF16X6, nb=0)
+    LU1, p1, i1 = factor(lu, A0, torch.float32, mixed=lu.LU_TU_BF16X6, nb=best.nb, sched=sched,
+                         lookahead=best.lookahead, tu_reserve=best.tu_reserve)
+    assert i0 == i1 == 0 and np.array_equal(p0, p1) and np.array_equal(LU0, LU1)
+    assert oracle.factor_error(A0, LU0, p0) <= 1e-5
