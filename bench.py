@@ -461,7 +461,7 @@ def prof_leaf(args, lu, torch, dt):
     import synth
     m, w = _shape(args, (16384, 16))
     P0 = torch.from_numpy(synth.normal_matrix(m, w, seed=3)).to(dt)
-    P = lu.colmajor(m, w, dtype=dt)
+    P = lu.api.colmajor(m, w, dtype=dt)
     ipiv = torch.zeros(w, dtype=torch.int32, device="cuda")
     info = torch.zeros(1, dtype=torch.int32, device="cuda")
     ms = _median_ms(lambda: lu.lu_panel_factor_ex(P, ipiv, info, lu.default_opts(leaf=w)), args.reps,
@@ -477,11 +477,11 @@ def prof_tc(args, lu, torch, dt):
     m, n, k, prec = _shape(args, (8192, 8192, 256, 6))
     g = synth.rng(5, 0)
     C0 = torch.from_numpy(g.standard_normal((m, n))).float()
-    A = lu.colmajor(m, k, dtype=torch.float32)
-    B = lu.colmajor(k, n, dtype=torch.float32)
+    A = lu.api.colmajor(m, k, dtype=torch.float32)
+    B = lu.api.colmajor(k, n, dtype=torch.float32)
     A.copy_(torch.from_numpy(g.standard_normal((m, k))).float())
     B.copy_(torch.from_numpy(g.standard_normal((k, n))).float())
-    C = lu.colmajor(m, n, dtype=torch.float32)
+    C = lu.api.colmajor(m, n, dtype=torch.float32)
     info = torch.zeros(1, dtype=torch.int32, device="cuda")
     ms = _median_ms(lambda: lu.lu_gemm_update_tc_ex(C, A, B, prec, info), args.reps, before=lambda: C.copy_(C0))
     parts = {6: 6, 3: 3}.get(prec, 1)
@@ -495,10 +495,10 @@ def prof_trsm(args, lu, torch, dt):
     m, n = _shape(args, (256, 16128))
     g = synth.rng(12, m)
     L0 = np.tril(g.uniform(-1, 1, size=(m, m)), -1) + np.eye(m)
-    Lt = lu.colmajor(m, m, dtype=dt)
+    Lt = lu.api.colmajor(m, m, dtype=dt)
     Lt.copy_(torch.from_numpy(L0).to(dt))
     B0 = torch.from_numpy(g.uniform(-1, 1, size=(m, n))).to(dt)
-    B = lu.colmajor(m, n, dtype=dt)
+    B = lu.api.colmajor(m, n, dtype=dt)
     ms = _median_ms(lambda: lu.lu_trsm_ex(Lt, B), args.reps, before=lambda: B.copy_(B0))
     es = B.element_size()
     _prof_line("trsm", {"m": m, "n": n}, ms, es * (2.0 * m * n + 0.5 * m * m), float(m) * m * n)
@@ -513,7 +513,7 @@ def prof_laswp(args, lu, torch, dt):
     ipiv = np.arange(1, n + 1, dtype=np.int32)
     for j in range(K):
         ipiv[j] = int(g.integers(j, n)) + 1
-    A = lu.colmajor(n, ncols, dtype=dt)
+    A = lu.api.colmajor(n, ncols, dtype=dt)
     A.copy_(torch.from_numpy(g.uniform(-1, 1, size=(n, ncols))).to(dt))
     piv = torch.from_numpy(ipiv).cuda()
     moved = len({int(p) - 1 for p in ipiv[:K]} | set(range(K)))
@@ -529,11 +529,11 @@ def prof_gemm(args, lu, torch, dt):
     m, n, k = _shape(args, (8192, 8192, 256))
     g = synth.rng(13, 0)
     C0 = torch.from_numpy(g.uniform(-1, 1, size=(m, n))).to(dt)
-    A = lu.colmajor(m, k, dtype=dt)
-    B = lu.colmajor(k, n, dtype=dt)
+    A = lu.api.colmajor(m, k, dtype=dt)
+    B = lu.api.colmajor(k, n, dtype=dt)
     A.copy_(torch.from_numpy(g.uniform(-1, 1, size=(m, k))).to(dt))
     B.copy_(torch.from_numpy(g.uniform(-1, 1, size=(k, n))).to(dt))
-    C = lu.colmajor(m, n, dtype=dt)
+    C = lu.api.colmajor(m, n, dtype=dt)
     ms = _median_ms(lambda: lu.lu_gemm_update_ex(C, A, B), args.reps, before=lambda: C.copy_(C0))
     es = C.element_size()
     _prof_line("gemm", {"m": m, "n": n, "k": k}, ms, es * (2.0 * m * n + (m + n) * k), 2.0 * m * n * k)
@@ -543,14 +543,14 @@ def prof_trsv(args, lu, torch, dt):
     """solve with the factors of an FP32 mixed factorization of order n (N(0,1))"""
     import synth
     (n,) = _shape(args, (16384,))
-    A = lu.colmajor(n, n, dtype=torch.float32)
+    A = lu.api.colmajor(n, n, dtype=torch.float32)
     A.copy_(torch.from_numpy(synth.normal_matrix(n, seed=0)).float())
     ipiv = torch.zeros(n, dtype=torch.int32, device="cuda")
     info = torch.zeros(1, dtype=torch.int32, device="cuda")
     lu.lu_factor_mixed_ex(A, ipiv, info, 6, lu.default_opts(nb=256))
     torch.cuda.synchronize()
     B0 = torch.ones((n, 1), dtype=torch.float32)
-    B = lu.colmajor(n, 1, dtype=torch.float32)
+    B = lu.api.colmajor(n, 1, dtype=torch.float32)
     ms = _median_ms(lambda: lu.lu_solve_ex(A, ipiv, B), args.reps, before=lambda: B.copy_(B0))
     _prof_line("trsv", {"n": n}, ms, 4.0 * n * n, 2.0 * n * n, info=int(info.item()))
 
@@ -564,8 +564,8 @@ def prof_batched(args, lu, torch, dt):
     g = synth.rng(0, 9)
     A0 = [torch.from_numpy(m).to(dt) for m in mats]
     B0 = [torch.from_numpy(g.uniform(-1, 1, size=(int(n), int(r)))).to(dt) for n, r in zip(sizes, nrhs)]
-    dA = [lu.colmajor(x.shape[0], x.shape[1], dtype=dt) for x in A0]
-    dB = [lu.colmajor(x.shape[0], x.shape[1], dtype=dt) for x in B0]
+    dA = [lu.api.colmajor(x.shape[0], x.shape[1], dtype=dt) for x in A0]
+    dB = [lu.api.colmajor(x.shape[0], x.shape[1], dtype=dt) for x in B0]
     piv = [torch.zeros(int(n), dtype=torch.int32, device="cuda") for n in sizes]
     batch = lu.Batch(dA, piv, dB)
 
@@ -581,7 +581,7 @@ def prof_batched(args, lu, torch, dt):
 
 
 def prof_peak(args, lu, torch, dt):
-    """CUDA-core FMA throughput (lu_peak_fma): blocks = SMs x 8 of 256 threads, 8 chains each"""
+    """CUDA-core FMA throughput (lu_peak_fma): blocks = SMs x 8 of 256 threads, 16 chains each"""
     L = lu.lib()
     sms = torch.cuda.get_device_properties(0).multi_processor_count
     res = {}
@@ -602,7 +602,7 @@ def prof_peak(args, lu, torch, dt):
         flops = 2.0 * L.lu_peak_fma_chains() * iters * blocks * threads
         res[name] = {"GFLOP/s": flops / (ms * 1e-3) / 1e9, "ms": ms, "clocks": clk.summary()}
     line = {"workload": "profile", "case": "peak", "fma_peak": res,
-            "how": "lu_peak_fma: SMs x 8 CTAs of 256 threads, 8 independent FMA chains per thread, "
+            "how": "lu_peak_fma: SMs x 8 CTAs of 256 threads, 16 independent FMA chains per thread, "
                    "median of CUDA-event-timed launches; no clock setting changed"}
     print(json.dumps(line), flush=True)
 
@@ -701,8 +701,9 @@ def run_tune(args):
     """Block-size sweeps through the library's autotuner (lu_tune_nb): the mixed
     factorization with the split-bf16 x6 update at n = 16384 and the FP64
     factorization at n = 8192, each candidate timed three times on a seeded
-    U[-1,1) matrix (least time counts).  One JSON object with the times per nb
-    and the chosen nb."""
+    U[-1,1) matrix (least time counts); then whole plans (lu_tune_plan) at
+    n = 16384 and 32768 (mixed) and 8192 (FP64), with the traced steps of the
+    chosen plan.  --shape filters the plan sizes.  One JSON object."""
     import torch
 
     import paper_1804_07017_gb300 as lu
@@ -716,6 +717,44 @@ def run_tune(args):
         out[name] = {"n": n, "best_nb": best,
                      "ms": {str(c): (round(t, 3) if t >= 0 else None) for c, t in zip(cand, ms)},
                      "gflops_at_best": round(2.0 * n ** 3 / 3.0 / (min(t for t in ms if t >= 0) * 1e-3) / 1e9, 1)}
+    # whole plans (lu_tune_plan): nb, the right update's SM reserve, look-ahead depth and
+    # a per-step schedule built from traced steps; fixed = the best plan without a schedule
+    plans = [("plan_mixed_bf16x6_n16384", lu.LU_TU_BF16X6, 16384),
+             ("plan_mixed_bf16x6_n32768", lu.LU_TU_BF16X6, 32768),
+             ("plan_fp64_n8192", lu.LU_TUNE_F64, 8192)]
+    if args.shape:
+        plans = [p for p in plans if str(p[2]) in args.shape.split(",")]
+    for name, kind, n in plans:
+        best, sched, ms, fixed = lu.lu_tune_plan(kind, n, reps=3)
+        h = lu.lu_step_trace(True)
+        A = torch.empty(0)
+        try:
+            import synth
+            A0 = synth.uniform_matrix(n, seed=0)
+            dt = torch.float64 if kind == lu.LU_TUNE_F64 else torch.float32
+            A = lu.api.colmajor(n, n, dtype=dt)
+            A.copy_(torch.from_numpy(A0).to(dt))
+            ipiv = torch.zeros(n, dtype=torch.int32, device="cuda")
+            info = torch.zeros(1, dtype=torch.int32, device="cuda")
+            if kind == lu.LU_TUNE_F64:
+                lu.lu_factor_ex(A, ipiv, info, best)
+            else:
+                lu.lu_factor_mixed_ex(A, ipiv, info, kind, best)
+            steps = lu.lu_step_trace_read(h)
+        finally:
+            lu.lu_step_trace(False)
+        del A
+        torch.cuda.empty_cache()
+        out[name] = {"n": n, "nb": best.nb, "tu_reserve": best.tu_reserve, "depth": best.lookahead,
+                     "schedule": sched, "ms_best": round(ms, 3), "ms_fixed_plan": round(fixed, 3),
+                     "gflops_best": round(2.0 * n ** 3 / 3.0 / (ms * 1e-3) / 1e9, 1),
+                     "trace_of_chosen_plan": {
+                         "steps": len(steps),
+                         "pu_ms_sum": round(sum(x["pu_ms"] for x in steps), 2),
+                         "tu_right_ms_sum": round(sum(x["tu_ms"] for x in steps), 2),
+                         "span_ms_sum": round(sum(x["span_ms"] for x in steps), 2),
+                         "steps_panel_bound": sum(1 for x in steps if x["pu_ms"] >= x["tu_ms"]),
+                         "note": "traced run, no graph replay"}}
     print(json.dumps(out))
     return 0
 
@@ -723,7 +762,8 @@ def run_tune(args):
 def run_configs(args):
     """The comparisons of the hot-path configurations, one JSON object:
     c1  FP64, n = 8192, nb = 256, N(0,1): look-ahead off / depth 1 / depth 1 with
-        stealing (factorization + solve, GFLOP/s of 2n^3/3);
+        stealing / depth 2 / the runtime-task DAG schedule (factorization +
+        solve, GFLOP/s of 2n^3/3);
     c2  n = 16384, nb = 256: the mixed solver with each trailing-update precision
         (N(0,1), one rhs), then bf16x6 on the row-scaled matrix and with 16 rhs;
     c3  n = 32768, nb = 256, A = diag(10^u) G: bf16x6 and e4m3 updates.
@@ -761,8 +801,10 @@ def run_configs(args):
     Ah = torch.from_numpy(A0).cuda()
     bh = torch.from_numpy(b0).cuda()
     c1 = {}
-    for name, la, steal in (("lookahead_off", 0, 0), ("lookahead_1", 1, 0), ("lookahead_1_steal", 1, 1)):
-        o = lu.default_opts(nb=256, lookahead=la, steal=steal)
+    for name, la, steal, rtm in (("lookahead_off", 0, 0, 0), ("lookahead_1", 1, 0, 0),
+                                 ("lookahead_1_steal", 1, 1, 0), ("lookahead_2_steal", 2, 1, 0),
+                                 ("rtm_task_dag", 1, 0, 1)):
+        o = lu.default_opts(nb=256, lookahead=la, steal=steal, rtm=rtm)
 
         def run():
             A.copy_(Ah)

@@ -101,6 +101,15 @@ typedef struct {
                       tensor-core update needs multiples of 64, FP8 of 128; other
                       widths run that step's update on the CUDA cores); read
                       during the call only */
+    int rtm;       /* 1: instead of the static look-ahead, the runtime-task
+                      schedule the paper compares against (Sec. 3.3, Listing 4):
+                      every PF(k), every block-column update TU(k, j) and the
+                      interchanges of panel k on the columns left of it are
+                      tasks of one dependency DAG, replayed as a CUDA graph whose
+                      executor starts each task when its inputs are ready (any
+                      look-ahead depth); PF(k) and TU(k, k+1) run at high
+                      priority.  FP64/FP32 factorizations on the CUDA cores
+                      (lu_factor_ex, lu_potrf_ex); 0 = static look-ahead */
 } lu_opts;
 
 /* Fills *opts with the defaults (nb = 256, lookahead = 1, steal = 1, automatic

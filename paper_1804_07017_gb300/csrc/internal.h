@@ -69,6 +69,16 @@ struct lu_context {
         int64_t k0 = 0, kb = 0;
         bool has_pu = false, has_tu = false;
     };
+    // Runtime-task schedule (rtm.cu): one stream per block-column class, the left
+    // interchanges' stream, the capture origin, per-panel and per-column events,
+    // and the DAG's instantiated graph with the arguments it was captured for.
+    std::vector<cudaStream_t> rtm_cols;
+    cudaStream_t rtm_left = nullptr, rtm_origin = nullptr;
+    std::vector<cudaEvent_t> rtm_pf, rtm_col;
+    cudaEvent_t rtm_ev = nullptr, rtm_ev2 = nullptr;
+    cudaGraphExec_t rtm_exec = nullptr;
+    uint64_t rtm_key[12] = {};
+    long long rtm_launches = 0;
     bool trace_on = false;
     std::vector<StepTrace> trace;
     int64_t trace_steps = 0;
@@ -190,6 +200,20 @@ int lu_check_opts(const lu_opts& o);
 void lu_panel_bounds(int64_t n, const lu_opts& o, std::vector<int64_t>* s, int* wmin, int* wmax);
 // SMs the right update leaves to the panel path (0 without look-ahead).
 int lu_resolve_reserve(const lu_context* c, const lu_opts& o);
+
+// One task of the factorization of step k (panel columns [k0, k0+kb)): TU_k on
+// columns [cb, ce) plus panel k's interchanges on the `left` leading columns
+// (lu_step_tu), and PF(k) with its interchange plan (lu_step_pf).
+template <typename T>
+int lu_step_tu(lu_context* c, cudaStream_t st, int64_t n, T* A, int64_t lda, int64_t k, int64_t k0, int64_t kb,
+               int64_t cb, int64_t ce, int64_t left, bool pivot);
+template <typename T>
+int lu_step_pf(lu_context* c, cudaStream_t st, T* A, int64_t lda, int64_t n, int64_t k, int64_t k0, int64_t kb,
+               int32_t* ipiv, const lu_opts& o, bool pivot);
+// The runtime-task (dependency DAG) schedule of the same factorization (rtm.cu).
+template <typename T>
+int lu_factor_rtm(lu_context* c, int64_t n, T* A, int64_t lda, int32_t* ipiv, const lu_opts& o, int32_t* info,
+                  bool pivot);
 
 // pivot = false: elimination without interchanges (the Cholesky path, chol.cu):
 // panels by lu_panel_nopiv, no interchange plans or row exchanges, ipiv unused.

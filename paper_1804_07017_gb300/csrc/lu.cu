@@ -98,6 +98,7 @@ extern "C" void lu_default_opts(lu_opts* o) {
     o->tu_reserve = 0;
     o->nsched = 0;
     o->sched = nullptr;
+    o->rtm = 0;
 }
 
 int lu_ctx_init(lu_context* c) {
@@ -134,6 +135,22 @@ int lu_ctx_release(lu_context* c) {
     cudaEvent_t evs[] = {c->ev_fork, c->ev_pf, c->ev_tu, c->ev_join_hi, c->ev_join_lo, c->ev_steal, c->ev_tu2};
     for (cudaEvent_t e : evs)
         if (e) cudaEventDestroy(e);
+    if (c->rtm_exec) cudaGraphExecDestroy(c->rtm_exec);
+    c->rtm_exec = nullptr;
+    for (cudaStream_t x : c->rtm_cols)
+        if (x) cudaStreamDestroy(x);
+    c->rtm_cols.clear();
+    for (cudaStream_t x : {c->rtm_left, c->rtm_origin})
+        if (x) cudaStreamDestroy(x);
+    c->rtm_left = c->rtm_origin = nullptr;
+    for (auto* v : {&c->rtm_pf, &c->rtm_col})
+        for (cudaEvent_t e : *v)
+            if (e) cudaEventDestroy(e);
+    c->rtm_pf.clear();
+    c->rtm_col.clear();
+    for (cudaEvent_t e : {c->rtm_ev, c->rtm_ev2})
+        if (e) cudaEventDestroy(e);
+    c->rtm_ev = c->rtm_ev2 = nullptr;
     for (auto& t : c->trace) {
         cudaEvent_t te[] = {t.pu0, t.pu1, t.tu0, t.tu1};
         for (cudaEvent_t e : te)
@@ -238,6 +255,7 @@ int lu_check_opts(const lu_opts& o) {
     if (o.lookahead < 0 || o.lookahead > 2) return -1;
     if (o.leaf < 0 || o.pf_ctas < 0 || o.pf_ctas > LU_PF_MAX_CTAS) return -1;
     if (o.tu_reserve < 0 || o.nsched < 0 || o.nsched > (1 << 20)) return -1;
+    if (o.rtm < 0 || o.rtm > 1) return -1;
     if (o.nsched > 0) {
         if (!o.sched) return -1;
         for (int i = 0; i < o.nsched; ++i)
@@ -294,6 +312,30 @@ static int trailing_update(lu_context* c, cudaStream_t st, int64_t n, T* A, int6
                                     A + (k0 + kb) + c_begin * lda, lda);
 }
 
+template <typename T>
+int lu_step_tu(lu_context* c, cudaStream_t st, int64_t n, T* A, int64_t lda, int64_t k, int64_t k0, int64_t kb,
+               int64_t cb, int64_t ce, int64_t left, bool pivot) {
+    return trailing_update<T>(c, st, n, A, lda, k, k0, kb, cb, ce, left, c->plans + (size_t)k * c->plan_stride,
+                              nullptr, 0, pivot);
+}
+
+template <typename T>
+int lu_step_pf(lu_context* c, cudaStream_t st, T* A, int64_t lda, int64_t n, int64_t k, int64_t k0, int64_t kb,
+               int32_t* ipiv, const lu_opts& o, bool pivot) {
+    if (!pivot) return lu_panel_nopiv<T>(st, A, lda, n, k0, kb, &c->sync[0]);
+    LU_TRY(lu_panel_recursive<T>(c, st, A, lda, n, k0, kb, ipiv, o));
+    return lu_launch_laswp_plan(st, ipiv, k0, k0 + kb, c->plans + (size_t)k * c->plan_stride);
+}
+
+template int lu_step_tu<double>(lu_context*, cudaStream_t, int64_t, double*, int64_t, int64_t, int64_t, int64_t,
+                                int64_t, int64_t, int64_t, bool);
+template int lu_step_tu<float>(lu_context*, cudaStream_t, int64_t, float*, int64_t, int64_t, int64_t, int64_t,
+                               int64_t, int64_t, int64_t, bool);
+template int lu_step_pf<double>(lu_context*, cudaStream_t, double*, int64_t, int64_t, int64_t, int64_t, int64_t,
+                                int32_t*, const lu_opts&, bool);
+template int lu_step_pf<float>(lu_context*, cudaStream_t, float*, int64_t, int64_t, int64_t, int64_t, int64_t,
+                               int32_t*, const lu_opts&, bool);
+
 // Timing events of one traced step (created on first use, kept by the handle).
 static int trace_slot(lu_context* c, int64_t k, lu_context::StepTrace** out) {
     if ((int64_t)c->trace.size() <= k) c->trace.resize((size_t)k + 1);
@@ -309,6 +351,7 @@ template <typename T>
 int lu_factor_blocked(lu_context* c, int64_t n, T* A, int64_t lda, int32_t* ipiv, const lu_opts& o, int32_t* info,
                       const LuTuEngine* eng, bool pivot) {
     if (o.nb < 1 && o.nsched < 1) return LU_ERR_UNSUPPORTED;  // nb = 0 is resolved before this point
+    if (o.rtm) return eng ? LU_ERR_UNSUPPORTED : lu_factor_rtm<T>(c, n, A, lda, ipiv, o, info, pivot);
     std::vector<int64_t> s;
     int wmin = 1, wmax = 1;
     lu_panel_bounds(n, o, &s, &wmin, &wmax);

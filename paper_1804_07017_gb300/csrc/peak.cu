@@ -11,7 +11,7 @@
 
 namespace {
 
-constexpr int kChains = 8;
+constexpr int kChains = 16;
 
 template <typename T>
 __global__ void __launch_bounds__(256) fma_peak_kernel(int64_t iters, T b, T c, T* sink) {

@@ -48,7 +48,7 @@ def test_argument_validation_without_gpu(built):
     assert L.lu_peak_fma(0, 0, 256, 1, ctypes.c_void_p(16), None) == -2
     assert L.lu_peak_fma(0, 1, 100, 1, ctypes.c_void_p(16), None) == -3
     assert L.lu_peak_fma(1, 1, 256, 1, None, None) == -5
-    assert L.lu_peak_fma_chains() == 8
+    assert L.lu_peak_fma_chains() == 16
 
 
 def test_header_compiles_as_c(tmp_path):

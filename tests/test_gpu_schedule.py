@@ -161,3 +161,60 @@ def test_tune_plan_and_nb_zero(lu):
                          lookahead=best.lookahead, tu_reserve=best.tu_reserve)
     assert i0 == i1 == 0 and np.array_equal(p0, p1) and np.array_equal(LU0, LU1)
     assert oracle.factor_error(A0, LU0, p0) <= 1e-5
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+@pytest.mark.parametrize("opts", [dict(nb=64), dict(nb=0, sched=[128, 64, 37, 256]), dict(nb=256)])
+def test_rtm_dag_identical_to_lookahead(lu, dtype, opts):
+    """The runtime-task schedule (a dependency DAG of PF(k), TU(k, j) and the
+    left interchanges, replayed as a CUDA graph) gives factors bit-identical
+    to the static look-ahead ones -- the same operations per element -- on the
+    first call (capture) and on a repeated call (replay), and meets the
+    oracle's criteria."""
+    n = 1300
+    A0 = synth.uniform_matrix(n, seed=75)
+    if dtype == torch.float32:
+        A0 = A0.astype(np.float32).astype(np.float64)
+    LU1, p1, i1 = factor(lu, A0, dtype, lookahead=1, **opts)
+    for _ in range(2):
+        LUr, pr, ir = factor(lu, A0, dtype, rtm=1, **opts)
+        assert ir == i1 == 0
+        assert np.array_equal(pr, p1) and np.array_equal(LUr, LU1)
+    _, piv_o, _, gap = oracle.getrf(A0)
+    sep = gap > TAU[dtype]
+    assert np.array_equal(pr[sep], piv_o[sep])
+    assert oracle.factor_error(A0, LUr, pr) <= BOUND[dtype]
+
+
+def test_rtm_designed_pivots_and_cholesky(lu):
+    """Designed interchange sequences come back exactly through the DAG
+    schedule, and the Cholesky factorization (elimination without
+    interchanges) under the DAG schedule equals its look-ahead result."""
+    import pivot_patterns as pp
+    for name in ("last_row", "mixed"):
+        A0, piv_expect = pp.patterned_matrix(name, 800, seed=23, panel=64)
+        LU, piv, info = factor(lu, A0, torch.float64, nb=64, rtm=1)
+        assert info == 0 and np.array_equal(piv, piv_expect), name
+        assert oracle.factor_error(A0, LU, piv) <= 1e-14
+    n = 900
+    S0 = synth.spd_matrix(n, seed=24)
+    outs = []
+    for o in (dict(nb=128), dict(nb=128, rtm=1)):
+        A = dev(S0, torch.float64)
+        info = torch.full((1,), -7, dtype=torch.int32, device="cuda")
+        lu.lu_potrf_ex(A, info, lu.default_opts(**o))
+        torch.cuda.synchronize()
+        assert int(info.item()) == 0
+        outs.append(np.tril(A.cpu().numpy()))
+    assert np.array_equal(outs[0], outs[1])
+    assert oracle.chol_error(S0, outs[1]) <= 1e-14
+
+
+def test_rtm_rejected_on_tensor_core_path(lu):
+    n = 512
+    A = dev(synth.normal_matrix(n, seed=76), torch.float32)
+    ipiv = torch.zeros(n, dtype=torch.int32, device="cuda")
+    info = torch.zeros(1, dtype=torch.int32, device="cuda")
+    with pytest.raises(lu.LuError) as e:
+        lu.lu_factor_mixed_ex(A, ipiv, info, lu.LU_TU_BF16X6, lu.default_opts(nb=128, rtm=1))
+    assert e.value.code == lu.LU_ERR_UNSUPPORTED
