@@ -474,6 +474,32 @@ int lu_tune_save(const char *path);
 int lu_tune_load(const char *path);
 
 /*
+ * lu_geqrf_ex -- Householder QR of an m x n matrix, A = Q R, on the blocked
+ * look-ahead skeleton of Sec. 4 (the paper's second factorization, Sec. 6.3;
+ * 4n^3/3 flops when m = n).  Per panel k: PF_k factors the panel column by
+ * column (reflector H_j = I - tau_j v_j v_j^T mapping the updated column j onto
+ * beta e_j with beta = -sign(a_jj) ||x||, tau_j = 0 when nothing lies below
+ * the diagonal), then the compact-WY form Q_k = I - V_k T_k V_k^T; TU_k applies
+ * Q_k^T to the columns on the right as C -= V_k (T_k^T (V_k^T C)).  With
+ * look-ahead, TU_k on panel k+1 and PF_{k+1} overlap TU_k on the rest.
+ *   dtype  LU_F64 or LU_F32; A (device, column-major, lda >= max(1, m)) is
+ *          overwritten in LAPACK geqrf layout: R on and above the diagonal, v_j
+ *          below it (v_j(j) = 1 implied)
+ *   tau    device array of min(m, n) scalars of the same type (out)
+ *   opts   nb 1..128 (0 or NULL: 128), lookahead 0 or 1, a schedule of widths
+ *          <= 128; other fields ignored
+ *   info   device int32 (out): 0, or LU_ERR_TIMEOUT if a bounded wait of the
+ *          panel gave up
+ * Workspace (the explicit V blocks, T factors, products, split-K partials)
+ * belongs to the handle.  Asynchronous on the handle's stream.  Returns 0, -i
+ * for an invalid argument, LU_ERR_UNSUPPORTED (nb > 128, depth 2, the task-DAG
+ * schedule, or a panel too tall for one co-resident grid: m beyond ~50000 in
+ * FP64), LU_ERR_NOMEM or LU_ERR_CUDA.
+ */
+int lu_geqrf_ex(lu_handle handle, lu_dtype dtype, int64_t m, int64_t n, void *A, int64_t lda, void *tau,
+                const lu_opts *opts, int32_t *info);
+
+/*
  * lu_tune_plan -- tune the whole schedule of the factorization of `kind` at
  * order n on a seeded synthetic matrix (iid U[-1,1)), in four measured stages:
  *   1. the block size b among 128, 192, 256, 320, 384, 512 (multiples of 64,

@@ -351,3 +351,14 @@ def lu_step_trace_read(handle: Handle | None = None):
     L.lu_step_trace_read(h.ptr, cnt, k0, kb, sp, pu, tu)
     return [{"k0": int(k0[i]), "kb": int(kb[i]), "span_ms": float(sp[i]), "pu_ms": float(pu[i]),
              "tu_ms": float(tu[i])} for i in range(cnt)]
+
+
+def lu_geqrf_ex(A: torch.Tensor, tau: torch.Tensor, info: torch.Tensor, opts: LuOpts | None = None,
+                handle: Handle | None = None) -> None:
+    """In-place Householder QR (LAPACK geqrf layout) of a column-major FP64/FP32
+    m x n matrix; tau receives min(m, n) reflector scalars (nb <= 128)."""
+    h = _handle(handle)
+    o = opts if opts is not None else default_opts(nb=128)
+    m, n = A.shape
+    _check("lu_geqrf_ex", lib().lu_geqrf_ex(h.ptr, _DT[A.dtype], m, n, _p(A), _ld(A, "A"), _p(tau),
+                                            ctypes.byref(o), _p(info)))

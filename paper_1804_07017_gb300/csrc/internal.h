@@ -74,7 +74,7 @@ struct lu_context {
     // and the DAG's instantiated graph with the arguments it was captured for.
     std::vector<cudaStream_t> rtm_cols;
     cudaStream_t rtm_left = nullptr, rtm_origin = nullptr;
-    std::vector<cudaEvent_t> rtm_pf, rtm_col;
+    std::vector<cudaEvent_t> rtm_pf, rtm_col, rtm_sev;
     cudaEvent_t rtm_ev = nullptr, rtm_ev2 = nullptr;
     cudaGraphExec_t rtm_exec = nullptr;
     uint64_t rtm_key[12] = {};

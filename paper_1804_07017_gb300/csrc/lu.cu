@@ -143,11 +143,12 @@ int lu_ctx_release(lu_context* c) {
     for (cudaStream_t x : {c->rtm_left, c->rtm_origin})
         if (x) cudaStreamDestroy(x);
     c->rtm_left = c->rtm_origin = nullptr;
-    for (auto* v : {&c->rtm_pf, &c->rtm_col})
+    for (auto* v : {&c->rtm_pf, &c->rtm_col, &c->rtm_sev})
         for (cudaEvent_t e : *v)
             if (e) cudaEventDestroy(e);
     c->rtm_pf.clear();
     c->rtm_col.clear();
+    c->rtm_sev.clear();
     for (cudaEvent_t e : {c->rtm_ev, c->rtm_ev2})
         if (e) cudaEventDestroy(e);
     c->rtm_ev = c->rtm_ev2 = nullptr;

@@ -1,0 +1,489 @@
+// Householder QR (geqrf) on the same look-ahead skeleton as the LU: the
+// paper's second dense factorization (Sec. 6.3; 4n^3/3 flops for a square
+// matrix), reorganised exactly as Sec. 4 reorganises LU_blk.
+//
+// Step k, panel k = columns [k0, k0+kb):
+//   PF_k  A(k0:m, panel) = Q_k R_k with Q_k = H_k0 ... H_{k0+kb-1},
+//         H_j = I - tau_j v_j v_j^T (LAPACK layout: R on and above the diagonal,
+//         v_j below it with v_j(j) = 1 implied); then the compact-WY factor T_k
+//         (Q_k = I - V_k T_k V_k^T, T_k upper triangular) and V_k made explicit.
+//   TU_k  A(k0:m, c) := Q_k^T A(k0:m, c) = A - V_k (T_k^T (V_k^T A)) for the
+//         columns c right of the panel: two products with V_k^T / T_k^T (a
+//         transposed-operand GEMM, split along its long inner dimension with a
+//         fixed-order reduction) and C -= V_k W (the LU's RL3 kernel).
+// With look-ahead, TU_k on panel k+1 and PF_{k+1} run on the high-priority
+// stream while TU_k on the remaining columns runs on the other stream.
+//
+// The panel leaf (up to 64 columns) keeps its rows in shared memory across a
+// grid of co-resident CTAs; per column: every CTA sums the squares of its part
+// of the column, one grid barrier, every CTA forms the reflector (norm, beta,
+// tau, the scaling) from the same fixed-order sum, every CTA forms its part of
+// w = v^T A for the columns to the right, a second barrier, the rank-1 update.
+// Wider panels split in two halves with a block-reflector update between them.
+#include <math.h>
+
+#include <cstring>
+
+#include "internal.h"
+#include "profile.h"
+
+namespace {
+
+constexpr int kQrThreads = 256;
+constexpr int kQrMaxLeaf = 64;
+
+template <typename T>
+__device__ __forceinline__ T block_sum(T v, T* red) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    T s = T(0);
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s += red[i];  // fixed order, same in every thread
+    return s;
+}
+
+// Leaf: Householder QR of the m x w block at A (w <= kQrMaxLeaf), rows split
+// across gridDim.x CTAs of R rows.  slots (global): [2][G] partial sums of
+// squares, [2] alpha, [G][kQrMaxLeaf] partial dot products.
+template <typename T>
+__global__ void __launch_bounds__(kQrThreads) qr_leaf_kernel(T* __restrict__ A, int64_t lda, int m, int w, int R,
+                                                             T* __restrict__ tau, LuSync* __restrict__ sync,
+                                                             T* __restrict__ slots) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* sA = reinterpret_cast<T*>(smem_raw);  // [w][R] this CTA's rows, column-major
+    __shared__ T red[kQrThreads / 32];
+    __shared__ T red2[kQrThreads / 32][kQrMaxLeaf];
+    __shared__ T sh_w[kQrMaxLeaf];
+    __shared__ int sh_flag;
+    const int G = gridDim.x, g = blockIdx.x, tid = threadIdx.x;
+    const int row0 = g * R;
+    const int nrows = max(0, min(R, m - row0));
+    // the sums of squares and alpha alternate between two buffers by column parity:
+    // a column without a reflector passes only one barrier, so the next column's
+    // writes must not land where a slower CTA may still be reading
+    T* s_ss = slots;                 // [2][G]
+    T* s_alpha = slots + 2 * G;      // [2]
+    T* s_w = slots + 2 * G + 2;      // [G][kQrMaxLeaf]
+    const int lane = tid & 31, warp = tid >> 5;
+    for (int c = 0; c < w; ++c)
+        for (int r = tid; r < nrows; r += kQrThreads) sA[c * R + r] = A[(int64_t)(row0 + r) + (int64_t)c * lda];
+    __syncthreads();
+    unsigned int target = 0;
+    bool ok = true;
+    const int kmax = min(m, w);
+    for (int jj = 0; jj < kmax && ok; ++jj) {
+        // 1. partial sum of squares below the diagonal; the owner of row jj publishes alpha
+        T ss = T(0);
+        for (int r = tid; r < nrows; r += kQrThreads) {
+            const int gr = row0 + r;
+            if (gr > jj) {
+                const T x = sA[jj * R + r];
+                ss = fma(x, x, ss);
+            }
+        }
+        ss = block_sum(ss, red);
+        const int par = jj & 1;
+        if (tid == 0) {
+            s_ss[par * G + g] = ss;
+            if (jj >= row0 && jj < row0 + nrows) s_alpha[par] = sA[jj * R + (jj - row0)];
+        }
+        target += G;
+        if (!lu_grid_barrier(sync, target, &sh_flag)) {
+            ok = false;
+            break;
+        }
+        // 2. the reflector, formed identically in every CTA from the fixed-order sum
+        T sum = T(0);
+        for (int q = 0; q < G; ++q) sum += __ldcg(&s_ss[par * G + q]);
+        const T alpha = __ldcg(&s_alpha[par]);
+        if (sum == T(0)) {
+            // nothing below the diagonal: H_j = I (tau = 0), the column stays as it is
+            if (g == 0 && tid == 0) tau[jj] = T(0);
+            continue;
+        }
+        const T norm = sqrt(fma(alpha, alpha, sum));
+        const T beta = alpha >= T(0) ? -norm : norm;
+        const T t = (beta - alpha) / beta;
+        const T scale = T(1) / (alpha - beta);
+        if (g == 0 && tid == 0) tau[jj] = t;
+        for (int r = tid; r < nrows; r += kQrThreads) {
+            const int gr = row0 + r;
+            if (gr > jj) sA[jj * R + r] *= scale;
+            else if (gr == jj) sA[jj * R + r] = beta;
+        }
+        __syncthreads();
+        // 3. partial w_c = A(jj, c) + sum_{i > jj} v_i A(i, c) for the columns right of jj
+        for (int c = jj + 1; c < w; ++c) {
+            T acc = T(0);
+            for (int r = tid; r < nrows; r += kQrThreads) {
+                const int gr = row0 + r;
+                if (gr > jj) acc = fma(sA[jj * R + r], sA[c * R + r], acc);
+                else if (gr == jj) acc += sA[c * R + r];
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+            if (lane == 0) red2[warp][c] = acc;
+        }
+        __syncthreads();
+        for (int c = jj + 1 + tid; c < w; c += kQrThreads) {
+            T acc = T(0);
+            for (int q = 0; q < kQrThreads / 32; ++q) acc += red2[q][c];
+            s_w[g * kQrMaxLeaf + c] = acc;
+        }
+        target += G;
+        if (!lu_grid_barrier(sync, target, &sh_flag)) {
+            ok = false;
+            break;
+        }
+        for (int c = jj + 1 + tid; c < w; c += kQrThreads) {
+            T s = T(0);
+            for (int q = 0; q < G; ++q) s += __ldcg(&s_w[q * kQrMaxLeaf + c]);
+            sh_w[c] = t * s;
+        }
+        __syncthreads();
+        // 4. rank-1 update A(jj:, c) -= v (tau w_c)
+        for (int c = jj + 1; c < w; ++c) {
+            const T tw = sh_w[c];
+            for (int r = tid; r < nrows; r += kQrThreads) {
+                const int gr = row0 + r;
+                if (gr > jj) sA[c * R + r] = fma(-sA[jj * R + r], tw, sA[c * R + r]);
+                else if (gr == jj) sA[c * R + r] -= tw;
+            }
+        }
+        __syncthreads();
+    }
+    if (ok)
+        for (int c = 0; c < w; ++c)
+            for (int r = tid; r < nrows; r += kQrThreads) A[(int64_t)(row0 + r) + (int64_t)c * lda] = sA[c * R + r];
+    lu_grid_exit(sync);
+}
+
+// Transposed-operand product P_s = A(K_s rows, M cols)^T B(K_s rows, N cols)
+// for the s-th of S slices of the inner dimension K (blockIdx.z): 64 x 64
+// output tiles, 16-deep K steps staged in shared memory, 4 x 4 outputs per
+// thread.  With S = 1 the tile is written to C directly, else to the partial
+// buffer P[s] (M x N, ld = M) for qr_splitk_reduce.
+constexpr int kTnBM = 64, kTnBN = 64, kTnBK = 16;
+
+template <typename T>
+__global__ void __launch_bounds__(256) gemm_tn_kernel(int M, int N, int64_t K, int64_t kslice, const T* __restrict__ A,
+                                                      int64_t lda, const T* __restrict__ B, int64_t ldb,
+                                                      T* __restrict__ C, int64_t ldc) {
+    __shared__ T sA[kTnBK][kTnBM + 1];  // sA[k][i] = A(k0 + k, i0 + i)
+    __shared__ T sB[kTnBK][kTnBN + 1];  // sB[k][j] = B(k0 + k, j0 + j)
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const int i0 = blockIdx.x * kTnBM, j0 = blockIdx.y * kTnBN;
+    const int64_t kb = (int64_t)blockIdx.z * kslice, ke = min(K, kb + kslice);
+    T acc[4][4];
+#pragma unroll
+    for (int x = 0; x < 4; ++x)
+#pragma unroll
+        for (int y = 0; y < 4; ++y) acc[x][y] = T(0);
+    for (int64_t k0 = kb; k0 < ke; k0 += kTnBK) {
+        // 256 threads load 16 x 64 of each operand: thread t takes row t % 16, 4 columns
+        for (int e = tid; e < kTnBK * kTnBM; e += 256) {
+            const int kk = e % kTnBK, ii = e / kTnBK;
+            const int64_t k = k0 + kk;
+            sA[kk][ii] = (k < ke && i0 + ii < M) ? A[k + (int64_t)(i0 + ii) * lda] : T(0);
+            sB[kk][ii] = (k < ke && j0 + ii < N) ? B[k + (int64_t)(j0 + ii) * ldb] : T(0);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < kTnBK; ++kk) {
+            T a[4], b[4];
+#pragma unroll
+            for (int x = 0; x < 4; ++x) a[x] = sA[kk][tx + 16 * x];
+#pragma unroll
+            for (int y = 0; y < 4; ++y) b[y] = sB[kk][ty + 16 * y];
+#pragma unroll
+            for (int x = 0; x < 4; ++x)
+#pragma unroll
+                for (int y = 0; y < 4; ++y) acc[x][y] = fma(a[x], b[y], acc[x][y]);
+        }
+        __syncthreads();
+    }
+    T* out = C + (gridDim.z > 1 ? (int64_t)blockIdx.z * M * N : 0);
+    const int64_t ldo = gridDim.z > 1 ? (int64_t)M : ldc;
+#pragma unroll
+    for (int x = 0; x < 4; ++x)
+#pragma unroll
+        for (int y = 0; y < 4; ++y) {
+            const int i = i0 + tx + 16 * x, j = j0 + ty + 16 * y;
+            if (i < M && j < N) out[i + (int64_t)j * ldo] = acc[x][y];
+        }
+}
+
+// C(M x N) = sum over s = 0 .. S-1 of P[s], in that order (deterministic).
+template <typename T>
+__global__ void qr_splitk_reduce(int M, int N, int S, const T* __restrict__ P, T* __restrict__ C, int64_t ldc) {
+    const int64_t total = (int64_t)M * N;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        T s = T(0);
+        for (int q = 0; q < S; ++q) s += P[(int64_t)q * total + e];
+        const int64_t i = e % M, j = e / M;
+        C[i + j * ldc] = s;
+    }
+}
+
+// V (m x w, ld = ldv) := the unit lower trapezoidal reflector block stored
+// below the diagonal of A(m x w): ones on the diagonal, zeros above it.
+template <typename T>
+__global__ void qr_extract_v(int64_t m, int w, const T* __restrict__ A, int64_t lda, T* __restrict__ V, int64_t ldv) {
+    const int64_t total = m * w;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = e % m;
+        const int j = (int)(e / m);
+        V[i + (int64_t)j * ldv] = i > j ? A[i + (int64_t)j * lda] : (i == j ? T(1) : T(0));
+    }
+}
+
+// Compact-WY factor (larft, forward, columnwise) from the Gram matrix
+// Gm = V^T V (w x w) and tau: T(j, j) = tau_j and, for i < j,
+// T(0:j, j) = -tau_j T(0:j, 0:j) Gm(0:j, j); the strict lower part is zeroed.
+// One CTA; column j depends on the columns before it.
+template <typename T>
+__global__ void __launch_bounds__(256) qr_larft_kernel(int w, const T* __restrict__ Gm, int64_t ldg,
+                                                       const T* __restrict__ tau, T* __restrict__ Tm, int64_t ldt) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* sT = reinterpret_cast<T*>(smem_raw);  // [w][w] column-major
+    T* z = sT + (size_t)w * w;               // [w]
+    for (int e = threadIdx.x; e < w * w; e += blockDim.x) sT[e] = T(0);
+    __syncthreads();
+    for (int j = 0; j < w; ++j) {
+        const T tj = tau[j];
+        for (int i = threadIdx.x; i < j; i += blockDim.x) z[i] = Gm[i + (int64_t)j * ldg];
+        __syncthreads();
+        // T(0:j, j) = -tau_j T(0:j, 0:j) z, T upper triangular: row i sums over l >= i
+        for (int i = threadIdx.x; i < j; i += blockDim.x) {
+            T s = T(0);
+            for (int l = i; l < j; ++l) s = fma(sT[i + l * w], z[l], s);
+            sT[i + j * w] = -tj * s;
+        }
+        if (threadIdx.x == 0) sT[j + j * w] = tj;
+        __syncthreads();
+    }
+    for (int e = threadIdx.x; e < w * w; e += blockDim.x) Tm[(e % w) + (int64_t)(e / w) * ldt] = sT[e];
+}
+
+}  // namespace
+
+namespace {
+
+constexpr int64_t kQrPartCap = 2 << 20;  // elements of one split-K partial buffer
+
+// Workspace of one QR factorization, carved from the handle's device buffer.
+template <typename T>
+struct QrWork {
+    T* V[2];      // explicit reflector blocks of panels k (parity), m x nbmax
+    T* Tm[2];     // their compact-WY factors, nbmax x nbmax
+    T* Vp;        // left half of a split panel, m x kQrMaxLeaf
+    T* Tp;        // its factor, kQrMaxLeaf^2
+    T* Gm;        // Gram matrix V^T V, nbmax^2
+    T* Whi[2];    // V^T C and T^T (V^T C) on the panel stream, nbmax x nbmax
+    T* Wlo[2];    // the same on the update stream, nbmax x n
+    T* part[2];   // split-K partials: [0] panel stream, [1] update stream
+    int nbmax;
+    static size_t bytes(int64_t m, int64_t n, int nbmax) {
+        const size_t e = 2 * (size_t)m * nbmax + 2 * (size_t)nbmax * nbmax + (size_t)m * kQrMaxLeaf +
+                         (size_t)kQrMaxLeaf * kQrMaxLeaf + (size_t)nbmax * nbmax + 2 * (size_t)nbmax * nbmax +
+                         2 * (size_t)nbmax * n + 2 * (size_t)kQrPartCap + 16 * 8;
+        return e * sizeof(T) + 16 * 256;
+    }
+    void carve(char* base, int64_t m, int64_t n, int nb) {
+        nbmax = nb;
+        size_t off = 0;
+        auto take = [&](size_t elems) {
+            T* p = reinterpret_cast<T*>(base + off);
+            off += (elems * sizeof(T) + 255) / 256 * 256;
+            return p;
+        };
+        for (int i = 0; i < 2; ++i) V[i] = take((size_t)m * nb);
+        for (int i = 0; i < 2; ++i) Tm[i] = take((size_t)nb * nb);
+        Vp = take((size_t)m * kQrMaxLeaf);
+        Tp = take((size_t)kQrMaxLeaf * kQrMaxLeaf);
+        Gm = take((size_t)nb * nb);
+        for (int i = 0; i < 2; ++i) Whi[i] = take((size_t)nb * nb);
+        for (int i = 0; i < 2; ++i) Wlo[i] = take((size_t)nb * n);
+        for (int i = 0; i < 2; ++i) part[i] = take((size_t)kQrPartCap);
+    }
+};
+
+// C(M x N) = A^T B with A (K x M) and B (K x N), split along K when the output
+// has too few tiles to fill the GPU.
+template <typename T>
+int qr_gemm_tn(lu_context* c, cudaStream_t st, int M, int N, int64_t K, const T* A, int64_t lda, const T* B,
+               int64_t ldb, T* C, int64_t ldc, T* part) {
+    if (M <= 0 || N <= 0) return LU_SUCCESS;
+    const int64_t tiles = lu_cdiv(M, kTnBM) * lu_cdiv(N, kTnBN);
+    int64_t S = 1;
+    if (tiles < 2 * (int64_t)c->num_sms && K > 512)
+        S = std::min<int64_t>(lu_cdiv(2 * (int64_t)c->num_sms, tiles), lu_cdiv(K, 256));
+    S = std::max<int64_t>(1, std::min<int64_t>({S, kQrPartCap / ((int64_t)M * N), 65535}));
+    const int64_t kslice = lu_cdiv(lu_cdiv(std::max<int64_t>(K, 1), S), kTnBK) * kTnBK;
+    S = std::max<int64_t>(1, lu_cdiv(std::max<int64_t>(K, 1), kslice));
+    LuProfScope prof(st, LU_K_GEMM, sizeof(T) * ((double)K * (M + N) + (double)M * N), 2.0 * M * N * K);
+    const dim3 grid((unsigned)lu_cdiv(M, kTnBM), (unsigned)lu_cdiv(N, kTnBN), (unsigned)S);
+    gemm_tn_kernel<T><<<grid, 256, 0, st>>>(M, N, K, kslice, A, lda, B, ldb, S > 1 ? part : C, ldc);
+    LU_CHECK_LAUNCH();
+    if (S > 1) {
+        const int64_t total = (int64_t)M * N;
+        qr_splitk_reduce<T><<<(unsigned)std::min<int64_t>(lu_cdiv(total, 256), 4 * (int64_t)c->num_sms), 256, 0, st>>>(
+            M, N, (int)S, part, C, ldc);
+        LU_CHECK_LAUNCH();
+    }
+    return LU_SUCCESS;
+}
+
+// Q^T applied to columns [cb, ce) of rows [r0, m): C -= V (T^T (V^T C)),
+// V (m - r0) x kb with ld ldv, T kb x kb with ld kb.
+template <typename T>
+int qr_apply(lu_context* c, cudaStream_t st, T* A, int64_t lda, int64_t m, int64_t r0, int kb, int64_t cb,
+             int64_t ce, const T* V, int64_t ldv, const T* Tm, T* W, T* W2, T* part) {
+    const int64_t rows = m - r0, nc = ce - cb;
+    if (nc <= 0 || rows <= 0 || kb <= 0) return LU_SUCCESS;
+    T* C = A + r0 + cb * lda;
+    LU_TRY(qr_gemm_tn<T>(c, st, kb, (int)nc, rows, V, ldv, C, lda, W, kb, part));
+    LU_TRY(qr_gemm_tn<T>(c, st, kb, (int)nc, kb, Tm, kb, W, kb, W2, kb, part));
+    return lu_launch_gemm_update<T>(st, rows, nc, kb, V, ldv, W2, kb, C, lda);
+}
+
+// Explicit V (rows x w) and its factor T (w x w) for reflectors already in A(r0:m, j0:j0+w).
+template <typename T>
+int qr_form_vt(lu_context* c, cudaStream_t st, const T* A, int64_t lda, int64_t m, int64_t r0, int64_t j0, int w,
+               const T* tau, T* V, T* Tm, T* Gm, T* part) {
+    const int64_t rows = m - r0;
+    {
+        LuProfScope prof(st, LU_K_OTHER, 2.0 * sizeof(T) * rows * w, 0.0);
+        qr_extract_v<T><<<(unsigned)std::min<int64_t>(lu_cdiv(rows * w, 256), 4 * (int64_t)c->num_sms), 256, 0, st>>>(
+            rows, w, A + r0 + j0 * lda, lda, V, rows);
+        LU_CHECK_LAUNCH();
+    }
+    LU_TRY(qr_gemm_tn<T>(c, st, w, w, rows, V, rows, V, rows, Gm, w, part));
+    const size_t smem = sizeof(T) * ((size_t)w * w + w);
+    LU_TRY(lu_func_smem(qr_larft_kernel<T>, (int)smem));
+    LuProfScope prof(st, LU_K_OTHER, sizeof(T) * 2.0 * w * w, (double)w * w * w / 3.0);
+    qr_larft_kernel<T><<<1, 256, smem, st>>>(w, Gm, w, tau + j0, Tm, w);
+    LU_CHECK_LAUNCH();
+    return LU_SUCCESS;
+}
+
+template <typename T>
+int qr_leaf(lu_context* c, cudaStream_t st, T* A, int64_t lda, int64_t m, int64_t j0, int w, T* tau) {
+    const int64_t rows = m - j0;
+    if (rows <= 0 || w <= 0) return LU_SUCCESS;
+    const int64_t G0 = std::min<int64_t>({(int64_t)c->num_sms, (int64_t)LU_PF_MAX_CTAS, lu_cdiv(rows, 32)});
+    const int64_t R = lu_cdiv(lu_cdiv(rows, G0), 32) * 32;
+    const int64_t G = lu_cdiv(rows, R);
+    const size_t smem = sizeof(T) * (size_t)R * w;
+    if (smem > 200 * 1024 || G > LU_PF_MAX_CTAS) return LU_ERR_UNSUPPORTED;
+    LU_TRY(lu_func_smem(qr_leaf_kernel<T>, (int)smem));
+    LuProfScope prof(st, LU_K_PANEL, 2.0 * sizeof(T) * rows * w, 2.0 * rows * w * w);
+    qr_leaf_kernel<T><<<(unsigned)G, kQrThreads, smem, st>>>(A + j0 + j0 * lda, lda, (int)rows, w, (int)R, tau + j0,
+                                                             &c->sync[0], reinterpret_cast<T*>(c->pf_slots));
+    LU_CHECK_LAUNCH();
+    return LU_SUCCESS;
+}
+
+// PF: Householder QR of columns [j0, j0+w) over rows [j0, m); w <= 2 * kQrMaxLeaf.
+template <typename T>
+int qr_panel(lu_context* c, cudaStream_t st, T* A, int64_t lda, int64_t m, int64_t j0, int w, T* tau, QrWork<T>& wk) {
+    if (w <= kQrMaxLeaf) return qr_leaf<T>(c, st, A, lda, m, j0, w, tau);
+    const int w1 = kQrMaxLeaf;
+    LU_TRY(qr_leaf<T>(c, st, A, lda, m, j0, w1, tau));
+    LU_TRY(qr_form_vt<T>(c, st, A, lda, m, j0, j0, w1, tau, wk.Vp, wk.Tp, wk.Gm, wk.part[0]));
+    LU_TRY(qr_apply<T>(c, st, A, lda, m, j0, w1, j0 + w1, j0 + w, wk.Vp, m - j0, wk.Tp, wk.Whi[0], wk.Whi[1],
+                       wk.part[0]));
+    return qr_leaf<T>(c, st, A, lda, m, j0 + w1, w - w1, tau);
+}
+
+}  // namespace
+
+template <typename T>
+static int qr_factor(lu_context* c, int64_t m, int64_t n, T* A, int64_t lda, T* tau, const lu_opts& o,
+                     int32_t* info) {
+    const int64_t kmax = std::min(m, n);
+    std::vector<int64_t> s;
+    int wmin = 1, wmax = 1;
+    lu_panel_bounds(kmax, o, &s, &wmin, &wmax);
+    if (wmax > 2 * kQrMaxLeaf) return LU_ERR_UNSUPPORTED;
+    LU_TRY(lu_ctx_reserve(c, std::max(m, n), wmin));
+    LU_TRY(lu_mx_reserve(c, QrWork<T>::bytes(m, n, wmax)));
+    QrWork<T> wk;
+    wk.carve((char*)c->mx, m, n, wmax);
+    cudaStream_t user = c->user;
+    LU_CHECK_CUDA(cudaMemsetAsync(&c->sync[0], 0, sizeof(LuSync), user));
+    if (kmax == 0) return lu_launch_finish_info(user, &c->sync[0], info);
+    LU_CHECK_CUDA(cudaEventRecord(c->ev_fork, user));
+    LU_CHECK_CUDA(cudaStreamWaitEvent(c->hi, c->ev_fork, 0));
+    LU_CHECK_CUDA(cudaStreamWaitEvent(c->lo, c->ev_fork, 0));
+    const int64_t nk = (int64_t)s.size() - 1;
+    cudaStream_t hi = c->hi, lo = c->lo;
+    auto width = [&](int64_t k) { return (int)(s[(size_t)k + 1] - s[(size_t)k]); };
+    // PF_k, then V_k and T_k (parity k) for the updates of step k
+    auto panel = [&](int64_t k) -> int {
+        const int64_t k0 = s[(size_t)k];
+        LU_TRY(qr_panel<T>(c, hi, A, lda, m, k0, width(k), tau, wk));
+        if (k0 + width(k) < n)
+            LU_TRY(qr_form_vt<T>(c, hi, A, lda, m, k0, k0, width(k), tau, wk.V[k & 1], wk.Tm[k & 1], wk.Gm,
+                                 wk.part[0]));
+        return LU_SUCCESS;
+    };
+    // TU_k on columns [cb, ce): on the panel stream with its buffers (which = 0) or the other (1)
+    auto tu = [&](cudaStream_t st, int64_t k, int64_t cb, int64_t ce, int which) -> int {
+        const int64_t k0 = s[(size_t)k];
+        T** W = which ? wk.Wlo : wk.Whi;
+        return qr_apply<T>(c, st, A, lda, m, k0, width(k), cb, ce, wk.V[k & 1], m - k0, wk.Tm[k & 1], W[0], W[1],
+                           wk.part[which]);
+    };
+    LU_TRY(panel(0));
+    for (int64_t k = 0; k < nk; ++k) {
+        const int64_t c1 = s[(size_t)k + 1];                                // first column right of panel k
+        const int64_t c2 = k + 1 < nk ? s[(size_t)k + 2] : c1;             // end of panel k+1
+        if (o.lookahead) {
+            // PU(k+1) = TU_k on panel k+1, then PF_{k+1}, beside TU_k on the rest
+            if (k + 1 < nk) LU_TRY(tu(hi, k, c1, c2, 0));
+            LU_CHECK_CUDA(cudaEventRecord(c->ev_pf, hi));
+            LU_CHECK_CUDA(cudaStreamWaitEvent(lo, c->ev_pf, 0));
+            LU_TRY(tu(lo, k, c2, n, 1));
+            LU_CHECK_CUDA(cudaEventRecord(c->ev_tu, lo));
+            if (k + 1 < nk) {
+                LU_TRY(panel(k + 1));
+                LU_CHECK_CUDA(cudaStreamWaitEvent(hi, c->ev_tu, 0));
+            }
+        } else {
+            LU_TRY(tu(hi, k, c1, n, 0));
+            if (k + 1 < nk) LU_TRY(panel(k + 1));
+        }
+    }
+    LU_CHECK_CUDA(cudaEventRecord(c->ev_join_hi, hi));
+    LU_CHECK_CUDA(cudaEventRecord(c->ev_join_lo, lo));
+    LU_CHECK_CUDA(cudaStreamWaitEvent(user, c->ev_join_hi, 0));
+    LU_CHECK_CUDA(cudaStreamWaitEvent(user, c->ev_join_lo, 0));
+    return lu_launch_finish_info(user, &c->sync[0], info);
+}
+
+extern "C" int lu_geqrf_ex(lu_handle h, lu_dtype dtype, int64_t m, int64_t n, void* A, int64_t lda, void* tau,
+                           const lu_opts* opts, int32_t* info) {
+    if (!h) return LU_ERR_HANDLE;
+    if (dtype != LU_F64 && dtype != LU_F32) return -2;
+    if (m < 0) return -3;
+    if (n < 0) return -4;
+    if (m > 0 && n > 0 && !A) return -5;
+    if (lda < std::max<int64_t>(1, m)) return -6;
+    if (std::min(m, n) > 0 && !tau) return -7;
+    lu_opts o;
+    lu_default_opts(&o);
+    o.nb = 128;
+    if (opts) o = *opts;
+    if (lu_check_opts(o) != 0) return -8;
+    if (!info) return -9;
+    if (o.nb == 0) o.nb = 128;
+    if (o.lookahead > 1 || o.rtm) return LU_ERR_UNSUPPORTED;
+    if (m > INT32_MAX / 2 || n > INT32_MAX / 2) return LU_ERR_UNSUPPORTED;
+    std::lock_guard<std::mutex> lk(h->mu);
+    if (dtype == LU_F64) return qr_factor<double>(h, m, n, (double*)A, lda, (double*)tau, o, info);
+    return qr_factor<float>(h, m, n, (float*)A, lda, (float*)tau, o, info);
+}

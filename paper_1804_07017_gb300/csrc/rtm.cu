@@ -8,7 +8,9 @@
 //              column block, RL2 on its block row and RL3 below it;
 //   LS(k)      panel k's interchanges on the columns left of the panel.
 // Dependencies: TU(k, j) needs PF(k) and TU(k-1, j); PF(k+1) needs TU(k, k+1);
-// LS(k) needs PF(k) (which follows every update of the columns it moves).
+// LS(k) needs PF(k) (which follows every update of the columns it moves) and
+// every TU(k-1, j): those read the L21 blocks of the earlier panels, whose rows
+// LS(k) exchanges.
 //
 // On the GPU the runtime is the CUDA graph executor: the DAG is captured once
 // across one stream per block-column class (tasks of one column stay ordered
@@ -37,6 +39,11 @@ int rtm_resources(lu_context* c, int64_t nk) {
     }
     if (!c->rtm_left) LU_CHECK_CUDA(cudaStreamCreateWithPriority(&c->rtm_left, cudaStreamNonBlocking, lo_prio));
     if (!c->rtm_origin) LU_CHECK_CUDA(cudaStreamCreateWithFlags(&c->rtm_origin, cudaStreamNonBlocking));
+    while ((int64_t)c->rtm_sev.size() < ncol) {
+        cudaEvent_t e = nullptr;
+        LU_CHECK_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        c->rtm_sev.push_back(e);
+    }
     for (auto* v : {&c->rtm_pf, &c->rtm_col})
         while ((int64_t)v->size() < nk + 1) {
             cudaEvent_t e = nullptr;
@@ -64,8 +71,18 @@ int issue(lu_context* c, cudaStream_t origin, const std::vector<int64_t>& s, int
     auto width = [&](int64_t k) { return s[(size_t)k + 1] - s[(size_t)k]; };
     LU_TRY(lu_step_pf<T>(c, hi, A, lda, n, 0, 0, width(0), ipiv, o, pivot));
     LU_CHECK_CUDA(cudaEventRecord(c->rtm_pf[0], hi));
+    std::vector<char> used((size_t)ncol, 0);
     for (int64_t k = 0; k < nk; ++k) {
         const int64_t k0 = s[(size_t)k], kb = width(k);
+        // LS(k): panel k's interchanges on the columns left of it, once PF(k) is
+        // done and every update of step k-1 (the last task on each column stream)
+        // has stopped reading the rows it moves
+        if (pivot && k0 > 0) {
+            LU_CHECK_CUDA(cudaStreamWaitEvent(left, c->rtm_pf[(size_t)k], 0));
+            for (int64_t q = 0; q < ncol; ++q)
+                if (used[(size_t)q]) LU_CHECK_CUDA(cudaStreamWaitEvent(left, c->rtm_sev[(size_t)q], 0));
+            LU_TRY(lu_step_tu<T>(c, left, n, A, lda, k, k0, kb, n, n, k0, pivot));
+        }
         // the critical chain: TU(k, k+1) after TU(k-1, k+1), then PF(k+1)
         if (k + 1 < nk) {
             if (k >= 1) LU_CHECK_CUDA(cudaStreamWaitEvent(hi, c->rtm_col[(size_t)k + 1], 0));
@@ -79,11 +96,9 @@ int issue(lu_context* c, cudaStream_t origin, const std::vector<int64_t>& s, int
             LU_CHECK_CUDA(cudaStreamWaitEvent(st, c->rtm_pf[(size_t)k], 0));
             LU_TRY(lu_step_tu<T>(c, st, n, A, lda, k, k0, kb, s[(size_t)j], s[(size_t)j + 1], 0, pivot));
             LU_CHECK_CUDA(cudaEventRecord(c->rtm_col[(size_t)j], st));
-        }
-        // LS(k): panel k's interchanges on the columns left of it
-        if (pivot && k0 > 0) {
-            LU_CHECK_CUDA(cudaStreamWaitEvent(left, c->rtm_pf[(size_t)k], 0));
-            LU_TRY(lu_step_tu<T>(c, left, n, A, lda, k, k0, kb, n, n, k0, pivot));
+            const int64_t q = j % ncol;
+            LU_CHECK_CUDA(cudaEventRecord(c->rtm_sev[(size_t)q], st));
+            used[(size_t)q] = 1;
         }
     }
     // join every forked stream back into the origin
