@@ -205,10 +205,10 @@ def main_with_args(argv):
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison path")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle sample")
     ap.add_argument("--workload", default="mixed",
-                    choices=["mixed", "batched", "configs", "tune", "chol", "profile"],
+                    choices=["mixed", "batched", "configs", "tune", "chol", "profile", "qr"],
                     help="mixed: the n=16384 solver (default); batched: 4096 uneven systems; "
                          "configs: the configuration comparisons; tune: the block-size sweeps; "
-                         "chol: the Cholesky factorization; profile: one kernel case (--case) for "
+                         "chol: the Cholesky factorization; qr: the Householder QR; profile: one kernel case (--case) for "
                          "profilers and event timing")
     ap.add_argument("--case", default="leaf", choices=sorted(PROFILE_CASES),
                     help="profile case: " + "; ".join(f"{k}: {v[1]}" for k, v in sorted(PROFILE_CASES.items())))
@@ -223,6 +223,8 @@ def main_with_args(argv):
         return summarize_launches(args.summarize_launches)
     if args.workload == "profile":
         return run_profile(args)
+    if args.workload == "qr":
+        return run_qr(args)
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "configs":
@@ -650,6 +652,39 @@ def run_profile(args):
         raise SystemExit("a CUDA device is required")
     dt = torch.float64 if args.dtype == "f64" else torch.float32
     PROFILE_CASES[args.case][0](args, lu, torch, dt)
+    return 0
+
+
+def run_qr(args):
+    """Householder QR (lu_geqrf_ex) on the look-ahead skeleton: FP64 n = 8192
+    and FP32 n = 16384, iid U[-1,1) (seed 0), look-ahead off and on, nb 64 and
+    128; the matrix is restored from a device copy before each run (outside the
+    timed region); median of three event-timed runs after one untimed run.
+    GFLOP/s of 4n^3/3.  One JSON object."""
+    import torch
+
+    import paper_1804_07017_gb300 as lu
+    import synth
+    torch.cuda.set_device(0)
+    out = {"metric": "QR GFLOP/s (4n^3/3)", "unit": "GFLOP/s", "data": "synthetic"}
+    for name, dt, n in (("fp64_n8192", torch.float64, 8192), ("fp32_n16384", torch.float32, 16384)):
+        if args.shape and str(n) not in args.shape.split(","):
+            continue
+        A0 = torch.from_numpy(synth.uniform_matrix(n, seed=0)).to(dt).cuda()
+        A = lu.api.colmajor(n, n, dtype=dt)
+        tau = torch.zeros(n, dtype=dt, device="cuda")
+        info = torch.zeros(1, dtype=torch.int32, device="cuda")
+        res = {}
+        for nb in (64, 128):
+            for la in (0, 1):
+                o = lu.default_opts(nb=nb, lookahead=la)
+                ms = _median_ms(lambda: lu.lu_geqrf_ex(A, tau, info, o), 4, before=lambda: A.copy_(A0))
+                res[f"nb{nb}_lookahead{la}"] = {"ms": round(ms, 3), "gflops": round(4.0 * n ** 3 / 3 / ms / 1e6, 1),
+                                                "info": int(info.item())}
+        out[name] = res
+        del A, A0
+        torch.cuda.empty_cache()
+    print(json.dumps(out))
     return 0
 
 
