@@ -19,9 +19,12 @@ __global__ void __launch_bounds__(256) fma_peak_kernel(int64_t iters, T b, T c, 
     T a[kChains];
 #pragma unroll
     for (int i = 0; i < kChains; ++i) a[i] = T(t % 97) * T(1e-3) + T(i);
+    // per-thread register operands (the products stay the same to rounding), so
+    // the FMAs read no constant-bank operand
+    const T bb = b + T(threadIdx.x & 1) * T(1e-30), cc = c + T(threadIdx.x & 2) * T(1e-30);
     for (int64_t it = 0; it < iters; ++it) {
 #pragma unroll
-        for (int i = 0; i < kChains; ++i) a[i] = fma(a[i], b, c);
+        for (int i = 0; i < kChains; ++i) a[i] = fma(a[i], bb, cc);
     }
     T s = T(0);
 #pragma unroll

@@ -161,58 +161,72 @@ __global__ void __launch_bounds__(kQrThreads) qr_leaf_kernel(T* __restrict__ A, 
     lu_grid_exit(sync);
 }
 
-// Transposed-operand product P_s = A(K_s rows, M cols)^T B(K_s rows, N cols)
-// for the s-th of S slices of the inner dimension K (blockIdx.z): 64 x 64
-// output tiles, 16-deep K steps staged in shared memory, 4 x 4 outputs per
-// thread.  With S = 1 the tile is written to C directly, else to the partial
-// buffer P[s] (M x N, ld = M) for qr_splitk_reduce.
-constexpr int kTnBM = 64, kTnBN = 64, kTnBK = 16;
+// Transposed-operand product C(M x N) = A(K x M)^T B(K x N): 64 x 64 output
+// tiles, 16-deep K steps staged in shared memory, 4 x 4 outputs per thread.
+// K is cut into fixed slices of kTnSlice rows; every slice's partial product
+// is summed from zero and the partials are added in slice order, whether one
+// CTA runs all slices (split = 0) or each slice has its own CTA (split = 1,
+// blockIdx.z = slice, partials to P[s] (M x N, ld = M) for qr_splitk_reduce).
+// So the result does not depend on how a product is cut into launches.
+constexpr int kTnBM = 64, kTnBN = 64, kTnBK = 16, kTnSlice = 256;
 
 template <typename T>
-__global__ void __launch_bounds__(256) gemm_tn_kernel(int M, int N, int64_t K, int64_t kslice, const T* __restrict__ A,
+__global__ void __launch_bounds__(256) gemm_tn_kernel(int M, int N, int64_t K, int split, const T* __restrict__ A,
                                                       int64_t lda, const T* __restrict__ B, int64_t ldb,
                                                       T* __restrict__ C, int64_t ldc) {
     __shared__ T sA[kTnBK][kTnBM + 1];  // sA[k][i] = A(k0 + k, i0 + i)
     __shared__ T sB[kTnBK][kTnBN + 1];  // sB[k][j] = B(k0 + k, j0 + j)
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
     const int i0 = blockIdx.x * kTnBM, j0 = blockIdx.y * kTnBN;
-    const int64_t kb = (int64_t)blockIdx.z * kslice, ke = min(K, kb + kslice);
-    T acc[4][4];
+    const int64_t nsl = (K + kTnSlice - 1) / kTnSlice;
+    const int64_t s0 = split ? (int64_t)blockIdx.z : 0, s1 = split ? s0 + 1 : nsl;
+    T tot[4][4];
 #pragma unroll
     for (int x = 0; x < 4; ++x)
 #pragma unroll
-        for (int y = 0; y < 4; ++y) acc[x][y] = T(0);
-    for (int64_t k0 = kb; k0 < ke; k0 += kTnBK) {
-        // 256 threads load 16 x 64 of each operand: thread t takes row t % 16, 4 columns
-        for (int e = tid; e < kTnBK * kTnBM; e += 256) {
-            const int kk = e % kTnBK, ii = e / kTnBK;
-            const int64_t k = k0 + kk;
-            sA[kk][ii] = (k < ke && i0 + ii < M) ? A[k + (int64_t)(i0 + ii) * lda] : T(0);
-            sB[kk][ii] = (k < ke && j0 + ii < N) ? B[k + (int64_t)(j0 + ii) * ldb] : T(0);
+        for (int y = 0; y < 4; ++y) tot[x][y] = T(0);
+    for (int64_t sl = s0; sl < s1; ++sl) {
+        const int64_t kb = sl * kTnSlice, ke = min(K, kb + kTnSlice);
+        T acc[4][4];
+#pragma unroll
+        for (int x = 0; x < 4; ++x)
+#pragma unroll
+            for (int y = 0; y < 4; ++y) acc[x][y] = T(0);
+        for (int64_t k0 = kb; k0 < ke; k0 += kTnBK) {
+            for (int e = tid; e < kTnBK * kTnBM; e += 256) {
+                const int kk = e % kTnBK, ii = e / kTnBK;
+                const int64_t k = k0 + kk;
+                sA[kk][ii] = (k < ke && i0 + ii < M) ? A[k + (int64_t)(i0 + ii) * lda] : T(0);
+                sB[kk][ii] = (k < ke && j0 + ii < N) ? B[k + (int64_t)(j0 + ii) * ldb] : T(0);
+            }
+            __syncthreads();
+#pragma unroll
+            for (int kk = 0; kk < kTnBK; ++kk) {
+                T a[4], b[4];
+#pragma unroll
+                for (int x = 0; x < 4; ++x) a[x] = sA[kk][tx + 16 * x];
+#pragma unroll
+                for (int y = 0; y < 4; ++y) b[y] = sB[kk][ty + 16 * y];
+#pragma unroll
+                for (int x = 0; x < 4; ++x)
+#pragma unroll
+                    for (int y = 0; y < 4; ++y) acc[x][y] = fma(a[x], b[y], acc[x][y]);
+            }
+            __syncthreads();
         }
-        __syncthreads();
 #pragma unroll
-        for (int kk = 0; kk < kTnBK; ++kk) {
-            T a[4], b[4];
+        for (int x = 0; x < 4; ++x)
 #pragma unroll
-            for (int x = 0; x < 4; ++x) a[x] = sA[kk][tx + 16 * x];
-#pragma unroll
-            for (int y = 0; y < 4; ++y) b[y] = sB[kk][ty + 16 * y];
-#pragma unroll
-            for (int x = 0; x < 4; ++x)
-#pragma unroll
-                for (int y = 0; y < 4; ++y) acc[x][y] = fma(a[x], b[y], acc[x][y]);
-        }
-        __syncthreads();
+            for (int y = 0; y < 4; ++y) tot[x][y] += acc[x][y];
     }
-    T* out = C + (gridDim.z > 1 ? (int64_t)blockIdx.z * M * N : 0);
-    const int64_t ldo = gridDim.z > 1 ? (int64_t)M : ldc;
+    T* out = split ? C + (int64_t)blockIdx.z * M * N : C;
+    const int64_t ldo = split ? (int64_t)M : ldc;
 #pragma unroll
     for (int x = 0; x < 4; ++x)
 #pragma unroll
         for (int y = 0; y < 4; ++y) {
             const int i = i0 + tx + 16 * x, j = j0 + ty + 16 * y;
-            if (i < M && j < N) out[i + (int64_t)j * ldo] = acc[x][y];
+            if (i < M && j < N) out[i + (int64_t)j * ldo] = tot[x][y];
         }
 }
 
@@ -318,20 +332,19 @@ int qr_gemm_tn(lu_context* c, cudaStream_t st, int M, int N, int64_t K, const T*
                int64_t ldb, T* C, int64_t ldc, T* part) {
     if (M <= 0 || N <= 0) return LU_SUCCESS;
     const int64_t tiles = lu_cdiv(M, kTnBM) * lu_cdiv(N, kTnBN);
-    int64_t S = 1;
-    if (tiles < 2 * (int64_t)c->num_sms && K > 512)
-        S = std::min<int64_t>(lu_cdiv(2 * (int64_t)c->num_sms, tiles), lu_cdiv(K, 256));
-    S = std::max<int64_t>(1, std::min<int64_t>({S, kQrPartCap / ((int64_t)M * N), 65535}));
-    const int64_t kslice = lu_cdiv(lu_cdiv(std::max<int64_t>(K, 1), S), kTnBK) * kTnBK;
-    S = std::max<int64_t>(1, lu_cdiv(std::max<int64_t>(K, 1), kslice));
+    const int64_t nsl = lu_cdiv(std::max<int64_t>(K, 1), kTnSlice);
+    // one CTA per K slice when the output alone has too few tiles to fill the GPU
+    // and the partials fit (the choice changes the speed, not the bits)
+    const bool split = tiles < 2 * (int64_t)c->num_sms && nsl > 1 && nsl <= 65535 &&
+                       nsl * (int64_t)M * N <= kQrPartCap;
     LuProfScope prof(st, LU_K_GEMM, sizeof(T) * ((double)K * (M + N) + (double)M * N), 2.0 * M * N * K);
-    const dim3 grid((unsigned)lu_cdiv(M, kTnBM), (unsigned)lu_cdiv(N, kTnBN), (unsigned)S);
-    gemm_tn_kernel<T><<<grid, 256, 0, st>>>(M, N, K, kslice, A, lda, B, ldb, S > 1 ? part : C, ldc);
+    const dim3 grid((unsigned)lu_cdiv(M, kTnBM), (unsigned)lu_cdiv(N, kTnBN), split ? (unsigned)nsl : 1u);
+    gemm_tn_kernel<T><<<grid, 256, 0, st>>>(M, N, K, split ? 1 : 0, A, lda, B, ldb, split ? part : C, ldc);
     LU_CHECK_LAUNCH();
-    if (S > 1) {
+    if (split) {
         const int64_t total = (int64_t)M * N;
         qr_splitk_reduce<T><<<(unsigned)std::min<int64_t>(lu_cdiv(total, 256), 4 * (int64_t)c->num_sms), 256, 0, st>>>(
-            M, N, (int)S, part, C, ldc);
+            M, N, (int)nsl, part, C, ldc);
         LU_CHECK_LAUNCH();
     }
     return LU_SUCCESS;

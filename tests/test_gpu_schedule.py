@@ -152,7 +152,7 @@ def test_tune_plan_and_nb_zero(lu):
     assert 0 < ms <= fixed
     plan = lu.lu_tune_plan_get(lu.LU_TU_BF16X6, n)
     assert plan is not None and plan[0] == best.nb and plan[3] == sched
-    assert best.lookahead in (1, 2) and best.tu_reserve >= 4
+    assert best.lookahead in (1, 2) and (best.tu_reserve == 0 or best.tu_reserve >= 4)  # 0: automatic
     print(f"\n[tune plan n={n} bf16x6] nb={best.nb} reserve={best.tu_reserve} depth={best.lookahead} "
           f"schedule={sched} best {ms:.2f} ms, fixed {fixed:.2f} ms")
     A0 = synth.normal_matrix(n, seed=74).astype(np.float32).astype(np.float64)
