@@ -474,6 +474,21 @@ int lu_tune_save(const char *path);
 int lu_tune_load(const char *path);
 
 /*
+ * lu_potrf_mixed_ex -- Cholesky A = L L^T of a symmetric positive definite FP32
+ * matrix (lu_potrf_ex's algorithm: elimination without interchanges on the
+ * look-ahead skeleton, only the lower block triangle updated, then L = L~ D^{1/2})
+ * with the trailing update A22 -= L21 U12 on the tensor cores in the operand
+ * precision prec (LU_TU_BF16X6 keeps FP32-level accuracy; LU_TU_F32 = the CUDA
+ * cores, as lu_potrf_ex).  The update takes only the tiles on or below the
+ * diagonal panel blocks (n^3/3 flops).  Arguments, layout, info and return codes
+ * as lu_potrf_ex; opts.nb must be a multiple of 64 for the tensor cores (other
+ * steps fall back to the CUDA cores) and opts.rtm is rejected with
+ * LU_ERR_UNSUPPORTED on the tensor-core path.
+ */
+int lu_potrf_mixed_ex(lu_handle handle, lu_prec prec, int64_t n, float *A, int64_t lda, const lu_opts *opts,
+                      int32_t *info);
+
+/*
  * lu_geqrf_ex -- Householder QR of an m x n matrix, A = Q R, on the blocked
  * look-ahead skeleton of Sec. 4 (the paper's second factorization, Sec. 6.3;
  * 4n^3/3 flops when m = n).  Per panel k: PF_k factors the panel column by

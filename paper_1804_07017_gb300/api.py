@@ -362,3 +362,13 @@ def lu_geqrf_ex(A: torch.Tensor, tau: torch.Tensor, info: torch.Tensor, opts: Lu
     m, n = A.shape
     _check("lu_geqrf_ex", lib().lu_geqrf_ex(h.ptr, _DT[A.dtype], m, n, _p(A), _ld(A, "A"), _p(tau),
                                             ctypes.byref(o), _p(info)))
+
+
+def lu_potrf_mixed_ex(A: torch.Tensor, info: torch.Tensor, prec: int, opts: LuOpts | None = None,
+                      handle: Handle | None = None) -> None:
+    """In-place Cholesky of an FP32 symmetric positive definite matrix with the
+    trailing update on the tensor cores in precision `prec` (an lu_prec)."""
+    h = _handle(handle)
+    o = opts if opts is not None else default_opts()
+    _check("lu_potrf_mixed_ex", lib().lu_potrf_mixed_ex(h.ptr, int(prec), A.shape[0], _p(A), _ld(A, "A"),
+                                                        ctypes.byref(o), _p(info)))

@@ -7,9 +7,12 @@
 // the Cholesky factor is L = L~ D^{1/2}.  The factorization therefore runs the
 // LU driver (lu_factor_blocked) with the pivot search switched off -- panels
 // below, no interchange plans or row exchanges -- and finishes with one scaling
-// pass over the lower triangle.  A is stored with both triangles; the trailing
-// update is the LU's A22 -= L21 U12 (twice the flops of a symmetric rank-k
-// update, on kernels that are already tuned).
+// pass over the lower triangle.  A is stored with both triangles, but only the
+// lower block triangle is kept current: the Schur complement of a symmetric
+// matrix stays symmetric, so U12 = D1 L~21^T is formed from the block column
+// below the panel (no RL2 on the upper part), and the trailing update
+// A22 -= L~21 U12 skips the tiles above the diagonal panel blocks -- n^3/3
+// flops, the symmetric rank-k update's count.
 #include <cmath>
 
 #include "internal.h"
@@ -78,6 +81,30 @@ __global__ void __launch_bounds__(256) np_rows_kernel(T* __restrict__ A, int64_t
         if (c < w) row[(int64_t)c * lda] = x[c];
 }
 
+// U12(p, c) = u_pp L~(c, k0 + p) for p < kb, c in [cb, ce): the block row of U
+// from the block column of L~ (U = D L~^T for a symmetric matrix), written over
+// A12 through a 32 x 32 shared-memory tile so both sides are read and written
+// along columns.
+template <typename T>
+__global__ void __launch_bounds__(256) sym_u12_kernel(T* __restrict__ A, int64_t lda, int64_t k0, int kb,
+                                                      int64_t cb, int64_t ncols) {
+    __shared__ T tile[32][33];
+    const int p0 = blockIdx.x * 32;
+    const int64_t c0 = (int64_t)blockIdx.y * 32;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
+    for (int q = ty; q < 32; q += 8) {  // read L~(c0 + tx, k0 + p0 + q)
+        const int p = p0 + q;
+        const int64_t c = c0 + tx;
+        tile[q][tx] = (p < kb && c < ncols) ? A[(cb + c) + (k0 + p) * lda] : T(0);
+    }
+    __syncthreads();
+    for (int q = ty; q < 32; q += 8) {  // write U12(p0 + tx, c0 + q)
+        const int p = p0 + tx;
+        const int64_t c = c0 + q;
+        if (p < kb && c < ncols) A[(k0 + p) + (cb + c) * lda] = A[(k0 + p) + (k0 + p) * lda] * tile[tx][q];
+    }
+}
+
 // Strict lower triangle: l_ij = l~_ij sqrt(u_jj) (the diagonal is still u_jj here).
 template <typename T>
 __global__ void __launch_bounds__(256) chol_scale_lower_kernel(T* __restrict__ A, int64_t lda, int64_t n) {
@@ -97,8 +124,14 @@ __global__ void __launch_bounds__(256) chol_scale_diag_kernel(T* __restrict__ A,
 }
 
 template <typename T>
-int potrf_impl(lu_context* h, int64_t n, T* A, int64_t lda, const lu_opts& o, int32_t* info) {
-    LU_TRY(lu_factor_blocked<T>(h, n, A, lda, nullptr, o, info, nullptr, false));
+int potrf_impl(lu_context* h, int64_t n, T* A, int64_t lda, const lu_opts& o, int32_t* info,
+               const LuTuEngine* eng = nullptr) {
+    // only the lower block triangle is updated when the panels sit on a fixed grid
+    // (their diagonal blocks then never straddle a band boundary)
+    h->sym_band = o.nsched == 0 ? o.nb : 0;
+    const int r = lu_factor_blocked<T>(h, n, A, lda, nullptr, o, info, eng, false);
+    h->sym_band = 0;
+    LU_TRY(r);
     if (n == 0) return LU_SUCCESS;
     cudaStream_t st = h->user;
     LuProfScope prof(st, LU_K_OTHER, 2.0 * sizeof(T) * (double)n * (double)n / 2.0, (double)n * (double)n / 2.0);
@@ -111,6 +144,11 @@ int potrf_impl(lu_context* h, int64_t n, T* A, int64_t lda, const lu_opts& o, in
 }
 
 }  // namespace
+
+int lu_chol_factor_f32(lu_context* h, int64_t n, float* A, int64_t lda, const lu_opts& o, int32_t* info,
+                       const LuTuEngine* eng) {
+    return potrf_impl<float>(h, n, A, lda, o, info, eng);
+}
 
 template <typename T>
 int lu_panel_nopiv(cudaStream_t st, T* A, int64_t lda, int64_t M, int64_t j0, int64_t width, LuSync* sync) {
@@ -139,6 +177,19 @@ int lu_panel_nopiv(cudaStream_t st, T* A, int64_t lda, int64_t M, int64_t j0, in
     return lu_panel_nopiv<T>(st, A, lda, M, j0 + w1, w2, sync);
 }
 
+template <typename T>
+int lu_launch_sym_u12(cudaStream_t st, T* A, int64_t lda, int64_t k0, int64_t kb, int64_t cb, int64_t ce) {
+    const int64_t nc = ce - cb;
+    if (nc <= 0 || kb <= 0) return LU_SUCCESS;
+    LuProfScope prof(st, LU_K_TRSM, sizeof(T) * 2.0 * (double)kb * (double)nc, (double)kb * (double)nc);
+    const dim3 grid((unsigned)lu_cdiv(kb, 32), (unsigned)lu_cdiv(nc, 32));
+    sym_u12_kernel<T><<<grid, 256, 0, st>>>(A, lda, k0, (int)kb, cb, nc);
+    LU_CHECK_LAUNCH();
+    return LU_SUCCESS;
+}
+
+template int lu_launch_sym_u12<double>(cudaStream_t, double*, int64_t, int64_t, int64_t, int64_t, int64_t);
+template int lu_launch_sym_u12<float>(cudaStream_t, float*, int64_t, int64_t, int64_t, int64_t, int64_t);
 template int lu_panel_nopiv<double>(cudaStream_t, double*, int64_t, int64_t, int64_t, int64_t, LuSync*);
 template int lu_panel_nopiv<float>(cudaStream_t, float*, int64_t, int64_t, int64_t, int64_t, LuSync*);
 

@@ -171,6 +171,10 @@ __global__ void __maxnreg__(144)
             int issued = 0;
             for (int t = 0;; ++t) {
                 int tile = atomicAdd(p.counter, 1);
+                // a symmetric update takes only the tiles on or below the band's diagonal blocks
+                while (p.band > 0 && tile < p.tiles &&
+                       p.row0 + (tile % p.tiles_m) * kTM + kTM <= ((p.col0 + (tile / p.tiles_m) * BN) / p.band) * p.band)
+                    tile = atomicAdd(p.counter, 1);
                 if (tile >= p.tiles) tile = -1;
                 const int slot = t % kRing;
                 if (!mbar_wait(&rempty[slot], ((t / kRing) & 1) ^ 1, abort_flag)) break;
@@ -350,7 +354,7 @@ int lu_tc_smem_bytes(int bn) { return bn == 256 ? TcLayout<256>::kSmemBytes : Tc
 int lu_launch_tc_update(cudaStream_t st, int kind, int fmt, float* C, int64_t ldc, int64_t row0, int64_t m,
                         int64_t col0, int64_t ncols, int64_t k, const void* Abuf, int64_t a_rows, const void* Bbuf,
                         int64_t b_rows, float scale, int* counter, int* error, int grid, int bn,
-                        const float* rscale, const float* cscale) {
+                        const float* rscale, const float* cscale, int band) {
     if (m <= 0 || ncols <= 0) return LU_SUCCESS;
     const int elem = (kind == LU_TC_KIND_F16) ? 2 : 1;
     const int kchunk = 128 / elem;
@@ -379,6 +383,7 @@ int lu_launch_tc_update(cudaStream_t st, int kind, int fmt, float* C, int64_t ld
     p.scale = scale;
     p.rscale = rscale;
     p.cscale = cscale;
+    p.band = band;
     // instruction descriptor: D = F32, A/B format, both K-major, N >> 3, M >> 4
     uint32_t idesc = (1u << 4) | ((uint32_t)fmt << 7) | ((uint32_t)fmt << 10) | ((uint32_t)(bn >> 3) << 17) |
                      ((uint32_t)(kTM >> 4) << 24);

@@ -62,6 +62,9 @@ struct lu_context {
     size_t pf_smem_budget = 160 * 1024;
     // SMs the right trailing update leaves to the panel path (set per factorization).
     int tu_reserve = 0;
+    // Symmetric (Cholesky) trailing update: > 0 = the panel width; the updates then
+    // form U12 from L21 and touch only the lower block triangle (chol.cu).
+    int sym_band = 0;
     // Per-step trace of the look-ahead schedule (lu_step_trace): timing events
     // around PU(k+1) on the panel stream and TU_right(k) on the update stream.
     struct StepTrace {
@@ -132,6 +135,12 @@ int lu_launch_trsm_lunit(cudaStream_t st, int64_t m, int64_t n, const T* L, int6
 template <typename T>
 int lu_launch_gemm_update(cudaStream_t st, int64_t m, int64_t n, int64_t k, const T* A,
                           int64_t lda, const T* B, int64_t ldb, T* C, int64_t ldc);
+// The same with a symmetric band: tiles whose rows all lie above the band-wide
+// diagonal block of their first column (absolute indices: C's first row r0,
+// first column c0) are skipped (band 0 = none).
+template <typename T>
+int lu_launch_gemm_update_band(cudaStream_t st, int64_t m, int64_t n, int64_t k, const T* A, int64_t lda,
+                               const T* B, int64_t ldb, T* C, int64_t ldc, int64_t r0, int64_t c0, int band);
 
 template <typename T>
 int lu_launch_perm_from_ipiv(cudaStream_t st, int64_t n, const int32_t* ipiv, int32_t* perm);
@@ -210,6 +219,13 @@ int lu_step_tu(lu_context* c, cudaStream_t st, int64_t n, T* A, int64_t lda, int
 template <typename T>
 int lu_step_pf(lu_context* c, cudaStream_t st, T* A, int64_t lda, int64_t n, int64_t k, int64_t k0, int64_t kb,
                int32_t* ipiv, const lu_opts& o, bool pivot);
+// Symmetric elimination (chol.cu): U12 := D1 L21^T for block row k (panel columns
+// [k0, k0+kb)) on columns [cb, ce), D1 the diagonal of U11, written over A12.
+template <typename T>
+int lu_launch_sym_u12(cudaStream_t st, T* A, int64_t lda, int64_t k0, int64_t kb, int64_t cb, int64_t ce);
+// Cholesky of FP32 A with an optional tensor-core trailing-update engine (chol.cu).
+int lu_chol_factor_f32(lu_context* h, int64_t n, float* A, int64_t lda, const lu_opts& o, int32_t* info,
+                       const LuTuEngine* eng);
 // The runtime-task (dependency DAG) schedule of the same factorization (rtm.cu).
 template <typename T>
 int lu_factor_rtm(lu_context* c, int64_t n, T* A, int64_t lda, int32_t* ipiv, const lu_opts& o, int32_t* info,

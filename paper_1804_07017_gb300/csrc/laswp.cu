@@ -96,15 +96,9 @@ __global__ void __launch_bounds__(kApplyThreads)
     extern __shared__ __align__(16) unsigned char smraw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     T* buf = reinterpret_cast<T*>(smraw) + (size_t)warp * 2 * K;
-    // the plan's indices, staged once per CTA: every column reuses them
-    int32_t* dst = reinterpret_cast<int32_t*>(reinterpret_cast<T*>(smraw) + (size_t)(kApplyThreads / 32) * 2 * K);
-    int32_t* src = dst + 2 * K;
     const int cnt = plan[0];
-    for (int e = threadIdx.x; e < cnt; e += kApplyThreads) {
-        dst[e] = plan[1 + e];
-        src[e] = plan[1 + 2 * K + e];
-    }
-    __syncthreads();
+    const int32_t* dst = plan + 1;
+    const int32_t* src = plan + 1 + 2 * K;
     const int64_t ncols = n1 + n2;
     for (int64_t q = (int64_t)blockIdx.x * (kApplyThreads / 32) + warp; q < ncols;
          q += (int64_t)gridDim.x * (kApplyThreads / 32)) {
@@ -135,8 +129,8 @@ int lu_launch_laswp_apply(cudaStream_t st, T* A, int64_t lda, int64_t c1, int64_
                           int64_t n2, const int32_t* plan, int64_t K, int num_sms, int max_blocks) {
     if (K <= 0 || n1 + n2 <= 0) return LU_SUCCESS;
     const int warps = kApplyThreads / 32;
-    size_t smem = sizeof(T) * 2 * (size_t)K * warps + sizeof(int32_t) * 4 * (size_t)K;
-    LU_TRY(lu_func_smem(laswp_apply_kernel<T>, (int)(sizeof(T) * 2 * LU_MAX_NB * warps + sizeof(int32_t) * 4 * LU_MAX_NB)));
+    size_t smem = sizeof(T) * 2 * (size_t)K * warps;
+    LU_TRY(lu_func_smem(laswp_apply_kernel<T>, (int)(sizeof(T) * 2 * LU_MAX_NB * warps)));
     int64_t blocks = lu_cdiv(n1 + n2, warps);
     blocks = std::min<int64_t>(blocks, max_blocks > 0 ? (int64_t)max_blocks : (int64_t)std::max(num_sms, 1) * 8);
     LuProfScope prof(st, LU_K_LASWP, 2.0 * 2.0 * K * (double)(n1 + n2) * sizeof(T), 0.0);

@@ -303,14 +303,18 @@ static int trailing_update(lu_context* c, cudaStream_t st, int64_t n, T* A, int6
     if (ncols <= 0) return LU_SUCCESS;
     T* A11 = A + k0 + k0 * lda;
     T* A12 = A + k0 + c_begin * lda;
-    LU_TRY(lu_launch_trsm_lunit<T>(st, kb, ncols, A11, lda, A12, lda, cap));
+    // symmetric elimination keeps only the lower block triangle current: U12 is
+    // formed from L21 (U12 = D1 L21^T) instead of RL2 on the (stale) upper part
+    const int band = pivot ? 0 : c->sym_band;
+    if (band > 0) LU_TRY(lu_launch_sym_u12<T>(st, A, lda, k0, kb, c_begin, c_end));
+    else LU_TRY(lu_launch_trsm_lunit<T>(st, kb, ncols, A11, lda, A12, lda, cap));
     const int64_t m2 = n - (k0 + kb);
     if (m2 <= 0) return LU_SUCCESS;
     if (eng && eng->uses_tc(kb)) {
         return eng->update(st, (float*)A, lda, k, k0, kb, c_begin, c_end, which);
     }
-    return lu_launch_gemm_update<T>(st, m2, ncols, kb, A + (k0 + kb) + k0 * lda, lda, A12, lda,
-                                    A + (k0 + kb) + c_begin * lda, lda);
+    return lu_launch_gemm_update_band<T>(st, m2, ncols, kb, A + (k0 + kb) + k0 * lda, lda, A12, lda,
+                                         A + (k0 + kb) + c_begin * lda, lda, k0 + kb, c_begin, band);
 }
 
 template <typename T>

@@ -96,6 +96,7 @@ struct TcEngine final : LuTuEngine {
     int* counter[2] = {nullptr, nullptr};
     int* error = nullptr;
     int grid_panel = 0, grid_right = 0, grid_steal = 0;
+    int band = 0;  // > 0: symmetric (Cholesky) update of the lower block triangle only
     cudaEvent_t ev_ready = nullptr;
     mutable int64_t last_k = -1;
     mutable int64_t last_k0 = 0, last_kb = 0, last_cb = 0, last_ce = 0;
@@ -126,7 +127,7 @@ struct TcEngine final : LuTuEngine {
         const char* bbuf = blo[k % nbuf] + (size_t)off * kb * esize() * segs();
         return lu_launch_tc_update(st, fp8() ? LU_TC_KIND_F8 : LU_TC_KIND_F16, fmt_mma(), A, lda, k0 + kb, m, cb,
                                    ce - cb, kb * segs(), alo[k % nbuf], m, bbuf, ce - cb, 1.0f, counter[which], error,
-                                   grid, 256, fp8() ? rscale(k) : nullptr, fp8() ? cscale(k, off) : nullptr);
+                                   grid, 256, fp8() ? rscale(k) : nullptr, fp8() ? cscale(k, off) : nullptr, band);
     }
 
     int update(cudaStream_t st, float* A, int64_t lda, int64_t k, int64_t k0, int64_t kb, int64_t cb, int64_t ce,
@@ -331,6 +332,31 @@ extern "C" int lu_factor_mixed_ex(lu_handle h, lu_prec prec, int64_t n, float* A
     LU_TRY(lu_ctx_reserve(h, n, narrowest(n, o)));
     LU_TRY(lu_mx_reserve(h, tc_engine_bytes(prec, std::max<int64_t>(n, 1), o)));
     return factor_mixed(h, prec, n, A, lda, ipiv, o, info, (char*)h->mx);
+}
+
+extern "C" int lu_potrf_mixed_ex(lu_handle h, lu_prec prec, int64_t n, float* A, int64_t lda, const lu_opts* opts,
+                                 int32_t* info) {
+    if (!h) return LU_ERR_HANDLE;
+    if (!lu_prec_is_tc(prec) && prec != LU_TU_F32) return -2;
+    if (n < 0) return -3;
+    if (n > 0 && !A) return -4;
+    if (lda < std::max<int64_t>(1, n)) return -5;
+    lu_opts o;
+    lu_default_opts(&o);
+    if (opts) o = *opts;
+    if (lu_check_opts(o) != 0) return -6;
+    if (!info) return -7;
+    if (n > INT32_MAX / 2) return LU_ERR_UNSUPPORTED;
+    if (o.nb == 0 && o.nsched == 0) lu_auto_opts(LU_TUNE_F32, n, &o);
+    if (o.rtm && lu_prec_is_tc(prec)) return LU_ERR_UNSUPPORTED;
+    std::lock_guard<std::mutex> lk(h->mu);
+    if (!lu_prec_is_tc(prec)) return lu_chol_factor_f32(h, n, A, lda, o, info, nullptr);
+    LU_TRY(lu_ctx_reserve(h, n, narrowest(n, o)));
+    LU_TRY(lu_mx_reserve(h, tc_engine_bytes(prec, std::max<int64_t>(n, 1), o)));
+    TcEngine e;
+    LU_TRY(setup_engine(e, h, prec, n, (char*)h->mx, A, lda, o));
+    e.band = o.nsched == 0 ? o.nb : 0;
+    return lu_chol_factor_f32(h, n, A, lda, o, info, &e);
 }
 
 // ---------------------------------------------------------------------------

@@ -354,9 +354,10 @@ int qr_gemm_tn(lu_context* c, cudaStream_t st, int M, int N, int64_t K, const T*
 // V (m - r0) x kb with ld ldv, T kb x kb with ld kb.
 template <typename T>
 int qr_apply(lu_context* c, cudaStream_t st, T* A, int64_t lda, int64_t m, int64_t r0, int kb, int64_t cb,
-             int64_t ce, const T* V, int64_t ldv, const T* Tm, T* W, T* W2, T* part) {
+             int64_t ce, const T* V, int64_t ldv, const T* Tm, T* W, T* W2, int64_t wcap, T* part) {
     const int64_t rows = m - r0, nc = ce - cb;
     if (nc <= 0 || rows <= 0 || kb <= 0) return LU_SUCCESS;
+    if ((int64_t)kb * nc > wcap) return LU_ERR_UNSUPPORTED;  // W and W2 hold kb x nc each
     T* C = A + r0 + cb * lda;
     LU_TRY(qr_gemm_tn<T>(c, st, kb, (int)nc, rows, V, ldv, C, lda, W, kb, part));
     LU_TRY(qr_gemm_tn<T>(c, st, kb, (int)nc, kb, Tm, kb, W, kb, W2, kb, part));
@@ -408,7 +409,7 @@ int qr_panel(lu_context* c, cudaStream_t st, T* A, int64_t lda, int64_t m, int64
     LU_TRY(qr_leaf<T>(c, st, A, lda, m, j0, w1, tau));
     LU_TRY(qr_form_vt<T>(c, st, A, lda, m, j0, j0, w1, tau, wk.Vp, wk.Tp, wk.Gm, wk.part[0]));
     LU_TRY(qr_apply<T>(c, st, A, lda, m, j0, w1, j0 + w1, j0 + w, wk.Vp, m - j0, wk.Tp, wk.Whi[0], wk.Whi[1],
-                       wk.part[0]));
+                       (int64_t)wk.nbmax * wk.nbmax, wk.part[0]));
     return qr_leaf<T>(c, st, A, lda, m, j0 + w1, w - w1, tau);
 }
 
@@ -444,12 +445,14 @@ static int qr_factor(lu_context* c, int64_t m, int64_t n, T* A, int64_t lda, T* 
                                  wk.part[0]));
         return LU_SUCCESS;
     };
-    // TU_k on columns [cb, ce): on the panel stream with its buffers (which = 0) or the other (1)
+    // TU_k on columns [cb, ce) with the narrow buffers (which = 0: at most one panel
+    // wide, the look-ahead's TU_k^L) or the wide ones (1: any width)
     auto tu = [&](cudaStream_t st, int64_t k, int64_t cb, int64_t ce, int which) -> int {
         const int64_t k0 = s[(size_t)k];
         T** W = which ? wk.Wlo : wk.Whi;
+        const int64_t cap = which ? (int64_t)wk.nbmax * n : (int64_t)wk.nbmax * wk.nbmax;
         return qr_apply<T>(c, st, A, lda, m, k0, width(k), cb, ce, wk.V[k & 1], m - k0, wk.Tm[k & 1], W[0], W[1],
-                           wk.part[which]);
+                           cap, wk.part[which]);
     };
     LU_TRY(panel(0));
     for (int64_t k = 0; k < nk; ++k) {
@@ -467,7 +470,7 @@ static int qr_factor(lu_context* c, int64_t m, int64_t n, T* A, int64_t lda, T* 
                 LU_CHECK_CUDA(cudaStreamWaitEvent(hi, c->ev_tu, 0));
             }
         } else {
-            LU_TRY(tu(hi, k, c1, n, 0));
+            LU_TRY(tu(hi, k, c1, n, 1));  // every column right of the panel: the wide buffers
             if (k + 1 < nk) LU_TRY(panel(k + 1));
         }
     }

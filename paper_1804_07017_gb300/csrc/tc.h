@@ -22,10 +22,12 @@ struct TcUpdateParams {
     float scale;       // acc is multiplied by this before the subtraction
     const float* rscale;  // optional per-row factor of acc (power-of-two block scales), m entries
     const float* cscale;  // optional per-column factor of acc, ncols entries
+    int band;          // > 0: symmetric update; tiles whose rows all lie above the band-wide
+                       // diagonal block of their first column are skipped
 };
 
 int lu_tc_smem_bytes(int bn);
 int lu_launch_tc_update(cudaStream_t st, int kind, int fmt, float* C, int64_t ldc, int64_t row0, int64_t m,
                         int64_t col0, int64_t ncols, int64_t k, const void* Abuf, int64_t a_rows, const void* Bbuf,
                         int64_t b_rows, float scale, int* counter, int* error, int grid, int bn,
-                        const float* rscale = nullptr, const float* cscale = nullptr);
+                        const float* rscale = nullptr, const float* cscale = nullptr, int band = 0);

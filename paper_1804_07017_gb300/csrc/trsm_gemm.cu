@@ -142,7 +142,8 @@ constexpr int BK = 16;
 template <typename T, int BM, int BN>
 __global__ void __launch_bounds__(kGemmThreads)
     gemm_update_kernel(int64_t m, int64_t n, int k, const T* __restrict__ A, int64_t lda,
-                       const T* __restrict__ B, int64_t ldb, T* __restrict__ C, int64_t ldc) {
+                       const T* __restrict__ B, int64_t ldb, T* __restrict__ C, int64_t ldc, int64_t r0,
+                       int64_t c0, int band) {
     constexpr int TX = BM / 4, TY = BN / 4;
     static_assert(TX * TY == kGemmThreads, "tile shape");
     constexpr int NA = BM * BK / kGemmThreads, NB = BK * BN / kGemmThreads;
@@ -150,6 +151,10 @@ __global__ void __launch_bounds__(kGemmThreads)
     __shared__ T sB[2][BK][BN + 1];
     const int tid = threadIdx.x, tx = tid % TX, ty = tid / TX;
     const int64_t i0 = (int64_t)blockIdx.x * BM, j0 = (int64_t)blockIdx.y * BN;
+    // band > 0 (symmetric updates): a tile whose rows all lie above the band-wide
+    // diagonal block of its first column (absolute row r0 + i, column c0 + j) is
+    // not needed and is skipped
+    if (band > 0 && r0 + i0 + BM <= ((c0 + j0) / band) * band) return;
     T acc[4][4];
 #pragma unroll
     for (int a = 0; a < 4; ++a)
@@ -372,23 +377,29 @@ int lu_launch_trsm_lunit(cudaStream_t st, int64_t m, int64_t n, const T* L, int6
 template <typename T>
 int lu_launch_gemm_update(cudaStream_t st, int64_t m, int64_t n, int64_t k, const T* A, int64_t lda,
                           const T* B, int64_t ldb, T* C, int64_t ldc) {
+    return lu_launch_gemm_update_band<T>(st, m, n, k, A, lda, B, ldb, C, ldc, 0, 0, 0);
+}
+
+template <typename T>
+int lu_launch_gemm_update_band(cudaStream_t st, int64_t m, int64_t n, int64_t k, const T* A, int64_t lda,
+                               const T* B, int64_t ldb, T* C, int64_t ldc, int64_t r0, int64_t c0, int band) {
     if (m <= 0 || n <= 0 || k <= 0) return LU_SUCCESS;
     LuProfScope prof(st, LU_K_GEMM, sizeof(T) * (2.0 * m * n + (double)m * k + (double)k * n), 2.0 * m * n * k);
     if constexpr (sizeof(T) == 4) {
         if (n <= 16) {
             gemm_update_kernel<T, 256, 16><<<dim3((unsigned)lu_cdiv(m, 256), (unsigned)lu_cdiv(n, 16)), kGemmThreads,
-                                              0, st>>>(m, n, (int)k, A, lda, B, ldb, C, ldc);
+                                              0, st>>>(m, n, (int)k, A, lda, B, ldb, C, ldc, r0, c0, band);
             LU_CHECK_LAUNCH();
             return LU_SUCCESS;
         }
     }
     if (n <= 32) {
         gemm_update_kernel<T, 128, 32><<<dim3((unsigned)lu_cdiv(m, 128), (unsigned)lu_cdiv(n, 32)), kGemmThreads, 0,
-                                          st>>>(m, n, (int)k, A, lda, B, ldb, C, ldc);
+                                          st>>>(m, n, (int)k, A, lda, B, ldb, C, ldc, r0, c0, band);
     } else {
         if (lu_cdiv(n, 64) > 65535) return LU_ERR_UNSUPPORTED;
         gemm_update_kernel<T, 64, 64><<<dim3((unsigned)lu_cdiv(m, 64), (unsigned)lu_cdiv(n, 64)), kGemmThreads, 0,
-                                        st>>>(m, n, (int)k, A, lda, B, ldb, C, ldc);
+                                        st>>>(m, n, (int)k, A, lda, B, ldb, C, ldc, r0, c0, band);
     }
     LU_CHECK_LAUNCH();
     return LU_SUCCESS;
@@ -400,6 +411,10 @@ template int lu_launch_trsm_lunit<float>(cudaStream_t, int64_t, int64_t, const f
                                          float*, int64_t, int);
 template int lu_launch_gemm_update<double>(cudaStream_t, int64_t, int64_t, int64_t, const double*,
                                            int64_t, const double*, int64_t, double*, int64_t);
+template int lu_launch_gemm_update_band<double>(cudaStream_t, int64_t, int64_t, int64_t, const double*, int64_t,
+                                                const double*, int64_t, double*, int64_t, int64_t, int64_t, int);
+template int lu_launch_gemm_update_band<float>(cudaStream_t, int64_t, int64_t, int64_t, const float*, int64_t,
+                                               const float*, int64_t, float*, int64_t, int64_t, int64_t, int);
 template int lu_launch_gemm_update<float>(cudaStream_t, int64_t, int64_t, int64_t, const float*,
                                           int64_t, const float*, int64_t, float*, int64_t);
 

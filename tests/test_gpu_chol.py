@@ -90,3 +90,45 @@ def test_potrf_solve_through_factor(lu):
     y = np.linalg.solve(L, b)
     x = np.linalg.solve(L.T, y)
     assert oracle.backward_error(A0, x[:, None], b[:, None]) <= 1e-14
+
+
+@pytest.mark.parametrize("prec_name", ["bf16x6", "f32"])
+def test_potrf_mixed_tensor_cores(lu, prec_name):
+    """FP32 Cholesky with the trailing update on the tensor cores (split-bf16
+    x6, FP32-level accuracy) or on the CUDA cores (f32, then bit-identical to
+    lu_potrf_ex in FP32): the FP32 factor bounds against the oracle, and
+    look-ahead on and off bit-identical."""
+    from paper_1804_07017_gb300.api import colmajor
+    prec = {"bf16x6": lu.LU_TU_BF16X6, "f32": lu.LU_TU_F32}[prec_name]
+    n, nb = 2048, 256
+    A0 = synth.spd_matrix(n, seed=11).astype(np.float32).astype(np.float64)
+    outs = []
+    for la in (0, 1):
+        A = colmajor(n, n, dtype=torch.float32)
+        A.copy_(torch.from_numpy(A0).float())
+        info = torch.full((1,), -7, dtype=torch.int32, device="cuda")
+        lu.lu_potrf_mixed_ex(A, info, prec, lu.default_opts(nb=nb, lookahead=la))
+        torch.cuda.synchronize()
+        assert int(info.item()) == 0
+        outs.append(np.tril(A.cpu().double().numpy()))
+    assert np.array_equal(outs[0], outs[1])
+    L = outs[1]
+    assert oracle.chol_error(A0, L) <= 8 * np.finfo(np.float32).eps
+    Lo, _ = oracle.potrf(A0)
+    assert np.abs(L - Lo).max() <= 1e-4 * np.abs(Lo).max()
+    if prec_name == "f32":
+        L32, info = potrf_gpu(lu, A0, nb, dtype=torch.float32)
+        assert info == 0 and np.array_equal(L32, L)
+
+
+def test_potrf_depth2_and_task_dag(lu):
+    """The symmetric update under depth-2 look-ahead and under the task-DAG
+    schedule: factors bit-identical to depth 1."""
+    n, nb = 1100, 128
+    A0 = synth.spd_matrix(n, seed=12)
+    L1, i1 = potrf_gpu(lu, A0, nb, lookahead=1)
+    L2, i2 = potrf_gpu(lu, A0, nb, lookahead=2)
+    L3, i3 = potrf_gpu(lu, A0, nb, rtm=1)
+    assert i1 == i2 == i3 == 0
+    assert np.array_equal(L1, L2) and np.array_equal(L1, L3)
+    assert oracle.chol_error(A0, L1) <= 1e-14
