@@ -689,9 +689,11 @@ def run_qr(args):
 
 
 def run_chol(args):
-    """Cholesky factorization (lu_potrf_ex, nb = 256, depth-1 look-ahead) of
-    A = G G^T / n + I, G iid U[-1,1) from a seeded torch generator (formed on the
-    device, outside the timed region): FP64 at n = 8192 and FP32 at n = 16384.
+    """Cholesky factorization (lu_potrf_ex, nb = 256, depth-1 look-ahead, the
+    lower block triangle updated) of A = G G^T / n + I, G iid U[-1,1) from a
+    seeded torch generator (formed on the device, outside the timed region):
+    FP64 at n = 8192 and FP32 at n = 16384 on the CUDA cores, and FP32 at
+    n = 16384 with the split-bf16 x6 tensor-core update (lu_potrf_mixed_ex).
     GFLOP/s of n^3/3 (the Cholesky count); two untimed runs, then the median of
     three event-timed runs, A restored from a device copy before each."""
     import statistics as st_
@@ -702,7 +704,8 @@ def run_chol(args):
 
     torch.cuda.set_device(0)
     out = {"metric": "Cholesky GFLOP/s (n^3/3)", "unit": "GFLOP/s", "data": "synthetic"}
-    for name, dt, n in (("f64_n8192", torch.float64, 8192), ("f32_n16384", torch.float32, 16384)):
+    for name, dt, n, prec in (("f64_n8192", torch.float64, 8192, None), ("f32_n16384", torch.float32, 16384, None),
+                              ("f32_n16384_tc_bf16x6", torch.float32, 16384, "bf16x6")):
         g = torch.Generator(device="cuda")
         g.manual_seed(0)
         G = torch.rand((n, n), generator=g, device="cuda", dtype=dt) * 2 - 1
@@ -718,7 +721,10 @@ def run_chol(args):
             torch.cuda.synchronize()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record()
-            lu.lu_potrf_ex(A, info, o)
+            if prec is None:
+                lu.lu_potrf_ex(A, info, o)
+            else:
+                lu.lu_potrf_mixed_ex(A, info, lu.LU_TU_BF16X6, o)
             e1.record()
             torch.cuda.synchronize()
             if it >= 2:
