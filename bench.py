@@ -800,6 +800,24 @@ def run_tune(args):
     return 0
 
 
+def reference_solution(name, A0):
+    """The CPU oracle's FP64 solution of configuration `name`, stored by
+    tests/golden/make_reference_solutions.py, if its matrix fingerprint matches
+    A0 (same generator, same bits); else (None, reason)."""
+    import hashlib
+    golden = os.path.join(ROOT, "tests", "golden")
+    try:
+        meta = json.load(open(os.path.join(golden, "reference_solutions.json")))[name]
+        x = np.load(os.path.join(golden, f"x_oracle_{name}.npy"))
+    except Exception:
+        return None, "no stored oracle solution"
+    flat = np.asfortranarray(A0).ravel(order="F")
+    fp = hashlib.sha256(np.ascontiguousarray(flat[::meta["fingerprint_stride"]]).tobytes()).hexdigest()
+    if fp != meta["fingerprint"]:
+        return None, "matrix fingerprint differs from the stored solution's"
+    return x, None
+
+
 def run_configs(args):
     """The comparisons of the hot-path configurations, one JSON object:
     c1  FP64, n = 8192, nb = 256, N(0,1): look-ahead off / depth 1 / depth 1 with
@@ -808,6 +826,9 @@ def run_configs(args):
     c2  n = 16384, nb = 256: the mixed solver with each trailing-update precision
         (N(0,1), one rhs), then bf16x6 on the row-scaled matrix and with 16 rhs;
     c3  n = 32768, nb = 256, A = diag(10^u) G: bf16x6 and e4m3 updates.
+    For c2 (N(0,1), one rhs) and c3 each variant also reports
+    ||x - x_oracle||_inf / ||x_oracle||_inf against the CPU oracle's FP64
+    solution stored by tests/golden/make_reference_solutions.py.
     Each configuration runs twice untimed, then once timed with CUDA events."""
     import numpy as np
     import torch
@@ -858,7 +879,7 @@ def run_configs(args):
     out["c1_fp64_n8192"] = c1
     del A, B, Ah, bh
 
-    def mixed(n, A0, B0, precs, tag):
+    def mixed(n, A0, B0, precs, tag, ref=None):
         A = colmajor(n, n)
         A.copy_(torch.from_numpy(A0))
         B = colmajor(n, B0.shape[1])
@@ -872,11 +893,20 @@ def run_configs(args):
             res[f"{tag}{name}"] = {"ms": ms, "gflops": 2 * n ** 3 / 3 / ms / 1e6, "status": int(st),
                                    "refinements": int(it), "bwd_err": float(eta),
                                    "converged": int(st) == 0}
+            if ref is not None:
+                x_or, why = ref
+                if x_or is None:
+                    res[f"{tag}{name}"]["fwd_err_vs_oracle"] = None
+                    res[f"{tag}{name}"]["fwd_err_note"] = why
+                else:
+                    x = X.cpu().numpy()
+                    res[f"{tag}{name}"]["fwd_err_vs_oracle"] = float(np.abs(x - x_or).max() / np.abs(x_or).max())
         return res
 
     n = 16384
     A0 = synth.normal_matrix(n, seed=0)
-    c2 = mixed(n, A0, synth.ones_rhs(A0), ["bf16x6", "bf16x3", "bf16", "fp16", "f32", "f64"], "")
+    c2 = mixed(n, A0, synth.ones_rhs(A0), ["bf16x6", "bf16x3", "bf16", "fp16", "f32", "f64"], "",
+               ref=reference_solution("c2_normal_n16384", A0))
     B16, _ = synth.random_rhs(A0, 16, seed=1)
     c2.update(mixed(n, A0, B16, ["bf16x6"], "rhs16_"))
     R0 = synth.row_scaled(A0, seed=3)
@@ -885,7 +915,8 @@ def run_configs(args):
     del A0, R0, B16
     n = 32768
     D0 = synth.diag_scaled_normal(n, seed=0)
-    out["c3_n32768_diag_scaled"] = mixed(n, D0, synth.ones_rhs(D0), ["bf16x6", "fp8"], "")
+    out["c3_n32768_diag_scaled"] = mixed(n, D0, synth.ones_rhs(D0), ["bf16x6", "fp8"], "",
+                                         ref=reference_solution("c3_diag_scaled_n32768", D0))
     print(json.dumps(out))
     return 0
 

@@ -377,9 +377,12 @@ int lu_factor_blocked(lu_context* c, int64_t n, T* A, int64_t lda, int32_t* ipiv
     // PF(k) followed by its interchange plan (and, for the tensor-core engine, the packed L21)
     auto panel = [&](int64_t k) -> int {
         const int64_t k0 = s[k], kb = s[k + 1] - s[k];
-        if (!pivot) return lu_panel_nopiv<T>(hi, A, lda, n, k0, kb, &c->sync[0]);
-        LU_TRY(lu_panel_recursive<T>(c, hi, A, lda, n, k0, kb, ipiv, o));
-        LU_TRY(lu_launch_laswp_plan(hi, ipiv, k0, k0 + kb, plan_of(k)));
+        if (!pivot) {
+            LU_TRY(lu_panel_nopiv<T>(hi, A, lda, n, k0, kb, &c->sync[0]));
+        } else {
+            LU_TRY(lu_panel_recursive<T>(c, hi, A, lda, n, k0, kb, ipiv, o));
+            LU_TRY(lu_launch_laswp_plan(hi, ipiv, k0, k0 + kb, plan_of(k)));
+        }
         if (eng && eng->uses_tc(kb) && k0 + kb < n) LU_TRY(eng->pack_panel(hi, (const float*)A, lda, k, k0, kb));
         return LU_SUCCESS;
     };
