@@ -657,7 +657,9 @@ def run_profile(args):
 
 def run_qr(args):
     """Householder QR (lu_geqrf_ex) on the look-ahead skeleton: FP64 n = 8192
-    and FP32 n = 16384, iid U[-1,1) (seed 0), look-ahead off and on, nb 64 and
+    and FP32 n = 16384 on the CUDA cores, FP32 n = 16384 with the update's last
+    product on the tensor cores (lu_geqrf_mixed_ex, split-bf16 x6); iid
+    U[-1,1) (seed 0), look-ahead off and on, nb 64 and
     128; the matrix is restored from a device copy before each run (outside the
     timed region); median of three event-timed runs after one untimed run.
     GFLOP/s of 4n^3/3.  One JSON object."""
@@ -667,7 +669,8 @@ def run_qr(args):
     import synth
     torch.cuda.set_device(0)
     out = {"metric": "QR GFLOP/s (4n^3/3)", "unit": "GFLOP/s", "data": "synthetic"}
-    for name, dt, n in (("fp64_n8192", torch.float64, 8192), ("fp32_n16384", torch.float32, 16384)):
+    for name, dt, n, prec in (("fp64_n8192", torch.float64, 8192, None), ("fp32_n16384", torch.float32, 16384, None),
+                              ("fp32_n16384_tc_bf16x6", torch.float32, 16384, lu.LU_TU_BF16X6)):
         if args.shape and str(n) not in args.shape.split(","):
             continue
         A0 = torch.from_numpy(synth.uniform_matrix(n, seed=0)).to(dt).cuda()
@@ -678,7 +681,11 @@ def run_qr(args):
         for nb in (64, 128):
             for la in (0, 1):
                 o = lu.default_opts(nb=nb, lookahead=la)
-                ms = _median_ms(lambda: lu.lu_geqrf_ex(A, tau, info, o), 4, before=lambda: A.copy_(A0))
+                if prec is None:
+                    fn = (lambda: lu.lu_geqrf_ex(A, tau, info, o))
+                else:
+                    fn = (lambda: lu.lu_geqrf_mixed_ex(A, tau, info, prec, o))
+                ms = _median_ms(fn, 4, before=lambda: A.copy_(A0))
                 res[f"nb{nb}_lookahead{la}"] = {"ms": round(ms, 3), "gflops": round(4.0 * n ** 3 / 3 / ms / 1e6, 1),
                                                 "info": int(info.item())}
         out[name] = res

@@ -515,6 +515,19 @@ int lu_geqrf_ex(lu_handle handle, lu_dtype dtype, int64_t m, int64_t n, void *A,
                 const lu_opts *opts, int32_t *info);
 
 /*
+ * lu_geqrf_mixed_ex -- lu_geqrf_ex for an FP32 matrix with the last of the three
+ * products of each update, C -= V_k (T_k^T V_k^T C), on the tensor cores in the
+ * operand precision prec (LU_TU_BF16X6 keeps FP32-level accuracy; LU_TU_BF16,
+ * LU_TU_FP16, LU_TU_BF16X3 trade accuracy; LU_TU_F32 = the CUDA cores, then the
+ * same as lu_geqrf_ex).  V_k is packed once per panel, T_k^T V_k^T C per update;
+ * steps whose width is not a multiple of 64 use the CUDA cores.  Arguments,
+ * layout, info and return codes as lu_geqrf_ex (-2: prec is LU_TU_FP8 or not a
+ * precision code).
+ */
+int lu_geqrf_mixed_ex(lu_handle handle, lu_prec prec, int64_t m, int64_t n, float *A, int64_t lda, float *tau,
+                      const lu_opts *opts, int32_t *info);
+
+/*
  * lu_tune_plan -- tune the whole schedule of the factorization of `kind` at
  * order n on a seeded synthetic matrix (iid U[-1,1)), in four measured stages:
  *   1. the block size b among 128, 192, 256, 320, 384, 512 (multiples of 64,

@@ -115,6 +115,7 @@ _SIGNATURES = {
                                ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_int32), i32, ctypes.POINTER(i32)]),
     "lu_geqrf_ex": (i32, [vp, i32, i64, i64, vp, i64, vp, ctypes.POINTER(LuOpts), vp]),
     "lu_potrf_mixed_ex": (i32, [vp, i32, i64, vp, i64, ctypes.POINTER(LuOpts), vp]),
+    "lu_geqrf_mixed_ex": (i32, [vp, i32, i64, i64, vp, i64, vp, ctypes.POINTER(LuOpts), vp]),
     "lu_step_trace": (i32, [vp, i32]),
     "lu_step_trace_read": (i64, [vp, i32, ctypes.POINTER(i64), ctypes.POINTER(ctypes.c_int32),
                                  ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float),

@@ -372,3 +372,14 @@ def lu_potrf_mixed_ex(A: torch.Tensor, info: torch.Tensor, prec: int, opts: LuOp
     o = opts if opts is not None else default_opts()
     _check("lu_potrf_mixed_ex", lib().lu_potrf_mixed_ex(h.ptr, int(prec), A.shape[0], _p(A), _ld(A, "A"),
                                                         ctypes.byref(o), _p(info)))
+
+
+def lu_geqrf_mixed_ex(A: torch.Tensor, tau: torch.Tensor, info: torch.Tensor, prec: int,
+                      opts: LuOpts | None = None, handle: Handle | None = None) -> None:
+    """Householder QR of an FP32 matrix with the update's last product on the
+    tensor cores in precision `prec` (an lu_prec other than FP8)."""
+    h = _handle(handle)
+    o = opts if opts is not None else default_opts(nb=128)
+    m, n = A.shape
+    _check("lu_geqrf_mixed_ex", lib().lu_geqrf_mixed_ex(h.ptr, int(prec), m, n, _p(A), _ld(A, "A"), _p(tau),
+                                                        ctypes.byref(o), _p(info)))

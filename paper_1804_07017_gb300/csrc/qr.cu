@@ -25,7 +25,9 @@
 #include <cstring>
 
 #include "internal.h"
+#include "pack.h"
 #include "profile.h"
+#include "tc.h"
 
 namespace {
 
@@ -300,6 +302,15 @@ struct QrWork {
     T* Wlo[2];    // the same on the update stream, nbmax x n
     T* part[2];   // split-K partials: [0] panel stream, [1] update stream
     int nbmax;
+    // tensor-core update C -= V W2 (FP32 only): packed V per panel parity, packed W2 per stream
+    int prec = -1;
+    char* Vpk[2] = {nullptr, nullptr};
+    char* Wpk[2] = {nullptr, nullptr};
+    static size_t tc_bytes(int prec, int64_t m, int64_t n, int nbmax) {
+        if (prec < 0) return 0;
+        const size_t seg = 2 * (size_t)lu_pack_segments(lu_prec_pack_fmt(prec));
+        return (2 * (size_t)m * nbmax + (size_t)nbmax * nbmax + (size_t)n * nbmax) * seg + 4 * 256;
+    }
     static size_t bytes(int64_t m, int64_t n, int nbmax) {
         const size_t e = 2 * (size_t)m * nbmax + 2 * (size_t)nbmax * nbmax + (size_t)m * kQrMaxLeaf +
                          (size_t)kQrMaxLeaf * kQrMaxLeaf + (size_t)nbmax * nbmax + 2 * (size_t)nbmax * nbmax +
@@ -322,6 +333,17 @@ struct QrWork {
         for (int i = 0; i < 2; ++i) Whi[i] = take((size_t)nb * nb);
         for (int i = 0; i < 2; ++i) Wlo[i] = take((size_t)nb * n);
         for (int i = 0; i < 2; ++i) part[i] = take((size_t)kQrPartCap);
+        if (prec >= 0) {
+            const size_t seg = 2 * (size_t)lu_pack_segments(lu_prec_pack_fmt(prec));
+            auto takeb = [&](size_t bytes) {
+                char* p = base + off;
+                off += (bytes + 255) / 256 * 256;
+                return p;
+            };
+            for (int i = 0; i < 2; ++i) Vpk[i] = takeb((size_t)m * nb * seg);
+            Wpk[0] = takeb((size_t)nb * nb * seg);
+            Wpk[1] = takeb((size_t)n * nb * seg);
+        }
     }
 };
 
@@ -352,15 +374,37 @@ int qr_gemm_tn(lu_context* c, cudaStream_t st, int M, int N, int64_t K, const T*
 
 // Q^T applied to columns [cb, ce) of rows [r0, m): C -= V (T^T (V^T C)),
 // V (m - r0) x kb with ld ldv, T kb x kb with ld kb.
+// Optional tensor-core form of the last product: V packed once per panel (vpk),
+// W2 packed per call into wpk, the tcgen05 update on C with the given tile
+// counter; prec < 0 or a width that is not a multiple of 64 keeps the CUDA cores.
+struct QrTc {
+    int prec = -1;
+    const char* vpk = nullptr;
+    char* wpk = nullptr;
+    int* counter = nullptr;
+};
+
 template <typename T>
 int qr_apply(lu_context* c, cudaStream_t st, T* A, int64_t lda, int64_t m, int64_t r0, int kb, int64_t cb,
-             int64_t ce, const T* V, int64_t ldv, const T* Tm, T* W, T* W2, int64_t wcap, T* part) {
+             int64_t ce, const T* V, int64_t ldv, const T* Tm, T* W, T* W2, int64_t wcap, T* part,
+             const QrTc& tc = QrTc()) {
     const int64_t rows = m - r0, nc = ce - cb;
     if (nc <= 0 || rows <= 0 || kb <= 0) return LU_SUCCESS;
     if ((int64_t)kb * nc > wcap) return LU_ERR_UNSUPPORTED;  // W and W2 hold kb x nc each
     T* C = A + r0 + cb * lda;
     LU_TRY(qr_gemm_tn<T>(c, st, kb, (int)nc, rows, V, ldv, C, lda, W, kb, part));
     LU_TRY(qr_gemm_tn<T>(c, st, kb, (int)nc, kb, Tm, kb, W, kb, W2, kb, part));
+    if constexpr (sizeof(T) == 4) {
+        if (tc.prec >= 0 && tc.vpk && kb % 64 == 0) {
+            const int fmt = lu_prec_pack_fmt(tc.prec);
+            const int sg = lu_pack_segments(fmt);
+            LU_TRY(lu_launch_pack_cols(st, fmt, (const float*)W2, kb, nc, kb, tc.wpk));
+            LU_CHECK_CUDA(cudaMemsetAsync(tc.counter, 0, sizeof(int), st));
+            return lu_launch_tc_update(st, LU_TC_KIND_F16, tc.prec == LU_TU_FP16 ? LU_TC_FMT_F16 : LU_TC_FMT_BF16,
+                                       (float*)A, lda, r0, rows, cb, nc, (int64_t)kb * sg, tc.vpk, rows, tc.wpk, nc,
+                                       1.0f, tc.counter, &c->sync[0].error, c->num_sms, 256);
+        }
+    }
     return lu_launch_gemm_update<T>(st, rows, nc, kb, V, ldv, W2, kb, C, lda);
 }
 
@@ -417,15 +461,16 @@ int qr_panel(lu_context* c, cudaStream_t st, T* A, int64_t lda, int64_t m, int64
 
 template <typename T>
 static int qr_factor(lu_context* c, int64_t m, int64_t n, T* A, int64_t lda, T* tau, const lu_opts& o,
-                     int32_t* info) {
+                     int32_t* info, int prec = -1) {
     const int64_t kmax = std::min(m, n);
     std::vector<int64_t> s;
     int wmin = 1, wmax = 1;
     lu_panel_bounds(kmax, o, &s, &wmin, &wmax);
     if (wmax > 2 * kQrMaxLeaf) return LU_ERR_UNSUPPORTED;
     LU_TRY(lu_ctx_reserve(c, std::max(m, n), wmin));
-    LU_TRY(lu_mx_reserve(c, QrWork<T>::bytes(m, n, wmax)));
+    LU_TRY(lu_mx_reserve(c, QrWork<T>::bytes(m, n, wmax) + QrWork<T>::tc_bytes(prec, m, n, wmax)));
     QrWork<T> wk;
+    wk.prec = prec;
     wk.carve((char*)c->mx, m, n, wmax);
     cudaStream_t user = c->user;
     LU_CHECK_CUDA(cudaMemsetAsync(&c->sync[0], 0, sizeof(LuSync), user));
@@ -440,9 +485,14 @@ static int qr_factor(lu_context* c, int64_t m, int64_t n, T* A, int64_t lda, T* 
     auto panel = [&](int64_t k) -> int {
         const int64_t k0 = s[(size_t)k];
         LU_TRY(qr_panel<T>(c, hi, A, lda, m, k0, width(k), tau, wk));
-        if (k0 + width(k) < n)
+        if (k0 + width(k) < n) {
             LU_TRY(qr_form_vt<T>(c, hi, A, lda, m, k0, k0, width(k), tau, wk.V[k & 1], wk.Tm[k & 1], wk.Gm,
                                  wk.part[0]));
+            if constexpr (sizeof(T) == 4)
+                if (wk.prec >= 0 && width(k) % 64 == 0)
+                    LU_TRY(lu_launch_pack_rows(hi, lu_prec_pack_fmt(wk.prec), (const float*)wk.V[k & 1], m - k0,
+                                               m - k0, width(k), wk.Vpk[k & 1]));
+        }
         return LU_SUCCESS;
     };
     // TU_k on columns [cb, ce) with the narrow buffers (which = 0: at most one panel
@@ -451,8 +501,15 @@ static int qr_factor(lu_context* c, int64_t m, int64_t n, T* A, int64_t lda, T* 
         const int64_t k0 = s[(size_t)k];
         T** W = which ? wk.Wlo : wk.Whi;
         const int64_t cap = which ? (int64_t)wk.nbmax * n : (int64_t)wk.nbmax * wk.nbmax;
+        QrTc tc;
+        if (wk.prec >= 0) {
+            tc.prec = wk.prec;
+            tc.vpk = wk.Vpk[k & 1];
+            tc.wpk = wk.Wpk[which];
+            tc.counter = (int*)&c->sync[4 + which].ticket;
+        }
         return qr_apply<T>(c, st, A, lda, m, k0, width(k), cb, ce, wk.V[k & 1], m - k0, wk.Tm[k & 1], W[0], W[1],
-                           cap, wk.part[which]);
+                           cap, wk.part[which], tc);
     };
     LU_TRY(panel(0));
     for (int64_t k = 0; k < nk; ++k) {
@@ -502,4 +559,26 @@ extern "C" int lu_geqrf_ex(lu_handle h, lu_dtype dtype, int64_t m, int64_t n, vo
     std::lock_guard<std::mutex> lk(h->mu);
     if (dtype == LU_F64) return qr_factor<double>(h, m, n, (double*)A, lda, (double*)tau, o, info);
     return qr_factor<float>(h, m, n, (float*)A, lda, (float*)tau, o, info);
+}
+
+extern "C" int lu_geqrf_mixed_ex(lu_handle h, lu_prec prec, int64_t m, int64_t n, float* A, int64_t lda, float* tau,
+                                 const lu_opts* opts, int32_t* info) {
+    if (!h) return LU_ERR_HANDLE;
+    if (prec == LU_TU_FP8 || (!lu_prec_is_tc(prec) && prec != LU_TU_F32)) return -2;
+    if (m < 0) return -3;
+    if (n < 0) return -4;
+    if (m > 0 && n > 0 && !A) return -5;
+    if (lda < std::max<int64_t>(1, m)) return -6;
+    if (std::min(m, n) > 0 && !tau) return -7;
+    lu_opts o;
+    lu_default_opts(&o);
+    o.nb = 128;
+    if (opts) o = *opts;
+    if (lu_check_opts(o) != 0) return -8;
+    if (!info) return -9;
+    if (o.nb == 0) o.nb = 128;
+    if (o.lookahead > 1 || o.rtm) return LU_ERR_UNSUPPORTED;
+    if (m > INT32_MAX / 2 || n > INT32_MAX / 2) return LU_ERR_UNSUPPORTED;
+    std::lock_guard<std::mutex> lk(h->mu);
+    return qr_factor<float>(h, m, n, A, lda, tau, o, info, lu_prec_is_tc(prec) ? (int)prec : -1);
 }

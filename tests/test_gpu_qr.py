@@ -98,3 +98,34 @@ def test_geqrf_tall_panel_rows(lu):
     # ||A^T A - R^T R|| small: Q has orthonormal columns
     G = A0.T @ A0
     assert np.abs(G - R.T @ R).max() <= 1e-12 * np.abs(G).max()
+
+
+@pytest.mark.parametrize("m,n,nb", [(2048, 2048, 128), (3000, 1000, 64), (1500, 1500, 96)])
+def test_geqrf_tensor_core_update(lu, m, n, nb):
+    """FP32 QR with the update's last product on the tensor cores (split-bf16 x6,
+    FP32-level accuracy): the FP32 residual and orthogonality bounds against the
+    oracle, reflectors within the FP32 tolerance, look-ahead off/on
+    bit-identical; with LU_TU_F32 it equals lu_geqrf_ex bit for bit."""
+    from paper_1804_07017_gb300.api import colmajor
+    A0 = synth.uniform_matrix(m, n, seed=84, stream=nb).astype(np.float32).astype(np.float64)
+
+    def run(prec, la):
+        A = colmajor(m, n, dtype=torch.float32)
+        A.copy_(torch.from_numpy(A0).float())
+        tau = torch.zeros(min(m, n), dtype=torch.float32, device="cuda")
+        info = torch.full((1,), -7, dtype=torch.int32, device="cuda")
+        lu.lu_geqrf_mixed_ex(A, tau, info, prec, lu.default_opts(nb=nb, lookahead=la))
+        torch.cuda.synchronize()
+        return A.cpu().double().numpy(), tau.cpu().double().numpy(), int(info.item())
+
+    QR0, t0, i0 = run(lu.LU_TU_BF16X6, 0)
+    QR1, t1, i1 = run(lu.LU_TU_BF16X6, 1)
+    assert i0 == i1 == 0 and np.array_equal(QR0, QR1) and np.array_equal(t0, t1)
+    u = np.finfo(np.float32).eps / 2
+    res, orth = oracle.qr_error(A0, QR1, t1)
+    assert res <= 8 * u and orth <= 50 * max(m, n) * u, (res, orth)
+    QRo, tauo = oracle.geqr2(A0)
+    assert np.abs(QR1 - QRo).max() <= 1e-3 * max(np.abs(QRo).max(), 1.0)
+    QRs, ts, _ = run(lu.LU_TU_F32, 1)
+    QRg, tg, _ = qr_gpu(lu, A0, torch.float32, nb=nb, lookahead=1)
+    assert np.array_equal(QRs, QRg) and np.array_equal(ts, tg)
