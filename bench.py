@@ -185,6 +185,7 @@ def workload_config(args):
     return {"workload": f"mixed-precision LU+solve+FP64 IR, n={args.n}, nb={args.nb}, N(0,1) seed 0, "
                         f"{args.nrhs} rhs b=A*ones, FP32 panels, {args.prec} tensor-core TU, depth-1 look-ahead",
             "n": args.n, "nb": args.nb, "nrhs": args.nrhs, "tu": args.prec, "lookahead": 1,
+            "pf_sms": getattr(args, "pf_sms", 0),
             "tol": TOL, "max_iter": MAX_ITER, "l2": "inputs larger than L2 (A is 2 GiB FP64)"}
 
 
@@ -201,6 +202,8 @@ def main_with_args(argv):
     ap.add_argument("--n", type=int, default=N_DEFAULT)
     ap.add_argument("--nb", type=int, default=NB_DEFAULT)
     ap.add_argument("--nrhs", type=int, default=1)
+    ap.add_argument("--pf-sms", type=int, default=0,
+                    help="SMs reserved for the panel leaves (a green-context partition; 0 = none)")
     ap.add_argument("--prec", default="bf16x6", choices=["bf16x6", "bf16x3", "bf16", "fp16", "f32"])
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison path")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle sample")
@@ -259,7 +262,7 @@ def main_with_args(argv):
     n, nrhs = args.n, args.nrhs
     prec = {"bf16": lu.LU_TU_BF16, "fp16": lu.LU_TU_FP16, "f32": lu.LU_TU_F32, "bf16x3": lu.LU_TU_BF16X3,
             "bf16x6": lu.LU_TU_BF16X6}[args.prec]
-    opts = lu.default_opts(nb=args.nb)
+    opts = lu.default_opts(nb=args.nb, pf_sms=args.pf_sms)
     A0, B0 = make_inputs(n, nrhs)
     A = colmajor(n, n)
     A.copy_(torch.from_numpy(A0))

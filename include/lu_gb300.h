@@ -110,6 +110,15 @@ typedef struct {
                       look-ahead depth); PF(k) and TU(k, k+1) run at high
                       priority.  FP64/FP32 factorizations on the CUDA cores
                       (lu_factor_ex, lu_potrf_ex); 0 = static look-ahead */
+    int pf_sms;    /* > 0, with look-ahead: an SM partition of at least this many
+                      SMs (rounded up to the device's granularity, 8 on GB300)
+                      reserved for the panel-factorization leaves, and the right
+                      trailing update confined to the other SMs (two green
+                      contexts: process-local, no device setting changes); the
+                      factors are bit-identical to pf_sms = 0.  If the device or
+                      driver cannot partition, the call runs without a partition.
+                      A repeated mixed factorization is then not replayed as a
+                      graph.  0 = no partition */
 } lu_opts;
 
 /* Fills *opts with the defaults (nb = 256, lookahead = 1, steal = 1, automatic

@@ -43,7 +43,8 @@ class LuError(RuntimeError):
 class LuOpts(ctypes.Structure):
     _fields_ = [("nb", ctypes.c_int), ("lookahead", ctypes.c_int), ("steal", ctypes.c_int),
                 ("leaf", ctypes.c_int), ("pf_ctas", ctypes.c_int), ("tu_reserve", ctypes.c_int),
-                ("nsched", ctypes.c_int), ("sched", ctypes.POINTER(ctypes.c_int32)), ("rtm", ctypes.c_int)]
+                ("nsched", ctypes.c_int), ("sched", ctypes.POINTER(ctypes.c_int32)), ("rtm", ctypes.c_int),
+                ("pf_sms", ctypes.c_int)]
 
     def set_schedule(self, widths):
         """Per-step block sizes (kept alive with the options); None or [] clears."""

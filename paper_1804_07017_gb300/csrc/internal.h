@@ -26,6 +26,8 @@ void lu_auto_opts(int kind, int64_t n, lu_opts* o);
 #define LU_PF_SMEM_BUDGET (78 * 1024)
 #define LU_PF_MAX_CTAS_CLUSTER 16  // CTAs of a cluster panel leaf (non-portable cluster size)
 
+struct LuGreen;  // green-context SM partition of the panel leaves (green.cu)
+
 struct lu_context {
     int device = 0;
     int num_sms = 0;
@@ -65,6 +67,9 @@ struct lu_context {
     // Symmetric (Cholesky) trailing update: > 0 = the panel width; the updates then
     // form U12 from L21 and touch only the lower block triangle (chol.cu).
     int sym_band = 0;
+    // SM partition for the panel leaves (lu_opts.pf_sms); active during a factorization
+    LuGreen* green = nullptr;
+    bool green_active = false;
     // Per-step trace of the look-ahead schedule (lu_step_trace): timing events
     // around PU(k+1) on the panel stream and TU_right(k) on the update stream.
     struct StepTrace {
@@ -204,6 +209,19 @@ struct LuTuEngine {
 };
 
 int lu_check_opts(const lu_opts& o);
+// Green-context partition (green.cu): set up (or keep) a partition of >= part_sms
+// SMs for the leaves and the rest for the right update; release it; the rest's
+// stream and SM count; make a partition's context current (enter/leave); fork
+// the leaf stream from st (entering the leaf context) and join it back.
+int lu_green_setup(lu_context* c, int part_sms);
+void lu_green_release(lu_context* c);
+cudaStream_t lu_green_rest_stream(lu_context* c);
+int lu_green_rest_sms(lu_context* c);
+int lu_green_enter(lu_context* c, bool leaf);
+void lu_green_leave();
+int lu_green_leaf_fork(lu_context* c, cudaStream_t st, cudaStream_t* leaf_st);
+int lu_green_leaf_join(lu_context* c, cudaStream_t st);
+void* lu_current_ctx();
 // Column boundaries of the panels: panel k is [s[k], s[k+1]), from the schedule
 // (opts.sched) or the fixed nb; wmin/wmax receive the narrowest and widest width.
 void lu_panel_bounds(int64_t n, const lu_opts& o, std::vector<int64_t>* s, int* wmin, int* wmax);

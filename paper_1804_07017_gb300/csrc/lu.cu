@@ -18,6 +18,7 @@
 #include <atomic>
 #include <map>
 #include <mutex>
+#include <tuple>
 #include <utility>
 
 #include "internal.h"
@@ -37,11 +38,13 @@ void lu_set_error_string(const char* what, const char* file, int line) {
 
 int lu_func_attrs(const void* fn, int smem_bytes, bool nonportable_cluster) {
     static std::mutex mu;
-    static std::map<std::pair<int, const void*>, int> done;  // (device, kernel) -> shared-memory limit set
+    // (device, context, kernel) -> shared-memory limit set; the context distinguishes
+    // the primary context from the green contexts of an SM partition
+    static std::map<std::tuple<int, void*, const void*>, int> done;
     int dev = 0;
     LU_CHECK_CUDA(cudaGetDevice(&dev));
     std::lock_guard<std::mutex> lk(mu);
-    const auto key = std::make_pair(dev, fn);
+    const auto key = std::make_tuple(dev, lu_current_ctx(), fn);
     auto it = done.find(key);
     if (it != done.end() && it->second >= smem_bytes) return LU_SUCCESS;
     if (nonportable_cluster)
@@ -99,6 +102,7 @@ extern "C" void lu_default_opts(lu_opts* o) {
     o->nsched = 0;
     o->sched = nullptr;
     o->rtm = 0;
+    o->pf_sms = 0;
 }
 
 int lu_ctx_init(lu_context* c) {
@@ -115,6 +119,7 @@ int lu_ctx_init(lu_context* c) {
 }
 
 int lu_ctx_release(lu_context* c) {
+    lu_green_release(c);
     if (c->ws) cudaFree(c->ws);
     c->ws = nullptr;
     if (c->scratch) cudaFree(c->scratch);
@@ -257,6 +262,7 @@ int lu_check_opts(const lu_opts& o) {
     if (o.leaf < 0 || o.pf_ctas < 0 || o.pf_ctas > LU_PF_MAX_CTAS) return -1;
     if (o.tu_reserve < 0 || o.nsched < 0 || o.nsched > (1 << 20)) return -1;
     if (o.rtm < 0 || o.rtm > 1) return -1;
+    if (o.pf_sms < 0 || o.pf_sms > 4096) return -1;
     if (o.nsched > 0) {
         if (!o.sched) return -1;
         for (int i = 0; i < o.nsched; ++i)
@@ -296,7 +302,7 @@ static int trailing_update(lu_context* c, cudaStream_t st, int64_t n, T* A, int6
     const int64_t ncols = c_end - c_begin;
     // the right update's interchanges and RL2 run on at most the right update's share
     // of the SMs (as its tensor-core part), leaving the rest to the panel path
-    const int cap = which == 1 ? std::max(1, c->num_sms - c->tu_reserve) : 0;
+    const int cap = which == 1 ? (c->green_active ? lu_green_rest_sms(c) : std::max(1, c->num_sms - c->tu_reserve)) : 0;
     if (pivot && (ncols > 0 || left_cols > 0))
         LU_TRY(lu_launch_laswp_apply<T>(st, A, lda, c_begin, std::max<int64_t>(ncols, 0), 0, left_cols,
                                         plan, kb, c->num_sms, cap));
@@ -366,13 +372,20 @@ int lu_factor_blocked(lu_context* c, int64_t n, T* A, int64_t lda, int32_t* ipiv
     c->trace_steps = 0;
     if (n == 0) return lu_launch_finish_info(user, &c->sync[0], info);
     c->tu_reserve = lu_resolve_reserve(c, o);
+    // an SM partition for the panel leaves: the right update then runs on the other SMs
+    c->green_active = o.pf_sms > 0 && o.lookahead >= 1 && lu_green_setup(c, o.pf_sms) == LU_SUCCESS;
+    struct GreenOff {
+        lu_context* c;
+        ~GreenOff() { c->green_active = false; }
+    } green_off{c};
+    cudaStream_t lo = c->green_active ? lu_green_rest_stream(c) : c->lo;
     LU_CHECK_CUDA(cudaEventRecord(c->ev_fork, user));
     LU_CHECK_CUDA(cudaStreamWaitEvent(c->hi, c->ev_fork, 0));
-    LU_CHECK_CUDA(cudaStreamWaitEvent(c->lo, c->ev_fork, 0));
+    LU_CHECK_CUDA(cudaStreamWaitEvent(lo, c->ev_fork, 0));
     const int64_t nk = (int64_t)s.size() - 1;
     auto start = [&](int64_t j) { return s[(size_t)std::min(j, nk)]; };  // first column of panel j (n past the end)
     auto plan_of = [&](int64_t k) { return c->plans + (size_t)k * c->plan_stride; };
-    cudaStream_t hi = c->hi, lo = c->lo;
+    cudaStream_t hi = c->hi;
     const bool trace = c->trace_on;
     // PF(k) followed by its interchange plan (and, for the tensor-core engine, the packed L21)
     auto panel = [&](int64_t k) -> int {
@@ -424,7 +437,15 @@ int lu_factor_blocked(lu_context* c, int64_t n, T* A, int64_t lda, int32_t* ipiv
         // TU_right(k): the columns past the panels the high-priority stream owns,
         // and panel k's deferred interchanges on the columns left of it
         if (tr) LU_CHECK_CUDA(cudaEventRecord(tr->tu0, lo));
-        LU_TRY(tu(lo, k, start(k + 1 + depth), n, k0, 1));
+        if (c->green_active) {
+            // launched with the partition's context current, so the update's CTAs stay on its SMs
+            LU_TRY(lu_green_enter(c, false));
+            const int r = tu(lo, k, start(k + 1 + depth), n, k0, 1);
+            lu_green_leave();
+            LU_TRY(r);
+        } else {
+            LU_TRY(tu(lo, k, start(k + 1 + depth), n, k0, 1));
+        }
         if (tr) LU_CHECK_CUDA(cudaEventRecord(tr->tu1, lo));
         LU_CHECK_CUDA(cudaEventRecord(ev_tu[k & 1], lo));
         if (k + 1 < nk) {

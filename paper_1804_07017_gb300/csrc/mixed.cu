@@ -147,7 +147,8 @@ struct TcEngine final : LuTuEngine {
             last_cb = cb;
             last_ce = ce;
         }
-        return launch(st, A, lda, k, k0, kb, cb, ce, which, which == 0 ? grid_panel : grid_right);
+        return launch(st, A, lda, k, k0, kb, cb, ce, which,
+                      which == 0 ? grid_panel : (c->green_active ? lu_green_rest_sms(c) : grid_right));
     }
 
     float* A_ = nullptr;
@@ -241,8 +242,9 @@ static int factor_mixed(lu_context* c, int prec, int64_t n, float* A32, int64_t 
                               ((uint64_t)o.nb << 32) | ((uint64_t)o.lookahead << 16) | (uint64_t)o.steal,
                               ((uint64_t)o.leaf << 32) | (uint64_t)o.pf_ctas, (uint64_t)(uintptr_t)engine_mem,
                               (uint64_t)(uintptr_t)c->user,
-                              ((uint64_t)(uint32_t)o.tu_reserve << 32) | (uint64_t)(uint32_t)o.nsched, sched_hash};
-    bool use_graph = !lu_profile_active() && !c->trace_on && n > 0;
+                              ((uint64_t)(uint32_t)o.tu_reserve << 32) | (uint64_t)(uint32_t)o.nsched,
+                              sched_hash ^ ((uint64_t)(uint32_t)o.rtm << 40) ^ ((uint64_t)(uint32_t)o.pf_sms << 48)};
+    bool use_graph = !lu_profile_active() && !c->trace_on && n > 0 && o.pf_sms == 0;
     if (use_graph && !c->gs) {
         // the caller's stream may be the legacy default stream, which cannot be
         // captured: the graph is captured on, and replayed from, a stream of its own

@@ -236,6 +236,18 @@ namespace {
 // One level of the recursive panel: columns [j0, j0+width) over rows [j0, M);
 // [pc0, pc0+pw) is the whole panel, whose other columns a cluster leaf updates
 // with its own interchanges.
+// Runs launch(stream) on the leaf partition's stream when one is active (entered
+// and left through events on st, with its context current), else on st.
+template <typename F>
+int on_leaf_sms(lu_context* c, cudaStream_t st, F&& launch) {
+    if (!c->green_active) return launch(st);
+    cudaStream_t ls = nullptr;
+    LU_TRY(lu_green_leaf_fork(c, st, &ls));
+    const int r = launch(ls);
+    const int r2 = lu_green_leaf_join(c, st);
+    return r != LU_SUCCESS ? r : r2;
+}
+
 template <typename T>
 int panel_rec(lu_context* c, cudaStream_t st, T* A, int64_t lda, int64_t M, int64_t j0, int64_t width,
               int32_t* ipiv, const lu_opts& o, int leaf, bool cluster, int64_t pc0, int64_t pw) {
@@ -246,8 +258,10 @@ int panel_rec(lu_context* c, cudaStream_t st, T* A, int64_t lda, int64_t M, int6
             int C = 0, R = 0;
             size_t smem = 0;
             if (lu_pf_cluster_shape<T>(rows, (int)width, c->pf_smem_budget, &C, &R, &smem))
-                return lu_launch_pf_leaf_cluster<T>(st, A + j0 + j0 * lda, lda, rows, (int)width, C, R, smem, j0 - pc0,
-                                                    pc0 + pw - (j0 + width), ipiv + j0, j0, &c->sync[0]);
+                return on_leaf_sms(c, st, [&](cudaStream_t ls) {
+                    return lu_launch_pf_leaf_cluster<T>(ls, A + j0 + j0 * lda, lda, rows, (int)width, C, R, smem,
+                                                        j0 - pc0, pc0 + pw - (j0 + width), ipiv + j0, j0, &c->sync[0]);
+                });
             return LU_ERR_UNSUPPORTED;
         }
         return lu_launch_pf_leaf<T>(c, st, A + j0 + j0 * lda, lda, rows, (int)width, ipiv + j0, j0, o.pf_ctas);
@@ -263,11 +277,14 @@ int panel_rec(lu_context* c, cudaStream_t st, T* A, int64_t lda, int64_t M, int6
         size_t sa = 0, sb = 0;
         if (lu_pf_cluster_shape<T>(rows, (int)w1, c->pf_smem_budget, &Ca, &Ra, &sa) &&
             lu_pf_cluster_shape<T>(rows - w1, (int)w2, c->pf_smem_budget, &Cb, &Rb, &sb)) {
-            LU_TRY(lu_launch_pf_leaf_cluster<T>(st, A + j0 + j0 * lda, lda, rows, (int)w1, Ca, Ra, sa, j0 - pc0,
-                                                pc0 + pw - (j0 + w1), ipiv + j0, j0, &c->sync[0], (int)w2, 0));
             const int64_t jb = j0 + w1;
-            return lu_launch_pf_leaf_cluster<T>(st, A + jb + jb * lda, lda, rows - w1, (int)w2, Cb, Rb, sb, jb - pc0,
-                                                pc0 + pw - (jb + w2), ipiv + jb, jb, &c->sync[0], 0, (int)w1);
+            return on_leaf_sms(c, st, [&](cudaStream_t ls) {
+                LU_TRY(lu_launch_pf_leaf_cluster<T>(ls, A + j0 + j0 * lda, lda, rows, (int)w1, Ca, Ra, sa, j0 - pc0,
+                                                    pc0 + pw - (j0 + w1), ipiv + j0, j0, &c->sync[0], (int)w2, 0));
+                return lu_launch_pf_leaf_cluster<T>(ls, A + jb + jb * lda, lda, rows - w1, (int)w2, Cb, Rb, sb,
+                                                    jb - pc0, pc0 + pw - (jb + w2), ipiv + jb, jb, &c->sync[0], 0,
+                                                    (int)w1);
+            });
         }
     }
     LU_TRY(panel_rec<T>(c, st, A, lda, M, j0, w1, ipiv, o, leaf, cluster, pc0, pw));

@@ -218,3 +218,25 @@ def test_rtm_rejected_on_tensor_core_path(lu):
     with pytest.raises(lu.LuError) as e:
         lu.lu_factor_mixed_ex(A, ipiv, info, lu.LU_TU_BF16X6, lu.default_opts(nb=128, rtm=1))
     assert e.value.code == lu.LU_ERR_UNSUPPORTED
+
+
+@pytest.mark.parametrize("pf_sms", [16, 24])
+def test_leaf_sm_partition_identical(lu, pf_sms):
+    """An SM partition for the panel leaves (green contexts; the right update on
+    the other SMs) moves work between SMs only: the mixed and the FP64
+    factorizations are bit-identical to the unpartitioned ones, and the refined
+    solve meets eta <= 1e-14."""
+    n = 2048
+    A0 = synth.normal_matrix(n, seed=77)
+    A32 = A0.astype(np.float32).astype(np.float64)
+    ref = factor(lu, A32, torch.float32, mixed=lu.LU_TU_BF16X6, nb=256)
+    got = factor(lu, A32, torch.float32, mixed=lu.LU_TU_BF16X6, nb=256, pf_sms=pf_sms)
+    assert ref[2] == got[2] == 0 and np.array_equal(ref[1], got[1]) and np.array_equal(ref[0], got[0])
+    r64 = factor(lu, A0, torch.float64, nb=128)
+    g64 = factor(lu, A0, torch.float64, nb=128, pf_sms=pf_sms)
+    assert np.array_equal(r64[1], g64[1]) and np.array_equal(r64[0], g64[0])
+    b0 = synth.ones_rhs(A0)
+    A, B, X = dev(A0, torch.float64), dev(b0, torch.float64), dev(np.zeros_like(b0), torch.float64)
+    st, it, eta = lu.lu_gesv_mixed(A, B, X, lu.LU_TU_BF16X6, opts=lu.default_opts(nb=256, pf_sms=pf_sms))
+    torch.cuda.synchronize()
+    assert st == 0 and oracle.backward_error(A0, X.cpu().numpy(), b0) <= 1e-14
