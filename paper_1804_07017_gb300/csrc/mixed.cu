@@ -244,7 +244,7 @@ static int factor_mixed(lu_context* c, int prec, int64_t n, float* A32, int64_t 
                               (uint64_t)(uintptr_t)c->user,
                               ((uint64_t)(uint32_t)o.tu_reserve << 32) | (uint64_t)(uint32_t)o.nsched,
                               sched_hash ^ ((uint64_t)(uint32_t)o.rtm << 40) ^ ((uint64_t)(uint32_t)o.pf_sms << 48)};
-    bool use_graph = !lu_profile_active() && !c->trace_on && n > 0 && o.pf_sms == 0;
+    bool use_graph = !lu_profile_active() && !c->trace_on && n > 0;
     if (use_graph && !c->gs) {
         // the caller's stream may be the legacy default stream, which cannot be
         // captured: the graph is captured on, and replayed from, a stream of its own

@@ -230,8 +230,17 @@ def test_leaf_sm_partition_identical(lu, pf_sms):
     A0 = synth.normal_matrix(n, seed=77)
     A32 = A0.astype(np.float32).astype(np.float64)
     ref = factor(lu, A32, torch.float32, mixed=lu.LU_TU_BF16X6, nb=256)
-    got = factor(lu, A32, torch.float32, mixed=lu.LU_TU_BF16X6, nb=256, pf_sms=pf_sms)
-    assert ref[2] == got[2] == 0 and np.array_equal(ref[1], got[1]) and np.array_equal(ref[0], got[0])
+    from paper_1804_07017_gb300.api import colmajor
+    A = colmajor(n, n, dtype=torch.float32)
+    ipiv = torch.zeros(n, dtype=torch.int32, device="cuda")
+    info = torch.full((1,), -7, dtype=torch.int32, device="cuda")
+    o = lu.default_opts(nb=256, pf_sms=pf_sms)
+    for _ in range(3):  # eager, captured as a graph, replayed
+        A.copy_(torch.from_numpy(A32).float())
+        lu.lu_factor_mixed_ex(A, ipiv, info, lu.LU_TU_BF16X6, o)
+        torch.cuda.synchronize()
+        got = (A.cpu().double().numpy(), ipiv.cpu().numpy(), int(info.item()))
+        assert ref[2] == got[2] == 0 and np.array_equal(ref[1], got[1]) and np.array_equal(ref[0], got[0])
     r64 = factor(lu, A0, torch.float64, nb=128)
     g64 = factor(lu, A0, torch.float64, nb=128, pf_sms=pf_sms)
     assert np.array_equal(r64[1], g64[1]) and np.array_equal(r64[0], g64[0])
