@@ -475,7 +475,8 @@ int lu_tune_clear(void);
 /* Writes the table to the host file `path` as text lines
  * "device<TAB>kind<TAB>ceil(log2 n)<TAB>nb<TAB>ms", followed for a tuned plan by
  * "<TAB>reserve<TAB>depth<TAB>schedule" (comma-separated block sizes, "-" for
- * none).  Returns 0, -1 (NULL path) or LU_ERR_IO. */
+ * none) and, when the plan has a leaf SM partition, "<TAB>pf_sms".  Returns 0,
+ * -1 (NULL path) or LU_ERR_IO. */
 int lu_tune_save(const char *path);
 /* Merges the lines of such a file into the table (an entry replaces one with the
  * same key).  Every line is validated first; on any malformed line nothing is
@@ -543,7 +544,8 @@ int lu_geqrf_mixed_ex(lu_handle handle, lu_prec prec, int64_t m, int64_t n, floa
  *      of 128 for LU_TU_FP8, on the tensor-core kinds);
  *   2. with look-ahead, the SMs the right update leaves to the panel path
  *      (lu_opts.tu_reserve) among 1/12, 1/6, 1/4 and 1/3 of the SMs;
- *   3. with look-ahead, the depth 1 or 2;
+ *   3. with look-ahead, the depth 1 or 2, then an SM partition of 16, 24 or 32
+ *      SMs for the panel leaves (lu_opts.pf_sms);
  *   4. a per-step schedule, the GPU form of the paper's early termination
  *      (Sec. 4.2: b adjusted on the fly when PU(k+1) and TU_right(k) are out of
  *      balance): the steps of the factorization at b/2, b and 2b are traced
@@ -569,15 +571,16 @@ int lu_tune_plan(lu_handle h, int kind, int64_t n, int reps, const lu_opts *opts
                  int cap, float *best_ms, float *fixed_ms);
 /* Stores a plan for (device, kind, ceil(log2 n)): nb, reserve (0 = automatic),
  * depth (0 = the caller's), a schedule of nsched block sizes (host array, may
- * be NULL when nsched is 0) and its time.  Returns 0 or -i for the i-th
- * argument (-7: a width outside 1..1024, or not a multiple of 128 for FP8). */
+ * be NULL when nsched is 0), the leaf SM partition pf_sms (0 = none) and its
+ * time.  Returns 0 or -i for the i-th argument (-7: a width outside 1..1024,
+ * or not a multiple of 128 for FP8). */
 int lu_tune_plan_set(const char *device, int kind, int64_t n, int nb, int reserve, int depth, const int32_t *sched,
-                     int nsched, float ms);
+                     int nsched, int pf_sms, float ms);
 /* Reads the plan for (device, kind, ceil(log2 n)) into the non-NULL outputs
  * (at most cap schedule entries; *nsched receives the full length).  Returns 1
  * when an entry exists, else 0. */
 int lu_tune_plan_get(const char *device, int kind, int64_t n, int *nb, int *reserve, int *depth, int32_t *sched,
-                     int cap, int *nsched);
+                     int cap, int *nsched, int *pf_sms);
 
 /*
  * lu_step_trace -- diagnostic of the look-ahead schedule (Sec. 4): with enable

@@ -111,9 +111,10 @@ _SIGNATURES = {
                            ctypes.POINTER(ctypes.c_int32), i32, ctypes.POINTER(ctypes.c_float),
                            ctypes.POINTER(ctypes.c_float)]),
     "lu_tune_plan_set": (i32, [ctypes.c_char_p, i32, i64, i32, i32, i32, ctypes.POINTER(ctypes.c_int32), i32,
-                               ctypes.c_float]),
+                               i32, ctypes.c_float]),
     "lu_tune_plan_get": (i32, [ctypes.c_char_p, i32, i64, ctypes.POINTER(i32), ctypes.POINTER(i32),
-                               ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_int32), i32, ctypes.POINTER(i32)]),
+                               ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_int32), i32, ctypes.POINTER(i32),
+                               ctypes.POINTER(i32)]),
     "lu_geqrf_ex": (i32, [vp, i32, i64, i64, vp, i64, vp, ctypes.POINTER(LuOpts), vp]),
     "lu_potrf_mixed_ex": (i32, [vp, i32, i64, vp, i64, ctypes.POINTER(LuOpts), vp]),
     "lu_geqrf_mixed_ex": (i32, [vp, i32, i64, i64, vp, i64, vp, ctypes.POINTER(LuOpts), vp]),

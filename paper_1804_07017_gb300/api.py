@@ -319,15 +319,15 @@ def lu_tune_plan(kind: int, n: int, reps: int = 3, opts: LuOpts | None = None, h
 
 
 def lu_tune_plan_get(kind: int, n: int, device: str | None = None):
-    """(nb, reserve, depth, schedule) stored for (device, kind, ceil(log2 n)), or None."""
-    nb, res, dep, cnt = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    """(nb, reserve, depth, schedule, pf_sms) stored for (device, kind, ceil(log2 n)), or None."""
+    nb, res, dep, cnt, pf = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
     L = lib()
     if not L.lu_tune_plan_get(_dev(device), int(kind), int(n), ctypes.byref(nb), ctypes.byref(res),
-                              ctypes.byref(dep), None, 0, ctypes.byref(cnt)):
+                              ctypes.byref(dep), None, 0, ctypes.byref(cnt), ctypes.byref(pf)):
         return None
     buf = (ctypes.c_int32 * max(cnt.value, 1))()
-    L.lu_tune_plan_get(_dev(device), int(kind), int(n), None, None, None, buf, cnt.value, None)
-    return nb.value, res.value, dep.value, [int(buf[i]) for i in range(cnt.value)]
+    L.lu_tune_plan_get(_dev(device), int(kind), int(n), None, None, None, buf, cnt.value, None, None)
+    return nb.value, res.value, dep.value, [int(buf[i]) for i in range(cnt.value)], pf.value
 
 
 def lu_step_trace(enable: bool, handle: Handle | None = None) -> Handle:

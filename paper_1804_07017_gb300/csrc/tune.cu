@@ -33,6 +33,7 @@ struct TuneEntry {
     int reserve = 0;               // 0: not tuned (automatic)
     int depth = 0;                 // 0: not tuned (the caller's)
     std::vector<int32_t> sched;    // empty: the fixed nb
+    int pf_sms = 0;                // SM partition for the panel leaves (0: none)
 };
 
 std::mutex g_mu;
@@ -150,12 +151,13 @@ void lu_auto_opts(int kind, int64_t n, lu_opts* o) {
             }
             if (o->tu_reserve == 0 && e.reserve > 0) o->tu_reserve = e.reserve;
             if (o->lookahead >= 1 && e.depth >= 1) o->lookahead = e.depth;
+            if (o->lookahead >= 1 && o->pf_sms == 0 && e.pf_sms > 0) o->pf_sms = e.pf_sms;
             return;
         }
 }
 
 extern "C" int lu_tune_plan_set(const char* device, int kind, int64_t n, int nb, int reserve, int depth,
-                                const int32_t* sched, int nsched, float ms) {
+                                const int32_t* sched, int nsched, int pf_sms, float ms) {
     std::string dev;
     if (!resolve_device(device, &dev)) return -1;
     if (!kind_valid(kind)) return -2;
@@ -166,6 +168,7 @@ extern "C" int lu_tune_plan_set(const char* device, int kind, int64_t n, int nb,
     if (nsched < 0 || nsched > (1 << 20) || (nsched > 0 && !sched)) return -8;
     for (int i = 0; i < nsched; ++i)
         if (!width_ok(kind, sched[i])) return -7;
+    if (pf_sms < 0 || pf_sms > 4096) return -9;
     TuneEntry e;
     e.device = dev;
     e.kind = kind;
@@ -175,13 +178,14 @@ extern "C" int lu_tune_plan_set(const char* device, int kind, int64_t n, int nb,
     e.reserve = reserve;
     e.depth = depth;
     e.sched.assign(sched, sched + nsched);
+    e.pf_sms = pf_sms;
     std::lock_guard<std::mutex> lk(g_mu);
     put_locked(e);
     return LU_SUCCESS;
 }
 
 extern "C" int lu_tune_plan_get(const char* device, int kind, int64_t n, int* nb, int* reserve, int* depth,
-                                int32_t* sched, int cap, int* nsched) {
+                                int32_t* sched, int cap, int* nsched, int* pf_sms) {
     if (n < 1) return 0;
     std::string dev;
     if (!resolve_device(device, &dev)) return 0;
@@ -193,6 +197,7 @@ extern "C" int lu_tune_plan_get(const char* device, int kind, int64_t n, int* nb
             if (reserve) *reserve = e.reserve;
             if (depth) *depth = e.depth;
             if (nsched) *nsched = (int)e.sched.size();
+            if (pf_sms) *pf_sms = e.pf_sms;
             if (sched)
                 for (int i = 0; i < cap && i < (int)e.sched.size(); ++i) sched[i] = e.sched[i];
             return 1;
@@ -238,11 +243,12 @@ extern "C" int lu_tune_save(const char* path) {
         for (const auto& e : g_table) {
             ok = ok && std::fprintf(f, "%s\t%d\t%d\t%d\t%.6g", e.device.c_str(), e.kind, e.bucket, e.nb,
                                     (double)e.ms) > 0;
-            if (e.reserve > 0 || e.depth > 0 || !e.sched.empty()) {
+            if (e.reserve > 0 || e.depth > 0 || !e.sched.empty() || e.pf_sms > 0) {
                 ok = ok && std::fprintf(f, "\t%d\t%d\t", e.reserve, e.depth) > 0;
                 if (e.sched.empty()) ok = ok && std::fputc('-', f) != EOF;
                 for (size_t i = 0; i < e.sched.size(); ++i)
                     ok = ok && std::fprintf(f, i ? ",%d" : "%d", (int)e.sched[i]) > 0;
+                if (e.pf_sms > 0) ok = ok && std::fprintf(f, "\t%d", e.pf_sms) > 0;
             }
             ok = ok && std::fputc('\n', f) != EOF;
         }
@@ -281,6 +287,10 @@ static bool parse_line(const std::string& line, TuneEntry* out) {
                 if (*p != ',') break;
                 ++p;
             }
+        }
+        if (*p == '\t') {
+            if (std::sscanf(p, "\t%d%n", &e.pf_sms, &used) != 1 || e.pf_sms < 0 || e.pf_sms > 4096) return false;
+            p += used;
         }
     }
     if (*p != '\0') return false;
@@ -485,6 +495,8 @@ extern "C" int lu_tune_plan(lu_handle h, int kind, int64_t n, int reps, const lu
     o.nb = 256;
     o.nsched = 0;
     o.sched = nullptr;
+    o.tu_reserve = 0;
+    o.pf_sms = 0;
     if (lu_check_opts(o) != 0) return -5;
     if (!best) return -6;
     if (cap < 0 || (cap > 0 && !sched)) return -8;
@@ -544,6 +556,20 @@ extern "C" int lu_tune_plan(lu_handle h, int kind, int64_t n, int reps, const lu
             if (d == b.lookahead) continue;
             lu_opts t = b;
             t.lookahead = d;
+            float ms = -1.f;
+            if ((rc = time_opts(r, t, reps, &ms)) != LU_SUCCESS) break;
+            if (ms >= 0.f && ms < t_best) {
+                t_best = ms;
+                b = t;
+            }
+        }
+    }
+    // 3b. with look-ahead, an SM partition for the panel leaves
+    if (rc == LU_SUCCESS && t_best >= 0.f && o.lookahead) {
+        const int parts[] = {16, 24, 32};
+        for (int pv : parts) {
+            lu_opts t = b;
+            t.pf_sms = pv;
             float ms = -1.f;
             if ((rc = time_opts(r, t, reps, &ms)) != LU_SUCCESS) break;
             if (ms >= 0.f && ms < t_best) {
@@ -657,6 +683,7 @@ extern "C" int lu_tune_plan(lu_handle h, int kind, int64_t n, int reps, const lu
     e.reserve = o.lookahead ? b.tu_reserve : 0;
     e.depth = o.lookahead ? b.lookahead : 0;
     e.sched = plan;
+    e.pf_sms = o.lookahead ? b.pf_sms : 0;
     std::lock_guard<std::mutex> lk(g_mu);
     put_locked(e);
     return LU_SUCCESS;

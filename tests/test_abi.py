@@ -119,44 +119,47 @@ def test_tune_plan_table_round_trip(built, tmp_path):
     dev = b"Plan GPU"
     assert L.lu_tune_clear() == 0
     sched = (C.c_int32 * 4)(512, 384, 256, 128)
-    assert L.lu_tune_plan_set(dev, pkg.LU_TU_BF16X6, 16384, 256, 25, 2, sched, 4, 75.0) == 0
+    assert L.lu_tune_plan_set(dev, pkg.LU_TU_BF16X6, 16384, 256, 25, 2, sched, 4, 24, 75.0) == 0
     assert L.lu_tune_set(dev, pkg.LU_TUNE_F64, 8192, 128, 300.0) == 0
-    nb, res, dep, cnt = C.c_int(), C.c_int(), C.c_int(), C.c_int()
+    nb, res, dep, cnt, pf = C.c_int(), C.c_int(), C.c_int(), C.c_int(), C.c_int()
     out = (C.c_int32 * 8)()
     assert L.lu_tune_plan_get(dev, pkg.LU_TU_BF16X6, 10000, C.byref(nb), C.byref(res), C.byref(dep), out, 8,
-                              C.byref(cnt)) == 1
-    assert (nb.value, res.value, dep.value, cnt.value) == (256, 25, 2, 4) and list(out[:4]) == [512, 384, 256, 128]
+                              C.byref(cnt), C.byref(pf)) == 1
+    assert (nb.value, res.value, dep.value, cnt.value, pf.value) == (256, 25, 2, 4, 24)
+    assert list(out[:4]) == [512, 384, 256, 128]
     assert L.lu_tune_get(dev, pkg.LU_TU_BF16X6, 16384) == 256
-    assert L.lu_tune_plan_get(dev, pkg.LU_TU_BF16, 16384, None, None, None, None, 0, None) == 0
+    assert L.lu_tune_plan_get(dev, pkg.LU_TU_BF16, 16384, None, None, None, None, 0, None, None) == 0
     # argument checks
-    assert L.lu_tune_plan_set(dev, pkg.LU_TU_FP8, 16384, 128, 0, 1, (C.c_int32 * 1)(192), 1, 0.0) == -7
-    assert L.lu_tune_plan_set(dev, pkg.LU_TU_BF16, 16384, 256, -1, 1, None, 0, 0.0) == -5
-    assert L.lu_tune_plan_set(dev, pkg.LU_TU_BF16, 16384, 256, 0, 3, None, 0, 0.0) == -6
-    assert L.lu_tune_plan_set(dev, pkg.LU_TU_BF16, 16384, 256, 0, 1, None, 2, 0.0) == -8
+    assert L.lu_tune_plan_set(dev, pkg.LU_TU_FP8, 16384, 128, 0, 1, (C.c_int32 * 1)(192), 1, 0, 0.0) == -7
+    assert L.lu_tune_plan_set(dev, pkg.LU_TU_BF16, 16384, 256, -1, 1, None, 0, 0, 0.0) == -5
+    assert L.lu_tune_plan_set(dev, pkg.LU_TU_BF16, 16384, 256, 0, 3, None, 0, 0, 0.0) == -6
+    assert L.lu_tune_plan_set(dev, pkg.LU_TU_BF16, 16384, 256, 0, 1, None, 2, 0, 0.0) == -8
     path = tmp_path / "plan.txt"
     assert L.lu_tune_save(str(path).encode()) == 0
     lines = sorted(path.read_text().splitlines())
-    assert lines == sorted(["Plan GPU\t6\t14\t256\t75\t25\t2\t512,384,256,128", "Plan GPU\t100\t13\t128\t300"])
+    assert lines == sorted(["Plan GPU\t6\t14\t256\t75\t25\t2\t512,384,256,128\t24", "Plan GPU\t100\t13\t128\t300"])
     assert L.lu_tune_clear() == 0 and L.lu_tune_load(str(path).encode()) == 0
     assert L.lu_tune_plan_get(dev, pkg.LU_TU_BF16X6, 16384, C.byref(nb), C.byref(res), C.byref(dep), out, 2,
-                              C.byref(cnt)) == 1
-    assert (nb.value, res.value, dep.value, cnt.value) == (256, 25, 2, 4) and list(out[:2]) == [512, 384]
+                              C.byref(cnt), C.byref(pf)) == 1
+    assert (nb.value, res.value, dep.value, cnt.value, pf.value) == (256, 25, 2, 4, 24)
+    assert list(out[:2]) == [512, 384]
     # a plan without a schedule
-    assert L.lu_tune_plan_set(dev, pkg.LU_TU_BF16, 4096, 192, 12, 1, None, 0, 5.0) == 0
+    assert L.lu_tune_plan_set(dev, pkg.LU_TU_BF16, 4096, 192, 12, 1, None, 0, 0, 5.0) == 0
     assert L.lu_tune_save(str(path).encode()) == 0
     assert "Plan GPU\t0\t12\t192\t5\t12\t1\t-" in path.read_text().splitlines()
     for bad in ["Plan GPU\t6\t14\t256\t75\t25\t2\t512,,256\n", "Plan GPU\t6\t14\t256\t75\t25\t3\t-\n",
                 "Plan GPU\t6\t14\t256\t75\t25\t2\t2000\n", "Plan GPU\t6\t14\t256\t75\t25\n",
-                "Plan GPU\t2\t14\t128\t75\t0\t1\t128,192\n", "Plan GPU\t6\t14\t256\t75\t25\t2\t256x\n"]:
+                "Plan GPU\t2\t14\t128\t75\t0\t1\t128,192\n", "Plan GPU\t6\t14\t256\t75\t25\t2\t256x\n",
+                "Plan GPU\t6\t14\t256\t75\t25\t2\t-\t-3\n", "Plan GPU\t6\t14\t256\t75\t25\t2\t-\t16\t1\n"]:
         f = tmp_path / "bad.txt"
         f.write_text("New GPU\t6\t14\t512\t1\n" + bad)
         assert L.lu_tune_load(str(f).encode()) == pkg.LU_ERR_IO, bad
     assert L.lu_tune_get(b"New GPU", pkg.LU_TU_BF16X6, 16384) == 0
     # a long schedule (over the 1 KiB read buffer) round-trips
     long = (C.c_int32 * 600)(*([64] * 600))
-    assert L.lu_tune_plan_set(dev, pkg.LU_TU_BF16X6, 32768, 64, 0, 0, long, 600, 1.0) == 0
+    assert L.lu_tune_plan_set(dev, pkg.LU_TU_BF16X6, 32768, 64, 0, 0, long, 600, 0, 1.0) == 0
     assert L.lu_tune_save(str(path).encode()) == 0
     assert L.lu_tune_clear() == 0 and L.lu_tune_load(str(path).encode()) == 0
-    assert L.lu_tune_plan_get(dev, pkg.LU_TU_BF16X6, 32768, None, None, None, None, 0, C.byref(cnt)) == 1
+    assert L.lu_tune_plan_get(dev, pkg.LU_TU_BF16X6, 32768, None, None, None, None, 0, C.byref(cnt), None) == 1
     assert cnt.value == 600
     assert L.lu_tune_clear() == 0

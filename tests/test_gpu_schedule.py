@@ -153,12 +153,13 @@ def test_tune_plan_and_nb_zero(lu):
     plan = lu.lu_tune_plan_get(lu.LU_TU_BF16X6, n)
     assert plan is not None and plan[0] == best.nb and plan[3] == sched
     assert best.lookahead in (1, 2) and (best.tu_reserve == 0 or best.tu_reserve >= 4)  # 0: automatic
+    assert plan[4] == best.pf_sms
     print(f"\n[tune plan n={n} bf16x6] nb={best.nb} reserve={best.tu_reserve} depth={best.lookahead} "
-          f"schedule={sched} best {ms:.2f} ms, fixed {fixed:.2f} ms")
+          f"pf_sms={best.pf_sms} schedule={sched} best {ms:.2f} ms, fixed {fixed:.2f} ms")
     A0 = synth.normal_matrix(n, seed=74).astype(np.float32).astype(np.float64)
     LU0, p0, i0 = factor(lu, A0, torch.float32, mixed=lu.LU_TU_BF16X6, nb=0)
     LU1, p1, i1 = factor(lu, A0, torch.float32, mixed=lu.LU_TU_BF16X6, nb=best.nb, sched=sched,
-                         lookahead=best.lookahead, tu_reserve=best.tu_reserve)
+                         lookahead=best.lookahead, tu_reserve=best.tu_reserve, pf_sms=best.pf_sms)
     assert i0 == i1 == 0 and np.array_equal(p0, p1) and np.array_equal(LU0, LU1)
     assert oracle.factor_error(A0, LU0, p0) <= 1e-5
 
