@@ -71,7 +71,7 @@ struct LuGreen {
     int rest_sms = 0;        // SMs of the rest
     CUgreenCtx g_leaf = nullptr, g_rest = nullptr;
     CUcontext c_leaf = nullptr, c_rest = nullptr;
-    cudaStream_t s_leaf = nullptr, s_rest = nullptr, s_rest_hi = nullptr;
+    cudaStream_t s_leaf = nullptr, s_rest = nullptr;
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;
 };
 
@@ -103,16 +103,14 @@ int lu_green_setup(lu_context* c, int part_sms) {
     g->rest_sms = (int)rest.sm.smCount;
     int lo_prio = 0, hi_prio = 0;
     cudaDeviceGetStreamPriorityRange(&lo_prio, &hi_prio);
-    CUstream sl = nullptr, sr = nullptr, srh = nullptr;
+    CUstream sl = nullptr, sr = nullptr;
     bool ok = a.create(&g->g_leaf, d_part, (CUdevice)c->device, CU_GREEN_CTX_DEFAULT_STREAM) == CUDA_SUCCESS &&
               a.create(&g->g_rest, d_rest, (CUdevice)c->device, CU_GREEN_CTX_DEFAULT_STREAM) == CUDA_SUCCESS &&
               a.fromGreen(&g->c_leaf, g->g_leaf) == CUDA_SUCCESS && a.fromGreen(&g->c_rest, g->g_rest) == CUDA_SUCCESS &&
               a.stream(&sl, g->g_leaf, CU_STREAM_NON_BLOCKING, hi_prio) == CUDA_SUCCESS &&
-              a.stream(&sr, g->g_rest, CU_STREAM_NON_BLOCKING, lo_prio) == CUDA_SUCCESS &&
-              a.stream(&srh, g->g_rest, CU_STREAM_NON_BLOCKING, hi_prio) == CUDA_SUCCESS;
+              a.stream(&sr, g->g_rest, CU_STREAM_NON_BLOCKING, lo_prio) == CUDA_SUCCESS;
     g->s_leaf = reinterpret_cast<cudaStream_t>(sl);
     g->s_rest = reinterpret_cast<cudaStream_t>(sr);
-    g->s_rest_hi = reinterpret_cast<cudaStream_t>(srh);
     ok = ok && cudaEventCreateWithFlags(&g->ev_in, cudaEventDisableTiming) == cudaSuccess &&
          cudaEventCreateWithFlags(&g->ev_out, cudaEventDisableTiming) == cudaSuccess;
     c->green = g;
@@ -156,7 +154,6 @@ void lu_green_release(lu_context* c) {
     cudaDeviceSynchronize();
     if (g->s_leaf) cudaStreamDestroy(g->s_leaf);
     if (g->s_rest) cudaStreamDestroy(g->s_rest);
-    if (g->s_rest_hi) cudaStreamDestroy(g->s_rest_hi);
     if (g->ev_in) cudaEventDestroy(g->ev_in);
     if (g->ev_out) cudaEventDestroy(g->ev_out);
     if (a.ok) {
@@ -169,7 +166,6 @@ void lu_green_release(lu_context* c) {
 }
 
 cudaStream_t lu_green_rest_stream(lu_context* c) { return c->green ? c->green->s_rest : nullptr; }
-cudaStream_t lu_green_rest_hi_stream(lu_context* c) { return c->green ? c->green->s_rest_hi : nullptr; }
 int lu_green_rest_sms(lu_context* c) { return c->green ? c->green->rest_sms : c->num_sms; }
 
 int lu_green_enter(lu_context* c, bool leaf) {

@@ -40,8 +40,7 @@ struct lu_context {
     char* ws = nullptr;
     size_t ws_bytes = 0;
     LuSync* sync = nullptr;   // [0] panel leaves + factorization errors, [1] triangular solves,
-                              // [2] standalone tensor-core update, [3] lu_factor info, [4]/[5] tile counters,
-                              // [6] wait self-test, [7] tile counter of the split look-ahead update
+                              // [2] standalone tensor-core update, [3] lu_factor info, [4]/[5] tile counters
     void* pf_slots = nullptr; // panel-leaf exchange slots
     int32_t* plans = nullptr; // per-panel interchange plans
     size_t plan_stride = 0;   // int32 entries per plan
@@ -68,14 +67,6 @@ struct lu_context {
     // Symmetric (Cholesky) trailing update: > 0 = the panel width; the updates then
     // form U12 from L21 and touch only the lower block triangle (chol.cu).
     int sym_band = 0;
-    // Split look-ahead update: TU_k on panel k+1's columns beyond its first leaf
-    // runs on `aux` (event ev_aux0 in, ev_aux out) while that leaf is factored;
-    // pf_gate (set for the next panel factorization) is the event its other
-    // launches wait for, pf_gate_cols the leading columns the first leaf covers.
-    cudaStream_t aux = nullptr;
-    cudaEvent_t ev_aux0 = nullptr, ev_aux = nullptr;
-    cudaEvent_t pf_gate = nullptr;
-    int64_t pf_gate_cols = 0;
     // SM partition for the panel leaves (lu_opts.pf_sms); active during a factorization
     LuGreen* green = nullptr;
     bool green_active = false;
@@ -230,11 +221,7 @@ int lu_green_enter(lu_context* c, bool leaf);
 void lu_green_leave();
 int lu_green_leaf_fork(lu_context* c, cudaStream_t st, cudaStream_t* leaf_st);
 int lu_green_leaf_join(lu_context* c, cudaStream_t st);
-cudaStream_t lu_green_rest_hi_stream(lu_context* c);
 void* lu_current_ctx();
-// Width of the first leaf-level node of a recursive panel of `width` columns
-// (the node whose leaf or leaf pair is launched first).
-int64_t lu_panel_first_node(int64_t width);
 // Column boundaries of the panels: panel k is [s[k], s[k+1]), from the schedule
 // (opts.sched) or the fixed nb; wmin/wmax receive the narrowest and widest width.
 void lu_panel_bounds(int64_t n, const lu_opts& o, std::vector<int64_t>* s, int* wmin, int* wmax);

@@ -112,9 +112,8 @@ int lu_ctx_init(lu_context* c) {
     LU_CHECK_CUDA(cudaDeviceGetStreamPriorityRange(&lo_prio, &hi_prio));
     LU_CHECK_CUDA(cudaStreamCreateWithPriority(&c->hi, cudaStreamNonBlocking, hi_prio));
     LU_CHECK_CUDA(cudaStreamCreateWithPriority(&c->lo, cudaStreamNonBlocking, lo_prio));
-    LU_CHECK_CUDA(cudaStreamCreateWithPriority(&c->aux, cudaStreamNonBlocking, hi_prio));
     cudaEvent_t* evs[] = {&c->ev_fork, &c->ev_pf, &c->ev_tu, &c->ev_join_hi, &c->ev_join_lo, &c->ev_steal,
-                          &c->ev_tu2, &c->ev_aux0, &c->ev_aux};
+                          &c->ev_tu2};
     for (cudaEvent_t* e : evs) LU_CHECK_CUDA(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
     return LU_SUCCESS;
 }
@@ -138,8 +137,7 @@ int lu_ctx_release(lu_context* c) {
     if (c->gs) cudaStreamDestroy(c->gs);
     c->ev_g0 = c->ev_g1 = nullptr;
     c->gs = nullptr;
-    cudaEvent_t evs[] = {c->ev_fork, c->ev_pf, c->ev_tu, c->ev_join_hi, c->ev_join_lo, c->ev_steal, c->ev_tu2,
-                         c->ev_aux0, c->ev_aux};
+    cudaEvent_t evs[] = {c->ev_fork, c->ev_pf, c->ev_tu, c->ev_join_hi, c->ev_join_lo, c->ev_steal, c->ev_tu2};
     for (cudaEvent_t e : evs)
         if (e) cudaEventDestroy(e);
     if (c->rtm_exec) cudaGraphExecDestroy(c->rtm_exec);
@@ -165,7 +163,6 @@ int lu_ctx_release(lu_context* c) {
             if (e) cudaEventDestroy(e);
     }
     c->trace.clear();
-    if (c->aux) cudaStreamDestroy(c->aux);
     if (c->hi) cudaStreamDestroy(c->hi);
     if (c->lo) cudaStreamDestroy(c->lo);
     return LU_SUCCESS;
@@ -397,10 +394,6 @@ int lu_factor_blocked(lu_context* c, int64_t n, T* A, int64_t lda, int32_t* ipiv
             LU_TRY(lu_panel_nopiv<T>(hi, A, lda, n, k0, kb, &c->sync[0]));
         } else {
             LU_TRY(lu_panel_recursive<T>(c, hi, A, lda, n, k0, kb, ipiv, o));
-            if (c->pf_gate) {  // not taken by the panel: wait for the split update here
-                LU_CHECK_CUDA(cudaStreamWaitEvent(hi, c->pf_gate, 0));
-                c->pf_gate = nullptr;
-            }
             LU_TRY(lu_launch_laswp_plan(hi, ipiv, k0, k0 + kb, plan_of(k)));
         }
         if (eng && eng->uses_tc(kb) && k0 + kb < n) LU_TRY(eng->pack_panel(hi, (const float*)A, lda, k, k0, kb));
@@ -438,27 +431,7 @@ int lu_factor_blocked(lu_context* c, int64_t n, T* A, int64_t lda, int32_t* ipiv
         // TU_k on panel k+1, then PF_{k+1}.  TU_k^L (a few narrow launches) is
         // issued before TU_right(k) is released, so that it does not wait behind
         // the right update's thousands of CTAs; PF_{k+1} then overlaps TU_right(k).
-        // TU_k on panel k+1 is split at its first leaf node: that part first on the
-        // panel stream, the rest on the auxiliary stream while the leaf runs (the
-        // panel waits for it through c->pf_gate before touching those columns)
-        const int64_t first = k + 1 < nk ? lu_panel_first_node(start(k + 2) - start(k + 1)) : 0;
-        const bool split = pivot && depth >= 1 && k + 1 < nk && first < start(k + 2) - start(k + 1) &&
-                           !o.rtm && o.leaf == 0;
-        if (split) {
-            cudaStream_t ax = c->green_active ? lu_green_rest_hi_stream(c) : c->aux;
-            LU_CHECK_CUDA(cudaEventRecord(c->ev_aux0, hi));
-            LU_TRY(tu(hi, k, start(k + 1), start(k + 1) + first, 0, 0));
-            LU_CHECK_CUDA(cudaStreamWaitEvent(ax, c->ev_aux0, 0));
-            if (c->green_active) LU_TRY(lu_green_enter(c, false));
-            const int ra = tu(ax, k, start(k + 1) + first, start(k + 2), 0, 2);
-            if (c->green_active) lu_green_leave();
-            LU_TRY(ra);
-            LU_CHECK_CUDA(cudaEventRecord(c->ev_aux, ax));
-            c->pf_gate = c->ev_aux;
-            c->pf_gate_cols = first;
-        } else if (k + 1 < nk) {
-            LU_TRY(tu(hi, k, start(k + 1), start(k + 2), 0, 0));
-        }
+        if (k + 1 < nk) LU_TRY(tu(hi, k, start(k + 1), start(k + 2), 0, 0));
         LU_CHECK_CUDA(cudaEventRecord(c->ev_pf, hi));
         LU_CHECK_CUDA(cudaStreamWaitEvent(lo, c->ev_pf, 0));
         // TU_right(k): the columns past the panels the high-priority stream owns,

@@ -93,7 +93,7 @@ struct TcEngine final : LuTuEngine {
     int nbuf = 2;
     char* alo[kMaxBuf] = {nullptr, nullptr, nullptr};
     char* blo[kMaxBuf] = {nullptr, nullptr, nullptr};
-    int* counter[3] = {nullptr, nullptr, nullptr};  // panel stream, right update, split look-ahead update
+    int* counter[2] = {nullptr, nullptr};
     int* error = nullptr;
     int grid_panel = 0, grid_right = 0, grid_steal = 0;
     int band = 0;  // > 0: symmetric (Cholesky) update of the lower block triangle only
@@ -147,9 +147,8 @@ struct TcEngine final : LuTuEngine {
             last_cb = cb;
             last_ce = ce;
         }
-        const int grid = which == 1 ? (c->green_active ? lu_green_rest_sms(c) : grid_right)
-                                    : (which == 2 && c->green_active ? lu_green_rest_sms(c) : grid_panel);
-        return launch(st, A, lda, k, k0, kb, cb, ce, which, grid);
+        return launch(st, A, lda, k, k0, kb, cb, ce, which,
+                      which == 0 ? grid_panel : (c->green_active ? lu_green_rest_sms(c) : grid_right));
     }
 
     float* A_ = nullptr;
@@ -206,7 +205,6 @@ int setup_engine(TcEngine& e, lu_context* c, int prec, int64_t n, char* base, fl
     }
     e.counter[0] = (int*)&c->sync[4].ticket;
     e.counter[1] = (int*)&c->sync[5].ticket;
-    e.counter[2] = (int*)&c->sync[7].ticket;
     e.error = &c->sync[0].error;
     e.A_ = A;
     e.lda_ = lda;

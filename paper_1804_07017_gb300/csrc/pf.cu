@@ -248,50 +248,22 @@ int on_leaf_sms(lu_context* c, cudaStream_t st, F&& launch) {
     return r != LU_SUCCESS ? r : r2;
 }
 
-// The panel's columns beyond its first leaf node may still be receiving TU_k
-// (c->pf_gate, see lu_factor_blocked): the first cluster leaf node then keeps
-// its interchanges to its own columns, and afterwards, once the gate event has
-// fired, they are applied to the rest of the panel; any other first launch
-// simply waits for the gate.
-static int consume_gate(lu_context* c, cudaStream_t st) {
-    if (!c->pf_gate) return LU_SUCCESS;
-    LU_CHECK_CUDA(cudaStreamWaitEvent(st, c->pf_gate, 0));
-    c->pf_gate = nullptr;
-    return LU_SUCCESS;
-}
-
-template <typename T>
-int gated_rest(lu_context* c, cudaStream_t st, T* A, int64_t lda, int64_t j0, int64_t width, int32_t* ipiv,
-               int64_t pc0, int64_t pw) {
-    LU_TRY(consume_gate(c, st));
-    const int64_t rest = pc0 + pw - (j0 + width);
-    if (rest <= 0) return LU_SUCCESS;
-    LU_TRY(lu_launch_laswp_plan(st, ipiv, j0, j0 + width, c->plan_tmp));
-    return lu_launch_laswp_apply<T>(st, A, lda, j0 + width, rest, 0, 0, c->plan_tmp, width, c->num_sms);
-}
-
 template <typename T>
 int panel_rec(lu_context* c, cudaStream_t st, T* A, int64_t lda, int64_t M, int64_t j0, int64_t width,
               int32_t* ipiv, const lu_opts& o, int leaf, bool cluster, int64_t pc0, int64_t pw) {
     if (width <= 0) return LU_SUCCESS;
     const int64_t rows = M - j0;
-    const bool gated = c->pf_gate && cluster && j0 == pc0 && width == c->pf_gate_cols;
     if (width <= leaf) {
         if (cluster) {
             int C = 0, R = 0;
             size_t smem = 0;
-            if (lu_pf_cluster_shape<T>(rows, (int)width, c->pf_smem_budget, &C, &R, &smem)) {
-                if (!gated) LU_TRY(consume_gate(c, st));
-                const int64_t right = gated ? 0 : pc0 + pw - (j0 + width);
-                LU_TRY(on_leaf_sms(c, st, [&](cudaStream_t ls) {
+            if (lu_pf_cluster_shape<T>(rows, (int)width, c->pf_smem_budget, &C, &R, &smem))
+                return on_leaf_sms(c, st, [&](cudaStream_t ls) {
                     return lu_launch_pf_leaf_cluster<T>(ls, A + j0 + j0 * lda, lda, rows, (int)width, C, R, smem,
-                                                        j0 - pc0, right, ipiv + j0, j0, &c->sync[0]);
-                }));
-                return gated ? gated_rest<T>(c, st, A, lda, j0, width, ipiv, pc0, pw) : LU_SUCCESS;
-            }
+                                                        j0 - pc0, pc0 + pw - (j0 + width), ipiv + j0, j0, &c->sync[0]);
+                });
             return LU_ERR_UNSUPPORTED;
         }
-        LU_TRY(consume_gate(c, st));
         return lu_launch_pf_leaf<T>(c, st, A + j0 + j0 * lda, lda, rows, (int)width, ipiv + j0, j0, o.pf_ctas);
     }
     int64_t w1 = ((width / 2 + 7) / 8) * 8;
@@ -306,17 +278,13 @@ int panel_rec(lu_context* c, cudaStream_t st, T* A, int64_t lda, int64_t M, int6
         if (lu_pf_cluster_shape<T>(rows, (int)w1, c->pf_smem_budget, &Ca, &Ra, &sa) &&
             lu_pf_cluster_shape<T>(rows - w1, (int)w2, c->pf_smem_budget, &Cb, &Rb, &sb)) {
             const int64_t jb = j0 + w1;
-            if (!gated) LU_TRY(consume_gate(c, st));
-            // gated: each leaf's interchanges stay within this node's columns
-            const int64_t ra = gated ? w2 : pc0 + pw - (j0 + w1);
-            const int64_t rb = gated ? 0 : pc0 + pw - (jb + w2);
-            LU_TRY(on_leaf_sms(c, st, [&](cudaStream_t ls) {
+            return on_leaf_sms(c, st, [&](cudaStream_t ls) {
                 LU_TRY(lu_launch_pf_leaf_cluster<T>(ls, A + j0 + j0 * lda, lda, rows, (int)w1, Ca, Ra, sa, j0 - pc0,
-                                                    ra, ipiv + j0, j0, &c->sync[0], (int)w2, 0));
+                                                    pc0 + pw - (j0 + w1), ipiv + j0, j0, &c->sync[0], (int)w2, 0));
                 return lu_launch_pf_leaf_cluster<T>(ls, A + jb + jb * lda, lda, rows - w1, (int)w2, Cb, Rb, sb,
-                                                    jb - pc0, rb, ipiv + jb, jb, &c->sync[0], 0, (int)w1);
-            }));
-            return gated ? gated_rest<T>(c, st, A, lda, j0, width, ipiv, pc0, pw) : LU_SUCCESS;
+                                                    jb - pc0, pc0 + pw - (jb + w2), ipiv + jb, jb, &c->sync[0], 0,
+                                                    (int)w1);
+            });
         }
     }
     LU_TRY(panel_rec<T>(c, st, A, lda, M, j0, w1, ipiv, o, leaf, cluster, pc0, pw));
@@ -377,17 +345,6 @@ int lu_panel_recursive(lu_context* c, cudaStream_t st, T* A, int64_t lda, int64_
         leaf >>= 1;
     }
     return panel_rec<T>(c, st, A, lda, M, j0, width, ipiv, o, leaf, false, j0, width);
-}
-
-int64_t lu_panel_first_node(int64_t width) {
-    int64_t w = width;
-    while (w > 32) {
-        int64_t w1 = ((w / 2 + 7) / 8) * 8;
-        if (w1 >= w) w1 = w / 2;
-        if (w1 < 1) w1 = 1;
-        w = w1;
-    }
-    return w;
 }
 
 template int lu_launch_pf_leaf<double>(lu_context*, cudaStream_t, double*, int64_t, int64_t, int,
