@@ -955,6 +955,15 @@ def run_batched(args):
            f"{count} systems, n log-uniform [16,512] (sum n^3 = {float(np.sum(sizes.astype(np.float64)**3)):.3e}), "
            f"nrhs 1..8, iid U[-1,1), seed 0", "flops": flops}
     for name, dt in (("f64", torch.float64), ("f32", torch.float32)):
+        # the batched update's tile cut-over, measured on this batch (lu_tune_batched) and
+        # kept in the table, so the timed launches below use it
+        cuts = [1, 33, 65, 97, 129, 193]
+        best_cut, cut_ms = lu.lu_tune_batched(lu.LU_F64 if dt == torch.float64 else lu.LU_F32, sizes, nrhs, cuts,
+                                              reps=3)
+        out[f"tile_cutover_{name}"] = {"best": best_cut,
+                                       "ms": {str(c): round(t, 3) for c, t in zip(cuts, cut_ms)},
+                                       "note": "32 x 32 update tiles below the cut-over, 64 x 64 above; "
+                                               "1 = always 64 x 64"}
         dA = []
         for m in mats:
             t = colmajor(m.shape[0], m.shape[1], dtype=dt)

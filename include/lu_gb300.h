@@ -438,6 +438,16 @@ int lu_potrf_ex(lu_handle h, lu_dtype dtype, int64_t n, void *A, int64_t lda, co
  */
 #define LU_TUNE_F64 100 /* FP64 factorization: lu_factor, lu_factor_ex(LU_F64), lu_gesv_mixed(LU_FULL_F64) */
 #define LU_TUNE_F32 101 /* FP32 factorization on the CUDA cores: lu_factor_ex(LU_F32) */
+/* The batched kernel (lu_gesv_batched and friends), FP64 / FP32: the table's value
+ * for these kinds is the tile cut-over of the batched trailing update -- a panel
+ * step whose trailing order is below it uses 32 x 32 output tiles, otherwise
+ * 64 x 64 (1 = always 64 x 64) -- looked up with n = 512. */
+#define LU_TUNE_BATCHED_F64 102
+#define LU_TUNE_BATCHED_F32 103
+/* Cut-overs used when none was tuned (measured on a GB300 with the 4096-system
+ * batch of orders log-uniform in [16, 512]). */
+#define LU_BATCHED_CUT_F64 1
+#define LU_BATCHED_CUT_F32 1
 
 /*
  * lu_tune_nb -- time the factorization of `kind` on a seeded synthetic n x n
@@ -462,6 +472,22 @@ int lu_potrf_ex(lu_handle h, lu_dtype dtype, int64_t n, void *A, int64_t lda, co
  */
 int lu_tune_nb(lu_handle h, int kind, int64_t n, const int *candidates, int count, int reps, const lu_opts *opts,
                int *best_nb, float *ms);
+
+/*
+ * lu_tune_batched -- time the batched factorization + solve (lu_gesv_batched)
+ * of `dtype` on a synthetic batch with the caller's sizes (host arrays n[batch],
+ * orders 0..512, and nrhs[batch], 0..8; entries iid U[-1,1) from a fixed seed)
+ * for each candidate tile cut-over cuts[count] (1..513, see
+ * LU_TUNE_BATCHED_F64), and store the fastest in the table (n = 512).
+ *   reps   >= 1 runs per candidate, the least time counts
+ *   best   host int (out): the chosen cut-over
+ *   ms     host float[count] or NULL (out): each candidate's least time
+ * Every candidate computes the same factors (the tile shape changes no
+ * operation).  Scratch matrices are allocated and freed inside.  Returns 0,
+ * -i for an invalid argument, LU_ERR_NOMEM or a runtime error.
+ */
+int lu_tune_batched(lu_handle h, lu_dtype dtype, int batch, const int32_t *n, const int32_t *nrhs, int reps,
+                    const int *cuts, int count, int *best, float *ms);
 
 /* The table's nb for (device, kind, ceil(log2 n)), or 0 when there is none.
  * device: host string, or NULL for the current CUDA device's name. */

@@ -13,14 +13,14 @@ import ctypes
 import os
 
 from ._lib import (LU_ERR_CUDA, LU_ERR_HANDLE, LU_ERR_IO, LU_ERR_NOMEM, LU_ERR_TIMEOUT, LU_ERR_UNSUPPORTED,
-                   LU_TUNE_F32, LU_TUNE_F64,
+                   LU_TUNE_F32, LU_TUNE_F64, LU_TUNE_BATCHED_F32, LU_TUNE_BATCHED_F64,
                    LU_F32, LU_F64, LU_SUCCESS, LU_TU_BF16, LU_TU_FP16, LU_TU_FP8, LU_TU_F32, LU_TU_BF16X3, LU_TU_BF16X6, LU_FULL_F64,
                    LU_WARN_NOT_CONVERGED, LuError, LuOpts, lib, library_path)
 from .api import (Batch, Handle, lu_factor_batched, lu_gesv_batched, lu_solve_batched, default_opts, lu_factor, lu_factor_ex, lu_factor_mixed_ex, lu_gemm_update_ex, lu_gemm_update_tc_ex, lu_gesv_mixed, lu_laswp_ex,
                   lu_launch_count, lu_panel_factor_ex, lu_panel_factor_noalloc, lu_solve, lu_solve_ex, lu_trsm_ex,
                   lu_tune_clear, lu_tune_get, lu_tune_load, lu_tune_nb, lu_tune_save, lu_tune_set, lu_potrf_ex,
                   lu_tune_plan, lu_tune_plan_get, lu_step_trace, lu_step_trace_read, lu_geqrf_ex,
-                  lu_potrf_mixed_ex, lu_geqrf_mixed_ex)
+                  lu_potrf_mixed_ex, lu_geqrf_mixed_ex, lu_tune_batched)
 
 __all__ = [
     "Batch", "Handle", "lu_factor_batched", "lu_gesv_batched", "lu_solve_batched", "LuError", "LuOpts", "default_opts", "lib", "library_path", "lu_factor", "lu_factor_ex",
@@ -30,5 +30,6 @@ __all__ = [
     "LU_TU_FP16", "LU_TU_FP8", "LU_TU_F32", "LU_TU_BF16X3", "LU_TU_BF16X6", "LU_FULL_F64",
     "LU_ERR_IO", "LU_TUNE_F64", "LU_TUNE_F32", "lu_tune_nb", "lu_tune_get", "lu_tune_set", "lu_tune_clear",
     "lu_tune_save", "lu_tune_load", "lu_potrf_ex", "lu_tune_plan", "lu_tune_plan_get", "lu_step_trace",
-    "lu_step_trace_read", "lu_geqrf_ex", "lu_potrf_mixed_ex", "lu_geqrf_mixed_ex",
+    "lu_step_trace_read", "lu_geqrf_ex", "lu_potrf_mixed_ex", "lu_geqrf_mixed_ex", "lu_tune_batched",
+    "LU_TUNE_BATCHED_F64", "LU_TUNE_BATCHED_F32",
 ]

@@ -32,6 +32,8 @@ LU_TU_BF16X6 = 6
 
 LU_TUNE_F64 = 100
 LU_TUNE_F32 = 101
+LU_TUNE_BATCHED_F64 = 102
+LU_TUNE_BATCHED_F32 = 103
 
 
 class LuError(RuntimeError):
@@ -118,6 +120,8 @@ _SIGNATURES = {
     "lu_geqrf_ex": (i32, [vp, i32, i64, i64, vp, i64, vp, ctypes.POINTER(LuOpts), vp]),
     "lu_potrf_mixed_ex": (i32, [vp, i32, i64, vp, i64, ctypes.POINTER(LuOpts), vp]),
     "lu_geqrf_mixed_ex": (i32, [vp, i32, i64, i64, vp, i64, vp, ctypes.POINTER(LuOpts), vp]),
+    "lu_tune_batched": (i32, [vp, i32, i32, ctypes.POINTER(i32), ctypes.POINTER(i32), i32, ctypes.POINTER(i32), i32,
+                              ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_float)]),
     "lu_step_trace": (i32, [vp, i32]),
     "lu_step_trace_read": (i64, [vp, i32, ctypes.POINTER(i64), ctypes.POINTER(ctypes.c_int32),
                                  ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float),

@@ -383,3 +383,19 @@ def lu_geqrf_mixed_ex(A: torch.Tensor, tau: torch.Tensor, info: torch.Tensor, pr
     m, n = A.shape
     _check("lu_geqrf_mixed_ex", lib().lu_geqrf_mixed_ex(h.ptr, int(prec), m, n, _p(A), _ld(A, "A"), _p(tau),
                                                         ctypes.byref(o), _p(info)))
+
+
+def lu_tune_batched(dtype: int, sizes, nrhs, cuts, reps: int = 3, handle: Handle | None = None):
+    """Times lu_gesv_batched of `dtype` (LU_F64/LU_F32) on a synthetic batch with these
+    orders and right-hand-side counts for each tile cut-over; returns (best, ms list)
+    and stores the best in the table (kinds LU_TUNE_BATCHED_F64/F32)."""
+    h = _handle(handle)
+    b = len(sizes)
+    nn = (ctypes.c_int * b)(*[int(v) for v in sizes])
+    rr = (ctypes.c_int * b)(*[int(v) for v in nrhs])
+    cc = (ctypes.c_int * len(cuts))(*[int(v) for v in cuts])
+    ms = (ctypes.c_float * len(cuts))()
+    best = ctypes.c_int(0)
+    _check("lu_tune_batched", lib().lu_tune_batched(h.ptr, int(dtype), b, nn, rr, int(reps), cc, len(cuts),
+                                                    ctypes.byref(best), ms))
+    return best.value, [float(t) for t in ms]

@@ -138,9 +138,89 @@ __device__ int block_argmax(T v, int i, T* red_v, int* red_i) {
 }
 
 // Factor one n x n matrix (column-major, lda) in place; ipiv 1-based; returns info.
+// RL3 of one panel step, A22 -= L21 U12, in TM x TN output tiles: a thread owns
+// rows i0 + tx + 16a (a < TM/16) and the TN/16 adjacent columns j0 + (TN/16) ty + b,
+// so its U12 values are adjacent in shared memory; every entry accumulates its
+// kBNB products in k order and is then subtracted once, whatever the tile shape.
+// L21 rows past mr hold stale shared data (inside the allocation) whose products
+// are never stored.
+template <typename T, int TM, int TN>
+__device__ __forceinline__ void rl3_tiles(T* __restrict__ A, int64_t lda, int k0, int kb, int mr, int nr,
+                                          const T* __restrict__ sP, T* __restrict__ sU) {
+    constexpr int MA = TM / 16, NB = TN / 16;
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    for (int j0 = 0; j0 < nr; j0 += TN) {
+        // U12 columns j0 .. j0+TN-1 into shared memory
+        {
+            constexpr int kPer = kBNB * TN / kBT;
+            T v[kPer];
+#pragma unroll
+            for (int t = 0; t < kPer; ++t) {
+                const int e = tid + t * kBT, kk = e & (kBNB - 1), jj = e / kBNB;
+                v[t] = (j0 + jj < nr) ? A[(int64_t)(k0 + kk) + (int64_t)(k0 + kb + j0 + jj) * lda] : T(0);
+            }
+#pragma unroll
+            for (int t = 0; t < kPer; ++t) {
+                const int e = tid + t * kBT, kk = e & (kBNB - 1), jj = e / kBNB;
+                sU[kk * kUS + jj] = v[t];
+            }
+        }
+        __syncthreads();
+        for (int i0 = 0; i0 < mr; i0 += TM) {
+            // the output tile is read before the product so that its load latency
+            // overlaps the kk loop
+            T acc[MA][NB], cv[MA][NB];
+#pragma unroll
+            for (int b = 0; b < NB; ++b) {
+                const int jc = j0 + NB * ty + b;
+                const T* col = A + (int64_t)(k0 + kb + min(jc, nr - 1)) * lda + (k0 + kb);
+#pragma unroll
+                for (int a = 0; a < MA; ++a) {
+                    const int r = i0 + tx + 16 * a;
+                    cv[a][b] = (jc < nr && r < mr) ? col[r] : T(0);
+                    acc[a][b] = T(0);
+                }
+            }
+            const T* lp = sP + kb + i0 + tx;
+            const T* up = sU + NB * ty;
+#pragma unroll 8
+            for (int kk = 0; kk < kBNB; ++kk) {
+                T lv[MA], uv[NB];
+#pragma unroll
+                for (int a = 0; a < MA; ++a) lv[a] = lp[kk * kNMAX + 16 * a];
+                if constexpr (NB == 4) {
+                    T q[4];
+                    load4(up + kk * kUS, q);
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) uv[b] = q[b];
+                } else {
+#pragma unroll
+                    for (int b = 0; b < NB; ++b) uv[b] = up[kk * kUS + b];
+                }
+#pragma unroll
+                for (int a = 0; a < MA; ++a)
+#pragma unroll
+                    for (int b = 0; b < NB; ++b) acc[a][b] = fma(lv[a], uv[b], acc[a][b]);
+            }
+#pragma unroll
+            for (int b = 0; b < NB; ++b) {
+                const int jc = j0 + NB * ty + b;
+                if (jc >= nr) continue;
+                T* col = A + (int64_t)(k0 + kb + jc) * lda + (k0 + kb);
+#pragma unroll
+                for (int a = 0; a < MA; ++a) {
+                    const int r = i0 + tx + 16 * a;
+                    if (r < mr) col[r] = cv[a][b] - acc[a][b];
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
 template <typename T>
 __device__ int factor_one(int n, T* __restrict__ A, int64_t lda, int32_t* __restrict__ ipiv, T* sP, T* sU,
-                          T* red_v, int* red_i) {
+                          T* red_v, int* red_i, int small_cut) {
     // interchange plan of the current panel (relative rows)
     __shared__ int s_pdst[2 * kBNB], s_psrc[2 * kBNB], s_pcur[2 * kBNB], s_ptgt[kBNB], s_pb[kBNB], s_pcnt;
     const int tid = threadIdx.x;
@@ -302,72 +382,11 @@ __device__ int factor_one(int n, T* __restrict__ A, int64_t lda, int32_t* __rest
                 if (i < kb) a[i] = x[i];
         }
         __syncthreads();
-        // ---- RL3: A22 -= L21 U12 in 64x64 output tiles, 4x4 per thread ----
-        // Here kb == kBNB (a trailing block exists only after a full panel).  A thread
-        // owns rows i0 + tx + 16a and the four adjacent columns j0 + 4ty + b, so its
-        // U12 values are one vector load; L21 rows past mr hold stale shared data
-        // (inside the allocation) whose products are never stored.
-        const int mr = m - kb;  // rows below the panel
-        const int tx = tid & 15, ty = tid >> 4;
-        for (int j0 = 0; j0 < nr; j0 += 64) {
-            // U12 columns j0 .. j0+63 into shared memory
-            {
-                constexpr int kPer = kBNB * 64 / kBT;
-                T v[kPer];
-#pragma unroll
-                for (int t = 0; t < kPer; ++t) {
-                    const int e = tid + t * kBT, kk = e & (kBNB - 1), jj = e / kBNB;
-                    v[t] = (j0 + jj < nr) ? A[(int64_t)(k0 + kk) + (int64_t)(k0 + kb + j0 + jj) * lda] : T(0);
-                }
-#pragma unroll
-                for (int t = 0; t < kPer; ++t) {
-                    const int e = tid + t * kBT, kk = e & (kBNB - 1), jj = e / kBNB;
-                    sU[kk * kUS + jj] = v[t];
-                }
-            }
-            __syncthreads();
-            for (int i0 = 0; i0 < mr; i0 += 64) {
-                // the output tile is read before the product so that its load
-                // latency overlaps the kk loop
-                T acc[4][4], cv[4][4];
-#pragma unroll
-                for (int b = 0; b < 4; ++b) {
-                    const int jc = j0 + 4 * ty + b;
-                    const T* col = A + (int64_t)(k0 + kb + min(jc, nr - 1)) * lda + (k0 + kb);
-#pragma unroll
-                    for (int a = 0; a < 4; ++a) {
-                        const int r = i0 + tx + 16 * a;
-                        cv[a][b] = (jc < nr && r < mr) ? col[r] : T(0);
-                        acc[a][b] = T(0);
-                    }
-                }
-                const T* lp = sP + kb + i0 + tx;
-                const T* up = sU + 4 * ty;
-#pragma unroll 8
-                for (int kk = 0; kk < kBNB; ++kk) {
-                    T lv[4], uv[4];
-#pragma unroll
-                    for (int a = 0; a < 4; ++a) lv[a] = lp[kk * kNMAX + 16 * a];
-                    load4(up + kk * kUS, uv);
-#pragma unroll
-                    for (int a = 0; a < 4; ++a)
-#pragma unroll
-                        for (int b = 0; b < 4; ++b) acc[a][b] = fma(lv[a], uv[b], acc[a][b]);
-                }
-#pragma unroll
-                for (int b = 0; b < 4; ++b) {
-                    const int jc = j0 + 4 * ty + b;
-                    if (jc >= nr) continue;
-                    T* col = A + (int64_t)(k0 + kb + jc) * lda + (k0 + kb);
-#pragma unroll
-                    for (int a = 0; a < 4; ++a) {
-                        const int r = i0 + tx + 16 * a;
-                        if (r < mr) col[r] = cv[a][b] - acc[a][b];
-                    }
-                }
-            }
-            __syncthreads();
-        }
+        // ---- RL3: A22 -= L21 U12 (kb == kBNB here: a trailing block exists only after
+        // a full panel); small trailing blocks take 32 x 32 tiles, which waste fewer
+        // padded products, larger ones 64 x 64 (same per-element order either way)
+        if (nr < small_cut) rl3_tiles<T, 32, 32>(A, lda, k0, kb, m - kb, nr, sP, sU);
+        else rl3_tiles<T, 64, 64>(A, lda, k0, kb, m - kb, nr, sP, sU);
     }
     return finfo;
 }
@@ -465,7 +484,7 @@ __global__ void __launch_bounds__(kBT) batched_gesv_kernel(int batch, const int3
                                                            const int64_t* __restrict__ ldbv,
                                                            int32_t* __restrict__ info,
                                                            const int32_t* __restrict__ order, int* __restrict__ counter,
-                                                           int do_factor) {
+                                                           int do_factor, int small_cut) {
     extern __shared__ __align__(16) unsigned char smraw[];
     T* sP = reinterpret_cast<T*>(smraw);
     T* sU = sP + (size_t)kBNB * kNMAX;
@@ -490,7 +509,8 @@ __global__ void __launch_bounds__(kBT) batched_gesv_kernel(int batch, const int3
             continue;
         }
         int finfo = 0;
-        if (n > 0 && do_factor) finfo = factor_one<T>(n, Aptr[mid], lda, ipivp[mid], sP, sU, red_v, red_i);
+        if (n > 0 && do_factor)
+            finfo = factor_one<T>(n, Aptr[mid], lda, ipivp[mid], sP, sU, red_v, red_i, small_cut);
         if (threadIdx.x == 0) info[mid] = finfo;
         if (Bptr && n > 0 && finfo == 0) {
             const int nrhs = nrhsv[mid];
@@ -506,10 +526,18 @@ __global__ void __launch_bounds__(kBT) batched_gesv_kernel(int batch, const int3
 
 }  // namespace
 
+// Trailing orders below which a panel step's RL3 takes 32 x 32 tiles: the tuned
+// value for this device and precision (lu_tune_batched), else the default.
+static int batched_tile_cut(lu_dtype dtype) {
+    const int kind = dtype == LU_F64 ? LU_TUNE_BATCHED_F64 : LU_TUNE_BATCHED_F32;
+    const int v = lu_tuned_value(kind, kNMAX);
+    return v > 0 ? v : (dtype == LU_F64 ? LU_BATCHED_CUT_F64 : LU_BATCHED_CUT_F32);
+}
+
 template <typename T>
 static int gesv_batched_impl(lu_context* c, int batch, const int32_t* n, T* const* A, const int64_t* lda,
                              int32_t* const* ipiv, const int32_t* nrhs, T* const* B, const int64_t* ldb, int32_t* info,
-                             int do_factor) {
+                             int do_factor, int small_cut) {
     cudaStream_t st = c->user;
     const size_t need = sizeof(int32_t) * ((size_t)batch + 64);
     if (c->batch_ws_bytes < need) {
@@ -539,7 +567,7 @@ static int gesv_batched_impl(lu_context* c, int batch, const int32_t* n, T* cons
     const int grid = std::max(1, std::min(batch, c->num_sms * std::max(per_sm, 1)));
     LuProfScope prof(st, LU_K_BATCHED, 0.0, 0.0);
     batched_gesv_kernel<T><<<grid, kBT, BatchSmem<T>::bytes, st>>>(batch, n, A, lda, ipiv, nrhs, B, ldb, info, order,
-                                                                   counter, do_factor);
+                                                                   counter, do_factor, small_cut);
     LU_CHECK_LAUNCH();
     return LU_SUCCESS;
 }
@@ -555,13 +583,14 @@ static int batched_entry(lu_handle h, lu_dtype dtype, int batch, const int32_t* 
     if (!do_factor && batch > 0 && !B) return -9;
     if (batch > 0 && !info) return -11;
     if (batch == 0) return LU_SUCCESS;
+    const int cut = h->batched_cut_override > 0 ? h->batched_cut_override : batched_tile_cut(dtype);
     std::lock_guard<std::mutex> lk(h->mu);
     LU_TRY(lu_ctx_reserve(h, 1, 1));
     if (dtype == LU_F64)
         return gesv_batched_impl<double>(h, batch, n, (double* const*)A, lda, ipiv, nrhs, (double* const*)B, ldb, info,
-                                         do_factor);
+                                         do_factor, cut);
     return gesv_batched_impl<float>(h, batch, n, (float* const*)A, lda, ipiv, nrhs, (float* const*)B, ldb, info,
-                                    do_factor);
+                                    do_factor, cut);
 }
 
 extern "C" int lu_gesv_batched(lu_handle h, lu_dtype dtype, int batch, const int32_t* n, void* const* A,
@@ -579,4 +608,146 @@ extern "C" int lu_solve_batched(lu_handle h, lu_dtype dtype, int batch, const in
                                 const int64_t* lda, int32_t* const* ipiv, const int32_t* nrhs, void* const* B,
                                 const int64_t* ldb, int32_t* info) {
     return batched_entry(h, dtype, batch, n, LU, lda, ipiv, nrhs, B, ldb, info, 0);
+}
+
+namespace {
+
+// Seeded U[-1, 1) entries for the tuner's synthetic batch: splitmix64 (Steele,
+// Lea and Flood, 2014) of the element index, top 53 bits as a fraction.
+template <typename T>
+__global__ void batch_fill_kernel(T* __restrict__ X, int64_t count, uint64_t seed) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < count; e += (int64_t)gridDim.x * blockDim.x) {
+        uint64_t z = seed + (uint64_t)(e + 1) * 0x9E3779B97F4A7C15ull;
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        z ^= z >> 31;
+        X[e] = (T)(2.0 * ((double)(z >> 11) * (1.0 / 9007199254740992.0)) - 1.0);
+    }
+}
+
+template <typename T>
+int tune_batched_impl(lu_handle h, lu_dtype dtype, int batch, const int32_t* n, const int32_t* nrhs, int reps,
+                      const int* cuts, int count, int* best, float* ms) {
+    std::vector<int64_t> aoff(batch), boff(batch), poff(batch);
+    int64_t ta = 0, tb = 0, tp = 0;
+    for (int i = 0; i < batch; ++i) {
+        aoff[i] = ta;
+        boff[i] = tb;
+        poff[i] = tp;
+        ta += (int64_t)n[i] * n[i];
+        tb += (int64_t)n[i] * std::max(nrhs[i], 0);
+        tp += std::max(n[i], 1);
+    }
+    T *A = nullptr, *A0 = nullptr, *B = nullptr, *B0 = nullptr;
+    int32_t *piv = nullptr, *info = nullptr, *dn = nullptr, *dr = nullptr;
+    int64_t *dlda = nullptr, *dldb = nullptr;
+    void **dA = nullptr, **dB = nullptr, **dP = nullptr;
+    auto cleanup = [&]() {
+        void* ps[] = {A, A0, B, B0, piv, info, dn, dr, dlda, dldb, dA, dB, dP};
+        for (void* q : ps)
+            if (q) cudaFree(q);
+    };
+    const size_t ea = (size_t)std::max<int64_t>(ta, 1), eb = (size_t)std::max<int64_t>(tb, 1);
+    if (cudaMalloc(&A, sizeof(T) * ea) != cudaSuccess || cudaMalloc(&A0, sizeof(T) * ea) != cudaSuccess ||
+        cudaMalloc(&B, sizeof(T) * eb) != cudaSuccess || cudaMalloc(&B0, sizeof(T) * eb) != cudaSuccess ||
+        cudaMalloc(&piv, sizeof(int32_t) * (size_t)std::max<int64_t>(tp, 1)) != cudaSuccess ||
+        cudaMalloc(&info, sizeof(int32_t) * batch) != cudaSuccess || cudaMalloc(&dn, sizeof(int32_t) * batch) != cudaSuccess ||
+        cudaMalloc(&dr, sizeof(int32_t) * batch) != cudaSuccess || cudaMalloc(&dlda, sizeof(int64_t) * batch) != cudaSuccess ||
+        cudaMalloc(&dldb, sizeof(int64_t) * batch) != cudaSuccess || cudaMalloc(&dA, sizeof(void*) * batch) != cudaSuccess ||
+        cudaMalloc(&dB, sizeof(void*) * batch) != cudaSuccess || cudaMalloc(&dP, sizeof(void*) * batch) != cudaSuccess) {
+        cudaGetLastError();
+        cleanup();
+        return LU_ERR_NOMEM;
+    }
+    std::vector<void*> ha(batch), hb(batch), hp(batch);
+    std::vector<int64_t> hl(batch), hlb(batch);
+    for (int i = 0; i < batch; ++i) {
+        ha[i] = A + aoff[i];
+        hb[i] = B + boff[i];
+        hp[i] = piv + poff[i];
+        hl[i] = std::max(n[i], 1);
+        hlb[i] = std::max(n[i], 1);
+    }
+    cudaStream_t st;
+    {
+        std::lock_guard<std::mutex> lk(h->mu);
+        st = h->user;
+    }
+    int rc = LU_SUCCESS;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaMemcpy(dn, n, sizeof(int32_t) * batch, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(dr, nrhs, sizeof(int32_t) * batch, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(dlda, hl.data(), sizeof(int64_t) * batch, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(dldb, hlb.data(), sizeof(int64_t) * batch, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(dA, ha.data(), sizeof(void*) * batch, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(dB, hb.data(), sizeof(void*) * batch, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(dP, hp.data(), sizeof(void*) * batch, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+        rc = LU_ERR_CUDA;
+    if (rc == LU_SUCCESS) {
+        batch_fill_kernel<T><<<4 * h->num_sms, 256, 0, st>>>(A0, (int64_t)ea, 0x5eedull);
+        batch_fill_kernel<T><<<4 * h->num_sms, 256, 0, st>>>(B0, (int64_t)eb, 0xb0b0ull);
+        if (cudaGetLastError() != cudaSuccess) rc = LU_ERR_CUDA;
+    }
+    float best_ms = -1.f;
+    int best_cut = 0;
+    for (int ci = 0; ci < count && rc == LU_SUCCESS; ++ci) {
+        float t = -1.f;
+        h->batched_cut_override = cuts[ci];
+        for (int r = 0; r < reps && rc == LU_SUCCESS; ++r) {
+            float el = 0.f;
+            if (cudaMemcpyAsync(A, A0, sizeof(T) * ea, cudaMemcpyDeviceToDevice, st) != cudaSuccess ||
+                cudaMemcpyAsync(B, B0, sizeof(T) * eb, cudaMemcpyDeviceToDevice, st) != cudaSuccess ||
+                cudaEventRecord(e0, st) != cudaSuccess) {
+                rc = LU_ERR_CUDA;
+                break;
+            }
+            const int r2 = lu_gesv_batched(h, dtype, batch, dn, dA, dlda, (int32_t* const*)dP, dr, dB, dldb, info);
+            if (r2 != LU_SUCCESS) {
+                rc = r2;
+                break;
+            }
+            if (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                cudaEventElapsedTime(&el, e0, e1) != cudaSuccess) {
+                rc = LU_ERR_CUDA;
+                break;
+            }
+            if (t < 0.f || el < t) t = el;
+        }
+        if (ms) ms[ci] = t;
+        if (rc == LU_SUCCESS && t >= 0.f && (best_ms < 0.f || t < best_ms)) {
+            best_ms = t;
+            best_cut = cuts[ci];
+        }
+    }
+    h->batched_cut_override = 0;
+    if (rc == LU_ERR_CUDA) cudaGetLastError();
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cleanup();
+    if (rc != LU_SUCCESS) return rc;
+    *best = best_cut;
+    return lu_tune_set(nullptr, dtype == LU_F64 ? LU_TUNE_BATCHED_F64 : LU_TUNE_BATCHED_F32, kNMAX, best_cut, best_ms);
+}
+
+}  // namespace
+
+extern "C" int lu_tune_batched(lu_handle h, lu_dtype dtype, int batch, const int32_t* n, const int32_t* nrhs, int reps,
+                               const int* cuts, int count, int* best, float* ms) {
+    if (!h) return LU_ERR_HANDLE;
+    if (dtype != LU_F64 && dtype != LU_F32) return -2;
+    if (batch < 1) return -3;
+    if (!n) return -4;
+    if (!nrhs) return -5;
+    for (int i = 0; i < batch; ++i) {
+        if (n[i] < 0 || n[i] > kNMAX) return -4;
+        if (nrhs[i] < 0 || nrhs[i] > kMaxRhs) return -5;
+    }
+    if (reps < 1) return -6;
+    if (!cuts || count < 1) return -7;
+    for (int i = 0; i < count; ++i)
+        if (cuts[i] < 1 || cuts[i] > kNMAX + 1) return -7;
+    if (!best) return -9;
+    if (dtype == LU_F64) return tune_batched_impl<double>(h, dtype, batch, n, nrhs, reps, cuts, count, best, ms);
+    return tune_batched_impl<float>(h, dtype, batch, n, nrhs, reps, cuts, count, best, ms);
 }

@@ -17,6 +17,8 @@
 // nb for a factorization called with nb = 0: the tuned value for (kind, n) on
 // the current device, else 256 (tune.cu).
 int lu_auto_nb(int kind, int64_t n);
+// The table's value for (kind, n) on the current device, or 0 (tune file loaded first).
+int lu_tuned_value(int kind, int64_t n);
 // Options of a factorization called with nb = 0 (and no schedule): the plan the
 // tuner stored for (kind, n) on the current device -- nb or a per-step schedule,
 // the right update's SM reserve (when o->tu_reserve is 0) and the look-ahead
@@ -67,6 +69,8 @@ struct lu_context {
     // Symmetric (Cholesky) trailing update: > 0 = the panel width; the updates then
     // form U12 from L21 and touch only the lower block triangle (chol.cu).
     int sym_band = 0;
+    // Batched kernel: a tile cut-over forced by lu_tune_batched while it times candidates (0 = none)
+    int batched_cut_override = 0;
     // SM partition for the panel leaves (lu_opts.pf_sms); active during a factorization
     LuGreen* green = nullptr;
     bool green_active = false;

@@ -46,8 +46,8 @@ int bucket_of(int64_t n) {
 }
 
 bool kind_valid(int kind) {
-    return kind == LU_TUNE_F64 || kind == LU_TUNE_F32 || kind == LU_TU_F32 ||
-           (kind >= 0 && kind <= LU_TU_BF16X6 && kind != LU_FULL_F64);
+    return kind == LU_TUNE_F64 || kind == LU_TUNE_F32 || kind == LU_TU_F32 || kind == LU_TUNE_BATCHED_F64 ||
+           kind == LU_TUNE_BATCHED_F32 || (kind >= 0 && kind <= LU_TU_BF16X6 && kind != LU_FULL_F64);
 }
 
 // Name of the current device (cached per device index).
@@ -100,7 +100,10 @@ void put_locked(const std::string& dev, int kind, int bucket, int nb, float ms) 
     put_locked(e);
 }
 
-bool width_ok(int kind, int w) { return w >= 1 && w <= LU_MAX_NB && !(kind == LU_TU_FP8 && w % 128 != 0); }
+bool width_ok(int kind, int w) {
+    if (kind == LU_TUNE_BATCHED_F64 || kind == LU_TUNE_BATCHED_F32) return w >= 1 && w <= 513;  // a tile cut-over
+    return w >= 1 && w <= LU_MAX_NB && !(kind == LU_TU_FP8 && w % 128 != 0);
+}
 
 // A seeded n x n matrix with entries iid U[-1, 1): splitmix64 (Steele, Lea and
 // Flood, 2014) of the element index, top 53 bits as a fraction.
@@ -126,6 +129,11 @@ void load_env_table_once() {
 }
 
 }  // namespace
+
+int lu_tuned_value(int kind, int64_t n) {
+    load_env_table_once();
+    return lu_tune_get(nullptr, kind, n);
+}
 
 int lu_auto_nb(int kind, int64_t n) {
     load_env_table_once();
@@ -221,7 +229,7 @@ extern "C" int lu_tune_set(const char* device, int kind, int64_t n, int nb, floa
     if (!resolve_device(device, &dev)) return -1;
     if (!kind_valid(kind)) return -2;
     if (n < 1) return -3;
-    if (nb < 1 || nb > LU_MAX_NB || (kind == LU_TU_FP8 && nb % 128 != 0)) return -4;
+    if (!width_ok(kind, nb)) return -4;
     std::lock_guard<std::mutex> lk(g_mu);
     put_locked(dev, kind, bucket_of(n), nb, ms);
     return LU_SUCCESS;

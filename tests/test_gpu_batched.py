@@ -243,3 +243,40 @@ def test_batched_nan_first_candidate(lu, dtype):
         d = int(diff[0]) if diff.size else n
         a, b = np.where(nan, 0.0, LU)[:d], np.where(nan, 0.0, LU_o)[:d]
         assert np.abs(a - b).max(initial=0.0) <= tol * max(np.abs(b).max(initial=0.0), 1e-300), (i, n)
+
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_batched_tile_cutover_and_tuner(lu, dtype):
+    """The batched trailing update's tile shape (32 x 32 below the tuned cut-over,
+    64 x 64 above) changes no operation: factors, pivots and solutions are
+    bit-identical for every cut-over, and lu_tune_batched stores the fastest
+    candidate, which later calls use."""
+    count = 60
+    sizes, nrhs = synth.batched_sizes(count, seed=17)
+    sizes[:3] = [512, 33, 97]
+    mats = synth.batched_matrices(sizes, seed=17)
+    g = synth.rng(17, 9)
+    rhs = [g.uniform(-1, 1, size=(int(n), int(r))) for n, r in zip(sizes, nrhs)]
+    code = lu.LU_F64 if dtype == torch.float64 else lu.LU_F32
+    kind = lu.LU_TUNE_BATCHED_F64 if dtype == torch.float64 else lu.LU_TUNE_BATCHED_F32
+    outs = []
+    for cut in (1, 65, 513):
+        lu.lu_tune_set(kind, 512, cut)
+        dA = [colmajor_dev(m, dtype) for m in mats]
+        dB = [colmajor_dev(b, dtype) for b in rhs]
+        piv = [torch.zeros(int(n), dtype=torch.int32, device="cuda") for n in sizes]
+        batch = lu.Batch(dA, piv, dB)
+        lu.lu_gesv_batched(batch)
+        torch.cuda.synchronize()
+        assert np.all(batch.info.cpu().numpy() == 0)
+        outs.append(([a.cpu() for a in dA], [p.cpu() for p in piv], [b.cpu() for b in dB]))
+    for o in outs[1:]:
+        for i in range(count):
+            assert torch.equal(o[0][i], outs[0][0][i]) and torch.equal(o[1][i], outs[0][1][i])
+            assert torch.equal(o[2][i], outs[0][2][i])
+    lu.lu_tune_clear()
+    best, ms = lu.lu_tune_batched(code, sizes, nrhs, [1, 65, 129], reps=2)
+    assert best in (1, 65, 129) and min(t for t in ms if t > 0) == ms[[1, 65, 129].index(best)]
+    assert lu.lu_tune_get(kind, 512) == best
+    lu.lu_tune_clear()
