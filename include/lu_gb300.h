@@ -446,8 +446,8 @@ int lu_potrf_ex(lu_handle h, lu_dtype dtype, int64_t n, void *A, int64_t lda, co
 #define LU_TUNE_BATCHED_F32 103
 /* Cut-overs used when none was tuned (measured on a GB300 with the 4096-system
  * batch of orders log-uniform in [16, 512]). */
-#define LU_BATCHED_CUT_F64 1
-#define LU_BATCHED_CUT_F32 1
+#define LU_BATCHED_CUT_F64 193
+#define LU_BATCHED_CUT_F32 97
 
 /*
  * lu_tune_nb -- time the factorization of `kind` on a seeded synthetic n x n
