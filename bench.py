@@ -613,7 +613,22 @@ def prof_peak(args, lu, torch, dt):
     print(json.dumps(line), flush=True)
 
 
+def prof_qr(args, lu, torch, dt):
+    """Householder QR (lu_geqrf_ex) of an n x n U[-1,1) matrix, nb columns per panel, look-ahead on"""
+    import synth
+    n, nb = _shape(args, (4096, 128))
+    A0 = torch.from_numpy(synth.uniform_matrix(n, seed=0)).to(dt)
+    A = lu.api.colmajor(n, n, dtype=dt)
+    tau = torch.zeros(n, dtype=dt, device="cuda")
+    info = torch.zeros(1, dtype=torch.int32, device="cuda")
+    o = lu.default_opts(nb=nb)
+    ms = _median_ms(lambda: lu.lu_geqrf_ex(A, tau, info, o), args.reps, before=lambda: A.copy_(A0))
+    _prof_line("qr", {"n": n, "nb": nb}, ms, float(A.element_size()) * 2 * n * n, 4.0 * n ** 3 / 3,
+               info=int(info.item()))
+
+
 PROFILE_CASES = {
+    "qr": (prof_qr, "Householder QR, --shape n,nb (4096,128)"),
     "leaf": (prof_leaf, "panel leaf, --shape m,w (16384,16)"),
     "tc": (prof_tc, "tensor-core update, --shape m,n,k,prec (8192,8192,256,6)"),
     "trsm": (prof_trsm, "RL2 solve, --shape m,n (256,16128)"),
