@@ -87,6 +87,7 @@ __global__ void __launch_bounds__(kQrThreads) qr_leaf_kernel(T* __restrict__ A, 
             }
         }
         ss = block_sum(ss, red);
+        __syncthreads();  // every thread has read red before it is reused below
         const int par = jj & 1;
         if (tid == 0) {
             s_ss[par * G + g] = ss;
@@ -97,9 +98,17 @@ __global__ void __launch_bounds__(kQrThreads) qr_leaf_kernel(T* __restrict__ A, 
             ok = false;
             break;
         }
-        // 2. the reflector, formed identically in every CTA from the fixed-order sum
-        T sum = T(0);
-        for (int q = 0; q < G; ++q) sum += __ldcg(&s_ss[par * G + q]);
+        // 2. the reflector, formed identically in every CTA from the same fixed-order sum
+        //    (lane l adds partials l, l+32, ..., then a butterfly over the lanes)
+        if (warp == 0) {
+            T p = T(0);
+            for (int q = lane; q < G; q += 32) p += __ldcg(&s_ss[par * G + q]);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) p += __shfl_xor_sync(0xffffffffu, p, o);
+            if (lane == 0) red[0] = p;
+        }
+        __syncthreads();
+        const T sum = red[0];
         const T alpha = __ldcg(&s_alpha[par]);
         if (sum == T(0)) {
             // nothing below the diagonal: H_j = I (tau = 0), the column stays as it is
@@ -140,10 +149,14 @@ __global__ void __launch_bounds__(kQrThreads) qr_leaf_kernel(T* __restrict__ A, 
             ok = false;
             break;
         }
-        for (int c = jj + 1 + tid; c < w; c += kQrThreads) {
-            T s = T(0);
-            for (int q = 0; q < G; ++q) s += __ldcg(&s_w[q * kQrMaxLeaf + c]);
-            sh_w[c] = t * s;
+        // the G partial dot products of each column, summed by one warp per column in
+        // the same fixed order as above
+        for (int c = jj + 1 + warp; c < w; c += kQrThreads / 32) {
+            T p = T(0);
+            for (int q = lane; q < G; q += 32) p += __ldcg(&s_w[q * kQrMaxLeaf + c]);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) p += __shfl_xor_sync(0xffffffffu, p, o);
+            if (lane == 0) sh_w[c] = t * p;
         }
         __syncthreads();
         // 4. rank-1 update A(jj:, c) -= v (tau w_c)
@@ -170,7 +183,7 @@ __global__ void __launch_bounds__(kQrThreads) qr_leaf_kernel(T* __restrict__ A, 
 // CTA runs all slices (split = 0) or each slice has its own CTA (split = 1,
 // blockIdx.z = slice, partials to P[s] (M x N, ld = M) for qr_splitk_reduce).
 // So the result does not depend on how a product is cut into launches.
-constexpr int kTnBM = 64, kTnBN = 64, kTnBK = 16, kTnSlice = 256;
+constexpr int kTnBM = 64, kTnBN = 64, kTnBK = 16, kTnSlice = 128;
 
 template <typename T>
 __global__ void __launch_bounds__(256) gemm_tn_kernel(int M, int N, int64_t K, int split, const T* __restrict__ A,
@@ -288,7 +301,7 @@ __global__ void __launch_bounds__(256) qr_larft_kernel(int w, const T* __restric
 
 namespace {
 
-constexpr int64_t kQrPartCap = 2 << 20;  // elements of one split-K partial buffer
+constexpr int64_t kQrPartCap = 8 << 20;  // elements of one split-K partial buffer
 
 // Workspace of one QR factorization, carved from the handle's device buffer.
 template <typename T>
@@ -432,7 +445,11 @@ template <typename T>
 int qr_leaf(lu_context* c, cudaStream_t st, T* A, int64_t lda, int64_t m, int64_t j0, int w, T* tau) {
     const int64_t rows = m - j0;
     if (rows <= 0 || w <= 0) return LU_SUCCESS;
-    const int64_t G0 = std::min<int64_t>({(int64_t)c->num_sms, (int64_t)LU_PF_MAX_CTAS, lu_cdiv(rows, 32)});
+    // as many rows per CTA as shared memory holds: fewer CTAs make the two grid
+    // barriers and the cross-CTA sums of every column cheaper, and the per-column
+    // work of a CTA stays small (R x w multiply-adds over 256 threads)
+    const int64_t Rmax = std::max<int64_t>(32, (int64_t)(200 * 1024 / (sizeof(T) * (size_t)w)) / 32 * 32);
+    const int64_t G0 = std::min<int64_t>({(int64_t)c->num_sms, (int64_t)LU_PF_MAX_CTAS, lu_cdiv(rows, Rmax)});
     const int64_t R = lu_cdiv(lu_cdiv(rows, G0), 32) * 32;
     const int64_t G = lu_cdiv(rows, R);
     const size_t smem = sizeof(T) * (size_t)R * w;
