@@ -58,10 +58,15 @@ def row_scaled(A: np.ndarray, seed: int = 0, stream: int = 3, lo: float = -3.0,
 
 def diag_scaled_normal(n: int, seed: int = 0, stream: int = 0, lo: float = -2.0,
                        hi: float = 2.0) -> np.ndarray:
-    """diag(d) G with G iid N(0,1) and d_i = 10**u_i, u_i ~ U[lo, hi)."""
+    """diag(d) G with G iid N(0,1) and d_i = 10**u_i, u_i ~ U[lo, hi).
+
+    d is rounded to single precision: pow is not correctly rounded, so its last
+    bit differs between math libraries (x86 SIMD, aarch64 libm); after the
+    rounding every platform builds the same matrix bit for bit."""
     G = normal_matrix(n, seed=seed, stream=stream)
     u = rng(seed, stream + 4).uniform(lo, hi, size=n)
-    return np.asfortranarray(G * (10.0 ** u)[:, None])
+    d = (10.0 ** u).astype(np.float32).astype(np.float64)
+    return np.asfortranarray(G * d[:, None])
 
 
 def ones_rhs(A: np.ndarray, nrhs: int = 1) -> np.ndarray:
