@@ -463,17 +463,19 @@ def _prof_line(case, sizes, ms, nbytes, flops, **extra):
 
 
 def prof_leaf(args, lu, torch, dt):
-    """panel factorization of an m x w N(0,1) panel (w <= 32: one cluster-leaf launch)"""
+    """panel factorization of an m x w N(0,1) panel with leaves of `leaf` columns
+    (default w; w <= 32 and leaf = w: one cluster-leaf launch) on clusters of at
+    most pf_ctas CTAs (0: the widest that fits)"""
     import synth
-    m, w = _shape(args, (16384, 16))
+    m, w, leaf, ctas = _shape(args, (16384, 16, 0, 0))
     P0 = torch.from_numpy(synth.normal_matrix(m, w, seed=3)).to(dt)
     P = lu.api.colmajor(m, w, dtype=dt)
     ipiv = torch.zeros(w, dtype=torch.int32, device="cuda")
     info = torch.zeros(1, dtype=torch.int32, device="cuda")
-    ms = _median_ms(lambda: lu.lu_panel_factor_ex(P, ipiv, info, lu.default_opts(leaf=w)), args.reps,
-                    before=lambda: P.copy_(P0))
+    o = lu.default_opts(leaf=leaf or w, pf_ctas=ctas)
+    ms = _median_ms(lambda: lu.lu_panel_factor_ex(P, ipiv, info, o), args.reps, before=lambda: P.copy_(P0))
     es = P.element_size()
-    _prof_line("leaf", {"m": m, "w": w}, ms, 2.0 * m * w * es, float(m) * w * w,
+    _prof_line("leaf", {"m": m, "w": w, "leaf": leaf or w, "pf_ctas": ctas}, ms, 2.0 * m * w * es, float(m) * w * w,
                us_per_column=ms * 1e3 / w, info=int(info.item()))
 
 
@@ -629,7 +631,7 @@ def prof_qr(args, lu, torch, dt):
 
 PROFILE_CASES = {
     "qr": (prof_qr, "Householder QR, --shape n,nb (4096,128)"),
-    "leaf": (prof_leaf, "panel leaf, --shape m,w (16384,16)"),
+    "leaf": (prof_leaf, "panel leaf, --shape m,w,leaf,pf_ctas (16384,16,w,0)"),
     "tc": (prof_tc, "tensor-core update, --shape m,n,k,prec (8192,8192,256,6)"),
     "trsm": (prof_trsm, "RL2 solve, --shape m,n (256,16128)"),
     "laswp": (prof_laswp, "row interchanges, --shape n,ncols,K (16384,16128,256)"),

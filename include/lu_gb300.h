@@ -88,7 +88,9 @@ typedef struct {
                       analogue of the malleable BLAS of Sec. 4.2); 0: they do not */
     int leaf;      /* column width handled by one panel-factorization leaf
                       kernel inside the recursive panel (0 = automatic) */
-    int pf_ctas;   /* maximum CTAs of a panel-factorization leaf (0 = automatic) */
+    int pf_ctas;   /* maximum CTAs of a panel-factorization leaf, also capping the
+                      thread-block cluster of a cluster leaf (0 = automatic: the
+                      largest cluster that fits) */
     int tu_reserve; /* with look-ahead: SMs the right trailing update leaves to the
                       panel path (and that rejoin it as stealing CTAs once the
                       panel is done); 0 = automatic (the tuned value, else a

@@ -121,7 +121,7 @@ int lu_green_setup(lu_context* c, int part_sms) {
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3(LU_PF_MAX_CTAS_CLUSTER, 1, 1);
         cfg.blockDim = dim3(256, 1, 1);
-        cfg.dynamicSmemBytes = 160 * 1024;
+        cfg.dynamicSmemBytes = LU_PF_SMEM_PART;
         cudaLaunchAttribute at[1];
         at[0].id = cudaLaunchAttributeClusterDimension;
         at[0].val.clusterDim.x = LU_PF_MAX_CTAS_CLUSTER;
@@ -132,7 +132,7 @@ int lu_green_setup(lu_context* c, int part_sms) {
         ok = cudaFuncSetAttribute(green_cluster_fit_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
                  cudaSuccess &&
              cudaFuncSetAttribute(green_cluster_fit_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  160 * 1024) == cudaSuccess &&
+                                  LU_PF_SMEM_PART) == cudaSuccess &&
              cudaOccupancyMaxActiveClusters(&fits, green_cluster_fit_kernel, &cfg) == cudaSuccess && fits >= 1;
         CUcontext dummy = nullptr;
         a.pop(&dummy);

@@ -26,6 +26,7 @@ int lu_tuned_value(int kind, int64_t n);
 // thread-local storage that stays valid until this thread's next call.
 void lu_auto_opts(int kind, int64_t n, lu_opts* o);
 #define LU_PF_SMEM_BUDGET (78 * 1024)
+#define LU_PF_SMEM_PART (160 * 1024)  // leaf budget on an SM partition of its own (checked at set-up)
 #define LU_PF_MAX_CTAS_CLUSTER 16  // CTAs of a cluster panel leaf (non-portable cluster size)
 
 struct LuGreen;  // green-context SM partition of the panel leaves (green.cu)
@@ -175,7 +176,8 @@ int lu_launch_trinv_diag(cudaStream_t st, int64_t n, const T* LU, int64_t lda, T
 int lu_launch_finish_info(cudaStream_t st, const LuSync* s, int32_t* info);
 
 template <typename T>
-bool lu_pf_cluster_shape(int64_t m, int w, size_t budget, int* C_out, int* R_out, size_t* smem_out);
+bool lu_pf_cluster_shape(int64_t m, int w, size_t budget, int* C_out, int* R_out, size_t* smem_out,
+                         int max_c = 0);  // max_c > 0 caps the cluster size
 // sib > 0: the leaf also applies L11^-1 to the top rows of the first sib columns to its
 // right (its sibling's U12); kprev > 0: the leaf first applies the preceding sibling's
 // rank-kprev update to its own columns.  Both need the pushed-message leaf

@@ -376,8 +376,15 @@ int lu_factor_blocked(lu_context* c, int64_t n, T* A, int64_t lda, int32_t* ipiv
     c->green_active = o.pf_sms > 0 && o.lookahead >= 1 && lu_green_setup(c, o.pf_sms) == LU_SUCCESS;
     struct GreenOff {
         lu_context* c;
-        ~GreenOff() { c->green_active = false; }
-    } green_off{c};
+        size_t budget;
+        ~GreenOff() {
+            c->green_active = false;
+            c->pf_smem_budget = budget;
+        }
+    } green_off{c, c->pf_smem_budget};
+    // on their own SMs the leaves need not leave room for update CTAs: wider leaves
+    // (32 columns at up to 16384 rows) fit
+    if (c->green_active) c->pf_smem_budget = std::max<size_t>(c->pf_smem_budget, LU_PF_SMEM_PART);
     cudaStream_t lo = c->green_active ? lu_green_rest_stream(c) : c->lo;
     LU_CHECK_CUDA(cudaEventRecord(c->ev_fork, user));
     LU_CHECK_CUDA(cudaStreamWaitEvent(c->hi, c->ev_fork, 0));

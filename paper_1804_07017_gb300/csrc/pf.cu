@@ -257,7 +257,7 @@ int panel_rec(lu_context* c, cudaStream_t st, T* A, int64_t lda, int64_t M, int6
         if (cluster) {
             int C = 0, R = 0;
             size_t smem = 0;
-            if (lu_pf_cluster_shape<T>(rows, (int)width, c->pf_smem_budget, &C, &R, &smem))
+            if (lu_pf_cluster_shape<T>(rows, (int)width, c->pf_smem_budget, &C, &R, &smem, o.pf_ctas))
                 return on_leaf_sms(c, st, [&](cudaStream_t ls) {
                     return lu_launch_pf_leaf_cluster<T>(ls, A + j0 + j0 * lda, lda, rows, (int)width, C, R, smem,
                                                         j0 - pc0, pc0 + pw - (j0 + width), ipiv + j0, j0, &c->sync[0]);
@@ -275,8 +275,8 @@ int panel_rec(lu_context* c, cudaStream_t st, T* A, int64_t lda, int64_t M, int6
     if (cluster && w1 <= 16 && w2 <= 16 && w1 <= leaf && w2 <= leaf && lu_pf_leaf_pairs_supported()) {
         int Ca = 0, Ra = 0, Cb = 0, Rb = 0;
         size_t sa = 0, sb = 0;
-        if (lu_pf_cluster_shape<T>(rows, (int)w1, c->pf_smem_budget, &Ca, &Ra, &sa) &&
-            lu_pf_cluster_shape<T>(rows - w1, (int)w2, c->pf_smem_budget, &Cb, &Rb, &sb)) {
+        if (lu_pf_cluster_shape<T>(rows, (int)w1, c->pf_smem_budget, &Ca, &Ra, &sa, o.pf_ctas) &&
+            lu_pf_cluster_shape<T>(rows - w1, (int)w2, c->pf_smem_budget, &Cb, &Rb, &sb, o.pf_ctas)) {
             const int64_t jb = j0 + w1;
             return on_leaf_sms(c, st, [&](cudaStream_t ls) {
                 LU_TRY(lu_launch_pf_leaf_cluster<T>(ls, A + j0 + j0 * lda, lda, rows, (int)w1, Ca, Ra, sa, j0 - pc0,
@@ -327,13 +327,16 @@ int lu_panel_recursive(lu_context* c, cudaStream_t st, T* A, int64_t lda, int64_
     while (leaf > 8) {
         int C, R;
         size_t smem;
-        if (lu_pf_cluster_shape<T>(rows, std::min<int>(leaf, (int)width), c->pf_smem_budget, &C, &R, &smem)) break;
+        if (lu_pf_cluster_shape<T>(rows, std::min<int>(leaf, (int)width), c->pf_smem_budget, &C, &R, &smem,
+                                   o.pf_ctas))
+            break;
         leaf >>= 1;
     }
     {
         int C, R;
         size_t smem;
-        if (lu_pf_cluster_shape<T>(rows, std::min<int>(leaf, (int)width), c->pf_smem_budget, &C, &R, &smem))
+        if (lu_pf_cluster_shape<T>(rows, std::min<int>(leaf, (int)width), c->pf_smem_budget, &C, &R, &smem,
+                                   o.pf_ctas))
             return panel_rec<T>(c, st, A, lda, M, j0, width, ipiv, o, leaf, true, j0, width);
     }
     leaf = o.leaf > 0 ? std::min(o.leaf, LU_PF_MAX_LEAF) : 32;

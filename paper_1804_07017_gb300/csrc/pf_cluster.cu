@@ -374,11 +374,12 @@ static int cluster_limit() {
 static int compiled_width(int w) { return w <= 8 ? 8 : (w <= 16 ? 16 : (w <= 32 ? 32 : 0)); }
 
 template <typename T>
-bool lu_pf_cluster_shape(int64_t m, int w, size_t budget, int* C_out, int* R_out, size_t* smem_out) {
+bool lu_pf_cluster_shape(int64_t m, int w, size_t budget, int* C_out, int* R_out, size_t* smem_out, int max_c) {
     if (m < w) return false;
     w = compiled_width(w);
     if (w == 0) return false;
-    const int cmax = cluster_limit<T>();
+    int cmax = cluster_limit<T>();
+    if (max_c > 0) cmax = std::min(cmax, max_c);
     if (cmax <= 0) return false;
     const int rqs[4] = {1, 2, 4, 8};
     for (int rq : rqs) {
@@ -449,8 +450,8 @@ int lu_launch_pf_leaf_cluster(cudaStream_t st, T* A, int64_t lda, int64_t m, int
     return LU_SUCCESS;
 }
 
-template bool lu_pf_cluster_shape<double>(int64_t, int, size_t, int*, int*, size_t*);
-template bool lu_pf_cluster_shape<float>(int64_t, int, size_t, int*, int*, size_t*);
+template bool lu_pf_cluster_shape<double>(int64_t, int, size_t, int*, int*, size_t*, int);
+template bool lu_pf_cluster_shape<float>(int64_t, int, size_t, int*, int*, size_t*, int);
 template int lu_launch_pf_leaf_cluster<double>(cudaStream_t, double*, int64_t, int64_t, int, int, int, size_t, int64_t,
                                                int64_t, int32_t*, int64_t, LuSync*, int, int);
 template int lu_launch_pf_leaf_cluster<float>(cudaStream_t, float*, int64_t, int64_t, int, int, int, size_t, int64_t,

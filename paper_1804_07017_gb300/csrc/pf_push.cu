@@ -163,12 +163,6 @@ __device__ __forceinline__ void leaf_wait(uint32_t bar, uint32_t parity, LuSync*
     }
 }
 
-template <typename T>
-__device__ __forceinline__ void cp_async_elem(T* dst, const T* src) {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(smem_u32(dst)), "l"(src), "n"((int)sizeof(T))
-                 : "memory");
-}
-
 template <typename T, int W, int RQ>
 struct PushSmem {
     static constexpr int SB = sub_block<T, RQ>();

@@ -8,6 +8,7 @@
 // static look-ahead's TU^L / TU^R split, Sec. 4) gives bit-identical results.
 #include "internal.h"
 #include "profile.h"
+#include "ptx.cuh"
 
 namespace {
 
@@ -31,15 +32,23 @@ __global__ void __launch_bounds__(kTrsmThreads)
     const int nc = (int)min((int64_t)COLS, n - col0);
     __syncthreads();
     for (int c = 0; c < COLS; ++c)
-        for (int r = tid; r < mp; r += kTrsmThreads)
-            sB[c * mp + r] = (c < nc && r < m) ? B[r + (col0 + c) * ldb] : T(0);
+        for (int r = tid; r < mp; r += kTrsmThreads) {
+            if (c < nc && r < m)
+                cp_async_elem<T>(sB + c * mp + r, B + r + (col0 + c) * ldb);
+            else
+                sB[c * mp + r] = T(0);
+        }
     for (int J = 0; J < m; J += 32) {
         const int jb = min(32, m - J);
         __syncthreads();
         for (int e = tid; e < 32 * 32; e += kTrsmThreads) {
             const int i = e & 31, j = e >> 5;
-            sL[j * 33 + i] = (i < jb && j < jb) ? L[(int64_t)(J + i) + (int64_t)(J + j) * ldl] : T(0);
+            if (i < jb && j < jb)
+                cp_async_elem<T>(sL + j * 33 + i, L + (int64_t)(J + i) + (int64_t)(J + j) * ldl);
+            else
+                sL[j * 33 + i] = T(0);
         }
+        cp_async_wait_all();
         __syncthreads();
         for (int c = warp; c < COLS; c += kTrsmThreads / 32) {
             T v = sB[c * mp + J + lane];
@@ -90,13 +99,19 @@ __global__ void __launch_bounds__(kTrsmThreads)
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t col0 = (int64_t)blockIdx.x * COLS;
     const int nc = (int)min((int64_t)COLS, n - col0);
-    for (int e = tid; e < m * m; e += kTrsmThreads) {
-        const int i = e % m, j = e / m;
-        if (i > j) sLp[i * (i - 1) / 2 + j] = L[(int64_t)i + (int64_t)j * ldl];
-    }
+    // staging by asynchronous element copies, all in flight at once (a load-then-store
+    // loop would wait one global round trip per iteration); lanes run down a column
+    // of L, so the global reads are coalesced
+    for (int j = warp; j < m - 1; j += kTrsmThreads / 32)
+        for (int i = j + 1 + lane; i < m; i += 32) cp_async_elem<T>(sLp + i * (i - 1) / 2 + j, L + i + (int64_t)j * ldl);
     for (int c = 0; c < COLS; ++c)
-        for (int r = tid; r < mp; r += kTrsmThreads)
-            sB[c * mp + r] = (c < nc && r < m) ? B[r + (col0 + c) * ldb] : T(0);
+        for (int r = tid; r < mp; r += kTrsmThreads) {
+            if (c < nc && r < m)
+                cp_async_elem<T>(sB + c * mp + r, B + r + (col0 + c) * ldb);
+            else
+                sB[c * mp + r] = T(0);
+        }
+    cp_async_wait_all();
     __syncthreads();
     for (int J = 0; J < m; J += 32) {
         const int jb = min(32, m - J);

@@ -233,7 +233,8 @@ def test_laswp_bit_exact(lu, dtype):
 
 
 @pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
-@pytest.mark.parametrize("m,n", [(256, 1000), (64, 33), (100, 7), (512, 300), (1024, 17)])
+@pytest.mark.parametrize("m,n", [(256, 1000), (64, 33), (100, 7), (512, 300), (1024, 17), (256, 256), (128, 128),
+                                 (31, 5)])
 def test_trsm(lu, dtype, m, n):
     """RL2 on the L11 that elimination produces (unit lower, |l_ij| <= 1), with
     junk stored on and above the diagonal that must be ignored.  Criteria:

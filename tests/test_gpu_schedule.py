@@ -224,9 +224,9 @@ def test_rtm_rejected_on_tensor_core_path(lu):
 @pytest.mark.parametrize("pf_sms", [16, 24])
 def test_leaf_sm_partition_identical(lu, pf_sms):
     """An SM partition for the panel leaves (green contexts; the right update on
-    the other SMs) moves work between SMs only: the mixed and the FP64
-    factorizations are bit-identical to the unpartitioned ones, and the refined
-    solve meets eta <= 1e-14."""
+    the other SMs) moves work between SMs; at n = 2048 the leaves keep their
+    shapes, so the mixed and the FP64 factorizations are bit-identical to the
+    unpartitioned ones, and the refined solve meets eta <= 1e-14."""
     n = 2048
     A0 = synth.normal_matrix(n, seed=77)
     A32 = A0.astype(np.float32).astype(np.float64)
@@ -248,5 +248,56 @@ def test_leaf_sm_partition_identical(lu, pf_sms):
     b0 = synth.ones_rhs(A0)
     A, B, X = dev(A0, torch.float64), dev(b0, torch.float64), dev(np.zeros_like(b0), torch.float64)
     st, it, eta = lu.lu_gesv_mixed(A, B, X, lu.LU_TU_BF16X6, opts=lu.default_opts(nb=256, pf_sms=pf_sms))
+    torch.cuda.synchronize()
+    assert st == 0 and oracle.backward_error(A0, X.cpu().numpy(), b0) <= 1e-14
+
+
+def sampled_residual(A0, LU, piv, rows):
+    """max over the sampled rows i of ||(PA - LU)(i, :)||_1 / (n ||A||_inf), each
+    row of L U formed on the host from row i of L and the rows of U it touches."""
+    n = A0.shape[0]
+    order = np.arange(n)
+    for k in range(n):
+        p = piv[k] - 1
+        order[k], order[p] = order[p], order[k]
+    anorm = np.abs(A0).sum(axis=1).max()
+    worst = 0.0
+    for i in rows:
+        l = LU[i, : i + 1].copy()
+        l[i] = 1.0
+        acc = np.zeros(n)
+        for p0 in range(0, i + 1, 512):
+            p1 = min(i + 1, p0 + 512)
+            acc += l[p0:p1] @ np.triu(LU[p0:p1, :], k=p0)
+        worst = max(worst, np.abs(A0[order[i], :] - acc).sum() / (n * anorm))
+    return worst
+
+
+@pytest.mark.parametrize("name", ["random", "in_panel"])
+def test_leaf_partition_wide_leaves(lu, name):
+    """On an SM partition of their own the panel leaves may take more shared
+    memory, so a panel taller than 8192 rows is factored by 32-column leaves
+    instead of pairs of 16-column ones: another rounding order inside the panel,
+    the same partial pivoting.  n = 9216 (the first panels take the wide leaves):
+    a designed interchange sequence comes back exactly; on N(0,1) the FP32
+    factorization's residual on sampled rows stays within 4 u32 and the refined
+    solve reaches eta <= 1e-14."""
+    import pivot_patterns as pp
+    n = 9216
+    A0, piv_expect = pp.patterned_matrix(name, n, seed=23, panel=256)
+    A32 = A0.astype(np.float32).astype(np.float64)
+    LU, piv, info = factor(lu, A32, torch.float32, mixed=lu.LU_TU_BF16X6, nb=256, pf_sms=24)
+    assert info == 0 and np.array_equal(piv, piv_expect)
+    del LU
+    A0 = synth.normal_matrix(n, seed=24)
+    A32 = A0.astype(np.float32).astype(np.float64)
+    LU, piv, info = factor(lu, A32, torch.float32, mixed=lu.LU_TU_BF16X6, nb=256, pf_sms=24)
+    assert info == 0
+    rows = np.concatenate([[0, 1, n // 2, n - 1], synth.rng(25, 0).integers(0, n, size=12)])
+    assert sampled_residual(A32, LU, piv, rows) <= BOUND[torch.float32]
+    del LU
+    b0 = synth.ones_rhs(A0)
+    A, B, X = dev(A0, torch.float64), dev(b0, torch.float64), dev(np.zeros_like(b0), torch.float64)
+    st, it, eta = lu.lu_gesv_mixed(A, B, X, lu.LU_TU_BF16X6, opts=lu.default_opts(nb=256, pf_sms=24))
     torch.cuda.synchronize()
     assert st == 0 and oracle.backward_error(A0, X.cpu().numpy(), b0) <= 1e-14
