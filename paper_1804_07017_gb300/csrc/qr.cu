@@ -27,6 +27,7 @@
 #include "internal.h"
 #include "pack.h"
 #include "profile.h"
+#include "ptx.cuh"
 #include "tc.h"
 
 namespace {
@@ -34,33 +35,48 @@ namespace {
 constexpr int kQrThreads = 256;
 constexpr int kQrMaxLeaf = 64;
 
+// Warp-wide sum whose result is the same in every lane: each lane adds partials
+// lane, lane + 32, ... (in that order), then a butterfly over the lanes, whose
+// additions are commutative pairwise, so every lane ends with the same bits.
 template <typename T>
-__device__ __forceinline__ T block_sum(T v, T* red) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    __syncthreads();
-    if (lane == 0) red[warp] = v;
-    __syncthreads();
+__device__ __forceinline__ T warp_sum_slots(const T* __restrict__ p, int count, int stride, int lane) {
     T s = T(0);
-    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s += red[i];  // fixed order, same in every thread
+    for (int q = lane; q < count; q += 32) s += __ldcg(&p[(int64_t)q * stride]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    return s;
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_allsum(T s) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     return s;
 }
 
 // Leaf: Householder QR of the m x w block at A (w <= kQrMaxLeaf), rows split
 // across gridDim.x CTAs of R rows.  slots (global): [2][G] partial sums of
 // squares, [2] alpha, [G][kQrMaxLeaf] partial dot products.
+//
+// Work is split by columns between the warps of a CTA: in the step of column
+// jj, warp q owns the columns jj+1+q, jj+1+q+8, ... (its lanes run down the
+// CTA's rows), so a column's dot product and its rank-1 update stay in one warp
+// and need no CTA-wide reduction.  Warp 0 owns column jj+1; while updating it
+// it also forms that column's sum of squares for the next step.  Per column:
+// warp 0 publishes the CTA's sum of squares (and alpha), grid barrier, every
+// warp forms the reflector from the same fixed-order sum, the CTA scales the
+// column, every warp forms its columns' partial v^T A, grid barrier, every warp
+// sums its columns' partials in a fixed order and updates them.
 template <typename T>
 __global__ void __launch_bounds__(kQrThreads) qr_leaf_kernel(T* __restrict__ A, int64_t lda, int m, int w, int R,
                                                              T* __restrict__ tau, LuSync* __restrict__ sync,
                                                              T* __restrict__ slots) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* sA = reinterpret_cast<T*>(smem_raw);  // [w][R] this CTA's rows, column-major
-    __shared__ T red[kQrThreads / 32];
-    __shared__ T red2[kQrThreads / 32][kQrMaxLeaf];
-    __shared__ T sh_w[kQrMaxLeaf];
     __shared__ int sh_flag;
+    constexpr int NW = kQrThreads / 32;
     const int G = gridDim.x, g = blockIdx.x, tid = threadIdx.x;
+    const int lane = tid & 31, warp = tid >> 5;
     const int row0 = g * R;
     const int nrows = max(0, min(R, m - row0));
     // the sums of squares and alpha alternate between two buffers by column parity:
@@ -69,46 +85,45 @@ __global__ void __launch_bounds__(kQrThreads) qr_leaf_kernel(T* __restrict__ A, 
     T* s_ss = slots;                 // [2][G]
     T* s_alpha = slots + 2 * G;      // [2]
     T* s_w = slots + 2 * G + 2;      // [G][kQrMaxLeaf]
-    const int lane = tid & 31, warp = tid >> 5;
     for (int c = 0; c < w; ++c)
-        for (int r = tid; r < nrows; r += kQrThreads) sA[c * R + r] = A[(int64_t)(row0 + r) + (int64_t)c * lda];
+        for (int r = tid; r < nrows; r += kQrThreads)
+            cp_async_elem<T>(sA + c * R + r, A + (int64_t)(row0 + r) + (int64_t)c * lda);
+    cp_async_wait_all();
     __syncthreads();
     unsigned int target = 0;
     bool ok = true;
     const int kmax = min(m, w);
+    // warp 0's sum of squares of column jj below the diagonal (valid when have_ss)
+    T ss = T(0);
+    bool have_ss = false;
     for (int jj = 0; jj < kmax && ok; ++jj) {
-        // 1. partial sum of squares below the diagonal; the owner of row jj publishes alpha
-        T ss = T(0);
-        for (int r = tid; r < nrows; r += kQrThreads) {
-            const int gr = row0 + r;
-            if (gr > jj) {
-                const T x = sA[jj * R + r];
-                ss = fma(x, x, ss);
+        const int lj = jj - row0;                        // local row of jj (owned if 0 <= lj < nrows)
+        const bool own_j = lj >= 0 && lj < nrows;
+        const int rs = max(0, lj + 1);                   // first local row below jj
+        const int par = jj & 1;
+        if (warp == 0) {
+            __syncwarp();  // column jj's last update came from other lanes of this warp
+            if (!have_ss) {
+                T s = T(0);
+                for (int r = rs + lane; r < nrows; r += 32) {
+                    const T x = sA[jj * R + r];
+                    s = fma(x, x, s);
+                }
+                ss = warp_allsum(s);
+            }
+            if (lane == 0) {
+                s_ss[par * G + g] = ss;
+                if (own_j) s_alpha[par] = sA[jj * R + lj];
             }
         }
-        ss = block_sum(ss, red);
-        __syncthreads();  // every thread has read red before it is reused below
-        const int par = jj & 1;
-        if (tid == 0) {
-            s_ss[par * G + g] = ss;
-            if (jj >= row0 && jj < row0 + nrows) s_alpha[par] = sA[jj * R + (jj - row0)];
-        }
+        have_ss = false;
         target += G;
         if (!lu_grid_barrier(sync, target, &sh_flag)) {
             ok = false;
             break;
         }
-        // 2. the reflector, formed identically in every CTA from the same fixed-order sum
-        //    (lane l adds partials l, l+32, ..., then a butterfly over the lanes)
-        if (warp == 0) {
-            T p = T(0);
-            for (int q = lane; q < G; q += 32) p += __ldcg(&s_ss[par * G + q]);
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) p += __shfl_xor_sync(0xffffffffu, p, o);
-            if (lane == 0) red[0] = p;
-        }
-        __syncthreads();
-        const T sum = red[0];
+        // the reflector, formed identically in every warp of every CTA
+        const T sum = warp_sum_slots(s_ss + par * G, G, 1, lane);
         const T alpha = __ldcg(&s_alpha[par]);
         if (sum == T(0)) {
             // nothing below the diagonal: H_j = I (tau = 0), the column stays as it is
@@ -120,56 +135,42 @@ __global__ void __launch_bounds__(kQrThreads) qr_leaf_kernel(T* __restrict__ A, 
         const T t = (beta - alpha) / beta;
         const T scale = T(1) / (alpha - beta);
         if (g == 0 && tid == 0) tau[jj] = t;
-        for (int r = tid; r < nrows; r += kQrThreads) {
-            const int gr = row0 + r;
-            if (gr > jj) sA[jj * R + r] *= scale;
-            else if (gr == jj) sA[jj * R + r] = beta;
-        }
+        for (int r = rs + tid; r < nrows; r += kQrThreads) sA[jj * R + r] *= scale;
+        if (own_j && tid == 0) sA[jj * R + lj] = beta;
         __syncthreads();
-        // 3. partial w_c = A(jj, c) + sum_{i > jj} v_i A(i, c) for the columns right of jj
-        for (int c = jj + 1; c < w; ++c) {
+        // partial w_c = A(jj, c) + sum_{i > jj} v_i A(i, c) of this warp's columns
+        for (int c = jj + 1 + warp; c < w; c += NW) {
             T acc = T(0);
-            for (int r = tid; r < nrows; r += kQrThreads) {
-                const int gr = row0 + r;
-                if (gr > jj) acc = fma(sA[jj * R + r], sA[c * R + r], acc);
-                else if (gr == jj) acc += sA[c * R + r];
-            }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-            if (lane == 0) red2[warp][c] = acc;
-        }
-        __syncthreads();
-        for (int c = jj + 1 + tid; c < w; c += kQrThreads) {
-            T acc = T(0);
-            for (int q = 0; q < kQrThreads / 32; ++q) acc += red2[q][c];
-            s_w[g * kQrMaxLeaf + c] = acc;
+            for (int r = rs + lane; r < nrows; r += 32) acc = fma(sA[jj * R + r], sA[c * R + r], acc);
+            acc = warp_allsum(acc);
+            if (own_j) acc += sA[c * R + lj];
+            if (lane == 0) s_w[g * kQrMaxLeaf + c] = acc;
         }
         target += G;
         if (!lu_grid_barrier(sync, target, &sh_flag)) {
             ok = false;
             break;
         }
-        // the G partial dot products of each column, summed by one warp per column in
-        // the same fixed order as above
-        for (int c = jj + 1 + warp; c < w; c += kQrThreads / 32) {
-            T p = T(0);
-            for (int q = lane; q < G; q += 32) p += __ldcg(&s_w[q * kQrMaxLeaf + c]);
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) p += __shfl_xor_sync(0xffffffffu, p, o);
-            if (lane == 0) sh_w[c] = t * p;
-        }
-        __syncthreads();
-        // 4. rank-1 update A(jj:, c) -= v (tau w_c)
-        for (int c = jj + 1; c < w; ++c) {
-            const T tw = sh_w[c];
-            for (int r = tid; r < nrows; r += kQrThreads) {
-                const int gr = row0 + r;
-                if (gr > jj) sA[c * R + r] = fma(-sA[jj * R + r], tw, sA[c * R + r]);
-                else if (gr == jj) sA[c * R + r] -= tw;
+        // rank-1 update A(jj:, c) -= v (tau w_c) of this warp's columns, each w_c the
+        // G partials summed in a fixed order; warp 0 also forms the next column's
+        // sum of squares below its diagonal
+        const int rs1 = max(0, lj + 2);
+        for (int c = jj + 1 + warp; c < w; c += NW) {
+            const T tw = t * warp_sum_slots(s_w + c, G, kQrMaxLeaf, lane);
+            T s = T(0);
+            for (int r = rs + lane; r < nrows; r += 32) {
+                const T x = fma(-sA[jj * R + r], tw, sA[c * R + r]);
+                sA[c * R + r] = x;
+                if (r >= rs1) s = fma(x, x, s);
+            }
+            if (own_j && lane == 0) sA[c * R + lj] -= tw;
+            if (c == jj + 1) {
+                ss = warp_allsum(s);
+                have_ss = true;
             }
         }
-        __syncthreads();
     }
+    __syncthreads();
     if (ok)
         for (int c = 0; c < w; ++c)
             for (int r = tid; r < nrows; r += kQrThreads) A[(int64_t)(row0 + r) + (int64_t)c * lda] = sA[c * R + r];
@@ -177,62 +178,94 @@ __global__ void __launch_bounds__(kQrThreads) qr_leaf_kernel(T* __restrict__ A, 
 }
 
 // Transposed-operand product C(M x N) = A(K x M)^T B(K x N): 64 x 64 output
-// tiles, 16-deep K steps staged in shared memory, 4 x 4 outputs per thread.
-// K is cut into fixed slices of kTnSlice rows; every slice's partial product
-// is summed from zero and the partials are added in slice order, whether one
-// CTA runs all slices (split = 0) or each slice has its own CTA (split = 1,
-// blockIdx.z = slice, partials to P[s] (M x N, ld = M) for qr_splitk_reduce).
-// So the result does not depend on how a product is cut into launches.
-constexpr int kTnBM = 64, kTnBN = 64, kTnBK = 16, kTnSlice = 128;
+// tiles, 4 x 4 outputs per thread.  K is cut into fixed slices of kTnSlice rows;
+// every slice's partial product is summed from zero and the partials are added
+// in slice order, whether one CTA runs all slices (split = 0) or each slice has
+// its own CTA (split = 1, blockIdx.z = slice, partials to P[s] (M x N, ld = M)
+// for qr_splitk_reduce).  So the result does not depend on how a product is cut
+// into launches.  The K rows stream through shared memory in chunks of kTnChunk
+// rows by asynchronous element copies, two chunks in flight, so a chunk's global
+// latency is paid once and overlaps the previous chunk's arithmetic.
+constexpr int kTnBM = 64, kTnBN = 64, kTnSlice = 128, kTnChunk = 64, kTnPad = kTnBM + 1;
+
+template <typename T>
+constexpr size_t gemm_tn_smem() {
+    return sizeof(T) * 2 * 2 * kTnChunk * kTnPad;
+}
 
 template <typename T>
 __global__ void __launch_bounds__(256) gemm_tn_kernel(int M, int N, int64_t K, int split, const T* __restrict__ A,
                                                       int64_t lda, const T* __restrict__ B, int64_t ldb,
                                                       T* __restrict__ C, int64_t ldc) {
-    __shared__ T sA[kTnBK][kTnBM + 1];  // sA[k][i] = A(k0 + k, i0 + i)
-    __shared__ T sB[kTnBK][kTnBN + 1];  // sB[k][j] = B(k0 + k, j0 + j)
+    static_assert(kTnSlice % kTnChunk == 0, "a slice is whole chunks");
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    // buf[b][0][k][i] = A(k0 + k, i0 + i), buf[b][1][k][j] = B(k0 + k, j0 + j)
+    T* buf = reinterpret_cast<T*>(smem_raw);
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
     const int i0 = blockIdx.x * kTnBM, j0 = blockIdx.y * kTnBN;
     const int64_t nsl = (K + kTnSlice - 1) / kTnSlice;
     const int64_t s0 = split ? (int64_t)blockIdx.z : 0, s1 = split ? s0 + 1 : nsl;
-    T tot[4][4];
+    const int64_t kbeg = s0 * kTnSlice, kend = min(K, s1 * kTnSlice);
+    const int64_t nch = (kend - kbeg + kTnChunk - 1) / kTnChunk;
+    auto issue = [&](int64_t q) {
+        T* sA = buf + (size_t)(q & 1) * 2 * kTnChunk * kTnPad;
+        T* sB = sA + kTnChunk * kTnPad;
+        const int64_t k0 = kbeg + q * kTnChunk;
+        const int64_t ke = min(kend, k0 + kTnChunk);
+        for (int e = tid; e < kTnChunk * kTnBM; e += 256) {
+            const int kk = e & (kTnChunk - 1), ii = e / kTnChunk;
+            const int64_t k = k0 + kk;
+            if (k < ke && i0 + ii < M)
+                cp_async_elem<T>(sA + kk * kTnPad + ii, A + k + (int64_t)(i0 + ii) * lda);
+            else
+                sA[kk * kTnPad + ii] = T(0);
+            if (k < ke && j0 + ii < N)
+                cp_async_elem<T>(sB + kk * kTnPad + ii, B + k + (int64_t)(j0 + ii) * ldb);
+            else
+                sB[kk * kTnPad + ii] = T(0);
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    };
+    T tot[4][4], acc[4][4];
 #pragma unroll
     for (int x = 0; x < 4; ++x)
 #pragma unroll
-        for (int y = 0; y < 4; ++y) tot[x][y] = T(0);
-    for (int64_t sl = s0; sl < s1; ++sl) {
-        const int64_t kb = sl * kTnSlice, ke = min(K, kb + kTnSlice);
-        T acc[4][4];
+        for (int y = 0; y < 4; ++y) tot[x][y] = acc[x][y] = T(0);
+    if (nch > 0) issue(0);
+    if (nch > 1) issue(1);
+    for (int64_t q = 0; q < nch; ++q) {
+        if (q + 1 < nch)
+            asm volatile("cp.async.wait_group 1;" ::: "memory");
+        else
+            asm volatile("cp.async.wait_group 0;" ::: "memory");
+        __syncthreads();
+        const T* sA = buf + (size_t)(q & 1) * 2 * kTnChunk * kTnPad;
+        const T* sB = sA + kTnChunk * kTnPad;
+#pragma unroll 8
+        for (int kk = 0; kk < kTnChunk; ++kk) {
+            T a[4], b[4];
 #pragma unroll
-        for (int x = 0; x < 4; ++x)
+            for (int x = 0; x < 4; ++x) a[x] = sA[kk * kTnPad + tx + 16 * x];
 #pragma unroll
-            for (int y = 0; y < 4; ++y) acc[x][y] = T(0);
-        for (int64_t k0 = kb; k0 < ke; k0 += kTnBK) {
-            for (int e = tid; e < kTnBK * kTnBM; e += 256) {
-                const int kk = e % kTnBK, ii = e / kTnBK;
-                const int64_t k = k0 + kk;
-                sA[kk][ii] = (k < ke && i0 + ii < M) ? A[k + (int64_t)(i0 + ii) * lda] : T(0);
-                sB[kk][ii] = (k < ke && j0 + ii < N) ? B[k + (int64_t)(j0 + ii) * ldb] : T(0);
-            }
-            __syncthreads();
+            for (int y = 0; y < 4; ++y) b[y] = sB[kk * kTnPad + ty + 16 * y];
 #pragma unroll
-            for (int kk = 0; kk < kTnBK; ++kk) {
-                T a[4], b[4];
+            for (int x = 0; x < 4; ++x)
 #pragma unroll
-                for (int x = 0; x < 4; ++x) a[x] = sA[kk][tx + 16 * x];
-#pragma unroll
-                for (int y = 0; y < 4; ++y) b[y] = sB[kk][ty + 16 * y];
-#pragma unroll
-                for (int x = 0; x < 4; ++x)
-#pragma unroll
-                    for (int y = 0; y < 4; ++y) acc[x][y] = fma(a[x], b[y], acc[x][y]);
-            }
-            __syncthreads();
+                for (int y = 0; y < 4; ++y) acc[x][y] = fma(a[x], b[y], acc[x][y]);
         }
+        // a slice ends: its partial product joins the total (slice order)
+        const int64_t kq = kbeg + (q + 1) * kTnChunk;
+        if (kq % kTnSlice == 0 || q + 1 == nch) {
 #pragma unroll
-        for (int x = 0; x < 4; ++x)
+            for (int x = 0; x < 4; ++x)
 #pragma unroll
-            for (int y = 0; y < 4; ++y) tot[x][y] += acc[x][y];
+                for (int y = 0; y < 4; ++y) {
+                    tot[x][y] += acc[x][y];
+                    acc[x][y] = T(0);
+                }
+        }
+        __syncthreads();
+        if (q + 2 < nch) issue(q + 2);
     }
     T* out = split ? C + (int64_t)blockIdx.z * M * N : C;
     const int64_t ldo = split ? (int64_t)M : ldc;
@@ -374,7 +407,9 @@ int qr_gemm_tn(lu_context* c, cudaStream_t st, int M, int N, int64_t K, const T*
                        nsl * (int64_t)M * N <= kQrPartCap;
     LuProfScope prof(st, LU_K_GEMM, sizeof(T) * ((double)K * (M + N) + (double)M * N), 2.0 * M * N * K);
     const dim3 grid((unsigned)lu_cdiv(M, kTnBM), (unsigned)lu_cdiv(N, kTnBN), split ? (unsigned)nsl : 1u);
-    gemm_tn_kernel<T><<<grid, 256, 0, st>>>(M, N, K, split ? 1 : 0, A, lda, B, ldb, split ? part : C, ldc);
+    LU_TRY(lu_func_smem(gemm_tn_kernel<T>, (int)gemm_tn_smem<T>()));
+    gemm_tn_kernel<T><<<grid, 256, gemm_tn_smem<T>(), st>>>(M, N, K, split ? 1 : 0, A, lda, B, ldb, split ? part : C,
+                                                           ldc);
     LU_CHECK_LAUNCH();
     if (split) {
         const int64_t total = (int64_t)M * N;

@@ -815,22 +815,6 @@ int lu_launch_trsv_blocked(lu_context* c, cudaStream_t st, bool lower_unit, int6
             return LU_SUCCESS;
         }
     }
-    if constexpr (sizeof(T) == 4) {
-        if (inv && xtag && nrhs == 1) {
-            LU_TRY(lu_func_smem(trsv_tag_kernel<true>, (int)C::smem));
-            LU_TRY(lu_func_smem(trsv_tag_kernel<false>, (int)C::smem));
-            // tags are unique per launch within the process (0 is never used: the buffer starts zeroed)
-            static std::atomic<unsigned> next_tag{1};
-            unsigned tag = next_tag.fetch_add(1);
-            if (tag == 0) tag = next_tag.fetch_add(1);
-            LU_CHECK_CUDA(cudaMemsetAsync(&c->sync[1].ticket, 0, sizeof(unsigned), st));
-            LuProfScope prof(st, LU_K_SOLVE, sizeof(T) * (0.5 * n * n + 2.0 * n), (double)n * n);
-            auto fn = lower_unit ? trsv_tag_kernel<true> : trsv_tag_kernel<false>;
-            fn<<<nblk, kTrsvThreads, C::smem, st>>>(map, dmap, n, (float*)X, xtag, tag, &c->sync[1]);
-            LU_CHECK_LAUNCH();
-            return LU_SUCCESS;
-        }
-    }
     for (int64_t c0 = 0; c0 < nrhs; c0 += kNR) {
         const int nr = (int)std::min<int64_t>(kNR, nrhs - c0);
         // reset the ticket and the done counter (the error word is kept: sticky)
