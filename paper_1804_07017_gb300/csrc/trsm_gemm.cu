@@ -242,6 +242,80 @@ __global__ void __launch_bounds__(kGemmThreads)
 
 
 
+// The same update for a short inner dimension (k <= kStagedK, the recursive
+// panel's own RL3): the CTA's whole A (BM x k) and B (k x BN) tiles are copied
+// to shared memory asynchronously and its C tile read into registers, all
+// issued at once, so the launch pays one global round trip instead of one per
+// 16-deep step.  Same thread mapping and the same k-ordered accumulation as
+// gemm_update_kernel, so the results are identical.
+constexpr int kStagedK = 128;
+
+template <typename T, int BM, int BN>
+__global__ void __launch_bounds__(kGemmThreads)
+    gemm_update_staged_kernel(int64_t m, int64_t n, int k, const T* __restrict__ A, int64_t lda,
+                              const T* __restrict__ B, int64_t ldb, T* __restrict__ C, int64_t ldc) {
+    constexpr int TX = BM / 4, TY = BN / 4;
+    static_assert(TX * TY == kGemmThreads, "tile shape");
+    extern __shared__ __align__(16) unsigned char smraw[];
+    T* sA = reinterpret_cast<T*>(smraw);  // [k][BM]: sA[p * BM + i] = A(i0 + i, p)
+    T* sB = sA + (size_t)k * BM;           // [k][BN + 1]: sB[p * (BN + 1) + j] = B(p, j0 + j)
+    const int tid = threadIdx.x, tx = tid % TX, ty = tid / TX;
+    const int64_t i0 = (int64_t)blockIdx.x * BM, j0 = (int64_t)blockIdx.y * BN;
+    for (int e = tid; e < BM * k; e += kGemmThreads) {
+        const int i = e % BM, p = e / BM;
+        if (i0 + i < m)
+            cp_async_elem<T>(sA + p * BM + i, A + (i0 + i) + (int64_t)p * lda);
+        else
+            sA[p * BM + i] = T(0);
+    }
+    for (int e = tid; e < BN * k; e += kGemmThreads) {
+        const int p = e % k, j = e / k;
+        if (j0 + j < n)
+            cp_async_elem<T>(sB + p * (BN + 1) + j, B + p + (j0 + j) * ldb);
+        else
+            sB[p * (BN + 1) + j] = T(0);
+    }
+    T cur[4][4];
+#pragma unroll
+    for (int y = 0; y < 4; ++y)
+#pragma unroll
+        for (int x = 0; x < 4; ++x) {
+            const int64_t i = i0 + tx + TX * x, j = j0 + ty + TY * y;
+            cur[x][y] = (i < m && j < n) ? C[i + j * ldc] : T(0);
+        }
+    cp_async_wait_all();
+    __syncthreads();
+    T acc[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = T(0);
+#pragma unroll 4
+    for (int p = 0; p < k; ++p) {
+        T a[4], b[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            a[q] = sA[p * BM + tx + TX * q];
+            b[q] = sB[p * (BN + 1) + ty + TY * q];
+        }
+#pragma unroll
+        for (int x = 0; x < 4; ++x)
+#pragma unroll
+            for (int y = 0; y < 4; ++y) acc[x][y] = fma(a[x], b[y], acc[x][y]);
+    }
+#pragma unroll
+    for (int y = 0; y < 4; ++y) {
+        const int64_t j = j0 + ty + TY * y;
+        if (j >= n) continue;
+#pragma unroll
+        for (int x = 0; x < 4; ++x) {
+            const int64_t i = i0 + tx + TX * x;
+            if (i < m) C[i + j * ldc] = cur[x][y] - acc[x][y];
+        }
+    }
+}
+
+
 // RL2 + RL3 of a narrow node of the recursive panel (w1 <= 32, w2 <= 32) in one
 // launch:  U12 := trilu(L11)^{-1} A12,  A22 := A22 - A21 U12.
 // Every CTA solves the w1 x w2 block U12 itself, in shared memory, with the
@@ -251,20 +325,42 @@ __global__ void __launch_bounds__(kGemmThreads)
 // so the results are bit-identical to the two separate launches.  U12 is
 // written back over A12 by the last CTA to have read A12 (an arrival counter
 // that this CTA resets), so no CTA can read an already solved block.
+// Latency: every global read of the CTA -- its A21 tile (asynchronous copies
+// into shared memory), its A22 outputs (into registers), L11 and A12 -- is
+// issued before the substitution, so the launch pays one round trip.
 template <typename T, int BM, int BN>
 __global__ void __launch_bounds__(kGemmThreads)
     trsm_gemm_narrow_kernel(int64_t m2, int w2, int w1, const T* __restrict__ L11, T* __restrict__ A12,
                             const T* __restrict__ A21, T* __restrict__ A22, int64_t lda, unsigned* __restrict__ arrivals) {
     constexpr int TX = BM / 4, TY = BN / 4;
     static_assert(TX * TY == kGemmThreads, "tile shape");
-    constexpr int NA = BM * BK / kGemmThreads;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    T* sA = reinterpret_cast<T*>(smraw);  // [32][BM]: sA[p * BM + i] = A21(i0 + i, p)
     __shared__ T sL[32 * 33];              // sL[j * 33 + i] = L(i, j)
     __shared__ T sU[32][BN + 1];           // U12, row p = k index
-    extern __shared__ __align__(16) unsigned char smraw[];
-    T* sA = reinterpret_cast<T*>(smraw);   // [2][BK][BM] A21 k-chunks
     __shared__ int s_last;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t i0 = (int64_t)blockIdx.x * BM;
+    const int tx = tid % TX, ty = tid / TX;
+    // this CTA's A21 tile, all copies in flight
+    if (i0 < m2)
+        for (int e = tid; e < 32 * BM; e += kGemmThreads) {
+            const int i = e % BM, p = e / BM;
+            if (i0 + i < m2 && p < w1)
+                cp_async_elem<T>(sA + p * BM + i, A21 + (i0 + i) + (int64_t)p * lda);
+            else
+                sA[p * BM + i] = T(0);
+        }
+    // its outputs' current values
+    T cur[4][4];
+#pragma unroll
+    for (int y = 0; y < 4; ++y)
+#pragma unroll
+        for (int x = 0; x < 4; ++x) {
+            const int j = ty + TY * y;
+            const int64_t i = i0 + tx + TX * x;
+            cur[x][y] = (j < w2 && i < m2) ? A22[i + (int64_t)j * lda] : T(0);
+        }
     for (int e = tid; e < 32 * 32; e += kGemmThreads) {
         const int i = e & 31, j = e >> 5;
         sL[j * 33 + i] = (i < w1 && j < w1) ? L11[i + (int64_t)j * lda] : T(0);
@@ -287,6 +383,7 @@ __global__ void __launch_bounds__(kGemmThreads)
         }
         if (lane < w1) sU[lane][c] = v;
     }
+    cp_async_wait_all();
     __syncthreads();
     if (s_last)
         for (int e = tid; e < w1 * w2; e += kGemmThreads) {
@@ -294,53 +391,22 @@ __global__ void __launch_bounds__(kGemmThreads)
             A12[i + (int64_t)j * lda] = sU[i][j];
         }
     if (i0 >= m2) return;
-    const int tx = tid % TX, ty = tid / TX;
     T acc[4][4];
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
         for (int b = 0; b < 4; ++b) acc[a][b] = T(0);
-    T ra[NA];
-    auto load_regs = [&](int p0) {
+    for (int p = 0; p < w1; ++p) {
+        T a[4], b[4];
 #pragma unroll
-        for (int q = 0; q < NA; ++q) {
-            const int e = tid + q * kGemmThreads;
-            const int i = e % BM, p = e / BM;
-            ra[q] = (i0 + i < m2 && p0 + p < w1) ? A21[(i0 + i) + (int64_t)(p0 + p) * lda] : T(0);
+        for (int q = 0; q < 4; ++q) {
+            a[q] = sA[p * BM + tx + TX * q];
+            b[q] = sU[p][ty + TY * q];
         }
-    };
-    auto store_smem = [&](int s) {
 #pragma unroll
-        for (int q = 0; q < NA; ++q) {
-            const int e = tid + q * kGemmThreads;
-            sA[(s * BK + e / BM) * BM + e % BM] = ra[q];
-        }
-    };
-    load_regs(0);
-    store_smem(0);
-    __syncthreads();
-    int s = 0;
-    for (int p0 = 0; p0 < w1; p0 += BK) {
-        const bool more = p0 + BK < w1;
-        if (more) load_regs(p0 + BK);
+        for (int x = 0; x < 4; ++x)
 #pragma unroll
-        for (int p = 0; p < BK; ++p) {
-            T a[4], b[4];
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                a[q] = sA[(s * BK + p) * BM + tx + TX * q];
-                b[q] = sU[p0 + p][ty + TY * q];
-            }
-#pragma unroll
-            for (int x = 0; x < 4; ++x)
-#pragma unroll
-                for (int y = 0; y < 4; ++y) acc[x][y] = fma(a[x], b[y], acc[x][y]);
-        }
-        if (more) {
-            store_smem(s ^ 1);
-            __syncthreads();
-            s ^= 1;
-        }
+            for (int y = 0; y < 4; ++y) acc[x][y] = fma(a[x], b[y], acc[x][y]);
     }
 #pragma unroll
     for (int y = 0; y < 4; ++y) {
@@ -349,7 +415,7 @@ __global__ void __launch_bounds__(kGemmThreads)
 #pragma unroll
         for (int x = 0; x < 4; ++x) {
             const int64_t i = i0 + tx + TX * x;
-            if (i < m2) A22[i + (int64_t)j * lda] -= acc[x][y];
+            if (i < m2) A22[i + (int64_t)j * lda] = cur[x][y] - acc[x][y];
         }
     }
 }
@@ -408,6 +474,17 @@ int lu_launch_gemm_update_band(cudaStream_t st, int64_t m, int64_t n, int64_t k,
             return LU_SUCCESS;
         }
     }
+    if constexpr (sizeof(T) == 4) {
+        // a short inner dimension (the recursive panel's own updates): one round trip
+        if (n > 32 && k <= kStagedK && band == 0 && lu_cdiv(n, 64) <= 65535) {
+            const size_t smem = sizeof(T) * ((size_t)k * 64 + (size_t)k * 65);
+            LU_TRY(lu_func_smem(gemm_update_staged_kernel<T, 64, 64>, (int)(sizeof(T) * kStagedK * 129)));
+            gemm_update_staged_kernel<T, 64, 64><<<dim3((unsigned)lu_cdiv(m, 64), (unsigned)lu_cdiv(n, 64)),
+                                                   kGemmThreads, smem, st>>>(m, n, (int)k, A, lda, B, ldb, C, ldc);
+            LU_CHECK_LAUNCH();
+            return LU_SUCCESS;
+        }
+    }
     if (n <= 32) {
         gemm_update_kernel<T, 128, 32><<<dim3((unsigned)lu_cdiv(m, 128), (unsigned)lu_cdiv(n, 32)), kGemmThreads, 0,
                                           st>>>(m, n, (int)k, A, lda, B, ldb, C, ldc, r0, c0, band);
@@ -437,7 +514,7 @@ template int lu_launch_gemm_update<float>(cudaStream_t, int64_t, int64_t, int64_
 template <typename T, int BM, int BN>
 static int launch_narrow(cudaStream_t st, int64_t m2, int64_t w2, int64_t w1, const T* L11, T* A12, const T* A21,
                          T* A22, int64_t lda, unsigned* arrivals) {
-    const size_t smem = sizeof(T) * 2 * BK * BM;
+    const size_t smem = sizeof(T) * 32 * BM;
     LU_TRY(lu_func_smem(trsm_gemm_narrow_kernel<T, BM, BN>, (int)smem));
     const unsigned gx = (unsigned)std::max<int64_t>(1, lu_cdiv(m2, BM));
     trsm_gemm_narrow_kernel<T, BM, BN><<<gx, kGemmThreads, smem, st>>>(m2, (int)w2, (int)w1, L11, A12, A21, A22, lda,
