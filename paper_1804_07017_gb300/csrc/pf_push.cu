@@ -309,13 +309,14 @@ __global__ void __maxnreg__(LU_PF_PUSH_MAXREG)
 #pragma unroll
                     for (int k = 0; k < SB; ++k) sA[lj * WP + c0 + k] = v[q][k];
         }
-        __syncwarp();
-        const int cw = (lc >= 0) ? (lc % kPT) >> 5 : 0;
-        if (warp == cw) {
+        // the rows are complete in shared memory; every warp then takes a share of the
+        // C x (chunks) pushes, so they leave in one or two rounds instead of one warp's five
+        __syncthreads();
+        {
             const T* rp = sA + (lc >= 0 ? lc : 0) * WP;
             const uint32_t base = smem_u32(msg) + (uint32_t)((buf * kMaxC + g) * ML::bytes);
             // row chunks carry 4 row words; the last chunk holds the key and the row index
-            for (int t = lane; t < C * ML::chunks; t += 32) {
+            for (int t = tid; t < C * ML::chunks; t += kPT) {
                 const int dst = t / ML::chunks, ch = t % ML::chunks;
                 uint32_t x0, x1, x2, x3;
                 if (ch < ML::jchunks) {
@@ -336,10 +337,10 @@ __global__ void __maxnreg__(LU_PF_PUSH_MAXREG)
                 push16(base + 16 * ch, bar0 + 8 * buf, dst, x0, x1, x2, x3);
             }
         }
-        if (own_j && warp == (lj % kPT) >> 5) {
+        if (own_j) {
             const T* rp = sA + lj * WP;
             const uint32_t base = smem_u32(jrow + buf * W);
-            for (int t = lane; t < C * ML::jchunks; t += 32) {
+            for (int t = tid; t < C * ML::jchunks; t += kPT) {
                 const int dst = t / ML::jchunks, ch = t % ML::jchunks;
                 push16(base + 16 * ch, bar0 + 8 * buf, dst, elem_word<T>(rp, 4 * ch), elem_word<T>(rp, 4 * ch + 1),
                        elem_word<T>(rp, 4 * ch + 2), elem_word<T>(rp, 4 * ch + 3));
@@ -480,19 +481,36 @@ __global__ void __maxnreg__(LU_PF_PUSH_MAXREG)
             leaf_wait(bar0 + 16, (uint32_t)(sb & 1), sync, failed);
             if (tid == 0 && c0 + 2 * SB < w) mbar_expect_cta(bar0 + 16, u_bytes);
             // ---- rank-SB update of the remaining leaf columns: A22 -= L21 U12 ----
-            for (int c = c0 + SB; c < w; ++c) {
-                T u[SB];
-#pragma unroll
-                for (int kk = 0; kk < SB; ++kk) u[kk] = su[kk * W + c];
+            // Four columns at a time, so that each thread has RQ x 4 independent
+            // multiply-add chains in flight (two warps per scheduler cannot hide
+            // the latency of one chain per row); every element still takes its SB
+            // products in order.  W is a multiple of 4 and c starts at a multiple
+            // of SB, so the four columns never pass W.
+            for (int cb = c0 + SB; cb < w; cb += 4) {
+                T a[RQ][4];
 #pragma unroll
                 for (int q = 0; q < RQ; ++q) {
                     const int r = tid + kPT * q;
-                    if (r < nrows && row0 + r >= c0 + SB) {
-                        T a = sA[r * WP + c];
 #pragma unroll
-                        for (int kk = 0; kk < SB; ++kk) a = fma(-v[q][kk], u[kk], a);
-                        sA[r * WP + c] = a;
-                    }
+                    for (int cc = 0; cc < 4; ++cc) a[q][cc] = sA[r * WP + cb + cc];
+                }
+#pragma unroll
+                for (int kk = 0; kk < SB; ++kk) {
+                    T u[4];
+#pragma unroll
+                    for (int cc = 0; cc < 4; ++cc) u[cc] = su[kk * W + cb + cc];
+#pragma unroll
+                    for (int q = 0; q < RQ; ++q)
+#pragma unroll
+                        for (int cc = 0; cc < 4; ++cc) a[q][cc] = fma(-v[q][kk], u[cc], a[q][cc]);
+                }
+#pragma unroll
+                for (int q = 0; q < RQ; ++q) {
+                    const int r = tid + kPT * q;
+                    if (r < nrows && row0 + r >= c0 + SB)
+#pragma unroll
+                        for (int cc = 0; cc < 4; ++cc)
+                            if (cb + cc < w) sA[r * WP + cb + cc] = a[q][cc];
                 }
             }
             __syncthreads();
