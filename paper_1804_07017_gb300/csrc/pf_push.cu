@@ -533,46 +533,51 @@ __global__ void __maxnreg__(LU_PF_PUSH_MAXREG)
     const int other = left_cols + right_cols;
     if (other > 0) {
         // ---- the leaf's interchanges on the other columns of the panel ----
-        // Plan: positions 0..w-1 (leaf rows) and the distinct targets below them.
-        if (tid == 0) {
-            int tgt[W], cur[2 * W];
+        // Plan: positions 0..w-1 (leaf rows) and the distinct targets below them, the
+        // leaf's swaps composed in order by one warp: lane i holds the current source
+        // of leaf row i and of the i-th target slot; a target's slot is found by a
+        // ballot.  The moves are listed leaf rows first, then targets, in slot order.
+        if (warp == 0) {
+            int cur_l = lane;         // source of leaf row `lane`
+            int tgt = -1, cur_t = -1;  // target slot `lane`: its row and its source
             int nt = 0;
-            for (int i = 0; i < w; ++i) cur[i] = i;
             for (int k = 0; k < w; ++k) {
                 const int pk = s_piv[k];
                 if (pk == k) continue;
-                int b;
+                const int xk = __shfl_sync(0xffffffffu, cur_l, k);
                 if (pk < w) {
-                    b = pk;
+                    const int xp = __shfl_sync(0xffffffffu, cur_l, pk);
+                    if (lane == k) cur_l = xp;
+                    if (lane == pk) cur_l = xk;
                 } else {
-                    int f = -1;
-                    for (int t = 0; t < nt; ++t)
-                        if (tgt[t] == pk) f = t;
-                    if (f < 0) {
+                    const unsigned hit = __ballot_sync(0xffffffffu, tgt == pk);
+                    int f;
+                    if (hit) {
+                        f = __ffs(hit) - 1;
+                    } else {
                         f = nt++;
-                        tgt[f] = pk;
-                        cur[w + f] = pk;
+                        if (lane == f) tgt = cur_t = pk;
                     }
-                    b = w + f;
+                    const int xf = __shfl_sync(0xffffffffu, cur_t, f);
+                    if (lane == k) cur_l = xf;
+                    if (lane == f) cur_t = xk;
                 }
-                const int x = cur[k];
-                cur[k] = cur[b];
-                cur[b] = x;
             }
-            int cnt = 0;
-            for (int i = 0; i < w; ++i)
-                if (cur[i] != i) {
-                    s_dst[cnt] = i;
-                    s_src[cnt] = cur[i];
-                    ++cnt;
-                }
-            for (int t = 0; t < nt; ++t)
-                if (cur[w + t] != tgt[t]) {
-                    s_dst[cnt] = tgt[t];
-                    s_src[cnt] = cur[w + t];
-                    ++cnt;
-                }
-            s_cnt = cnt;
+            const bool mv_l = lane < w && cur_l != lane;
+            const unsigned bl = __ballot_sync(0xffffffffu, mv_l);
+            const int nl = __popc(bl);
+            const unsigned below = (1u << lane) - 1u;
+            if (mv_l) {
+                s_dst[__popc(bl & below)] = lane;
+                s_src[__popc(bl & below)] = cur_l;
+            }
+            const bool mv_t = lane < nt && cur_t != tgt;
+            const unsigned bt = __ballot_sync(0xffffffffu, mv_t);
+            if (mv_t) {
+                s_dst[nl + __popc(bt & below)] = tgt;
+                s_src[nl + __popc(bt & below)] = cur_t;
+            }
+            if (lane == 0) s_cnt = nl + __popc(bt);
         }
         __syncthreads();
         const int cnt = s_cnt;
