@@ -855,7 +855,8 @@ def run_configs(args):
     c2  n = 16384, nb = 256: the mixed solver with each trailing-update precision
         (N(0,1), one rhs), then bf16x6 on the row-scaled matrix and with 16 rhs;
     c3  n = 32768, nb = 256, A = diag(10^u) G: bf16x6 and e4m3 updates.
-    For c2 (N(0,1), one rhs) and c3 each variant also reports
+    c2 and c3 run with the panel leaves on an SM partition of --pf-sms SMs, as
+    the default bench does.  For c2 (N(0,1), one rhs) and c3 each variant also reports
     ||x - x_oracle||_inf / ||x_oracle||_inf against the CPU oracle's FP64
     solution stored by tests/golden/make_reference_solutions.py.
     Each configuration runs twice untimed, then once timed with CUDA events."""
@@ -918,10 +919,10 @@ def run_configs(args):
         for name in precs:
             code = {"bf16": 0, "fp16": 1, "fp8": 2, "f32": 3, "bf16x3": 4, "f64": 5, "bf16x6": 6}[name]
             ms, (st, it, eta) = timed(lambda: lu.lu_gesv_mixed(A, B, X, code, TOL, MAX_ITER,
-                                                                 lu.default_opts(nb=256)))
+                                                                 lu.default_opts(nb=256, pf_sms=args.pf_sms)))
             res[f"{tag}{name}"] = {"ms": ms, "gflops": 2 * n ** 3 / 3 / ms / 1e6, "status": int(st),
                                    "refinements": int(it), "bwd_err": float(eta),
-                                   "converged": int(st) == 0}
+                                   "converged": int(st) == 0, "pf_sms": args.pf_sms}
             if ref is not None:
                 x_or, why = ref
                 if x_or is None:

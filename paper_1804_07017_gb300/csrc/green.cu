@@ -114,13 +114,13 @@ int lu_green_setup(lu_context* c, int part_sms) {
     ok = ok && cudaEventCreateWithFlags(&g->ev_in, cudaEventDisableTiming) == cudaSuccess &&
          cudaEventCreateWithFlags(&g->ev_out, cudaEventDisableTiming) == cudaSuccess;
     c->green = g;
-    // the leaf partition must hold the widest cluster a leaf launches (16 CTAs of up to
-    // 160 KB of shared memory); otherwise the partition is not used
+    // the leaf partition must hold the widest cluster a leaf launches (16 CTAs of 512
+    // threads and up to 160 KB of shared memory); otherwise the partition is not used
     if (ok && a.push(g->c_leaf) == CUDA_SUCCESS) {
         int fits = 0;
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3(LU_PF_MAX_CTAS_CLUSTER, 1, 1);
-        cfg.blockDim = dim3(256, 1, 1);
+        cfg.blockDim = dim3(512, 1, 1);
         cfg.dynamicSmemBytes = LU_PF_SMEM_PART;
         cudaLaunchAttribute at[1];
         at[0].id = cudaLaunchAttributeClusterDimension;

@@ -65,6 +65,9 @@ struct lu_context {
     // Shared memory a panel leaf CTA may use: small enough, on the mixed path, to
     // sit beside a tensor-core trailing-update CTA on the same SM.
     size_t pf_smem_budget = 160 * 1024;
+    // threads per CTA of an FP32 cluster leaf: 512 (half the rows per thread of 256)
+    // wherever the leaf may take most of an SM, 256 beside the tensor-core update
+    int pf_threads = 512;
     // SMs the right trailing update leaves to the panel path (set per factorization).
     int tu_reserve = 0;
     // Symmetric (Cholesky) trailing update: > 0 = the panel width; the updates then
@@ -176,8 +179,10 @@ int lu_launch_trinv_diag(cudaStream_t st, int64_t n, const T* LU, int64_t lda, T
 int lu_launch_finish_info(cudaStream_t st, const LuSync* s, int32_t* info);
 
 template <typename T>
+// max_c > 0 caps the cluster size; nt = 512 asks for the 512-thread leaf (FP32
+// pushed-message leaf only; otherwise 256), the thread count taken goes to nt_out.
 bool lu_pf_cluster_shape(int64_t m, int w, size_t budget, int* C_out, int* R_out, size_t* smem_out,
-                         int max_c = 0);  // max_c > 0 caps the cluster size
+                         int max_c = 0, int nt = 256, int* nt_out = nullptr);
 // sib > 0: the leaf also applies L11^-1 to the top rows of the first sib columns to its
 // right (its sibling's U12); kprev > 0: the leaf first applies the preceding sibling's
 // rank-kprev update to its own columns.  Both need the pushed-message leaf
@@ -185,14 +190,14 @@ bool lu_pf_cluster_shape(int64_t m, int w, size_t budget, int* C_out, int* R_out
 template <typename T>
 int lu_launch_pf_leaf_cluster(cudaStream_t st, T* A, int64_t lda, int64_t m, int w, int C, int R, size_t smem,
                               int64_t left_cols, int64_t right_cols, int32_t* ipiv, int64_t ipiv_add, LuSync* sync,
-                              int sib = 0, int kprev = 0);
+                              int sib = 0, int kprev = 0, int nt = 256);
 bool lu_pf_leaf_pairs_supported();
 // Pushed-message cluster leaf (pf_push.cu): w columns of a kernel compiled for wc.
-size_t lu_pf_push_smem(int esize, int w, int rq);
+size_t lu_pf_push_smem(int esize, int w, int rq, int nt = 256);
 template <typename T>
 int lu_launch_pf_leaf_push(cudaStream_t st, T* A, int64_t lda, int64_t m, int w, int wc, int C, int R,
                            int64_t left_cols, int64_t right_cols, int32_t* ipiv, int64_t ipiv_add, LuSync* sync,
-                           int sib, int kprev);
+                           int sib, int kprev, int nt = 256);
 
 // Recursive panel factorization of columns [j0, j0+width) over rows [j0, M)
 // of the matrix at A (absolute indices; ipiv absolute, 1-based).

@@ -377,14 +377,20 @@ int lu_factor_blocked(lu_context* c, int64_t n, T* A, int64_t lda, int32_t* ipiv
     struct GreenOff {
         lu_context* c;
         size_t budget;
+        int threads;
         ~GreenOff() {
             c->green_active = false;
             c->pf_smem_budget = budget;
+            c->pf_threads = threads;
         }
-    } green_off{c, c->pf_smem_budget};
+    } green_off{c, c->pf_smem_budget, c->pf_threads};
     // on their own SMs the leaves need not leave room for update CTAs: wider leaves
-    // (32 columns at up to 16384 rows) fit
-    if (c->green_active) c->pf_smem_budget = std::max<size_t>(c->pf_smem_budget, LU_PF_SMEM_PART);
+    // (32 columns at up to 16384 rows) fit, and 512 threads per CTA halve the rows
+    // each thread carries through the per-column chain
+    if (c->green_active) {
+        c->pf_smem_budget = std::max<size_t>(c->pf_smem_budget, LU_PF_SMEM_PART);
+        c->pf_threads = 512;
+    }
     cudaStream_t lo = c->green_active ? lu_green_rest_stream(c) : c->lo;
     LU_CHECK_CUDA(cudaEventRecord(c->ev_fork, user));
     LU_CHECK_CUDA(cudaStreamWaitEvent(c->hi, c->ev_fork, 0));

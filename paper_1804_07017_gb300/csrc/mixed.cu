@@ -231,7 +231,9 @@ static int factor_mixed(lu_context* c, int prec, int64_t n, float* A32, int64_t 
     LU_TRY(setup_engine(e, c, prec, n, engine_mem, A32, lda, o));
     // panel leaves must fit beside a tensor-core update CTA on the same SM
     const size_t saved = c->pf_smem_budget;
+    const int saved_threads = c->pf_threads;
     c->pf_smem_budget = LU_PF_SMEM_BUDGET;
+    c->pf_threads = 256;
     // The launch sequence depends only on these arguments, so a repeated call
     // replays it as one CUDA graph (no per-kernel launch gaps on the panel path):
     // a key is run eagerly on first use, captured on its second, replayed after.
@@ -312,6 +314,7 @@ static int factor_mixed(lu_context* c, int prec, int64_t n, float* A32, int64_t 
         memcpy(c->fkey_seen, key, sizeof(key));
     }
     c->pf_smem_budget = saved;
+    c->pf_threads = saved_threads;
     return r;
 }
 

@@ -253,14 +253,16 @@ int panel_rec(lu_context* c, cudaStream_t st, T* A, int64_t lda, int64_t M, int6
               int32_t* ipiv, const lu_opts& o, int leaf, bool cluster, int64_t pc0, int64_t pw) {
     if (width <= 0) return LU_SUCCESS;
     const int64_t rows = M - j0;
+    const int nt_want = sizeof(T) == 4 ? c->pf_threads : 256;
     if (width <= leaf) {
         if (cluster) {
-            int C = 0, R = 0;
+            int C = 0, R = 0, nt = 256;
             size_t smem = 0;
-            if (lu_pf_cluster_shape<T>(rows, (int)width, c->pf_smem_budget, &C, &R, &smem, o.pf_ctas))
+            if (lu_pf_cluster_shape<T>(rows, (int)width, c->pf_smem_budget, &C, &R, &smem, o.pf_ctas, nt_want, &nt))
                 return on_leaf_sms(c, st, [&](cudaStream_t ls) {
                     return lu_launch_pf_leaf_cluster<T>(ls, A + j0 + j0 * lda, lda, rows, (int)width, C, R, smem,
-                                                        j0 - pc0, pc0 + pw - (j0 + width), ipiv + j0, j0, &c->sync[0]);
+                                                        j0 - pc0, pc0 + pw - (j0 + width), ipiv + j0, j0, &c->sync[0],
+                                                        0, 0, nt);
                 });
             return LU_ERR_UNSUPPORTED;
         }
@@ -273,17 +275,18 @@ int panel_rec(lu_context* c, cudaStream_t st, T* A, int64_t lda, int64_t M, int6
     // Two 16-column leaves: the first also forms its sibling's U12 and the second
     // applies the matching rank-w1 update in its prologue (no launch in between).
     if (cluster && w1 <= 16 && w2 <= 16 && w1 <= leaf && w2 <= leaf && lu_pf_leaf_pairs_supported()) {
-        int Ca = 0, Ra = 0, Cb = 0, Rb = 0;
+        int Ca = 0, Ra = 0, Cb = 0, Rb = 0, nta = 256, ntb = 256;
         size_t sa = 0, sb = 0;
-        if (lu_pf_cluster_shape<T>(rows, (int)w1, c->pf_smem_budget, &Ca, &Ra, &sa, o.pf_ctas) &&
-            lu_pf_cluster_shape<T>(rows - w1, (int)w2, c->pf_smem_budget, &Cb, &Rb, &sb, o.pf_ctas)) {
+        if (lu_pf_cluster_shape<T>(rows, (int)w1, c->pf_smem_budget, &Ca, &Ra, &sa, o.pf_ctas, nt_want, &nta) &&
+            lu_pf_cluster_shape<T>(rows - w1, (int)w2, c->pf_smem_budget, &Cb, &Rb, &sb, o.pf_ctas, nt_want, &ntb)) {
             const int64_t jb = j0 + w1;
             return on_leaf_sms(c, st, [&](cudaStream_t ls) {
                 LU_TRY(lu_launch_pf_leaf_cluster<T>(ls, A + j0 + j0 * lda, lda, rows, (int)w1, Ca, Ra, sa, j0 - pc0,
-                                                    pc0 + pw - (j0 + w1), ipiv + j0, j0, &c->sync[0], (int)w2, 0));
+                                                    pc0 + pw - (j0 + w1), ipiv + j0, j0, &c->sync[0], (int)w2, 0,
+                                                    nta));
                 return lu_launch_pf_leaf_cluster<T>(ls, A + jb + jb * lda, lda, rows - w1, (int)w2, Cb, Rb, sb,
                                                     jb - pc0, pc0 + pw - (jb + w2), ipiv + jb, jb, &c->sync[0], 0,
-                                                    (int)w1);
+                                                    (int)w1, ntb);
             });
         }
     }
@@ -323,12 +326,13 @@ int lu_panel_recursive(lu_context* c, cudaStream_t st, T* A, int64_t lda, int64_
     const int64_t rows = M - j0;
     // Cluster leaves (distributed shared memory, hardware barrier) when the tallest
     // leaf fits one cluster; otherwise grid-barrier leaves.
+    const int nt_want = sizeof(T) == 4 ? c->pf_threads : 256;
     int leaf = o.leaf > 0 ? std::min(o.leaf, LU_PF_MAX_LEAF) : 32;
     while (leaf > 8) {
         int C, R;
         size_t smem;
         if (lu_pf_cluster_shape<T>(rows, std::min<int>(leaf, (int)width), c->pf_smem_budget, &C, &R, &smem,
-                                   o.pf_ctas))
+                                   o.pf_ctas, nt_want))
             break;
         leaf >>= 1;
     }
@@ -336,7 +340,7 @@ int lu_panel_recursive(lu_context* c, cudaStream_t st, T* A, int64_t lda, int64_
         int C, R;
         size_t smem;
         if (lu_pf_cluster_shape<T>(rows, std::min<int>(leaf, (int)width), c->pf_smem_budget, &C, &R, &smem,
-                                   o.pf_ctas))
+                                   o.pf_ctas, nt_want))
             return panel_rec<T>(c, st, A, lda, M, j0, width, ipiv, o, leaf, true, j0, width);
     }
     leaf = o.leaf > 0 ? std::min(o.leaf, LU_PF_MAX_LEAF) : 32;

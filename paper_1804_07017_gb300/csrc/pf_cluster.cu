@@ -373,21 +373,27 @@ static int cluster_limit() {
 // w one of the compiled widths (8, 16, 32).
 static int compiled_width(int w) { return w <= 8 ? 8 : (w <= 16 ? 16 : (w <= 32 ? 32 : 0)); }
 
+static int leaf_mode();
+
 template <typename T>
-bool lu_pf_cluster_shape(int64_t m, int w, size_t budget, int* C_out, int* R_out, size_t* smem_out, int max_c) {
+bool lu_pf_cluster_shape(int64_t m, int w, size_t budget, int* C_out, int* R_out, size_t* smem_out, int max_c,
+                         int nt, int* nt_out) {
     if (m < w) return false;
     w = compiled_width(w);
     if (w == 0) return false;
     int cmax = cluster_limit<T>();
     if (max_c > 0) cmax = std::min(cmax, max_c);
     if (cmax <= 0) return false;
+    // the 512-thread leaf exists only as the pushed-message kernel (FP32)
+    if (nt != kNT && (leaf_mode() != 2 || lu_pf_push_smem((int)sizeof(T), w, 1, nt) == 0)) nt = kNT;
     const int rqs[4] = {1, 2, 4, 8};
     for (int rq : rqs) {
-        if (!LeafTable<T>::get(w, rq, false)) continue;
-        const int64_t R = (int64_t)kNT * rq;
+        const size_t push = lu_pf_push_smem((int)sizeof(T), w, rq, nt);
+        if (nt == kNT ? !LeafTable<T>::get(w, rq, false) : push == 0) continue;
+        const int64_t R = (int64_t)nt * rq;
         const int64_t C = lu_cdiv(m, R);
         if (C > cmax) continue;
-        const size_t smem = std::max(cluster_smem<T>(w, rq), lu_pf_push_smem((int)sizeof(T), w, rq));
+        const size_t smem = nt == kNT ? std::max(cluster_smem<T>(w, rq), push) : push;
         if (smem > budget) return false;
         int Cp = 1;
         while (Cp < C) Cp <<= 1;  // power-of-two cluster sizes
@@ -395,6 +401,7 @@ bool lu_pf_cluster_shape(int64_t m, int w, size_t budget, int* C_out, int* R_out
         *C_out = Cp;
         *R_out = (int)R;
         *smem_out = smem;
+        if (nt_out) *nt_out = nt;
         return true;
     }
     return false;
@@ -418,12 +425,12 @@ bool lu_pf_leaf_pairs_supported() { return leaf_mode() == 2; }
 template <typename T>
 int lu_launch_pf_leaf_cluster(cudaStream_t st, T* A, int64_t lda, int64_t m, int w, int C, int R, size_t smem,
                               int64_t left_cols, int64_t right_cols, int32_t* ipiv, int64_t ipiv_add, LuSync* sync,
-                              int sib, int kprev) {
+                              int sib, int kprev, int nt) {
     const int mode = leaf_mode();
     if (mode == 2)
         return lu_launch_pf_leaf_push<T>(st, A, lda, m, w, compiled_width(w), C, R, left_cols, right_cols, ipiv,
-                                         ipiv_add, sync, sib, kprev);
-    if (sib != 0 || kprev != 0) return LU_ERR_UNSUPPORTED;
+                                         ipiv_add, sync, sib, kprev, nt);
+    if (sib != 0 || kprev != 0 || nt != kNT) return LU_ERR_UNSUPPORTED;
     const int hw = mode;
     auto fn = LeafTable<T>::get(compiled_width(w), R / kNT, hw != 0);
     if (!fn) return LU_ERR_UNSUPPORTED;
@@ -450,9 +457,9 @@ int lu_launch_pf_leaf_cluster(cudaStream_t st, T* A, int64_t lda, int64_t m, int
     return LU_SUCCESS;
 }
 
-template bool lu_pf_cluster_shape<double>(int64_t, int, size_t, int*, int*, size_t*, int);
-template bool lu_pf_cluster_shape<float>(int64_t, int, size_t, int*, int*, size_t*, int);
+template bool lu_pf_cluster_shape<double>(int64_t, int, size_t, int*, int*, size_t*, int, int, int*);
+template bool lu_pf_cluster_shape<float>(int64_t, int, size_t, int*, int*, size_t*, int, int, int*);
 template int lu_launch_pf_leaf_cluster<double>(cudaStream_t, double*, int64_t, int64_t, int, int, int, size_t, int64_t,
-                                               int64_t, int32_t*, int64_t, LuSync*, int, int);
+                                               int64_t, int32_t*, int64_t, LuSync*, int, int, int);
 template int lu_launch_pf_leaf_cluster<float>(cudaStream_t, float*, int64_t, int64_t, int, int, int, size_t, int64_t,
-                                              int64_t, int32_t*, int64_t, LuSync*, int, int);
+                                              int64_t, int32_t*, int64_t, LuSync*, int, int, int);

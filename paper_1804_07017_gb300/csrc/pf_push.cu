@@ -163,13 +163,13 @@ __device__ __forceinline__ void leaf_wait(uint32_t bar, uint32_t parity, LuSync*
     }
 }
 
-template <typename T, int W, int RQ>
+template <typename T, int W, int RQ, int NT>
 struct PushSmem {
     static constexpr int SB = sub_block<T, RQ>();
     static constexpr size_t msg = 2ull * kMaxC * MsgLayout<T, W>::bytes;
     static constexpr size_t jrow = 2ull * W * sizeof(T);
     static constexpr size_t su = (size_t)SB * W * sizeof(T);
-    static constexpr size_t block = (size_t)kPT * RQ * (W + 1) * sizeof(T);
+    static constexpr size_t block = (size_t)NT * RQ * (W + 1) * sizeof(T);
     static constexpr size_t total = msg + jrow + su + block + 16;
 };
 
@@ -180,13 +180,13 @@ struct PushSmem {
 // sU (kprev x (W+1)); the same k-ordered FMA accumulation followed by one
 // subtraction as the separate update kernel.  Kept out of line so that its
 // registers do not add to the column loop's.
-template <typename T, int W, int RQ>
+template <typename T, int W, int RQ, int NT>
 __device__ __noinline__ void leaf_prologue(const T* __restrict__ A, int64_t lda, int row0, int nrows, int w,
                                            int kprev, T* __restrict__ sA, const T* __restrict__ sU) {
     constexpr int WP = W + 1;
 #pragma unroll 1
     for (int q = 0; q < RQ; ++q) {
-        const int r = threadIdx.x + kPT * q;
+        const int r = threadIdx.x + NT * q;
         if (r >= nrows) continue;
         T l[kMaxPrev];
 #pragma unroll
@@ -203,15 +203,15 @@ __device__ __noinline__ void leaf_prologue(const T* __restrict__ A, int64_t lda,
     }
 }
 
-template <typename T, int W, int RQ>
+template <typename T, int W, int RQ, int NT>
 __global__ void __maxnreg__(LU_PF_PUSH_MAXREG)
     pf_leaf_push_kernel(T* __restrict__ A, int64_t lda, int m, int w, int left_cols, int right_cols,
                         int32_t* __restrict__ ipiv, int ipiv_add, LuSync* __restrict__ sync, int sib, int kprev) {
     typedef PivKey<T> PK;
     typedef typename PK::K K;
     typedef MsgLayout<T, W> ML;
-    constexpr int SB = PushSmem<T, W, RQ>::SB;
-    constexpr int R = kPT * RQ;
+    constexpr int SB = PushSmem<T, W, RQ, NT>::SB;
+    constexpr int R = NT * RQ;
     constexpr int WP = W + 1;
     constexpr int UCH = (int)(SB * W * sizeof(T) / 16);
     static_assert(W % SB == 0 && W <= 32 && (W * sizeof(T)) % 16 == 0, "leaf shape");
@@ -219,12 +219,12 @@ __global__ void __maxnreg__(LU_PF_PUSH_MAXREG)
     cg::cluster_group cluster = cg::this_cluster();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     unsigned char* msg = smem_raw;                                                   // [2][kMaxC][ML::bytes]
-    T* jrow = reinterpret_cast<T*>(smem_raw + PushSmem<T, W, RQ>::msg);              // [2][W]
+    T* jrow = reinterpret_cast<T*>(smem_raw + PushSmem<T, W, RQ, NT>::msg);              // [2][W]
     T* su = jrow + 2 * W;                                                            // [SB][W]
     T* sA = su + SB * W;                                                             // [R][WP]
     __shared__ __align__(8) uint64_t bars[3];
-    __shared__ K red_k[kPT / 32];
-    __shared__ int red_i[kPT / 32];
+    __shared__ K red_k[NT / 32];
+    __shared__ int red_i[NT / 32];
     __shared__ int s_piv[W];
     __shared__ int s_info;
     __shared__ int s_dst[2 * W], s_src[2 * W], s_cnt;
@@ -254,7 +254,7 @@ __global__ void __maxnreg__(LU_PF_PUSH_MAXREG)
     for (int c = 0; c < W; ++c)
 #pragma unroll
         for (int q = 0; q < RQ; ++q) {
-            const int r = tid + kPT * q;
+            const int r = tid + NT * q;
             if (r < nrows) {
                 if (c < w)
                     cp_async_elem<T>(sA + r * WP + c, A + (int64_t)(row0 + r) + (int64_t)c * lda);
@@ -264,14 +264,14 @@ __global__ void __maxnreg__(LU_PF_PUSH_MAXREG)
         }
     asm volatile("cp.async.commit_group;\n\tcp.async.wait_all;" ::: "memory");
     // U12 of the preceding sibling leaf: rows -kprev..-1 of this leaf's columns
-    for (int e = tid; e < kprev * w; e += kPT) {
+    for (int e = tid; e < kprev * w; e += NT) {
         const int k = e % kprev, c = e / kprev;
         sU0[k][c] = A[(int64_t)(k - kprev) + (int64_t)c * lda];
     }
     // every CTA's barriers are initialised before anyone pushes
     cluster.sync();
     if (kprev > 0) {
-        leaf_prologue<T, W, RQ>(A, lda, row0, nrows, w, kprev, sA, &sU0[0][0]);
+        leaf_prologue<T, W, RQ, NT>(A, lda, row0, nrows, w, kprev, sA, &sU0[0][0]);
         __syncthreads();
     }
 
@@ -285,24 +285,24 @@ __global__ void __maxnreg__(LU_PF_PUSH_MAXREG)
             red_i[warp] = bi;
         }
         __syncthreads();
-        K ck = (lane < kPT / 32) ? red_k[lane] : K(0);
-        int ci = (lane < kPT / 32) ? red_i[lane] : INT_MAX;
+        K ck = (lane < NT / 32) ? red_k[lane] : K(0);
+        int ci = (lane < NT / 32) ? red_i[lane] : INT_MAX;
         PK::warp_best(ck, ci);
         const int buf = jj & 1;
         const int lc = (ci != INT_MAX) ? ci - row0 : -1;
         const int lj = jj - row0;
         const bool own_j = jj >= row0 && jj < row0 + nrows;
         // the owners put their register columns into the shared-memory rows
-        if (lc >= 0 && tid == lc % kPT) {
-            const int oq = lc / kPT;
+        if (lc >= 0 && tid == lc % NT) {
+            const int oq = lc / NT;
 #pragma unroll
             for (int q = 0; q < RQ; ++q)
                 if (q == oq)
 #pragma unroll
                     for (int k = 0; k < SB; ++k) sA[lc * WP + c0 + k] = v[q][k];
         }
-        if (own_j && tid == lj % kPT) {
-            const int oq = lj / kPT;
+        if (own_j && tid == lj % NT) {
+            const int oq = lj / NT;
 #pragma unroll
             for (int q = 0; q < RQ; ++q)
                 if (q == oq)
@@ -316,7 +316,7 @@ __global__ void __maxnreg__(LU_PF_PUSH_MAXREG)
             const T* rp = sA + (lc >= 0 ? lc : 0) * WP;
             const uint32_t base = smem_u32(msg) + (uint32_t)((buf * kMaxC + g) * ML::bytes);
             // row chunks carry 4 row words; the last chunk holds the key and the row index
-            for (int t = tid; t < C * ML::chunks; t += kPT) {
+            for (int t = tid; t < C * ML::chunks; t += NT) {
                 const int dst = t / ML::chunks, ch = t % ML::chunks;
                 uint32_t x0, x1, x2, x3;
                 if (ch < ML::jchunks) {
@@ -340,7 +340,7 @@ __global__ void __maxnreg__(LU_PF_PUSH_MAXREG)
         if (own_j) {
             const T* rp = sA + lj * WP;
             const uint32_t base = smem_u32(jrow + buf * W);
-            for (int t = tid; t < C * ML::jchunks; t += kPT) {
+            for (int t = tid; t < C * ML::jchunks; t += NT) {
                 const int dst = t / ML::jchunks, ch = t % ML::jchunks;
                 push16(base + 16 * ch, bar0 + 8 * buf, dst, elem_word<T>(rp, 4 * ch), elem_word<T>(rp, 4 * ch + 1),
                        elem_word<T>(rp, 4 * ch + 2), elem_word<T>(rp, 4 * ch + 3));
@@ -354,7 +354,7 @@ __global__ void __maxnreg__(LU_PF_PUSH_MAXREG)
         int bi = INT_MAX;
 #pragma unroll
         for (int q = 0; q < RQ; ++q) {
-            const int r = tid + kPT * q;
+            const int r = tid + NT * q;
 #pragma unroll
             for (int k = 0; k < SB; ++k) v[q][k] = (r < nrows) ? sA[r * WP + c0 + k] : T(0);
             if (r < nrows && row0 + r >= c0) {
@@ -395,10 +395,10 @@ __global__ void __maxnreg__(LU_PF_PUSH_MAXREG)
                         const T* src = side ? jr : pr;
                         if (pos >= row0 && pos < row0 + nrows) {
                             const int lr = pos - row0;
-                            if (warp == (lr % kPT) >> 5 && lane < w && (lane < c0 || lane >= c0 + SB))
+                            if (warp == (lr % NT) >> 5 && lane < w && (lane < c0 || lane >= c0 + SB))
                                 sA[lr * WP + lane] = src[lane];
-                            if (tid == lr % kPT) {
-                                const int oq = lr / kPT;
+                            if (tid == lr % NT) {
+                                const int oq = lr / NT;
 #pragma unroll
                                 for (int q = 0; q < RQ; ++q)
                                     if (q == oq)
@@ -421,7 +421,7 @@ __global__ void __maxnreg__(LU_PF_PUSH_MAXREG)
                 bi = INT_MAX;
 #pragma unroll
                 for (int q = 0; q < RQ; ++q) {
-                    const int r = tid + kPT * q;
+                    const int r = tid + NT * q;
                     const int gr = row0 + r;
                     if (r < nrows && gr > jj) {
                         if (piv != T(0)) {
@@ -444,7 +444,7 @@ __global__ void __maxnreg__(LU_PF_PUSH_MAXREG)
         }
 #pragma unroll
         for (int q = 0; q < RQ; ++q) {
-            const int r = tid + kPT * q;
+            const int r = tid + NT * q;
             if (r < nrows)
 #pragma unroll
                 for (int k = 0; k < SB; ++k) sA[r * WP + c0 + k] = v[q][k];
@@ -465,7 +465,7 @@ __global__ void __maxnreg__(LU_PF_PUSH_MAXREG)
                 }
                 __syncthreads();
                 const uint32_t base = smem_u32(su);
-                for (int t = tid; t < C * UCH; t += kPT) {
+                for (int t = tid; t < C * UCH; t += NT) {
                     const int dst = t / UCH, ch = t % UCH;
                     uint32_t x[4];
 #pragma unroll
@@ -490,7 +490,7 @@ __global__ void __maxnreg__(LU_PF_PUSH_MAXREG)
                 T a[RQ][4];
 #pragma unroll
                 for (int q = 0; q < RQ; ++q) {
-                    const int r = tid + kPT * q;
+                    const int r = tid + NT * q;
 #pragma unroll
                     for (int cc = 0; cc < 4; ++cc) a[q][cc] = sA[r * WP + cb + cc];
                 }
@@ -506,7 +506,7 @@ __global__ void __maxnreg__(LU_PF_PUSH_MAXREG)
                 }
 #pragma unroll
                 for (int q = 0; q < RQ; ++q) {
-                    const int r = tid + kPT * q;
+                    const int r = tid + NT * q;
                     if (r < nrows && row0 + r >= c0 + SB)
 #pragma unroll
                         for (int cc = 0; cc < 4; ++cc)
@@ -523,11 +523,11 @@ __global__ void __maxnreg__(LU_PF_PUSH_MAXREG)
     for (int c = 0; c < w; ++c)
 #pragma unroll
         for (int q = 0; q < RQ; ++q) {
-            const int r = tid + kPT * q;
+            const int r = tid + NT * q;
             if (r < nrows) A[(int64_t)(row0 + r) + (int64_t)c * lda] = sA[r * WP + c];
         }
     if (g == 0) {
-        for (int j = tid; j < w; j += kPT) ipiv[j] = s_piv[j] + 1 + ipiv_add;
+        for (int j = tid; j < w; j += NT) ipiv[j] = s_piv[j] + 1 + ipiv_add;
         if (tid == 0 && s_info != 0) atomicCAS(&sync->info, 0, s_info + ipiv_add);
     }
     const int other = left_cols + right_cols;
@@ -587,7 +587,7 @@ __global__ void __maxnreg__(LU_PF_PUSH_MAXREG)
         // makes them the sibling's U12; the sibling folds the matching update into
         // its prologue.
         if (g == 0) {
-            for (int t = warp; t < sib; t += kPT / 32) {
+            for (int t = warp; t < sib; t += NT / 32) {
                 T* a = A + (int64_t)(w + t) * lda;
                 T vv[(2 * W + 31) / 32];
 #pragma unroll
@@ -607,7 +607,7 @@ __global__ void __maxnreg__(LU_PF_PUSH_MAXREG)
             }
         }
         // columns q = g, g + C, ... of the other columns; one warp per column
-        for (int q = g * (kPT / 32) + warp; cnt > 0 && q < other; q += C * (kPT / 32)) {
+        for (int q = g * (NT / 32) + warp; cnt > 0 && q < other; q += C * (NT / 32)) {
             if (q >= left_cols && q < left_cols + sib) continue;
             const int64_t col = (q < left_cols) ? (int64_t)q - left_cols : (int64_t)w + (q - left_cols);
             T* a = A + col * lda;
@@ -627,15 +627,21 @@ __global__ void __maxnreg__(LU_PF_PUSH_MAXREG)
 template <typename T>
 struct PushTable {
     typedef void (*Fn)(T*, int64_t, int, int, int, int, int32_t*, int, LuSync*, int, int);
-    static Fn get(int w, int rq, size_t* smem) {
-#define LU_PUSH_CASE(WW, RR)                                        \
-    if (w == WW && rq == RR) {                                      \
-        if (smem) *smem = PushSmem<T, WW, RR>::total;               \
-        return pf_leaf_push_kernel<T, WW, RR>;                      \
+    static Fn get(int w, int rq, int nt, size_t* smem) {
+#define LU_PUSH_CASE(WW, RR, NN)                                    \
+    if (w == WW && rq == RR && nt == NN) {                          \
+        if (smem) *smem = PushSmem<T, WW, RR, NN>::total;           \
+        return pf_leaf_push_kernel<T, WW, RR, NN>;                  \
     }
-        LU_PUSH_CASE(8, 1) LU_PUSH_CASE(8, 2) LU_PUSH_CASE(8, 4) LU_PUSH_CASE(8, 8)
-        LU_PUSH_CASE(16, 1) LU_PUSH_CASE(16, 2) LU_PUSH_CASE(16, 4) LU_PUSH_CASE(16, 8)
-        LU_PUSH_CASE(32, 1) LU_PUSH_CASE(32, 2) LU_PUSH_CASE(32, 4)
+        LU_PUSH_CASE(8, 1, 256) LU_PUSH_CASE(8, 2, 256) LU_PUSH_CASE(8, 4, 256) LU_PUSH_CASE(8, 8, 256)
+        LU_PUSH_CASE(16, 1, 256) LU_PUSH_CASE(16, 2, 256) LU_PUSH_CASE(16, 4, 256) LU_PUSH_CASE(16, 8, 256)
+        LU_PUSH_CASE(32, 1, 256) LU_PUSH_CASE(32, 2, 256) LU_PUSH_CASE(32, 4, 256)
+        // 512 threads (FP32, leaves on SMs of their own): half the rows per thread
+        if constexpr (sizeof(T) == 4) {
+            LU_PUSH_CASE(8, 1, 512) LU_PUSH_CASE(8, 2, 512) LU_PUSH_CASE(8, 4, 512)
+            LU_PUSH_CASE(16, 1, 512) LU_PUSH_CASE(16, 2, 512) LU_PUSH_CASE(16, 4, 512)
+            LU_PUSH_CASE(32, 1, 512) LU_PUSH_CASE(32, 2, 512)
+        }
 #undef LU_PUSH_CASE
         return nullptr;
     }
@@ -644,27 +650,27 @@ struct PushTable {
 }  // namespace
 
 // Dynamic shared memory of the pushed-message leaf (0 if the shape is not compiled).
-size_t lu_pf_push_smem(int esize, int w, int rq) {
+size_t lu_pf_push_smem(int esize, int w, int rq, int nt) {
     size_t s = 0;
     if (esize == 8)
-        PushTable<double>::get(w, rq, &s);
+        PushTable<double>::get(w, rq, nt, &s);
     else
-        PushTable<float>::get(w, rq, &s);
+        PushTable<float>::get(w, rq, nt, &s);
     return s;
 }
 
 template <typename T>
 int lu_launch_pf_leaf_push(cudaStream_t st, T* A, int64_t lda, int64_t m, int w, int wc, int C, int R,
                            int64_t left_cols, int64_t right_cols, int32_t* ipiv, int64_t ipiv_add, LuSync* sync,
-                           int sib, int kprev) {
+                           int sib, int kprev, int nt) {
     size_t smem = 0;
-    auto fn = PushTable<T>::get(wc, R / kPT, &smem);
+    auto fn = (nt > 0 && R % nt == 0) ? PushTable<T>::get(wc, R / nt, nt, &smem) : nullptr;
     if (!fn || C > kMaxC || sib < 0 || sib > wc || sib > right_cols || kprev < 0 || kprev > kMaxPrev)
         return LU_ERR_UNSUPPORTED;
     LU_TRY(lu_func_smem(fn, (int)smem, true));
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(C, 1, 1);
-    cfg.blockDim = dim3(kPT, 1, 1);
+    cfg.blockDim = dim3(nt, 1, 1);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = st;
     cudaLaunchAttribute attr[1];
@@ -677,8 +683,9 @@ int lu_launch_pf_leaf_push(cudaStream_t st, T* A, int64_t lda, int64_t m, int w,
     LuProfScope prof(st, LU_K_PANEL, 2.0 * m * w * sizeof(T) + 4.0 * w * (left_cols + right_cols) * sizeof(T),
                      (double)m * w * w);
     if (getenv("LU_GB300_TRACE_LAUNCH"))
-        fprintf(stderr, "[lu launch] push leaf esize %d m %lld w %d (compiled %d) C %d R %d smem %zu left %lld right %lld\n",
-                (int)sizeof(T), (long long)m, w, wc, C, R, smem, (long long)left_cols, (long long)right_cols);
+        fprintf(stderr, "[lu launch] push leaf esize %d m %lld w %d (compiled %d) C %d R %d threads %d smem %zu left %lld "
+                "right %lld\n", (int)sizeof(T), (long long)m, w, wc, C, R, nt, smem, (long long)left_cols,
+                (long long)right_cols);
     LU_CHECK_CUDA(cudaLaunchKernelEx(&cfg, fn, A, lda, (int)m, w, (int)left_cols, (int)right_cols, ipiv, (int)ipiv_add,
                                      sync, sib, kprev));
     lu_count_launch();
@@ -686,6 +693,6 @@ int lu_launch_pf_leaf_push(cudaStream_t st, T* A, int64_t lda, int64_t m, int w,
 }
 
 template int lu_launch_pf_leaf_push<double>(cudaStream_t, double*, int64_t, int64_t, int, int, int, int, int64_t,
-                                            int64_t, int32_t*, int64_t, LuSync*, int, int);
+                                            int64_t, int32_t*, int64_t, LuSync*, int, int, int);
 template int lu_launch_pf_leaf_push<float>(cudaStream_t, float*, int64_t, int64_t, int, int, int, int, int64_t,
-                                           int64_t, int32_t*, int64_t, LuSync*, int, int);
+                                           int64_t, int32_t*, int64_t, LuSync*, int, int, int);
