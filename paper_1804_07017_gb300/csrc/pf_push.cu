@@ -39,8 +39,9 @@ namespace cg = cooperative_groups;
 
 namespace {
 
-constexpr int kPT = 256;                     // threads per CTA
-// Registers per thread: 256 x 72 beside a 320 x 144 tensor-core update CTA fills one SM's 64 K.
+// Threads per CTA: a template parameter NT (256 beside the tensor-core update, 512
+// where the leaf may fill an SM).  Registers per thread: 256 x 72 beside a 320 x 144
+// tensor-core update CTA fills one SM's 64 K.
 #ifndef LU_PF_PUSH_MAXREG
 #define LU_PF_PUSH_MAXREG 72
 #endif
@@ -533,49 +534,40 @@ __global__ void __maxnreg__(LU_PF_PUSH_MAXREG)
     const int other = left_cols + right_cols;
     if (other > 0) {
         // ---- the leaf's interchanges on the other columns of the panel ----
-        // Plan: positions 0..w-1 (leaf rows) and the distinct targets below them, the
-        // leaf's swaps composed in order by one warp: lane i holds the current source
-        // of leaf row i and of the i-th target slot; a target's slot is found by a
-        // ballot.  The moves are listed leaf rows first, then targets, in slot order.
+        // Plan: positions 0..w-1 (leaf rows) and the distinct targets below them.  After
+        // the leaf's interchanges in order, position x holds the row that
+        // sigma_0(sigma_1(...sigma_{w-1}(x))) held (sigma_k swaps k and s_piv[k]), so
+        // one warp follows every position's chain at once: lane i the leaf row i and,
+        // if interchange i is the first to reach its target below the leaf, that
+        // target.  The moves are listed leaf rows first, then targets in order of
+        // first occurrence.
         if (warp == 0) {
-            int cur_l = lane;         // source of leaf row `lane`
-            int tgt = -1, cur_t = -1;  // target slot `lane`: its row and its source
-            int nt = 0;
-            for (int k = 0; k < w; ++k) {
-                const int pk = s_piv[k];
-                if (pk == k) continue;
-                const int xk = __shfl_sync(0xffffffffu, cur_l, k);
-                if (pk < w) {
-                    const int xp = __shfl_sync(0xffffffffu, cur_l, pk);
-                    if (lane == k) cur_l = xp;
-                    if (lane == pk) cur_l = xk;
-                } else {
-                    const unsigned hit = __ballot_sync(0xffffffffu, tgt == pk);
-                    int f;
-                    if (hit) {
-                        f = __ffs(hit) - 1;
-                    } else {
-                        f = nt++;
-                        if (lane == f) tgt = cur_t = pk;
-                    }
-                    const int xf = __shfl_sync(0xffffffffu, cur_t, f);
-                    if (lane == k) cur_l = xf;
-                    if (lane == f) cur_t = xk;
+            auto chain = [&](int x) {
+                for (int q = w - 1; q >= 0; --q) {
+                    const int pq = s_piv[q];
+                    x = (x == q) ? pq : ((x == pq) ? q : x);
                 }
-            }
-            const bool mv_l = lane < w && cur_l != lane;
+                return x;
+            };
+            const int src_l = lane < w ? chain(lane) : lane;
+            const int pk = lane < w ? s_piv[lane] : -1;
+            const bool is_t = pk >= w;
+            const unsigned same = __match_any_sync(0xffffffffu, is_t ? pk : -1 - lane);
+            const bool first = is_t && (__ffs(same) - 1 == lane);
+            const int src_t = first ? chain(pk) : pk;
+            const bool mv_l = lane < w && src_l != lane;
+            const bool mv_t = first && src_t != pk;
             const unsigned bl = __ballot_sync(0xffffffffu, mv_l);
+            const unsigned bt = __ballot_sync(0xffffffffu, mv_t);
             const int nl = __popc(bl);
             const unsigned below = (1u << lane) - 1u;
             if (mv_l) {
                 s_dst[__popc(bl & below)] = lane;
-                s_src[__popc(bl & below)] = cur_l;
+                s_src[__popc(bl & below)] = src_l;
             }
-            const bool mv_t = lane < nt && cur_t != tgt;
-            const unsigned bt = __ballot_sync(0xffffffffu, mv_t);
             if (mv_t) {
-                s_dst[nl + __popc(bt & below)] = tgt;
-                s_src[nl + __popc(bt & below)] = cur_t;
+                s_dst[nl + __popc(bt & below)] = pk;
+                s_src[nl + __popc(bt & below)] = src_t;
             }
             if (lane == 0) s_cnt = nl + __popc(bt);
         }
