@@ -279,7 +279,7 @@ __global__ void __maxnreg__(LU_PF_PUSH_MAXREG)
     T v[RQ][SB];
 
     // CTA reduction of (key, row) and the pushes of column jj's messages.
-    auto publish = [&](int jj, int c0, K bk, int bi) {
+    auto publish = [&](int jj, int cr, int ce, K bk, int bi) {
         PK::warp_best(bk, bi);
         if (lane == 0) {
             red_k[warp] = bk;
@@ -293,14 +293,15 @@ __global__ void __maxnreg__(LU_PF_PUSH_MAXREG)
         const int lc = (ci != INT_MAX) ? ci - row0 : -1;
         const int lj = jj - row0;
         const bool own_j = jj >= row0 && jj < row0 + nrows;
-        // the owners put their register columns into the shared-memory rows
+        // the owners put their register columns (cr .. ce-1) into the shared-memory rows
         if (lc >= 0 && tid == lc % NT) {
             const int oq = lc / NT;
 #pragma unroll
             for (int q = 0; q < RQ; ++q)
                 if (q == oq)
 #pragma unroll
-                    for (int k = 0; k < SB; ++k) sA[lc * WP + c0 + k] = v[q][k];
+                    for (int k = 0; k < SB; ++k)
+                        if (cr + k < ce) sA[lc * WP + cr + k] = v[q][k];
         }
         if (own_j && tid == lj % NT) {
             const int oq = lj / NT;
@@ -308,7 +309,8 @@ __global__ void __maxnreg__(LU_PF_PUSH_MAXREG)
             for (int q = 0; q < RQ; ++q)
                 if (q == oq)
 #pragma unroll
-                    for (int k = 0; k < SB; ++k) sA[lj * WP + c0 + k] = v[q][k];
+                    for (int k = 0; k < SB; ++k)
+                        if (cr + k < ce) sA[lj * WP + cr + k] = v[q][k];
         }
         // the rows are complete in shared memory; every warp then takes a share of the
         // C x (chunks) pushes, so they leave in one or two rounds instead of one warp's five
@@ -351,6 +353,8 @@ __global__ void __maxnreg__(LU_PF_PUSH_MAXREG)
 
     for (int sb = 0; sb < nsb; ++sb) {
         const int c0 = sb * SB;
+        const int ce = c0 + SB;
+        const int nk = min(SB, w - c0);
         K bk = 0;
         int bi = INT_MAX;
 #pragma unroll
@@ -366,89 +370,91 @@ __global__ void __maxnreg__(LU_PF_PUSH_MAXREG)
                 }
             }
         }
-        publish(c0, c0, bk, bi);
-#pragma unroll
-        for (int k = 0; k < SB; ++k) {
+        publish(c0, c0, ce, bk, bi);
+        // The sub-block's columns one after another, in a loop that is not unrolled
+        // (one copy of its code, which the instruction cache holds): the current
+        // column is always v[.][0].  Once eliminated, a column is final in every row,
+        // so it goes back to shared memory and the register columns shift down by one.
+#pragma unroll 1
+        for (int k = 0; k < nk; ++k) {
             const int jj = c0 + k;
-            if (jj < w) {
-                const int buf = jj & 1;
-                leaf_wait(bar0 + 8 * buf, (uint32_t)((jj >> 1) & 1), sync, failed);
-                if (tid == 0 && jj + 2 < w) mbar_expect_cta(bar0 + 8 * buf, col_bytes);
-                // ---- pivot: first maximum over the C pushed candidates ----
-                K ck = 0;
-                int ci = INT_MAX;
-                if (lane < C) {
-                    const unsigned char* mp = msg + (buf * kMaxC + lane) * ML::bytes;
-                    ck = *reinterpret_cast<const K*>(mp + ML::key_off);
-                    ci = *reinterpret_cast<const int*>(mp + ML::idx_off);
-                    if (ck == 0) ci = INT_MAX;
-                }
-                PK::warp_best(ck, ci);
-                const int p = (ci == INT_MAX) ? jj : ci;
-                const T* jr = jrow + buf * W;
-                const T* pr = (ci == INT_MAX) ? jr : reinterpret_cast<const T*>(msg + (buf * kMaxC + ci / R) * ML::bytes);
-                if (tid == 0) s_piv[jj] = p;
-                // ---- interchange rows jj and p where this CTA holds them ----
-                if (p != jj) {
-#pragma unroll
-                    for (int side = 0; side < 2; ++side) {
-                        const int pos = side ? p : jj;
-                        const T* src = side ? jr : pr;
-                        if (pos >= row0 && pos < row0 + nrows) {
-                            const int lr = pos - row0;
-                            if (warp == (lr % NT) >> 5 && lane < w && (lane < c0 || lane >= c0 + SB))
-                                sA[lr * WP + lane] = src[lane];
-                            if (tid == lr % NT) {
-                                const int oq = lr / NT;
-#pragma unroll
-                                for (int q = 0; q < RQ; ++q)
-                                    if (q == oq)
-#pragma unroll
-                                        for (int kk = 0; kk < SB; ++kk) v[q][kk] = src[c0 + kk];
-                            }
-                        }
-                    }
-                }
-                const T piv = pr[jj];
-                if (piv == T(0) && tid == 0 && s_info == 0) s_info = jj + 1;
-                // multiply by the reciprocal when it is representable (as getf2), else divide
-                const bool use_rcp = fabs(piv) >= std::numeric_limits<T>::min();
-                const T rpiv = use_rcp ? T(1) / piv : T(0);
-                T prv[SB];
-#pragma unroll
-                for (int kk = k + 1; kk < SB; ++kk) prv[kk] = pr[c0 + kk];
-                // ---- scale column jj, rank-1 update of the register columns ----
-                bk = 0;
-                bi = INT_MAX;
-#pragma unroll
-                for (int q = 0; q < RQ; ++q) {
-                    const int r = tid + NT * q;
-                    const int gr = row0 + r;
-                    if (r < nrows && gr > jj) {
-                        if (piv != T(0)) {
-                            const T l = use_rcp ? v[q][k] * rpiv : v[q][k] / piv;
-                            v[q][k] = l;
-#pragma unroll
-                            for (int kk = k + 1; kk < SB; ++kk) v[q][kk] = fma(-l, prv[kk], v[q][kk]);
-                        }
-                        if (k + 1 < SB) {
-                            const K kk = PK::of(v[q][k + 1 < SB ? k + 1 : k]);
-                            if (kk > bk) {
-                                bk = kk;
-                                bi = gr;
-                            }
-                        }
-                    }
-                }
-                if (k + 1 < SB && jj + 1 < w) publish(jj + 1, c0, bk, bi);
+            const int left = SB - k;  // register columns still live: jj .. ce-1
+            const int buf = jj & 1;
+            leaf_wait(bar0 + 8 * buf, (uint32_t)((jj >> 1) & 1), sync, failed);
+            if (tid == 0 && jj + 2 < w) mbar_expect_cta(bar0 + 8 * buf, col_bytes);
+            // ---- pivot: first maximum over the C pushed candidates ----
+            K ck = 0;
+            int ci = INT_MAX;
+            if (lane < C) {
+                const unsigned char* mp = msg + (buf * kMaxC + lane) * ML::bytes;
+                ck = *reinterpret_cast<const K*>(mp + ML::key_off);
+                ci = *reinterpret_cast<const int*>(mp + ML::idx_off);
+                if (ck == 0) ci = INT_MAX;
             }
-        }
+            PK::warp_best(ck, ci);
+            const int p = (ci == INT_MAX) ? jj : ci;
+            const T* jr = jrow + buf * W;
+            const T* pr = (ci == INT_MAX) ? jr : reinterpret_cast<const T*>(msg + (buf * kMaxC + ci / R) * ML::bytes);
+            if (tid == 0) s_piv[jj] = p;
+            // ---- interchange rows jj and p where this CTA holds them ----
+            if (p != jj) {
 #pragma unroll
-        for (int q = 0; q < RQ; ++q) {
-            const int r = tid + NT * q;
-            if (r < nrows)
+                for (int side = 0; side < 2; ++side) {
+                    const int pos = side ? p : jj;
+                    const T* src = side ? jr : pr;
+                    if (pos >= row0 && pos < row0 + nrows) {
+                        const int lr = pos - row0;
+                        if (warp == (lr % NT) >> 5 && lane < w && (lane < jj || lane >= ce))
+                            sA[lr * WP + lane] = src[lane];
+                        if (tid == lr % NT) {
+                            const int oq = lr / NT;
 #pragma unroll
-                for (int k = 0; k < SB; ++k) sA[r * WP + c0 + k] = v[q][k];
+                            for (int q = 0; q < RQ; ++q)
+                                if (q == oq)
+#pragma unroll
+                                    for (int kk = 0; kk < SB; ++kk)
+                                        if (kk < left) v[q][kk] = src[jj + kk];
+                        }
+                    }
+                }
+            }
+            const T piv = pr[jj];
+            if (piv == T(0) && tid == 0 && s_info == 0) s_info = jj + 1;
+            // multiply by the reciprocal when it is representable (as getf2), else divide
+            const bool use_rcp = fabs(piv) >= std::numeric_limits<T>::min();
+            const T rpiv = use_rcp ? T(1) / piv : T(0);
+            T prv[SB];
+#pragma unroll
+            for (int kk = 1; kk < SB; ++kk) prv[kk] = (kk < left) ? pr[jj + kk] : T(0);
+            // ---- scale column jj, rank-1 update of the register columns ----
+            bk = 0;
+            bi = INT_MAX;
+#pragma unroll
+            for (int q = 0; q < RQ; ++q) {
+                const int r = tid + NT * q;
+                const int gr = row0 + r;
+                if (r < nrows) {
+                    if (gr > jj && piv != T(0)) {
+                        const T l = use_rcp ? v[q][0] * rpiv : v[q][0] / piv;
+                        v[q][0] = l;
+#pragma unroll
+                        for (int kk = 1; kk < SB; ++kk)
+                            if (kk < left) v[q][kk] = fma(-l, prv[kk], v[q][kk]);
+                    }
+                    // column jj is final in this row: back to shared memory, shift down
+                    sA[r * WP + jj] = v[q][0];
+#pragma unroll
+                    for (int kk = 0; kk + 1 < SB; ++kk) v[q][kk] = v[q][kk + 1];
+                    if (gr > jj && k + 1 < nk) {
+                        const K kk = PK::of(v[q][0]);
+                        if (kk > bk) {
+                            bk = kk;
+                            bi = gr;
+                        }
+                    }
+                }
+            }
+            if (k + 1 < nk) publish(jj + 1, jj + 1, ce, bk, bi);
         }
         if (c0 + SB < w) {
             __syncthreads();
@@ -482,6 +488,13 @@ __global__ void __maxnreg__(LU_PF_PUSH_MAXREG)
             leaf_wait(bar0 + 16, (uint32_t)(sb & 1), sync, failed);
             if (tid == 0 && c0 + 2 * SB < w) mbar_expect_cta(bar0 + 16, u_bytes);
             // ---- rank-SB update of the remaining leaf columns: A22 -= L21 U12 ----
+            // The multipliers L21 of this thread's rows, from shared memory (it wrote them).
+#pragma unroll
+            for (int q = 0; q < RQ; ++q) {
+                const int r = tid + NT * q;
+#pragma unroll
+                for (int kk = 0; kk < SB; ++kk) v[q][kk] = (r < nrows) ? sA[r * WP + c0 + kk] : T(0);
+            }
             // Four columns at a time, so that each thread has RQ x 4 independent
             // multiply-add chains in flight (two warps per scheduler cannot hide
             // the latency of one chain per row); every element still takes its SB
