@@ -359,8 +359,10 @@ def main_with_args(argv):
         # latency view: the leaves' time per eliminated column (every column passes one leaf)
         roof["latency"] = {"us_per_column": d["ms"] * PROF_STRIDE / args.steps / n * 1e3,
                            "columns_per_step": n,
-                           "note": "pipelined, beside the tensor-core update; a leaf timed alone "
-                                   "(--workload profile --case leaf) takes 2.8 us per column at m = 16384"}
+                           "note": "pipelined: the leaves run on their own SMs (--pf-sms) or beside the "
+                                   "tensor-core update (--pf-sms 0); a 32-column leaf at m = 16384 takes 1.9 us "
+                                   "per column of kernel time alone (ncu), 2.6 us per column event-timed with "
+                                   "its launch (--workload profile --case leaf --shape 16384,32)"}
     roof["sampled"] = (f"1 launch in {PROF_STRIDE} of the class carries events, over {args.steps} timed steps "
                        f"of the same workload run after the value's timed region ({roof_ms_step:.1f} ms per step "
                        f"there: launches that carry events are not replayed as a graph)")
