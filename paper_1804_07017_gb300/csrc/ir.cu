@@ -80,18 +80,21 @@ __device__ __forceinline__ double block_max(double v, double* sh) {
     return v;  // valid in thread 0
 }
 
-// out[0] = max_i sum_q partial[q * n + i]   (||A||_inf from row-sum partials)
-__global__ void __launch_bounds__(1024) norm_finish_kernel(int64_t n, int nchunks, const double* __restrict__ partial,
-                                                           double* __restrict__ out) {
+// out = max_i sum_q partial[q * n + i]   (||A||_inf from row-sum partials), as the
+// bits of a non-negative double (whose integer order is its numeric order): each CTA
+// sums its rows' partials in chunk order and takes the maximum, then an atomic max.
+// *out_bits must be zero before the launch.
+__global__ void __launch_bounds__(256) norm_finish_kernel(int64_t n, int nchunks, const double* __restrict__ partial,
+                                                          unsigned long long* __restrict__ out_bits) {
     __shared__ double sh[32];
     double best = 0.0;
-    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         double s = 0.0;
         for (int q = 0; q < nchunks; ++q) s += partial[(int64_t)q * n + i];
         best = (s > best || s != s) ? s : best;
     }
     best = block_max(best, sh);
-    if (threadIdx.x == 0) out[0] = best;
+    if (threadIdx.x == 0) atomicMax(out_bits, (unsigned long long)__double_as_longlong(best));
 }
 
 // eta per rhs column (one CTA per column), then out_eta[0] = max over columns.
@@ -196,7 +199,9 @@ int lu_launch_norm_inf(cudaStream_t st, int64_t n, const double* A, int64_t lda,
     }
     LU_CHECK_LAUNCH();
     LuProfScope prof(st, LU_K_RESIDUAL, 8.0 * nch * n, 0.0);
-    norm_finish_kernel<<<1, 1024, 0, st>>>(n, nch, partial, out);
+    LU_CHECK_CUDA(cudaMemsetAsync(out, 0, sizeof(double), st));
+    norm_finish_kernel<<<(unsigned)std::min<int64_t>(lu_cdiv(n, 256), 1024), 256, 0, st>>>(
+        n, nch, partial, reinterpret_cast<unsigned long long*>(out));
     LU_CHECK_LAUNCH();
     return LU_SUCCESS;
 }

@@ -22,25 +22,50 @@
 
 namespace {
 
-// The interchanges are sequential, so one lane applies them to the row order
-// held in shared memory while the warp prefetches the next 32 pivots.
+// The row order held in shared memory, updated 32 interchanges at a time by one
+// warp: after interchanges k0 .. k0+31 in order, position x holds the entry that
+// sigma_k0(sigma_k0+1(...sigma_k0+31(x))) held (sigma_k swaps k and ipiv[k]), so
+// lane i follows that chain for position k0+i and, when interchange k0+i is the
+// first of the 32 to reach its target below them, for that target; the warp
+// then gathers all those positions at once.  The result equals applying the
+// interchanges one by one.
 __global__ void perm_from_ipiv_smem_kernel(int n, const int32_t* __restrict__ ipiv, int32_t* __restrict__ perm) {
     extern __shared__ int32_t order[];  // [n]
     for (int i = threadIdx.x; i < n; i += blockDim.x) order[i] = i;
     __syncthreads();
     if (threadIdx.x < 32) {
         const int lane = threadIdx.x;
+        // the pivots of the next two chunks are loaded ahead, so their latency overlaps
+        // the current chunk's work
+        int pa = (lane < n) ? ipiv[lane] - 1 : 0;
+        int pb = (32 + lane < n) ? ipiv[32 + lane] - 1 : 0;
         for (int k0 = 0; k0 < n; k0 += 32) {
-            const int pv = (k0 + lane < n) ? ipiv[k0 + lane] - 1 : 0;
             const int cnt = min(32, n - k0);
-            for (int t = 0; t < cnt; ++t) {
-                const int p = __shfl_sync(0xffffffffu, pv, t);
-                if (lane == 0) {
-                    const int a = order[k0 + t];
-                    order[k0 + t] = order[p];
-                    order[p] = a;
-                }
+            const int pcur = pa;
+            pa = pb;
+            pb = (k0 + 64 + lane < n) ? ipiv[k0 + 64 + lane] - 1 : 0;
+            // past the last pivot, interchange k0+i with itself (no move)
+            const int pv = (lane < cnt) ? pcur : k0 + lane;
+            const int xr = k0 + lane;
+            const bool is_t = lane < cnt && pv >= k0 + cnt;
+            const unsigned same = __match_any_sync(0xffffffffu, is_t ? pv : -1 - lane);
+            const bool first = is_t && (__ffs(same) - 1 == lane);
+            // both chains at once, all 32 steps unrolled (the pivots come by shuffles that
+            // do not depend on the chains)
+            int src_r = xr, src_t = first ? pv : xr;
+#pragma unroll
+            for (int q = 31; q >= 0; --q) {
+                const int pq = __shfl_sync(0xffffffffu, pv, q);
+                const int b = k0 + q;
+                src_r = (src_r == b) ? pq : ((src_r == pq) ? b : src_r);
+                src_t = (src_t == b) ? pq : ((src_t == pq) ? b : src_t);
             }
+            const int v_r = (lane < cnt) ? order[src_r] : 0;
+            const int v_t = first ? order[src_t] : 0;
+            __syncwarp();
+            if (lane < cnt) order[xr] = v_r;
+            if (first) order[pv] = v_t;
+            __syncwarp();
         }
     }
     __syncthreads();
