@@ -857,8 +857,9 @@ def run_configs(args):
     c2  n = 16384, nb = 256: the mixed solver with each trailing-update precision
         (N(0,1), one rhs), then bf16x6 on the row-scaled matrix and with 16 rhs;
     c3  n = 32768, nb = 256, A = diag(10^u) G: bf16x6 and e4m3 updates.
-    c2 and c3 run with the panel leaves on an SM partition of --pf-sms SMs, as
-    the default bench does.  For c2 (N(0,1), one rhs) and c3 each variant also reports
+    The tensor-core variants of c2 and c3 run with the panel leaves on an SM
+    partition of --pf-sms SMs, as the default bench does (FP32 and FP64 updates
+    on the CUDA cores keep every SM).  For c2 (N(0,1), one rhs) and c3 each variant also reports
     ||x - x_oracle||_inf / ||x_oracle||_inf against the CPU oracle's FP64
     solution stored by tests/golden/make_reference_solutions.py.
     Each configuration runs twice untimed, then once timed with CUDA events."""
@@ -920,11 +921,14 @@ def run_configs(args):
         res = {}
         for name in precs:
             code = {"bf16": 0, "fp16": 1, "fp8": 2, "f32": 3, "bf16x3": 4, "f64": 5, "bf16x6": 6}[name]
+            # the leaf partition pays off beside the fast tensor-core update; a CUDA-core
+            # update (FP32, FP64) needs every SM
+            pf = 0 if name in ("f32", "f64") else args.pf_sms
             ms, (st, it, eta) = timed(lambda: lu.lu_gesv_mixed(A, B, X, code, TOL, MAX_ITER,
-                                                                 lu.default_opts(nb=256, pf_sms=args.pf_sms)))
+                                                                 lu.default_opts(nb=256, pf_sms=pf)))
             res[f"{tag}{name}"] = {"ms": ms, "gflops": 2 * n ** 3 / 3 / ms / 1e6, "status": int(st),
                                    "refinements": int(it), "bwd_err": float(eta),
-                                   "converged": int(st) == 0, "pf_sms": args.pf_sms}
+                                   "converged": int(st) == 0, "pf_sms": pf}
             if ref is not None:
                 x_or, why = ref
                 if x_or is None:
