@@ -272,9 +272,11 @@ int panel_rec(lu_context* c, cudaStream_t st, T* A, int64_t lda, int64_t M, int6
     if (w1 >= width) w1 = width / 2;
     if (w1 < 1) w1 = 1;
     const int64_t w2 = width - w1;
-    // Two 16-column leaves: the first also forms its sibling's U12 and the second
-    // applies the matching rank-w1 update in its prologue (no launch in between).
-    if (cluster && w1 <= 16 && w2 <= 16 && w1 <= leaf && w2 <= leaf && lu_pf_leaf_pairs_supported()) {
+    // Two sibling leaves (16 columns, or 32 in FP32): the first also forms its sibling's
+    // U12 and the second applies the matching rank-w1 update in its prologue (no
+    // launch in between).
+    const int64_t pair_max = sizeof(T) == 4 ? 32 : 16;
+    if (cluster && w1 <= pair_max && w2 <= pair_max && w1 <= leaf && w2 <= leaf && lu_pf_leaf_pairs_supported()) {
         int Ca = 0, Ra = 0, Cb = 0, Rb = 0, nta = 256, ntb = 256;
         size_t sa = 0, sb = 0;
         if (lu_pf_cluster_shape<T>(rows, (int)w1, c->pf_smem_budget, &Ca, &Ra, &sa, o.pf_ctas, nt_want, &nta) &&

@@ -46,7 +46,7 @@ namespace {
 #define LU_PF_PUSH_MAXREG 72
 #endif
 constexpr int kMaxC = LU_PF_MAX_CTAS_CLUSTER;  // message slots per buffer
-constexpr int kMaxPrev = 16;                   // widest preceding sibling folded into a leaf's prologue
+constexpr int kMaxPrev = 32;                   // widest preceding sibling folded into a leaf's prologue
 
 // Ordering key of a pivot candidate: |a| as an unsigned integer plus one (IEEE
 // order of non-negative values is the integer order of their bits); NaN and
@@ -185,22 +185,34 @@ template <typename T, int W, int RQ, int NT>
 __device__ __noinline__ void leaf_prologue(const T* __restrict__ A, int64_t lda, int row0, int nrows, int w,
                                            int kprev, T* __restrict__ sA, const T* __restrict__ sU) {
     constexpr int WP = W + 1;
+    constexpr int KC = 8;  // multipliers per round; the next round's are loaded during this one
 #pragma unroll 1
     for (int q = 0; q < RQ; ++q) {
         const int r = threadIdx.x + NT * q;
         if (r >= nrows) continue;
-        T l[kMaxPrev];
+        const T* lrow = A + (int64_t)(row0 + r) - (int64_t)kprev * lda;  // L(r, 0)
+        T acc[W];
 #pragma unroll
-        for (int k = 0; k < kMaxPrev; ++k)
-            l[k] = (k < kprev) ? A[(int64_t)(row0 + r) + (int64_t)(k - kprev) * lda] : T(0);
+        for (int c = 0; c < W; ++c) acc[c] = T(0);
+        T lc[KC], ln[KC];
+#pragma unroll
+        for (int kk = 0; kk < KC; ++kk) lc[kk] = (kk < kprev) ? lrow[(int64_t)kk * lda] : T(0);
 #pragma unroll 1
-        for (int c = 0; c < w; ++c) {
-            T acc = T(0);
+        for (int k0 = 0; k0 < kprev; k0 += KC) {
 #pragma unroll
-            for (int k = 0; k < kMaxPrev; ++k)
-                if (k < kprev) acc = fma(l[k], sU[k * (W + 1) + c], acc);
-            sA[r * WP + c] -= acc;
+            for (int kk = 0; kk < KC; ++kk)
+                ln[kk] = (k0 + KC + kk < kprev) ? lrow[(int64_t)(k0 + KC + kk) * lda] : T(0);
+#pragma unroll
+            for (int kk = 0; kk < KC; ++kk)
+                if (k0 + kk < kprev)
+#pragma unroll
+                    for (int c = 0; c < W; ++c) acc[c] = fma(lc[kk], sU[(k0 + kk) * (W + 1) + c], acc[c]);
+#pragma unroll
+            for (int kk = 0; kk < KC; ++kk) lc[kk] = ln[kk];
         }
+#pragma unroll
+        for (int c = 0; c < W; ++c)
+            if (c < w) sA[r * WP + c] -= acc[c];
     }
 }
 
