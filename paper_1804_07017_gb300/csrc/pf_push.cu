@@ -2,20 +2,25 @@
 // (RL1 of LU_blk, Sec. 3: the unblocked LU with partial pivoting of a w-column
 // block of the panel).
 //
-// The leaf's m rows are split across the C <= 16 CTAs of one cluster; each CTA
-// keeps its R x w block in shared memory and the SB columns currently being
-// eliminated in registers (SB = 8 for FP32).  Per column jj:
+// The leaf's m rows are split across the C <= 16 CTAs of one cluster (256 or
+// 512 threads each, every thread holding RQ rows); each CTA keeps its R x w
+// block in shared memory and the SB columns of the current sub-block in
+// registers (SB = 8 for FP32).  Per column jj:
 //   1. every CTA reduces its local pivot candidate (redux.sync first maximum:
-//      largest |a|, then smallest row) and one warp PUSHES a message -- the
-//      candidate's whole leaf row, its ordering key and its row index -- into
-//      every CTA's shared memory with st.async; the owner of row jj pushes that
-//      row too.  Each st.async completes transaction bytes on the receiving
-//      CTA's mbarrier, so a CTA learns that all C candidates have arrived by a
-//      local (bounded) wait: no cluster barrier and no remote loads per column;
+//      largest |a|, then smallest row) and PUSHES a message -- the candidate's
+//      whole leaf row, its ordering key and its row index -- into every CTA's
+//      shared memory with st.async, the pushes shared by all its warps; the
+//      owner of row jj pushes that row too.  Each st.async completes
+//      transaction bytes on the receiving CTA's mbarrier, so a CTA learns that
+//      all C candidates have arrived by a local (bounded) wait: no cluster
+//      barrier and no remote loads per column;
 //   2. every CTA picks the pivot (first maximum over the C keys) from its own
-//      shared memory, swaps rows jj and p where it owns them, divides column jj
-//      by the pivot and applies the rank-1 update to the SB register columns,
-//      fusing the next column's candidate search into the update.
+//      shared memory, swaps rows jj and p where it owns them, scales column jj
+//      (by the reciprocal of the pivot where that is representable, else by
+//      division) and applies the rank-1 update to the register columns,
+//      fusing the next column's candidate search into the update.  The
+//      eliminated column then goes back to shared memory and the register
+//      columns shift down by one, so the column loop is not unrolled.
 // After SB columns the block is right-looking at the sub-block level: the
 // CTA holding rows c0..c0+SB-1 computes U12 = L11^-1 A12 for the remaining
 // leaf columns and pushes it to all CTAs, which apply the rank-SB update
